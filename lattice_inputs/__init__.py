@@ -1,0 +1,239 @@
+"""Seeded synthetic inputs for level-set lattice problems.
+
+This module only draws random numbers and lays them out; it holds none of the
+solver's arithmetic (no basis functions, quadrature, Jacobians or algebra), so
+that the CPU oracle and the GPU library can both consume exactly the same
+inputs without sharing any code of the method itself.
+
+Geometry conventions (shared by every consumer):
+
+* The lattice has ``nx * ny`` cells; cell ``c = cx + nx * cy`` occupies the
+  parametric square ``[0,1]^2`` (Sec. 2.1.1) and is mapped to physical space by
+  a tensor-product Lagrange map of order ``m`` whose nodes are equispaced at
+  ``a/m`` (a = 0..m) in each direction.  The map control points of all cells
+  form one shared grid of ``(m*nx+1) x (m*ny+1)`` points, point
+  ``g = gx + (m*nx+1)*gy``, so neighbouring cells share their edge maps (the
+  untrimmed compatibility condition, Eq. (GEO untrimmed compatibility)).
+* ``mu[c] = (mu_1, mu_2, mu_3, mu_4)``: threshold values at the bottom-left,
+  bottom-right, top-left and top-right corners (Sec. 2.1.2, bilinear
+  threshold).
+* ``family[c]``: 0 = circular hole of radius mu centred in the cell,
+  1 = solid cross of half-width mu.
+* Edges of the lattice boundary are numbered 0 left, 1 right, 2 bottom, 3 top;
+  ``dirichlet_mask`` bit e clamps edge e, ``traction[e]`` is the physical
+  traction per unit length applied on edge e.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FAMILY_CIRCLE = 0
+FAMILY_CROSS = 1
+
+EDGE_LEFT, EDGE_RIGHT, EDGE_BOTTOM, EDGE_TOP = 0, 1, 2, 3
+
+
+@dataclass
+class Lattice:
+    nx: int
+    ny: int
+    p: int                     # polynomial degree of the cell basis
+    m: int                     # order of the geometric map
+    basis: int                 # 0 = GLL Lagrange, 1 = Bernstein
+    ctrl: np.ndarray           # [(m*nx+1)*(m*ny+1), 2] float64
+    mu: np.ndarray             # [nx*ny, 4] float64
+    family: np.ndarray         # [nx*ny] int32
+    E: float = 1.0
+    nu: float = 0.3
+    rho: float = 5e-4
+    dirichlet_mask: int = 1 << EDGE_LEFT
+    traction: np.ndarray = field(default_factory=lambda: np.array(
+        [[0.0, 0.0], [0.0, -1.0], [0.0, 0.0], [0.0, 0.0]]))
+    name: str = ""
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclass
+class RomSpec:
+    """Training recipe of one reduced model (one family, one cluster)."""
+    family: int
+    lo: float
+    hi: float
+    p: int
+    q: int = 2
+    r: int = 6
+    n_r: int = 40
+    n_s: int = 400
+    seed: int = 0
+
+    @property
+    def n_v(self) -> int:
+        return self.n_r + 10
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed), int(stream)])
+
+
+# Independent random streams per purpose.
+STREAM_GEOMETRY, STREAM_MU, STREAM_FAMILY, STREAM_LOADS, STREAM_FD, STREAM_LHS, STREAM_SAMPLE = range(7)
+
+
+def reference_grid(nx: int, ny: int, m: int) -> np.ndarray:
+    """Undeformed control grid: point (gx, gy) sits at (gx/m, gy/m)."""
+    gx, gy = np.meshgrid(np.arange(m * nx + 1) / m, np.arange(m * ny + 1) / m, indexing="xy")
+    return np.stack([gx.ravel(), gy.ravel()], axis=1).astype(np.float64)
+
+
+def smooth_field(X: np.ndarray, seed: int, amplitude: float = 0.1, n_modes: int = 8,
+                 min_wavelength: float = 8.0) -> np.ndarray:
+    """Smooth random displacement d(X) = sum_j a_j (sin(k_j.X+f_j), cos(k'_j.X+f'_j)),
+    rescaled so that max |d| over the given points equals ``amplitude``.
+    Wave numbers are bounded by 2*pi/min_wavelength, so |grad d| stays below
+    amplitude*2*pi/min_wavelength*n_modes-scale bounds and the map stays regular."""
+    g = _rng(seed, STREAM_GEOMETRY)
+    kmax = 2.0 * math.pi / min_wavelength
+    d = np.zeros_like(X)
+    for _ in range(n_modes):
+        a = g.uniform(-1.0, 1.0)
+        th, th2 = g.uniform(0, 2 * math.pi, size=2)
+        kk, kk2 = g.uniform(0.3 * kmax, kmax, size=2)
+        f, f2 = g.uniform(0, 2 * math.pi, size=2)
+        k = kk * np.array([math.cos(th), math.sin(th)])
+        k2 = kk2 * np.array([math.cos(th2), math.sin(th2)])
+        d[:, 0] += a * np.sin(X @ k + f)
+        d[:, 1] += a * np.cos(X @ k2 + f2)
+    nrm = np.sqrt((d ** 2).sum(axis=1)).max()
+    return d * (amplitude / nrm)
+
+
+def vertex_values_to_cells(v: np.ndarray, nx: int, ny: int) -> np.ndarray:
+    """Per-vertex values [(nx+1)*(ny+1)] -> per-cell corner tuples (bl, br, tl, tr)."""
+    V = v.reshape(ny + 1, nx + 1)
+    return np.stack([V[:-1, :-1], V[:-1, 1:], V[1:, :-1], V[1:, 1:]], axis=-1).reshape(nx * ny, 4)
+
+
+def lattice(nx: int, ny: int, p: int, m: int, *, seed: int, basis: int = 0,
+            geometry: str = "smooth", amplitude: float = 0.1, jitter: float = 0.05,
+            mu_mode: str = "graded", mu_range=(0.2, 0.42), cross_range=(0.08, 0.2),
+            cross_fraction: float = 0.0, E: float = 1.0, nu: float = 0.3, rho: float = 5e-4,
+            dirichlet_mask: int = 1 << EDGE_LEFT, name: str = "") -> Lattice:
+    """Build one synthetic lattice.
+
+    geometry: "smooth" (X + smooth random field), "jitter" (uniform vertex
+      jitter, used with m = 1) or "affine" (undeformed grid).
+    mu_mode:  "graded"  vertex thresholds mu_range[0] -> mu_range[1] linearly in x,
+              "uniform" one value per cell drawn from mu_range (or cross_range),
+    cross_fraction: probability that a cell belongs to the cross family.
+    """
+    X = reference_grid(nx, ny, m)
+    if geometry == "smooth":
+        ctrl = X + smooth_field(X, seed, amplitude=amplitude)
+    elif geometry == "jitter":
+        g = _rng(seed, STREAM_GEOMETRY)
+        ctrl = X + g.uniform(-jitter, jitter, size=X.shape)
+    elif geometry == "affine":
+        ctrl = X.copy()
+    else:
+        raise ValueError(geometry)
+
+    n = nx * ny
+    gf = _rng(seed, STREAM_FAMILY)
+    family = (gf.uniform(size=n) < cross_fraction).astype(np.int32)
+
+    gm = _rng(seed, STREAM_MU)
+    if mu_mode == "graded":
+        vx = np.tile(np.arange(nx + 1), ny + 1).astype(np.float64)
+        v = mu_range[0] + (mu_range[1] - mu_range[0]) * vx / nx
+        mu = vertex_values_to_cells(v, nx, ny)
+    elif mu_mode == "uniform":
+        rc = gm.uniform(mu_range[0], mu_range[1], size=n)
+        rx = gm.uniform(cross_range[0], cross_range[1], size=n)
+        r = np.where(family == FAMILY_CROSS, rx, rc)
+        mu = np.repeat(r[:, None], 4, axis=1)
+    else:
+        raise ValueError(mu_mode)
+
+    return Lattice(nx=nx, ny=ny, p=p, m=m, basis=basis, ctrl=np.ascontiguousarray(ctrl),
+                   mu=np.ascontiguousarray(mu, dtype=np.float64), family=family,
+                   E=E, nu=nu, rho=rho, dirichlet_mask=dirichlet_mask, name=name)
+
+
+def config(k: int) -> Lattice:
+    """The five synthetic workloads (seed 1000 + k)."""
+    s = 1000 + k
+    if k == 1:   # 8x8 bilinear jittered cells, circle holes, Bernstein p=4, full quadrature
+        return lattice(8, 8, 4, 1, seed=s, basis=1, geometry="jitter", jitter=0.05,
+                       mu_mode="uniform", mu_range=(0.25, 0.40), rho=1e-6, name="cfg1-8x8-p4-bernstein")
+    if k == 2:   # 64x64 cubic maps, graded circle holes, p=6
+        return lattice(64, 64, 6, 3, seed=s, mu_mode="graded", mu_range=(0.2, 0.42),
+                       name="cfg2-64x64-p6-graded-circle")
+    if k == 3:   # 132x132 quartic maps, 50/50 circle/cross, p=6
+        return lattice(132, 132, 6, 4, seed=s, mu_mode="uniform", mu_range=(0.2, 0.4),
+                       cross_range=(0.08, 0.2), cross_fraction=0.5,
+                       name="cfg3-132x132-p6-circle-cross")
+    if k == 4:   # gradient workload: 64x64 cubic, per-cell radius
+        return lattice(64, 64, 6, 3, seed=s, mu_mode="uniform", mu_range=(0.2, 0.42),
+                       name="cfg4-64x64-p6-circle-R")
+    if k == 5:   # 256x256 quartic maps, graded circle holes, p=8
+        return lattice(256, 256, 8, 4, seed=s, mu_mode="graded", mu_range=(0.2, 0.42),
+                       name="cfg5-256x256-p8-graded-circle")
+    raise ValueError(k)
+
+
+def rom_specs(k: int) -> list[RomSpec]:
+    """ROM training recipes of each workload (one cluster per family)."""
+    s = 2000 + k
+    if k in (2, 4):
+        return [RomSpec(FAMILY_CIRCLE, 0.18, 0.44, p=6, n_r=40, seed=s)]
+    if k == 3:
+        return [RomSpec(FAMILY_CIRCLE, 0.18, 0.42, p=6, n_r=60, seed=s),
+                RomSpec(FAMILY_CROSS, 0.07, 0.21, p=6, n_r=60, seed=s + 100)]
+    if k == 5:
+        return [RomSpec(FAMILY_CIRCLE, 0.18, 0.44, p=8, n_r=80, seed=s)]
+    return []
+
+
+def lhs(n_s: int, lo: float, hi: float, seed: int, dim: int = 4) -> np.ndarray:
+    """Latin hypercube sample of n_s points in [lo, hi]^dim (one point per stratum
+    and dimension, strata permuted independently, uniform jitter inside)."""
+    g = _rng(seed, STREAM_LHS)
+    out = np.empty((n_s, dim))
+    for d in range(dim):
+        perm = g.permutation(n_s)
+        out[:, d] = (perm + g.uniform(size=n_s)) / n_s
+    return lo + (hi - lo) * out
+
+
+def uniform_box(n: int, lo: float, hi: float, seed: int, dim: int = 4) -> np.ndarray:
+    """n independent uniform points in [lo, hi]^dim (held-out test samples)."""
+    return _rng(seed, STREAM_SAMPLE).uniform(lo, hi, size=(n, dim))
+
+
+def traction_sets(n: int, seed: int, magnitude: float = 1.0) -> np.ndarray:
+    """n traction directions for the right edge, rotated by seeded angles:
+    [n, 4, 2] (edge-major, see module doc)."""
+    g = _rng(seed, STREAM_LOADS)
+    ang = g.uniform(0, 2 * math.pi, size=n)
+    out = np.zeros((n, 4, 2))
+    out[:, EDGE_RIGHT, 0] = magnitude * np.sin(ang)
+    out[:, EDGE_RIGHT, 1] = -magnitude * np.cos(ang)
+    return out
+
+
+def directions(n: int, dim: int, seed: int) -> np.ndarray:
+    """n random unit directions in R^dim (finite-difference checks)."""
+    v = _rng(seed, STREAM_FD).standard_normal((n, dim))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def sample_cells(ncells: int, frac: float, seed: int) -> np.ndarray:
+    """Seeded sorted subset of cell indices (e.g. the 1% full-quadrature check)."""
+    k = max(1, int(round(frac * ncells)))
+    return np.sort(_rng(seed, STREAM_SAMPLE).choice(ncells, size=k, replace=False))

@@ -1,0 +1,195 @@
+"""Reduced order model of the fast-assembly tensor (Sec. 4.2, Algorithms 3, 5).
+
+Offline, per level-set family and parameter box M = [lo, hi]^4 (one cluster):
+
+1. snapshots I(mu^s) by full trimmed quadrature at Latin-hypercube samples
+   (Sec. 4.2.2; the samples are drawn by the seeded input module and passed in);
+2. U_r = first n_r left singular vectors of the snapshot matrix (Sec. 4.2.2;
+   the exact truncated SVD, which the paper's randomized SVD approximates);
+3. magic points by Algorithm 3;
+4. I_r(mu_g) at the (r+1)^4 tensor GLL nodes of the box, from the magic-point
+   entries of exactly integrated I(mu_g): U_r[m, :] I_r = I[m]  (Sec. 4.2.3).
+
+Online (Algorithm 5): I(mu) = U_r I_r(mu), with I_r interpolated by degree-r
+tensor Lagrange polynomials on those GLL nodes.
+
+ROM file format (little endian), one family / one cluster per file:
+
+  0   char[8]  "ROMBDDC1"
+  8   int32    version = 1
+  12  int32    family
+  16  int32    basis kind (0 GLL Lagrange, 1 Bernstein)
+  20  int32    p
+  24  int32    q
+  28  int32    r
+  32  int32    n_r
+  36  int32    n_k (clusters per parameter; 1)
+  40  float64  lo
+  48  float64  hi
+  56  int64    n_i
+  64  reserved (zeros) up to byte 128
+  128 float64  I_Pi[n_i]
+      float64  U_r[n_r][n_i]        (basis vector j contiguous)
+      float64  A[n_r][(r+1)^4]      (I_r at grid node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4)))
+      int64    magic[n_r]
+"""
+from __future__ import annotations
+
+import struct
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import assembly, basis, quadrature
+
+MAGIC = b"ROMBDDC1"
+HEADER = 128
+
+
+@dataclass
+class Rom:
+    family: int
+    kind: int
+    p: int
+    q: int
+    r: int
+    lo: float
+    hi: float
+    I_pi: np.ndarray          # [n_i]
+    U: np.ndarray             # [n_i, n_r]
+    A: np.ndarray             # [n_r, (r+1)^4]
+    magic: np.ndarray         # [n_r]
+
+    @property
+    def n_r(self) -> int:
+        return self.U.shape[1]
+
+
+def snapshot(family: int, mu4: np.ndarray, kind: int, p: int, q: int) -> np.ndarray:
+    """I(mu) of Eq. (MDEIM I) by full trimmed quadrature."""
+    n = max(16, p + q // 2 + 4)
+    return assembly.fa_tensor(kind, p, q, quadrature.trimmed_rule(family, mu4, n_out=n, n_in=n))
+
+
+def entries(family: int, mu4: np.ndarray, kind: int, p: int, q: int, idx: np.ndarray) -> np.ndarray:
+    """Selected entries of I(mu) (the magic points), integrated directly."""
+    n = max(16, p + q // 2 + 4)
+    x1, x2, w = quadrature.trimmed_rule(family, mu4, n_out=n, n_in=n)
+    _, dB = basis.basis_2d(kind, p, x1, x2)
+    L = basis.interp_2d(q, x1, x2)
+    nB, nL = dB.shape[2], L.shape[1]
+    out = np.empty(len(idx))
+    for t, m in enumerate(idx):
+        m = int(m)
+        j2 = m % 2
+        j1 = (m // 2) % 2
+        k3 = (m // 4) % nL
+        k2 = (m // (4 * nL)) % nB
+        k1 = m // (4 * nL * nB)
+        out[t] = np.sum(w * dB[:, j1, k1] * dB[:, j2, k2] * L[:, k3])
+    return out
+
+
+def svd_basis(S: np.ndarray, n_r: int) -> tuple[np.ndarray, np.ndarray]:
+    """First n_r left singular vectors and all singular values of the snapshot
+    matrix (columns = snapshots)."""
+    U, s, _ = np.linalg.svd(S, full_matrices=False)
+    return U[:, :n_r], s
+
+
+def magic_points(U: np.ndarray) -> np.ndarray:
+    """Algorithm 3.  m_1 = argmax |U_1|; then for j > 1, U_j minus its
+    projection on span{U_1..U_{j-1}}, and m_j = argmax of the residual.
+
+    The projection is read as the interpolatory one through the magic points
+    already selected (the empirical interpolation step of the cited EIM and
+    DEIM): with orthonormal columns the orthogonal projection would vanish
+    identically.  Ties go to the lowest index."""
+    n_i, n_r = U.shape
+    m = np.empty(n_r, dtype=np.int64)
+    m[0] = int(np.argmax(np.abs(U[:, 0])))
+    for j in range(1, n_r):
+        c = np.linalg.solve(U[m[:j], :j], U[m[:j], j])
+        res = U[:, j] - U[:, :j] @ c
+        m[j] = int(np.argmax(np.abs(res)))
+    return m
+
+
+def mu_nodes(lo: float, hi: float, r: int) -> np.ndarray:
+    """Degree-r GLL nodes of the parameter interval [lo, hi] (Sec. 4.2.3)."""
+    return lo + (hi - lo) * basis.gll_nodes(r)
+
+
+def grid_points(lo: float, hi: float, r: int) -> np.ndarray:
+    """The (r+1)^4 tensor grid, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))."""
+    n = mu_nodes(lo, hi, r)
+    G4, G3, G2, G1 = np.meshgrid(n, n, n, n, indexing="ij")
+    return np.stack([G1.ravel(), G2.ravel(), G3.ravel(), G4.ravel()], axis=1)
+
+
+def train(family: int, kind: int, p: int, q: int, r: int, n_r: int, lo: float, hi: float,
+          samples: np.ndarray, n_v: int | None = None) -> Rom:
+    """Offline phase of Sec. 4.4 for one family and one cluster."""
+    S = np.stack([snapshot(family, mu, kind, p, q) for mu in samples], axis=1)
+    U, _ = svd_basis(S, n_r)
+    magic = magic_points(U)
+    G = grid_points(lo, hi, r)
+    Um = U[magic, :]
+    A = np.empty((n_r, len(G)))
+    for g, mu in enumerate(G):
+        A[:, g] = np.linalg.solve(Um, entries(family, mu, kind, p, q, magic))
+    I_pi = assembly.fa_tensor_untrimmed(kind, p, q)
+    return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic)
+
+
+def find_cluster(rom: Rom, mu4: np.ndarray) -> int:
+    """FindCluster of Algorithm 5 for a single cluster: parameters outside the
+    trained box are rejected (the surrogate is only queried inside it)."""
+    if np.any(mu4 < rom.lo) or np.any(mu4 > rom.hi):
+        raise ValueError(f"threshold {mu4} outside the trained box [{rom.lo}, {rom.hi}]")
+    return 0
+
+
+def reduced_vector(rom: Rom, mu4: np.ndarray) -> np.ndarray:
+    """I_r(mu) by tensor degree-r Lagrange interpolation on the GLL grid."""
+    find_cluster(rom, mu4)
+    nodes = mu_nodes(rom.lo, rom.hi, rom.r)
+    l = [basis.lagrange(nodes, np.array([mu4[d]]))[0][0] for d in range(4)]
+    w = np.einsum("d,c,b,a->dcba", l[3], l[2], l[1], l[0]).ravel()
+    return rom.A @ w
+
+
+def mdeim(rom: Rom, mu4: np.ndarray) -> np.ndarray:
+    """Algorithm 5: I(mu) ~ U_r I_r(mu)."""
+    return rom.U @ reduced_vector(rom, mu4)
+
+
+def write(rom: Rom, path: str) -> None:
+    n_i = rom.U.shape[0]
+    hdr = MAGIC + struct.pack("<8i", 1, rom.family, rom.kind, rom.p, rom.q, rom.r, rom.n_r, 1)
+    hdr += struct.pack("<ddq", rom.lo, rom.hi, n_i)
+    hdr += b"\0" * (HEADER - len(hdr))
+    with open(path, "wb") as f:
+        f.write(hdr)
+        f.write(np.ascontiguousarray(rom.I_pi, dtype="<f8").tobytes())
+        f.write(np.ascontiguousarray(rom.U.T, dtype="<f8").tobytes())
+        f.write(np.ascontiguousarray(rom.A, dtype="<f8").tobytes())
+        f.write(np.ascontiguousarray(rom.magic, dtype="<i8").tobytes())
+
+
+def read(path: str) -> Rom:
+    with open(path, "rb") as f:
+        buf = f.read()
+    if buf[:8] != MAGIC:
+        raise ValueError("not a ROM file")
+    version, family, kind, p, q, r, n_r, n_k = struct.unpack_from("<8i", buf, 8)
+    lo, hi, n_i = struct.unpack_from("<ddq", buf, 40)
+    if version != 1 or n_k != 1:
+        raise ValueError("unsupported ROM file")
+    o = HEADER
+    I_pi = np.frombuffer(buf, "<f8", n_i, o).copy(); o += 8 * n_i
+    U = np.frombuffer(buf, "<f8", n_r * n_i, o).reshape(n_r, n_i).T.copy(); o += 8 * n_r * n_i
+    ng = (r + 1) ** 4
+    A = np.frombuffer(buf, "<f8", n_r * ng, o).reshape(n_r, ng).copy(); o += 8 * n_r * ng
+    magic = np.frombuffer(buf, "<i8", n_r, o).copy()
+    return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic)

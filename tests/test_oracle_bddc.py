@@ -1,0 +1,125 @@
+"""Pins of oracle.bddc (Sec. 3, Algorithms 1-2): brute-force global solves,
+the paper's printed DoF statistics, constraint identities and closed forms."""
+import numpy as np
+import pytest
+
+import lattice_inputs as LI
+from oracle import basis, bddc, geometry, pipeline
+
+
+def _lat(nx, ny, p, cross=0.0, basis_kind=0, m=2, rho=1e-3, seed=7, mask=1):
+    return LI.lattice(nx, ny, p, m, seed=seed, basis=basis_kind, mu_mode="uniform", mu_range=(0.2, 0.35),
+                      cross_range=(0.1, 0.2), cross_fraction=cross, rho=rho, dirichlet_mask=mask)
+
+
+@pytest.mark.parametrize("nx,ny,p,cross,kind,mask", [
+    (1, 1, 3, 0.0, 0, 1), (2, 1, 3, 0.0, 0, 1), (2, 2, 3, 0.5, 0, 1), (3, 3, 3, 0.5, 1, 1),
+    (3, 2, 3, 0.5, 0, 5), (2, 3, 4, 1.0, 0, 1)])
+def test_bddc_matches_direct_solve(nx, ny, p, cross, kind, mask):
+    lat = _lat(nx, ny, p, cross, kind, mask=mask)
+    K = pipeline.matrices_full(lat)
+    f = bddc.lattice_loads(lat)
+    r = pipeline.solve(lat, K, f, rtol=1e-13)
+    ud = bddc.direct_solve(lat, K, f)
+    assert np.linalg.norm(r["u"] - ud) <= 1e-10 * np.linalg.norm(ud)
+
+
+def test_single_cell_is_one_iteration():
+    lat = _lat(1, 1, 3)
+    r = pipeline.solve(lat, pipeline.matrices_full(lat), rtol=1e-12)
+    assert r["iters"] == 1
+
+
+@pytest.mark.parametrize("n2,dofs,coarse", [
+    (32, 263168, 16704), (46, 543168, 34316), (64, 1050624, 66176), (90, 2076480, 130500),
+    (92, 2169728, 136344)])
+def test_dof_statistics_of_the_paper(n2, dofs, coarse):
+    # Table (RES weak) and Sec. 5.1.3: quarter annulus, n1 = 2 n2, p = 8, the
+    # short edge xi1 = 0 clamped.  n_I = 2 (p-1)^2 per cell.
+    p = 8
+    lat = LI.lattice(2 * n2, n2, p, 1, seed=1, geometry="affine", mu_mode="graded")
+    L = bddc.Lattice(lat)
+    n_I = 2 * (p - 1) ** 2 * lat.ncells
+    assert n_I + L.n_U == dofs
+    assert L.n_C == coarse
+    if n2 == 92:
+        assert L.n_U == 510784 and n_I == 1658944
+
+
+def test_coarse_functionals_constant_field():
+    # the edge "averages" of a constant field are the physical edge lengths and
+    # the moment of a translation vanishes on a straight edge
+    p = 4
+    Aff = np.array([[1.3, 0.2], [-0.1, 0.9]])
+    P = geometry.cell_control_points(LI.reference_grid(1, 1, 1), 1, 1, 0, 0) @ Aff.T
+    Q = bddc.coarse_functionals(0, p, P)
+    u = np.tile([1.0, 0.0], (p + 1) ** 2)
+    corners = P.reshape(-1, 2)[[0, 1, 2, 3]]  # bl, br, tl, tr
+    lens = [np.linalg.norm(corners[2] - corners[0]), np.linalg.norm(corners[3] - corners[1]),
+            np.linalg.norm(corners[1] - corners[0]), np.linalg.norm(corners[3] - corners[2])]
+    for e in range(4):
+        assert abs(Q[8 + 3 * e] @ u - lens[e]) < 1e-13
+        assert abs(Q[9 + 3 * e] @ u) < 1e-15
+        assert abs(Q[10 + 3 * e] @ u) < 1e-13
+
+
+def test_curved_edge_length_against_polyline():
+    lat = LI.lattice(1, 1, 3, 3, seed=4, amplitude=0.1)
+    P = geometry.cell_control_points(lat.ctrl, 1, 3, 0, 0)
+    Q = bddc.coarse_functionals(0, 3, P)
+    t = np.linspace(0, 1, 200001)
+    x, _ = geometry.map_eval(P, np.ones_like(t), t)
+    poly = np.sum(np.linalg.norm(np.diff(x, axis=0), axis=1))
+    u = np.tile([0.0, 1.0], 16)
+    assert abs(Q[8 + 3 + 1] @ u - poly) < 1e-9
+
+
+def test_load_resultant_is_traction_times_solid_length():
+    lat = _lat(2, 3, 3, cross=1.0)
+    f = bddc.lattice_loads(lat)
+    tot = f[:, 1::2].sum()
+    ref = 0.0
+    for cy in range(3):
+        c = 1 + 2 * cy
+        P = geometry.cell_control_points(lat.ctrl, 2, lat.m, 1, cy)
+        for (u, v) in bddc.quadrature.edge_solid_intervals(1, lat.mu[c], 1):
+            t = np.linspace(u, v, 100001)
+            x, _ = geometry.map_eval(P, np.ones_like(t), t)
+            ref += np.sum(np.linalg.norm(np.diff(x, axis=0), axis=1))
+    assert abs(tot + ref) < 1e-8
+
+
+def test_coarse_basis_satisfies_constraints():
+    lat = _lat(2, 2, 3, 0.5)
+    B = bddc.Bddc(lat, pipeline.matrices_full(lat), bddc.lattice_loads(lat))
+    for cell in B.cells:
+        assert np.abs(cell["C"] @ cell["Psi"] - np.eye(len(cell["Cg"]))).max() < 1e-10
+    ev = np.linalg.eigvalsh(B.S_C.toarray())
+    assert ev[0] > 0
+
+
+def test_partition_of_unity_sums_to_one():
+    lat = _lat(3, 2, 3, 0.5)
+    B = bddc.Bddc(lat, pipeline.matrices_full(lat), bddc.lattice_loads(lat))
+    s = np.zeros(B.L.n_U)
+    for cell in B.cells:
+        np.add.at(s, cell["Ug"], cell["D"])
+    assert np.abs(s - 1).max() < 1e-14
+
+
+def test_basis_change_gives_same_field():
+    # GLL-Lagrange and Bernstein span the same space: same converged field
+    def field(kind):
+        lat = _lat(2, 2, 3, 0.0, kind, m=1)
+        r = pipeline.solve(lat, pipeline.matrices_full(lat), rtol=1e-13)
+        L = bddc.Lattice(lat)
+        pts = np.linspace(0.1, 0.9, 5)
+        out = []
+        for cy in range(2):
+            for cx in range(2):
+                g = L.cell_global_nodes(cx, cy)
+                B, _ = basis.basis_2d(kind, 3, np.repeat(pts, 5), np.tile(pts, 5))
+                out.append(B @ r["u"][g])
+        return np.array(out)
+    a, b = field(0), field(1)
+    assert np.abs(a - b).max() < 1e-9 * np.abs(a).max()

@@ -1,0 +1,73 @@
+"""Pins of oracle.rom (Sec. 4.2, Algorithms 3 and 5)."""
+import numpy as np
+import pytest
+
+import lattice_inputs as LI
+from oracle import assembly, quadrature, rom
+
+
+@pytest.fixture(scope="module")
+def small_rom():
+    S = LI.lhs(24, 0.2, 0.34, seed=11)
+    return rom.train(0, 0, 2, 2, 2, 12, 0.2, 0.34, S)
+
+
+def test_basis_orthonormal_and_magic_distinct(small_rom):
+    U = small_rom.U
+    assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-12
+    assert len(set(small_rom.magic.tolist())) == len(small_rom.magic)
+    # the interpolation matrix at the magic points is well posed
+    assert np.linalg.cond(U[small_rom.magic]) < 1e8
+
+
+def test_magic_points_first_is_argmax(small_rom):
+    assert small_rom.magic[0] == np.argmax(np.abs(small_rom.U[:, 0]))
+
+
+def test_interpolation_exact_at_grid_nodes(small_rom):
+    # at a GLL grid node the online interpolant returns the offline I_r, which
+    # matches the exact I at the magic points (Sec. 4.2.3)
+    G = rom.grid_points(small_rom.lo, small_rom.hi, small_rom.r)
+    for g in [0, 13, 40, 80]:
+        I = rom.snapshot(0, G[g], 0, 2, 2)
+        Ir = rom.mdeim(small_rom, G[g])
+        assert np.abs(Ir[small_rom.magic] - I[small_rom.magic]).max() < 1e-13
+
+
+def test_entries_decode(small_rom):
+    mu = np.array([0.22, 0.3, 0.25, 0.31])
+    I = rom.snapshot(0, mu, 0, 2, 2)
+    idx = np.array([0, 5, 123, len(I) - 1])
+    assert np.allclose(rom.entries(0, mu, 0, 2, 2, idx), I[idx], rtol=1e-13, atol=1e-15)
+
+
+def test_heldout_projection_error(small_rom):
+    # held-out ROM error indicator (Sec. 5.1.2) is small for a smooth family
+    for mu in LI.uniform_box(3, 0.2, 0.34, seed=5):
+        I = rom.snapshot(0, mu, 0, 2, 2)
+        err = np.abs(rom.mdeim(small_rom, mu) - I).max() / np.abs(I).max()
+        assert err < 1e-2
+
+
+def test_out_of_box_rejected(small_rom):
+    with pytest.raises(ValueError):
+        rom.reduced_vector(small_rom, np.array([0.1, 0.3, 0.3, 0.3]))
+
+
+def test_roundtrip(tmp_path, small_rom):
+    path = str(tmp_path / "r.rom")
+    rom.write(small_rom, path)
+    R = rom.read(path)
+    assert np.array_equal(R.U, small_rom.U) and np.array_equal(R.A, small_rom.A)
+    assert np.array_equal(R.magic, small_rom.magic) and np.array_equal(R.I_pi, small_rom.I_pi)
+    assert (R.p, R.q, R.r, R.lo, R.hi) == (2, 2, 2, 0.2, 0.34)
+
+
+def test_full_rank_rom_is_exact_on_training_snapshots():
+    # with n_r = n_s the basis spans every snapshot: projecting a training
+    # snapshot through the magic points reproduces it
+    S = LI.lhs(6, 0.2, 0.34, seed=3)
+    R = rom.train(0, 0, 2, 2, 1, 6, 0.2, 0.34, S)
+    I = rom.snapshot(0, S[2], 0, 2, 2)
+    Ir = np.linalg.solve(R.U[R.magic], I[R.magic])
+    assert np.abs(R.U @ Ir - I).max() < 1e-12 * np.abs(I).max()
