@@ -1,0 +1,181 @@
+/*
+ * romb.h -- C ABI of the GB300 library for the ROM-accelerated BDDC solver of
+ * unfitted p-FEM level-set lattices (Bonilla Moreno, Guarino, Antolin,
+ * arXiv 2604.09113).
+ *
+ * The library owns every device buffer it needs; the caller passes plain host
+ * (or, where stated, device) pointers and sizes.  All calls enqueue work on the
+ * context's CUDA stream.  Calls that return data to host memory synchronise that
+ * stream before returning.  Every call returns a romb_status; a failed call
+ * leaves the context usable (unless the status is ROMB_E_CUDA after a sticky
+ * device error).
+ *
+ * Call order (anything else returns ROMB_E_STATE):
+ *   romb_create -> romb_train_load (one per level-set family)
+ *     -> romb_assemble | romb_assemble_host_K -> romb_factor
+ *     -> romb_bddc_solve (any number of times) -> romb_destroy.
+ *
+ * Conventions shared by every call
+ *  - Lattice of nx*ny cells, cell c = cx + nx*cy, each cell the parametric unit
+ *    square (Sec. 2.1.1) mapped by a tensor-product Lagrange map of order m on
+ *    equispaced nodes a/m, a = 0..m.  The map control points of all cells form
+ *    one grid of (m*nx+1) x (m*ny+1) points g = gx + (m*nx+1)*gy, so shared
+ *    edges have shared maps (Eq. GEO untrimmed compatibility).
+ *  - Thresholds mu[c][0..3] at the bottom-left, bottom-right, top-left and
+ *    top-right corners, interpolated bilinearly (Sec. 2.1.2).
+ *  - Families: 0 circle hole (solid where |xi - (1/2,1/2)| > mu(xi)),
+ *    1 solid cross (solid where min(|xi1 - 1/2|, |xi2 - 1/2|) < mu(xi)).
+ *  - Cell basis: degree-p tensor polynomials on GLL nodes (Sec. 2.2.2) or
+ *    Bernstein polynomials; local node k = a + (p+1) b, local DoF 2k + i.
+ *  - Displacements are returned on the global node grid (p*nx+1) x (p*ny+1),
+ *    node n = gx + (p*nx+1) gy, as u[n][2] (for the Bernstein basis these are
+ *    the basis coefficients at the same grid positions).
+ *  - Lattice edges 0 left, 1 right, 2 bottom, 3 top.
+ */
+#ifndef ROMB_H
+#define ROMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct romb_ctx romb_ctx;
+
+typedef enum {
+  ROMB_OK = 0,
+  ROMB_E_ARG = -1,            /* invalid argument or unsupported size          */
+  ROMB_E_CUDA = -2,           /* CUDA runtime error                            */
+  ROMB_E_OOM = -3,            /* device allocation failed or budget exceeded   */
+  ROMB_E_OUT_OF_BOX = -4,     /* a threshold lies outside its ROM's box        */
+  ROMB_E_BAD_MAP = -5,        /* det J <= 0 at an interpolation node           */
+  ROMB_E_NOT_SPD = -6,        /* non-positive pivot in a local or coarse factor */
+  ROMB_E_NOT_CONVERGED = -7,  /* PCG reached maxit (u_out holds the last iterate) */
+  ROMB_E_NAN = -8,            /* non-finite value detected                     */
+  ROMB_E_FORMAT = -9,         /* malformed ROM file                            */
+  ROMB_E_STATE = -10          /* call out of order                             */
+} romb_status;
+
+typedef enum {
+  ROMB_FP64 = 0,        /* assembly contraction in FP64 on the CUDA cores          */
+  ROMB_FP32_SPLIT = 1,  /* tcgen05 kind::tf32, 3-term hi/lo split, FP32 accumulate */
+  ROMB_BF16_SPLIT = 2   /* tcgen05 kind::f16 (bf16), 3-term split, FP32 accumulate */
+} romb_precision;
+
+typedef enum { ROMB_MEM_HOST = 0, ROMB_MEM_DEVICE = 1 } romb_mem;
+
+/* Problem statement of Sec. 2.2.1: geometry (maps + level sets + thresholds),
+ * material, loads and Dirichlet constraints.  Pointers follow `mem`: host
+ * memory (copied to the device during the call) or device memory on the
+ * context's device (read in place, must stay valid until romb_factor returns). */
+typedef struct {
+  int nx, ny;              /* cells per direction, >= 1                          */
+  int p;                   /* polynomial degree of the cell basis, 3..8          */
+  int map_order;           /* m, 1..4                                            */
+  int basis;               /* 0 GLL Lagrange, 1 Bernstein                        */
+  int mem;                 /* romb_mem of every pointer below (and of u_out)     */
+  const double* ctrl;      /* [(m*nx+1)*(m*ny+1)][2] map control points          */
+  const double* mu;        /* [nx*ny][4] corner thresholds                       */
+  const int32_t* family;   /* [nx*ny] family id of a loaded ROM                  */
+  double E, nu;            /* Young modulus, Poisson ratio (plane stress)        */
+  double rho;              /* alpha-stabilisation factor, Eq. (MOD stabilization) */
+  unsigned dirichlet_mask; /* bit e: lattice edge e clamped (u = 0, strong)      */
+  const double* traction;  /* [4][2] physical traction per unit length per edge, */
+                           /* applied on the solid (conformal) part of the edge  */
+} romb_lattice;
+
+/* Create a context on `device`.  `cuda_stream` is a cudaStream_t owned by the
+ * caller (NULL: the library creates its own).  mem_budget_bytes caps the
+ * device memory the context may hold (0: no cap). */
+romb_status romb_create(romb_ctx** ctx, int device, size_t mem_budget_bytes, void* cuda_stream);
+void romb_destroy(romb_ctx* ctx);
+const char* romb_strerror(romb_status s);
+
+/* Load one trained reduced model (Sec. 4.2, offline phase of Sec. 4.4) and keep
+ * it resident in HBM.  File format: 128-byte header "ROMBDDC1", int32 version 1,
+ * family, basis, p, q, r, n_r, n_k=1, float64 lo, hi, int64 n_i; then float64
+ * I_Pi[n_i], U_r[n_r][n_i], A[n_r][(r+1)^4] (I_r at the tensor GLL nodes of
+ * [lo,hi]^4, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64 magic[n_r].
+ * The fast-assembly vector is I[((k1*nB+k2)*nL+k3)*4 + 2*j1 + j2] (Eq. MDEIM I).
+ * *family_out receives the file's family id.  Errors: ROMB_E_FORMAT. */
+romb_status romb_train_load(romb_ctx* ctx, const char* rom_path, int* family_out);
+
+/* Online assembly of every cell stiffness matrix (Algorithms 4 and 5):
+ * theta = ((1-rho) I_r(mu), rho) from the MDEIM interpolation of the cell's
+ * family, Chat at the (q+1)^2 interpolation nodes (Eq. FAST interpolation), and
+ * the contraction K = sum_{j1 j2 k3} [U_r I_r (1-rho) + rho I_Pi] C.
+ * Errors: ROMB_E_OUT_OF_BOX, ROMB_E_BAD_MAP (per-cell flags via romb_stats). */
+romb_status romb_assemble(romb_ctx* ctx, const romb_lattice* lat, romb_precision prec);
+
+/* As romb_assemble, but with caller-supplied dense cell matrices
+ * K[nx*ny][ndof][ndof] (ndof = 2 (p+1)^2, local DoF 2k+i), e.g. from full
+ * trimmed quadrature (the unaccelerated baseline of Sec. 5.1). */
+romb_status romb_assemble_host_K(romb_ctx* ctx, const romb_lattice* lat, const double* K);
+
+/* BDDC set-up (Sec. 3): per cell the Cholesky factor of K_II and the Schur
+ * complement S = K_UU - K_UI K_II^-1 K_IU, the constrained-Neumann factors of
+ * Algorithm 2, the coarse basis Psi of Eq. (BDDC local basis), the stiffness
+ * partition of unity D, the explicit fine operator D F D and the local coarse
+ * matrix Psi^T S Psi; then the assembly of S_C and its sparse Cholesky factor
+ * (nested dissection).  Errors: ROMB_E_NOT_SPD. */
+romb_status romb_factor(romb_ctx* ctx);
+
+/* PCG on the Schur system S u = f (Eq. BDDC system) preconditioned by
+ * S_BDDC^-1 (Eq. BDDC preconditioner, Algorithm 1), x0 = 0, stopping when
+ * ||r||_2 <= rtol ||f||_2; then interior recovery u_I = K_II^-1 (f_I - K_IU u).
+ * traction_sets: [nrhs][4][2] (NULL: the lattice's traction, nrhs must be 1).
+ * u_out: [nrhs][(p*nx+1)*(p*ny+1)][2] in the lattice's memory kind;
+ * iters_out, relres_out: [nrhs] host arrays (may be NULL).
+ * Errors: ROMB_E_NOT_CONVERGED (u_out holds the last iterate). */
+romb_status romb_bddc_solve(romb_ctx* ctx, int nrhs, const double* traction_sets, double rtol,
+                            int maxit, double* u_out, int* iters_out, double* relres_out);
+
+/* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
+ * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
+ * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits
+ * (1 out of box, 2 bad map, 4 not SPD, 8 non-finite); either may be NULL. */
+romb_status romb_stats(romb_ctx* ctx, double* phase_ms, int* flags_out);
+
+/* Copy an internal per-cell array to host memory (inspection and testing).
+ * `bytes` must equal the field's size; see romb_field_bytes. */
+typedef enum {
+  ROMB_FIELD_CHAT = 0,     /* [cells][(q+1)^2][2][2][2][2] f64: C_{i1 j1 i2 j2 k}     */
+  ROMB_FIELD_THETA = 1,    /* [cells][n_r+1] f64: (rho, (1-rho) I_r(mu))            */
+  ROMB_FIELD_K = 2,        /* [cells][ndof(ndof+1)/2] f64: K, packed upper, row-major */
+  ROMB_FIELD_S = 3,        /* [cells][nU*(nU+1)/2] f64: Schur complement, packed     */
+  ROMB_FIELD_PSI = 4,      /* [cells][nU][20] f64: coarse basis (absent slots zero)  */
+  ROMB_FIELD_SC_LOCAL = 5, /* [cells][20][20] f64: Psi^T S Psi                       */
+  ROMB_FIELD_D = 6,        /* [cells][nU] f64: partition of unity                    */
+  ROMB_FIELD_FINE = 7,     /* [cells][nU*(nU+1)/2] f64: D F D, packed                */
+  ROMB_FIELD_FLAGS = 8     /* [cells] int32                                          */
+} romb_field;
+size_t romb_field_bytes(romb_ctx* ctx, int field);
+romb_status romb_read(romb_ctx* ctx, int field, void* out, size_t bytes);
+
+/* Offline ROM training (Sec. 4.2 and the offline phase of Sec. 4.4), on the
+ * host CPU: snapshots I(mu_s) of Eq. (MDEIM I) at the given threshold samples
+ * (e.g. a Latin hypercube in [lo,hi]^4), the leading n_r left singular vectors,
+ * the magic points of Algorithm 3 and the I_r samples on the (r+1)^4 tensor
+ * GLL grid of the box; written as a ROM file (format above).  samples:
+ * [n_s][4] host array; n_threads host threads (0: all cores).
+ * Errors: ROMB_E_ARG (bad spec, n_r > n_s, unwritable path), ROMB_E_NAN. */
+typedef struct {
+  int family;     /* 0 circle hole, 1 cross                   */
+  int basis;      /* 0 GLL Lagrange, 1 Bernstein              */
+  int p, q, r;    /* cell degree (3..8), q = 2, grid degree r */
+  int n_r;        /* reduced basis size                       */
+  int n_threads;
+  double lo, hi;  /* parameter box [lo, hi]^4                 */
+} romb_train_spec;
+romb_status romb_train(const romb_train_spec* spec, const double* samples, int n_s, const char* rom_path);
+
+/* One fast-assembly snapshot I(mu) (Eq. MDEIM I) by the trainer's quadrature:
+ * I_out[n_i], n_i = (p+1)^4 (q+1)^2 4, layout as in the ROM file. */
+romb_status romb_train_snapshot(const romb_train_spec* spec, const double* mu4, double* I_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROMB_H */

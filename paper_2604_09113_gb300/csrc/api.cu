@@ -1,0 +1,661 @@
+// C-ABI entry points of romb: context, memory, ROM loading, lattice set-up and
+// the orchestration of the online phase (Sec. 4.4): assemble -> factor -> solve.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "romb_internal.cuh"
+#include "tables.cuh"
+
+static thread_local std::string g_err;
+void romb_set_error(const std::string& s) { g_err = s; }
+
+extern "C" const char* romb_strerror(romb_status s) {
+  switch (s) {
+    case ROMB_OK: return "ok";
+    case ROMB_E_ARG: return "invalid argument";
+    case ROMB_E_CUDA: return g_err.empty() ? "CUDA error" : g_err.c_str();
+    case ROMB_E_OOM: return "out of device memory or budget";
+    case ROMB_E_OUT_OF_BOX: return "threshold outside the trained ROM box";
+    case ROMB_E_BAD_MAP: return "non-positive Jacobian determinant at an interpolation node";
+    case ROMB_E_NOT_SPD: return "non-positive pivot in a Cholesky factorisation";
+    case ROMB_E_NOT_CONVERGED: return "PCG did not converge within maxit";
+    case ROMB_E_NAN: return "non-finite value";
+    case ROMB_E_FORMAT: return "malformed ROM file";
+    case ROMB_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+static romb_status alloc_into(romb_ctx* c, void** p, size_t bytes, std::vector<void*>& list) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->budget && c->used + bytes > c->budget) return ROMB_E_OOM;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return ROMB_E_OOM;
+  }
+  c->used += bytes;
+  c->sizes[*p] = bytes;
+  if (&list == &c->rom_allocs) c->rom_bytes += bytes;
+  list.push_back(*p);
+  return ROMB_OK;
+}
+
+romb_status romb_alloc(romb_ctx* c, void** p, size_t bytes) { return alloc_into(c, p, bytes, c->allocs); }
+romb_status romb_alloc_persist(romb_ctx* c, void** p, size_t bytes) {
+  return alloc_into(c, p, bytes, c->rom_allocs);
+}
+
+static void romb_free_ptr(romb_ctx* c, void* p) {
+  if (!p) return;
+  for (auto* list : {&c->allocs, &c->rom_allocs}) {
+    auto it = std::find(list->begin(), list->end(), p);
+    if (it != list->end()) {
+      if (list == &c->rom_allocs) c->rom_bytes -= c->sizes[p];
+      list->erase(it);
+    }
+  }
+  c->used -= c->sizes[p];
+  c->sizes.erase(p);
+  cudaFree(p);
+}
+
+// Free every lattice-dependent buffer (the loaded ROMs stay).
+void romb_free_lattice(romb_ctx* c) {
+  for (void* p : c->allocs) {
+    cudaFree(p);
+    c->sizes.erase(p);
+  }
+  c->allocs.clear();
+  auto sizes = c->sizes;
+  const size_t rom_bytes = c->rom_bytes;
+  RombRom roms[ROMB_MAX_FAMILIES];
+  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) roms[i] = c->roms[i];
+  std::vector<void*> keep = c->rom_allocs;
+  cudaStream_t st = c->stream;
+  bool own = c->own_stream;
+  int dev = c->device, sms = c->sms;
+  size_t budget = c->budget;
+  double* h_red = c->h_red;
+  cudaEvent_t ev[16];
+  for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
+  *c = romb_ctx();
+  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->roms[i] = roms[i];
+  c->rom_allocs = keep;
+  c->stream = st;
+  c->own_stream = own;
+  c->device = dev;
+  c->sms = sms;
+  c->budget = budget;
+  c->h_red = h_red;
+  for (int i = 0; i < 16; ++i) c->ev[i] = ev[i];
+  c->sizes = sizes;
+  c->rom_bytes = rom_bytes;
+  c->used = rom_bytes;
+}
+
+void romb_free_all(romb_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->rom_allocs) cudaFree(p);
+  c->allocs.clear();
+  c->rom_allocs.clear();
+  c->used = 0;
+}
+
+extern "C" romb_status romb_create(romb_ctx** out, int device, size_t budget, void* stream) {
+  if (!out) return ROMB_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    (void)cudaGetLastError();
+    romb_set_error("no CUDA device");
+    return ROMB_E_CUDA;
+  }
+  ROMB_CUDA(cudaSetDevice(device));
+  romb_ctx* c = new romb_ctx();
+  c->device = device;
+  c->budget = budget;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return ROMB_E_CUDA;
+    }
+    c->own_stream = true;
+  }
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  if (cudaMallocHost(&c->h_red, 64 * sizeof(double)) != cudaSuccess) {
+    delete c;
+    return ROMB_E_OOM;
+  }
+  *out = c;
+  return ROMB_OK;
+}
+
+extern "C" void romb_destroy(romb_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  romb_free_all(c);
+  for (int l = 0; l < (int)c->nd.d_level_fronts.size(); ++l) c->nd.d_level_fronts[l] = nullptr;
+  for (auto& e : c->ev) cudaEventDestroy(e);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// ROM loading
+// ---------------------------------------------------------------------------
+static bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
+
+extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* family_out) {
+  if (!c || !path) return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  FILE* f = fopen(path, "rb");
+  if (!f) return ROMB_E_ARG;
+  unsigned char hdr[128];
+  if (!rd(f, hdr, 128) || memcmp(hdr, "ROMBDDC1", 8) != 0) {
+    fclose(f);
+    return ROMB_E_FORMAT;
+  }
+  int32_t iv[8];
+  double lohi[2];
+  int64_t n_i;
+  memcpy(iv, hdr + 8, 32);
+  memcpy(lohi, hdr + 40, 16);
+  memcpy(&n_i, hdr + 56, 8);
+  const int version = iv[0], family = iv[1], kind = iv[2], p = iv[3], q = iv[4], r = iv[5], n_r = iv[6],
+            n_k = iv[7];
+  const int nB = (p + 1) * (p + 1), nL = (q + 1) * (q + 1);
+  if (version != 1 || n_k != 1 || family < 0 || family >= ROMB_MAX_FAMILIES || p < 3 || p > ROMB_MAX_P ||
+      q != 2 || r < 1 || r > 10 || n_r < 1 || n_r > 127 || n_i != (int64_t)nB * nB * nL * 4 ||
+      !(lohi[1] > lohi[0])) {
+    fclose(f);
+    return ROMB_E_FORMAT;
+  }
+  const long long ng = 1;
+  long long ngrid = ng;
+  for (int d = 0; d < 4; ++d) ngrid *= (r + 1);
+  std::vector<double> Ipi(n_i), U((size_t)n_r * n_i), A((size_t)n_r * ngrid);
+  bool ok = rd(f, Ipi.data(), 8 * n_i) && rd(f, U.data(), 8 * (size_t)n_r * n_i) &&
+            rd(f, A.data(), 8 * (size_t)n_r * ngrid);
+  fclose(f);
+  if (!ok) return ROMB_E_FORMAT;
+
+  // Rearrange into the pair-major half layout used by the contraction: row t of
+  // U' is I_Pi (t = 0) or U_r column t-1; column (pair(k1<=k2), k3, j1, j2).
+  const long long npairs = (long long)nB * (nB + 1) / 2;
+  const long long n_half = npairs * nL * 4;
+  const int K = n_r + 1;
+  std::vector<double> Uh((size_t)K * n_half);
+  long long pr = 0;
+  for (int k1 = 0; k1 < nB; ++k1)
+    for (int k2 = k1; k2 < nB; ++k2, ++pr)
+      for (int e = 0; e < nL * 4; ++e) {
+        const long long src = ((long long)k1 * nB + k2) * nL * 4 + e;
+        const long long dst = pr * nL * 4 + e;
+        Uh[dst] = Ipi[src];
+        for (int t = 0; t < n_r; ++t) Uh[(size_t)(t + 1) * n_half + dst] = U[(size_t)t * n_i + src];
+      }
+
+  RombRom& R = c->roms[family];
+  if (R.loaded) {
+    romb_free_ptr(c, R.U64);
+    romb_free_ptr(c, R.Uhi);
+    romb_free_ptr(c, R.Ulo);
+    romb_free_ptr(c, R.A);
+    romb_free_ptr(c, R.At);
+    R = RombRom();
+  }
+  romb_status s;
+  if ((s = romb_alloc_persist(c, (void**)&R.U64, 8 * Uh.size())) != ROMB_OK) return s;
+  if ((s = romb_alloc_persist(c, (void**)&R.A, 8 * A.size())) != ROMB_OK) return s;
+  if ((s = romb_alloc_persist(c, (void**)&R.At, 8 * A.size())) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpy(R.U64, Uh.data(), 8 * Uh.size(), cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(R.A, A.data(), 8 * A.size(), cudaMemcpyHostToDevice));
+  {
+    std::vector<double> At(A.size());
+    for (long long g = 0; g < ngrid; ++g)
+      for (int t = 0; t < n_r; ++t) At[(size_t)g * n_r + t] = A[(size_t)t * ngrid + g];
+    ROMB_CUDA(cudaMemcpy(R.At, At.data(), 8 * At.size(), cudaMemcpyHostToDevice));
+  }
+  R.kpad = (K + 7) / 8 * 8;
+  {
+    // tensor-core operands: hi/lo FP32 split of U', K padded with zero rows
+    std::vector<float> hi((size_t)R.kpad * n_half, 0.f), lo((size_t)R.kpad * n_half, 0.f);
+    for (size_t i = 0; i < Uh.size(); ++i) {
+      float h = tf32_round((float)Uh[i]);
+      hi[i] = h;
+      lo[i] = tf32_round((float)(Uh[i] - (double)h));
+    }
+    if ((s = romb_alloc_persist(c, (void**)&R.Uhi, 4 * hi.size())) != ROMB_OK) return s;
+    if ((s = romb_alloc_persist(c, (void**)&R.Ulo, 4 * lo.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(R.Uhi, hi.data(), 4 * hi.size(), cudaMemcpyHostToDevice));
+    ROMB_CUDA(cudaMemcpy(R.Ulo, lo.data(), 4 * lo.size(), cudaMemcpyHostToDevice));
+  }
+  R.loaded = true;
+  R.family = family;
+  R.kind = kind;
+  R.p = p;
+  R.q = q;
+  R.r = r;
+  R.n_r = n_r;
+  R.lo = lohi[0];
+  R.hi = lohi[1];
+  R.n_half = n_half;
+  if (family_out) *family_out = family;
+  return ROMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lattice set-up: copies inputs, builds structural index tables
+// ---------------------------------------------------------------------------
+static romb_status setup_lattice(romb_ctx* c, const romb_lattice* L) {
+  if (!L || L->nx < 1 || L->ny < 1 || L->p < 3 || L->p > ROMB_MAX_P || L->map_order < 1 ||
+      L->map_order > 4 || (L->basis != 0 && L->basis != 1) || !L->ctrl || !L->mu || !L->family ||
+      (L->mem != ROMB_MEM_HOST && L->mem != ROMB_MEM_DEVICE) || !(L->rho >= 0.0) || !(L->E > 0) ||
+      !(L->nu > -1.0 && L->nu < 0.5))
+    return ROMB_E_ARG;
+  const long long cells = (long long)L->nx * L->ny;
+  if (cells > (1LL << 22)) return ROMB_E_ARG;
+  const bool same = c->have_lattice && c->nx == L->nx && c->ny == L->ny && c->p == L->p &&
+                    c->m == L->map_order && c->dmask == L->dirichlet_mask;
+  if (!same) {
+    romb_free_lattice(c);
+    return ROMB_E_STATE;
+  }
+  return ROMB_OK;
+}
+
+static romb_status build_tables(romb_ctx* c) {
+  romb_status s;
+  const int p = c->p, nx = c->nx, ny = c->ny, nB = c->nB, nU = c->nU, nI = c->nI;
+  const long long cells = c->ncells;
+  // local slot tables
+  LocalTables T = make_local_tables(p);
+  ROMB_CUDA(cudaMemcpy(c->d_islot, T.islot, sizeof(int) * nI, cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(c->d_uslot, T.uslot, sizeof(int) * nU, cudaMemcpyHostToDevice));
+  // skeleton map per cell, coarse map per cell
+  std::vector<int> umap((size_t)cells * nU), cmap((size_t)cells * ROMB_NSLOT);
+  const long long NH = (long long)(ny + 1) * (p * nx + 1);
+  auto dir_node = [&](int gx, int gy) {
+    return ((c->dmask & 1) && gx == 0) || ((c->dmask & 2) && gx == p * nx) || ((c->dmask & 4) && gy == 0) ||
+           ((c->dmask & 8) && gy == p * ny);
+  };
+  const long long NCV = 2LL * (nx + 1) * (ny + 1), NCH = 3LL * nx * (ny + 1);
+  for (int cy = 0; cy < ny; ++cy)
+    for (int cx = 0; cx < nx; ++cx) {
+      const long long cell = cx + (long long)nx * cy;
+      for (int u = 0; u < nU; ++u) {
+        const int k = T.uslot[u] / 2, comp = T.uslot[u] % 2;
+        const int a = k % (p + 1), b = k / (p + 1);
+        const int gx = p * cx + a, gy = p * cy + b;
+        long long id;
+        if (gy % p == 0) id = (long long)(gy / p) * (p * nx + 1) + gx;
+        else id = NH + ((long long)cy * (nx + 1) + gx / p) * (p - 1) + (b - 1);
+        umap[cell * nU + u] = dir_node(gx, gy) ? -1 : (int)(2 * id + comp);
+      }
+      int* cm = &cmap[cell * ROMB_NSLOT];
+      const int vxs[4] = {cx, cx + 1, cx, cx + 1}, vys[4] = {cy, cy, cy + 1, cy + 1};
+      for (int v = 0; v < 4; ++v) {
+        const bool d = dir_node(p * vxs[v], p * vys[v]);
+        const long long base = 2LL * ((long long)vys[v] * (nx + 1) + vxs[v]);
+        cm[2 * v] = d ? -1 : (int)base;
+        cm[2 * v + 1] = d ? -1 : (int)(base + 1);
+      }
+      // edges: left (vx=cx), right (vx=cx+1), bottom (vy=cy), top (vy=cy+1)
+      for (int e = 0; e < 4; ++e) {
+        long long base;
+        bool d;
+        if (e < 2) {
+          const int vx = cx + e;
+          d = (vx == 0 && (c->dmask & 1)) || (vx == nx && (c->dmask & 2));
+          base = NCV + NCH + 3LL * ((long long)cy * (nx + 1) + vx);
+        } else {
+          const int vy = cy + (e - 2);
+          d = (vy == 0 && (c->dmask & 4)) || (vy == ny && (c->dmask & 8));
+          base = NCV + 3LL * ((long long)vy * nx + cx);
+        }
+        for (int t = 0; t < 3; ++t) cm[8 + 3 * e + t] = d ? -1 : (int)(base + t);
+      }
+    }
+  ROMB_CUDA(cudaMemcpy(c->d_ucell_map, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(c->d_cmap, cmap.data(), sizeof(int) * cmap.size(), cudaMemcpyHostToDevice));
+  c->ncoarse_all = NCV + NCH + 3LL * (nx + 1) * ny;
+  {
+    // owners of every coarse DoF, in increasing cell order
+    std::vector<int> own((size_t)c->ncoarse_all * 4, -1);
+    std::vector<int> cnt((size_t)c->ncoarse_all, 0);
+    for (long long cell = 0; cell < cells; ++cell)
+      for (int j = 0; j < ROMB_NSLOT; ++j) {
+        const int g = cmap[cell * ROMB_NSLOT + j];
+        if (g < 0) continue;
+        if (cnt[g] >= 4) return ROMB_E_ARG;
+        own[(size_t)g * 4 + cnt[g]++] = (int)(cell * ROMB_NSLOT + j);
+      }
+    ROMB_CUDA(cudaMemcpy(c->d_cowner, own.data(), sizeof(int) * own.size(), cudaMemcpyHostToDevice));
+  }
+  if ((s = coarse_build(c)) != ROMB_OK) return s;
+  return ROMB_OK;
+}
+
+static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
+  romb_status s;
+  c->nx = L->nx;
+  c->ny = L->ny;
+  c->p = L->p;
+  c->m = L->map_order;
+  c->dmask = L->dirichlet_mask;
+  c->ncells = L->nx * L->ny;
+  c->nB = (c->p + 1) * (c->p + 1);
+  c->ndof = 2 * c->nB;
+  c->nI = 2 * (c->p - 1) * (c->p - 1);
+  c->nU = 8 * c->p;
+  c->kpack = tri(c->ndof);
+  c->upack = tri(c->nU);
+  const long long cells = c->ncells;
+  const int p = c->p, nx = c->nx, ny = c->ny;
+  const long long nctrl = (long long)(c->m * nx + 1) * (c->m * ny + 1);
+  c->nskel_nodes = (long long)(ny + 1) * (p * nx + 1) + (long long)ny * (nx + 1) * (p - 1);
+  c->nskel = 2 * c->nskel_nodes;
+  const long long nodes = (long long)(p * nx + 1) * (p * ny + 1);
+#define A_(ptr, n)                                          \
+  if ((s = romb_alloc_t(c, &(ptr), (size_t)(n))) != ROMB_OK) \
+    return s;
+  A_(c->d_ctrl, 2 * nctrl);
+  A_(c->d_mu, 4 * cells);
+  A_(c->d_family, cells);
+  A_(c->d_flags, cells);
+  A_(c->d_chat, cells * 9 * 16);
+  A_(c->d_theta, cells * 128);
+  A_(c->d_theta_hi, cells * 128);
+  A_(c->d_theta_lo, cells * 128);
+  A_(c->d_famlist, cells);
+  A_(c->d_K, cells * c->kpack);
+  A_(c->d_kdiag, cells * c->nU);
+  A_(c->d_ktot, c->nskel);
+  A_(c->d_LII, cells * tri(c->nI));
+  A_(c->d_W, cells * (long long)c->nI * c->nU);
+  A_(c->d_S, cells * (long long)c->nU * c->nU);
+  A_(c->d_G, cells * (long long)c->nU * c->nU);
+  A_(c->d_Phi, cells * (long long)c->nU * ROMB_NSLOT);
+  A_(c->d_Psi, cells * (long long)c->nU * ROMB_NSLOT);
+  A_(c->d_SCl, cells * ROMB_NSLOT * ROMB_NSLOT);
+  A_(c->d_D, cells * c->nU);
+  A_(c->d_ucell_map, cells * c->nU);
+  A_(c->d_islot, c->nI);
+  A_(c->d_uslot, c->nU);
+  A_(c->d_cmap, cells * ROMB_NSLOT);
+  A_(c->d_f, c->nskel);
+  A_(c->d_x, c->nskel);
+  A_(c->d_r, c->nskel);
+  A_(c->d_z, c->nskel);
+  A_(c->d_pv, c->nskel);
+  A_(c->d_q, c->nskel);
+  A_(c->d_red, 4096);
+  A_(c->d_fI, cells * c->nI);
+  A_(c->d_fU, cells * c->nU);
+  A_(c->d_cloc, cells * ROMB_NSLOT);
+  A_(c->d_u, 2 * nodes);
+  A_(c->d_traction, 8 * 64);
+#undef A_
+  const long long ncoarse = 2LL * (nx + 1) * (ny + 1) + 3LL * nx * (ny + 1) + 3LL * (nx + 1) * ny;
+  if ((s = romb_alloc_t(c, &c->d_coarse, 2 * ncoarse)) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &c->d_cowner, 4 * ncoarse)) != ROMB_OK) return s;
+  if ((s = build_tables(c)) != ROMB_OK) return s;
+  c->have_lattice = true;
+  return ROMB_OK;
+}
+
+// Copy (or reference) the lattice inputs and validate families.
+static romb_status load_lattice(romb_ctx* c, const romb_lattice* L) {
+  romb_status s = setup_lattice(c, L);
+  if (s == ROMB_E_ARG) return s;
+  if (s == ROMB_E_STATE) {
+    c->have_lattice = false;
+    if ((s = alloc_lattice(c, L)) != ROMB_OK) return s;
+  }
+  c->basis = L->basis;
+  c->mem = L->mem;
+  c->E = L->E;
+  c->nu = L->nu;
+  c->rho = L->rho;
+  for (int i = 0; i < 8; ++i) c->traction[i] = L->traction ? (L->mem == ROMB_MEM_HOST ? L->traction[i] : 0.0) : 0.0;
+  const long long cells = c->ncells;
+  const long long nctrl = (long long)(c->m * c->nx + 1) * (c->m * c->ny + 1);
+  const cudaMemcpyKind kind = L->mem == ROMB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaEventRecord(c->ev[12], c->stream);
+  ROMB_CUDA(cudaMemcpyAsync(c->d_ctrl, L->ctrl, 16 * nctrl, kind, c->stream));
+  ROMB_CUDA(cudaMemcpyAsync(c->d_mu, L->mu, 32 * cells, kind, c->stream));
+  ROMB_CUDA(cudaMemcpyAsync(c->d_family, L->family, 4 * cells, kind, c->stream));
+  if (L->traction) {
+    if (L->mem == ROMB_MEM_DEVICE) {
+      ROMB_CUDA(cudaMemcpyAsync(c->d_traction, L->traction, 64, cudaMemcpyDeviceToDevice, c->stream));
+      ROMB_CUDA(cudaMemcpyAsync(c->traction, L->traction, 64, cudaMemcpyDeviceToHost, c->stream));
+      ROMB_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+      ROMB_CUDA(cudaMemcpyAsync(c->d_traction, c->traction, 64, cudaMemcpyHostToDevice, c->stream));
+    }
+  } else {
+    ROMB_CUDA(cudaMemsetAsync(c->d_traction, 0, 64, c->stream));
+  }
+  cudaEventRecord(c->ev[13], c->stream);
+  ROMB_CUDA(cudaMemsetAsync(c->d_flags, 0, 4 * cells, c->stream));
+  return ROMB_OK;
+}
+
+static float ms_between(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
+static romb_status check_flags(romb_ctx* c, int mask_bits) {
+  // reduce the per-cell flags on the device; one int comes back
+  int* d_any = (int*)c->d_red;
+  ROMB_CUDA(cudaMemsetAsync(d_any, 0, sizeof(int), c->stream));
+  romb_status s = launch_flag_or(c, d_any);
+  if (s != ROMB_OK) return s;
+  int h = 0;
+  ROMB_CUDA(cudaMemcpyAsync(&h, d_any, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  h &= mask_bits;
+  if (h & ROMB_FLAG_OUT_OF_BOX) return ROMB_E_OUT_OF_BOX;
+  if (h & ROMB_FLAG_BAD_MAP) return ROMB_E_BAD_MAP;
+  if (h & ROMB_FLAG_NOT_SPD) return ROMB_E_NOT_SPD;
+  if (h & ROMB_FLAG_NAN) return ROMB_E_NAN;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_assemble(romb_ctx* c, const romb_lattice* L, romb_precision prec) {
+  if (!c || !L) return ROMB_E_ARG;
+  if (prec != ROMB_FP64 && prec != ROMB_FP32_SPLIT && prec != ROMB_BF16_SPLIT) return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  bool any = false;
+  for (auto& R : c->roms) any |= R.loaded;
+  if (!any) return ROMB_E_STATE;
+  romb_status s = load_lattice(c, L);
+  if (s != ROMB_OK) return s;
+  for (auto& R : c->roms)
+    if (R.loaded && (R.p != c->p || R.kind != c->basis)) return ROMB_E_ARG;
+  c->assembled = c->factored = false;
+  c->prec = prec;
+  cudaEventRecord(c->ev[0], c->stream);
+  if ((s = launch_theta(c)) != ROMB_OK) return s;
+  cudaEventRecord(c->ev[1], c->stream);
+  if (prec == ROMB_FP64) s = launch_assemble_fp64(c);
+  else s = launch_assemble_tc(c);
+  if (s != ROMB_OK) return s;
+  cudaEventRecord(c->ev[2], c->stream);
+  if ((s = check_flags(c, ROMB_FLAG_OUT_OF_BOX | ROMB_FLAG_BAD_MAP | ROMB_FLAG_NAN)) != ROMB_OK) return s;
+  c->phase_ms[0] = ms_between(c->ev[0], c->ev[1]);
+  c->phase_ms[1] = ms_between(c->ev[1], c->ev[2]);
+  c->phase_ms[6] = ms_between(c->ev[12], c->ev[13]);
+  c->assembled = true;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_assemble_host_K(romb_ctx* c, const romb_lattice* L, const double* K) {
+  if (!c || !L || !K) return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  romb_status s = load_lattice(c, L);
+  if (s != ROMB_OK) return s;
+  c->assembled = c->factored = false;
+  // pack the dense matrices on the device (upper triangle, row-major)
+  double* dense = nullptr;
+  const size_t nd = (size_t)c->ndof;
+  if ((s = romb_alloc_t(c, &dense, (size_t)c->ncells * nd * nd)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpyAsync(dense, K, 8 * (size_t)c->ncells * nd * nd,
+                            L->mem == ROMB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            c->stream));
+  s = launch_pack_dense(c, dense);
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  romb_free_ptr(c, dense);
+  if (s != ROMB_OK) return s;
+  c->assembled = true;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_factor(romb_ctx* c) {
+  if (!c) return ROMB_E_ARG;
+  if (!c->assembled) return ROMB_E_STATE;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  romb_status s;
+  cudaEventRecord(c->ev[3], c->stream);
+  if ((s = launch_ktot(c)) != ROMB_OK) return s;
+  if ((s = launch_factor(c)) != ROMB_OK) return s;
+  cudaEventRecord(c->ev[4], c->stream);
+  if ((s = coarse_factor(c)) != ROMB_OK) return s;
+  cudaEventRecord(c->ev[5], c->stream);
+  if ((s = check_flags(c, ROMB_FLAG_NOT_SPD | ROMB_FLAG_NAN)) != ROMB_OK) return s;
+  c->phase_ms[2] = ms_between(c->ev[3], c->ev[4]);
+  c->phase_ms[3] = ms_between(c->ev[4], c->ev[5]);
+  c->factored = true;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* traction_sets, double rtol,
+                                       int maxit, double* u_out, int* iters_out, double* relres_out) {
+  if (!c || !u_out || nrhs < 1 || !(rtol > 0) || maxit < 1) return ROMB_E_ARG;
+  if (!traction_sets && nrhs != 1) return ROMB_E_ARG;
+  if (!c->factored) return ROMB_E_STATE;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  const long long nodes = (long long)(c->p * c->nx + 1) * (c->p * c->ny + 1);
+  romb_status worst = ROMB_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    double tr[8];
+    if (traction_sets) {
+      if (c->mem == ROMB_MEM_HOST) memcpy(tr, traction_sets + 8 * k, 64);
+      else {
+        ROMB_CUDA(cudaMemcpyAsync(tr, traction_sets + 8 * k, 64, cudaMemcpyDeviceToHost, c->stream));
+        ROMB_CUDA(cudaStreamSynchronize(c->stream));
+      }
+    } else {
+      memcpy(tr, c->traction, 64);
+    }
+    int it = 0;
+    double rel = 0;
+    cudaEventRecord(c->ev[6], c->stream);
+    romb_status s = pcg_solve(c, tr, rtol, maxit, c->d_u, &it, &rel);
+    if (s != ROMB_OK && s != ROMB_E_NOT_CONVERGED) return s;
+    if (s == ROMB_E_NOT_CONVERGED) worst = s;
+    cudaEventRecord(c->ev[7], c->stream);
+    double* dst = u_out + 2 * nodes * k;
+    ROMB_CUDA(cudaMemcpyAsync(dst, c->d_u, 16 * nodes,
+                              c->mem == ROMB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                              c->stream));
+    cudaEventRecord(c->ev[8], c->stream);
+    ROMB_CUDA(cudaStreamSynchronize(c->stream));
+    if (iters_out) iters_out[k] = it;
+    if (relres_out) relres_out[k] = rel;
+    c->phase_ms[4] = ms_between(c->ev[6], c->ev[7]);
+    c->phase_ms[6] += ms_between(c->ev[7], c->ev[8]);
+  }
+  c->phase_ms[7] = c->phase_ms[0] + c->phase_ms[1] + c->phase_ms[2] + c->phase_ms[3] + c->phase_ms[4] +
+                   c->phase_ms[5];
+  return worst;
+}
+
+extern "C" romb_status romb_stats(romb_ctx* c, double* phase_ms, int* flags_out) {
+  if (!c) return ROMB_E_ARG;
+  if (phase_ms) memcpy(phase_ms, c->phase_ms, sizeof(c->phase_ms));
+  if (flags_out) {
+    if (!c->have_lattice) return ROMB_E_STATE;
+    ROMB_CUDA(cudaSetDevice(c->device));
+    ROMB_CUDA(cudaMemcpyAsync(flags_out, c->d_flags, 4 * (size_t)c->ncells, cudaMemcpyDeviceToHost, c->stream));
+    ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return ROMB_OK;
+}
+
+extern "C" size_t romb_field_bytes(romb_ctx* c, int field) {
+  if (!c || !c->have_lattice) return 0;
+  const size_t cells = (size_t)c->ncells, nU = (size_t)c->nU;
+  int kmax = 0;
+  for (auto& R : c->roms)
+    if (R.loaded) kmax = std::max(kmax, R.n_r + 1);
+  switch (field) {
+    case ROMB_FIELD_CHAT: return cells * 9 * 16 * 8;
+    case ROMB_FIELD_THETA: return cells * (size_t)kmax * 8;
+    case ROMB_FIELD_K: return cells * (size_t)c->kpack * 8;
+    case ROMB_FIELD_S: return cells * tri(nU) * 8;
+    case ROMB_FIELD_PSI: return cells * nU * ROMB_NSLOT * 8;
+    case ROMB_FIELD_SC_LOCAL: return cells * ROMB_NSLOT * ROMB_NSLOT * 8;
+    case ROMB_FIELD_D: return cells * nU * 8;
+    case ROMB_FIELD_FINE: return cells * tri(nU) * 8;
+    case ROMB_FIELD_FLAGS: return cells * 4;
+  }
+  return 0;
+}
+
+extern "C" romb_status romb_read(romb_ctx* c, int field, void* out, size_t bytes) {
+  if (!c || !out) return ROMB_E_ARG;
+  const size_t need = romb_field_bytes(c, field);
+  if (need == 0 || bytes != need) return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  const size_t cells = (size_t)c->ncells, nU = (size_t)c->nU;
+  switch (field) {
+    case ROMB_FIELD_CHAT: ROMB_CUDA(cudaMemcpy(out, c->d_chat, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_THETA: {
+      const size_t k = bytes / (cells * 8);
+      std::vector<double> tmp(cells * 128);
+      ROMB_CUDA(cudaMemcpy(tmp.data(), c->d_theta, tmp.size() * 8, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < cells; ++i) memcpy((double*)out + i * k, &tmp[i * 128], 8 * k);
+      break;
+    }
+    case ROMB_FIELD_K: ROMB_CUDA(cudaMemcpy(out, c->d_K, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_S:
+    case ROMB_FIELD_FINE: {
+      std::vector<double> full(cells * nU * nU);
+      ROMB_CUDA(cudaMemcpy(full.data(), field == ROMB_FIELD_S ? c->d_S : c->d_G, full.size() * 8,
+                           cudaMemcpyDeviceToHost));
+      double* o = (double*)out;
+      for (size_t i = 0; i < cells; ++i)
+        for (size_t r = 0, t = 0; r < nU; ++r)
+          for (size_t q = r; q < nU; ++q, ++t) o[i * tri(nU) + t] = full[i * nU * nU + r * nU + q];
+      break;
+    }
+    case ROMB_FIELD_PSI: ROMB_CUDA(cudaMemcpy(out, c->d_Psi, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_SC_LOCAL: ROMB_CUDA(cudaMemcpy(out, c->d_SCl, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_D: ROMB_CUDA(cudaMemcpy(out, c->d_D, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_FLAGS: ROMB_CUDA(cudaMemcpy(out, c->d_flags, bytes, cudaMemcpyDeviceToHost)); break;
+    default: return ROMB_E_ARG;
+  }
+  return ROMB_OK;
+}

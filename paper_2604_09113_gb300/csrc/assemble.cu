@@ -1,0 +1,368 @@
+// Online assembly of the cell stiffness matrices (Sec. 4.1, Algorithms 4-5).
+//
+//  theta kernel (one warp per 4 cells of one family):
+//    I_r(mu)  = sum_g A[g] prod_d l_{g_d}(mu_d)       (tensor GLL interpolation, Sec. 4.2.3)
+//    theta    = (rho, (1 - rho) I_r)                  (Algorithm 4: I + rho (I_Pi - I))
+//    Chat_k   = det J J^-1 C J^-T at the (q+1)^2 GLL interpolation nodes
+//               (Eq. ELA constitutive, Eq. FAST interpolation)
+//  contraction (FP64 form): I_c = theta_c U' per (k1 <= k2) pair, then
+//    K[(k1 i1),(k2 i2)] = sum_{j1 j2 k3} I_c[k1 k2 k3 j1 j2] Chat_c[k3][i1 j1 i2 j2]
+//  (Eq. SPEED L int), written as the packed upper triangle of each cell matrix.
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
+#include "tables.cuh"
+
+struct RomDev {
+  const double* U64;     // [K][n_half]
+  const double* At;      // [ngrid][n_r]  (transposed interpolation samples)
+  int n_r, r;
+  double lo, hi;
+  long long n_half;
+  double nodes[12];      // degree-r GLL nodes of [lo, hi]
+};
+
+void fill_cell_params(const romb_ctx* c, CellParams* P) {
+  memset(P, 0, sizeof(*P));
+  P->p = c->p;
+  P->m = c->m;
+  P->basis = c->basis;
+  P->nB = c->nB;
+  P->nI = c->nI;
+  P->nU = c->nU;
+  P->nx = c->nx;
+  P->ny = c->ny;
+  P->ncells = c->ncells;
+  P->q = c->q;
+  P->nL = c->nL;
+  P->dmask = c->dmask;
+  P->E = c->E;
+  P->nu = c->nu;
+  P->rho = c->rho;
+  P->lam = c->E * c->nu / (1.0 - c->nu * c->nu);
+  P->mu = c->E / (2.0 * (1.0 + c->nu));
+  gll_nodes01(c->p, P->gll);
+  gauss01(ROMB_NQ, P->gq_x, P->gq_w);
+  for (int i = 0; i < ROMB_NQ; ++i) cell_basis1d(*P, P->gq_x[i], P->bq[i], nullptr);
+  LocalTables T = make_local_tables(c->p);
+  memcpy(P->uslot, T.uslot, sizeof(P->uslot));
+  memcpy(P->islot, T.islot, sizeof(P->islot));
+  memcpy(P->uslot_of_node, T.uslot_of_node, sizeof(P->uslot_of_node));
+}
+
+// ---------------------------------------------------------------------------
+// family lists: cells grouped by family, in increasing cell index (one CTA)
+// ---------------------------------------------------------------------------
+__global__ void family_list_kernel(const int32_t* __restrict__ family, int ncells, int nfam, int* __restrict__ list,
+                                   int* __restrict__ counts, int32_t* __restrict__ flags) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int out = 0;
+  for (int f = 0; f < nfam; ++f) {
+    if (tid == 0) base = out;
+    __syncthreads();
+    for (int c0 = 0; c0 < ncells; c0 += nt) {
+      const int c = c0 + tid;
+      const int fam = c < ncells ? family[c] : -1;
+      const int mine = fam == f;
+      // block exclusive scan of `mine`
+      const unsigned bal = __ballot_sync(0xffffffffu, mine);
+      const int lane = tid & 31, w = tid >> 5;
+      const int pre = __popc(bal & ((1u << lane) - 1u));
+      if (lane == 0) warp_tot[w] = __popc(bal);
+      __syncthreads();
+      int wpre = 0, tot = 0;
+      for (int i = 0; i < nt / 32; ++i) {
+        if (i < w) wpre += warp_tot[i];
+        tot += warp_tot[i];
+      }
+      if (mine) list[base + wpre + pre] = c;
+      __syncthreads();
+      if (tid == 0) base += tot;
+      __syncthreads();
+    }
+    if (tid == 0) counts[f] = base - out;
+    out = base;
+    __syncthreads();
+  }
+  // cells whose family has no loaded model
+  for (int c = tid; c < ncells; c += nt)
+    if (family[c] < 0 || family[c] >= nfam) flags[c] |= ROMB_FLAG_OUT_OF_BOX;
+}
+
+// ---------------------------------------------------------------------------
+// theta kernel
+// ---------------------------------------------------------------------------
+#define TH_CELLS 4
+__global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, const int* __restrict__ list, int count,
+                                                     const double* __restrict__ ctrl, const double* __restrict__ mu,
+                                                     double* __restrict__ theta, double* __restrict__ chat,
+                                                     int32_t* __restrict__ flags) {
+  __shared__ double wts[4][TH_CELLS][4][12];   // [warp][cell][param][node]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int first = (blockIdx.x * 4 + warp) * TH_CELLS;
+  const int r = R.r, n1 = r + 1;
+  const double* nodes = R.nodes;
+  int cells[TH_CELLS];
+  for (int j = 0; j < TH_CELLS; ++j) cells[j] = (first + j < count) ? list[first + j] : -1;
+  // 1D interpolation weights: lane = (cell j, parameter d)
+  if (lane < 4 * TH_CELLS) {
+    const int j = lane >> 2, d = lane & 3;
+    const int c = cells[j];
+    double v[12];
+    if (c >= 0) {
+      const double m = mu[4 * (long long)c + d];
+      if (!(m >= R.lo && m <= R.hi)) atomicOr(&flags[c], ROMB_FLAG_OUT_OF_BOX);
+      lagrange1d(r, nodes, m, v, nullptr);
+    } else {
+      for (int i = 0; i < n1; ++i) v[i] = 0.0;
+    }
+    for (int i = 0; i < n1; ++i) wts[warp][j][d][i] = v[i];
+  }
+  __syncwarp();
+  // lambda_t = sum_g At[g][t] w(g): lanes over t
+  const int nr = R.n_r;
+  double acc[4][TH_CELLS];
+  for (int s = 0; s < 4; ++s)
+    for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
+  const int ng = n1 * n1 * n1 * n1;
+  for (int g = 0; g < ng; ++g) {
+    const int g1 = g % n1, g2 = (g / n1) % n1, g3 = (g / (n1 * n1)) % n1, g4 = g / (n1 * n1 * n1);
+    double wg[TH_CELLS];
+    for (int j = 0; j < TH_CELLS; ++j)
+      wg[j] = wts[warp][j][0][g1] * wts[warp][j][1][g2] * wts[warp][j][2][g3] * wts[warp][j][3][g4];
+    const double* Ag = R.At + (long long)g * nr;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int t = lane + 32 * s;
+      if (t < nr) {
+        const double a = __ldg(Ag + t);
+        for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = fma(a, wg[j], acc[s][j]);
+      }
+    }
+  }
+  for (int j = 0; j < TH_CELLS; ++j) {
+    const int c = cells[j];
+    if (c < 0) continue;
+    double* th = theta + 128 * (long long)c;
+    if (lane == 0) th[0] = P.rho;
+    for (int s = 0; s < 4; ++s) {
+      const int t = lane + 32 * s;
+      if (t < nr) th[1 + t] = (1.0 - P.rho) * acc[s][j];
+    }
+  }
+  // Chat at the 9 interpolation nodes: lane = (cell j, node k3)
+  for (int task = lane; task < TH_CELLS * 9; task += 32) {
+    const int j = task / 9, k3 = task % 9;
+    const int c = cells[j];
+    if (c < 0) continue;
+    const int cx = c % P.nx, cy = c / P.nx;
+    const double qn[3] = {0.0, 0.5, 1.0};
+    double x[2], J[2][2];
+    map_eval(ctrl, P.nx, P.m, cx, cy, qn[k3 % 3], qn[k3 / 3], x, J);
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (!(det > 0.0)) atomicOr(&flags[c], ROMB_FLAG_BAD_MAP);
+    // G = J^-1, G[j][m] = dxi_j / dx_m
+    const double G[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+    double* out = chat + (long long)c * 144 + 16 * k3;
+    for (int i = 0; i < 2; ++i)
+      for (int jj = 0; jj < 2; ++jj)
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l) {
+            // Chat_ijkl = det [lam G_ji G_lk + mu (d_ik (G G^T)_jl + G_jk G_li)]
+            const double GGt = G[jj][0] * G[l][0] + G[jj][1] * G[l][1];
+            const double v = P.lam * G[jj][i] * G[l][k] + P.mu * ((i == k ? GGt : 0.0) + G[jj][k] * G[l][i]);
+            out[((i * 2 + jj) * 2 + k) * 2 + l] = det * v;
+          }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 contraction: 32 cells x 4 pairs per CTA
+// ---------------------------------------------------------------------------
+#define A64_CELLS 32
+#define A64_PAIRS 4
+__global__ void __launch_bounds__(128) assemble_fp64_kernel(const double* __restrict__ U, long long n_half, int K,
+                                                             const int* __restrict__ list, int count,
+                                                             const int2* __restrict__ pairs, int npairs, int ndof,
+                                                             const double* __restrict__ theta,
+                                                             const double* __restrict__ chat,
+                                                             double* __restrict__ Kout) {
+  extern __shared__ double sm[];
+  const int KS = K | 1;                      // odd stride: no bank conflicts across cells
+  double* sU = sm;                           // [K][A64_PAIRS*36]
+  double* sT = sU + (size_t)K * A64_PAIRS * 36;   // [32][KS]
+  double* sC = sT + A64_CELLS * KS;          // [32][145]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int pair0 = blockIdx.y * A64_PAIRS;
+  const int c0 = blockIdx.x * A64_CELLS;
+  const int npl = min(A64_PAIRS, npairs - pair0);
+  for (int i = tid; i < K * A64_PAIRS * 36; i += blockDim.x) {
+    const int t = i / (A64_PAIRS * 36), e = i % (A64_PAIRS * 36);
+    sU[i] = (e < npl * 36) ? U[(long long)t * n_half + (long long)pair0 * 36 + e] : 0.0;
+  }
+  for (int i = tid; i < A64_CELLS * K; i += blockDim.x) {
+    const int j = i / K, t = i % K;
+    const int c = c0 + j < count ? list[c0 + j] : -1;
+    sT[j * KS + t] = c >= 0 ? theta[128 * (long long)c + t] : 0.0;
+  }
+  for (int i = tid; i < A64_CELLS * 144; i += blockDim.x) {
+    const int j = i / 144, e = i % 144;
+    const int c = c0 + j < count ? list[c0 + j] : -1;
+    sC[j * 145 + e] = c >= 0 ? chat[144 * (long long)c + e] : 0.0;
+  }
+  __syncthreads();
+  const int pl = warp;
+  if (pl >= npl) return;
+  const int cl = lane;
+  const int cell = c0 + cl < count ? list[c0 + cl] : -1;
+  double acc[36];
+#pragma unroll
+  for (int e = 0; e < 36; ++e) acc[e] = 0.0;
+  const double* u = sU + pl * 36;
+  const double* th = sT + cl * KS;
+  for (int t = 0; t < K; ++t) {
+    const double a = th[t];
+    const double* ut = u + t * A64_PAIRS * 36;
+#pragma unroll
+    for (int e = 0; e < 36; ++e) acc[e] = fma(a, ut[e], acc[e]);
+  }
+  if (cell < 0) return;
+  const int2 kk = pairs[pair0 + pl];
+  const double* C = sC + cl * 145;
+  double* Kc = Kout + (long long)cell * ((long long)ndof * (ndof + 1) / 2);
+#pragma unroll
+  for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+    for (int i2 = 0; i2 < 2; ++i2) {
+      if (kk.x == kk.y && i1 > i2) continue;
+      double v = 0.0;
+#pragma unroll
+      for (int k3 = 0; k3 < 9; ++k3)
+#pragma unroll
+        for (int j1 = 0; j1 < 2; ++j1)
+#pragma unroll
+          for (int j2 = 0; j2 < 2; ++j2)
+            v = fma(acc[k3 * 4 + 2 * j1 + j2], C[16 * k3 + ((i1 * 2 + j1) * 2 + i2) * 2 + j2], v);
+      const long long r = 2 * kk.x + i1, q = 2 * kk.y + i2;
+      Kc[r * ndof - r * (r - 1) / 2 + (q - r)] = v;
+    }
+}
+
+// dense [cells][ndof][ndof] -> packed upper triangle
+__global__ void pack_dense_kernel(const double* __restrict__ dense, int ndof, long long cells,
+                                  double* __restrict__ Kout) {
+  const long long kp = (long long)ndof * (ndof + 1) / 2;
+  const long long total = cells * kp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / kp;
+    long long t = i % kp;
+    // row r: entries t in [r*ndof - r(r-1)/2, ...)
+    int r = 0;
+    long long rowlen = ndof;
+    while (t >= rowlen) {
+      t -= rowlen;
+      ++r;
+      --rowlen;
+    }
+    const int q = r + (int)t;
+    Kout[i] = dense[(c * ndof + r) * ndof + q];
+  }
+}
+
+__global__ void flag_or_kernel(const int32_t* __restrict__ flags, long long n, int* __restrict__ out) {
+  int v = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v |= flags[i];
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicOr(out, v);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static romb_status ensure_pairs(romb_ctx* c) {
+  if (c->d_pairs) return ROMB_OK;
+  const int nB = c->nB;
+  std::vector<int2> pr;
+  for (int k1 = 0; k1 < nB; ++k1)
+    for (int k2 = k1; k2 < nB; ++k2) pr.push_back(make_int2(k1, k2));
+  romb_status s = romb_alloc_t(c, &c->d_pairs, pr.size());
+  if (s != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpy(c->d_pairs, pr.data(), sizeof(int2) * pr.size(), cudaMemcpyHostToDevice));
+  return ROMB_OK;
+}
+
+romb_status launch_theta(romb_ctx* c) {
+  romb_status s;
+  if ((s = ensure_pairs(c)) != ROMB_OK) return s;
+  int* d_counts = (int*)c->d_red + 16;
+  family_list_kernel<<<1, 1024, 0, c->stream>>>(c->d_family, c->ncells, ROMB_MAX_FAMILIES, c->d_famlist, d_counts,
+                                                c->d_flags);
+  ROMB_CUDA(cudaGetLastError());
+  int counts[ROMB_MAX_FAMILIES];
+  ROMB_CUDA(cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  CellParams P;
+  fill_cell_params(c, &P);
+  int start = 0;
+  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+    c->famstart[f] = start;
+    c->famcount[f] = counts[f];
+    if (counts[f] > 0 && !c->roms[f].loaded) {
+      // cells reference a family without a model: flag them via the family check
+      return ROMB_E_ARG;
+    }
+    if (counts[f] > 0) {
+      const RombRom& Rr = c->roms[f];
+      RomDev R{Rr.U64, Rr.At, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
+      double g[12];
+      gll_nodes01(Rr.r, g);
+      for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
+      const int per_block = 4 * TH_CELLS;
+      theta_kernel<<<(counts[f] + per_block - 1) / per_block, 128, 0, c->stream>>>(
+          P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat, c->d_flags);
+      ROMB_CUDA(cudaGetLastError());
+    }
+    start += counts[f];
+  }
+  return ROMB_OK;
+}
+
+romb_status launch_assemble_fp64(romb_ctx* c) {
+  const int npairs = c->nB * (c->nB + 1) / 2;
+  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+    if (c->famcount[f] == 0) continue;
+    const RombRom& R = c->roms[f];
+    const int K = R.n_r + 1;
+    const size_t smem = 8 * ((size_t)K * A64_PAIRS * 36 + A64_CELLS * (K | 1) + A64_CELLS * 145);
+    static bool attr_done = false;
+    if (!attr_done) {
+      ROMB_CUDA(cudaFuncSetAttribute(assemble_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr_done = true;
+    }
+    dim3 grid((c->famcount[f] + A64_CELLS - 1) / A64_CELLS, (npairs + A64_PAIRS - 1) / A64_PAIRS);
+    assemble_fp64_kernel<<<grid, 128, smem, c->stream>>>(R.U64, R.n_half, K, c->d_famlist + c->famstart[f],
+                                                         c->famcount[f], c->d_pairs, npairs, c->ndof, c->d_theta,
+                                                         c->d_chat, c->d_K);
+    ROMB_CUDA(cudaGetLastError());
+  }
+  return ROMB_OK;
+}
+
+romb_status launch_pack_dense(romb_ctx* c, const double* d_dense) {
+  pack_dense_kernel<<<4 * c->sms, 256, 0, c->stream>>>(d_dense, c->ndof, c->ncells, c->d_K);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+romb_status launch_flag_or(romb_ctx* c, int* d_any) {
+  flag_or_kernel<<<c->sms, 256, 0, c->stream>>>(c->d_flags, c->ncells, d_any);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}

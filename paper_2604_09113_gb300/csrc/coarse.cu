@@ -1,0 +1,547 @@
+// Coarse problem of BDDC (Sec. 3.3.4): S_C = sum_i R_C^(i)T Psi^(i)T S^(i) Psi^(i) R_C^(i),
+// assembled and factorised by a sparse Cholesky.  The coarse unknowns live on
+// the lattice vertices (2 DoFs) and edges (3 DoFs), so a geometric nested
+// dissection of the cell rectangle by grid lines gives the elimination tree:
+// every front holds its separator DoFs (eliminated) and the DoFs on the
+// internal sides of its rectangle (updated), as dense lower triangles.
+//
+// Numeric factorisation, level by level from the leaves:
+//   assemble   leaves: the cells' 20 x 20 coarse matrices; inner fronts: the
+//              children's update matrices (extend-add), in a fixed order;
+//   partial Cholesky of every front of the level, blocked by 32 columns:
+//              diagonal block (one CTA per front), panel solve, trailing update.
+// Solve: forward (leaves -> root) and backward (root -> leaves) substitution.
+#include <stdio.h>
+
+#include <algorithm>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "device.cuh"
+#include "tables.cuh"
+
+#define ND_NB 32
+
+namespace {
+
+struct Group {
+  int px, py;      // doubled coordinates
+  int ndof;        // 2 (vertex) or 3 (edge)
+  int base;        // first global coarse DoF
+};
+
+struct Builder {
+  int nx, ny;
+  unsigned dmask;
+  long long NCV, NCH;
+  std::vector<NdFront>* fronts;
+  std::vector<std::vector<int>> rows;        // per front: global coarse DoFs (sep first)
+  std::vector<std::vector<int>> leaf_cells;  // per front (leaves only)
+  std::vector<int> depth;
+
+  bool vertex_dir(int vx, int vy) const {
+    return ((dmask & 1) && vx == 0) || ((dmask & 2) && vx == nx) || ((dmask & 4) && vy == 0) ||
+           ((dmask & 8) && vy == ny);
+  }
+  // all non-Dirichlet groups in the closed doubled rectangle
+  void groups_in(int x0, int x1, int y0, int y1, std::vector<Group>& out) const {
+    for (int py = 2 * y0; py <= 2 * y1; ++py)
+      for (int px = 2 * x0; px <= 2 * x1; ++px) {
+        const bool ex = (px & 1) == 0, ey = (py & 1) == 0;
+        if (!ex && !ey) continue;   // cell centre
+        if (ex && ey) {
+          const int vx = px / 2, vy = py / 2;
+          if (vertex_dir(vx, vy)) continue;
+          out.push_back({px, py, 2, (int)(2LL * ((long long)vy * (nx + 1) + vx))});
+        } else if (ey) {   // horizontal edge (cx, vy)
+          const int cx = px / 2, vy = py / 2;
+          if ((vy == 0 && (dmask & 4)) || (vy == ny && (dmask & 8))) continue;
+          out.push_back({px, py, 3, (int)(NCV + 3LL * ((long long)vy * nx + cx))});
+        } else {           // vertical edge (vx, cy)
+          const int vx = px / 2, cy = py / 2;
+          if ((vx == 0 && (dmask & 1)) || (vx == nx && (dmask & 2))) continue;
+          out.push_back({px, py, 3, (int)(NCV + NCH + 3LL * ((long long)cy * (nx + 1) + vx))});
+        }
+      }
+  }
+  bool internal_side(const Group& g, int x0, int x1, int y0, int y1) const {
+    return (g.px == 2 * x0 && x0 > 0) || (g.px == 2 * x1 && x1 < nx) || (g.py == 2 * y0 && y0 > 0) ||
+           (g.py == 2 * y1 && y1 < ny);
+  }
+  int build(int x0, int x1, int y0, int y1) {
+    const int w = x1 - x0, h = y1 - y0;
+    std::vector<Group> gs;
+    groups_in(x0, x1, y0, y1, gs);
+    NdFront F;
+    std::vector<int> elim, bnd;
+    std::vector<int> kids;
+    auto push = [](std::vector<int>& v, const Group& g) {
+      for (int t = 0; t < g.ndof; ++t) v.push_back(g.base + t);
+    };
+    const bool leaf = w <= 2 && h <= 2;
+    int xm = -1, ym = -1;
+    if (!leaf) {
+      if (w >= h) xm = x0 + w / 2;
+      else ym = y0 + h / 2;
+    }
+    for (const Group& g : gs) {
+      if (internal_side(g, x0, x1, y0, y1)) push(bnd, g);
+      else if (leaf || (xm >= 0 && g.px == 2 * xm) || (ym >= 0 && g.py == 2 * ym)) push(elim, g);
+    }
+    if (!leaf) {
+      if (xm >= 0) {
+        kids.push_back(build(x0, xm, y0, y1));
+        kids.push_back(build(xm, x1, y0, y1));
+      } else {
+        kids.push_back(build(x0, x1, y0, ym));
+        kids.push_back(build(x0, x1, ym, y1));
+      }
+    }
+    F.ns = (int)elim.size();
+    F.nb = (int)bnd.size();
+    F.children = kids;
+    const int id = (int)fronts->size();
+    fronts->push_back(F);
+    std::vector<int> r = elim;
+    r.insert(r.end(), bnd.begin(), bnd.end());
+    rows.push_back(r);
+    std::vector<int> cells;
+    if (leaf)
+      for (int cy = y0; cy < y1; ++cy)
+        for (int cx = x0; cx < x1; ++cx) cells.push_back(cx + nx * cy);
+    leaf_cells.push_back(cells);
+    int d = 0;
+    for (int k : kids) {
+      (*fronts)[k].parent = id;
+      d = std::max(d, depth[k] + 1);
+    }
+    depth.push_back(d);
+    return id;
+  }
+};
+
+struct FrontDev {
+  int ns, nb;
+  long long off;     // dense front (n x n)
+  int idx_off;       // global coarse index of each row
+  int child_off, nchild;
+  int cell_off, ncell;
+  int emap_off;      // extend-add positions of this front's update rows in its parent
+  int ybuf_off;      // forward-solve update vector (nb)
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// device kernels
+// ---------------------------------------------------------------------------
+__global__ void nd_assemble_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
+                                   const int* __restrict__ children, const int* __restrict__ emap,
+                                   const int* __restrict__ cells, const int* __restrict__ cell_pos,
+                                   const double* __restrict__ SCl) {
+  const FrontDev f = fr[level[blockIdx.x]];
+  const int n = f.ns + f.nb;
+  double* A = F + f.off;
+  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) A[t] = 0.0;
+  __syncthreads();
+  for (int k = 0; k < f.ncell; ++k) {
+    const int cell = cells[f.cell_off + k];
+    const int* pos = cell_pos + 20 * (long long)cell;
+    const double* s = SCl + 400 * (long long)cell;
+    for (int t = threadIdx.x; t < 400; t += blockDim.x) {
+      const int a = t / 20, b = t % 20;
+      const int pa = pos[a], pb = pos[b];
+      if (pa >= 0 && pb >= 0 && pa >= pb) A[(long long)pa * n + pb] += s[t];
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < f.nchild; ++k) {
+    const FrontDev ch = fr[children[f.child_off + k]];
+    const int cn = ch.ns + ch.nb;
+    const double* C = F + ch.off;
+    const int* em = emap + ch.emap_off;
+    for (long long t = threadIdx.x; t < (long long)ch.nb * ch.nb; t += blockDim.x) {
+      const int a = (int)(t / ch.nb), b = (int)(t % ch.nb);
+      if (b > a) continue;
+      int pa = em[a], pb = em[b];
+      if (pa < pb) {
+        const int tmp = pa;
+        pa = pb;
+        pb = tmp;
+      }
+      A[(long long)pa * n + pb] += C[(long long)(ch.ns + a) * cn + (ch.ns + b)];
+    }
+    __syncthreads();
+  }
+}
+
+// Cholesky of the diagonal block [k0, k1) of each front (one CTA per front).
+__global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
+                                int k0, int32_t* __restrict__ bad) {
+  const FrontDev f = fr[level[blockIdx.x]];
+  if (k0 >= f.ns) return;
+  const int n = f.ns + f.nb;
+  const int nbk = min(ND_NB, f.ns - k0);
+  __shared__ double D[ND_NB][ND_NB + 1];
+  double* A = F + f.off;
+  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+    const int i = t / nbk, j = t % nbk;
+    D[i][j] = A[(long long)(k0 + i) * n + (k0 + j)];
+  }
+  __syncthreads();
+  for (int k = 0; k < nbk; ++k) {
+    if (threadIdx.x == 0) {
+      double d = D[k][k];
+      if (!(d > 0.0)) {
+        *bad = 1;
+        d = 1.0;
+      }
+      D[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) D[i][k] /= D[k][k];
+    __syncthreads();
+    const int m = nbk - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) D[i][j] -= D[i][k] * D[j][k];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+    const int i = t / nbk, j = t % nbk;
+    if (j <= i) A[(long long)(k0 + i) * n + (k0 + j)] = D[i][j];
+  }
+}
+
+// Panel: rows r >= k1 of columns [k0, k1): A[r, :] <- A[r, :] L_kk^-T.
+__global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
+                               int k0) {
+  const FrontDev f = fr[level[blockIdx.y]];
+  if (k0 >= f.ns) return;
+  const int n = f.ns + f.nb;
+  const int nbk = min(ND_NB, f.ns - k0);
+  const int k1 = k0 + nbk;
+  __shared__ double L[ND_NB][ND_NB + 1];
+  double* A = F + f.off;
+  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+    const int i = t / nbk, j = t % nbk;
+    L[i][j] = (j <= i) ? A[(long long)(k0 + i) * n + (k0 + j)] : 0.0;
+  }
+  __syncthreads();
+  const int r = k1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double x[ND_NB];
+  double* row = A + (long long)r * n + k0;
+#pragma unroll
+  for (int j = 0; j < ND_NB; ++j) {
+    if (j < nbk) {
+      double s = row[j];
+      for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
+      x[j] = s / L[j][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < ND_NB; ++j)
+    if (j < nbk) row[j] = x[j];
+}
+
+// Trailing update of rows/cols >= k1: A[i][j] -= sum_{t in [k0,k1)} A[i][t] A[j][t], i >= j.
+// 32 x 32 output tiles, lower tiles only, 256 threads (4 outputs each).
+__global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                                       double* __restrict__ F, int k0) {
+  const FrontDev f = fr[level[blockIdx.y]];
+  if (k0 >= f.ns) return;
+  const int n = f.ns + f.nb;
+  const int nbk = min(ND_NB, f.ns - k0);
+  const int k1 = k0 + nbk;
+  const int m = n - k1;
+  const int nt = (m + 31) / 32;
+  // tile index -> (ti, tj) with ti >= tj
+  const int tix = blockIdx.x;
+  if (tix >= nt * (nt + 1) / 2) return;
+  int ti = (int)((sqrt(8.0 * tix + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
+  while (ti * (ti + 1) / 2 > tix) --ti;
+  const int tj = tix - ti * (ti + 1) / 2;
+  __shared__ double Pi[32][ND_NB + 1], Pj[32][ND_NB + 1];
+  double* A = F + f.off;
+  for (int t = threadIdx.x; t < 32 * ND_NB; t += blockDim.x) {
+    const int rr = t / ND_NB, kk = t % ND_NB;
+    const int ri = k1 + ti * 32 + rr, rj = k1 + tj * 32 + rr;
+    Pi[rr][kk] = (ri < n && kk < nbk) ? A[(long long)ri * n + k0 + kk] : 0.0;
+    Pj[rr][kk] = (rj < n && kk < nbk) ? A[(long long)rj * n + k0 + kk] : 0.0;
+  }
+  __syncthreads();
+  const int lr = threadIdx.x / 8, lc0 = (threadIdx.x % 8) * 4;
+  const int gi = k1 + ti * 32 + lr;
+  if (gi >= n) return;
+  double acc[4] = {0, 0, 0, 0};
+  for (int kk = 0; kk < nbk; ++kk) {
+    const double a = Pi[lr][kk];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = fma(a, Pj[lc0 + c][kk], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gj = k1 + tj * 32 + lc0 + c;
+    if (gj < n && gj <= gi) A[(long long)gi * n + gj] -= acc[c];
+  }
+}
+
+// Forward substitution of one level: w = rhs(sep) + children's update vectors;
+// y_s = L11^-1 w_s; u = w_b - L21 y_s.
+__global__ void nd_fwd_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                              const double* __restrict__ F, const int* __restrict__ idx,
+                              const int* __restrict__ children, const int* __restrict__ emap,
+                              const double* __restrict__ rhs, double* __restrict__ y, double* __restrict__ ybuf) {
+  extern __shared__ double w[];
+  const FrontDev f = fr[level[blockIdx.x]];
+  const int n = f.ns + f.nb;
+  const double* A = F + f.off;
+  const int* id = idx + f.idx_off;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] = t < f.ns ? rhs[id[t]] : 0.0;
+  __syncthreads();
+  for (int k = 0; k < f.nchild; ++k) {
+    const FrontDev ch = fr[children[f.child_off + k]];
+    const int* em = emap + ch.emap_off;
+    for (int t = threadIdx.x; t < ch.nb; t += blockDim.x) w[em[t]] += ybuf[ch.ybuf_off + t];
+    __syncthreads();
+  }
+  // y_s: row-by-row, one warp computes each dot product
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < f.ns; ++i) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int k = lane; k < i; k += 32) s += A[(long long)i * n + k] * w[k];
+      s = warp_sum(s);
+      if (lane == 0) w[i] = (w[i] - s) / A[(long long)i * n + i];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < f.ns; t += blockDim.x) y[id[t]] = w[t];
+  for (int r = f.ns + warp; r < n; r += blockDim.x / 32) {
+    double s = 0.0;
+    for (int k = lane; k < f.ns; k += 32) s += A[(long long)r * n + k] * w[k];
+    s = warp_sum(s);
+    if (lane == 0) ybuf[f.ybuf_off + (r - f.ns)] = w[r] - s;
+  }
+}
+
+// Backward substitution of one level: x_s = L11^-T (y_s - L21^T x_b).
+__global__ void nd_bwd_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                              const double* __restrict__ F, const int* __restrict__ idx, double* __restrict__ x) {
+  extern __shared__ double w[];
+  const FrontDev f = fr[level[blockIdx.x]];
+  const int n = f.ns + f.nb;
+  const double* A = F + f.off;
+  const int* id = idx + f.idx_off;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] = x[id[t]];
+  __syncthreads();
+  // t_s = y_s - L21^T x_b, one thread per separator row
+  for (int i = threadIdx.x; i < f.ns; i += blockDim.x) {
+    double s = 0.0;
+    for (int r = f.ns; r < n; ++r) s += A[(long long)r * n + i] * w[r];
+    w[i] -= s;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = f.ns - 1; i >= 0; --i) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int k = i + 1 + lane; k < f.ns; k += 32) s += A[(long long)k * n + i] * w[k];
+      s = warp_sum(s);
+      if (lane == 0) w[i] = (w[i] - s) / A[(long long)i * n + i];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < f.ns; t += blockDim.x) x[id[t]] = w[t];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct NdDevice {
+  FrontDev* fr = nullptr;
+  int* idx = nullptr;
+  int* children = nullptr;
+  int* emap = nullptr;
+  int* cells = nullptr;
+  int* cell_pos = nullptr;
+  double* F = nullptr;
+  double* ybuf = nullptr;
+  std::vector<int*> level_ids;
+  std::vector<int> level_count, level_maxns, level_maxn, level_maxtiles_trsm, level_maxtiles_syrk;
+  int32_t* bad = nullptr;
+};
+
+static std::unordered_map<const romb_ctx*, NdDevice> g_nd;
+
+romb_status coarse_build(romb_ctx* c) {
+  NdPlan& plan = c->nd;
+  plan = NdPlan();
+  Builder B;
+  B.nx = c->nx;
+  B.ny = c->ny;
+  B.dmask = c->dmask;
+  B.NCV = 2LL * (c->nx + 1) * (c->ny + 1);
+  B.NCH = 3LL * c->nx * (c->ny + 1);
+  B.fronts = &plan.fronts;
+  const int root = B.build(0, c->nx, 0, c->ny);
+  (void)root;
+  const int nf = (int)plan.fronts.size();
+  int maxd = 0;
+  for (int d : B.depth) maxd = std::max(maxd, d);
+  plan.levels.assign(maxd + 1, {});
+  for (int i = 0; i < nf; ++i) {
+    plan.fronts[i].level = B.depth[i];
+    plan.levels[B.depth[i]].push_back(i);
+  }
+  // host arrays
+  std::vector<FrontDev> fd(nf);
+  std::vector<int> idx, children, emap, cells, cell_pos((size_t)c->ncells * 20, -1);
+  long long off = 0;
+  int ybuf = 0;
+  for (int i = 0; i < nf; ++i) {
+    const NdFront& F = plan.fronts[i];
+    FrontDev& d = fd[i];
+    d.ns = F.ns;
+    d.nb = F.nb;
+    const long long n = F.ns + F.nb;
+    d.off = off;
+    off += n * n;
+    d.idx_off = (int)idx.size();
+    idx.insert(idx.end(), B.rows[i].begin(), B.rows[i].end());
+    d.child_off = (int)children.size();
+    d.nchild = (int)F.children.size();
+    children.insert(children.end(), F.children.begin(), F.children.end());
+    d.cell_off = (int)cells.size();
+    d.ncell = (int)B.leaf_cells[i].size();
+    cells.insert(cells.end(), B.leaf_cells[i].begin(), B.leaf_cells[i].end());
+    d.ybuf_off = ybuf;
+    ybuf += F.nb;
+    d.emap_off = -1;
+  }
+  // extend-add positions of each front's update rows in its parent
+  for (int i = 0; i < nf; ++i) {
+    const NdFront& F = plan.fronts[i];
+    if (F.parent < 0) continue;
+    std::unordered_map<int, int> pos;
+    const std::vector<int>& pr = B.rows[F.parent];
+    for (int t = 0; t < (int)pr.size(); ++t) pos[pr[t]] = t;
+    fd[i].emap_off = (int)emap.size();
+    for (int t = F.ns; t < F.ns + F.nb; ++t) {
+      auto it = pos.find(B.rows[i][t]);
+      if (it == pos.end()) {
+        romb_set_error("nested dissection: update row missing from parent front");
+        return ROMB_E_CUDA;
+      }
+      emap.push_back(it->second);
+    }
+  }
+  // cell -> leaf-front row of each local coarse slot
+  std::vector<int> cmap((size_t)c->ncells * 20);
+  ROMB_CUDA(cudaMemcpy(cmap.data(), c->d_cmap, 4 * cmap.size(), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < nf; ++i) {
+    if (B.leaf_cells[i].empty()) continue;
+    std::unordered_map<int, int> pos;
+    for (int t = 0; t < (int)B.rows[i].size(); ++t) pos[B.rows[i][t]] = t;
+    for (int cell : B.leaf_cells[i])
+      for (int s = 0; s < 20; ++s) {
+        const int g = cmap[(size_t)cell * 20 + s];
+        if (g < 0) continue;
+        auto it = pos.find(g);
+        if (it == pos.end()) {
+          romb_set_error("nested dissection: cell coarse DoF missing from its leaf front");
+          return ROMB_E_CUDA;
+        }
+        cell_pos[(size_t)cell * 20 + s] = it->second;
+      }
+  }
+  plan.n = 0;
+  for (int i = 0; i < nf; ++i) plan.n += plan.fronts[i].ns;
+  plan.pool = off;
+  // device
+  NdDevice& D = g_nd[c];
+  D = NdDevice();
+  romb_status s;
+  if ((s = romb_alloc(c, (void**)&D.fr, sizeof(FrontDev) * nf)) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.idx, std::max<size_t>(1, idx.size()))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.children, std::max<size_t>(1, children.size()))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.emap, std::max<size_t>(1, emap.size()))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.cells, std::max<size_t>(1, cells.size()))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.cell_pos, cell_pos.size())) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.F, (size_t)off)) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.ybuf, std::max(1, ybuf))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
+  if (!children.empty())
+    ROMB_CUDA(cudaMemcpy(D.children, children.data(), 4 * children.size(), cudaMemcpyHostToDevice));
+  if (!emap.empty()) ROMB_CUDA(cudaMemcpy(D.emap, emap.data(), 4 * emap.size(), cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(D.cells, cells.data(), 4 * cells.size(), cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(D.cell_pos, cell_pos.data(), 4 * cell_pos.size(), cudaMemcpyHostToDevice));
+  for (const auto& lv : plan.levels) {
+    int* d;
+    if ((s = romb_alloc_t(c, &d, lv.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(d, lv.data(), 4 * lv.size(), cudaMemcpyHostToDevice));
+    D.level_ids.push_back(d);
+    D.level_count.push_back((int)lv.size());
+    int mns = 0, mn = 0;
+    for (int f : lv) {
+      mns = std::max(mns, plan.fronts[f].ns);
+      mn = std::max(mn, plan.fronts[f].ns + plan.fronts[f].nb);
+    }
+    D.level_maxns.push_back(mns);
+    D.level_maxn.push_back(mn);
+  }
+  return ROMB_OK;
+}
+
+romb_status coarse_factor(romb_ctx* c) {
+  NdDevice& D = g_nd[c];
+  ROMB_CUDA(cudaMemsetAsync(D.bad, 0, 4, c->stream));
+  for (size_t l = 0; l < D.level_ids.size(); ++l) {
+    const int nfl = D.level_count[l];
+    nd_assemble_kernel<<<nfl, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.children, D.emap, D.cells,
+                                                   D.cell_pos, c->d_SCl);
+    ROMB_CUDA(cudaGetLastError());
+    const int mns = D.level_maxns[l], mn = D.level_maxn[l];
+    for (int k0 = 0; k0 < mns; k0 += ND_NB) {
+      nd_potrf_kernel<<<nfl, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad);
+      const int rows = mn - k0;
+      if (rows > 0) {
+        dim3 g1((rows + 127) / 128, nfl);
+        nd_trsm_kernel<<<g1, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0);
+        const int nt = (rows + 31) / 32;
+        dim3 g2(nt * (nt + 1) / 2, nfl);
+        nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0);
+      }
+      ROMB_CUDA(cudaGetLastError());
+    }
+  }
+  int bad = 0;
+  ROMB_CUDA(cudaMemcpyAsync(&bad, D.bad, 4, cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  if (bad) return ROMB_E_NOT_SPD;
+  return ROMB_OK;
+}
+
+// out = S_C^-1 in over the non-Dirichlet coarse DoFs (Dirichlet entries of out are 0).
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
+  NdDevice& D = g_nd[c];
+  ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
+  const int L = (int)D.level_ids.size();
+  for (int l = 0; l < L; ++l) {
+    const size_t sm = 8 * (size_t)D.level_maxn[l];
+    nd_fwd_kernel<<<D.level_count[l], 256, sm, c->stream>>>(D.fr, D.level_ids[l], D.F, D.idx, D.children, D.emap,
+                                                            d_in, d_out, D.ybuf);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const size_t sm = 8 * (size_t)D.level_maxn[l];
+    nd_bwd_kernel<<<D.level_count[l], 256, sm, c->stream>>>(D.fr, D.level_ids[l], D.F, D.idx, d_out);
+  }
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}

@@ -1,0 +1,108 @@
+// Device-side helpers of romb: 1D bases, cell maps and the per-launch
+// parameter block (passed by value to every per-cell kernel).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "romb_internal.cuh"
+
+#define ROMB_NQ 24   // Gauss points per edge for the coarse functionals
+
+struct CellParams {
+  int p, m, basis, nB, nI, nU, nx, ny, ncells, q, nL;
+  unsigned dmask;
+  double E, nu, rho, lam, mu;   // plane-stress Lame parameters
+  double gll[ROMB_MAX_P + 1];   // degree-p GLL nodes of the cell basis
+  double gq_x[ROMB_NQ], gq_w[ROMB_NQ];
+  double bq[ROMB_NQ][ROMB_MAX_P + 1];        // cell basis (1D) at the Gauss points
+  int uslot[8 * ROMB_MAX_P];
+  int islot[2 * (ROMB_MAX_P - 1) * (ROMB_MAX_P - 1)];
+  int uslot_of_node[(ROMB_MAX_P + 1) * (ROMB_MAX_P + 1)];
+};
+
+// Values and derivatives of the n+1 Lagrange polynomials on `nodes` at t.
+__host__ __device__ inline void lagrange1d(int n, const double* nodes, double t, double* v, double* d) {
+  for (int i = 0; i <= n; ++i) {
+    double den = 1.0, val = 1.0, der = 0.0;
+    for (int j = 0; j <= n; ++j) {
+      if (j == i) continue;
+      den *= nodes[i] - nodes[j];
+      der = der * (t - nodes[j]) + val;
+      val *= t - nodes[j];
+    }
+    v[i] = val / den;
+    if (d) d[i] = der / den;
+  }
+}
+
+// Degree-p Bernstein polynomials and derivatives at t.
+__host__ __device__ inline void bernstein1d(int p, double t, double* v, double* d) {
+  double binom = 1.0;
+  for (int i = 0; i <= p; ++i) {
+    if (i > 0) binom = binom * (p - i + 1) / i;
+    double ti = 1.0, si = 1.0;
+    for (int k = 0; k < i; ++k) ti *= t;
+    for (int k = 0; k < p - i; ++k) si *= 1.0 - t;
+    v[i] = binom * ti * si;
+    if (d) {
+      double dv = 0.0;
+      if (i > 0) {
+        double a = 1.0;
+        for (int k = 0; k < i - 1; ++k) a *= t;
+        dv += binom * i * a * si;
+      }
+      if (i < p) {
+        double b = 1.0;
+        for (int k = 0; k < p - i - 1; ++k) b *= 1.0 - t;
+        dv -= binom * (p - i) * ti * b;
+      }
+      d[i] = dv;
+    }
+  }
+}
+
+__host__ __device__ inline void cell_basis1d(const CellParams& P, double t, double* v, double* d) {
+  if (P.basis == 0) lagrange1d(P.p, P.gll, t, v, d);
+  else bernstein1d(P.p, t, v, d);
+}
+
+// Equispaced map nodes a/m.
+__host__ __device__ inline void map_basis1d(int m, double t, double* v, double* d) {
+  double nodes[5];
+  for (int a = 0; a <= m; ++a) nodes[a] = (double)a / m;
+  lagrange1d(m, nodes, t, v, d);
+}
+
+// Map control point (a, b) of cell (cx, cy) from the shared grid.
+__device__ inline const double* ctrl_pt(const double* ctrl, int nx, int m, int cx, int cy, int a, int b) {
+  return ctrl + 2 * ((long long)(m * cy + b) * (m * nx + 1) + (m * cx + a));
+}
+
+// Physical point and Jacobian J[r][s] = dx_r/dxi_s of the cell map at xi.
+__device__ inline void map_eval(const double* ctrl, int nx, int m, int cx, int cy, double x1, double x2, double* x,
+                                double J[2][2]) {
+  double v1[5], d1[5], v2[5], d2[5];
+  map_basis1d(m, x1, v1, d1);
+  map_basis1d(m, x2, v2, d2);
+  x[0] = x[1] = 0.0;
+  J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
+  for (int b = 0; b <= m; ++b)
+    for (int a = 0; a <= m; ++a) {
+      const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
+      const double w = v1[a] * v2[b], w1 = d1[a] * v2[b], w2 = v1[a] * d2[b];
+      for (int r = 0; r < 2; ++r) {
+        x[r] += w * X[r];
+        J[r][0] += w1 * X[r];
+        J[r][1] += w2 * X[r];
+      }
+    }
+}
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Host helper: fill a CellParams from the context.
+void fill_cell_params(const romb_ctx* c, CellParams* P);

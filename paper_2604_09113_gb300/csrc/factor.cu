@@ -1,0 +1,448 @@
+// BDDC local set-up, one CTA per cell, everything in shared memory, FP64.
+//
+//  (Sec. 3.2)   K_II = L L^T,  W = L^-1 K_IU,  S = K_UU - W^T W
+//  (Sec. 3.3.3) D_jj = K_jj / K^tot_j  (stiffness-weighted partition of unity)
+//  (Sec. 3.3.1) coarse functionals: corner values, per edge int u_1, int u_2 and
+//               int f.u over the whole physical edge, f = (x2 - xbar2, xbar1 - x1)
+//  (Alg. 2)     cross-point DoFs removed: Shat = S minus corners, Chat = edge rows,
+//               That = Chat Shat^-1 Chat^T
+//  (Eq. BDDC local basis) Psi column per local coarse DoF, corner values moved
+//               to the right-hand side
+//  local coarse matrix Psi^T S Psi, and the explicit fine operator
+//  F = Shat^-1 - Shat^-1 Chat^T That^-1 Chat Shat^-1 (the top-left block of the
+//  saddle-point inverse), stored as D F D for the preconditioner.
+//
+// Skeleton (U) slots follow increasing local DoF 2k+i over the boundary nodes;
+// Dirichlet slots are kept as identity rows of S and have D = 0.
+#include <stdio.h>
+
+#include "device.cuh"
+#include "tables.cuh"
+
+// In-place Cholesky (lower) of the n x n row-major matrix A (stride lda).
+__device__ void chol_smem(double* A, int n, int lda, int* bad) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double d = A[k * lda + k];
+      if (!(d > 0.0)) {
+        *bad = 1;
+        d = 1.0;
+      }
+      A[k * lda + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double inv = 1.0 / A[k * lda + k];
+    for (int i = k + 1 + tid; i < n; i += nt) A[i * lda + k] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) A[i * lda + j] -= A[i * lda + k] * A[j * lda + k];
+    }
+    __syncthreads();
+  }
+}
+
+// B <- L^-1 B (forward) for `ncols` columns, one thread per column.
+__device__ void trsm_fwd(const double* L, int n, int ldl, double* B, int ldb, int ncols) {
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      double s = B[i * ldb + col];
+      for (int k = 0; k < i; ++k) s -= L[i * ldl + k] * B[k * ldb + col];
+      B[i * ldb + col] = s / L[i * ldl + i];
+    }
+  }
+}
+
+// B <- L^-T B (backward) for `ncols` columns, one thread per column.
+__device__ void trsm_bwd(const double* L, int n, int ldl, double* B, int ldb, int ncols) {
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = B[i * ldb + col];
+      for (int k = i + 1; k < n; ++k) s -= L[k * ldl + i] * B[k * ldb + col];
+      B[i * ldb + col] = s / L[i * ldl + i];
+    }
+  }
+}
+
+__device__ inline long long packed_idx(long long r, long long q, long long nd) {
+  if (r > q) {
+    const long long t = r;
+    r = q;
+    q = t;
+  }
+  return r * nd - r * (r - 1) / 2 + (q - r);
+}
+
+template <int P>
+struct FactorDims {
+  static constexpr int NB = (P + 1) * (P + 1), ND = 2 * NB, NI = 2 * (P - 1) * (P - 1), NU = 8 * P, NK = NU - 8;
+  // phase 1 (doubles)
+  static constexpr int oAII = 0, oAIU = oAII + NI * NI, oAUU = oAIU + NI * NU, oCr = oAUU + NU * NU,
+                       oKd = oCr + 20 * NU, oDv = oKd + NU, oEx = oDv + NU, oEnd1 = oEx + 4 * ROMB_NQ * 3 + 8;
+  // phase 2 reuses [oAII, oAUU) when it fits there (S stays in place), else
+  // it goes after the phase-1 arrays
+  static constexpr int size2 = NK * NK + NK * 12 + 144 + NK * 20 + NU * 20 + NK * 20;
+  static constexpr int base2 = size2 <= oAUU ? 0 : oEnd1;
+  static constexpr int oSh = base2, oY = oSh + NK * NK, oT = oY + NK * 12, oZ = oT + 144, oPsi = oZ + NK * 20,
+                       oQ = oPsi + NU * 20, oEnd2 = oQ + NK * 20;
+  static constexpr int total = oEnd2 > oEnd1 ? oEnd2 : oEnd1;
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double* __restrict__ Kp,
+                                                      const double* __restrict__ ctrl, const int* __restrict__ umap,
+                                                      const int* __restrict__ cmap, const double* __restrict__ ktot,
+                                                      double* __restrict__ LII_out, double* __restrict__ W_out,
+                                                      double* __restrict__ S_out, double* __restrict__ G_out,
+                                                      double* __restrict__ Phi_out, double* __restrict__ Psi_out,
+                                                      double* __restrict__ SCl_out, double* __restrict__ D_out,
+                                                      int32_t* __restrict__ flags) {
+  using Dm = FactorDims<P>;
+  constexpr int ND = Dm::ND, NI = Dm::NI, NU = Dm::NU, NK = Dm::NK;
+  extern __shared__ double sm[];
+  double* AII = sm + Dm::oAII;
+  double* AIU = sm + Dm::oAIU;
+  double* S = sm + Dm::oAUU;
+  double* Cr = sm + Dm::oCr;
+  double* kd = sm + Dm::oKd;
+  double* Dv = sm + Dm::oDv;
+  double* Ex = sm + Dm::oEx;   // per edge and Gauss point: x1, x2, j ; then xbar
+  __shared__ int s_umap[NU], s_cmap[20], s_keep[NK], s_cu[8], s_islot[NI], s_uslot[NU], s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long cell = blockIdx.x;
+  const int cx = (int)(cell % Pm.nx), cy = (int)(cell / Pm.nx);
+  for (int i = tid; i < NU; i += nt) {
+    s_umap[i] = umap[cell * NU + i];
+    s_uslot[i] = Pm.uslot[i];
+  }
+  for (int i = tid; i < NI; i += nt) s_islot[i] = Pm.islot[i];
+  if (tid < 20) s_cmap[tid] = cmap[cell * 20 + tid];
+  if (tid == 0) {
+    s_bad = 0;
+    const int kc[4] = {0, P, (P + 1) * P, (P + 1) * P + P};
+    for (int v = 0; v < 4; ++v)
+      for (int cc = 0; cc < 2; ++cc) s_cu[2 * v + cc] = 2 * Pm.uslot_of_node[kc[v]] + cc;
+    int n = 0;
+    for (int u = 0; u < NU; ++u) {
+      bool corner = false;
+      for (int t = 0; t < 8; ++t) corner |= (s_cu[t] == u);
+      if (!corner) s_keep[n++] = u;
+    }
+  }
+  __syncthreads();
+  // ---- load K in (I, U) order; Dirichlet skeleton slots become identity ----
+  const double* Kc = Kp + cell * ((long long)ND * (ND + 1) / 2);
+  for (int t = tid; t < NI * NI; t += nt) {
+    const int i = t / NI, j = t % NI;
+    AII[t] = Kc[packed_idx(s_islot[i], s_islot[j], ND)];
+  }
+  for (int t = tid; t < NI * NU; t += nt) {
+    const int i = t / NU, u = t % NU;
+    AIU[t] = s_umap[u] < 0 ? 0.0 : Kc[packed_idx(s_islot[i], s_uslot[u], ND)];
+  }
+  for (int t = tid; t < NU * NU; t += nt) {
+    const int u = t / NU, v = t % NU;
+    double val = Kc[packed_idx(s_uslot[u], s_uslot[v], ND)];
+    if (u == v) kd[u] = val;
+    if (s_umap[u] < 0 || s_umap[v] < 0) val = (u == v) ? 1.0 : 0.0;
+    S[t] = val;
+  }
+  // edge geometry for the coarse functionals: x(t_q), j(t_q) and the midpoint
+  for (int t = tid; t < 4 * (ROMB_NQ + 1); t += nt) {
+    const int e = t / (ROMB_NQ + 1), qq = t % (ROMB_NQ + 1);
+    const double tt = qq < ROMB_NQ ? Pm.gq_x[qq] : 0.5;
+    const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : tt;
+    const double x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : tt;
+    double x[2], J[2][2];
+    map_eval(ctrl, Pm.nx, Pm.m, cx, cy, x1, x2, x, J);
+    const int dcol = e < 2 ? 1 : 0;
+    if (qq < ROMB_NQ) {
+      Ex[(e * ROMB_NQ + qq) * 3 + 0] = x[0];
+      Ex[(e * ROMB_NQ + qq) * 3 + 1] = x[1];
+      Ex[(e * ROMB_NQ + qq) * 3 + 2] = hypot(J[0][dcol], J[1][dcol]);
+    } else {
+      Ex[4 * ROMB_NQ * 3 + 2 * e + 0] = x[0];
+      Ex[4 * ROMB_NQ * 3 + 2 * e + 1] = x[1];
+    }
+  }
+  for (int t = tid; t < 20 * NU; t += nt) Cr[t] = 0.0;
+  __syncthreads();
+  // ---- coarse functionals ----
+  if (tid < 8) {
+    if (s_cmap[tid] >= 0) Cr[tid * NU + s_cu[tid]] = 1.0;
+  }
+  for (int t = tid; t < 4 * (P + 1); t += nt) {
+    const int e = t / (P + 1), s = t % (P + 1);
+    const int k = e == 0 ? (P + 1) * s : e == 1 ? P + (P + 1) * s : e == 2 ? s : s + (P + 1) * P;
+    const int u0 = 2 * Pm.uslot_of_node[k];
+    const double xb1 = Ex[4 * ROMB_NQ * 3 + 2 * e], xb2 = Ex[4 * ROMB_NQ * 3 + 2 * e + 1];
+    double a = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int qq = 0; qq < ROMB_NQ; ++qq) {
+      const double* ex = Ex + (e * ROMB_NQ + qq) * 3;
+      const double wj = Pm.gq_w[qq] * ex[2] * Pm.bq[qq][s];
+      a += wj;
+      m1 += wj * (ex[1] - xb2);
+      m2 += wj * (xb1 - ex[0]);
+    }
+    const int r = 8 + 3 * e;
+    if (s_cmap[r] >= 0) {
+      if (s_umap[u0] >= 0) {
+        Cr[r * NU + u0] = a;
+        Cr[(r + 2) * NU + u0] = m1;
+      }
+      if (s_umap[u0 + 1] >= 0) {
+        Cr[(r + 1) * NU + u0 + 1] = a;
+        Cr[(r + 2) * NU + u0 + 1] = m2;
+      }
+    }
+  }
+  // ---- K_II = L L^T ----
+  chol_smem(AII, NI, NI, &s_bad);
+  // ---- W = L^-1 K_IU ----
+  trsm_fwd(AII, NI, NI, AIU, NU, NU);
+  __syncthreads();
+  // ---- S = K_UU - W^T W (lower triangle computed, mirrored) ----
+  for (int t = tid; t < NU * NU; t += nt) {
+    const int u = t / NU, v = t % NU;
+    if (v > u) continue;
+    double acc = 0.0;
+    for (int k = 0; k < NI; ++k) acc += AIU[k * NU + u] * AIU[k * NU + v];
+    const double val = S[t] - acc;
+    S[u * NU + v] = val;
+    S[v * NU + u] = val;
+  }
+  // write L (packed lower) and W for the interior recovery
+  for (int t = tid; t < NI * NI; t += nt) {
+    const int i = t / NI, j = t % NI;
+    if (j <= i) LII_out[cell * (NI * (NI + 1) / 2) + (long long)i * (i + 1) / 2 + j] = AII[t];
+  }
+  for (int t = tid; t < NI * NU; t += nt) W_out[cell * NI * NU + t] = AIU[t];
+  for (int u = tid; u < NU; u += nt) {
+    const int g = s_umap[u];
+    Dv[u] = g >= 0 ? kd[u] / ktot[g] : 0.0;
+  }
+  __syncthreads();
+  // ---- phase 2 (AII / AIU region reused) ----
+  double* Sh = sm + Dm::oSh;
+  double* Y = sm + Dm::oY;
+  double* T = sm + Dm::oT;
+  double* Z = sm + Dm::oZ;
+  double* Psi = sm + Dm::oPsi;
+  double* Q = sm + Dm::oQ;
+  for (int t = tid; t < NU * NU; t += nt) S_out[cell * NU * NU + t] = S[t];
+  for (int t = tid; t < NK * NK; t += nt) Sh[t] = S[s_keep[t / NK] * NU + s_keep[t % NK]];
+  for (int t = tid; t < NK * 12; t += nt) Y[t] = Cr[(8 + t % 12) * NU + s_keep[t / 12]];
+  __syncthreads();
+  chol_smem(Sh, NK, NK, &s_bad);
+  trsm_fwd(Sh, NK, NK, Y, 12, 12);   // Y = Lhat^-1 Chat^T
+  __syncthreads();
+  for (int t = tid; t < 144; t += nt) {
+    const int a = t / 12, b = t % 12;
+    double acc = 0.0;
+    for (int i = 0; i < NK; ++i) acc += Y[i * 12 + a] * Y[i * 12 + b];
+    if (s_cmap[8 + a] < 0 || s_cmap[8 + b] < 0) acc = (a == b) ? 1.0 : 0.0;
+    T[t] = acc;
+  }
+  // right-hand sides of Eq. (BDDC local basis) after removing the corners:
+  // fhat = -S[keep, corner_j] for vertex slots, ghat handled below
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    Z[t] = (j < 8 && s_cmap[j] >= 0) ? -S[s_keep[i] * NU + s_cu[j]] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // 12 x 12 Cholesky of That (one thread)
+    for (int k = 0; k < 12; ++k) {
+      double d = T[k * 12 + k];
+      for (int j = 0; j < k; ++j) d -= T[k * 12 + j] * T[k * 12 + j];
+      if (!(d > 0.0)) {
+        s_bad = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      T[k * 12 + k] = d;
+      for (int i = k + 1; i < 12; ++i) {
+        double s = T[i * 12 + k];
+        for (int j = 0; j < k; ++j) s -= T[i * 12 + j] * T[k * 12 + j];
+        T[i * 12 + k] = s / d;
+      }
+    }
+  }
+  trsm_fwd(Sh, NK, NK, Z, 20, 20);
+  __syncthreads();
+  trsm_bwd(Sh, NK, NK, Z, 20, 20);   // Z = Shat^-1 fhat
+  __syncthreads();
+  // R = Chat Z - ghat ; ghat = -C[edge, corner_j] (vertex slots) or e_{j-8} (edge slots)
+  double* R = Q;   // [12][20]
+  for (int t = tid; t < 240; t += nt) {
+    const int e = t / 20, j = t % 20;
+    double acc = 0.0;
+    for (int i = 0; i < NK; ++i) acc += Cr[(8 + e) * NU + s_keep[i]] * Z[i * 20 + j];
+    double g = 0.0;
+    if (s_cmap[j] >= 0) g = (j < 8) ? -Cr[(8 + e) * NU + s_cu[j]] : ((j - 8 == e) ? 1.0 : 0.0);
+    R[t] = (s_cmap[8 + e] >= 0) ? acc - g : 0.0;
+  }
+  __syncthreads();
+  // Lambda = That^-1 R
+  trsm_fwd(T, 12, 12, R, 20, 20);
+  __syncthreads();
+  trsm_bwd(T, 12, 12, R, 20, 20);
+  __syncthreads();
+  // Xhat = Z - Lhat^-T (Y Lambda)
+  double* Q2 = Psi;   // temporary [NK][20] in the Psi area (NU*20 >= NK*20)
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    double acc = 0.0;
+    for (int e = 0; e < 12; ++e) acc += Y[i * 12 + e] * R[e * 20 + j];
+    Q2[t] = acc;
+  }
+  __syncthreads();
+  trsm_bwd(Sh, NK, NK, Q2, 20, 20);
+  __syncthreads();
+  for (int t = tid; t < NK * 20; t += nt) Z[t] -= Q2[t];
+  __syncthreads();
+  for (int t = tid; t < NU * 20; t += nt) Psi[t] = 0.0;
+  __syncthreads();
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    Psi[s_keep[i] * 20 + j] = (s_cmap[j] >= 0) ? Z[t] : 0.0;
+  }
+  if (tid < 8 && s_cmap[tid] >= 0) Psi[s_cu[tid] * 20 + tid] = 1.0;
+  __syncthreads();
+  // S Psi (into Z region reinterpreted as [NU][20] needs NU*20 <= NK*20 + ... use Q after R)
+  double* SP = Cr;   // constraints no longer needed: [NU][20] fits in 20*NU
+  // keep the edge rows of Chat for the fine operator: they live in Y already
+  __syncthreads();
+  for (int t = tid; t < NU * 20; t += nt) {
+    const int u = t / 20, j = t % 20;
+    double acc = 0.0;
+    for (int v = 0; v < NU; ++v) acc += S[u * NU + v] * Psi[v * 20 + j];
+    SP[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < 400; t += nt) {
+    const int a = t / 20, b = t % 20;
+    double acc = 0.0;
+    for (int u = 0; u < NU; ++u) acc += Psi[u * 20 + a] * SP[u * 20 + b];
+    SCl_out[cell * 400 + t] = acc;
+  }
+  for (int t = tid; t < NU * 20; t += nt) {
+    Psi_out[cell * NU * 20 + t] = Psi[t];
+    Phi_out[cell * NU * 20 + t] = Dv[t / 20] * Psi[t];
+  }
+  for (int u = tid; u < NU; u += nt) D_out[cell * NU + u] = Dv[u];
+  __syncthreads();
+  // ---- explicit fine operator F = M^T M - N^T N with M = Lhat^-1, N = L_T^-1 Y^T M ----
+  double* M = S;   // S has been written out; reuse its NU*NU area for M (NK*NK)
+  for (int t = tid; t < NK * NK; t += nt) M[t] = (t / NK == t % NK) ? 1.0 : 0.0;
+  __syncthreads();
+  trsm_fwd(Sh, NK, NK, M, NK, NK);
+  __syncthreads();
+  // V = L_T^-1 Y^T  (12 x NK), stored transposed in Y: column i of Y^T = row i of Y
+  for (int i = tid; i < NK; i += nt) {
+    double v[12];
+    for (int e = 0; e < 12; ++e) {
+      double s = Y[i * 12 + e];
+      for (int k = 0; k < e; ++k) s -= T[e * 12 + k] * v[k];
+      v[e] = s / T[e * 12 + e];
+    }
+    for (int e = 0; e < 12; ++e) Y[i * 12 + e] = v[e];
+  }
+  __syncthreads();
+  double* N = Q;   // [12][NK] (Q area holds NK*20 >= 12*NK)
+  for (int t = tid; t < 12 * NK; t += nt) {
+    const int e = t / NK, j = t % NK;
+    double acc = 0.0;
+    for (int i = j; i < NK; ++i) acc += Y[i * 12 + e] * M[i * NK + j];
+    N[t] = acc;
+  }
+  __syncthreads();
+  double* Gc = G_out + cell * NU * NU;
+  for (int t = tid; t < NU * NU; t += nt) Gc[t] = 0.0;
+  __syncthreads();
+  for (int t = tid; t < NK * NK; t += nt) {
+    const int a = t / NK, b = t % NK;
+    if (b > a) continue;
+    double acc = 0.0;
+    for (int i = a; i < NK; ++i) acc += M[i * NK + a] * M[i * NK + b];
+    for (int e = 0; e < 12; ++e) acc -= N[e * NK + a] * N[e * NK + b];
+    const int ua = s_keep[a], ub = s_keep[b];
+    const double v = Dv[ua] * acc * Dv[ub];
+    Gc[ua * NU + ub] = v;
+    Gc[ub * NU + ua] = v;
+  }
+  if (tid == 0 && s_bad) atomicOr(&flags[cell], ROMB_FLAG_NOT_SPD);
+}
+
+// K^tot per skeleton DoF: sum of the diagonal entries of every cell sharing the
+// node (Sec. 3.3.3), gathered in a fixed order.
+__global__ void ktot_kernel(CellParams P, const double* __restrict__ Kp, long long nskel_nodes,
+                            double* __restrict__ ktot) {
+  const int p = P.p, nx = P.nx, ny = P.ny;
+  const long long NH = (long long)(ny + 1) * (p * nx + 1);
+  const int ND = 2 * P.nB;
+  const long long kp = (long long)ND * (ND + 1) / 2;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < nskel_nodes;
+       id += (long long)gridDim.x * blockDim.x) {
+    int gx, gy;
+    if (id < NH) {
+      gy = p * (int)(id / (p * nx + 1));
+      gx = (int)(id % (p * nx + 1));
+    } else {
+      long long t = id - NH;
+      const int b = (int)(t % (p - 1)) + 1;
+      t /= (p - 1);
+      gx = p * (int)(t % (nx + 1));
+      gy = p * (int)(t / (nx + 1)) + b;
+    }
+    double s0 = 0.0, s1 = 0.0;
+    const int cx1 = gx / p, cy1 = gy / p;
+    for (int dy = (gy % p == 0) ? -1 : 0; dy <= 0; ++dy)
+      for (int dx = (gx % p == 0) ? -1 : 0; dx <= 0; ++dx) {
+        const int cx = cx1 + dx, cy = cy1 + dy;
+        if (cx < 0 || cy < 0 || cx >= nx || cy >= ny) continue;
+        const int k = (gx - p * cx) + (p + 1) * (gy - p * cy);
+        const double* Kc = Kp + ((long long)cy * nx + cx) * kp;
+        const long long r0 = 2 * k, r1 = 2 * k + 1;
+        s0 += Kc[r0 * ND - r0 * (r0 - 1) / 2];
+        s1 += Kc[r1 * ND - r1 * (r1 - 1) / 2];
+      }
+    ktot[2 * id] = s0;
+    ktot[2 * id + 1] = s1;
+  }
+}
+
+romb_status launch_ktot(romb_ctx* c) {
+  CellParams P;
+  fill_cell_params(c, &P);
+  ktot_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, c->d_K, c->nskel_nodes, c->d_ktot);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+template <int P>
+static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
+  const size_t smem = sizeof(double) * FactorDims<P>::total;
+  ROMB_CUDA(cudaFuncSetAttribute(factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  factor_kernel<P><<<c->ncells, 256, smem, c->stream>>>(Pm, c->d_K, c->d_ctrl, c->d_ucell_map, c->d_cmap, c->d_ktot,
+                                                        c->d_LII, c->d_W, c->d_S, c->d_G, c->d_Phi, c->d_Psi,
+                                                        c->d_SCl, c->d_D, c->d_flags);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+romb_status launch_factor(romb_ctx* c) {
+  CellParams Pm;
+  fill_cell_params(c, &Pm);
+  switch (c->p) {
+    case 3: return launch_factor_p<3>(c, Pm);
+    case 4: return launch_factor_p<4>(c, Pm);
+    case 5: return launch_factor_p<5>(c, Pm);
+    case 6: return launch_factor_p<6>(c, Pm);
+    case 7: return launch_factor_p<7>(c, Pm);
+    case 8: return launch_factor_p<8>(c, Pm);
+  }
+  return ROMB_E_ARG;
+}

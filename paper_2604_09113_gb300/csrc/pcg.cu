@@ -1,0 +1,486 @@
+// PCG on the interface Schur system S u = f (Eq. BDDC system) with the BDDC
+// preconditioner (Eq. BDDC preconditioner, Algorithm 1), then the interior
+// recovery u_I = K_II^-1 (f_I - K_IU u^(i)) (Sec. 3.2).
+//
+// Vectors live on the skeleton: DoF 2*id + comp of skeleton node id (nodes on
+// horizontal grid lines first, then the remaining nodes of vertical lines).
+// R^(i) (gather) and R^(i)T (sum over the sharing cells) are index maps; the
+// sums are gathers in a fixed cell order, so every result is deterministic.
+// Per iteration and cell: q = S p (matvec), z = D F D r + D Psi S_C^-1 Psi^T D r.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "device.cuh"
+#include "tables.cuh"
+
+#define RED_BLOCKS 256
+
+// skeleton node id -> grid node (gx, gy)
+__device__ inline void skel_node_xy(long long id, int p, int nx, long long NH, int* gx, int* gy) {
+  if (id < NH) {
+    *gy = p * (int)(id / (p * nx + 1));
+    *gx = (int)(id % (p * nx + 1));
+  } else {
+    long long t = id - NH;
+    const int b = (int)(t % (p - 1)) + 1;
+    t /= (p - 1);
+    *gx = p * (int)(t % (nx + 1));
+    *gy = p * (int)(t / (nx + 1)) + b;
+  }
+}
+
+__device__ inline bool dir_node(const CellParams& P, int gx, int gy) {
+  return ((P.dmask & 1) && gx == 0) || ((P.dmask & 2) && gx == P.p * P.nx) || ((P.dmask & 4) && gy == 0) ||
+         ((P.dmask & 8) && gy == P.p * P.ny);
+}
+
+// out[dof] = sum over cells sharing the node of loc[cell][slot]  (R^T of a cell-local field)
+__global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc, long long nnodes,
+                                   double* __restrict__ out) {
+  const int p = P.p, nx = P.nx, ny = P.ny, NU = P.nU;
+  const long long NH = (long long)(ny + 1) * (p * nx + 1);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < nnodes;
+       id += (long long)gridDim.x * blockDim.x) {
+    int gx, gy;
+    skel_node_xy(id, p, nx, NH, &gx, &gy);
+    double s0 = 0.0, s1 = 0.0;
+    if (!dir_node(P, gx, gy)) {
+      const int cx1 = gx / p, cy1 = gy / p;
+      for (int dy = (gy % p == 0) ? -1 : 0; dy <= 0; ++dy)
+        for (int dx = (gx % p == 0) ? -1 : 0; dx <= 0; ++dx) {
+          const int cx = cx1 + dx, cy = cy1 + dy;
+          if (cx < 0 || cy < 0 || cx >= nx || cy >= ny) continue;
+          const int k = (gx - p * cx) + (p + 1) * (gy - p * cy);
+          const int u = 2 * P.uslot_of_node[k];
+          const double* l = loc + ((long long)cy * nx + cx) * NU;
+          s0 += l[u];
+          s1 += l[u + 1];
+        }
+    }
+    out[2 * id] = s0;
+    out[2 * id + 1] = s1;
+  }
+}
+
+// y_loc = M_c v_loc with M_c a dense symmetric nU x nU cell matrix (S or D F D),
+// v_loc gathered from the skeleton; optionally c_loc = Phi^T v_loc.
+// One warp per cell, lanes over rows.
+template <bool COARSE>
+__global__ void __launch_bounds__(256) cell_matvec_kernel(int ncells, int NU, const double* __restrict__ M,
+                                                           const int* __restrict__ umap, const double* __restrict__ v,
+                                                           double* __restrict__ yloc, const double* __restrict__ Phi,
+                                                           double* __restrict__ cloc) {
+  __shared__ double sv[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * 8 + warp;
+  if (cell >= ncells) return;
+  for (int u = lane; u < NU; u += 32) {
+    const int g = umap[cell * NU + u];
+    sv[warp][u] = g >= 0 ? v[g] : 0.0;
+  }
+  __syncwarp();
+  const double* Mc = M + cell * NU * NU;
+  for (int r = lane; r < NU; r += 32) {
+    double acc = 0.0;
+    for (int k = 0; k < NU; ++k) acc = fma(Mc[k * NU + r], sv[warp][k], acc);   // symmetric: column r
+    yloc[cell * NU + r] = acc;
+  }
+  if (COARSE) {
+    const double* Pc = Phi + cell * NU * 20;
+    if (lane < 20) {
+      double acc = 0.0;
+      for (int u = 0; u < NU; ++u) acc = fma(Pc[u * 20 + lane], sv[warp][u], acc);
+      cloc[cell * 20 + lane] = acc;
+    }
+  }
+}
+
+// y_loc += Phi g_loc  (coarse prolongation, Algorithm 1)
+__global__ void __launch_bounds__(256) cell_prolong_kernel(int ncells, int NU, const double* __restrict__ Phi,
+                                                            const int* __restrict__ cmap, const double* __restrict__ g,
+                                                            double* __restrict__ yloc) {
+  __shared__ double sg[8][20];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * 8 + warp;
+  if (cell >= ncells) return;
+  if (lane < 20) {
+    const int k = cmap[cell * 20 + lane];
+    sg[warp][lane] = k >= 0 ? g[k] : 0.0;
+  }
+  __syncwarp();
+  const double* Pc = Phi + cell * NU * 20;
+  for (int u = lane; u < NU; u += 32) {
+    double acc = yloc[cell * NU + u];
+    for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[warp][j], acc);
+    yloc[cell * NU + u] = acc;
+  }
+}
+
+// z[k] = sum over the cells owning coarse DoF k of c_loc[cell][slot] (fixed order)
+__global__ void coarse_gather_kernel(const int* __restrict__ owners, long long ncoarse, const double* __restrict__ cloc,
+                                     double* __restrict__ z) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncoarse;
+       k += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < 4; ++t) {
+      const int o = owners[4 * k + t];
+      if (o >= 0) s += cloc[o];
+    }
+    z[k] = s;
+  }
+}
+
+// deterministic dot products: fixed-size grid of partial sums, then one block
+__global__ void dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                   double* __restrict__ part) {
+  __shared__ double sw[8];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sw[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
+  __shared__ double sw[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sw[w];
+    *out = t;
+  }
+}
+
+// scalars: [0] rz, [1] pq, [2] rz_new, [3] rr
+__global__ void pcg_update_x_r(long long n, const double* __restrict__ sc, double* __restrict__ x,
+                               double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q) {
+  const double alpha = sc[0] / sc[1];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+__global__ void pcg_update_p(long long n, double* __restrict__ sc, double* __restrict__ p,
+                             const double* __restrict__ z) {
+  const double beta = sc[2] / sc[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void pcg_shift_scalars(double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = sc[2];
+}
+
+// Traction loads on the solid part of the loaded lattice edges (Eq. ELA
+// constitutive: that = j t), one thread per (cell, edge node).
+__device__ int edge_solid(int family, const double* mu4, int e, double* lo, double* hi) {
+  // parameter t along the edge; fixed coordinate c0
+  const double c0 = (e == 1 || e == 3) ? 1.0 : 0.0;
+  double a, b;
+  if (e < 2) {   // vertical edge: mu(c0, t)
+    a = mu4[0] * (1.0 - c0) + mu4[1] * c0;
+    b = (mu4[2] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[1]) * c0;
+  } else {       // horizontal edge: mu(t, c0)
+    a = mu4[0] * (1.0 - c0) + mu4[2] * c0;
+    b = (mu4[1] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[2]) * c0;
+  }
+  int n = 0;
+  if (family == 0) {   // solid outside |xi - c| = mu
+    const double A = 1.0 - b * b, B = -1.0 - 2.0 * a * b, C = (c0 - 0.5) * (c0 - 0.5) + 0.25 - a * a;
+    const double disc = B * B - 4.0 * A * C;
+    if (disc <= 0.0) {
+      lo[0] = 0.0;
+      hi[0] = 1.0;
+      return 1;
+    }
+    const double s = sqrt(disc), r1 = (-B - s) / (2.0 * A), r2 = (-B + s) / (2.0 * A);
+    if (r1 > 0.0) {
+      lo[n] = 0.0;
+      hi[n] = fmin(r1, 1.0);
+      if (hi[n] > lo[n]) ++n;
+    }
+    if (r2 < 1.0) {
+      lo[n] = fmax(r2, 0.0);
+      hi[n] = 1.0;
+      if (hi[n] > lo[n]) ++n;
+    }
+    return n;
+  }
+  // cross: |c0 - 1/2| < a + b t  or  |t - 1/2| < a + b t
+  double l1, h1;
+  const double tt = fabs(c0 - 0.5) - a;
+  bool has1 = true;
+  if (b > 0.0) {
+    l1 = tt / b;
+    h1 = 1e300;
+  } else if (b < 0.0) {
+    l1 = -1e300;
+    h1 = tt / b;
+  } else if (tt < 0.0) {
+    l1 = -1e300;
+    h1 = 1e300;
+  } else {
+    has1 = false;
+    l1 = h1 = 0.0;
+  }
+  const double l2 = (0.5 - a) / (1.0 + b), h2 = (0.5 + a) / (1.0 - b);
+  double L[2], H[2];
+  int m = 0;
+  if (has1) {
+    L[m] = fmax(l1, 0.0);
+    H[m] = fmin(h1, 1.0);
+    if (H[m] > L[m]) ++m;
+  }
+  L[m] = fmax(l2, 0.0);
+  H[m] = fmin(h2, 1.0);
+  if (H[m] > L[m]) ++m;
+  if (m == 2 && L[1] < L[0]) {
+    double t = L[0];
+    L[0] = L[1];
+    L[1] = t;
+    t = H[0];
+    H[0] = H[1];
+    H[1] = t;
+  }
+  for (int i = 0; i < m; ++i) {
+    if (n > 0 && L[i] <= hi[n - 1]) hi[n - 1] = fmax(hi[n - 1], H[i]);
+    else {
+      lo[n] = L[i];
+      hi[n] = H[i];
+      ++n;
+    }
+  }
+  return n;
+}
+
+__global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, const double* __restrict__ mu,
+                             const int32_t* __restrict__ family, const double* __restrict__ trac,
+                             double* __restrict__ fU) {
+  const int p = P.p, nx = P.nx, ny = P.ny;
+  // tasks: for each lattice edge e, its cells, each edge node s
+  const int ncell_e[4] = {ny, ny, nx, nx};
+  long long task = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (int e = 0; e < 4; ++e) {
+    const long long ntask = (long long)ncell_e[e] * (p + 1);
+    if (task >= ntask) {
+      task -= ntask;
+      continue;
+    }
+    const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
+    if (t0 == 0.0 && t1 == 0.0) return;
+    const int j = (int)(task / (p + 1)), s = (int)(task % (p + 1));
+    const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
+    const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
+    const long long cell = cx + (long long)nx * cy;
+    const int k = e == 0 ? (p + 1) * s : e == 1 ? p + (p + 1) * s : e == 2 ? s : s + (p + 1) * p;
+    double lo[3], hi[3];
+    const int nint = edge_solid(family[cell], mu + 4 * cell, e, lo, hi);
+    double acc = 0.0;
+    for (int iv = 0; iv < nint; ++iv) {
+      const double len = hi[iv] - lo[iv];
+      for (int qq = 0; qq < ROMB_NQ; ++qq) {
+        const double t = lo[iv] + len * P.gq_x[qq];
+        const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : t;
+        const double x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : t;
+        double x[2], J[2][2];
+        map_eval(ctrl, nx, P.m, cx, cy, x1, x2, x, J);
+        const int dc = e < 2 ? 1 : 0;
+        double bv[ROMB_MAX_P + 1];
+        cell_basis1d(P, t, bv, nullptr);
+        acc += len * P.gq_w[qq] * hypot(J[0][dc], J[1][dc]) * bv[s];
+      }
+    }
+    const int u = 2 * P.uslot_of_node[k];
+    atomicAdd(&fU[cell * P.nU + u], acc * t0);
+    atomicAdd(&fU[cell * P.nU + u + 1], acc * t1);
+    return;
+  }
+}
+
+// Interior recovery and nodal output: u_I = -L^-T W u_loc (f_I = 0: no body force),
+// one warp per cell.
+__global__ void recover_kernel(CellParams P, const double* __restrict__ LII, const double* __restrict__ W,
+                               const int* __restrict__ umap, const double* __restrict__ x, double* __restrict__ u) {
+  __shared__ double sv[4][64];
+  __shared__ double sy[4][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * 4 + warp;
+  if (cell >= P.ncells) return;
+  const int NI = P.nI, NU = P.nU, p = P.p;
+  for (int t = lane; t < NU; t += 32) {
+    const int g = umap[cell * NU + t];
+    sv[warp][t] = g >= 0 ? x[g] : 0.0;
+  }
+  __syncwarp();
+  const double* Wc = W + cell * NI * NU;
+  for (int i = lane; i < NI; i += 32) {
+    double acc = 0.0;
+    for (int t = 0; t < NU; ++t) acc = fma(Wc[i * NU + t], sv[warp][t], acc);
+    sy[warp][i] = -acc;   // L^-1 f_I - W u with f_I = 0
+  }
+  __syncwarp();
+  const double* L = LII + cell * (NI * (NI + 1) / 2);
+  // backward substitution L^T z = y, one lane at a time per row, dot over lanes
+  for (int i = NI - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1 + lane; k < NI; k += 32) s += L[(long long)k * (k + 1) / 2 + i] * sy[warp][k];
+    s = warp_sum(s);
+    if (lane == 0) sy[warp][i] = (sy[warp][i] - s) / L[(long long)i * (i + 1) / 2 + i];
+    __syncwarp();
+  }
+  const int cx = (int)(cell % P.nx), cy = (int)(cell / P.nx);
+  const long long gnx = (long long)p * P.nx + 1;
+  for (int i = lane; i < NI; i += 32) {
+    const int dof = P.islot[i], k = dof / 2, comp = dof % 2;
+    const int a = k % (p + 1), b = k / (p + 1);
+    u[2 * ((long long)(p * cy + b) * gnx + (p * cx + a)) + comp] = sy[warp][i];
+  }
+}
+
+// skeleton nodes of the nodal output (Dirichlet nodes get 0)
+__global__ void skel_to_nodes_kernel(CellParams P, long long nnodes, const double* __restrict__ x,
+                                     double* __restrict__ u) {
+  const int p = P.p, nx = P.nx, ny = P.ny;
+  const long long NH = (long long)(ny + 1) * (p * nx + 1);
+  const long long gnx = (long long)p * nx + 1;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < nnodes;
+       id += (long long)gridDim.x * blockDim.x) {
+    int gx, gy;
+    skel_node_xy(id, p, nx, NH, &gx, &gy);
+    const bool d = dir_node(P, gx, gy);
+    u[2 * (gy * gnx + gx)] = d ? 0.0 : x[2 * id];
+    u[2 * (gy * gnx + gx) + 1] = d ? 0.0 : x[2 * id + 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static romb_status dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
+  double* part = c->d_red + 64;
+  dot_partial_kernel<<<RED_BLOCKS, 256, 0, c->stream>>>(a, b, n, part);
+  dot_final_kernel<<<1, 256, 0, c->stream>>>(part, RED_BLOCKS, out);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+static int grid_for(const romb_ctx* c, long long n) {
+  long long g = (n + 255) / 256;
+  const long long cap = 8LL * c->sms;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// z = S_BDDC^-1 r  (Algorithm 1)
+static romb_status precondition(romb_ctx* c, const CellParams& P, const double* r, double* z, double* yloc,
+                                double* cloc) {
+  const int cb = (c->ncells + 7) / 8;
+  cell_matvec_kernel<true><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_G, c->d_ucell_map, r, yloc, c->d_Phi,
+                                                      cloc);
+  double* zc = c->d_coarse;
+  double* gc = c->d_coarse + c->ncoarse_all;
+  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->stream>>>(c->d_cowner, c->ncoarse_all, cloc, zc);
+  ROMB_CUDA(cudaGetLastError());
+  romb_status s = coarse_solve(c, zc, gc);
+  if (s != ROMB_OK) return s;
+  cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc);
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, z);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
+  const int cb = (c->ncells + 7) / 8;
+  cell_matvec_kernel<false><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_S, c->d_ucell_map, v, yloc, nullptr,
+                                                       nullptr);
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out);
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, double* d_u, int* iters,
+                      double* relres) {
+  CellParams P;
+  fill_cell_params(c, &P);
+  romb_status s;
+  const long long n = c->nskel;
+  double* yloc = c->d_fU;       // loads first, then cell-local scratch
+  double* cloc = c->d_cloc;
+  // loads -> f
+  ROMB_CUDA(cudaMemcpyAsync(c->d_traction, tr, 64, cudaMemcpyHostToDevice, c->stream));
+  ROMB_CUDA(cudaMemsetAsync(c->d_fU, 0, 8 * (size_t)c->ncells * c->nU, c->stream));
+  {
+    const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
+    loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family,
+                                                                    c->d_traction, c->d_fU);
+    ROMB_CUDA(cudaGetLastError());
+  }
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->d_fU, c->nskel_nodes, c->d_f);
+  double* sc = c->d_red;   // scalars
+  if ((s = dot(c, c->d_f, c->d_f, n, sc + 4)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 4, 8, cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  const double nf = sqrt(c->h_red[0]);
+  ROMB_CUDA(cudaMemsetAsync(c->d_x, 0, 8 * n, c->stream));
+  *iters = 0;
+  *relres = 0.0;
+  romb_status result = ROMB_OK;
+  if (nf > 0.0) {
+    ROMB_CUDA(cudaMemcpyAsync(c->d_r, c->d_f, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpyAsync(c->d_pv, c->d_z, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = dot(c, c->d_r, c->d_z, n, sc + 0)) != ROMB_OK) return s;
+    int it = 0;
+    double rel = 1.0;
+    const int g = grid_for(c, n);
+    while (it < maxit) {
+      if ((s = apply_S(c, P, c->d_pv, c->d_q, yloc)) != ROMB_OK) return s;
+      if ((s = dot(c, c->d_pv, c->d_q, n, sc + 1)) != ROMB_OK) return s;
+      pcg_update_x_r<<<g, 256, 0, c->stream>>>(n, sc, c->d_x, c->d_r, c->d_pv, c->d_q);
+      if ((s = dot(c, c->d_r, c->d_r, n, sc + 3)) != ROMB_OK) return s;
+      ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+      ROMB_CUDA(cudaStreamSynchronize(c->stream));
+      ++it;
+      rel = sqrt(c->h_red[0]) / nf;
+      if (!(rel == rel)) {
+        result = ROMB_E_NAN;
+        break;
+      }
+      if (rel <= rtol) break;
+      if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
+      if ((s = dot(c, c->d_r, c->d_z, n, sc + 2)) != ROMB_OK) return s;
+      pcg_update_p<<<g, 256, 0, c->stream>>>(n, sc, c->d_pv, c->d_z);
+      pcg_shift_scalars<<<1, 32, 0, c->stream>>>(sc);
+      ROMB_CUDA(cudaGetLastError());
+    }
+    *iters = it;
+    *relres = rel;
+    if (result == ROMB_OK && rel > rtol) result = ROMB_E_NOT_CONVERGED;
+  }
+  // recovery + nodal output
+  cudaEventRecord(c->ev[9], c->stream);
+  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, c->stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, c->d_x, d_u);
+  skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->nskel_nodes, c->d_x, d_u);
+  ROMB_CUDA(cudaGetLastError());
+  cudaEventRecord(c->ev[10], c->stream);
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev[9], c->ev[10]);
+  c->phase_ms[5] = ms;
+  return result;
+}

@@ -1,0 +1,190 @@
+// Internal declarations of the romb library (context, device buffers, kernel
+// launchers).  Everything here is private to the shared library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/romb.h"
+
+#define ROMB_MAX_FAMILIES 4
+#define ROMB_MAX_P 8
+#define ROMB_NSLOT 20      // local coarse slots: 4 corners x 2 + 4 edges x 3
+
+// Per-cell error bits (romb_stats flags).
+#define ROMB_FLAG_OUT_OF_BOX 1
+#define ROMB_FLAG_BAD_MAP 2
+#define ROMB_FLAG_NOT_SPD 4
+#define ROMB_FLAG_NAN 8
+
+#define ROMB_CUDA(call)                                                     \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      romb_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      return ROMB_E_CUDA;                                                   \
+    }                                                                       \
+  } while (0)
+
+void romb_set_error(const std::string& s);
+
+// One loaded reduced model (Sec. 4.2), resident in HBM.
+struct RombRom {
+  bool loaded = false;
+  int family = -1, kind = 0, p = 0, q = 0, r = 0, n_r = 0;
+  double lo = 0, hi = 0;
+  long long n_half = 0;        // pairs k1 <= k2 times 4 (q+1)^2 columns
+  double* U64 = nullptr;       // [(n_r+1)][n_half]: row 0 = I_Pi, rows 1.. = U_r
+  float* Uhi = nullptr;        // same, tf32/bf16 hi part (tensor-core forms)
+  float* Ulo = nullptr;        // same, lo part
+  double* A = nullptr;         // [n_r][(r+1)^4]
+  double* At = nullptr;        // [(r+1)^4][n_r]
+  int kpad = 0;                // n_r+1 rounded up for the tensor-core K dimension
+};
+
+// Nested-dissection coarse solver (a5): symbolic tree built on the host from
+// the lattice shape, numeric fronts on the device.
+struct NdFront {
+  int ns = 0, nb = 0;          // eliminated (separator) rows, update (boundary) rows
+  long long off = 0;           // offset of the dense front (n x n, n = ns + nb) in the pool
+  long long upd_off = 0;       // offset of its update matrix (nb x nb)
+  int level = 0, parent = -1;
+  long long idx_off = 0;       // offset of its n global coarse indices
+  std::vector<int> children;
+};
+
+struct NdPlan {
+  int n = 0;                   // coarse unknowns (Dirichlet ones excluded)
+  std::vector<NdFront> fronts;
+  std::vector<std::vector<int>> levels;   // front ids per level, leaves first
+  long long pool = 0, upd_pool = 0, idx_total = 0;
+  // device
+  double* F = nullptr;         // dense fronts
+  double* Upd = nullptr;       // update matrices
+  int* idx = nullptr;          // global coarse index of each front row
+  int* d_meta = nullptr;       // per-front {ns, nb, off_lo, off_hi, upd_lo, upd_hi, idx_lo, idx_hi}
+  // child extend-add maps: for each child row, its position in the parent front
+  int* d_cmap = nullptr;
+  long long cmap_total = 0;
+  std::vector<long long> cmap_off;        // per front (as child)
+  // cell -> leaf assembly: for each cell its leaf and the leaf-row of each slot
+  int* d_cell_leaf = nullptr;
+  int* d_cell_pos = nullptr;              // [cells][20], -1 absent
+  double* d_rhs = nullptr;                // [n] work vector
+  double* d_ybuf = nullptr;               // per-front update buffers for solves
+  long long ybuf_total = 0;
+  std::vector<long long> ybuf_off;
+  int* d_ybuf_off = nullptr;
+  int* d_children = nullptr;              // flattened child lists
+  int* d_child_off = nullptr;             // [nfronts+1]
+  std::vector<int*> d_level_fronts;       // per level: device list of front ids
+  int max_ns_small = 0;
+};
+
+struct romb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0, used = 0, rom_bytes = 0;
+  int sms = 0;
+  std::vector<void*> allocs;       // lattice-dependent buffers
+  std::vector<void*> rom_allocs;   // loaded reduced models
+  std::unordered_map<void*, size_t> sizes;
+
+  RombRom roms[ROMB_MAX_FAMILIES];
+
+  // lattice
+  bool have_lattice = false, assembled = false, factored = false;
+  int nx = 0, ny = 0, p = 0, m = 0, basis = 0, ncells = 0, mem = 0;
+  int nB = 0, ndof = 0, nI = 0, nU = 0, q = 2, nL = 9;
+  long long kpack = 0, upack = 0;   // packed sizes of K and of nU x nU
+  double E = 1, nu = 0.3, rho = 0;
+  unsigned dmask = 0;
+  double traction[8] = {0};
+  int prec = 0;
+
+  double* d_ctrl = nullptr;
+  double* d_mu = nullptr;
+  int32_t* d_family = nullptr;
+  int32_t* d_flags = nullptr;
+
+  // per-cell arrays
+  double* d_chat = nullptr;     // [cells][nL][16]
+  double* d_theta = nullptr;    // [cells][kmax]
+  float* d_theta_hi = nullptr;  // [cells][kpad] tensor-core operand (hi)
+  float* d_theta_lo = nullptr;  // [cells][kpad] (lo)
+  int* d_famlist = nullptr;     // cells grouped by family
+  int2* d_pairs = nullptr;      // (k1, k2), k1 <= k2, in pair order
+  int famcount[ROMB_MAX_FAMILIES] = {0};
+  int famstart[ROMB_MAX_FAMILIES] = {0};
+  double* d_K = nullptr;        // [cells][kpack]
+  double* d_kdiag = nullptr;    // [cells][nU] diagonal of K at the skeleton slots
+  double* d_ktot = nullptr;     // [skeleton DoFs] sum of the diagonals of sharing cells
+  double* d_LII = nullptr;      // [cells][nI(nI+1)/2] Cholesky factor of K_II, packed lower
+  double* d_W = nullptr;        // [cells][nI][nU]  L_II^-1 K_IU
+  double* d_S = nullptr;        // [cells][upack]
+  double* d_G = nullptr;        // [cells][upack]   D F D
+  double* d_Phi = nullptr;      // [cells][nU][20]  D Psi
+  double* d_Psi = nullptr;      // [cells][nU][20]
+  double* d_SCl = nullptr;      // [cells][20][20]
+  double* d_D = nullptr;        // [cells][nU]
+
+  // skeleton
+  long long nskel_nodes = 0, nskel = 0;   // nodes / DoFs (Dirichlet ones included, masked)
+  int* d_ucell_map = nullptr;   // [cells][nU] skeleton DoF of each local U slot (-1 Dirichlet)
+  int* d_islot = nullptr;       // [nI] local DoF of each interior slot (device table)
+  int* d_uslot = nullptr;       // [nU] local DoF of each skeleton slot
+
+  // coarse
+  long long ncoarse_all = 0;    // all coarse DoFs incl. Dirichlet (masked)
+  int* d_cmap = nullptr;        // [cells][20] global coarse DoF (-1 absent)
+  int* d_cnum = nullptr;        // [ncoarse_all] -> ND unknown (-1 Dirichlet)
+  NdPlan nd;
+
+  // PCG work vectors (skeleton length)
+  double *d_f = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr;
+  double* d_coarse = nullptr;   // [ncoarse_all]
+  double* d_red = nullptr;      // reduction scratch
+  double* h_red = nullptr;      // pinned host copy
+  double* d_fI = nullptr;       // [cells][nI] interior forces
+  double* d_fU = nullptr;       // [cells][nU] skeleton-slot forces
+  double* d_cloc = nullptr;     // [cells][20] coarse restriction Psi^T D r
+  int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
+  double* d_u = nullptr;        // nodal output [nodes][2]
+  double* d_traction = nullptr;
+
+  // timing
+  cudaEvent_t ev[16];
+  double phase_ms[8] = {0};
+};
+
+// allocation helpers (respect the budget)
+romb_status romb_alloc(romb_ctx* c, void** p, size_t bytes);
+romb_status romb_alloc_persist(romb_ctx* c, void** p, size_t bytes);
+void romb_free_lattice(romb_ctx* c);
+template <class T>
+inline romb_status romb_alloc_t(romb_ctx* c, T** p, size_t n) {
+  return romb_alloc(c, (void**)p, n * sizeof(T));
+}
+void romb_free_all(romb_ctx* c);
+
+// kernel launchers (each returns ROMB_OK or ROMB_E_CUDA)
+romb_status launch_theta(romb_ctx* c);
+romb_status launch_assemble_fp64(romb_ctx* c);
+romb_status launch_assemble_tc(romb_ctx* c);
+romb_status launch_factor(romb_ctx* c);
+romb_status coarse_build(romb_ctx* c);      // symbolic (once per lattice shape)
+romb_status coarse_factor(romb_ctx* c);     // numeric
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out);
+romb_status launch_ktot(romb_ctx* c);
+romb_status launch_flag_or(romb_ctx* c, int* d_any);
+romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
+romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxit, double* d_u_out,
+                      int* iters, double* relres);
+
+// small host helpers
+inline long long tri(long long n) { return n * (n + 1) / 2; }

@@ -1,0 +1,525 @@
+// Offline ROM training (Sec. 4.2, offline phase of Sec. 4.4), host C++.
+//
+// Snapshots I(mu) of Eq. (MDEIM I) are computed from the Legendre moments of the
+// trimmed cell, M[a][b] = int_Omega P_a(2 xi1 - 1) P_b(2 xi2 - 1): every entry of
+// I is a product f(xi1) g(xi2) of 1D polynomials of degree <= 2p+q, so
+// I = F^T M G with F, G the Legendre coefficients of those 1D products.  The
+// moments use the height-function form of the quadrature (Sec. 2.2.3): along
+// xi2 the level set's roots are closed-form for the bilinear threshold and the
+// Legendre antiderivatives integrate each solid interval exactly; along xi1 an
+// adaptive Gauss rule is refined until the moment matrix converges.
+//
+// U_r: eigen-decomposition of the snapshot Gram matrix (cyclic Jacobi), the
+// leading n_r left singular vectors re-orthonormalised (Sec. 4.2.2).
+// Magic points: Algorithm 3 with the interpolatory projection of empirical
+// interpolation.  I_r at the (r+1)^4 tensor GLL nodes of the box from the
+// magic-point entries (Sec. 4.2.3).  Output: the ROM file of romb.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <thread>
+#include <vector>
+
+#include "romb_internal.cuh"
+#include "tables.cuh"
+
+namespace {
+
+// Legendre P_0..P_n at t in [-1, 1]
+inline void legendre(int n, double t, double* P) {
+  P[0] = 1.0;
+  if (n >= 1) P[1] = t;
+  for (int k = 2; k <= n; ++k) P[k] = ((2 * k - 1) * t * P[k - 1] - (k - 1) * P[k - 2]) / k;
+}
+
+// int_0^y P_b(2s - 1) ds for b = 0..n  (needs P up to n+1)
+inline void legendre_antideriv(int n, double y, double* out) {
+  double P[64];
+  const double t = 2.0 * y - 1.0;
+  legendre(n + 1, t, P);
+  out[0] = y;
+  for (int b = 1; b <= n; ++b) out[b] = 0.5 * (P[b + 1] - P[b - 1]) / (2 * b + 1);
+}
+
+// solid intervals of [0,1] in xi2 at xi1 = x (bilinear threshold)
+int solid_y(int family, const double* mu, double x, double* lo, double* hi) {
+  const double a = mu[0] * (1.0 - x) + mu[1] * x;
+  const double b = (mu[2] - mu[0]) * (1.0 - x) + (mu[3] - mu[1]) * x;
+  int n = 0;
+  if (family == 0) {
+    const double A = 1.0 - b * b, B = -1.0 - 2.0 * a * b, C = (x - 0.5) * (x - 0.5) + 0.25 - a * a;
+    const double disc = B * B - 4.0 * A * C;
+    if (disc <= 0.0) {
+      lo[0] = 0.0;
+      hi[0] = 1.0;
+      return 1;
+    }
+    const double s = sqrt(disc), r1 = (-B - s) / (2.0 * A), r2 = (-B + s) / (2.0 * A);
+    if (r1 > 0.0 && fmin(r1, 1.0) > 0.0) {
+      lo[n] = 0.0;
+      hi[n++] = fmin(r1, 1.0);
+    }
+    if (r2 < 1.0 && fmax(r2, 0.0) < 1.0) {
+      lo[n] = fmax(r2, 0.0);
+      hi[n++] = 1.0;
+    }
+    return n;
+  }
+  double L[2], H[2];
+  int m = 0;
+  const double t = fabs(x - 0.5) - a;
+  double l1 = 0, h1 = 0;
+  bool has1 = true;
+  if (b > 0.0) {
+    l1 = t / b;
+    h1 = 2.0;
+  } else if (b < 0.0) {
+    l1 = -1.0;
+    h1 = t / b;
+  } else if (t < 0.0) {
+    l1 = -1.0;
+    h1 = 2.0;
+  } else {
+    has1 = false;
+  }
+  if (has1 && fmin(h1, 1.0) > fmax(l1, 0.0)) {
+    L[m] = fmax(l1, 0.0);
+    H[m++] = fmin(h1, 1.0);
+  }
+  const double l2 = (0.5 - a) / (1.0 + b), h2 = (0.5 + a) / (1.0 - b);
+  if (fmin(h2, 1.0) > fmax(l2, 0.0)) {
+    L[m] = fmax(l2, 0.0);
+    H[m++] = fmin(h2, 1.0);
+  }
+  if (m == 2 && L[1] < L[0]) {
+    std::swap(L[0], L[1]);
+    std::swap(H[0], H[1]);
+  }
+  for (int i = 0; i < m; ++i) {
+    if (n > 0 && L[i] <= hi[n - 1]) hi[n - 1] = fmax(hi[n - 1], H[i]);
+    else {
+      lo[n] = L[i];
+      hi[n++] = H[i];
+    }
+  }
+  return n;
+}
+
+struct Trainer {
+  int family, kind, p, q, r, n_r;
+  double lo, hi;
+  int nB, nL, D, n_i, nF;
+  std::vector<double> F;    // [nF][D+1] Legendre coefficients of the xi1 factors (= xi2 factors)
+  std::vector<double> gx, gw;   // outer Gauss rule on [0,1]
+
+  void setup(const romb_train_spec& s) {
+    family = s.family;
+    kind = s.basis;
+    p = s.p;
+    q = s.q;
+    r = s.r;
+    n_r = s.n_r;
+    lo = s.lo;
+    hi = s.hi;
+    init();
+  }
+
+  void init() {
+    nB = (p + 1) * (p + 1);
+    nL = (q + 1) * (q + 1);
+    D = 2 * p + q;
+    n_i = nB * nB * nL * 4;
+    // 1D factor (a1, d1, a2, d2, c): b^(d1)_a1 b^(d2)_a2 l_c, index ((((a1*2+d1)*(p+1)+a2)*2+d2)*(q+1)+c)
+    nF = (p + 1) * 2 * (p + 1) * 2 * (q + 1);
+    F.assign((size_t)nF * (D + 1), 0.0);
+    const int ng = D + 1;
+    std::vector<double> x(ng), w(ng);
+    gauss01(ng, x.data(), w.data());
+    double gll[ROMB_MAX_P + 1], qn[8];
+    gll_nodes01(p, gll);
+    gll_nodes01(q, qn);
+    for (int g = 0; g < ng; ++g) {
+      double bv[ROMB_MAX_P + 1], bd[ROMB_MAX_P + 1], lv[8], P[64];
+      if (kind == 0) lagrange1d_host(p, gll, x[g], bv, bd);
+      else bernstein1d_host(p, x[g], bv, bd);
+      lagrange1d_host(q, qn, x[g], lv, nullptr);
+      legendre(D, 2.0 * x[g] - 1.0, P);
+      for (int a1 = 0; a1 <= p; ++a1)
+        for (int d1 = 0; d1 < 2; ++d1)
+          for (int a2 = 0; a2 <= p; ++a2)
+            for (int d2 = 0; d2 < 2; ++d2)
+              for (int cc = 0; cc <= q; ++cc) {
+                const int f = (((a1 * 2 + d1) * (p + 1) + a2) * 2 + d2) * (q + 1) + cc;
+                const double v = (d1 ? bd[a1] : bv[a1]) * (d2 ? bd[a2] : bv[a2]) * lv[cc];
+                for (int a = 0; a <= D; ++a) F[(size_t)f * (D + 1) + a] += (2 * a + 1) * w[g] * v * P[a];
+              }
+    }
+    gx.resize(20);
+    gw.resize(20);
+    gauss01(20, gx.data(), gw.data());
+  }
+
+  static void lagrange1d_host(int n, const double* nodes, double t, double* v, double* d) {
+    for (int i = 0; i <= n; ++i) {
+      double den = 1.0, val = 1.0, der = 0.0;
+      for (int j = 0; j <= n; ++j) {
+        if (j == i) continue;
+        den *= nodes[i] - nodes[j];
+        der = der * (t - nodes[j]) + val;
+        val *= t - nodes[j];
+      }
+      v[i] = val / den;
+      if (d) d[i] = der / den;
+    }
+  }
+  static void bernstein1d_host(int p, double t, double* v, double* d) {
+    double binom = 1.0;
+    for (int i = 0; i <= p; ++i) {
+      if (i > 0) binom = binom * (p - i + 1) / i;
+      v[i] = binom * pow(t, i) * pow(1.0 - t, p - i);
+      double dv = 0.0;
+      if (i > 0) dv += binom * i * pow(t, i - 1) * pow(1.0 - t, p - i);
+      if (i < p) dv -= binom * (p - i) * pow(t, i) * pow(1.0 - t, p - i - 1);
+      d[i] = dv;
+    }
+  }
+
+  // moments of the solid part over xi1 in [a, b] with one 20-point Gauss panel
+  void panel(const double* mu, double a, double b, double* M) const {
+    const int n = D + 1;
+    for (int i = 0; i < n * n; ++i) M[i] = 0.0;
+    double lo[4], hi[4], P[64], Au[64], Av[64], inner[64];
+    for (int g = 0; g < 20; ++g) {
+      const double x = a + (b - a) * gx[g], w = (b - a) * gw[g];
+      const int ni = solid_y(family, mu, x, lo, hi);
+      for (int t = 0; t < n; ++t) inner[t] = 0.0;
+      for (int k = 0; k < ni; ++k) {
+        legendre_antideriv(D, lo[k], Au);
+        legendre_antideriv(D, hi[k], Av);
+        for (int t = 0; t < n; ++t) inner[t] += Av[t] - Au[t];
+      }
+      legendre(D, 2.0 * x - 1.0, P);
+      for (int s = 0; s < n; ++s) {
+        const double ws = w * P[s];
+        for (int t = 0; t < n; ++t) M[s * n + t] += ws * inner[t];
+      }
+    }
+  }
+
+  void moments(const double* mu, double* M) const {
+    const int n = D + 1, nn = n * n;
+    for (int i = 0; i < nn; ++i) M[i] = 0.0;
+    struct Item {
+      double a, b;
+      int depth;
+      std::vector<double> Mp;
+    };
+    std::vector<Item> stack;
+    for (int h = 0; h < 2; ++h) {
+      Item it{0.5 * h, 0.5 * h + 0.5, 0, std::vector<double>(nn)};
+      panel(mu, it.a, it.b, it.Mp.data());
+      stack.push_back(std::move(it));
+    }
+    std::vector<double> L(nn), R(nn);
+    while (!stack.empty()) {
+      Item it = std::move(stack.back());
+      stack.pop_back();
+      const double m = 0.5 * (it.a + it.b);
+      panel(mu, it.a, m, L.data());
+      panel(mu, m, it.b, R.data());
+      double err = 0.0;
+      for (int i = 0; i < nn; ++i) err = fmax(err, fabs(it.Mp[i] - L[i] - R[i]));
+      if (err <= 1e-15 || it.depth >= 50) {
+        for (int i = 0; i < nn; ++i) M[i] += L[i] + R[i];
+      } else {
+        stack.push_back(Item{it.a, m, it.depth + 1, L});
+        stack.push_back(Item{m, it.b, it.depth + 1, R});
+      }
+    }
+  }
+
+  // factor indices of entry e of I
+  inline void factors(int e, int* f, int* g) const {
+    const int j2 = e & 1, j1 = (e >> 1) & 1;
+    int t = e >> 2;
+    const int k3 = t % nL;
+    t /= nL;
+    const int k2 = t % nB, k1 = t / nB;
+    const int a1 = k1 % (p + 1), b1 = k1 / (p + 1), a2 = k2 % (p + 1), b2 = k2 / (p + 1);
+    const int c1 = k3 % (q + 1), c2 = k3 / (q + 1);
+    // xi1 factor: derivative where j == 0; xi2 factor: derivative where j == 1
+    *f = (((a1 * 2 + (j1 == 0)) * (p + 1) + a2) * 2 + (j2 == 0)) * (q + 1) + c1;
+    *g = (((b1 * 2 + (j1 == 1)) * (p + 1) + b2) * 2 + (j2 == 1)) * (q + 1) + c2;
+  }
+
+  // I (all entries) from the moment matrix
+  void snapshot_from_moments(const double* M, double* I) const {
+    const int n = D + 1;
+    std::vector<double> H((size_t)n * nF);   // H[a][g] = sum_b M[a][b] G[g][b]
+    for (int a = 0; a < n; ++a)
+      for (int g = 0; g < nF; ++g) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += M[a * n + b] * F[(size_t)g * n + b];
+        H[(size_t)a * nF + g] = s;
+      }
+    for (int e = 0; e < n_i; ++e) {
+      int f, g;
+      factors(e, &f, &g);
+      double s = 0.0;
+      for (int a = 0; a < n; ++a) s += F[(size_t)f * n + a] * H[(size_t)a * nF + g];
+      I[e] = s;
+    }
+  }
+
+  double entry_from_moments(const double* M, int e) const {
+    const int n = D + 1;
+    int f, g;
+    factors(e, &f, &g);
+    double s = 0.0;
+    for (int a = 0; a < n; ++a) {
+      double h = 0.0;
+      for (int b = 0; b < n; ++b) h += M[a * n + b] * F[(size_t)g * n + b];
+      s += F[(size_t)f * n + a] * h;
+    }
+    return s;
+  }
+};
+
+template <class Fn>
+void parallel_for(int n, int nthreads, Fn fn) {
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&]() {
+      for (int i = next++; i < n; i = next++) fn(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+// symmetric eigen-decomposition by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w, vectors V (columns)
+void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int pp = 0; pp < n - 1; ++pp)
+      for (int qq = pp + 1; qq < n; ++qq) {
+        const double apq = A[(size_t)pp * n + qq];
+        if (fabs(apq) < 1e-300) continue;
+        const double app = A[(size_t)pp * n + pp], aqq = A[(size_t)qq * n + qq];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[(size_t)k * n + pp], akq = A[(size_t)k * n + qq];
+          A[(size_t)k * n + pp] = c * akp - s * akq;
+          A[(size_t)k * n + qq] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[(size_t)pp * n + k], aqk = A[(size_t)qq * n + k];
+          A[(size_t)pp * n + k] = c * apk - s * aqk;
+          A[(size_t)qq * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[(size_t)k * n + pp], vkq = V[(size_t)k * n + qq];
+          V[(size_t)k * n + pp] = c * vkp - s * vkq;
+          V[(size_t)k * n + qq] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// LU with partial pivoting (n small): solve A x = b for many b
+struct LU {
+  int n;
+  std::vector<double> a;
+  std::vector<int> piv;
+  bool factor(int n_, const std::vector<double>& A) {
+    n = n_;
+    a = A;
+    piv.resize(n);
+    for (int k = 0; k < n; ++k) {
+      int m = k;
+      for (int i = k + 1; i < n; ++i)
+        if (fabs(a[(size_t)i * n + k]) > fabs(a[(size_t)m * n + k])) m = i;
+      piv[k] = m;
+      if (a[(size_t)m * n + k] == 0.0) return false;
+      if (m != k)
+        for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)m * n + j]);
+      for (int i = k + 1; i < n; ++i) {
+        a[(size_t)i * n + k] /= a[(size_t)k * n + k];
+        for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
+      }
+    }
+    return true;
+  }
+  void solve(double* b) const {
+    for (int k = 0; k < n; ++k) std::swap(b[k], b[piv[k]]);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < i; ++k) b[i] -= a[(size_t)i * n + k] * b[k];
+    for (int i = n - 1; i >= 0; --i) {
+      for (int k = i + 1; k < n; ++k) b[i] -= a[(size_t)i * n + k] * b[k];
+      b[i] /= a[(size_t)i * n + i];
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" romb_status romb_train_snapshot(const romb_train_spec* sp, const double* mu4, double* I_out) {
+  if (!sp || !mu4 || !I_out || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family != 0 && sp->family != 1))
+    return ROMB_E_ARG;
+  Trainer T;
+  T.setup(*sp);
+  std::vector<double> M((size_t)(T.D + 1) * (T.D + 1));
+  T.moments(mu4, M.data());
+  T.snapshot_from_moments(M.data(), I_out);
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_train(const romb_train_spec* sp, const double* samples, int n_s, const char* path) {
+  if (!sp || !samples || !path || n_s < 1 || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || sp->r < 1 ||
+      sp->r > 10 || sp->n_r < 1 || sp->n_r > 127 || sp->n_r > n_s || !(sp->hi > sp->lo) ||
+      (sp->family != 0 && sp->family != 1) || (sp->basis != 0 && sp->basis != 1))
+    return ROMB_E_ARG;
+  Trainer T;
+  T.setup(*sp);
+  const int nth = sp->n_threads > 0 ? sp->n_threads : std::max(1u, std::thread::hardware_concurrency());
+  const int n_i = T.n_i, nm = (T.D + 1) * (T.D + 1);
+  // snapshots (column s contiguous)
+  std::vector<double> S((size_t)n_s * n_i);
+  parallel_for(n_s, nth, [&](int s) {
+    std::vector<double> M(nm);
+    T.moments(samples + 4 * s, M.data());
+    T.snapshot_from_moments(M.data(), &S[(size_t)s * n_i]);
+  });
+  // Gram matrix and its eigen-decomposition
+  std::vector<double> G((size_t)n_s * n_s);
+  parallel_for(n_s, nth, [&](int i) {
+    for (int j = 0; j <= i; ++j) {
+      const double* a = &S[(size_t)i * n_i];
+      const double* b = &S[(size_t)j * n_i];
+      double s = 0.0;
+      for (int e = 0; e < n_i; ++e) s += a[e] * b[e];
+      G[(size_t)i * n_s + j] = G[(size_t)j * n_s + i] = s;
+    }
+  });
+  std::vector<double> w, V;
+  jacobi_eig(n_s, G, w, V);
+  std::vector<int> order(n_s);
+  for (int i = 0; i < n_s; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+  const int n_r = sp->n_r;
+  // U_r columns = S v / sigma, then two passes of Gram-Schmidt
+  std::vector<double> U((size_t)n_r * n_i, 0.0);
+  parallel_for(n_r, nth, [&](int k) {
+    const int j = order[k];
+    double* u = &U[(size_t)k * n_i];
+    for (int s = 0; s < n_s; ++s) {
+      const double v = V[(size_t)s * n_s + j];
+      const double* col = &S[(size_t)s * n_i];
+      for (int e = 0; e < n_i; ++e) u[e] += v * col[e];
+    }
+  });
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < n_r; ++k) {
+      double* u = &U[(size_t)k * n_i];
+      for (int l = 0; l < k; ++l) {
+        const double* v = &U[(size_t)l * n_i];
+        double d = 0.0;
+        for (int e = 0; e < n_i; ++e) d += u[e] * v[e];
+        for (int e = 0; e < n_i; ++e) u[e] -= d * v[e];
+      }
+      double nrm = 0.0;
+      for (int e = 0; e < n_i; ++e) nrm += u[e] * u[e];
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0)) return ROMB_E_NAN;
+      for (int e = 0; e < n_i; ++e) u[e] /= nrm;
+    }
+  // magic points (Algorithm 3, interpolatory projection)
+  std::vector<long long> magic(n_r);
+  {
+    auto argmax_abs = [&](const std::vector<double>& v) {
+      int m = 0;
+      for (int e = 1; e < n_i; ++e)
+        if (fabs(v[e]) > fabs(v[m])) m = e;
+      return m;
+    };
+    std::vector<double> res(U.begin(), U.begin() + n_i);
+    magic[0] = argmax_abs(res);
+    for (int j = 1; j < n_r; ++j) {
+      std::vector<double> A((size_t)j * j), c(j);
+      for (int a = 0; a < j; ++a) {
+        for (int b = 0; b < j; ++b) A[(size_t)a * j + b] = U[(size_t)b * n_i + magic[a]];
+        c[a] = U[(size_t)j * n_i + magic[a]];
+      }
+      LU lu;
+      if (!lu.factor(j, A)) return ROMB_E_NAN;
+      lu.solve(c.data());
+      for (int e = 0; e < n_i; ++e) {
+        double s = U[(size_t)j * n_i + e];
+        for (int b = 0; b < j; ++b) s -= U[(size_t)b * n_i + e] * c[b];
+        res[e] = s;
+      }
+      magic[j] = argmax_abs(res);
+    }
+  }
+  // interpolation samples on the tensor GLL grid
+  const int n1 = sp->r + 1;
+  const int ng = n1 * n1 * n1 * n1;
+  double g1d[12];
+  gll_nodes01(sp->r, g1d);
+  std::vector<double> Um((size_t)n_r * n_r);
+  for (int a = 0; a < n_r; ++a)
+    for (int b = 0; b < n_r; ++b) Um[(size_t)a * n_r + b] = U[(size_t)b * n_i + magic[a]];
+  LU lu;
+  if (!lu.factor(n_r, Um)) return ROMB_E_NAN;
+  std::vector<double> A((size_t)n_r * ng);
+  parallel_for(ng, nth, [&](int g) {
+    const int i1 = g % n1, i2 = (g / n1) % n1, i3 = (g / (n1 * n1)) % n1, i4 = g / (n1 * n1 * n1);
+    const double mu[4] = {sp->lo + (sp->hi - sp->lo) * g1d[i1], sp->lo + (sp->hi - sp->lo) * g1d[i2],
+                          sp->lo + (sp->hi - sp->lo) * g1d[i3], sp->lo + (sp->hi - sp->lo) * g1d[i4]};
+    std::vector<double> M(nm), b(n_r);
+    T.moments(mu, M.data());
+    for (int a = 0; a < n_r; ++a) b[a] = T.entry_from_moments(M.data(), (int)magic[a]);
+    lu.solve(b.data());
+    for (int a = 0; a < n_r; ++a) A[(size_t)a * ng + g] = b[a];
+  });
+  // I_Pi: untrimmed moments are e_0 e_0^T
+  std::vector<double> Ipi(n_i);
+  {
+    std::vector<double> M(nm, 0.0);
+    M[0] = 1.0;
+    T.snapshot_from_moments(M.data(), Ipi.data());
+  }
+  FILE* f = fopen(path, "wb");
+  if (!f) return ROMB_E_ARG;
+  unsigned char hdr[128];
+  memset(hdr, 0, sizeof(hdr));
+  memcpy(hdr, "ROMBDDC1", 8);
+  const int32_t iv[8] = {1, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
+  memcpy(hdr + 8, iv, 32);
+  const double lohi[2] = {sp->lo, sp->hi};
+  memcpy(hdr + 40, lohi, 16);
+  const int64_t ni64 = n_i;
+  memcpy(hdr + 56, &ni64, 8);
+  bool ok = fwrite(hdr, 1, 128, f) == 128;
+  ok = ok && fwrite(Ipi.data(), 8, n_i, f) == (size_t)n_i;
+  ok = ok && fwrite(U.data(), 8, U.size(), f) == U.size();
+  ok = ok && fwrite(A.data(), 8, A.size(), f) == A.size();
+  ok = ok && fwrite(magic.data(), 8, n_r, f) == (size_t)n_r;
+  fclose(f);
+  return ok ? ROMB_OK : ROMB_E_ARG;
+}
