@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: cells/s assembled + solved by the ROM-accelerated BDDC path.
+
+Workload: 132 x 132 = 17,424 cells, p = 6, quartic maps from a smooth random
+field, circle-hole and cross families mixed 50/50, one reduced model of rank 60
+per family (trained by the library's host trainer before timing), rho = 5e-4,
+left edge clamped, unit downward traction on the right edge, PCG rtol 1e-8.
+
+One step = romb_assemble (theta + contraction) -> romb_factor (local BDDC
+set-up + coarse Cholesky) -> romb_bddc_solve (PCG + interior recovery).
+`value` times steps whose inputs are already resident in HBM (device pointers);
+`e2e` times the same calls with pinned host inputs and a host read of the
+displacement inside the timed region.  L2 is flushed (a 512 MB write) between
+timed steps, outside the timed events.
+
+--impl reference times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cells/s assembled+solved at 17,424 cells p=6; FP32 vs FP64 form at ≤1e-6 error"
+CONFIG = 3
+SAMPLE_NX = SAMPLE_NY = 16      # bounded CPU sample per reference-arm step
+BASE_NX = BASE_NY = 24          # bounded CPU sample of the cpu_baseline leg (~15 s)
+FP64_PEAK_GFLOPS = 1250.0       # nominal dense FP64 rate of GB300 (profiling recipe)
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32split"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-json", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--rom-dir", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# shared set-up
+# ---------------------------------------------------------------------------
+def train_models(rom_dir: str):
+    """Offline phase: the library's host trainer, LHS samples from the seeded inputs."""
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+    paths = []
+    t0 = time.time()
+    for spec in LI.rom_specs(CONFIG):
+        path = os.path.join(rom_dir, f"family{spec.family}.rom")
+        if not os.path.exists(path):
+            S = LI.lhs(spec.n_s, spec.lo, spec.hi, seed=spec.seed)
+            romb.romb_train(spec.family, 0, spec.p, spec.r, spec.n_r, spec.lo, spec.hi, S, path)
+        paths.append(path)
+    return paths, time.time() - t0
+
+
+def sub_lattice(lat, sx: int, sy: int):
+    """The first sx x sy cells of a lattice (same maps, thresholds, families)."""
+    import numpy as np
+    import lattice_inputs as LI
+    m = lat.m
+    G = lat.ctrl.reshape(m * lat.ny + 1, m * lat.nx + 1, 2)[: m * sy + 1, : m * sx + 1]
+    cells = (np.arange(sy)[:, None] * lat.nx + np.arange(sx)[None, :]).ravel()
+    return LI.Lattice(nx=sx, ny=sy, p=lat.p, m=m, basis=lat.basis, ctrl=np.ascontiguousarray(G.reshape(-1, 2)),
+                      mu=lat.mu[cells].copy(), family=lat.family[cells].copy(), E=lat.E, nu=lat.nu, rho=lat.rho,
+                      dirichlet_mask=lat.dirichlet_mask, traction=lat.traction.copy(), name=lat.name + "-sample")
+
+
+def oracle_sample_seconds(rom_paths, steps: int = 1, nx: int = SAMPLE_NX, ny: int = SAMPLE_NY):
+    """Time the oracle's online phase (MDEIM assembly, BDDC set-up, PCG,
+    recovery) on a bounded sample; returns (seconds per step, cells)."""
+    import lattice_inputs as LI
+    from oracle import bddc as obddc, pipeline, rom as orom
+    lat = sub_lattice(LI.config(CONFIG), nx, ny)
+    roms = {}
+    for p in rom_paths:
+        R = orom.read(p)
+        roms[R.family] = R
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        K = pipeline.matrices_rom(lat, roms)
+        pipeline.solve(lat, K, obddc.lattice_loads(lat), rtol=1e-8)
+        times.append(time.perf_counter() - t0)
+    return times, lat.ncells
+
+
+def cpu_baseline(rom_paths):
+    """The oracle, single-threaded, in a child process (threads fixed before numpy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.NamedTemporaryFile(suffix=".json", delete=False) as f:
+        out = f.name
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-json", out, "--rom-dir",
+           os.path.dirname(rom_paths[0])]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "cells/s", "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    d = json.load(open(out))
+    os.unlink(out)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile(suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.file.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# flop models (algorithmic counts per cell, documented in the design doc)
+# ---------------------------------------------------------------------------
+def factor_flops(p: int) -> float:
+    NI, NU = 2 * (p - 1) ** 2, 8 * p
+    NK = NU - 8
+    f = NI ** 3 / 3 + NI ** 2 * NU + NU * (NU + 1) * NI          # chol K_II, W, S
+    f += NK ** 3 / 3 + NK ** 2 * 12 + 12 * 13 * NK               # chol Shat, Y, That
+    f += 2 * NK ** 2 * 20 + 2 * 12 * NK * 20 + 2 * 144 * 20      # Z, R, Lambda
+    f += 2 * NK * 12 * 20 + NK ** 2 * 20                         # Y Lambda, Lhat^-T
+    f += 2 * NU * NU * 20 + 2 * 400 * NU                         # S Psi, Psi^T S Psi
+    f += NK ** 3 / 3 + 144 * NK + 12 * NK ** 2 + NK * NK * (NK / 3 + 12)   # M, V, N, F
+    return f
+
+
+def assembly_flops(p: int, n_r: int) -> float:
+    nB = (p + 1) ** 2
+    pairs = nB * (nB + 1) // 2
+    return 2.0 * (n_r + 1) * 36 * pairs + 2.0 * 4 * 36 * pairs
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(a):
+    import numpy as np
+    import torch
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
+    paths, train_s = train_models(rom_dir)
+    lat = LI.config(CONFIG)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = romb.Context(local, 0, stream.cuda_stream)
+    for p_ in paths:
+        romb.romb_train_load(ctx.h, p_)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    darr = {"ctrl": torch.from_numpy(lat.ctrl).to(dev), "mu": torch.from_numpy(lat.mu).to(dev),
+            "family": torch.from_numpy(lat.family).to(dev),
+            "traction": torch.from_numpy(lat.traction.reshape(8).copy()).to(dev)}
+    u_dev = torch.zeros((1, nodes, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MB > L2
+
+    have_tc = a.precision != "fp64"
+    precisions = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT}
+    if have_tc:
+        try:
+            romb.romb_assemble(ctx.h, lat, romb.ROMB_FP32_SPLIT, device_arrays=darr)
+        except romb.RombError:
+            have_tc = False
+    if a.precision == "auto":
+        form = "fp32split" if have_tc else "fp64"
+    else:
+        form = a.precision
+    prec = precisions[form]
+
+    def step(pr, host=None):
+        if host is None:
+            romb.romb_assemble(ctx.h, lat, pr, device_arrays=darr)
+        else:
+            romb.romb_assemble(ctx.h, host["lat"], pr)
+        romb.romb_factor(ctx.h)
+        out = u_dev if host is None else host["u"]
+        _, its, rel = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-8, maxit=500, out=out)
+        return int(its[0]), float(rel[0])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(a.warmup):
+        step(prec)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = romb.romb_launch_count(ctx.h)
+    times, phases, iters = [], [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rel = step(prec)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(romb.romb_stats(ctx.h)[0].copy())
+        iters.append(it)
+    launches = (romb.romb_launch_count(ctx.h) - l0) // max(1, a.steps)
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / a.steps
+    value = world * lat.ncells / (ms / 1e3)
+    ph = np.mean(np.array(phases), axis=0)
+
+    # accuracy of the split form against the FP64 form (same device, same inputs)
+    u_form = u_dev.clone()
+    acc = {}
+    if have_tc:
+        other = romb.ROMB_FP64 if form == "fp32split" else romb.ROMB_FP32_SPLIT
+        step(other)
+        num = torch.linalg.vector_norm(u_form - u_dev).item()
+        den = torch.linalg.vector_norm(u_dev if form == "fp32split" else u_form).item()
+        acc["disp_rel_l2_fp32split_vs_fp64"] = num / den
+        step(prec)
+
+    # end to end: pinned host inputs, host output, through the public API
+    e2e = None
+    if not a.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+               for k, v in {"ctrl": lat.ctrl, "mu": lat.mu, "family": lat.family,
+                            "traction": lat.traction}.items()}
+        hl = LI.Lattice(**{**lat.__dict__, "ctrl": pin["ctrl"].numpy(), "mu": pin["mu"].numpy(),
+                           "family": pin["family"].numpy(), "traction": pin["traction"].numpy()})
+        u_host = torch.zeros((1, nodes, 2), dtype=torch.float64).pin_memory().numpy()
+        host = {"lat": hl, "u": u_host}
+        step(prec, host)
+        et = []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec, host)
+            e1.record(stream)
+            e1.synchronize()
+            et.append(e0.elapsed_time(e1))
+        ems = sum(et) / len(et)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = lat.ctrl.nbytes + lat.mu.nbytes + lat.family.nbytes + lat.traction.nbytes
+        e2e = {"value": world * lat.ncells / (ems / 1e3), "unit": "cells/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(u_host.nbytes)}
+
+    # dominant kernel and its roofline (measured phase times on the context stream)
+    names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery"]
+    dom = int(np.argmax(ph[:6]))
+    n_r = max(s.n_r for s in LI.rom_specs(CONFIG))
+    roof = None
+    if names[dom] == "local_factor":
+        fl = factor_flops(lat.p) * lat.ncells
+        roof = {"kernel": "factor_kernel<6> (+ktot)", "bound": "alu", "achieved": fl / (ph[dom] / 1e3) / 1e9,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": None}
+    elif names[dom] == "contraction" and form == "fp64":
+        fl = assembly_flops(lat.p, n_r) * lat.ncells
+        roof = {"kernel": "assemble_fp64_kernel", "bound": "alu", "achieved": fl / (ph[dom] / 1e3) / 1e9,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": None}
+    else:
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s (FP64)", "traffic": None}
+    if roof["achieved"] is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["peak_source"] = "nominal FP64 rate of the profiling recipe"
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(paths)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if form == "fp64" else "tf32x3+f64", "data": "synthetic",
+            "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
+                       "cells": lat.ncells, "p": lat.p, "assembly_form": form,
+                       "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+            "cpu_baseline": cpu, "pcg_iters": iters[-1],
+            "phase_ms": {n: float(v) for n, v in zip(names + ["copies", "total"], ph)},
+            "offline_train_s": train_s, "accuracy": acc or None,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
+    paths, _ = train_models(rom_dir)
+    oracle_sample_seconds(paths, steps=min(a.warmup, 1))
+    times, cells = oracle_sample_seconds(paths, steps=a.steps)
+    s = sum(times) / len(times)
+    v = cells / s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
+                       "sample": f"first {SAMPLE_NX}x{SAMPLE_NY} cells of the workload per step"},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{cells} cells ({SAMPLE_NX}x{SAMPLE_NY}) per step"},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = args_parse()
+    if a.cpu_sample_json:
+        paths = sorted(os.path.join(a.rom_dir, f) for f in os.listdir(a.rom_dir) if f.endswith(".rom"))
+        times, cells = oracle_sample_seconds(paths, steps=1, nx=BASE_NX, ny=BASE_NY)
+        json.dump({"value": cells / times[0], "unit": "cells/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{cells} cells: first {BASE_NX}x{BASE_NY} cells of the workload, "
+                             f"MDEIM assembly + BDDC set-up + PCG + recovery, single thread",
+                   "seconds": times[0]}, open(a.cpu_sample_json, "w"))
+        return
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

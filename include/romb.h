@@ -138,6 +138,9 @@ romb_status romb_bddc_solve(romb_ctx* ctx, int nrhs, const double* traction_sets
  * (1 out of box, 2 bad map, 4 not SPD, 8 non-finite); either may be NULL. */
 romb_status romb_stats(romb_ctx* ctx, double* phase_ms, int* flags_out);
 
+/* Number of CUDA kernels this context has launched since romb_create. */
+long long romb_launch_count(romb_ctx* ctx);
+
 /* Copy an internal per-cell array to host memory (inspection and testing).
  * `bytes` must equal the field's size; see romb_field_bytes. */
 typedef enum {

@@ -61,6 +61,7 @@ def _load():
         "romb_field_bytes": ([P, I], S),
         "romb_read": ([P, I, P, S], I),
         "romb_train": ([ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
+        "romb_launch_count": ([P], ctypes.c_longlong),
         "romb_train_snapshot": ([ctypes.POINTER(RombTrainSpec), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -162,6 +163,10 @@ def romb_stats(ctx, ncells: int | None = None):
     flags = np.zeros(ncells, dtype=np.int32) if ncells else None
     _check(_lib.romb_stats(ctx, ms.ctypes.data, None if flags is None else flags.ctypes.data), "romb_stats")
     return ms, flags
+
+
+def romb_launch_count(ctx) -> int:
+    return int(_lib.romb_launch_count(ctx))
 
 
 def romb_read(ctx, field: str) -> np.ndarray:

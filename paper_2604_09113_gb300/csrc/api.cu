@@ -71,6 +71,10 @@ static void romb_free_ptr(romb_ctx* c, void* p) {
 
 // Free every lattice-dependent buffer (the loaded ROMs stay).
 void romb_free_lattice(romb_ctx* c) {
+  if (c->pcg_graph) {
+    cudaGraphExecDestroy(c->pcg_graph);
+    c->pcg_graph = nullptr;
+  }
   for (void* p : c->allocs) {
     cudaFree(p);
     c->sizes.erase(p);
@@ -147,6 +151,7 @@ extern "C" void romb_destroy(romb_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
   romb_free_all(c);
   for (int l = 0; l < (int)c->nd.d_level_fronts.size(); ++l) c->nd.d_level_fronts[l] = nullptr;
   for (auto& e : c->ev) cudaEventDestroy(e);
@@ -213,8 +218,7 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   RombRom& R = c->roms[family];
   if (R.loaded) {
     romb_free_ptr(c, R.U64);
-    romb_free_ptr(c, R.Uhi);
-    romb_free_ptr(c, R.Ulo);
+    romb_free_ptr(c, R.Utiles);
     romb_free_ptr(c, R.A);
     romb_free_ptr(c, R.At);
     R = RombRom();
@@ -233,17 +237,11 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   }
   R.kpad = (K + 7) / 8 * 8;
   {
-    // tensor-core operands: hi/lo FP32 split of U', K padded with zero rows
-    std::vector<float> hi((size_t)R.kpad * n_half, 0.f), lo((size_t)R.kpad * n_half, 0.f);
-    for (size_t i = 0; i < Uh.size(); ++i) {
-      float h = tf32_round((float)Uh[i]);
-      hi[i] = h;
-      lo[i] = tf32_round((float)(Uh[i] - (double)h));
-    }
-    if ((s = romb_alloc_persist(c, (void**)&R.Uhi, 4 * hi.size())) != ROMB_OK) return s;
-    if ((s = romb_alloc_persist(c, (void**)&R.Ulo, 4 * lo.size())) != ROMB_OK) return s;
-    ROMB_CUDA(cudaMemcpy(R.Uhi, hi.data(), 4 * hi.size(), cudaMemcpyHostToDevice));
-    ROMB_CUDA(cudaMemcpy(R.Ulo, lo.data(), 4 * lo.size(), cudaMemcpyHostToDevice));
+    // tensor-core operand tiles (TF32 hi/lo of rows 2.., rows 0-1 in FP64)
+    std::vector<float> tiles;
+    tc_tile_rom(Uh, n_half, K, R.kpad, tiles, &R.ntiles);
+    if ((s = romb_alloc_persist(c, (void**)&R.Utiles, 4 * tiles.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(R.Utiles, tiles.data(), 4 * tiles.size(), cudaMemcpyHostToDevice));
   }
   R.loaded = true;
   R.family = family;
@@ -379,6 +377,7 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_family, cells);
   A_(c->d_flags, cells);
   A_(c->d_chat, cells * 9 * 16);
+  A_(c->d_chat32, cells * 144);
   A_(c->d_theta, cells * 128);
   A_(c->d_theta_hi, cells * 128);
   A_(c->d_theta_lo, cells * 128);
@@ -408,6 +407,7 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_fI, cells * c->nI);
   A_(c->d_fU, cells * c->nU);
   A_(c->d_cloc, cells * ROMB_NSLOT);
+  A_(c->d_yloc, cells * c->nU);
   A_(c->d_u, 2 * nodes);
   A_(c->d_traction, 8 * 64);
 #undef A_
@@ -495,6 +495,7 @@ extern "C" romb_status romb_assemble(romb_ctx* c, const romb_lattice* L, romb_pr
     if (R.loaded && (R.p != c->p || R.kind != c->basis)) return ROMB_E_ARG;
   c->assembled = c->factored = false;
   c->prec = prec;
+  c->assembled_split = prec != ROMB_FP64;
   cudaEventRecord(c->ev[0], c->stream);
   if ((s = launch_theta(c)) != ROMB_OK) return s;
   cudaEventRecord(c->ev[1], c->stream);
@@ -516,6 +517,7 @@ extern "C" romb_status romb_assemble_host_K(romb_ctx* c, const romb_lattice* L, 
   romb_status s = load_lattice(c, L);
   if (s != ROMB_OK) return s;
   c->assembled = c->factored = false;
+  c->assembled_split = false;
   // pack the dense matrices on the device (upper triangle, row-major)
   double* dense = nullptr;
   const size_t nd = (size_t)c->ndof;
@@ -536,6 +538,10 @@ extern "C" romb_status romb_factor(romb_ctx* c) {
   if (!c->assembled) return ROMB_E_STATE;
   ROMB_CUDA(cudaSetDevice(c->device));
   romb_status s;
+  if (c->pcg_graph) {
+    cudaGraphExecDestroy(c->pcg_graph);
+    c->pcg_graph = nullptr;
+  }
   cudaEventRecord(c->ev[3], c->stream);
   if ((s = launch_ktot(c)) != ROMB_OK) return s;
   if ((s = launch_factor(c)) != ROMB_OK) return s;
@@ -602,6 +608,8 @@ extern "C" romb_status romb_stats(romb_ctx* c, double* phase_ms, int* flags_out)
   }
   return ROMB_OK;
 }
+
+extern "C" long long romb_launch_count(romb_ctx* c) { return c ? c->launches : -1; }
 
 extern "C" size_t romb_field_bytes(romb_ctx* c, int field) {
   if (!c || !c->have_lattice) return 0;

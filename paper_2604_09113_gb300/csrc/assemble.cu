@@ -97,11 +97,19 @@ __global__ void family_list_kernel(const int32_t* __restrict__ family, int ncell
 // ---------------------------------------------------------------------------
 // theta kernel
 // ---------------------------------------------------------------------------
-#define TH_CELLS 4
+#define TH_CELLS 8
+__device__ inline float tf32_round_dev(float f) {
+  uint32_t u = __float_as_uint(f);
+  if ((u & 0x7f800000u) == 0x7f800000u) return f;
+  u = (u + 0x1000u) & 0xffffe000u;
+  return __uint_as_float(u);
+}
+
 __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, const int* __restrict__ list, int count,
                                                      const double* __restrict__ ctrl, const double* __restrict__ mu,
                                                      double* __restrict__ theta, double* __restrict__ chat,
-                                                     int32_t* __restrict__ flags) {
+                                                     float* __restrict__ th_hi, float* __restrict__ th_lo,
+                                                     float* __restrict__ chat32, int32_t* __restrict__ flags) {
   __shared__ double wts[4][TH_CELLS][4][12];   // [warp][cell][param][node]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int first = (blockIdx.x * 4 + warp) * TH_CELLS;
@@ -110,8 +118,8 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
   int cells[TH_CELLS];
   for (int j = 0; j < TH_CELLS; ++j) cells[j] = (first + j < count) ? list[first + j] : -1;
   // 1D interpolation weights: lane = (cell j, parameter d)
-  if (lane < 4 * TH_CELLS) {
-    const int j = lane >> 2, d = lane & 3;
+  for (int task = lane; task < 4 * TH_CELLS; task += 32) {
+    const int j = task >> 2, d = task & 3;
     const int c = cells[j];
     double v[12];
     if (c >= 0) {
@@ -124,35 +132,54 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
     for (int i = 0; i < n1; ++i) wts[warp][j][d][i] = v[i];
   }
   __syncwarp();
-  // lambda_t = sum_g At[g][t] w(g): lanes over t
+  // lambda_t = sum_{g2 g3 g4} w2 w3 w4 (sum_{g1} w1[g1] At[g][t]): lanes over t
   const int nr = R.n_r;
   double acc[4][TH_CELLS];
   for (int s = 0; s < 4; ++s)
     for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
-  const int ng = n1 * n1 * n1 * n1;
-  for (int g = 0; g < ng; ++g) {
-    const int g1 = g % n1, g2 = (g / n1) % n1, g3 = (g / (n1 * n1)) % n1, g4 = g / (n1 * n1 * n1);
-    double wg[TH_CELLS];
-    for (int j = 0; j < TH_CELLS; ++j)
-      wg[j] = wts[warp][j][0][g1] * wts[warp][j][1][g2] * wts[warp][j][2][g3] * wts[warp][j][3][g4];
-    const double* Ag = R.At + (long long)g * nr;
+  const int n3 = n1 * n1 * n1;
+  for (int g234 = 0; g234 < n3; ++g234) {
+    const int g2 = g234 % n1, g3 = (g234 / n1) % n1, g4 = g234 / (n1 * n1);
+    double inner[4][TH_CELLS];
+    for (int s = 0; s < 4; ++s)
+      for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = 0.0;
+    for (int g1 = 0; g1 < n1; ++g1) {
+      const double* Ag = R.At + (long long)(g234 * n1 + g1) * nr;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int t = lane + 32 * s;
-      if (t < nr) {
-        const double a = __ldg(Ag + t);
-        for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = fma(a, wg[j], acc[s][j]);
+      for (int s = 0; s < 4; ++s) {
+        const int t = lane + 32 * s;
+        if (t < nr) {
+          const double a = __ldg(Ag + t);
+#pragma unroll
+          for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = fma(a, wts[warp][j][0][g1], inner[s][j]);
+        }
       }
+    }
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) {
+      const double w234 = wts[warp][j][1][g2] * wts[warp][j][2][g3] * wts[warp][j][3][g4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) acc[s][j] = fma(w234, inner[s][j], acc[s][j]);
     }
   }
   for (int j = 0; j < TH_CELLS; ++j) {
     const int c = cells[j];
     if (c < 0) continue;
     double* th = theta + 128 * (long long)c;
+    float* hi = th_hi + 128 * (long long)c;
+    float* lo = th_lo + 128 * (long long)c;
     if (lane == 0) th[0] = P.rho;
     for (int s = 0; s < 4; ++s) {
       const int t = lane + 32 * s;
       if (t < nr) th[1 + t] = (1.0 - P.rho) * acc[s][j];
+    }
+    __syncwarp();
+    // TF32 hi / lo split of theta, zero padded to 128 slots
+    for (int t = lane; t < 128; t += 32) {
+      const double v = (t >= 2 && t <= nr) ? th[t] : 0.0;
+      const float h = tf32_round_dev((float)v);
+      hi[t] = h;
+      lo[t] = tf32_round_dev((float)(v - (double)h));
     }
   }
   // Chat at the 9 interpolation nodes: lane = (cell j, node k3)
@@ -175,8 +202,10 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
           for (int l = 0; l < 2; ++l) {
             // Chat_ijkl = det [lam G_ji G_lk + mu (d_ik (G G^T)_jl + G_jk G_li)]
             const double GGt = G[jj][0] * G[l][0] + G[jj][1] * G[l][1];
-            const double v = P.lam * G[jj][i] * G[l][k] + P.mu * ((i == k ? GGt : 0.0) + G[jj][k] * G[l][i]);
+            // products grouped so that Chat_ijkl and Chat_klij round identically
+            const double v = P.lam * (G[jj][i] * G[l][k]) + P.mu * ((i == k ? GGt : 0.0) + G[jj][k] * G[l][i]);
             out[((i * 2 + jj) * 2 + k) * 2 + l] = det * v;
+            chat32[(long long)c * 144 + 16 * k3 + ((i * 2 + jj) * 2 + k) * 2 + l] = (float)(det * v);
           }
   }
 }
@@ -303,7 +332,7 @@ romb_status launch_theta(romb_ctx* c) {
   if ((s = ensure_pairs(c)) != ROMB_OK) return s;
   int* d_counts = (int*)c->d_red + 16;
   family_list_kernel<<<1, 1024, 0, c->stream>>>(c->d_family, c->ncells, ROMB_MAX_FAMILIES, c->d_famlist, d_counts,
-                                                c->d_flags);
+                                                c->d_flags); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   int counts[ROMB_MAX_FAMILIES];
   ROMB_CUDA(cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, c->stream));
@@ -326,7 +355,8 @@ romb_status launch_theta(romb_ctx* c) {
       for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
       const int per_block = 4 * TH_CELLS;
       theta_kernel<<<(counts[f] + per_block - 1) / per_block, 128, 0, c->stream>>>(
-          P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat, c->d_flags);
+          P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat, c->d_theta_hi,
+          c->d_theta_lo, c->d_chat32, c->d_flags); ++c->launches;
       ROMB_CUDA(cudaGetLastError());
     }
     start += counts[f];
@@ -349,20 +379,20 @@ romb_status launch_assemble_fp64(romb_ctx* c) {
     dim3 grid((c->famcount[f] + A64_CELLS - 1) / A64_CELLS, (npairs + A64_PAIRS - 1) / A64_PAIRS);
     assemble_fp64_kernel<<<grid, 128, smem, c->stream>>>(R.U64, R.n_half, K, c->d_famlist + c->famstart[f],
                                                          c->famcount[f], c->d_pairs, npairs, c->ndof, c->d_theta,
-                                                         c->d_chat, c->d_K);
+                                                         c->d_chat, c->d_K); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
   return ROMB_OK;
 }
 
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense) {
-  pack_dense_kernel<<<4 * c->sms, 256, 0, c->stream>>>(d_dense, c->ndof, c->ncells, c->d_K);
+  pack_dense_kernel<<<4 * c->sms, 256, 0, c->stream>>>(d_dense, c->ndof, c->ncells, c->d_K); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
 romb_status launch_flag_or(romb_ctx* c, int* d_any) {
-  flag_or_kernel<<<c->sms, 256, 0, c->stream>>>(c->d_flags, c->ncells, d_any);
+  flag_or_kernel<<<c->sms, 256, 0, c->stream>>>(c->d_flags, c->ncells, d_any); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }

@@ -129,6 +129,8 @@ struct FrontDev {
   int cell_off, ncell;
   int emap_off;      // extend-add positions of this front's update rows in its parent
   int ybuf_off;      // forward-solve update vector (nb)
+  int wbuf_off;      // gathered right-hand side (n)
+  int sbuf_off;      // separator solution / backward right-hand side (ns)
 };
 
 }  // namespace
@@ -143,8 +145,10 @@ __global__ void nd_assemble_kernel(const FrontDev* __restrict__ fr, const int* _
   const FrontDev f = fr[level[blockIdx.x]];
   const int n = f.ns + f.nb;
   double* A = F + f.off;
-  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) A[t] = 0.0;
+  for (long long t = threadIdx.x; t < (long long)(n + f.ns) * n; t += blockDim.x) A[t] = 0.0;
   __syncthreads();
+  // identity below the front: the elimination turns it into L11^-T
+  for (int e = threadIdx.x; e < f.ns; e += blockDim.x) A[(long long)(n + e) * n + e] = 1.0;
   for (int k = 0; k < f.ncell; ++k) {
     const int cell = cells[f.cell_off + k];
     const int* pos = cell_pos + 20 * (long long)cell;
@@ -231,7 +235,7 @@ __global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __res
   }
   __syncthreads();
   const int r = k1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  if (r >= n + f.ns) return;
   double x[ND_NB];
   double* row = A + (long long)r * n + k0;
 #pragma unroll
@@ -247,8 +251,9 @@ __global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __res
     if (j < nbk) row[j] = x[j];
 }
 
-// Trailing update of rows/cols >= k1: A[i][j] -= sum_{t in [k0,k1)} A[i][t] A[j][t], i >= j.
-// 32 x 32 output tiles, lower tiles only, 256 threads (4 outputs each).
+// Trailing update: A[i][j] -= sum_{t in [k0,k1)} A[i][t] A[j][t] for rows i >= k1,
+// columns k1 <= j < n with j <= i for front rows, j < ns for the rows below the
+// front (which accumulate L11^-T).  32 x 32 tiles, 256 threads (4 outputs each).
 __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
                                                        double* __restrict__ F, int k0) {
   const FrontDev f = fr[level[blockIdx.y]];
@@ -256,50 +261,53 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   const int n = f.ns + f.nb;
   const int nbk = min(ND_NB, f.ns - k0);
   const int k1 = k0 + nbk;
-  const int m = n - k1;
-  const int nt = (m + 31) / 32;
-  // tile index -> (ti, tj) with ti >= tj
+  const int ntr = (n + f.ns - k1 + 31) / 32, ntc = (n - k1 + 31) / 32;
   const int tix = blockIdx.x;
-  if (tix >= nt * (nt + 1) / 2) return;
-  int ti = (int)((sqrt(8.0 * tix + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
-  while (ti * (ti + 1) / 2 > tix) --ti;
-  const int tj = tix - ti * (ti + 1) / 2;
+  if (tix >= ntr * ntc) return;
+  const int ti = tix / ntc, tj = tix % ntc;
+  const int r0 = k1 + ti * 32, c0 = k1 + tj * 32;
+  // skip tiles with no valid output
+  if (r0 < n && c0 > r0 + 31) return;
+  if (r0 >= n && c0 >= f.ns) return;
   __shared__ double Pi[32][ND_NB + 1], Pj[32][ND_NB + 1];
   double* A = F + f.off;
   for (int t = threadIdx.x; t < 32 * ND_NB; t += blockDim.x) {
     const int rr = t / ND_NB, kk = t % ND_NB;
-    const int ri = k1 + ti * 32 + rr, rj = k1 + tj * 32 + rr;
-    Pi[rr][kk] = (ri < n && kk < nbk) ? A[(long long)ri * n + k0 + kk] : 0.0;
+    const int ri = r0 + rr, rj = c0 + rr;
+    Pi[rr][kk] = (ri < n + f.ns && kk < nbk) ? A[(long long)ri * n + k0 + kk] : 0.0;
     Pj[rr][kk] = (rj < n && kk < nbk) ? A[(long long)rj * n + k0 + kk] : 0.0;
   }
   __syncthreads();
   const int lr = threadIdx.x / 8, lc0 = (threadIdx.x % 8) * 4;
-  const int gi = k1 + ti * 32 + lr;
-  if (gi >= n) return;
+  const int gi = r0 + lr;
+  if (gi >= n + f.ns) return;
   double acc[4] = {0, 0, 0, 0};
   for (int kk = 0; kk < nbk; ++kk) {
     const double a = Pi[lr][kk];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = fma(a, Pj[lc0 + c][kk], acc[c]);
   }
+  const int jmax = gi < n ? gi : f.ns - 1;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const int gj = k1 + tj * 32 + lc0 + c;
-    if (gj < n && gj <= gi) A[(long long)gi * n + gj] -= acc[c];
+    const int gj = c0 + lc0 + c;
+    if (gj < n && gj <= jmax) A[(long long)gi * n + gj] -= acc[c];
   }
 }
 
-// Forward substitution of one level: w = rhs(sep) + children's update vectors;
-// y_s = L11^-1 w_s; u = w_b - L21 y_s.
-__global__ void nd_fwd_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                              const double* __restrict__ F, const int* __restrict__ idx,
-                              const int* __restrict__ children, const int* __restrict__ emap,
-                              const double* __restrict__ rhs, double* __restrict__ y, double* __restrict__ ybuf) {
-  extern __shared__ double w[];
+// ---- solves: every step is a GEMV over the stored L21 and L11^-T ----
+struct NdItem {
+  int front, start;
+};
+
+// w = [rhs(separator rows); 0] + extend-add of the children's update vectors
+__global__ void nd_gather_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                 const int* __restrict__ idx, const int* __restrict__ children,
+                                 const int* __restrict__ emap, const double* __restrict__ rhs,
+                                 const double* __restrict__ ybuf, double* __restrict__ wbuf) {
   const FrontDev f = fr[level[blockIdx.x]];
   const int n = f.ns + f.nb;
-  const double* A = F + f.off;
+  double* w = wbuf + f.wbuf_off;
   const int* id = idx + f.idx_off;
   for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] = t < f.ns ? rhs[id[t]] : 0.0;
   __syncthreads();
@@ -309,54 +317,88 @@ __global__ void nd_fwd_kernel(const FrontDev* __restrict__ fr, const int* __rest
     for (int t = threadIdx.x; t < ch.nb; t += blockDim.x) w[em[t]] += ybuf[ch.ybuf_off + t];
     __syncthreads();
   }
-  // y_s: row-by-row, one warp computes each dot product
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < f.ns; ++i) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int k = lane; k < i; k += 32) s += A[(long long)i * n + k] * w[k];
-      s = warp_sum(s);
-      if (lane == 0) w[i] = (w[i] - s) / A[(long long)i * n + i];
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < f.ns; t += blockDim.x) y[id[t]] = w[t];
-  for (int r = f.ns + warp; r < n; r += blockDim.x / 32) {
-    double s = 0.0;
-    for (int k = lane; k < f.ns; k += 32) s += A[(long long)r * n + k] * w[k];
-    s = warp_sum(s);
-    if (lane == 0) ybuf[f.ybuf_off + (r - f.ns)] = w[r] - s;
-  }
 }
 
-// Backward substitution of one level: x_s = L11^-T (y_s - L21^T x_b).
-__global__ void nd_bwd_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                              const double* __restrict__ F, const int* __restrict__ idx, double* __restrict__ x) {
-  extern __shared__ double w[];
-  const FrontDev f = fr[level[blockIdx.x]];
+// y_s = L11^-1 w_s = (L11^-T)^T w_s: thread per separator row j
+__global__ void nd_fwd_y_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                const double* __restrict__ F, const int* __restrict__ idx,
+                                const double* __restrict__ wbuf, double* __restrict__ sbuf, double* __restrict__ x) {
+  const NdItem it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
   const int n = f.ns + f.nb;
-  const double* A = F + f.off;
-  const int* id = idx + f.idx_off;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] = x[id[t]];
-  __syncthreads();
-  // t_s = y_s - L21^T x_b, one thread per separator row
-  for (int i = threadIdx.x; i < f.ns; i += blockDim.x) {
-    double s = 0.0;
-    for (int r = f.ns; r < n; ++r) s += A[(long long)r * n + i] * w[r];
-    w[i] -= s;
+  const int j = it.start + threadIdx.x;
+  if (j >= f.ns) return;
+  const double* Y = F + f.off + (long long)n * n;   // row e: (L11^-T)[e][:]
+  const double* w = wbuf + f.wbuf_off;
+  double s0 = 0.0, s1 = 0.0;
+  int e = 0;
+  for (; e + 1 <= j; e += 2) {
+    s0 = fma(Y[(long long)e * n + j], w[e], s0);
+    s1 = fma(Y[(long long)(e + 1) * n + j], w[e + 1], s1);
   }
-  __syncthreads();
+  if (e <= j) s0 = fma(Y[(long long)e * n + j], w[e], s0);
+  const double y = s0 + s1;
+  sbuf[f.sbuf_off + j] = y;
+  x[idx[f.idx_off + j]] = y;
+}
+
+// update vector u_b = w_b - L21 y_s: warp per boundary row
+__global__ void nd_fwd_upd_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                  const double* __restrict__ F, const double* __restrict__ wbuf,
+                                  const double* __restrict__ sbuf, double* __restrict__ ybuf) {
+  const NdItem it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
+  const int n = f.ns + f.nb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = f.ns - 1; i >= 0; --i) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int k = i + 1 + lane; k < f.ns; k += 32) s += A[(long long)k * n + i] * w[k];
-      s = warp_sum(s);
-      if (lane == 0) w[i] = (w[i] - s) / A[(long long)i * n + i];
-    }
-    __syncthreads();
+  const int r = it.start + warp;
+  if (r >= f.nb) return;
+  const double* row = F + f.off + (long long)(f.ns + r) * n;
+  const double* y = sbuf + f.sbuf_off;
+  double s = 0.0;
+  for (int j = lane; j < f.ns; j += 32) s = fma(row[j], y[j], s);
+  s = warp_sum(s);
+  if (lane == 0) ybuf[f.ybuf_off + r] = wbuf[f.wbuf_off + f.ns + r] - s;
+}
+
+// t_s = y_s - L21^T x_b: thread per separator row j (x_b staged in shared memory)
+__global__ void nd_bwd_t_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                const double* __restrict__ F, const int* __restrict__ idx,
+                                const double* __restrict__ x, double* __restrict__ sbuf) {
+  extern __shared__ double xb[];
+  const NdItem it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
+  const int n = f.ns + f.nb;
+  for (int r = threadIdx.x; r < f.nb; r += blockDim.x) xb[r] = x[idx[f.idx_off + f.ns + r]];
+  __syncthreads();
+  const int j = it.start + threadIdx.x;
+  if (j >= f.ns) return;
+  const double* L21 = F + f.off + (long long)f.ns * n;
+  double s0 = 0.0, s1 = 0.0;
+  int r = 0;
+  for (; r + 1 < f.nb; r += 2) {
+    s0 = fma(L21[(long long)r * n + j], xb[r], s0);
+    s1 = fma(L21[(long long)(r + 1) * n + j], xb[r + 1], s1);
   }
-  for (int t = threadIdx.x; t < f.ns; t += blockDim.x) x[id[t]] = w[t];
+  if (r < f.nb) s0 = fma(L21[(long long)r * n + j], xb[r], s0);
+  sbuf[f.sbuf_off + j] -= s0 + s1;
+}
+
+// x_s = L11^-T t_s: warp per separator row e
+__global__ void nd_bwd_x_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                const double* __restrict__ F, const int* __restrict__ idx,
+                                const double* __restrict__ sbuf, double* __restrict__ x) {
+  const NdItem it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
+  const int n = f.ns + f.nb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = it.start + warp;
+  if (e >= f.ns) return;
+  const double* Y = F + f.off + (long long)(n + e) * n;
+  const double* t = sbuf + f.sbuf_off;
+  double s = 0.0;
+  for (int j = e + lane; j < f.ns; j += 32) s = fma(Y[j], t[j], s);
+  s = warp_sum(s);
+  if (lane == 0) x[idx[f.idx_off + e]] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -364,6 +406,10 @@ __global__ void nd_bwd_kernel(const FrontDev* __restrict__ fr, const int* __rest
 // ---------------------------------------------------------------------------
 struct NdDevice {
   FrontDev* fr = nullptr;
+  double* wbuf = nullptr;
+  double* sbuf = nullptr;
+  std::vector<NdItem*> col_items, brow_items, srow_items;
+  std::vector<int> col_n, brow_n, srow_n, level_maxnb;
   int* idx = nullptr;
   int* children = nullptr;
   int* emap = nullptr;
@@ -402,7 +448,7 @@ romb_status coarse_build(romb_ctx* c) {
   std::vector<FrontDev> fd(nf);
   std::vector<int> idx, children, emap, cells, cell_pos((size_t)c->ncells * 20, -1);
   long long off = 0;
-  int ybuf = 0;
+  int ybuf = 0, wbuf_tot = 0, sbuf_tot = 0;
   for (int i = 0; i < nf; ++i) {
     const NdFront& F = plan.fronts[i];
     FrontDev& d = fd[i];
@@ -410,7 +456,7 @@ romb_status coarse_build(romb_ctx* c) {
     d.nb = F.nb;
     const long long n = F.ns + F.nb;
     d.off = off;
-    off += n * n;
+    off += (n + F.ns) * n;   // rows n.. hold L11^-T after the factorisation
     d.idx_off = (int)idx.size();
     idx.insert(idx.end(), B.rows[i].begin(), B.rows[i].end());
     d.child_off = (int)children.size();
@@ -421,6 +467,10 @@ romb_status coarse_build(romb_ctx* c) {
     cells.insert(cells.end(), B.leaf_cells[i].begin(), B.leaf_cells[i].end());
     d.ybuf_off = ybuf;
     ybuf += F.nb;
+    d.wbuf_off = wbuf_tot;
+    wbuf_tot += (int)n;
+    d.sbuf_off = sbuf_tot;
+    sbuf_tot += F.ns;
     d.emap_off = -1;
   }
   // extend-add positions of each front's update rows in its parent
@@ -474,6 +524,8 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.cell_pos, cell_pos.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.F, (size_t)off)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.ybuf, std::max(1, ybuf))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.wbuf, std::max(1, wbuf_tot))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
   ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
   ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
@@ -495,6 +547,34 @@ romb_status coarse_build(romb_ctx* c) {
     }
     D.level_maxns.push_back(mns);
     D.level_maxn.push_back(mn);
+    // work lists of the solve kernels
+    std::vector<NdItem> ci, bi, si;
+    int mnb = 0;
+    for (int f : lv) {
+      const NdFront& Fr = plan.fronts[f];
+      mnb = std::max(mnb, Fr.nb);
+      for (int j = 0; j < Fr.ns; j += 256) ci.push_back({f, j});
+      for (int r = 0; r < Fr.nb; r += 8) bi.push_back({f, r});
+      for (int e = 0; e < Fr.ns; e += 8) si.push_back({f, e});
+    }
+    D.level_maxnb.push_back(mnb);
+    for (auto* pr : {&ci, &bi, &si}) {
+      NdItem* dptr = nullptr;
+      if (!pr->empty()) {
+        if ((s = romb_alloc_t(c, &dptr, pr->size())) != ROMB_OK) return s;
+        ROMB_CUDA(cudaMemcpy(dptr, pr->data(), sizeof(NdItem) * pr->size(), cudaMemcpyHostToDevice));
+      }
+      if (pr == &ci) {
+        D.col_items.push_back(dptr);
+        D.col_n.push_back((int)pr->size());
+      } else if (pr == &bi) {
+        D.brow_items.push_back(dptr);
+        D.brow_n.push_back((int)pr->size());
+      } else {
+        D.srow_items.push_back(dptr);
+        D.srow_n.push_back((int)pr->size());
+      }
+    }
   }
   return ROMB_OK;
 }
@@ -505,18 +585,18 @@ romb_status coarse_factor(romb_ctx* c) {
   for (size_t l = 0; l < D.level_ids.size(); ++l) {
     const int nfl = D.level_count[l];
     nd_assemble_kernel<<<nfl, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.children, D.emap, D.cells,
-                                                   D.cell_pos, c->d_SCl);
+                                                   D.cell_pos, c->d_SCl); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     const int mns = D.level_maxns[l], mn = D.level_maxn[l];
     for (int k0 = 0; k0 < mns; k0 += ND_NB) {
-      nd_potrf_kernel<<<nfl, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad);
-      const int rows = mn - k0;
-      if (rows > 0) {
+      nd_potrf_kernel<<<nfl, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad); ++c->launches;
+      const int rows = mn + mns - k0, cols = mn - k0;
+      if (rows > 0 && cols > 0) {
         dim3 g1((rows + 127) / 128, nfl);
-        nd_trsm_kernel<<<g1, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0);
-        const int nt = (rows + 31) / 32;
-        dim3 g2(nt * (nt + 1) / 2, nfl);
-        nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0);
+        nd_trsm_kernel<<<g1, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0); ++c->launches;
+        const int ntr = (rows + 31) / 32, ntc = (cols + 31) / 32;
+        dim3 g2(ntr * ntc, nfl);
+        nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0); ++c->launches;
       }
       ROMB_CUDA(cudaGetLastError());
     }
@@ -534,13 +614,22 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
   const int L = (int)D.level_ids.size();
   for (int l = 0; l < L; ++l) {
-    const size_t sm = 8 * (size_t)D.level_maxn[l];
-    nd_fwd_kernel<<<D.level_count[l], 256, sm, c->stream>>>(D.fr, D.level_ids[l], D.F, D.idx, D.children, D.emap,
-                                                            d_in, d_out, D.ybuf);
+    nd_gather_kernel<<<D.level_count[l], 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.idx, D.children, D.emap,
+                                                              d_in, D.ybuf, D.wbuf); ++c->launches;
+    if (D.col_n[l])
+      nd_fwd_y_kernel<<<D.col_n[l], 256, 0, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, D.wbuf, D.sbuf,
+                                                         d_out); ++c->launches;
+    if (D.brow_n[l])
+      nd_fwd_upd_kernel<<<D.brow_n[l], 256, 0, c->stream>>>(D.fr, D.brow_items[l], D.F, D.wbuf, D.sbuf,
+                                                            D.ybuf); ++c->launches;
   }
   for (int l = L - 1; l >= 0; --l) {
-    const size_t sm = 8 * (size_t)D.level_maxn[l];
-    nd_bwd_kernel<<<D.level_count[l], 256, sm, c->stream>>>(D.fr, D.level_ids[l], D.F, D.idx, d_out);
+    if (D.col_n[l]) {
+      const size_t sm = 8 * (size_t)std::max(1, D.level_maxnb[l]);
+      nd_bwd_t_kernel<<<D.col_n[l], 256, sm, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, d_out, D.sbuf); ++c->launches;
+    }
+    if (D.srow_n[l])
+      nd_bwd_x_kernel<<<D.srow_n[l], 256, 0, c->stream>>>(D.fr, D.srow_items[l], D.F, D.idx, D.sbuf, d_out); ++c->launches;
   }
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;

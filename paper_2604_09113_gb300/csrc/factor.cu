@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
                                                       double* __restrict__ S_out, double* __restrict__ G_out,
                                                       double* __restrict__ Phi_out, double* __restrict__ Psi_out,
                                                       double* __restrict__ SCl_out, double* __restrict__ D_out,
-                                                      int32_t* __restrict__ flags) {
+                                                      int32_t* __restrict__ flags, int rowsum_fix) {
   using Dm = FactorDims<P>;
   constexpr int ND = Dm::ND, NI = Dm::NI, NU = Dm::NU, NK = Dm::NK;
   extern __shared__ double sm[];
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   double* Dv = sm + Dm::oDv;
   double* Ex = sm + Dm::oEx;   // per edge and Gauss point: x1, x2, j ; then xbar
   __shared__ int s_umap[NU], s_cmap[20], s_keep[NK], s_cu[8], s_islot[NI], s_uslot[NU], s_bad;
+  __shared__ double s_rs[ND][2];   // row sums over each displacement component (translation test)
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long cell = blockIdx.x;
   const int cx = (int)(cell % Pm.nx), cy = (int)(cell / Pm.nx);
@@ -134,9 +135,25 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   __syncthreads();
   // ---- load K in (I, U) order; Dirichlet skeleton slots become identity ----
   const double* Kc = Kp + cell * ((long long)ND * (ND + 1) / 2);
+  // Split-precision matrices: restore the exact null space of rigid translations
+  // (sum_k2 K[(k1 i1), (k2 i2)] = 0, since the basis derivatives sum to zero) by
+  // moving each row sum onto the node's own 2x2 diagonal block, symmetrised.
+  for (int t = tid; t < 2 * ND; t += nt) {
+    const int r = t >> 1, i2 = t & 1;
+    double acc = 0.0;
+    if (rowsum_fix)
+      for (int k2 = 0; k2 < ND / 2; ++k2) acc += Kc[packed_idx(r, 2 * k2 + i2, ND)];
+    s_rs[r][i2] = acc;
+  }
+  __syncthreads();
+  auto kval = [&](int r, int q) -> double {
+    double v = Kc[packed_idx(r, q, ND)];
+    if ((r >> 1) == (q >> 1)) v -= 0.5 * (s_rs[r][q & 1] + s_rs[q][r & 1]);
+    return v;
+  };
   for (int t = tid; t < NI * NI; t += nt) {
     const int i = t / NI, j = t % NI;
-    AII[t] = Kc[packed_idx(s_islot[i], s_islot[j], ND)];
+    AII[t] = kval(s_islot[i], s_islot[j]);
   }
   for (int t = tid; t < NI * NU; t += nt) {
     const int i = t / NU, u = t % NU;
@@ -144,7 +161,7 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   }
   for (int t = tid; t < NU * NU; t += nt) {
     const int u = t / NU, v = t % NU;
-    double val = Kc[packed_idx(s_uslot[u], s_uslot[v], ND)];
+    double val = kval(s_uslot[u], s_uslot[v]);
     if (u == v) kd[u] = val;
     if (s_umap[u] < 0 || s_umap[v] < 0) val = (u == v) ? 1.0 : 0.0;
     S[t] = val;
@@ -417,7 +434,7 @@ __global__ void ktot_kernel(CellParams P, const double* __restrict__ Kp, long lo
 romb_status launch_ktot(romb_ctx* c) {
   CellParams P;
   fill_cell_params(c, &P);
-  ktot_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, c->d_K, c->nskel_nodes, c->d_ktot);
+  ktot_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, c->d_K, c->nskel_nodes, c->d_ktot); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
@@ -428,7 +445,8 @@ static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
   ROMB_CUDA(cudaFuncSetAttribute(factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   factor_kernel<P><<<c->ncells, 256, smem, c->stream>>>(Pm, c->d_K, c->d_ctrl, c->d_ucell_map, c->d_cmap, c->d_ktot,
                                                         c->d_LII, c->d_W, c->d_S, c->d_G, c->d_Phi, c->d_Psi,
-                                                        c->d_SCl, c->d_D, c->d_flags);
+                                                        c->d_SCl, c->d_D, c->d_flags,
+                                                        c->assembled_split ? 1 : 0); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }

@@ -372,8 +372,8 @@ __global__ void skel_to_nodes_kernel(CellParams P, long long nnodes, const doubl
 // ---------------------------------------------------------------------------
 static romb_status dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
   double* part = c->d_red + 64;
-  dot_partial_kernel<<<RED_BLOCKS, 256, 0, c->stream>>>(a, b, n, part);
-  dot_final_kernel<<<1, 256, 0, c->stream>>>(part, RED_BLOCKS, out);
+  dot_partial_kernel<<<RED_BLOCKS, 256, 0, c->stream>>>(a, b, n, part); ++c->launches;
+  dot_final_kernel<<<1, 256, 0, c->stream>>>(part, RED_BLOCKS, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
@@ -391,15 +391,15 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
                                 double* cloc) {
   const int cb = (c->ncells + 7) / 8;
   cell_matvec_kernel<true><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_G, c->d_ucell_map, r, yloc, c->d_Phi,
-                                                      cloc);
+                                                      cloc); ++c->launches;
   double* zc = c->d_coarse;
   double* gc = c->d_coarse + c->ncoarse_all;
-  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->stream>>>(c->d_cowner, c->ncoarse_all, cloc, zc);
+  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->stream>>>(c->d_cowner, c->ncoarse_all, cloc, zc); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   romb_status s = coarse_solve(c, zc, gc);
   if (s != ROMB_OK) return s;
-  cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc);
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, z);
+  cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc); ++c->launches;
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, z); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
@@ -407,10 +407,36 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
 static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
   const int cb = (c->ncells + 7) / 8;
   cell_matvec_kernel<false><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_S, c->d_ucell_map, v, yloc, nullptr,
-                                                       nullptr);
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out);
+                                                       nullptr); ++c->launches;
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
+}
+
+// One PCG iteration (Algorithm 1 inside CG), a fixed sequence of launches:
+//   z = M r; rz' = r.z; p = z + (rz'/rz) p; rz = rz'; q = S p; pq = p.q;
+//   x += (rz/pq) p; r -= (rz/pq) q; rr = r.r -> pinned host word.
+// With p = 0 and rz = 1 on entry the first iteration is the same body.
+static romb_status pcg_body(romb_ctx* c, const CellParams& P, double* yloc, double* cloc) {
+  romb_status s;
+  const long long n = c->nskel;
+  const int g = grid_for(c, n);
+  double* sc = c->d_red;
+  if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
+  if ((s = dot(c, c->d_r, c->d_z, n, sc + 2)) != ROMB_OK) return s;
+  pcg_update_p<<<g, 256, 0, c->stream>>>(n, sc, c->d_pv, c->d_z); ++c->launches;
+  pcg_shift_scalars<<<1, 32, 0, c->stream>>>(sc); ++c->launches;
+  if ((s = apply_S(c, P, c->d_pv, c->d_q, yloc)) != ROMB_OK) return s;
+  if ((s = dot(c, c->d_pv, c->d_q, n, sc + 1)) != ROMB_OK) return s;
+  pcg_update_x_r<<<g, 256, 0, c->stream>>>(n, sc, c->d_x, c->d_r, c->d_pv, c->d_q); ++c->launches;
+  if ((s = dot(c, c->d_r, c->d_r, n, sc + 3)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+__global__ void pcg_init_scalars(double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = 1.0;
 }
 
 romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, double* d_u, int* iters,
@@ -419,7 +445,7 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
   fill_cell_params(c, &P);
   romb_status s;
   const long long n = c->nskel;
-  double* yloc = c->d_fU;       // loads first, then cell-local scratch
+  double* yloc = c->d_yloc;
   double* cloc = c->d_cloc;
   // loads -> f
   ROMB_CUDA(cudaMemcpyAsync(c->d_traction, tr, 64, cudaMemcpyHostToDevice, c->stream));
@@ -427,33 +453,42 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
   {
     const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
     loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family,
-                                                                    c->d_traction, c->d_fU);
+                                                                    c->d_traction, c->d_fU); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->d_fU, c->nskel_nodes, c->d_f);
-  double* sc = c->d_red;   // scalars
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->d_fU, c->nskel_nodes, c->d_f); ++c->launches;
+  double* sc = c->d_red;   // scalars: [0] rz, [1] pq, [2] rz_new, [3] rr, [4] ff
   if ((s = dot(c, c->d_f, c->d_f, n, sc + 4)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 4, 8, cudaMemcpyDeviceToHost, c->stream));
+  ROMB_CUDA(cudaMemcpyAsync(c->h_red + 1, sc + 4, 8, cudaMemcpyDeviceToHost, c->stream));
   ROMB_CUDA(cudaStreamSynchronize(c->stream));
-  const double nf = sqrt(c->h_red[0]);
+  const double nf = sqrt(c->h_red[1]);
   ROMB_CUDA(cudaMemsetAsync(c->d_x, 0, 8 * n, c->stream));
   *iters = 0;
   *relres = 0.0;
   romb_status result = ROMB_OK;
   if (nf > 0.0) {
     ROMB_CUDA(cudaMemcpyAsync(c->d_r, c->d_f, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
-    if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
-    ROMB_CUDA(cudaMemcpyAsync(c->d_pv, c->d_z, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
-    if ((s = dot(c, c->d_r, c->d_z, n, sc + 0)) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemsetAsync(c->d_pv, 0, 8 * n, c->stream));
+    pcg_init_scalars<<<1, 32, 0, c->stream>>>(sc); ++c->launches;
+    // the iteration body is captured once per factorisation and replayed
+    if (!c->pcg_graph) {
+      const long long l0 = c->launches;
+      ROMB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      s = pcg_body(c, P, yloc, cloc);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+      if (s != ROMB_OK) return s;
+      ROMB_CUDA(e);
+      ROMB_CUDA(cudaGraphInstantiate(&c->pcg_graph, graph, 0));
+      cudaGraphDestroy(graph);
+      c->pcg_graph_launches = c->launches - l0;
+      c->launches = l0;
+    }
     int it = 0;
     double rel = 1.0;
-    const int g = grid_for(c, n);
     while (it < maxit) {
-      if ((s = apply_S(c, P, c->d_pv, c->d_q, yloc)) != ROMB_OK) return s;
-      if ((s = dot(c, c->d_pv, c->d_q, n, sc + 1)) != ROMB_OK) return s;
-      pcg_update_x_r<<<g, 256, 0, c->stream>>>(n, sc, c->d_x, c->d_r, c->d_pv, c->d_q);
-      if ((s = dot(c, c->d_r, c->d_r, n, sc + 3)) != ROMB_OK) return s;
-      ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+      ROMB_CUDA(cudaGraphLaunch(c->pcg_graph, c->stream));
+      c->launches += c->pcg_graph_launches;
       ROMB_CUDA(cudaStreamSynchronize(c->stream));
       ++it;
       rel = sqrt(c->h_red[0]) / nf;
@@ -462,11 +497,6 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
         break;
       }
       if (rel <= rtol) break;
-      if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
-      if ((s = dot(c, c->d_r, c->d_z, n, sc + 2)) != ROMB_OK) return s;
-      pcg_update_p<<<g, 256, 0, c->stream>>>(n, sc, c->d_pv, c->d_z);
-      pcg_shift_scalars<<<1, 32, 0, c->stream>>>(sc);
-      ROMB_CUDA(cudaGetLastError());
     }
     *iters = it;
     *relres = rel;
@@ -474,8 +504,8 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
   }
   // recovery + nodal output
   cudaEventRecord(c->ev[9], c->stream);
-  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, c->stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, c->d_x, d_u);
-  skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->nskel_nodes, c->d_x, d_u);
+  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, c->stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, c->d_x, d_u); ++c->launches;
+  skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->nskel_nodes, c->d_x, d_u); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   cudaEventRecord(c->ev[10], c->stream);
   ROMB_CUDA(cudaStreamSynchronize(c->stream));

@@ -39,8 +39,10 @@ struct RombRom {
   double lo = 0, hi = 0;
   long long n_half = 0;        // pairs k1 <= k2 times 4 (q+1)^2 columns
   double* U64 = nullptr;       // [(n_r+1)][n_half]: row 0 = I_Pi, rows 1.. = U_r
-  float* Uhi = nullptr;        // same, tf32/bf16 hi part (tensor-core forms)
-  float* Ulo = nullptr;        // same, lo part
+  float* Uhi = nullptr;        // unused (kept for layout compatibility)
+  float* Ulo = nullptr;        // unused
+  float* Utiles = nullptr;     // tensor-core operand: N-tiles of 144 columns, hi then lo, canonical layout
+  int ntiles = 0;
   double* A = nullptr;         // [n_r][(r+1)^4]
   double* At = nullptr;        // [(r+1)^4][n_r]
   int kpad = 0;                // n_r+1 rounded up for the tensor-core K dimension
@@ -99,6 +101,7 @@ struct romb_ctx {
 
   // lattice
   bool have_lattice = false, assembled = false, factored = false;
+  bool assembled_split = false;   // cell matrices from a split-precision form
   int nx = 0, ny = 0, p = 0, m = 0, basis = 0, ncells = 0, mem = 0;
   int nB = 0, ndof = 0, nI = 0, nU = 0, q = 2, nL = 9;
   long long kpack = 0, upack = 0;   // packed sizes of K and of nU x nU
@@ -114,6 +117,7 @@ struct romb_ctx {
 
   // per-cell arrays
   double* d_chat = nullptr;     // [cells][nL][16]
+  float* d_chat32 = nullptr;    // [cells][144] FP32 copy for the tensor-core epilogue
   double* d_theta = nullptr;    // [cells][kmax]
   float* d_theta_hi = nullptr;  // [cells][kpad] tensor-core operand (hi)
   float* d_theta_lo = nullptr;  // [cells][kpad] (lo)
@@ -153,11 +157,15 @@ struct romb_ctx {
   double* d_fI = nullptr;       // [cells][nI] interior forces
   double* d_fU = nullptr;       // [cells][nU] skeleton-slot forces
   double* d_cloc = nullptr;     // [cells][20] coarse restriction Psi^T D r
+  double* d_yloc = nullptr;     // [cells][nU] cell-local PCG scratch
+  cudaGraphExec_t pcg_graph = nullptr;   // captured PCG iteration (per factorisation)
+  long long pcg_graph_launches = 0;
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
   double* d_u = nullptr;        // nodal output [nodes][2]
   double* d_traction = nullptr;
 
-  // timing
+  // timing and launch accounting
+  long long launches = 0;      // kernels launched by this context so far
   cudaEvent_t ev[16];
   double phase_ms[8] = {0};
 };
@@ -185,6 +193,9 @@ romb_status launch_flag_or(romb_ctx* c, int* d_any);
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
 romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxit, double* d_u_out,
                       int* iters, double* relres);
+
+void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<float>& tiles,
+                 int* ntiles);
 
 // small host helpers
 inline long long tri(long long n) { return n * (n + 1) / 2; }
