@@ -45,6 +45,9 @@ def args_parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32split"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--sub", type=int, default=0,
+                    help="profiling only: run the first N x N cells of the workload")
     ap.add_argument("--cpu-sample-json", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--rom-dir", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -158,8 +161,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate(total_ms: float, cells_per_rank: int, world: int, device=None):
+    """Whole-job throughput of independent replicas: every rank processes its own
+    copy of the workload; the job time is the slowest rank's (all_reduce MAX)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * cells_per_rank / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
-# flop models (algorithmic counts per cell, documented in the design doc)
+# flop models (algorithmic counts per cell)
 # ---------------------------------------------------------------------------
 def factor_flops(p: int) -> float:
     NI, NU = 2 * (p - 1) ** 2, 8 * p
@@ -200,6 +215,8 @@ def run_ours(a):
     rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
     paths, train_s = train_models(rom_dir)
     lat = LI.config(CONFIG)
+    if a.sub:
+        lat = sub_lattice(lat, a.sub, a.sub)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = romb.Context(local, 0, stream.cuda_stream)
@@ -214,7 +231,7 @@ def run_ours(a):
 
     have_tc = a.precision != "fp64"
     precisions = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT}
-    if have_tc:
+    if a.precision == "auto":
         try:
             romb.romb_assemble(ctx.h, lat, romb.ROMB_FP32_SPLIT, device_arrays=darr)
         except romb.RombError:
@@ -261,11 +278,7 @@ def run_ours(a):
     launches = (romb.romb_launch_count(ctx.h) - l0) // max(1, a.steps)
     barrier()
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, _ = aggregate(sum(times), lat.ncells, world, dev)
     ms = total_ms / a.steps
     value = world * lat.ncells / (ms / 1e3)
     ph = np.mean(np.array(phases), axis=0)
@@ -273,7 +286,7 @@ def run_ours(a):
     # accuracy of the split form against the FP64 form (same device, same inputs)
     u_form = u_dev.clone()
     acc = {}
-    if have_tc:
+    if have_tc and not a.no_accuracy:
         other = romb.ROMB_FP64 if form == "fp32split" else romb.ROMB_FP32_SPLIT
         step(other)
         num = torch.linalg.vector_norm(u_form - u_dev).item()

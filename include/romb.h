@@ -132,6 +132,21 @@ romb_status romb_factor(romb_ctx* ctx);
 romb_status romb_bddc_solve(romb_ctx* ctx, int nrhs, const double* traction_sets, double rtol,
                             int maxit, double* u_out, int* iters_out, double* relres_out);
 
+/* Compliance c = f^T u of the last solve (first right-hand side) and its
+ * gradient by the discrete adjoint (Sec. 6: the ROM makes the gradient
+ * available): dc = 2 u^T df - sum_i u_i^T dK_i u_i, with dK_i through the
+ * pulled-back tensor of Eq. (ELA constitutive) for the map control points and
+ * through I_r(mu) of Algorithm 5 for the thresholds; cell matrices are
+ * differentiated in their FP64 form.  The traction loads are differentiated
+ * through the edge Jacobian only (their active interval is taken fixed in mu).
+ * dc_dctrl: [(m*nx+1)*(m*ny+1)][2]; dc_dmu: [cells][4] (nullable);
+ * dc_dR: [cells] = sum of the four dc/dmu_i (nullable; the derivative with
+ * respect to a uniform per-cell threshold such as a hole radius).  Pointers
+ * follow the lattice's memory kind.  Requires romb_assemble (not _host_K) and
+ * a solve.  Errors: ROMB_E_STATE. */
+romb_status romb_compliance_grad(romb_ctx* ctx, double* compliance, double* dc_dctrl, double* dc_dR,
+                                 double* dc_dmu);
+
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
  * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits

@@ -3,7 +3,7 @@
 The paper notes that the ROM surrogate makes the gradient of the solution with
 respect to the design parameters straightforward (Sec. 6); it gives no formula.
 This module writes out the discrete adjoint of the model the solver actually
-solves (reading: the gradient of the discrete compliance, SURVEY 8(c) xv):
+solves (read as: the gradient of the discrete compliance):
 
     c = f^T u,   K u = f   (K, f assembled from the cells, Dirichlet DoFs removed)
     dc = 2 u^T df - u^T dK u          (K symmetric: the adjoint state is u itself)

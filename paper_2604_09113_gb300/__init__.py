@@ -62,6 +62,7 @@ def _load():
         "romb_read": ([P, I, P, S], I),
         "romb_train": ([ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
         "romb_launch_count": ([P], ctypes.c_longlong),
+        "romb_compliance_grad": ([P, P, P, P, P], I),
         "romb_train_snapshot": ([ctypes.POINTER(RombTrainSpec), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -163,6 +164,17 @@ def romb_stats(ctx, ncells: int | None = None):
     flags = np.zeros(ncells, dtype=np.int32) if ncells else None
     _check(_lib.romb_stats(ctx, ms.ctypes.data, None if flags is None else flags.ctypes.data), "romb_stats")
     return ms, flags
+
+
+def romb_compliance_grad(ctx, n_ctrl: int, ncells: int):
+    """Returns (compliance, dc/dctrl [n_ctrl, 2], dc/dR [cells], dc/dmu [cells, 4]) of the last solve."""
+    c = ctypes.c_double()
+    dx = np.zeros((n_ctrl, 2))
+    dR = np.zeros(ncells)
+    dmu = np.zeros((ncells, 4))
+    _check(_lib.romb_compliance_grad(ctx, ctypes.byref(c), dx.ctypes.data, dR.ctypes.data, dmu.ctypes.data),
+           "romb_compliance_grad")
+    return c.value, dx, dR, dmu
 
 
 def romb_launch_count(ctx) -> int:

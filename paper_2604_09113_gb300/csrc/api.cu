@@ -493,9 +493,10 @@ extern "C" romb_status romb_assemble(romb_ctx* c, const romb_lattice* L, romb_pr
   if (s != ROMB_OK) return s;
   for (auto& R : c->roms)
     if (R.loaded && (R.p != c->p || R.kind != c->basis)) return ROMB_E_ARG;
-  c->assembled = c->factored = false;
+  c->assembled = c->factored = c->solved = false;
   c->prec = prec;
   c->assembled_split = prec != ROMB_FP64;
+  c->assembled_rom = true;
   cudaEventRecord(c->ev[0], c->stream);
   if ((s = launch_theta(c)) != ROMB_OK) return s;
   cudaEventRecord(c->ev[1], c->stream);
@@ -516,8 +517,9 @@ extern "C" romb_status romb_assemble_host_K(romb_ctx* c, const romb_lattice* L, 
   ROMB_CUDA(cudaSetDevice(c->device));
   romb_status s = load_lattice(c, L);
   if (s != ROMB_OK) return s;
-  c->assembled = c->factored = false;
+  c->assembled = c->factored = c->solved = false;
   c->assembled_split = false;
+  c->assembled_rom = false;
   // pack the dense matrices on the device (upper triangle, row-major)
   double* dense = nullptr;
   const size_t nd = (size_t)c->ndof;
@@ -594,7 +596,52 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
   }
   c->phase_ms[7] = c->phase_ms[0] + c->phase_ms[1] + c->phase_ms[2] + c->phase_ms[3] + c->phase_ms[4] +
                    c->phase_ms[5];
+  c->solved = true;
   return worst;
+}
+
+__global__ void sum4_kernel(const double* __restrict__ dmu, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = dmu[4 * i] + dmu[4 * i + 1] + dmu[4 * i + 2] + dmu[4 * i + 3];
+}
+
+extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, double* dc_dctrl, double* dc_dR,
+                                            double* dc_dmu) {
+  if (!c || !compliance || !dc_dctrl) return ROMB_E_ARG;
+  if (!c->solved || !c->assembled_rom) return ROMB_E_STATE;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  romb_status s;
+  const long long nctrl = (long long)(c->m * c->nx + 1) * (c->m * c->ny + 1);
+  if (!c->d_gdmu) {
+    if ((s = romb_alloc_t(c, &c->d_gdmu, 4 * (size_t)c->ncells)) != ROMB_OK) return s;
+    if ((s = romb_alloc_t(c, &c->d_gdctrl, 2 * (size_t)nctrl)) != ROMB_OK) return s;
+  }
+  // c = f^T u on the skeleton (no interior forces)
+  if ((s = romb_dot(c, c->d_f, c->d_x, c->nskel, c->d_red + 8)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpyAsync(c->h_red + 2, c->d_red + 8, 8, cudaMemcpyDeviceToHost, c->stream));
+  const bool dev = c->mem == ROMB_MEM_DEVICE;
+  double* d_ctrl_out = dev ? dc_dctrl : c->d_gdctrl;
+  double* d_mu_out = (dev && dc_dmu) ? dc_dmu : c->d_gdmu;
+  if ((s = launch_grad(c, d_ctrl_out, d_mu_out)) != ROMB_OK) return s;
+  if (dc_dR) {
+    double* d_r_out = dev ? dc_dR : c->d_gdctrl + 0;   // host case handled below
+    if (dev) {
+      sum4_kernel<<<c->sms, 256, 0, c->stream>>>(d_mu_out, c->ncells, d_r_out); ++c->launches;
+      ROMB_CUDA(cudaGetLastError());
+    }
+  }
+  if (!dev) {
+    ROMB_CUDA(cudaMemcpyAsync(dc_dctrl, c->d_gdctrl, 16 * nctrl, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> dmu(4 * (size_t)c->ncells);
+    ROMB_CUDA(cudaMemcpyAsync(dmu.data(), c->d_gdmu, 32 * (size_t)c->ncells, cudaMemcpyDeviceToHost, c->stream));
+    ROMB_CUDA(cudaStreamSynchronize(c->stream));
+    if (dc_dmu) memcpy(dc_dmu, dmu.data(), 32 * (size_t)c->ncells);
+    if (dc_dR)
+      for (long long i = 0; i < c->ncells; ++i) dc_dR[i] = dmu[4 * i] + dmu[4 * i + 1] + dmu[4 * i + 2] + dmu[4 * i + 3];
+  }
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  *compliance = c->h_red[2];
+  return ROMB_OK;
 }
 
 extern "C" romb_status romb_stats(romb_ctx* c, double* phase_ms, int* flags_out) {

@@ -27,6 +27,8 @@
 
 #include <vector>
 
+#include <string.h>
+
 #include <string>
 
 #include "device.cuh"
@@ -38,12 +40,17 @@
 #define TC_THREADS 384
 #define TC_WAIT_CYCLES (4000000000LL)   // ~2 s at 2 GHz
 
-struct TcParams {
-  const float* Utiles;     // per tile: hi [TC_N x KT], lo [TC_N x KT] (canonical layout), then f64 rows 0, 1 [2][TC_N]
-  const double* theta;     // [cells][128] f64 (slots 0, 1 used exactly)
-  int ntiles, KT;
+struct TcFamily {
+  const float* Utiles;     // per tile: hi, lo [TC_N x KT] (canonical layout), then rows 0, 1 as float pairs [2][TC_N][2]
   const int* list;         // cells of this family
-  int count;
+  int count, mtile0;       // cells, first M-tile index of this family in the grid
+};
+
+struct TcParams {
+  TcFamily fam[ROMB_MAX_FAMILIES];
+  int nfam;
+  const double* theta;     // [cells][128] f64 (slots 0, 1 applied exactly in the epilogue)
+  int ntiles, KT;
   const float* th_hi;      // [cells][128]
   const float* th_lo;
   const float* chat32;     // [cells][144]
@@ -151,6 +158,42 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// ---- double-float (pair of FP32) arithmetic for the epilogue: ~48-bit
+// significands on the FP32 pipe, which GB300 runs ~64x faster than FP64 ----
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl df_quick(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = df_two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return df_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dfl df_mul_f(dfl x, float c) {
+  const float p = x.hi * c;
+  float e = fmaf(x.hi, c, -p);
+  e = fmaf(x.lo, c, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dfl df_from_double(double d) {
+  const float h = (float)d;
+  return {h, (float)(d - (double)h)};
+}
+
 // byte offset of element (row, k) in a canonical tile with SBO = KT * 32
 __host__ __device__ inline uint32_t canon_off(int row, int k, int KT) {
   return (uint32_t)((row >> 3) * (KT * 32) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
@@ -172,7 +215,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
   unsigned char* Bst = base + 2 * a_bytes;   // stage s at Bst + s * 2 * b_bytes (hi, lo)
   const int S = P.stages;
   const int T = P.ntiles;
-  const int m0 = blockIdx.x * TC_M;
+  int fi = 0;
+  while (fi + 1 < P.nfam && (int)blockIdx.x >= P.fam[fi + 1].mtile0) ++fi;
+  const TcFamily F = P.fam[fi];
+  const int m0 = ((int)blockIdx.x - F.mtile0) * TC_M;
 
   if (tid == 0) {
     s_abort = 0;
@@ -196,8 +242,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
     const int row = i / KT, k = i % KT;
     const int ci = m0 + row;
     float h = 0.f, l = 0.f;
-    if (ci < P.count) {
-      const long long cell = P.list[ci];
+    if (ci < F.count) {
+      const long long cell = F.list[ci];
       h = P.th_hi[cell * 128 + k];
       l = P.th_lo[cell * 128 + k];
     }
@@ -224,7 +270,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         }
         unsigned char* dst = Bst + (size_t)s * stage_bytes;
         mbar_expect_tx(&bar_full[s], stage_bytes);
-        bulk_g2s(dst, (const unsigned char*)P.Utiles + (size_t)t * stage_bytes, stage_bytes, &bar_full[s]);
+        bulk_g2s(dst, (const unsigned char*)F.Utiles + (size_t)t * stage_bytes, stage_bytes, &bar_full[s]);
         armed_last[s] = t;
       }
       // drain: every armed copy must land before the CTA exits
@@ -270,15 +316,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
     const int g = (warp - 4) >> 2;
     const int row = ((warp & 3) << 5) + lane;
     const int ci = m0 + row;
-    const bool valid = ci < P.count;
-    const long long cell = valid ? P.list[ci] : 0;
+    const bool valid = ci < F.count;
+    const long long cell = valid ? F.list[ci] : 0;
     float C[72];   // Chat[k3][g][j1][i2][j2]
 #pragma unroll
     for (int k3 = 0; k3 < 9; ++k3)
 #pragma unroll
       for (int e = 0; e < 8; ++e) C[8 * k3 + e] = valid ? P.chat32[cell * 144 + 16 * k3 + 8 * g + e] : 0.f;
-    const double th0 = valid ? P.theta[cell * 128 + 0] : 0.0;
-    const double th1 = valid ? P.theta[cell * 128 + 1] : 0.0;
+    const dfl th0 = df_from_double(valid ? P.theta[cell * 128 + 0] : 0.0);
+    const dfl th1 = df_from_double(valid ? P.theta[cell * 128 + 1] : 0.0);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const long long kp = (long long)P.ndof * (P.ndof + 1) / 2;
     double* Kc = P.Kout + cell * kp;
@@ -290,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         break;
       }
       tc_fence_after();
-      const double* U01 = (const double*)(Bst + (size_t)s * stage_bytes + 2 * b_bytes);   // [2][TC_N]
+      const float2* U01 = (const float2*)(Bst + (size_t)s * stage_bytes + 2 * b_bytes);   // [2][TC_N] (hi, lo)
 #pragma unroll 1
       for (int pl = 0; pl < TC_PAIRS; ++pl) {
         float acc[36];
@@ -302,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         const int pr = t * TC_PAIRS + pl;
         if (!valid || pr >= P.npairs) continue;
         const int2 kk = P.pairs[pr];
-        double v0 = 0.0, v1 = 0.0;
+        dfl v0 = {0.f, 0.f}, v1 = {0.f, 0.f};
 #pragma unroll
         for (int k3 = 0; k3 < 9; ++k3)
 #pragma unroll
@@ -310,14 +356,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
 #pragma unroll
             for (int j2 = 0; j2 < 2; ++j2) {
               const int e = k3 * 4 + 2 * j1 + j2;
-              const double Ie = fma(th0, U01[36 * pl + e], fma(th1, U01[TC_N + 36 * pl + e], (double)acc[e]));
-              v0 = fma(Ie, (double)C[8 * k3 + 4 * j1 + j2], v0);       // i2 = 0
-              v1 = fma(Ie, (double)C[8 * k3 + 4 * j1 + 2 + j2], v1);   // i2 = 1
+              const float2 u0 = U01[36 * pl + e], u1 = U01[TC_N + 36 * pl + e];
+              dfl Ie = df_add(df_mul(th0, {u0.x, u0.y}), df_mul(th1, {u1.x, u1.y}));
+              Ie = df_add(Ie, {acc[e], 0.f});
+              v0 = df_add(v0, df_mul_f(Ie, C[8 * k3 + 4 * j1 + j2]));       // i2 = 0
+              v1 = df_add(v1, df_mul_f(Ie, C[8 * k3 + 4 * j1 + 2 + j2]));   // i2 = 1
             }
         const long long r = 2 * kk.x + g, q0 = 2 * kk.y;
         double* Kr = Kc + r * P.ndof - r * (r - 1) / 2 - r;
-        if (!(kk.x == kk.y && g == 1)) Kr[q0] = v0;
-        Kr[q0 + 1] = v1;
+        if (!(kk.x == kk.y && g == 1)) Kr[q0] = (double)v0.hi + (double)v0.lo;
+        Kr[q0 + 1] = (double)v1.hi + (double)v1.lo;
       }
       tc_fence_before();
       mbar_arrive(&bar_accempty[b]);
@@ -350,12 +398,16 @@ void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad
   tiles.assign((size_t)T * stage_floats, 0.f);
   for (long long t = 0; t < T; ++t) {
     float* base = tiles.data() + (size_t)t * stage_floats;
-    double* rows01 = (double*)(base + 2 * tile_floats);
+    float* rows01 = base + 2 * tile_floats;   // [2][TC_N][hi, lo]
     for (int n = 0; n < ncol_tile; ++n) {
       const long long col = t * ncol_tile + n;
       if (col >= n_half) continue;
-      rows01[n] = U[(size_t)0 * n_half + col];
-      rows01[ncol_tile + n] = K > 1 ? U[(size_t)1 * n_half + col] : 0.0;
+      for (int rr = 0; rr < 2; ++rr) {
+        const double x = rr < K ? U[(size_t)rr * n_half + col] : 0.0;
+        const float h = (float)x;
+        rows01[2 * (rr * ncol_tile + n)] = h;
+        rows01[2 * (rr * ncol_tile + n) + 1] = (float)(x - (double)h);
+      }
       for (int k = 2; k < K; ++k) {
         const double x = U[(size_t)k * n_half + col];
         const float h = tf32_round((float)x);
@@ -374,40 +426,52 @@ romb_status launch_assemble_tc(romb_ctx* c) {
   }
   int* d_err = (int*)c->d_red + 32;
   ROMB_CUDA(cudaMemsetAsync(d_err, 0, 4, c->stream));
+  TcParams P;
+  memset(&P, 0, sizeof(P));
+  int KT = -1, T = -1, grid = 0;
   for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
-    TcParams P;
-    P.Utiles = R.Utiles;
-    P.theta = c->d_theta;
-    P.ntiles = R.ntiles;
-    P.KT = R.kpad;
-    P.list = c->d_famlist + c->famstart[f];
-    P.count = c->famcount[f];
-    P.th_hi = c->d_theta_hi;
-    P.th_lo = c->d_theta_lo;
-    P.chat32 = c->d_chat32;
-    P.Kout = c->d_K;
-    P.ndof = c->ndof;
-    P.pairs = c->d_pairs;
-    P.npairs = c->nB * (c->nB + 1) / 2;
-    P.err = d_err;
-    const size_t a_bytes = (size_t)TC_M * P.KT * 4, b_bytes = (size_t)TC_N * P.KT * 4;
-    const size_t stage_bytes = 2 * b_bytes + 2 * TC_N * 8;
-    const size_t limit = 227 * 1024 - 1024 - 256;
-    int stages = 2;
-    if (2 * a_bytes + 2 * stage_bytes > limit) stages = 1;
-    if (2 * a_bytes + stage_bytes > limit) {
-      romb_set_error("tensor-core assembly: reduced basis too large for shared memory");
+    if (KT < 0) {
+      KT = R.kpad;
+      T = R.ntiles;
+    } else if (KT != R.kpad || T != R.ntiles) {
+      romb_set_error("tensor-core assembly: all reduced models of one lattice must share n_r");
       return ROMB_E_ARG;
     }
-    P.stages = stages;
-    const size_t smem = 1024 + 2 * a_bytes + (size_t)stages * stage_bytes;
-    ROMB_CUDA(cudaFuncSetAttribute(assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (P.count + TC_M - 1) / TC_M;
-    assemble_tc_kernel<<<grid, TC_THREADS, smem, c->stream>>>(P); ++c->launches;
-    ROMB_CUDA(cudaGetLastError());
+    TcFamily& F = P.fam[P.nfam++];
+    F.Utiles = R.Utiles;
+    F.list = c->d_famlist + c->famstart[f];
+    F.count = c->famcount[f];
+    F.mtile0 = grid;
+    grid += (F.count + TC_M - 1) / TC_M;
   }
+  if (grid == 0) return ROMB_OK;
+  P.theta = c->d_theta;
+  P.ntiles = T;
+  P.KT = KT;
+  P.th_hi = c->d_theta_hi;
+  P.th_lo = c->d_theta_lo;
+  P.chat32 = c->d_chat32;
+  P.Kout = c->d_K;
+  P.ndof = c->ndof;
+  P.pairs = c->d_pairs;
+  P.npairs = c->nB * (c->nB + 1) / 2;
+  P.err = d_err;
+  const size_t a_bytes = (size_t)TC_M * KT * 4, b_bytes = (size_t)TC_N * KT * 4;
+  const size_t stage_bytes = 2 * b_bytes + 2 * TC_N * 8;
+  const size_t limit = 227 * 1024 - 1024 - 256;
+  int stages = 2;
+  if (2 * a_bytes + 2 * stage_bytes > limit) stages = 1;
+  if (2 * a_bytes + stage_bytes > limit) {
+    romb_set_error("tensor-core assembly: reduced basis too large for shared memory");
+    return ROMB_E_ARG;
+  }
+  P.stages = stages;
+  const size_t smem = 1024 + 2 * a_bytes + (size_t)stages * stage_bytes;
+  ROMB_CUDA(cudaFuncSetAttribute(assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  assemble_tc_kernel<<<grid, TC_THREADS, smem, c->stream>>>(P); ++c->launches;
+  ROMB_CUDA(cudaGetLastError());
   int h_err = 0;
   ROMB_CUDA(cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, c->stream));
   ROMB_CUDA(cudaStreamSynchronize(c->stream));

@@ -319,27 +319,32 @@ __global__ void nd_gather_kernel(const FrontDev* __restrict__ fr, const int* __r
   }
 }
 
-// y_s = L11^-1 w_s = (L11^-T)^T w_s: thread per separator row j
-__global__ void nd_fwd_y_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                const double* __restrict__ F, const int* __restrict__ idx,
-                                const double* __restrict__ wbuf, double* __restrict__ sbuf, double* __restrict__ x) {
+// y_s = L11^-1 w_s = (L11^-T)^T w_s: a CTA owns 32 separator columns j, its 8
+// warps split the rows e (coalesced row reads), partial sums reduced in shared memory.
+__global__ void __launch_bounds__(1024) nd_fwd_y_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                                        const double* __restrict__ F, const int* __restrict__ idx,
+                                                        const double* __restrict__ wbuf, double* __restrict__ sbuf,
+                                                        double* __restrict__ x) {
+  __shared__ double part[32][33];
   const NdItem it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int n = f.ns + f.nb;
-  const int j = it.start + threadIdx.x;
-  if (j >= f.ns) return;
-  const double* Y = F + f.off + (long long)n * n;   // row e: (L11^-T)[e][:]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = it.start + lane;
+  const double* Y = F + f.off + (long long)n * n;   // row e: (L11^-T)[e][:], zero for e > j
   const double* w = wbuf + f.wbuf_off;
-  double s0 = 0.0, s1 = 0.0;
-  int e = 0;
-  for (; e + 1 <= j; e += 2) {
-    s0 = fma(Y[(long long)e * n + j], w[e], s0);
-    s1 = fma(Y[(long long)(e + 1) * n + j], w[e + 1], s1);
+  double s = 0.0;
+  if (j < f.ns)
+    for (int e = warp; e <= j; e += 32) s = fma(Y[(long long)e * n + j], w[e], s);
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && j < f.ns) {
+    double y = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) y += part[k][lane];
+    sbuf[f.sbuf_off + j] = y;
+    x[idx[f.idx_off + j]] = y;
   }
-  if (e <= j) s0 = fma(Y[(long long)e * n + j], w[e], s0);
-  const double y = s0 + s1;
-  sbuf[f.sbuf_off + j] = y;
-  x[idx[f.idx_off + j]] = y;
 }
 
 // update vector u_b = w_b - L21 y_s: warp per boundary row
@@ -360,27 +365,106 @@ __global__ void nd_fwd_upd_kernel(const FrontDev* __restrict__ fr, const NdItem*
   if (lane == 0) ybuf[f.ybuf_off + r] = wbuf[f.wbuf_off + f.ns + r] - s;
 }
 
-// t_s = y_s - L21^T x_b: thread per separator row j (x_b staged in shared memory)
-__global__ void nd_bwd_t_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                const double* __restrict__ F, const int* __restrict__ idx,
-                                const double* __restrict__ x, double* __restrict__ sbuf) {
+// t_s = y_s - L21^T x_b: a CTA owns 32 separator columns, 8 warps split the
+// boundary rows (x_b staged in shared memory).
+__global__ void __launch_bounds__(1024) nd_bwd_t_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
+                                                        const double* __restrict__ F, const int* __restrict__ idx,
+                                                        const double* __restrict__ x, double* __restrict__ sbuf) {
   extern __shared__ double xb[];
+  __shared__ double part[32][33];
   const NdItem it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int n = f.ns + f.nb;
   for (int r = threadIdx.x; r < f.nb; r += blockDim.x) xb[r] = x[idx[f.idx_off + f.ns + r]];
   __syncthreads();
-  const int j = it.start + threadIdx.x;
-  if (j >= f.ns) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = it.start + lane;
   const double* L21 = F + f.off + (long long)f.ns * n;
-  double s0 = 0.0, s1 = 0.0;
-  int r = 0;
-  for (; r + 1 < f.nb; r += 2) {
-    s0 = fma(L21[(long long)r * n + j], xb[r], s0);
-    s1 = fma(L21[(long long)(r + 1) * n + j], xb[r + 1], s1);
+  double s = 0.0;
+  if (j < f.ns)
+    for (int r = warp; r < f.nb; r += 32) s = fma(L21[(long long)r * n + j], xb[r], s);
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && j < f.ns) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) t += part[k][lane];
+    sbuf[f.sbuf_off + j] -= t;
   }
-  if (r < f.nb) s0 = fma(L21[(long long)r * n + j], xb[r], s0);
-  sbuf[f.sbuf_off + j] -= s0 + s1;
+}
+
+// Levels of small fronts: the whole forward step of a front in one warp
+// (gather, y_s = L11^-1 w_s, u_b = w_b - L21 y_s); 8 fronts per CTA.
+__global__ void __launch_bounds__(256) nd_fwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                                            int nfronts, const double* __restrict__ F,
+                                                            const int* __restrict__ idx, const int* __restrict__ children,
+                                                            const int* __restrict__ emap, const double* __restrict__ rhs,
+                                                            double* __restrict__ ybuf, double* __restrict__ x, int maxn) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int fi = blockIdx.x * 8 + warp;
+  if (fi >= nfronts) return;
+  const FrontDev f = fr[level[fi]];
+  const int n = f.ns + f.nb;
+  double* w = sh + (size_t)warp * 2 * maxn;
+  double* y = w + maxn;
+  const int* id = idx + f.idx_off;
+  for (int t = lane; t < n; t += 32) w[t] = t < f.ns ? rhs[id[t]] : 0.0;
+  __syncwarp();
+  for (int k = 0; k < f.nchild; ++k) {
+    const FrontDev ch = fr[children[f.child_off + k]];
+    const int* em = emap + ch.emap_off;
+    for (int t = lane; t < ch.nb; t += 32) w[em[t]] += ybuf[ch.ybuf_off + t];
+    __syncwarp();
+  }
+  const double* A = F + f.off;
+  const double* Y = A + (long long)n * n;
+  for (int j = lane; j < f.ns; j += 32) {
+    double s = 0.0;
+    for (int e = 0; e <= j; ++e) s = fma(Y[(long long)e * n + j], w[e], s);
+    y[j] = s;
+    x[id[j]] = s;
+  }
+  __syncwarp();
+  for (int r = 0; r < f.nb; ++r) {
+    const double* row = A + (long long)(f.ns + r) * n;
+    double s = 0.0;
+    for (int j = lane; j < f.ns; j += 32) s = fma(row[j], y[j], s);
+    s = warp_sum(s);
+    if (lane == 0) ybuf[f.ybuf_off + r] = w[f.ns + r] - s;
+  }
+}
+
+// Levels of small fronts: the whole backward step of a front in one warp.
+__global__ void __launch_bounds__(256) nd_bwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                                            int nfronts, const double* __restrict__ F,
+                                                            const int* __restrict__ idx, double* __restrict__ x, int maxn) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int fi = blockIdx.x * 8 + warp;
+  if (fi >= nfronts) return;
+  const FrontDev f = fr[level[fi]];
+  const int n = f.ns + f.nb;
+  double* xb = sh + (size_t)warp * 2 * maxn;
+  double* t = xb + maxn;
+  const int* id = idx + f.idx_off;
+  for (int r = lane; r < f.nb; r += 32) xb[r] = x[id[f.ns + r]];
+  __syncwarp();
+  const double* A = F + f.off;
+  const double* L21 = A + (long long)f.ns * n;
+  for (int j = lane; j < f.ns; j += 32) {
+    double s = x[id[j]];   // y_s, stored by the forward pass
+    for (int r = 0; r < f.nb; ++r) s = fma(-L21[(long long)r * n + j], xb[r], s);
+    t[j] = s;
+  }
+  __syncwarp();
+  const double* Y = A + (long long)n * n;
+  for (int e = 0; e < f.ns; ++e) {
+    double s = 0.0;
+    for (int j = e + lane; j < f.ns; j += 32) s = fma(Y[(long long)e * n + j], t[j], s);
+    s = warp_sum(s);
+    if (lane == 0) x[id[e]] = s;
+  }
 }
 
 // x_s = L11^-T t_s: warp per separator row e
@@ -553,7 +637,7 @@ romb_status coarse_build(romb_ctx* c) {
     for (int f : lv) {
       const NdFront& Fr = plan.fronts[f];
       mnb = std::max(mnb, Fr.nb);
-      for (int j = 0; j < Fr.ns; j += 256) ci.push_back({f, j});
+      for (int j = 0; j < Fr.ns; j += 32) ci.push_back({f, j});
       for (int r = 0; r < Fr.nb; r += 8) bi.push_back({f, r});
       for (int e = 0; e < Fr.ns; e += 8) si.push_back({f, e});
     }
@@ -609,24 +693,40 @@ romb_status coarse_factor(romb_ctx* c) {
 }
 
 // out = S_C^-1 in over the non-Dirichlet coarse DoFs (Dirichlet entries of out are 0).
+// Levels whose fronts are all small use one warp per front; the few levels of
+// large fronts spread each GEMV over many CTAs.
+#define ND_SMALL_N 128
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
   const int L = (int)D.level_ids.size();
   for (int l = 0; l < L; ++l) {
+    if (D.level_maxn[l] <= ND_SMALL_N) {
+      const size_t sm = 8 * 2 * (size_t)D.level_maxn[l] * 8;
+      nd_fwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
+          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.children, D.emap, d_in, D.ybuf, d_out,
+          D.level_maxn[l]); ++c->launches;
+      continue;
+    }
     nd_gather_kernel<<<D.level_count[l], 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.idx, D.children, D.emap,
                                                               d_in, D.ybuf, D.wbuf); ++c->launches;
     if (D.col_n[l])
-      nd_fwd_y_kernel<<<D.col_n[l], 256, 0, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, D.wbuf, D.sbuf,
-                                                         d_out); ++c->launches;
+      nd_fwd_y_kernel<<<D.col_n[l], 1024, 0, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, D.wbuf, D.sbuf,
+                                                          d_out); ++c->launches;
     if (D.brow_n[l])
       nd_fwd_upd_kernel<<<D.brow_n[l], 256, 0, c->stream>>>(D.fr, D.brow_items[l], D.F, D.wbuf, D.sbuf,
                                                             D.ybuf); ++c->launches;
   }
   for (int l = L - 1; l >= 0; --l) {
+    if (D.level_maxn[l] <= ND_SMALL_N) {
+      const size_t sm = 8 * 2 * (size_t)D.level_maxn[l] * 8;
+      nd_bwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
+          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, d_out, D.level_maxn[l]); ++c->launches;
+      continue;
+    }
     if (D.col_n[l]) {
       const size_t sm = 8 * (size_t)std::max(1, D.level_maxnb[l]);
-      nd_bwd_t_kernel<<<D.col_n[l], 256, sm, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, d_out, D.sbuf); ++c->launches;
+      nd_bwd_t_kernel<<<D.col_n[l], 1024, sm, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, d_out, D.sbuf); ++c->launches;
     }
     if (D.srow_n[l])
       nd_bwd_x_kernel<<<D.srow_n[l], 256, 0, c->stream>>>(D.fr, D.srow_items[l], D.F, D.idx, D.sbuf, d_out); ++c->launches;

@@ -67,54 +67,70 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
 
 // y_loc = M_c v_loc with M_c a dense symmetric nU x nU cell matrix (S or D F D),
 // v_loc gathered from the skeleton; optionally c_loc = Phi^T v_loc.
-// One warp per cell, lanes over rows.
+// One half-warp per cell, 16 lanes over the rows (nU = 8p <= 64 rows).
 template <bool COARSE>
 __global__ void __launch_bounds__(256) cell_matvec_kernel(int ncells, int NU, const double* __restrict__ M,
                                                            const int* __restrict__ umap, const double* __restrict__ v,
                                                            double* __restrict__ yloc, const double* __restrict__ Phi,
                                                            double* __restrict__ cloc) {
-  __shared__ double sv[8][64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long cell = (long long)blockIdx.x * 8 + warp;
-  if (cell >= ncells) return;
-  for (int u = lane; u < NU; u += 32) {
-    const int g = umap[cell * NU + u];
-    sv[warp][u] = g >= 0 ? v[g] : 0.0;
+  __shared__ double sv[16][64];
+  const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
+  const long long cell0 = (long long)blockIdx.x * 16 + slot;
+  const bool active = cell0 < ncells;
+  const long long cell = active ? cell0 : 0;
+  for (int u = hl; u < NU; u += 16) {
+    const int g = active ? umap[cell * NU + u] : -1;
+    sv[slot][u] = g >= 0 ? v[g] : 0.0;
   }
   __syncwarp();
+  if (!active) return;
   const double* Mc = M + cell * NU * NU;
-  for (int r = lane; r < NU; r += 32) {
-    double acc = 0.0;
-    for (int k = 0; k < NU; ++k) acc = fma(Mc[k * NU + r], sv[warp][k], acc);   // symmetric: column r
-    yloc[cell * NU + r] = acc;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int nrow = (NU + 15 - hl) >> 4;   // rows hl, hl+16, ...
+#pragma unroll 4
+  for (int k = 0; k < NU; ++k) {
+    const double vk = sv[slot][k];
+    const double* col = Mc + k * NU + hl;   // symmetric: column k = row k
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < nrow) acc[i] = fma(col[16 * i], vk, acc[i]);
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < nrow) yloc[cell * NU + hl + 16 * i] = acc[i];
   if (COARSE) {
     const double* Pc = Phi + cell * NU * 20;
-    if (lane < 20) {
-      double acc = 0.0;
-      for (int u = 0; u < NU; ++u) acc = fma(Pc[u * 20 + lane], sv[warp][u], acc);
-      cloc[cell * 20 + lane] = acc;
+    double a0 = 0.0, a1 = 0.0;
+    for (int u = 0; u < NU; ++u) {
+      const double vu = sv[slot][u];
+      a0 = fma(Pc[u * 20 + hl], vu, a0);
+      if (hl < 4) a1 = fma(Pc[u * 20 + 16 + hl], vu, a1);
     }
+    cloc[cell * 20 + hl] = a0;
+    if (hl < 4) cloc[cell * 20 + 16 + hl] = a1;
   }
 }
 
-// y_loc += Phi g_loc  (coarse prolongation, Algorithm 1)
+// y_loc += Phi g_loc  (coarse prolongation, Algorithm 1); half-warp per cell
 __global__ void __launch_bounds__(256) cell_prolong_kernel(int ncells, int NU, const double* __restrict__ Phi,
                                                             const int* __restrict__ cmap, const double* __restrict__ g,
                                                             double* __restrict__ yloc) {
-  __shared__ double sg[8][20];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long cell = (long long)blockIdx.x * 8 + warp;
-  if (cell >= ncells) return;
-  if (lane < 20) {
-    const int k = cmap[cell * 20 + lane];
-    sg[warp][lane] = k >= 0 ? g[k] : 0.0;
+  __shared__ double sg[16][20];
+  const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
+  const long long cell0 = (long long)blockIdx.x * 16 + slot;
+  const bool active = cell0 < ncells;
+  const long long cell = active ? cell0 : 0;
+  for (int j = hl; j < 20; j += 16) {
+    const int k = active ? cmap[cell * 20 + j] : -1;
+    sg[slot][j] = k >= 0 ? g[k] : 0.0;
   }
   __syncwarp();
+  if (!active) return;
   const double* Pc = Phi + cell * NU * 20;
-  for (int u = lane; u < NU; u += 32) {
+  for (int u = hl; u < NU; u += 16) {
     double acc = yloc[cell * NU + u];
-    for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[warp][j], acc);
+#pragma unroll
+    for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[slot][j], acc);
     yloc[cell * NU + u] = acc;
   }
 }
@@ -187,86 +203,6 @@ __global__ void pcg_shift_scalars(double* sc) {
 
 // Traction loads on the solid part of the loaded lattice edges (Eq. ELA
 // constitutive: that = j t), one thread per (cell, edge node).
-__device__ int edge_solid(int family, const double* mu4, int e, double* lo, double* hi) {
-  // parameter t along the edge; fixed coordinate c0
-  const double c0 = (e == 1 || e == 3) ? 1.0 : 0.0;
-  double a, b;
-  if (e < 2) {   // vertical edge: mu(c0, t)
-    a = mu4[0] * (1.0 - c0) + mu4[1] * c0;
-    b = (mu4[2] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[1]) * c0;
-  } else {       // horizontal edge: mu(t, c0)
-    a = mu4[0] * (1.0 - c0) + mu4[2] * c0;
-    b = (mu4[1] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[2]) * c0;
-  }
-  int n = 0;
-  if (family == 0) {   // solid outside |xi - c| = mu
-    const double A = 1.0 - b * b, B = -1.0 - 2.0 * a * b, C = (c0 - 0.5) * (c0 - 0.5) + 0.25 - a * a;
-    const double disc = B * B - 4.0 * A * C;
-    if (disc <= 0.0) {
-      lo[0] = 0.0;
-      hi[0] = 1.0;
-      return 1;
-    }
-    const double s = sqrt(disc), r1 = (-B - s) / (2.0 * A), r2 = (-B + s) / (2.0 * A);
-    if (r1 > 0.0) {
-      lo[n] = 0.0;
-      hi[n] = fmin(r1, 1.0);
-      if (hi[n] > lo[n]) ++n;
-    }
-    if (r2 < 1.0) {
-      lo[n] = fmax(r2, 0.0);
-      hi[n] = 1.0;
-      if (hi[n] > lo[n]) ++n;
-    }
-    return n;
-  }
-  // cross: |c0 - 1/2| < a + b t  or  |t - 1/2| < a + b t
-  double l1, h1;
-  const double tt = fabs(c0 - 0.5) - a;
-  bool has1 = true;
-  if (b > 0.0) {
-    l1 = tt / b;
-    h1 = 1e300;
-  } else if (b < 0.0) {
-    l1 = -1e300;
-    h1 = tt / b;
-  } else if (tt < 0.0) {
-    l1 = -1e300;
-    h1 = 1e300;
-  } else {
-    has1 = false;
-    l1 = h1 = 0.0;
-  }
-  const double l2 = (0.5 - a) / (1.0 + b), h2 = (0.5 + a) / (1.0 - b);
-  double L[2], H[2];
-  int m = 0;
-  if (has1) {
-    L[m] = fmax(l1, 0.0);
-    H[m] = fmin(h1, 1.0);
-    if (H[m] > L[m]) ++m;
-  }
-  L[m] = fmax(l2, 0.0);
-  H[m] = fmin(h2, 1.0);
-  if (H[m] > L[m]) ++m;
-  if (m == 2 && L[1] < L[0]) {
-    double t = L[0];
-    L[0] = L[1];
-    L[1] = t;
-    t = H[0];
-    H[0] = H[1];
-    H[1] = t;
-  }
-  for (int i = 0; i < m; ++i) {
-    if (n > 0 && L[i] <= hi[n - 1]) hi[n - 1] = fmax(hi[n - 1], H[i]);
-    else {
-      lo[n] = L[i];
-      hi[n] = H[i];
-      ++n;
-    }
-  }
-  return n;
-}
-
 __global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, const double* __restrict__ mu,
                              const int32_t* __restrict__ family, const double* __restrict__ trac,
                              double* __restrict__ fU) {
@@ -288,7 +224,7 @@ __global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, cons
     const long long cell = cx + (long long)nx * cy;
     const int k = e == 0 ? (p + 1) * s : e == 1 ? p + (p + 1) * s : e == 2 ? s : s + (p + 1) * p;
     double lo[3], hi[3];
-    const int nint = edge_solid(family[cell], mu + 4 * cell, e, lo, hi);
+    const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
     double acc = 0.0;
     for (int iv = 0; iv < nint; ++iv) {
       const double len = hi[iv] - lo[iv];
@@ -370,7 +306,9 @@ __global__ void skel_to_nodes_kernel(CellParams P, long long nnodes, const doubl
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-static romb_status dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
+romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
+static romb_status dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) { return romb_dot(c, a, b, n, out); }
+romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
   double* part = c->d_red + 64;
   dot_partial_kernel<<<RED_BLOCKS, 256, 0, c->stream>>>(a, b, n, part); ++c->launches;
   dot_final_kernel<<<1, 256, 0, c->stream>>>(part, RED_BLOCKS, out); ++c->launches;
@@ -389,7 +327,7 @@ static int grid_for(const romb_ctx* c, long long n) {
 // z = S_BDDC^-1 r  (Algorithm 1)
 static romb_status precondition(romb_ctx* c, const CellParams& P, const double* r, double* z, double* yloc,
                                 double* cloc) {
-  const int cb = (c->ncells + 7) / 8;
+  const int cb = (c->ncells + 15) / 16;
   cell_matvec_kernel<true><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_G, c->d_ucell_map, r, yloc, c->d_Phi,
                                                       cloc); ++c->launches;
   double* zc = c->d_coarse;
@@ -405,7 +343,7 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
 }
 
 static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
-  const int cb = (c->ncells + 7) / 8;
+  const int cb = (c->ncells + 15) / 16;
   cell_matvec_kernel<false><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_S, c->d_ucell_map, v, yloc, nullptr,
                                                        nullptr); ++c->launches;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out); ++c->launches;

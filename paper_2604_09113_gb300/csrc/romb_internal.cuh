@@ -164,6 +164,15 @@ struct romb_ctx {
   double* d_u = nullptr;        // nodal output [nodes][2]
   double* d_traction = nullptr;
 
+  // gradient
+  bool solved = false, assembled_rom = false;
+  double* d_gW = nullptr;       // [cells][144] sum_{k1 k2} u u I'
+  double* d_gQ = nullptr;       // [cells][128] u^T dK/dtheta_t u
+  double* d_gloc = nullptr;     // [cells][(m+1)^2][2] local control-point gradient
+  double* d_gnodes = nullptr;
+  double* d_gdmu = nullptr;     // [cells][4]
+  double* d_gdctrl = nullptr;   // [ctrl][2]
+
   // timing and launch accounting
   long long launches = 0;      // kernels launched by this context so far
   cudaEvent_t ev[16];
@@ -190,6 +199,8 @@ romb_status coarse_factor(romb_ctx* c);     // numeric
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out);
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
+romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu);
+romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
 romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxit, double* d_u_out,
                       int* iters, double* relres);
