@@ -55,7 +55,9 @@ typedef enum {
   ROMB_E_NOT_CONVERGED = -7,  /* PCG reached maxit (u_out holds the last iterate) */
   ROMB_E_NAN = -8,            /* non-finite value detected                     */
   ROMB_E_FORMAT = -9,         /* malformed ROM file                            */
-  ROMB_E_STATE = -10          /* call out of order                             */
+  ROMB_E_STATE = -10,         /* call out of order                             */
+  ROMB_E_SCRATCH = -11        /* problem too large for the fixed scratch of    */
+                              /* romb_compliance_grad_noalloc                  */
 } romb_status;
 
 typedef enum {
@@ -146,6 +148,36 @@ romb_status romb_bddc_solve(romb_ctx* ctx, int nrhs, const double* traction_sets
  * a solve.  Errors: ROMB_E_STATE. */
 romb_status romb_compliance_grad(romb_ctx* ctx, double* compliance, double* dc_dctrl, double* dc_dR,
                                  double* dc_dmu);
+
+/* Size in bytes of the fixed device scratch of romb_compliance_grad_noalloc
+ * (one array per device, 16 MiB). */
+#define ROMB_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* romb_compliance_grad for callers that cannot allocate device memory when
+ * they need the gradient.  The paper has no counterpart of this call.
+ *
+ * Arguments, results, memory kinds and errors are those of
+ * romb_compliance_grad, and the results are bitwise equal to its results.
+ * romb_compliance_grad allocates its intermediate arrays in the context on
+ * its first call; this call allocates nothing (no cudaMalloc, no library call
+ * that allocates) and keeps them in one static device array of
+ * ROMB_NOALLOC_SCRATCH_BYTES instead.  The problem must fit in it: with
+ * C cells and control grid (m*nx+1) x (m*ny+1) = G points it needs
+ *   8 * (C * (277 + 2 (m+1)^2) + 2 G + 64) bytes plus at most 7 * 255 of
+ * alignment, e.g. 10.7 MB for 64 x 64 cells at m = 3 and roughly 5,800 cells
+ * at m = 4; larger problems return ROMB_E_SCRATCH and change nothing.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress, which may load the
+ * library's device code and its static memory.  Make that first call before
+ * any stream capture, at a point where that one-time load is acceptable.
+ * Every call clears the part of the array it uses before using it.
+ *
+ * The array is shared by every context on the device: calls that overlap in
+ * time on one device (from several host threads, or from contexts on
+ * unordered streams) race on it and must be serialised by the caller. */
+romb_status romb_compliance_grad_noalloc(romb_ctx* ctx, double* compliance, double* dc_dctrl, double* dc_dR,
+                                         double* dc_dmu);
 
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,

@@ -20,7 +20,7 @@ ROMB_MEM_HOST, ROMB_MEM_DEVICE = 0, 1
 FIELDS = {"chat": 0, "theta": 1, "K": 2, "S": 3, "psi": 4, "sc_local": 5, "D": 6, "fine": 7, "flags": 8}
 STATUS = {0: "ROMB_OK", -1: "ROMB_E_ARG", -2: "ROMB_E_CUDA", -3: "ROMB_E_OOM", -4: "ROMB_E_OUT_OF_BOX",
           -5: "ROMB_E_BAD_MAP", -6: "ROMB_E_NOT_SPD", -7: "ROMB_E_NOT_CONVERGED", -8: "ROMB_E_NAN",
-          -9: "ROMB_E_FORMAT", -10: "ROMB_E_STATE"}
+          -9: "ROMB_E_FORMAT", -10: "ROMB_E_STATE", -11: "ROMB_E_SCRATCH"}
 
 
 class RombError(RuntimeError):
@@ -63,6 +63,7 @@ def _load():
         "romb_train": ([ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
         "romb_launch_count": ([P], ctypes.c_longlong),
         "romb_compliance_grad": ([P, P, P, P, P], I),
+        "romb_compliance_grad_noalloc": ([P, P, P, P, P], I),
         "romb_train_snapshot": ([ctypes.POINTER(RombTrainSpec), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -174,6 +175,18 @@ def romb_compliance_grad(ctx, n_ctrl: int, ncells: int):
     dmu = np.zeros((ncells, 4))
     _check(_lib.romb_compliance_grad(ctx, ctypes.byref(c), dx.ctypes.data, dR.ctypes.data, dmu.ctypes.data),
            "romb_compliance_grad")
+    return c.value, dx, dR, dmu
+
+
+def romb_compliance_grad_noalloc(ctx, n_ctrl: int, ncells: int):
+    """romb_compliance_grad computed in the library's fixed static scratch
+    (no device allocation in the call); same results."""
+    c = ctypes.c_double()
+    dx = np.zeros((n_ctrl, 2))
+    dR = np.zeros(ncells)
+    dmu = np.zeros((ncells, 4))
+    _check(_lib.romb_compliance_grad_noalloc(ctx, ctypes.byref(c), dx.ctypes.data, dR.ctypes.data,
+                                             dmu.ctypes.data), "romb_compliance_grad_noalloc")
     return c.value, dx, dR, dmu
 
 

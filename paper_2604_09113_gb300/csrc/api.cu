@@ -28,6 +28,7 @@ extern "C" const char* romb_strerror(romb_status s) {
     case ROMB_E_NAN: return "non-finite value";
     case ROMB_E_FORMAT: return "malformed ROM file";
     case ROMB_E_STATE: return "call out of order";
+    case ROMB_E_SCRATCH: return "problem larger than the fixed scratch of the no-allocation call";
   }
   return "unknown status";
 }

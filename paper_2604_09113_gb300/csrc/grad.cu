@@ -299,3 +299,41 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
+
+// The launches of launch_grad with caller-supplied intermediate arrays: W
+// [cells][144], Q [cells][128], gloc [cells][2 (m+1)^2] and one 16-double
+// node table per family (nodes_dev + 16 f), so that families need no stream
+// synchronisation between them.  Used by the no-allocation gradient.
+romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* nodes_dev, double* d_dctrl,
+                                double* d_dmu) {
+  CellParams P;
+  fill_cell_params(c, &P);
+  const int npairs = c->nB * (c->nB + 1) / 2;
+  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+    if (c->famcount[f] == 0) continue;
+    const RombRom& R = c->roms[f];
+    const int K = R.n_r + 1;
+    const size_t smem = 8 * ((size_t)K * GW_PAIRS * 36 + GW_CELLS * 2 * c->nB + GW_CELLS * K + GW_CELLS * 144 +
+                             2 * GW_CELLS * 36);
+    ROMB_CUDA(cudaFuncSetAttribute(grad_wq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    grad_wq_kernel<<<(c->famcount[f] + GW_CELLS - 1) / GW_CELLS, 512, smem, c->stream>>>(
+        P, R.U64, R.n_half, K, c->d_famlist + c->famstart[f], c->famcount[f], c->d_pairs, npairs, c->d_theta,
+        c->d_chat, c->d_u, W, Q); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+    double nodes[16] = {0.0}, g1[12] = {0.0};
+    gll_nodes01(R.r, g1);
+    for (int i = 0; i <= R.r; ++i) nodes[i] = R.lo + (R.hi - R.lo) * g1[i];
+    double* nd = nodes_dev + 16 * f;
+    // pageable source: the call returns once `nodes` has been staged
+    ROMB_CUDA(cudaMemcpyAsync(nd, nodes, sizeof(nodes), cudaMemcpyHostToDevice, c->stream));
+    grad_mu_kernel<<<(c->famcount[f] + 7) / 8, 256, 0, c->stream>>>(
+        P, R.A, R.n_r, R.r, nd, R.lo, R.hi, c->d_famlist + c->famstart[f], c->famcount[f], c->d_mu, Q, d_dmu);
+    ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
+  grad_chain_kernel<<<(c->ncells + 127) / 128, 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, W, c->d_u,
+                                                                     c->d_traction, gloc); ++c->launches;
+  grad_gather_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, gloc, d_dctrl); ++c->launches;
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}

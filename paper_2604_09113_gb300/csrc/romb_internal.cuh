@@ -200,6 +200,8 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out);
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
 romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu);
+romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* nodes_dev, double* d_dctrl,
+                                double* d_dmu);
 romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
 romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxit, double* d_u_out,
