@@ -10,7 +10,10 @@
 //              children's update matrices (extend-add), in a fixed order;
 //   partial Cholesky of every front of the level, blocked by 32 columns:
 //              diagonal block (one CTA per front), panel solve, trailing update.
-// Solve: forward (leaves -> root) and backward (root -> leaves) substitution.
+//   The rows appended below each front (an identity block) take part in the
+//   elimination and end as B = [L11^-T | -(L21 L11^-1)^T].
+// Solve: forward (leaves -> root) and backward (root -> leaves) substitution,
+// one GEMV with B per front and sweep, one launch per level and sweep.
 #include <stdio.h>
 
 #include <algorithm>
@@ -22,6 +25,7 @@
 #include "tables.cuh"
 
 #define ND_NB 32
+#define ND_SMALL_N 128   // levels whose fronts all have n <= this use one warp per front
 
 namespace {
 
@@ -129,8 +133,10 @@ struct FrontDev {
   int cell_off, ncell;
   int emap_off;      // extend-add positions of this front's update rows in its parent
   int ybuf_off;      // forward-solve update vector (nb)
-  int wbuf_off;      // gathered right-hand side (n)
-  int sbuf_off;      // separator solution / backward right-hand side (ns)
+  int wbuf_off;      // extend-add sources of each of the n rows (gsrc)
+  int sbuf_off;      // forward result y_s = L11^-1 w_s (ns)
+  int ntiles;        // forward tiles of the front (tiled levels)
+  long long zoff;    // forward partial sums: [chunks][n]
 };
 
 }  // namespace
@@ -252,8 +258,9 @@ __global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __res
 }
 
 // Trailing update: A[i][j] -= sum_{t in [k0,k1)} A[i][t] A[j][t] for rows i >= k1,
-// columns k1 <= j < n with j <= i for front rows, j < ns for the rows below the
-// front (which accumulate L11^-T).  32 x 32 tiles, 256 threads (4 outputs each).
+// columns k1 <= j < n with j <= i for front rows and every j < n for the rows
+// below the front, which end as B = [L11^-T | -(L21 L11^-1)^T] (ns x n).
+// 32 x 32 tiles, 256 threads (4 outputs each).
 __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
                                                        double* __restrict__ F, int k0) {
   const FrontDev f = fr[level[blockIdx.y]];
@@ -268,7 +275,6 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   const int r0 = k1 + ti * 32, c0 = k1 + tj * 32;
   // skip tiles with no valid output
   if (r0 < n && c0 > r0 + 31) return;
-  if (r0 >= n && c0 >= f.ns) return;
   __shared__ double Pi[32][ND_NB + 1], Pj[32][ND_NB + 1];
   double* A = F + f.off;
   for (int t = threadIdx.x; t < 32 * ND_NB; t += blockDim.x) {
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = fma(a, Pj[lc0 + c][kk], acc[c]);
   }
-  const int jmax = gi < n ? gi : f.ns - 1;
+  const int jmax = gi < n ? gi : n - 1;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int gj = c0 + lc0 + c;
@@ -295,194 +301,183 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   }
 }
 
-// ---- solves: every step is a GEMV over the stored L21 and L11^-T ----
-struct NdItem {
-  int front, start;
+// ---- solves: one GEMV per front and sweep over B = [L11^-T | -M^T] ----
+//
+// With M = L21 L11^-1 (= A21 A11^-1) the forward step of a front,
+//   y_s = L11^-1 w_s,   u_b = w_b - M w_s,
+// is z = B^T w_s (y_s = z[0, ns), u_b = w_b + z[ns, n)), and the backward step,
+//   x_s = L11^-T (y_s - L21^T x_b) = L11^-T y_s - M^T x_b,
+// is x_s = B [y_s; x_b].  Both read the ns x n rows below the front once.
+// w is gathered from the right-hand side and the children's update vectors
+// through gsrc (up to two sources per row, in a fixed order).
+#define ND_RC 64   // rows (separator DoFs) per forward chunk
+#define ND_CT 64   // columns per forward tile
+
+struct NdTile {
+  int front, chunk, col0;
+};
+struct NdRows {
+  int front, row0;
 };
 
-// w = [rhs(separator rows); 0] + extend-add of the children's update vectors
-__global__ void nd_gather_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                                 const int* __restrict__ idx, const int* __restrict__ children,
-                                 const int* __restrict__ emap, const double* __restrict__ rhs,
-                                 const double* __restrict__ ybuf, double* __restrict__ wbuf) {
-  const FrontDev f = fr[level[blockIdx.x]];
-  const int n = f.ns + f.nb;
-  double* w = wbuf + f.wbuf_off;
-  const int* id = idx + f.idx_off;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] = t < f.ns ? rhs[id[t]] : 0.0;
-  __syncthreads();
-  for (int k = 0; k < f.nchild; ++k) {
-    const FrontDev ch = fr[children[f.child_off + k]];
-    const int* em = emap + ch.emap_off;
-    for (int t = threadIdx.x; t < ch.nb; t += blockDim.x) w[em[t]] += ybuf[ch.ybuf_off + t];
-    __syncthreads();
-  }
+__device__ inline double nd_gather_row(const int2 s, const double* __restrict__ ybuf) {
+  double v = 0.0;
+  if (s.x >= 0) v += ybuf[s.x];
+  if (s.y >= 0) v += ybuf[s.y];
+  return v;
 }
 
-// y_s = L11^-1 w_s = (L11^-T)^T w_s: a CTA owns 32 separator columns j, its 8
-// warps split the rows e (coalesced row reads), partial sums reduced in shared memory.
-__global__ void __launch_bounds__(1024) nd_fwd_y_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                                        const double* __restrict__ F, const int* __restrict__ idx,
-                                                        const double* __restrict__ wbuf, double* __restrict__ sbuf,
-                                                        double* __restrict__ x) {
-  __shared__ double part[32][33];
-  const NdItem it = items[blockIdx.x];
-  const FrontDev f = fr[it.front];
-  const int n = f.ns + f.nb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = it.start + lane;
-  const double* Y = F + f.off + (long long)n * n;   // row e: (L11^-T)[e][:], zero for e > j
-  const double* w = wbuf + f.wbuf_off;
-  double s = 0.0;
-  if (j < f.ns)
-    for (int e = warp; e <= j; e += 32) s = fma(Y[(long long)e * n + j], w[e], s);
-  part[warp][lane] = s;
-  __syncthreads();
-  if (warp == 0 && j < f.ns) {
-    double y = 0.0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) y += part[k][lane];
-    sbuf[f.sbuf_off + j] = y;
-    x[idx[f.idx_off + j]] = y;
-  }
-}
-
-// update vector u_b = w_b - L21 y_s: warp per boundary row
-__global__ void nd_fwd_upd_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                  const double* __restrict__ F, const double* __restrict__ wbuf,
-                                  const double* __restrict__ sbuf, double* __restrict__ ybuf) {
-  const NdItem it = items[blockIdx.x];
-  const FrontDev f = fr[it.front];
-  const int n = f.ns + f.nb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r = it.start + warp;
-  if (r >= f.nb) return;
-  const double* row = F + f.off + (long long)(f.ns + r) * n;
-  const double* y = sbuf + f.sbuf_off;
-  double s = 0.0;
-  for (int j = lane; j < f.ns; j += 32) s = fma(row[j], y[j], s);
-  s = warp_sum(s);
-  if (lane == 0) ybuf[f.ybuf_off + r] = wbuf[f.wbuf_off + f.ns + r] - s;
-}
-
-// t_s = y_s - L21^T x_b: a CTA owns 32 separator columns, 8 warps split the
-// boundary rows (x_b staged in shared memory).
-__global__ void __launch_bounds__(1024) nd_bwd_t_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                                        const double* __restrict__ F, const int* __restrict__ idx,
-                                                        const double* __restrict__ x, double* __restrict__ sbuf) {
-  extern __shared__ double xb[];
-  __shared__ double part[32][33];
-  const NdItem it = items[blockIdx.x];
-  const FrontDev f = fr[it.front];
-  const int n = f.ns + f.nb;
-  for (int r = threadIdx.x; r < f.nb; r += blockDim.x) xb[r] = x[idx[f.idx_off + f.ns + r]];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = it.start + lane;
-  const double* L21 = F + f.off + (long long)f.ns * n;
-  double s = 0.0;
-  if (j < f.ns)
-    for (int r = warp; r < f.nb; r += 32) s = fma(L21[(long long)r * n + j], xb[r], s);
-  part[warp][lane] = s;
-  __syncthreads();
-  if (warp == 0 && j < f.ns) {
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) t += part[k][lane];
-    sbuf[f.sbuf_off + j] -= t;
-  }
-}
-
-// Levels of small fronts: the whole forward step of a front in one warp
-// (gather, y_s = L11^-1 w_s, u_b = w_b - L21 y_s); 8 fronts per CTA.
+// Levels of small fronts: one warp per front (8 per CTA), lanes over columns.
 __global__ void __launch_bounds__(256) nd_fwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
                                                             int nfronts, const double* __restrict__ F,
-                                                            const int* __restrict__ idx, const int* __restrict__ children,
-                                                            const int* __restrict__ emap, const double* __restrict__ rhs,
-                                                            double* __restrict__ ybuf, double* __restrict__ x, int maxn) {
+                                                            const int* __restrict__ idx, const int2* __restrict__ gsrc,
+                                                            const double* __restrict__ rhs, double* __restrict__ ybuf,
+                                                            double* __restrict__ sbuf, int maxn) {
   extern __shared__ double sh[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int fi = blockIdx.x * 8 + warp;
   if (fi >= nfronts) return;
   const FrontDev f = fr[level[fi]];
-  const int n = f.ns + f.nb;
-  double* w = sh + (size_t)warp * 2 * maxn;
-  double* y = w + maxn;
+  const int ns = f.ns, n = ns + f.nb;
+  double* w = sh + (size_t)warp * maxn;
   const int* id = idx + f.idx_off;
-  for (int t = lane; t < n; t += 32) w[t] = t < f.ns ? rhs[id[t]] : 0.0;
+  const int2* gs = gsrc + f.wbuf_off;
+  for (int t = lane; t < n; t += 32) w[t] = (t < ns ? rhs[id[t]] : 0.0) + nd_gather_row(gs[t], ybuf);
   __syncwarp();
-  for (int k = 0; k < f.nchild; ++k) {
-    const FrontDev ch = fr[children[f.child_off + k]];
-    const int* em = emap + ch.emap_off;
-    for (int t = lane; t < ch.nb; t += 32) w[em[t]] += ybuf[ch.ybuf_off + t];
-    __syncwarp();
-  }
-  const double* A = F + f.off;
-  const double* Y = A + (long long)n * n;
-  for (int j = lane; j < f.ns; j += 32) {
-    double s = 0.0;
-    for (int e = 0; e <= j; ++e) s = fma(Y[(long long)e * n + j], w[e], s);
-    y[j] = s;
-    x[id[j]] = s;
-  }
-  __syncwarp();
-  for (int r = 0; r < f.nb; ++r) {
-    const double* row = A + (long long)(f.ns + r) * n;
-    double s = 0.0;
-    for (int j = lane; j < f.ns; j += 32) s = fma(row[j], y[j], s);
-    s = warp_sum(s);
-    if (lane == 0) ybuf[f.ybuf_off + r] = w[f.ns + r] - s;
+  const double* B = F + f.off + (long long)n * n;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int c = c0 + lane;
+    const int emax = c0 + 32 <= ns ? c0 + 32 : ns;   // rows e > c of L11^-T are zero
+    double z0 = 0.0, z1 = 0.0;
+    if (c < n) {
+      int e = 0;
+      for (; e + 1 < emax; e += 2) {
+        z0 = fma(B[(long long)e * n + c], w[e], z0);
+        z1 = fma(B[(long long)(e + 1) * n + c], w[e + 1], z1);
+      }
+      if (e < emax) z0 = fma(B[(long long)e * n + c], w[e], z0);
+      const double z = z0 + z1;
+      if (c < ns) sbuf[f.sbuf_off + c] = z;
+      else ybuf[f.ybuf_off + c - ns] = w[c] + z;
+    }
   }
 }
 
-// Levels of small fronts: the whole backward step of a front in one warp.
 __global__ void __launch_bounds__(256) nd_bwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
                                                             int nfronts, const double* __restrict__ F,
-                                                            const int* __restrict__ idx, double* __restrict__ x, int maxn) {
+                                                            const int* __restrict__ idx, const double* __restrict__ sbuf,
+                                                            double* __restrict__ x, int maxn) {
   extern __shared__ double sh[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int fi = blockIdx.x * 8 + warp;
   if (fi >= nfronts) return;
   const FrontDev f = fr[level[fi]];
-  const int n = f.ns + f.nb;
-  double* xb = sh + (size_t)warp * 2 * maxn;
-  double* t = xb + maxn;
+  const int ns = f.ns, n = ns + f.nb;
+  double* v = sh + (size_t)warp * (maxn + 32 * 33);
+  double* part = v + maxn;   // [32][33]
   const int* id = idx + f.idx_off;
-  for (int r = lane; r < f.nb; r += 32) xb[r] = x[id[f.ns + r]];
+  for (int c = lane; c < n; c += 32) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
   __syncwarp();
-  const double* A = F + f.off;
-  const double* L21 = A + (long long)f.ns * n;
-  for (int j = lane; j < f.ns; j += 32) {
-    double s = x[id[j]];   // y_s, stored by the forward pass
-    for (int r = 0; r < f.nb; ++r) s = fma(-L21[(long long)r * n + j], xb[r], s);
-    t[j] = s;
-  }
-  __syncwarp();
-  const double* Y = A + (long long)n * n;
-  for (int e = 0; e < f.ns; ++e) {
-    double s = 0.0;
-    for (int j = e + lane; j < f.ns; j += 32) s = fma(Y[(long long)e * n + j], t[j], s);
-    s = warp_sum(s);
-    if (lane == 0) x[id[e]] = s;
+  const double* B = F + f.off + (long long)n * n;
+  for (int g0 = 0; g0 < ns; g0 += 32) {
+    const int ge = min(32, ns - g0);
+    for (int k = 0; k < ge; ++k) {
+      const int e = g0 + k;
+      const double* row = B + (long long)e * n;
+      double s = 0.0;
+      for (int c = (e & ~31) + lane; c < n; c += 32) s = fma(row[c], v[c], s);
+      part[k * 33 + lane] = s;
+    }
+    __syncwarp();
+    if (lane < ge) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) s += part[lane * 33 + l];
+      x[id[g0 + lane]] = s;
+    }
+    __syncwarp();
   }
 }
 
-// x_s = L11^-T t_s: warp per separator row e
-__global__ void nd_bwd_x_kernel(const FrontDev* __restrict__ fr, const NdItem* __restrict__ items,
-                                const double* __restrict__ F, const int* __restrict__ idx,
-                                const double* __restrict__ sbuf, double* __restrict__ x) {
-  const NdItem it = items[blockIdx.x];
-  const FrontDev f = fr[it.front];
-  const int n = f.ns + f.nb;
+// Tiled forward step: a CTA owns ND_RC rows x ND_CT columns of one front's B
+// and writes its partial z; the last CTA of the front (counted with an
+// atomic after a fence) sums the partials in chunk order and writes y_s and u_b.
+__global__ void __launch_bounds__(256) nd_fwd_tile_kernel(const FrontDev* __restrict__ fr, const NdTile* __restrict__ tiles,
+                                                           const double* __restrict__ F, const int* __restrict__ idx,
+                                                           const int2* __restrict__ gsrc, const double* __restrict__ rhs,
+                                                           double* __restrict__ ybuf, double* __restrict__ sbuf,
+                                                           double* __restrict__ zpart, int* __restrict__ counter) {
+  __shared__ double ws[ND_RC];
+  __shared__ double red[8][ND_CT + 1];
+  __shared__ int is_last;
+  const NdTile T = tiles[blockIdx.x];
+  const FrontDev f = fr[T.front];
+  const int ns = f.ns, n = ns + f.nb;
+  const int e0 = T.chunk * ND_RC, ne = max(0, min(ND_RC, ns - e0));
+  const int* id = idx + f.idx_off;
+  const int2* gs = gsrc + f.wbuf_off;
+  for (int t = threadIdx.x; t < ne; t += blockDim.x) ws[t] = rhs[id[e0 + t]] + nd_gather_row(gs[e0 + t], ybuf);
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = it.start + warp;
-  if (e >= f.ns) return;
-  const double* Y = F + f.off + (long long)(n + e) * n;
-  const double* t = sbuf + f.sbuf_off;
-  double s = 0.0;
-  for (int j = e + lane; j < f.ns; j += 32) s = fma(Y[j], t[j], s);
-  s = warp_sum(s);
-  if (lane == 0) x[idx[f.idx_off + e]] = s;
+  const double* B = F + f.off + (long long)n * n + (long long)e0 * n;
+  const int ca = T.col0 + lane, cb = T.col0 + 32 + lane;
+  double za = 0.0, zb = 0.0;
+  for (int t = warp; t < ne; t += 8) {
+    const double wv = ws[t];
+    const double* row = B + (long long)t * n;
+    if (ca < n) za = fma(row[ca], wv, za);
+    if (cb < n) zb = fma(row[cb], wv, zb);
+  }
+  red[warp][lane] = za;
+  red[warp][32 + lane] = zb;
+  __syncthreads();
+  if (threadIdx.x < ND_CT) {
+    const int c = T.col0 + threadIdx.x;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+    if (c < n) zpart[f.zoff + (long long)T.chunk * n + c] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counter + T.front, 1) == f.ntiles - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int nch = max(1, (ns + ND_RC - 1) / ND_RC);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double z = 0.0;
+    for (int k = 0; k < nch; ++k) z += __ldcg(zpart + f.zoff + (long long)k * n + c);
+    if (c < ns) sbuf[f.sbuf_off + c] = z;
+    else ybuf[f.ybuf_off + c - ns] = nd_gather_row(gs[c], ybuf) + z;
+  }
+}
+
+// Tiled backward step: a CTA owns 8 rows e of one front's B, a warp per row.
+__global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
+                                                           const double* __restrict__ F, const int* __restrict__ idx,
+                                                           const double* __restrict__ sbuf, double* __restrict__ x) {
+  extern __shared__ double v[];   // [n]: y_s then x_b
+  const NdRows it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
+  const int ns = f.ns, n = ns + f.nb;
+  const int* id = idx + f.idx_off;
+  const int cstart = it.row0 & ~31;
+  for (int c = cstart + threadIdx.x; c < n; c += blockDim.x) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = it.row0 + warp;
+  if (e >= ns) return;
+  const double* row = F + f.off + (long long)(n + e) * n;
+  double s0 = 0.0, s1 = 0.0;
+  int c = (e & ~31) + lane;
+  for (; c + 32 < n; c += 64) {
+    s0 = fma(row[c], v[c], s0);
+    s1 = fma(row[c + 32], v[c + 32], s1);
+  }
+  if (c < n) s0 = fma(row[c], v[c], s0);
+  const double s = warp_sum(s0 + s1);
+  if (lane == 0) x[id[e]] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -490,10 +485,14 @@ __global__ void nd_bwd_x_kernel(const FrontDev* __restrict__ fr, const NdItem* _
 // ---------------------------------------------------------------------------
 struct NdDevice {
   FrontDev* fr = nullptr;
-  double* wbuf = nullptr;
+  int2* gsrc = nullptr;
   double* sbuf = nullptr;
-  std::vector<NdItem*> col_items, brow_items, srow_items;
-  std::vector<int> col_n, brow_n, srow_n, level_maxnb;
+  double* zpart = nullptr;
+  int* counter = nullptr;
+  int nfronts = 0;
+  std::vector<NdTile*> fwd_tiles;
+  std::vector<NdRows*> bwd_rows;
+  std::vector<int> fwd_n, bwd_n;
   int* idx = nullptr;
   int* children = nullptr;
   int* emap = nullptr;
@@ -531,7 +530,7 @@ romb_status coarse_build(romb_ctx* c) {
   // host arrays
   std::vector<FrontDev> fd(nf);
   std::vector<int> idx, children, emap, cells, cell_pos((size_t)c->ncells * 20, -1);
-  long long off = 0;
+  long long off = 0, ztot = 0;
   int ybuf = 0, wbuf_tot = 0, sbuf_tot = 0;
   for (int i = 0; i < nf; ++i) {
     const NdFront& F = plan.fronts[i];
@@ -556,6 +555,9 @@ romb_status coarse_build(romb_ctx* c) {
     d.sbuf_off = sbuf_tot;
     sbuf_tot += F.ns;
     d.emap_off = -1;
+    d.zoff = ztot;
+    ztot += (long long)std::max(1, (F.ns + ND_RC - 1) / ND_RC) * n;
+    d.ntiles = 0;
   }
   // extend-add positions of each front's update rows in its parent
   for (int i = 0; i < nf; ++i) {
@@ -572,6 +574,23 @@ romb_status coarse_build(romb_ctx* c) {
         return ROMB_E_CUDA;
       }
       emap.push_back(it->second);
+    }
+  }
+  // extend-add sources of every front row: the children's update-vector entries
+  std::vector<int2> gsrc((size_t)std::max(1, wbuf_tot), make_int2(-1, -1));
+  for (int i = 0; i < nf; ++i) {
+    const NdFront& F = plan.fronts[i];
+    if (F.parent < 0) continue;
+    const FrontDev& pd = fd[F.parent];
+    for (int a = 0; a < F.nb; ++a) {
+      int2& s = gsrc[(size_t)pd.wbuf_off + emap[fd[i].emap_off + a]];
+      const int src = fd[i].ybuf_off + a;
+      if (s.x < 0) s.x = src;
+      else if (s.y < 0) s.y = src;
+      else {
+        romb_set_error("nested dissection: more than two update sources for a front row");
+        return ROMB_E_CUDA;
+      }
     }
   }
   // cell -> leaf-front row of each local coarse slot
@@ -608,10 +627,17 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.cell_pos, cell_pos.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.F, (size_t)off)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.ybuf, std::max(1, ybuf))) != ROMB_OK) return s;
-  if ((s = romb_alloc_t(c, &D.wbuf, std::max(1, wbuf_tot))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.gsrc, gsrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.zpart, (size_t)std::max(1LL, ztot))) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.counter, nf)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
+  D.nfronts = nf;
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 8 * 8 * (ND_SMALL_N + 32 * 33)));
+  ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
+  // partial sums of skipped (zero) tiles are never written: they stay 0
+  ROMB_CUDA(cudaMemset(D.zpart, 0, 8 * (size_t)std::max(1LL, ztot)));
   ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
   if (!children.empty())
     ROMB_CUDA(cudaMemcpy(D.children, children.data(), 4 * children.size(), cudaMemcpyHostToDevice));
@@ -631,35 +657,39 @@ romb_status coarse_build(romb_ctx* c) {
     }
     D.level_maxns.push_back(mns);
     D.level_maxn.push_back(mn);
-    // work lists of the solve kernels
-    std::vector<NdItem> ci, bi, si;
-    int mnb = 0;
+    // work lists of the tiled solve kernels
+    std::vector<NdTile> ft;
+    std::vector<NdRows> br;
     for (int f : lv) {
       const NdFront& Fr = plan.fronts[f];
-      mnb = std::max(mnb, Fr.nb);
-      for (int j = 0; j < Fr.ns; j += 32) ci.push_back({f, j});
-      for (int r = 0; r < Fr.nb; r += 8) bi.push_back({f, r});
-      for (int e = 0; e < Fr.ns; e += 8) si.push_back({f, e});
+      const int n = Fr.ns + Fr.nb, nch = std::max(1, (Fr.ns + ND_RC - 1) / ND_RC);
+      int cnt = 0;
+      for (int k = 0; k < nch; ++k)
+        for (int c0 = 0; c0 < n; c0 += ND_CT) {
+          if (c0 + ND_CT <= k * ND_RC) continue;   // below the diagonal of L11^-T: zero
+          ft.push_back({f, k, c0});
+          ++cnt;
+        }
+      fd[f].ntiles = cnt;
+      for (int e = 0; e < Fr.ns; e += 8) br.push_back({f, e});
     }
-    D.level_maxnb.push_back(mnb);
-    for (auto* pr : {&ci, &bi, &si}) {
-      NdItem* dptr = nullptr;
-      if (!pr->empty()) {
-        if ((s = romb_alloc_t(c, &dptr, pr->size())) != ROMB_OK) return s;
-        ROMB_CUDA(cudaMemcpy(dptr, pr->data(), sizeof(NdItem) * pr->size(), cudaMemcpyHostToDevice));
-      }
-      if (pr == &ci) {
-        D.col_items.push_back(dptr);
-        D.col_n.push_back((int)pr->size());
-      } else if (pr == &bi) {
-        D.brow_items.push_back(dptr);
-        D.brow_n.push_back((int)pr->size());
-      } else {
-        D.srow_items.push_back(dptr);
-        D.srow_n.push_back((int)pr->size());
-      }
+    NdTile* dt = nullptr;
+    NdRows* dr = nullptr;
+    if (!ft.empty()) {
+      if ((s = romb_alloc_t(c, &dt, ft.size())) != ROMB_OK) return s;
+      ROMB_CUDA(cudaMemcpy(dt, ft.data(), sizeof(NdTile) * ft.size(), cudaMemcpyHostToDevice));
     }
+    if (!br.empty()) {
+      if ((s = romb_alloc_t(c, &dr, br.size())) != ROMB_OK) return s;
+      ROMB_CUDA(cudaMemcpy(dr, br.data(), sizeof(NdRows) * br.size(), cudaMemcpyHostToDevice));
+    }
+    D.fwd_tiles.push_back(dt);
+    D.fwd_n.push_back((int)ft.size());
+    D.bwd_rows.push_back(dr);
+    D.bwd_n.push_back((int)br.size());
   }
+  // front descriptors last: they carry the tile counts
+  ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
   return ROMB_OK;
 }
 
@@ -695,41 +725,32 @@ romb_status coarse_factor(romb_ctx* c) {
 // out = S_C^-1 in over the non-Dirichlet coarse DoFs (Dirichlet entries of out are 0).
 // Levels whose fronts are all small use one warp per front; the few levels of
 // large fronts spread each GEMV over many CTAs.
-#define ND_SMALL_N 128
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
+  ROMB_CUDA(cudaMemsetAsync(D.counter, 0, 4 * (size_t)D.nfronts, c->stream));
   const int L = (int)D.level_ids.size();
   for (int l = 0; l < L; ++l) {
     if (D.level_maxn[l] <= ND_SMALL_N) {
-      const size_t sm = 8 * 2 * (size_t)D.level_maxn[l] * 8;
+      const size_t sm = 8 * 8 * (size_t)D.level_maxn[l];
       nd_fwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
-          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.children, D.emap, d_in, D.ybuf, d_out,
-          D.level_maxn[l]); ++c->launches;
-      continue;
+          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.gsrc, d_in, D.ybuf, D.sbuf, D.level_maxn[l]);
+      ++c->launches;
+    } else if (D.fwd_n[l]) {
+      nd_fwd_tile_kernel<<<D.fwd_n[l], 256, 0, c->stream>>>(D.fr, D.fwd_tiles[l], D.F, D.idx, D.gsrc, d_in, D.ybuf,
+                                                            D.sbuf, D.zpart, D.counter); ++c->launches;
     }
-    nd_gather_kernel<<<D.level_count[l], 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.idx, D.children, D.emap,
-                                                              d_in, D.ybuf, D.wbuf); ++c->launches;
-    if (D.col_n[l])
-      nd_fwd_y_kernel<<<D.col_n[l], 1024, 0, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, D.wbuf, D.sbuf,
-                                                          d_out); ++c->launches;
-    if (D.brow_n[l])
-      nd_fwd_upd_kernel<<<D.brow_n[l], 256, 0, c->stream>>>(D.fr, D.brow_items[l], D.F, D.wbuf, D.sbuf,
-                                                            D.ybuf); ++c->launches;
   }
   for (int l = L - 1; l >= 0; --l) {
     if (D.level_maxn[l] <= ND_SMALL_N) {
-      const size_t sm = 8 * 2 * (size_t)D.level_maxn[l] * 8;
+      const size_t sm = 8 * 8 * ((size_t)D.level_maxn[l] + 32 * 33);
       nd_bwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
-          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, d_out, D.level_maxn[l]); ++c->launches;
-      continue;
+          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.sbuf, d_out, D.level_maxn[l]); ++c->launches;
+    } else if (D.bwd_n[l]) {
+      const size_t sm = 8 * (size_t)D.level_maxn[l];
+      nd_bwd_rows_kernel<<<D.bwd_n[l], 256, sm, c->stream>>>(D.fr, D.bwd_rows[l], D.F, D.idx, D.sbuf, d_out);
+      ++c->launches;
     }
-    if (D.col_n[l]) {
-      const size_t sm = 8 * (size_t)std::max(1, D.level_maxnb[l]);
-      nd_bwd_t_kernel<<<D.col_n[l], 1024, sm, c->stream>>>(D.fr, D.col_items[l], D.F, D.idx, d_out, D.sbuf); ++c->launches;
-    }
-    if (D.srow_n[l])
-      nd_bwd_x_kernel<<<D.srow_n[l], 256, 0, c->stream>>>(D.fr, D.srow_items[l], D.F, D.idx, D.sbuf, d_out); ++c->launches;
   }
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
