@@ -31,6 +31,7 @@
 
 #include <string>
 
+#include "bulk.cuh"
 #include "device.cuh"
 #include "tables.cuh"
 
@@ -38,7 +39,6 @@
 #define TC_N 144
 #define TC_PAIRS 4
 #define TC_THREADS 384
-#define TC_WAIT_CYCLES (4000000000LL)   // ~2 s at 2 GHz
 
 struct TcFamily {
   const float* Utiles;     // per tile: hi, lo [TC_N x KT] (canonical layout), then rows 0, 1 as float pairs [2][TC_N][2]
@@ -61,47 +61,6 @@ struct TcParams {
   int stages;
   int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (abort_flag && *abort_flag) return false;
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
-  }
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout of
 // 8-row x 16-byte core matrices; LBO = core-matrix stride along K, SBO = stride

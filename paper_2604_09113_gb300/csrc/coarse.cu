@@ -21,11 +21,13 @@
 #include <unordered_map>
 #include <vector>
 
+#include "bulk.cuh"
 #include "device.cuh"
 #include "tables.cuh"
 
 #define ND_NB 32
-#define ND_SMALL_N 128   // levels whose fronts all have n <= this use one warp per front
+#define ND_SMALL_N 256       // levels whose fronts all have n <= this use one warp per front,
+#define ND_SMALL_SMEM 6144   // ... if B and one vector of the largest fit in this many doubles
 
 namespace {
 
@@ -327,35 +329,76 @@ __device__ inline double nd_gather_row(const int2 s, const double* __restrict__ 
   return v;
 }
 
-// Levels of small fronts: one warp per front (8 per CTA), lanes over columns.
-__global__ void __launch_bounds__(256) nd_fwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                                                            int nfronts, const double* __restrict__ F,
-                                                            const int* __restrict__ idx, const int2* __restrict__ gsrc,
-                                                            const double* __restrict__ rhs, double* __restrict__ ybuf,
-                                                            double* __restrict__ sbuf, int maxn) {
-  extern __shared__ double sh[];
+// Every solve kernel first stages its part of B (static between solves) into
+// shared memory with bulk copies, then waits for the previous kernel
+// (programmatic dependent launch: the copies and the launch overlap the
+// previous level's tail), gathers what that level produced and finally waits
+// (bounded) for its copies.  GB300 issues an FP64 warp instruction every 16 SM
+// cycles, so the loops have exact, warp-uniform trip counts.  A copy that does
+// not arrive in time sets *err and the CTA skips its work.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+#define ND_WPC 4     // warps (fronts) per CTA in the small-front kernels
+#define ND_SROW 66   // shared row stride of a staged forward tile (64 + alignment slack, even)
+
+// Small fronts: one warp per front.  Shared memory per warp: `stride`
+// doubles = the B block (ns x n, contiguous in the front, staged by one bulk
+// copy) at offset 0 and a vector of n at offset `voff`.
+__device__ __forceinline__ bool nd_stage_block(const FrontDev& f, const double* __restrict__ F, double* region,
+                                               uint64_t* bar, int lane, int* first) {
+  const int n = f.ns + f.nb;
+  const Span16 sp = span16(F + f.off + (long long)n * n, (long long)f.ns * n);
+  *first = sp.first;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    mbar_expect_tx(bar, sp.bytes);
+    if (sp.bytes) bulk_g2s(region, sp.start, sp.bytes, bar);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
+    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
+    const int* __restrict__ idx, const int2* __restrict__ gsrc, const double* __restrict__ rhs,
+    double* __restrict__ ybuf, double* __restrict__ sbuf, int stride, int voff, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sh[];
+  __shared__ uint64_t bar[ND_WPC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int fi = blockIdx.x * 8 + warp;
-  if (fi >= nfronts) return;
-  const FrontDev f = fr[level[fi]];
+  const int fi = blockIdx.x * ND_WPC + warp;
+  const bool has = fi < nfronts;
+  const FrontDev f = fr[level[has ? fi : 0]];
   const int ns = f.ns, n = ns + f.nb;
-  double* w = sh + (size_t)warp * maxn;
+  double* region = sh + (size_t)warp * stride;
+  double* w = region + voff;
+  int first = 0;
+  if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
+  __syncwarp();   // the barrier is initialised before any lane waits on it
+  pdl_trigger();
+  pdl_wait();
+  if (!has) return;
   const int* id = idx + f.idx_off;
   const int2* gs = gsrc + f.wbuf_off;
   for (int t = lane; t < n; t += 32) w[t] = (t < ns ? rhs[id[t]] : 0.0) + nd_gather_row(gs[t], ybuf);
+  const bool ok = mbar_wait(&bar[warp], 0);
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
   __syncwarp();
-  const double* B = F + f.off + (long long)n * n;
+  const double* Bs = region + first;
   for (int c0 = 0; c0 < n; c0 += 32) {
     const int c = c0 + lane;
-    const int emax = c0 + 32 <= ns ? c0 + 32 : ns;   // rows e > c of L11^-T are zero
-    double z0 = 0.0, z1 = 0.0;
+    const int emax = min(ns, c0 + 32);   // rows e > c of L11^-T are zero
     if (c < n) {
+      double z0 = 0.0, z1 = 0.0;
       int e = 0;
       for (; e + 1 < emax; e += 2) {
-        z0 = fma(B[(long long)e * n + c], w[e], z0);
-        z1 = fma(B[(long long)(e + 1) * n + c], w[e + 1], z1);
+        z0 = fma(Bs[e * n + c], w[e], z0);
+        z1 = fma(Bs[(e + 1) * n + c], w[e + 1], z1);
       }
-      if (e < emax) z0 = fma(B[(long long)e * n + c], w[e], z0);
+      if (e < emax) z0 = fma(Bs[e * n + c], w[e], z0);
       const double z = z0 + z1;
       if (c < ns) sbuf[f.sbuf_off + c] = z;
       else ybuf[f.ybuf_off + c - ns] = w[c] + z;
@@ -363,121 +406,209 @@ __global__ void __launch_bounds__(256) nd_fwd_small_kernel(const FrontDev* __res
   }
 }
 
-__global__ void __launch_bounds__(256) nd_bwd_small_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                                                            int nfronts, const double* __restrict__ F,
-                                                            const int* __restrict__ idx, const double* __restrict__ sbuf,
-                                                            double* __restrict__ x, int maxn) {
-  extern __shared__ double sh[];
+// x_s = B [y_s; x_b]: lanes = (row r, column phase h) with R rows x P phases,
+// R the smallest power of two >= min(ns, 32); phases combined by shuffles.
+__global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
+    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
+    const int* __restrict__ idx, const double* __restrict__ sbuf, double* __restrict__ x, int stride, int voff,
+    int* __restrict__ err) {
+  extern __shared__ __align__(16) double sh[];
+  __shared__ uint64_t bar[ND_WPC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int fi = blockIdx.x * 8 + warp;
-  if (fi >= nfronts) return;
-  const FrontDev f = fr[level[fi]];
+  const int fi = blockIdx.x * ND_WPC + warp;
+  const bool has = fi < nfronts;
+  const FrontDev f = fr[level[has ? fi : 0]];
   const int ns = f.ns, n = ns + f.nb;
-  double* v = sh + (size_t)warp * (maxn + 32 * 33);
-  double* part = v + maxn;   // [32][33]
+  double* region = sh + (size_t)warp * stride;
+  double* v = region + voff;
+  int first = 0;
+  if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
+  __syncwarp();   // the barrier is initialised before any lane waits on it
+  pdl_trigger();
+  pdl_wait();
+  if (!has) return;
   const int* id = idx + f.idx_off;
   for (int c = lane; c < n; c += 32) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
+  const bool ok = mbar_wait(&bar[warp], 0);
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
   __syncwarp();
-  const double* B = F + f.off + (long long)n * n;
-  for (int g0 = 0; g0 < ns; g0 += 32) {
-    const int ge = min(32, ns - g0);
-    for (int k = 0; k < ge; ++k) {
-      const int e = g0 + k;
-      const double* row = B + (long long)e * n;
-      double s = 0.0;
-      for (int c = (e & ~31) + lane; c < n; c += 32) s = fma(row[c], v[c], s);
-      part[k * 33 + lane] = s;
+  const double* Bs = region + first;
+  int R = 1;
+  while (R < ns && R < 32) R <<= 1;
+  const int P = 32 / R, r = lane & (R - 1), h = lane / R;
+  for (int e0 = 0; e0 < ns; e0 += R) {
+    const int e = e0 + r;
+    double s = 0.0;
+    if (e < ns) {
+      const double* row = Bs + e * n;
+      for (int c = (e0 / P) * P + h; c < n; c += P) s = fma(row[c], v[c], s);
     }
-    __syncwarp();
-    if (lane < ge) {
-      double s = 0.0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) s += part[lane * 33 + l];
-      x[id[g0 + lane]] = s;
-    }
-    __syncwarp();
+    for (int o = R; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (h == 0 && e < ns) x[id[e]] = s;
   }
 }
 
-// Tiled forward step: a CTA owns ND_RC rows x ND_CT columns of one front's B
-// and writes its partial z; the last CTA of the front (counted with an
-// atomic after a fence) sums the partials in chunk order and writes y_s and u_b.
+// Tiled forward step: a CTA owns ND_RC rows x ND_CT columns of one front's B,
+// staged row by row (one bulk copy per row, issued by warp 0); thread =
+// column x row group (rows rg, rg+4, ...).  Fronts with one row chunk write y_s
+// and u_b directly; otherwise every CTA writes its partial z and the last CTA
+// of the front (counted with an atomic after a fence) sums the partials in
+// chunk order.
 __global__ void __launch_bounds__(256) nd_fwd_tile_kernel(const FrontDev* __restrict__ fr, const NdTile* __restrict__ tiles,
                                                            const double* __restrict__ F, const int* __restrict__ idx,
                                                            const int2* __restrict__ gsrc, const double* __restrict__ rhs,
                                                            double* __restrict__ ybuf, double* __restrict__ sbuf,
-                                                           double* __restrict__ zpart, int* __restrict__ counter) {
+                                                           double* __restrict__ zpart, int* __restrict__ counter,
+                                                           int* __restrict__ err) {
+  __shared__ __align__(16) double S[ND_RC * ND_SROW];
   __shared__ double ws[ND_RC];
-  __shared__ double red[8][ND_CT + 1];
+  __shared__ double red[4][ND_CT + 1];
+  __shared__ int first[ND_RC];
+  __shared__ uint64_t bar;
   __shared__ int is_last;
   const NdTile T = tiles[blockIdx.x];
   const FrontDev f = fr[T.front];
   const int ns = f.ns, n = ns + f.nb;
   const int e0 = T.chunk * ND_RC, ne = max(0, min(ND_RC, ns - e0));
+  const int nc = min(ND_CT, n - T.col0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    const double* B = F + f.off + (long long)(n + e0) * n + T.col0;
+    Span16 sp[2];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int r = lane + 32 * k;
+      sp[k] = span16(B + (long long)r * n, r < ne ? nc : 0);
+      mine += sp[k].bytes;
+      if (r < ne) first[r] = sp[k].first;
+    }
+    const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+      mbar_expect_tx(&bar, total);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (sp[k].bytes) bulk_g2s(S + (lane + 32 * k) * ND_SROW, sp[k].start, sp[k].bytes, &bar);
+  }
+  pdl_trigger();
+  pdl_wait();
+  const int col = threadIdx.x & (ND_CT - 1), rg = threadIdx.x / ND_CT;
+  const int c = T.col0 + col;
   const int* id = idx + f.idx_off;
   const int2* gs = gsrc + f.wbuf_off;
-  for (int t = threadIdx.x; t < ne; t += blockDim.x) ws[t] = rhs[id[e0 + t]] + nd_gather_row(gs[e0 + t], ybuf);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double* B = F + f.off + (long long)n * n + (long long)e0 * n;
-  const int ca = T.col0 + lane, cb = T.col0 + 32 + lane;
-  double za = 0.0, zb = 0.0;
-  for (int t = warp; t < ne; t += 8) {
-    const double wv = ws[t];
-    const double* row = B + (long long)t * n;
-    if (ca < n) za = fma(row[ca], wv, za);
-    if (cb < n) zb = fma(row[cb], wv, zb);
+  const int nch = max(1, (ns + ND_RC - 1) / ND_RC);
+  double wc = 0.0;   // w at this column's update row (single-chunk fronts)
+  if (nch == 1 && rg == 0 && c >= ns && c < n) wc = nd_gather_row(gs[c], ybuf);
+  for (int r = threadIdx.x; r < ne; r += blockDim.x) ws[r] = rhs[id[e0 + r]] + nd_gather_row(gs[e0 + r], ybuf);
+  __syncthreads();   // bar initialised, first[] and ws written
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
   }
-  red[warp][lane] = za;
-  red[warp][32 + lane] = zb;
-  __syncthreads();
-  if (threadIdx.x < ND_CT) {
-    const int c = T.col0 + threadIdx.x;
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
-    if (c < n) zpart[f.zoff + (long long)T.chunk * n + c] = s;
+  double z0 = 0.0, z1 = 0.0;
+  int r = rg;
+  for (; r + 4 < ne; r += 8) {
+    z0 = fma(S[r * ND_SROW + first[r] + col], ws[r], z0);
+    z1 = fma(S[(r + 4) * ND_SROW + first[r + 4] + col], ws[r + 4], z1);
   }
+  if (r < ne) z0 = fma(S[r * ND_SROW + first[r] + col], ws[r], z0);
+  red[rg][col] = z0 + z1;
+  __syncthreads();
+  double z = 0.0;
+  if (rg == 0) z = (red[0][col] + red[1][col]) + (red[2][col] + red[3][col]);
+  if (nch == 1) {
+    if (rg == 0 && c < n) {
+      if (c < ns) sbuf[f.sbuf_off + c] = z;
+      else ybuf[f.ybuf_off + c - ns] = wc + z;
+    }
+    return;
+  }
+  if (rg == 0 && c < n) zpart[f.zoff + (long long)T.chunk * n + c] = z;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = atomicAdd(counter + T.front, 1) == f.ntiles - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int nch = max(1, (ns + ND_RC - 1) / ND_RC);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double z = 0.0;
-    for (int k = 0; k < nch; ++k) z += __ldcg(zpart + f.zoff + (long long)k * n + c);
-    if (c < ns) sbuf[f.sbuf_off + c] = z;
-    else ybuf[f.ybuf_off + c - ns] = nd_gather_row(gs[c], ybuf) + z;
+  for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nch; ++k) s += __ldcg(zpart + f.zoff + (long long)k * n + cc);
+    if (cc < ns) sbuf[f.sbuf_off + cc] = s;
+    else ybuf[f.ybuf_off + cc - ns] = nd_gather_row(gs[cc], ybuf) + s;
   }
 }
 
-// Tiled backward step: a CTA owns 8 rows e of one front's B, a warp per row.
+// Tiled backward step: a CTA owns rb rows of one front's B (rb = 1, 2, 4 or 8;
+// 8 / rb warps per row, lanes over columns), staged by one bulk copy per row
+// into rows of `rstride` doubles; the columns left of the block's first row
+// are zero in L11^-T and skipped.
 __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
                                                            const double* __restrict__ F, const int* __restrict__ idx,
-                                                           const double* __restrict__ sbuf, double* __restrict__ x) {
-  extern __shared__ double v[];   // [n]: y_s then x_b
+                                                           const double* __restrict__ sbuf, double* __restrict__ x,
+                                                           int rb, int rstride, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sh[];   // [rb][rstride] rows, then v [n]
+  __shared__ double red[8];
+  __shared__ int first[8];
+  __shared__ uint64_t bar;
   const NdRows it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int ns = f.ns, n = ns + f.nb;
-  const int* id = idx + f.idx_off;
-  const int cstart = it.row0 & ~31;
-  for (int c = cstart + threadIdx.x; c < n; c += blockDim.x) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = it.row0 + warp;
-  if (e >= ns) return;
-  const double* row = F + f.off + (long long)(n + e) * n;
-  double s0 = 0.0, s1 = 0.0;
-  int c = (e & ~31) + lane;
-  for (; c + 32 < n; c += 64) {
-    s0 = fma(row[c], v[c], s0);
-    s1 = fma(row[c + 32], v[c + 32], s1);
+  const int cs = it.row0 & ~31;
+  double* v = sh + (size_t)rb * rstride;
+  if (warp == 0) {
+    const int e = it.row0 + lane;
+    const bool mine_row = lane < rb && e < ns;
+    const Span16 sp = span16(F + f.off + (long long)(n + (mine_row ? e : 0)) * n + cs, mine_row ? n - cs : 0);
+    if (lane < rb) first[lane] = sp.first;
+    const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
+    if (lane == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+      mbar_expect_tx(&bar, total);
+    }
+    __syncwarp();
+    if (sp.bytes) bulk_g2s(sh + (size_t)lane * rstride, sp.start, sp.bytes, &bar);
   }
-  if (c < n) s0 = fma(row[c], v[c], s0);
+  pdl_trigger();
+  pdl_wait();
+  const int* id = idx + f.idx_off;
+  for (int c = cs + threadIdx.x; c < n; c += blockDim.x) v[c - cs] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  const int wpr = 8 / rb, j = warp / wpr, k = warp % wpr;
+  const int e = it.row0 + j;
+  double s0 = 0.0, s1 = 0.0;
+  if (e < ns) {
+    const double* row = sh + (size_t)j * rstride + first[j];
+    const int w = n - cs, step = 32 * wpr;
+    int cc = 32 * k + lane;
+    for (; cc + step < w; cc += 2 * step) {
+      s0 = fma(row[cc], v[cc], s0);
+      s1 = fma(row[cc + step], v[cc + step], s1);
+    }
+    if (cc < w) s0 = fma(row[cc], v[cc], s0);
+  }
   const double s = warp_sum(s0 + s1);
-  if (lane == 0) x[id[e]] = s;
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x < rb && it.row0 + threadIdx.x < ns) {
+    double t = 0.0;
+    for (int q = 0; q < wpr; ++q) t += red[threadIdx.x * wpr + q];
+    x[id[it.row0 + threadIdx.x]] = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -492,7 +623,7 @@ struct NdDevice {
   int nfronts = 0;
   std::vector<NdTile*> fwd_tiles;
   std::vector<NdRows*> bwd_rows;
-  std::vector<int> fwd_n, bwd_n;
+  std::vector<int> fwd_n, bwd_n, bwd_rpw, level_small, level_maxb;
   int* idx = nullptr;
   int* children = nullptr;
   int* emap = nullptr;
@@ -503,6 +634,7 @@ struct NdDevice {
   std::vector<int*> level_ids;
   std::vector<int> level_count, level_maxns, level_maxn, level_maxtiles_trsm, level_maxtiles_syrk;
   int32_t* bad = nullptr;
+  int* err = nullptr;   // set by a solve kernel whose staging copy timed out
 };
 
 static std::unordered_map<const romb_ctx*, NdDevice> g_nd;
@@ -625,16 +757,17 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.emap, std::max<size_t>(1, emap.size()))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.cells, std::max<size_t>(1, cells.size()))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.cell_pos, cell_pos.size())) != ROMB_OK) return s;
-  if ((s = romb_alloc_t(c, &D.F, (size_t)off)) != ROMB_OK) return s;
+  // +2 doubles: bulk copies read 16-byte aligned spans that may pass the end
+  if ((s = romb_alloc_t(c, &D.F, (size_t)off + 2)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.ybuf, std::max(1, ybuf))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.gsrc, gsrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.zpart, (size_t)std::max(1LL, ztot))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.counter, nf)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.err, 1)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemset(D.err, 0, 4));
   D.nfronts = nf;
-  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 8 * 8 * (ND_SMALL_N + 32 * 33)));
   ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
   // partial sums of skipped (zero) tiles are never written: they stay 0
   ROMB_CUDA(cudaMemset(D.zpart, 0, 8 * (size_t)std::max(1LL, ztot)));
@@ -657,6 +790,14 @@ romb_status coarse_build(romb_ctx* c) {
     }
     D.level_maxns.push_back(mns);
     D.level_maxn.push_back(mn);
+    int mb = 0;
+    for (int f : lv) mb = std::max(mb, plan.fronts[f].ns * (plan.fronts[f].ns + plan.fronts[f].nb));
+    D.level_maxb.push_back(mb);
+    D.level_small.push_back(mn <= ND_SMALL_N && mb + mn + 8 <= ND_SMALL_SMEM);
+    // backward rows per CTA: as many (<= 8) as keep the staged rows within 96 KB
+    int rpw = 8;
+    while (rpw > 1 && (size_t)rpw * (mn + 2) * 8 > 96 * 1024) rpw >>= 1;
+    D.bwd_rpw.push_back(rpw);
     // work lists of the tiled solve kernels
     std::vector<NdTile> ft;
     std::vector<NdRows> br;
@@ -671,7 +812,7 @@ romb_status coarse_build(romb_ctx* c) {
           ++cnt;
         }
       fd[f].ntiles = cnt;
-      for (int e = 0; e < Fr.ns; e += 8) br.push_back({f, e});
+      for (int e = 0; e < Fr.ns; e += rpw) br.push_back({f, e});
     }
     NdTile* dt = nullptr;
     NdRows* dr = nullptr;
@@ -690,6 +831,19 @@ romb_status coarse_build(romb_ctx* c) {
   }
   // front descriptors last: they carry the tile counts
   ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
+  const int small_smem = 8 * ND_WPC * ND_SMALL_SMEM;
+  size_t rows_smem = 0;   // staged rows + one vector of the widest tiled level
+  for (size_t l = 0; l < D.level_maxn.size(); ++l) {
+    const size_t rstride = (D.level_maxn[l] + 2 + 1) & ~1;
+    rows_smem = std::max(rows_smem, 8 * ((size_t)D.bwd_rpw[l] * rstride + D.level_maxn[l]));
+  }
+  if (rows_smem > 227 * 1024) {
+    romb_set_error("nested dissection: a coarse front is too wide for the staged backward solve");
+    return ROMB_E_ARG;
+  }
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
   return ROMB_OK;
 }
 
@@ -725,33 +879,81 @@ romb_status coarse_factor(romb_ctx* c) {
 // out = S_C^-1 in over the non-Dirichlet coarse DoFs (Dirichlet entries of out are 0).
 // Levels whose fronts are all small use one warp per front; the few levels of
 // large fronts spread each GEMV over many CTAs.
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous one drains; it waits (griddepcontrol.wait) before reading what
+// that kernel wrote.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
   ROMB_CUDA(cudaMemsetAsync(D.counter, 0, 4 * (size_t)D.nfronts, c->stream));
   const int L = (int)D.level_ids.size();
+  auto small_shape = [&](int l, int* stride, int* voff) {
+    *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
+    *stride = (*voff + D.level_maxn[l] + 1) & ~1;       // + one vector, even (16-byte regions)
+  };
   for (int l = 0; l < L; ++l) {
-    if (D.level_maxn[l] <= ND_SMALL_N) {
-      const size_t sm = 8 * 8 * (size_t)D.level_maxn[l];
-      nd_fwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
-          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.gsrc, d_in, D.ybuf, D.sbuf, D.level_maxn[l]);
+    if (D.level_small[l]) {
+      int stride, voff;
+      small_shape(l, &stride, &voff);
+      ROMB_CUDA(launch_pdl(nd_fwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
+                           8 * ND_WPC * (size_t)stride, c->stream, (const FrontDev*)D.fr,
+                           (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
+                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, stride, voff, D.err));
       ++c->launches;
     } else if (D.fwd_n[l]) {
-      nd_fwd_tile_kernel<<<D.fwd_n[l], 256, 0, c->stream>>>(D.fr, D.fwd_tiles[l], D.F, D.idx, D.gsrc, d_in, D.ybuf,
-                                                            D.sbuf, D.zpart, D.counter); ++c->launches;
+      ROMB_CUDA(launch_pdl(nd_fwd_tile_kernel, D.fwd_n[l], 256, 0, c->stream, (const FrontDev*)D.fr,
+                           (const NdTile*)D.fwd_tiles[l], (const double*)D.F, (const int*)D.idx,
+                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, D.zpart, D.counter, D.err));
+      ++c->launches;
     }
   }
   for (int l = L - 1; l >= 0; --l) {
-    if (D.level_maxn[l] <= ND_SMALL_N) {
-      const size_t sm = 8 * 8 * ((size_t)D.level_maxn[l] + 32 * 33);
-      nd_bwd_small_kernel<<<(D.level_count[l] + 7) / 8, 256, sm, c->stream>>>(
-          D.fr, D.level_ids[l], D.level_count[l], D.F, D.idx, D.sbuf, d_out, D.level_maxn[l]); ++c->launches;
+    if (D.level_small[l]) {
+      int stride, voff;
+      small_shape(l, &stride, &voff);
+      ROMB_CUDA(launch_pdl(nd_bwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
+                           8 * ND_WPC * (size_t)stride, c->stream, (const FrontDev*)D.fr,
+                           (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
+                           (const double*)D.sbuf, d_out, stride, voff, D.err));
+      ++c->launches;
     } else if (D.bwd_n[l]) {
-      const size_t sm = 8 * (size_t)D.level_maxn[l];
-      nd_bwd_rows_kernel<<<D.bwd_n[l], 256, sm, c->stream>>>(D.fr, D.bwd_rows[l], D.F, D.idx, D.sbuf, d_out);
+      const int rb = D.bwd_rpw[l], rstride = (D.level_maxn[l] + 2 + 1) & ~1;
+      const size_t sm = 8 * ((size_t)rb * rstride + D.level_maxn[l]);
+      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, sm, c->stream, (const FrontDev*)D.fr,
+                           (const NdRows*)D.bwd_rows[l], (const double*)D.F, (const int*)D.idx,
+                           (const double*)D.sbuf, d_out, rb, rstride, D.err));
       ++c->launches;
     }
   }
   ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+// Reports (and clears) a staging timeout of the solve kernels since the last call.
+romb_status coarse_solve_check(romb_ctx* c) {
+  NdDevice& D = g_nd[c];
+  int e = 0;
+  ROMB_CUDA(cudaMemcpy(&e, D.err, 4, cudaMemcpyDeviceToHost));
+  if (e) {
+    ROMB_CUDA(cudaMemset(D.err, 0, 4));
+    romb_set_error("coarse solve: a shared-memory staging copy did not complete in time");
+    return ROMB_E_CUDA;
+  }
   return ROMB_OK;
 }

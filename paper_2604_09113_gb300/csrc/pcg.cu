@@ -438,6 +438,7 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
     }
     *iters = it;
     *relres = rel;
+    if ((s = coarse_solve_check(c)) != ROMB_OK) return s;
     if (result == ROMB_OK && rel > rtol) result = ROMB_E_NOT_CONVERGED;
   }
   // recovery + nodal output

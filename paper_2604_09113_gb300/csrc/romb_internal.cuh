@@ -197,6 +197,7 @@ romb_status launch_factor(romb_ctx* c);
 romb_status coarse_build(romb_ctx* c);      // symbolic (once per lattice shape)
 romb_status coarse_factor(romb_ctx* c);     // numeric
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out);
+romb_status coarse_solve_check(romb_ctx* c);   // staging timeouts of the solve kernels
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
 romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu);
