@@ -146,6 +146,8 @@ struct FrontDev {
 // ---------------------------------------------------------------------------
 // device kernels
 // ---------------------------------------------------------------------------
+// Leaf fronts (level 0): zero the front, put the identity below it and add the
+// cells' 20 x 20 coarse matrices (cells in a fixed order).  One CTA per front.
 __global__ void nd_assemble_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
                                    const int* __restrict__ children, const int* __restrict__ emap,
                                    const int* __restrict__ cells, const int* __restrict__ cell_pos,
@@ -188,6 +190,45 @@ __global__ void nd_assemble_kernel(const FrontDev* __restrict__ fr, const int* _
   }
 }
 
+// Inner fronts: every entry of the lower triangle and of the identity rows
+// below the front is written once, as the sum of the (at most two) children's
+// update-matrix entries that land on it (asrc: per front row, the child front
+// and the child's update row of each source, -1 if none).  The upper triangle
+// is never read and is not written.  CTA = 8 rows of one front, warp per row.
+__global__ void __launch_bounds__(256) nd_assemble_inner_kernel(const FrontDev* __restrict__ fr,
+                                                                 const int* __restrict__ level, double* __restrict__ F,
+                                                                 const int4* __restrict__ asrc) {
+  const FrontDev f = fr[level[blockIdx.y]];
+  const int ns = f.ns, n = ns + f.nb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= n + ns) return;
+  double* A = F + f.off + (long long)i * n;
+  if (i >= n) {   // identity rows: the elimination turns them into [L11^-T | -M^T]
+    for (int j = lane; j < n; j += 32) A[j] = (j == i - n) ? 1.0 : 0.0;
+    return;
+  }
+  const int4* src = asrc + f.wbuf_off;
+  const int4 si = src[i];
+  for (int j = lane; j <= i; j += 32) {
+    const int4 sj = src[j];
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int chi = a == 0 ? si.x : si.z, ri = a == 0 ? si.y : si.w;
+      if (chi < 0) continue;
+      int rj = -1;
+      if (sj.x == chi) rj = sj.y;
+      else if (sj.z == chi) rj = sj.w;
+      if (rj < 0) continue;
+      const FrontDev ch = fr[chi];
+      const int cn = ch.ns + ch.nb, hi = max(ri, rj), lo = min(ri, rj);
+      v += F[ch.off + (long long)(ch.ns + hi) * cn + (ch.ns + lo)];
+    }
+    A[j] = v;
+  }
+}
+
 // Cholesky of the diagonal block [k0, k1) of each front (one CTA per front).
 __global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
                                 int k0, int32_t* __restrict__ bad) {
@@ -202,6 +243,7 @@ __global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __re
     D[i][j] = A[(long long)(k0 + i) * n + (k0 + j)];
   }
   __syncthreads();
+  __shared__ double inv;
   for (int k = 0; k < nbk; ++k) {
     if (threadIdx.x == 0) {
       double d = D[k][k];
@@ -209,10 +251,12 @@ __global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __re
         *bad = 1;
         d = 1.0;
       }
-      D[k][k] = sqrt(d);
+      d = sqrt(d);
+      D[k][k] = d;
+      inv = 1.0 / d;
     }
     __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) D[i][k] /= D[k][k];
+    for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) D[i][k] *= inv;
     __syncthreads();
     const int m = nbk - k - 1;
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
@@ -236,11 +280,14 @@ __global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __res
   const int nbk = min(ND_NB, f.ns - k0);
   const int k1 = k0 + nbk;
   __shared__ double L[ND_NB][ND_NB + 1];
+  __shared__ double invd[ND_NB];
   double* A = F + f.off;
   for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
     const int i = t / nbk, j = t % nbk;
     L[i][j] = (j <= i) ? A[(long long)(k0 + i) * n + (k0 + j)] : 0.0;
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nbk; j += blockDim.x) invd[j] = 1.0 / L[j][j];
   __syncthreads();
   const int r = k1 + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n + f.ns) return;
@@ -251,7 +298,7 @@ __global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __res
     if (j < nbk) {
       double s = row[j];
       for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
-      x[j] = s / L[j][j];
+      x[j] = s * invd[j];
     }
   }
 #pragma unroll
@@ -617,6 +664,7 @@ __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __rest
 struct NdDevice {
   FrontDev* fr = nullptr;
   int2* gsrc = nullptr;
+  int4* asrc = nullptr;
   double* sbuf = nullptr;
   double* zpart = nullptr;
   int* counter = nullptr;
@@ -709,6 +757,8 @@ romb_status coarse_build(romb_ctx* c) {
     }
   }
   // extend-add sources of every front row: the children's update-vector entries
+  // (gsrc, for the solves) and the child front / update row (asrc, for the assembly)
+  std::vector<int4> asrc((size_t)std::max(1, wbuf_tot), make_int4(-1, -1, -1, -1));
   std::vector<int2> gsrc((size_t)std::max(1, wbuf_tot), make_int2(-1, -1));
   for (int i = 0; i < nf; ++i) {
     const NdFront& F = plan.fronts[i];
@@ -716,10 +766,17 @@ romb_status coarse_build(romb_ctx* c) {
     const FrontDev& pd = fd[F.parent];
     for (int a = 0; a < F.nb; ++a) {
       int2& s = gsrc[(size_t)pd.wbuf_off + emap[fd[i].emap_off + a]];
+      int4& q = asrc[(size_t)pd.wbuf_off + emap[fd[i].emap_off + a]];
       const int src = fd[i].ybuf_off + a;
-      if (s.x < 0) s.x = src;
-      else if (s.y < 0) s.y = src;
-      else {
+      if (s.x < 0) {
+        s.x = src;
+        q.x = i;
+        q.y = a;
+      } else if (s.y < 0) {
+        s.y = src;
+        q.z = i;
+        q.w = a;
+      } else {
         romb_set_error("nested dissection: more than two update sources for a front row");
         return ROMB_E_CUDA;
       }
@@ -761,6 +818,7 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.F, (size_t)off + 2)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.ybuf, std::max(1, ybuf))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.gsrc, gsrc.size())) != ROMB_OK) return s;
+  if ((s = romb_alloc_t(c, &D.asrc, asrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.zpart, (size_t)std::max(1LL, ztot))) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.counter, nf)) != ROMB_OK) return s;
@@ -769,6 +827,7 @@ romb_status coarse_build(romb_ctx* c) {
   ROMB_CUDA(cudaMemset(D.err, 0, 4));
   D.nfronts = nf;
   ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
+  ROMB_CUDA(cudaMemcpy(D.asrc, asrc.data(), sizeof(int4) * asrc.size(), cudaMemcpyHostToDevice));
   // partial sums of skipped (zero) tiles are never written: they stay 0
   ROMB_CUDA(cudaMemset(D.zpart, 0, 8 * (size_t)std::max(1LL, ztot)));
   ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
@@ -852,8 +911,14 @@ romb_status coarse_factor(romb_ctx* c) {
   ROMB_CUDA(cudaMemsetAsync(D.bad, 0, 4, c->stream));
   for (size_t l = 0; l < D.level_ids.size(); ++l) {
     const int nfl = D.level_count[l];
-    nd_assemble_kernel<<<nfl, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.children, D.emap, D.cells,
-                                                   D.cell_pos, c->d_SCl); ++c->launches;
+    if (l == 0) {
+      nd_assemble_kernel<<<nfl, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.children, D.emap, D.cells,
+                                                     D.cell_pos, c->d_SCl);
+    } else {
+      const dim3 ga((D.level_maxn[l] + D.level_maxns[l] + 7) / 8, nfl);
+      nd_assemble_inner_kernel<<<ga, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.asrc);
+    }
+    ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     const int mns = D.level_maxns[l], mn = D.level_maxn[l];
     for (int k0 = 0; k0 < mns; k0 += ND_NB) {

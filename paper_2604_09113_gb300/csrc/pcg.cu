@@ -355,7 +355,7 @@ static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, do
 //   z = M r; rz' = r.z; p = z + (rz'/rz) p; rz = rz'; q = S p; pq = p.q;
 //   x += (rz/pq) p; r -= (rz/pq) q; rr = r.r -> pinned host word.
 // With p = 0 and rz = 1 on entry the first iteration is the same body.
-static romb_status pcg_body(romb_ctx* c, const CellParams& P, double* yloc, double* cloc) {
+static romb_status pcg_body(romb_ctx* c, const CellParams& P, double* yloc, double* cloc, bool host_copy) {
   romb_status s;
   const long long n = c->nskel;
   const int g = grid_for(c, n);
@@ -368,9 +368,70 @@ static romb_status pcg_body(romb_ctx* c, const CellParams& P, double* yloc, doub
   if ((s = dot(c, c->d_pv, c->d_q, n, sc + 1)) != ROMB_OK) return s;
   pcg_update_x_r<<<g, 256, 0, c->stream>>>(n, sc, c->d_x, c->d_r, c->d_pv, c->d_q); ++c->launches;
   if ((s = dot(c, c->d_r, c->d_r, n, sc + 3)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+  if (host_copy) ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
+}
+
+// Loop control of the device-side PCG loop: sc[16] = (rtol |f|)^2, sc[17] =
+// maxit, sc[18] = iterations done.  Continues while |r|^2 > sc[16], |r| is
+// finite and fewer than maxit iterations have run.
+__global__ void pcg_loop_init(double* sc, double thr2, int maxit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc[0] = 1.0;
+    sc[16] = thr2;
+    sc[17] = (double)maxit;
+    sc[18] = 0.0;
+  }
+}
+
+__global__ void pcg_loop_check(cudaGraphConditionalHandle h, double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double it = sc[18] + 1.0;
+    sc[18] = it;
+    const double rr = sc[3];
+    cudaGraphSetConditional(h, (rr == rr && rr > sc[16] && it < sc[17]) ? 1u : 0u);
+  }
+}
+
+// The whole PCG loop as one graph: a conditional while node whose body is the
+// captured iteration followed by pcg_loop_check.  Returns false (with the
+// stream out of capture and no error pending) if the driver refuses any step.
+static bool build_device_loop(romb_ctx* c, const CellParams& P, double* yloc, double* cloc) {
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return (void)cudaGetLastError(), false;
+  bool ok = false;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess &&
+        cudaStreamBeginCaptureToGraph(c->stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const long long l0 = c->launches;
+      romb_status s = pcg_body(c, P, yloc, cloc, false);
+      pcg_loop_check<<<1, 32, 0, c->stream>>>(h, c->d_red);
+      ++c->launches;
+      cudaGraph_t body = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->stream, &body);
+      if (s == ROMB_OK && e == cudaSuccess && cudaGraphInstantiate(&c->pcg_graph, g, 0) == cudaSuccess) {
+        c->pcg_graph_launches = c->launches - l0;
+        ok = true;
+      }
+      c->launches = l0;
+    }
+  }
+  cudaGraphDestroy(g);
+  if (!ok) {
+    (void)cudaGetLastError();
+    if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
+    c->pcg_graph = nullptr;
+  }
+  return ok;
 }
 
 __global__ void pcg_init_scalars(double* sc) {
@@ -407,24 +468,40 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
   if (nf > 0.0) {
     ROMB_CUDA(cudaMemcpyAsync(c->d_r, c->d_f, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
     ROMB_CUDA(cudaMemsetAsync(c->d_pv, 0, 8 * n, c->stream));
-    pcg_init_scalars<<<1, 32, 0, c->stream>>>(sc); ++c->launches;
-    // the iteration body is captured once per factorisation and replayed
+    // the loop (or, where the driver cannot build it, one iteration) is captured
+    // once per factorisation and replayed
     if (!c->pcg_graph) {
-      const long long l0 = c->launches;
-      ROMB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      s = pcg_body(c, P, yloc, cloc);
-      cudaGraph_t graph = nullptr;
-      const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-      if (s != ROMB_OK) return s;
-      ROMB_CUDA(e);
-      ROMB_CUDA(cudaGraphInstantiate(&c->pcg_graph, graph, 0));
-      cudaGraphDestroy(graph);
-      c->pcg_graph_launches = c->launches - l0;
-      c->launches = l0;
+      c->pcg_device_loop = build_device_loop(c, P, yloc, cloc);
+      if (!c->pcg_device_loop) {
+        const long long l0 = c->launches;
+        ROMB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        s = pcg_body(c, P, yloc, cloc, true);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (s != ROMB_OK) return s;
+        ROMB_CUDA(e);
+        ROMB_CUDA(cudaGraphInstantiate(&c->pcg_graph, graph, 0));
+        cudaGraphDestroy(graph);
+        c->pcg_graph_launches = c->launches - l0;
+        c->launches = l0;
+      }
     }
     int it = 0;
     double rel = 1.0;
-    while (it < maxit) {
+    if (c->pcg_device_loop && maxit > 0) {   // the while body runs at least once
+      const double thr = rtol * nf;
+      pcg_loop_init<<<1, 32, 0, c->stream>>>(sc, thr * thr, maxit); ++c->launches;
+      ROMB_CUDA(cudaGraphLaunch(c->pcg_graph, c->stream));
+      ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+      ROMB_CUDA(cudaMemcpyAsync(c->h_red + 3, sc + 18, 8, cudaMemcpyDeviceToHost, c->stream));
+      ROMB_CUDA(cudaStreamSynchronize(c->stream));
+      it = (int)c->h_red[3];
+      c->launches += (long long)it * c->pcg_graph_launches;
+      rel = sqrt(c->h_red[0]) / nf;
+      if (!(rel == rel)) result = ROMB_E_NAN;
+    }
+    if (!c->pcg_device_loop) pcg_init_scalars<<<1, 32, 0, c->stream>>>(sc), ++c->launches;
+    while (!c->pcg_device_loop && it < maxit) {
       ROMB_CUDA(cudaGraphLaunch(c->pcg_graph, c->stream));
       c->launches += c->pcg_graph_launches;
       ROMB_CUDA(cudaStreamSynchronize(c->stream));

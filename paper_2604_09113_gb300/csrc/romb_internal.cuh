@@ -160,6 +160,7 @@ struct romb_ctx {
   double* d_yloc = nullptr;     // [cells][nU] cell-local PCG scratch
   cudaGraphExec_t pcg_graph = nullptr;   // captured PCG iteration (per factorisation)
   long long pcg_graph_launches = 0;
+  bool pcg_device_loop = false;          // the graph holds the whole loop (conditional while node)
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
   double* d_u = nullptr;        // nodal output [nodes][2]
   double* d_traction = nullptr;
