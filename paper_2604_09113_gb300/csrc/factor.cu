@@ -19,8 +19,23 @@
 #include "device.cuh"
 #include "tables.cuh"
 
-// In-place Cholesky (lower) of the n x n row-major matrix A (stride lda).
-__device__ void chol_smem(double* A, int n, int lda, int* bad) {
+// GB300 issues an FP64 warp instruction every 16 SM cycles, so every dense
+// step below maps threads onto exactly the entries that do work (lower
+// triangles through tri_ij, trailing blocks row-major) and multiplies by
+// reciprocal pivots instead of dividing.
+
+// Lower-triangle position (i, j), j <= i, of the row-major linear index t.
+__device__ __forceinline__ void tri_ij(int t, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= t) ++r;
+  else if (r * (r + 1) / 2 > t) --r;
+  i = r;
+  j = t - r * (r + 1) / 2;
+}
+
+// In-place right-looking Cholesky (lower) of the n x n row-major A (stride
+// lda); invd[k] = 1 / L_kk.  Trailing updates touch the lower triangle only.
+__device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
@@ -29,40 +44,62 @@ __device__ void chol_smem(double* A, int n, int lda, int* bad) {
         *bad = 1;
         d = 1.0;
       }
-      A[k * lda + k] = sqrt(d);
+      d = sqrt(d);
+      A[k * lda + k] = d;
+      invd[k] = 1.0 / d;
     }
     __syncthreads();
-    const double inv = 1.0 / A[k * lda + k];
+    const double inv = invd[k];
     for (int i = k + 1 + tid; i < n; i += nt) A[i * lda + k] *= inv;
     __syncthreads();
-    const int m = n - k - 1;
-    for (int t = tid; t < m * m; t += nt) {
-      const int i = k + 1 + t / m, j = k + 1 + t % m;
-      if (j <= i) A[i * lda + j] -= A[i * lda + k] * A[j * lda + k];
+    const int m = n - k - 1, np = m * (m + 1) / 2;
+    for (int t = tid; t < np; t += nt) {
+      int a, b;
+      tri_ij(t, a, b);
+      const int i = k + 1 + a, j = k + 1 + b;
+      A[i * lda + j] = fma(-A[i * lda + k], A[j * lda + k], A[i * lda + j]);
     }
     __syncthreads();
   }
 }
 
-// B <- L^-1 B (forward) for `ncols` columns, one thread per column.
-__device__ void trsm_fwd(const double* L, int n, int ldl, double* B, int ldb, int ncols) {
-  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
-    for (int i = 0; i < n; ++i) {
-      double s = B[i * ldb + col];
-      for (int k = 0; k < i; ++k) s -= L[i * ldl + k] * B[k * ldb + col];
-      B[i * ldb + col] = s / L[i * ldl + i];
+// B <- L^-1 B (n x ncols, stride ldb), right-looking: step i subtracts row i
+// from the rows below; row i+1 is final after step i and is scaled there.
+__device__ void trsm_lower(const double* L, int n, int ldl, const double* invd, double* B, int ldb, int ncols) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < ncols; c += nt) B[c] *= invd[0];
+  __syncthreads();
+  for (int i = 0; i + 1 < n; ++i) {
+    const int tot = (n - i - 1) * ncols;
+    for (int t = tid; t < tot; t += nt) {
+      const int r = i + 1 + t / ncols, c = t % ncols;
+      double v = fma(-L[r * ldl + i], B[i * ldb + c], B[r * ldb + c]);
+      if (r == i + 1) v *= invd[r];
+      B[r * ldb + c] = v;
     }
+    __syncthreads();
   }
 }
 
-// B <- L^-T B (backward) for `ncols` columns, one thread per column.
-__device__ void trsm_bwd(const double* L, int n, int ldl, double* B, int ldb, int ncols) {
-  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
-    for (int i = n - 1; i >= 0; --i) {
-      double s = B[i * ldb + col];
-      for (int k = i + 1; k < n; ++k) s -= L[k * ldl + i] * B[k * ldb + col];
-      B[i * ldb + col] = s / L[i * ldl + i];
+// M <- L^-1 in place of nothing: M (n x n, stride ldm) is written whole
+// (zero above the diagonal).  Step i updates rows r > i in columns c <= i,
+// the only non-zero part of row i; row i+1 is scaled in the same step.
+__device__ void tri_inverse(const double* L, int n, int ldl, const double* invd, double* M, int ldm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < n * n; t += nt) {
+    const int r = t / n, c = t % n;
+    M[r * ldm + c] = (r == c) ? invd[r] : 0.0;
+  }
+  __syncthreads();
+  for (int i = 0; i + 1 < n; ++i) {
+    const int w = i + 1, tot = (n - i - 1) * w;
+    for (int t = tid; t < tot; t += nt) {
+      const int r = i + 1 + t / w, c = t % w;
+      double v = fma(-L[r * ldl + i], M[i * ldm + c], M[r * ldm + c]);
+      if (r == i + 1) v *= invd[r];
+      M[r * ldm + c] = v;
     }
+    __syncthreads();
   }
 }
 
@@ -216,24 +253,27 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     }
   }
   // ---- K_II = L L^T ----
-  chol_smem(AII, NI, NI, &s_bad);
+  __shared__ double s_inv[NI > NK ? NI : NK];
+  __shared__ double s_invT[12];
+  chol_smem(AII, NI, NI, s_inv, &s_bad);
   // ---- W = L^-1 K_IU ----
-  trsm_fwd(AII, NI, NI, AIU, NU, NU);
-  __syncthreads();
-  // ---- S = K_UU - W^T W (lower triangle computed, mirrored) ----
-  for (int t = tid; t < NU * NU; t += nt) {
-    const int u = t / NU, v = t % NU;
-    if (v > u) continue;
+  trsm_lower(AII, NI, NI, s_inv, AIU, NU, NU);
+  // ---- S = K_UU - W^T W (lower triangle, mirrored) ----
+  for (int t = tid; t < NU * (NU + 1) / 2; t += nt) {
+    int u, v;
+    tri_ij(t, u, v);
     double acc = 0.0;
-    for (int k = 0; k < NI; ++k) acc += AIU[k * NU + u] * AIU[k * NU + v];
-    const double val = S[t] - acc;
+#pragma unroll 5
+    for (int k = 0; k < NI; ++k) acc = fma(AIU[k * NU + u], AIU[k * NU + v], acc);
+    const double val = S[u * NU + v] - acc;
     S[u * NU + v] = val;
     S[v * NU + u] = val;
   }
   // write L (packed lower) and W for the interior recovery
-  for (int t = tid; t < NI * NI; t += nt) {
-    const int i = t / NI, j = t % NI;
-    if (j <= i) LII_out[cell * (NI * (NI + 1) / 2) + (long long)i * (i + 1) / 2 + j] = AII[t];
+  for (int t = tid; t < NI * (NI + 1) / 2; t += nt) {
+    int i, j;
+    tri_ij(t, i, j);
+    LII_out[cell * (NI * (NI + 1) / 2) + t] = AII[i * NI + j];
   }
   for (int t = tid; t < NI * NU; t += nt) W_out[cell * NI * NU + t] = AIU[t];
   for (int u = tid; u < NU; u += nt) {
@@ -241,34 +281,60 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     Dv[u] = g >= 0 ? kd[u] / ktot[g] : 0.0;
   }
   __syncthreads();
-  // ---- phase 2 (AII / AIU region reused) ----
+  // ---- phase 2 (AII / AIU region reused; S is written out and its area
+  //      becomes M = Lhat^-1 once Shat, Chat^T and the right-hand sides are built) ----
   double* Sh = sm + Dm::oSh;
   double* Y = sm + Dm::oY;
   double* T = sm + Dm::oT;
   double* Z = sm + Dm::oZ;
   double* Psi = sm + Dm::oPsi;
   double* Q = sm + Dm::oQ;
-  for (int t = tid; t < NU * NU; t += nt) S_out[cell * NU * NU + t] = S[t];
+  double* M = S;
+  double* Sg = S_out + cell * NU * NU;
+  for (int t = tid; t < NU * NU; t += nt) Sg[t] = S[t];
   for (int t = tid; t < NK * NK; t += nt) Sh[t] = S[s_keep[t / NK] * NU + s_keep[t % NK]];
-  for (int t = tid; t < NK * 12; t += nt) Y[t] = Cr[(8 + t % 12) * NU + s_keep[t / 12]];
+  // right-hand sides of Eq. (BDDC local basis) after removing the corners:
+  // fhat = -S[keep, corner_j] for vertex slots (into Q, then Z = Shat^-1 fhat)
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    Q[t] = (j < 8 && s_cmap[j] >= 0) ? -S[s_keep[i] * NU + s_cu[j]] : 0.0;
+  }
   __syncthreads();
-  chol_smem(Sh, NK, NK, &s_bad);
-  trsm_fwd(Sh, NK, NK, Y, 12, 12);   // Y = Lhat^-1 Chat^T
+  chol_smem(Sh, NK, NK, s_inv, &s_bad);
+  tri_inverse(Sh, NK, NK, s_inv, M, NK);
+  // Y = M Chat^T (M lower triangular)
+  for (int t = tid; t < NK * 12; t += nt) {
+    const int i = t / 12, e = t % 12;
+    const double* Ce = Cr + (8 + e) * NU;
+    double acc = 0.0;
+    for (int k = 0; k <= i; ++k) acc = fma(M[i * NK + k], Ce[s_keep[k]], acc);
+    Y[t] = acc;
+  }
+  // Z1 = M fhat
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    double acc = 0.0;
+    for (int k = 0; k <= i; ++k) acc = fma(M[i * NK + k], Q[k * 20 + j], acc);
+    Z[t] = acc;
+  }
   __syncthreads();
+  // That = Y^T Y
   for (int t = tid; t < 144; t += nt) {
     const int a = t / 12, b = t % 12;
     double acc = 0.0;
-    for (int i = 0; i < NK; ++i) acc += Y[i * 12 + a] * Y[i * 12 + b];
+    for (int i = 0; i < NK; ++i) acc = fma(Y[i * 12 + a], Y[i * 12 + b], acc);
     if (s_cmap[8 + a] < 0 || s_cmap[8 + b] < 0) acc = (a == b) ? 1.0 : 0.0;
     T[t] = acc;
   }
-  // right-hand sides of Eq. (BDDC local basis) after removing the corners:
-  // fhat = -S[keep, corner_j] for vertex slots, ghat handled below
+  // Z = M^T Z1 = Shat^-1 fhat
   for (int t = tid; t < NK * 20; t += nt) {
     const int i = t / 20, j = t % 20;
-    Z[t] = (j < 8 && s_cmap[j] >= 0) ? -S[s_keep[i] * NU + s_cu[j]] : 0.0;
+    double acc = 0.0;
+    for (int k = i; k < NK; ++k) acc = fma(M[k * NK + i], Z[k * 20 + j], acc);
+    Q[t] = acc;
   }
   __syncthreads();
+  for (int t = tid; t < NK * 20; t += nt) Z[t] = Q[t];
   if (tid == 0) {
     // 12 x 12 Cholesky of That (one thread)
     for (int k = 0; k < 12; ++k) {
@@ -280,45 +346,56 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
       }
       d = sqrt(d);
       T[k * 12 + k] = d;
+      const double inv = 1.0 / d;
+      s_invT[k] = inv;
       for (int i = k + 1; i < 12; ++i) {
         double s = T[i * 12 + k];
         for (int j = 0; j < k; ++j) s -= T[i * 12 + j] * T[k * 12 + j];
-        T[i * 12 + k] = s / d;
+        T[i * 12 + k] = s * inv;
       }
     }
   }
-  trsm_fwd(Sh, NK, NK, Z, 20, 20);
-  __syncthreads();
-  trsm_bwd(Sh, NK, NK, Z, 20, 20);   // Z = Shat^-1 fhat
   __syncthreads();
   // R = Chat Z - ghat ; ghat = -C[edge, corner_j] (vertex slots) or e_{j-8} (edge slots)
   double* R = Q;   // [12][20]
   for (int t = tid; t < 240; t += nt) {
     const int e = t / 20, j = t % 20;
     double acc = 0.0;
-    for (int i = 0; i < NK; ++i) acc += Cr[(8 + e) * NU + s_keep[i]] * Z[i * 20 + j];
+    for (int i = 0; i < NK; ++i) acc = fma(Cr[(8 + e) * NU + s_keep[i]], Z[i * 20 + j], acc);
     double g = 0.0;
     if (s_cmap[j] >= 0) g = (j < 8) ? -Cr[(8 + e) * NU + s_cu[j]] : ((j - 8 == e) ? 1.0 : 0.0);
     R[t] = (s_cmap[8 + e] >= 0) ? acc - g : 0.0;
   }
   __syncthreads();
-  // Lambda = That^-1 R
-  trsm_fwd(T, 12, 12, R, 20, 20);
+  // Lambda = That^-1 R (one thread per column, 12 x 12 triangles)
+  for (int j = tid; j < 20; j += nt) {
+    for (int i = 0; i < 12; ++i) {
+      double s = R[i * 20 + j];
+      for (int k = 0; k < i; ++k) s -= T[i * 12 + k] * R[k * 20 + j];
+      R[i * 20 + j] = s * s_invT[i];
+    }
+    for (int i = 11; i >= 0; --i) {
+      double s = R[i * 20 + j];
+      for (int k = i + 1; k < 12; ++k) s -= T[k * 12 + i] * R[k * 20 + j];
+      R[i * 20 + j] = s * s_invT[i];
+    }
+  }
   __syncthreads();
-  trsm_bwd(T, 12, 12, R, 20, 20);
-  __syncthreads();
-  // Xhat = Z - Lhat^-T (Y Lambda)
+  // Xhat = Z - Lhat^-T (Y Lambda) = Z - M^T (Y Lambda)
   double* Q2 = Psi;   // temporary [NK][20] in the Psi area (NU*20 >= NK*20)
   for (int t = tid; t < NK * 20; t += nt) {
     const int i = t / 20, j = t % 20;
     double acc = 0.0;
-    for (int e = 0; e < 12; ++e) acc += Y[i * 12 + e] * R[e * 20 + j];
+    for (int e = 0; e < 12; ++e) acc = fma(Y[i * 12 + e], R[e * 20 + j], acc);
     Q2[t] = acc;
   }
   __syncthreads();
-  trsm_bwd(Sh, NK, NK, Q2, 20, 20);
-  __syncthreads();
-  for (int t = tid; t < NK * 20; t += nt) Z[t] -= Q2[t];
+  for (int t = tid; t < NK * 20; t += nt) {
+    const int i = t / 20, j = t % 20;
+    double acc = 0.0;
+    for (int k = i; k < NK; ++k) acc = fma(M[k * NK + i], Q2[k * 20 + j], acc);
+    Z[t] -= acc;
+  }
   __syncthreads();
   for (int t = tid; t < NU * 20; t += nt) Psi[t] = 0.0;
   __syncthreads();
@@ -328,21 +405,21 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   }
   if (tid < 8 && s_cmap[tid] >= 0) Psi[s_cu[tid] * 20 + tid] = 1.0;
   __syncthreads();
-  // S Psi (into Z region reinterpreted as [NU][20] needs NU*20 <= NK*20 + ... use Q after R)
+  // S Psi, with S read back from its copy in global memory (written above by this CTA)
   double* SP = Cr;   // constraints no longer needed: [NU][20] fits in 20*NU
-  // keep the edge rows of Chat for the fine operator: they live in Y already
-  __syncthreads();
   for (int t = tid; t < NU * 20; t += nt) {
     const int u = t / 20, j = t % 20;
+    const double* Su = Sg + u * NU;
     double acc = 0.0;
-    for (int v = 0; v < NU; ++v) acc += S[u * NU + v] * Psi[v * 20 + j];
+#pragma unroll 4
+    for (int v = 0; v < NU; ++v) acc = fma(Su[v], Psi[v * 20 + j], acc);
     SP[t] = acc;
   }
   __syncthreads();
   for (int t = tid; t < 400; t += nt) {
     const int a = t / 20, b = t % 20;
     double acc = 0.0;
-    for (int u = 0; u < NU; ++u) acc += Psi[u * 20 + a] * SP[u * 20 + b];
+    for (int u = 0; u < NU; ++u) acc = fma(Psi[u * 20 + a], SP[u * 20 + b], acc);
     SCl_out[cell * 400 + t] = acc;
   }
   for (int t = tid; t < NU * 20; t += nt) {
@@ -350,20 +427,14 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     Phi_out[cell * NU * 20 + t] = Dv[t / 20] * Psi[t];
   }
   for (int u = tid; u < NU; u += nt) D_out[cell * NU + u] = Dv[u];
-  __syncthreads();
-  // ---- explicit fine operator F = M^T M - N^T N with M = Lhat^-1, N = L_T^-1 Y^T M ----
-  double* M = S;   // S has been written out; reuse its NU*NU area for M (NK*NK)
-  for (int t = tid; t < NK * NK; t += nt) M[t] = (t / NK == t % NK) ? 1.0 : 0.0;
-  __syncthreads();
-  trsm_fwd(Sh, NK, NK, M, NK, NK);
-  __syncthreads();
+  // ---- explicit fine operator F = M^T M - N^T N with N = L_T^-1 Y^T M ----
   // V = L_T^-1 Y^T  (12 x NK), stored transposed in Y: column i of Y^T = row i of Y
   for (int i = tid; i < NK; i += nt) {
     double v[12];
     for (int e = 0; e < 12; ++e) {
       double s = Y[i * 12 + e];
       for (int k = 0; k < e; ++k) s -= T[e * 12 + k] * v[k];
-      v[e] = s / T[e * 12 + e];
+      v[e] = s * s_invT[e];
     }
     for (int e = 0; e < 12; ++e) Y[i * 12 + e] = v[e];
   }
@@ -372,19 +443,19 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   for (int t = tid; t < 12 * NK; t += nt) {
     const int e = t / NK, j = t % NK;
     double acc = 0.0;
-    for (int i = j; i < NK; ++i) acc += Y[i * 12 + e] * M[i * NK + j];
+    for (int i = j; i < NK; ++i) acc = fma(Y[i * 12 + e], M[i * NK + j], acc);
     N[t] = acc;
   }
   __syncthreads();
   double* Gc = G_out + cell * NU * NU;
   for (int t = tid; t < NU * NU; t += nt) Gc[t] = 0.0;
   __syncthreads();
-  for (int t = tid; t < NK * NK; t += nt) {
-    const int a = t / NK, b = t % NK;
-    if (b > a) continue;
+  for (int t = tid; t < NK * (NK + 1) / 2; t += nt) {
+    int a, b;
+    tri_ij(t, a, b);
     double acc = 0.0;
-    for (int i = a; i < NK; ++i) acc += M[i * NK + a] * M[i * NK + b];
-    for (int e = 0; e < 12; ++e) acc -= N[e * NK + a] * N[e * NK + b];
+    for (int i = a; i < NK; ++i) acc = fma(M[i * NK + a], M[i * NK + b], acc);
+    for (int e = 0; e < 12; ++e) acc = fma(-N[e * NK + a], N[e * NK + b], acc);
     const int ua = s_keep[a], ub = s_keep[b];
     const double v = Dv[ua] * acc * Dv[ub];
     Gc[ua * NU + ub] = v;
