@@ -411,7 +411,9 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_yloc, cells * c->nU);
   A_(c->d_u, 2 * nodes);
   A_(c->d_traction, 8 * 64);
+  A_(c->d_pcg_err, 1);
 #undef A_
+  ROMB_CUDA(cudaMemsetAsync(c->d_pcg_err, 0, 4, c->stream));
   const long long ncoarse = 2LL * (nx + 1) * (ny + 1) + 3LL * nx * (ny + 1) + 3LL * (nx + 1) * ny;
   if ((s = romb_alloc_t(c, &c->d_coarse, 2 * ncoarse)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &c->d_cowner, 4 * ncoarse)) != ROMB_OK) return s;

@@ -8,11 +8,14 @@
 // sums are gathers in a fixed cell order, so every result is deterministic.
 // Per iteration and cell: q = S p (matvec), z = D F D r + D Psi S_C^-1 Psi^T D r.
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
+#include "bulk.cuh"
 #include "device.cuh"
 #include "tables.cuh"
 
@@ -108,6 +111,106 @@ __global__ void __launch_bounds__(256) cell_matvec_kernel(int ncells, int NU, co
     }
     cloc[cell * 20 + hl] = a0;
     if (hl < 4) cloc[cell * 20 + 16 + hl] = a1;
+  }
+}
+
+// y_loc = M_c v_loc for every cell (M_c a dense symmetric nU x nU cell matrix:
+// S, or D F D), and with COARSE also c_loc = Phi_c^T v_loc.  Persistent CTAs
+// take the cells blockIdx.x, blockIdx.x + gridDim.x, ...; each streams its
+// cells' M_c (and Phi_c) and index rows through a CA_STAGES-deep shared ring
+// filled by bulk copies, so the HBM stream overlaps the FP64 work.  Row r of
+// y is summed by two lanes (r, half of k) of one warp, one shuffle apart: every
+// FP64 instruction has all its lanes busy.  One barrier per cell releases the
+// stage and publishes the next cell's gathered v.
+#define CA_STAGES 3
+template <int P>
+struct CellApplyShape {
+  static constexpr int NU = 8 * P, WARPS = (NU + 15) / 16, THREADS = 32 * WARPS;
+  static constexpr int stage_bytes(bool coarse) { return NU * NU * 8 + (coarse ? NU * 20 * 8 : 0) + NU * 4; }
+};
+
+template <int P, bool COARSE>
+__global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
+    int ncells, const double* __restrict__ M, const int* __restrict__ umap, const double* __restrict__ v,
+    double* __restrict__ yloc, const double* __restrict__ Phi, double* __restrict__ cloc, int* __restrict__ err) {
+  using Sh = CellApplyShape<P>;
+  constexpr int NU = Sh::NU, H = NU / 2, NT = Sh::THREADS;
+  constexpr int MB = NU * NU * 8, PB = COARSE ? NU * 20 * 8 : 0, SB = MB + PB + NU * 4;
+  extern __shared__ __align__(16) unsigned char ring[];
+  __shared__ uint64_t full[CA_STAGES];
+  __shared__ double sv[2][NU];
+  __shared__ double cpart[2][4][20];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nmine = blockIdx.x < ncells ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto cell_of = [&](int j) { return (long long)blockIdx.x + (long long)j * gridDim.x; };
+  auto issue = [&](int j) {
+    const long long cell = cell_of(j);
+    unsigned char* st = ring + (size_t)(j % CA_STAGES) * SB;
+    uint64_t* bar = &full[j % CA_STAGES];
+    mbar_expect_tx(bar, SB);
+    bulk_g2s(st, M + cell * NU * NU, MB, bar);
+    if (COARSE) bulk_g2s(st + MB, Phi + cell * NU * 20, PB, bar);
+    bulk_g2s(st + MB + PB, umap + cell * NU, NU * 4, bar);
+  };
+  if (tid == 0) {
+    for (int s = 0; s < CA_STAGES; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+    for (int j = 0; j < CA_STAGES && j < nmine; ++j) issue(j);
+  }
+  __syncthreads();
+  // v at the first cell's skeleton slots
+  bool ok = true;
+  if (nmine > 0) {
+    ok = mbar_wait(&full[0], 0);
+    if (ok) {
+      const int* us = reinterpret_cast<const int*>(ring + MB + PB);
+      for (int u = tid; u < NU; u += NT) sv[0][u] = us[u] >= 0 ? v[us[u]] : 0.0;
+    }
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  const int r = 16 * warp + (lane & 15), q = lane >> 4;
+  for (int j = 0; j < nmine; ++j) {
+    const long long cell = cell_of(j);
+    const unsigned char* st = ring + (size_t)(j % CA_STAGES) * SB;
+    const double* Ms = reinterpret_cast<const double*>(st);
+    const double* x = sv[j & 1];
+    // y = M_c v: lane (r, q) sums k in [q H, q H + H) of M[k][r] v[k] (M symmetric)
+    double acc = 0.0;
+    if (r < NU) {
+      const double* mk = Ms + q * H * NU + r;
+#pragma unroll 8
+      for (int k = 0; k < H; ++k) acc = fma(mk[k * NU], x[q * H + k], acc);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (q == 0 && r < NU) yloc[cell * NU + r] = acc;
+    if (COARSE) {
+      // c = Phi^T v: thread (j, part) sums a quarter of the slots
+      const double* Ps = reinterpret_cast<const double*>(st + MB);
+      for (int t = tid; t < 80; t += NT) {
+        const int jj = t % 20, part = t / 20;
+        double a = 0.0;
+        for (int u = part * (NU / 4); u < (part + 1) * (NU / 4); ++u) a = fma(Ps[u * 20 + jj], x[u], a);
+        cpart[j & 1][part][jj] = a;
+      }
+    }
+    // next cell's v (its stage was issued CA_STAGES - 1 cells ago)
+    if (j + 1 < nmine) {
+      ok = mbar_wait(&full[(j + 1) % CA_STAGES], (uint32_t)(((j + 1) / CA_STAGES) & 1));
+      if (ok) {
+        const int* us = reinterpret_cast<const int*>(ring + (size_t)((j + 1) % CA_STAGES) * SB + MB + PB);
+        for (int u = tid; u < NU; u += NT) sv[(j + 1) & 1][u] = us[u] >= 0 ? v[us[u]] : 0.0;
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      return;
+    }
+    if (COARSE && tid < 20)
+      cloc[cell * 20 + tid] = (cpart[j & 1][0][tid] + cpart[j & 1][1][tid]) + (cpart[j & 1][2][tid] + cpart[j & 1][3][tid]);
+    if (tid == 0 && j + CA_STAGES < nmine) issue(j + CA_STAGES);   // stage j % CA_STAGES is free
   }
 }
 
@@ -325,11 +428,47 @@ static int grid_for(const romb_ctx* c, long long n) {
 }
 
 // z = S_BDDC^-1 r  (Algorithm 1)
+// prepare = true (outside stream capture): set the shared-memory limit and size
+// the persistent grid (resident CTAs per SM x SMs); prepare = false: launch.
+template <int P, bool COARSE>
+static romb_status cell_apply_p(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
+                                double* cloc) {
+  using Sh = CellApplyShape<P>;
+  const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(COARSE);
+  if (prepare) {
+    ROMB_CUDA(cudaFuncSetAttribute(cell_apply_kernel<P, COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    int per_sm = 0;
+    ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_apply_kernel<P, COARSE>, Sh::THREADS, smem));
+    c->ca_grid[COARSE] = std::max(1, std::min(c->ncells, std::max(1, per_sm) * c->sms));
+    return ROMB_OK;
+  }
+  cell_apply_kernel<P, COARSE><<<c->ca_grid[COARSE], Sh::THREADS, smem, c->stream>>>(
+      c->ncells, M, c->d_ucell_map, v, yloc, c->d_Phi, cloc, c->d_pcg_err);
+  ++c->launches;
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
+template <bool COARSE>
+static romb_status cell_apply(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
+                              double* cloc) {
+  switch (c->p) {
+    case 3: return cell_apply_p<3, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 4: return cell_apply_p<4, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 5: return cell_apply_p<5, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 6: return cell_apply_p<6, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 7: return cell_apply_p<7, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 8: return cell_apply_p<8, COARSE>(c, prepare, M, v, yloc, cloc);
+  }
+  return ROMB_E_ARG;
+}
+
 static romb_status precondition(romb_ctx* c, const CellParams& P, const double* r, double* z, double* yloc,
                                 double* cloc) {
   const int cb = (c->ncells + 15) / 16;
-  cell_matvec_kernel<true><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_G, c->d_ucell_map, r, yloc, c->d_Phi,
-                                                      cloc); ++c->launches;
+  romb_status s0 = cell_apply<true>(c, false, c->d_G, r, yloc, cloc);
+  if (s0 != ROMB_OK) return s0;
   double* zc = c->d_coarse;
   double* gc = c->d_coarse + c->ncoarse_all;
   coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->stream>>>(c->d_cowner, c->ncoarse_all, cloc, zc); ++c->launches;
@@ -343,9 +482,8 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
 }
 
 static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
-  const int cb = (c->ncells + 15) / 16;
-  cell_matvec_kernel<false><<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_S, c->d_ucell_map, v, yloc, nullptr,
-                                                       nullptr); ++c->launches;
+  romb_status s0 = cell_apply<false>(c, false, c->d_S, v, yloc, nullptr);
+  if (s0 != ROMB_OK) return s0;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
@@ -471,7 +609,12 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
     // the loop (or, where the driver cannot build it, one iteration) is captured
     // once per factorisation and replayed
     if (!c->pcg_graph) {
-      c->pcg_device_loop = build_device_loop(c, P, yloc, cloc);
+      if ((s = cell_apply<true>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<false>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      // ROMB_PCG_HOST_LOOP=1 keeps the loop on the host (one graph launch per
+      // iteration): profilers cannot replay kernels inside conditional nodes.
+      const char* hl = getenv("ROMB_PCG_HOST_LOOP");
+      c->pcg_device_loop = !(hl && hl[0] == '1') && build_device_loop(c, P, yloc, cloc);
       if (!c->pcg_device_loop) {
         const long long l0 = c->launches;
         ROMB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -516,6 +659,15 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
     *iters = it;
     *relres = rel;
     if ((s = coarse_solve_check(c)) != ROMB_OK) return s;
+    {
+      int e = 0;
+      ROMB_CUDA(cudaMemcpy(&e, c->d_pcg_err, 4, cudaMemcpyDeviceToHost));
+      if (e) {
+        ROMB_CUDA(cudaMemset(c->d_pcg_err, 0, 4));
+        romb_set_error("PCG: a cell-operator staging copy did not complete in time");
+        return ROMB_E_CUDA;
+      }
+    }
     if (result == ROMB_OK && rel > rtol) result = ROMB_E_NOT_CONVERGED;
   }
   // recovery + nodal output

@@ -158,6 +158,8 @@ struct romb_ctx {
   double* d_fU = nullptr;       // [cells][nU] skeleton-slot forces
   double* d_cloc = nullptr;     // [cells][20] coarse restriction Psi^T D r
   double* d_yloc = nullptr;     // [cells][nU] cell-local PCG scratch
+  int* d_pcg_err = nullptr;     // set by a PCG cell kernel whose staging copy timed out
+  int ca_grid[2] = {0, 0};      // persistent grid of the cell operator kernels (S, D F D + Phi^T)
   cudaGraphExec_t pcg_graph = nullptr;   // captured PCG iteration (per factorisation)
   long long pcg_graph_launches = 0;
   bool pcg_device_loop = false;          // the graph holds the whole loop (conditional while node)
