@@ -47,6 +47,7 @@ void fill_cell_params(const romb_ctx* c, CellParams* P) {
   gll_nodes01(c->p, P->gll);
   gauss01(ROMB_NQ, P->gq_x, P->gq_w);
   for (int i = 0; i < ROMB_NQ; ++i) cell_basis1d(*P, P->gq_x[i], P->bq[i], nullptr);
+  for (int i = 0; i <= ROMB_NQ; ++i) map_basis1d(c->m, i < ROMB_NQ ? P->gq_x[i] : 0.5, P->mq[i], P->dmq[i]);
   LocalTables T = make_local_tables(c->p);
   memcpy(P->uslot, T.uslot, sizeof(P->uslot));
   memcpy(P->islot, T.islot, sizeof(P->islot));

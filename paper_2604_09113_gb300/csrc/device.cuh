@@ -19,6 +19,9 @@ struct CellParams {
   int uslot[8 * ROMB_MAX_P];
   int islot[2 * (ROMB_MAX_P - 1) * (ROMB_MAX_P - 1)];
   int uslot_of_node[(ROMB_MAX_P + 1) * (ROMB_MAX_P + 1)];
+  // 1D map basis (order m, equispaced nodes) and its derivative at the edge
+  // Gauss points gq_x[q], q < ROMB_NQ, and at the midpoint (q = ROMB_NQ)
+  double mq[ROMB_NQ + 1][5], dmq[ROMB_NQ + 1][5];
 };
 
 // Values and derivatives of the n+1 Lagrange polynomials on `nodes` at t.
@@ -97,6 +100,26 @@ __device__ inline void map_eval(const double* ctrl, int nx, int m, int cx, int c
         J[r][1] += w2 * X[r];
       }
     }
+}
+
+// Physical point and tangent dx/dt of the cell map on lattice-cell edge e
+// (0 left, 1 right, 2 bottom, 3 top; t runs along the free coordinate) at the
+// tabulated edge point q: on an edge one 1D factor of the tensor map basis is a
+// Kronecker delta, so only the m+1 control points of that edge contribute.
+__device__ inline void edge_map_point(const CellParams& P, const double* ctrl, int cx, int cy, int e, int q,
+                                      double* x, double* tan) {
+  const int m = P.m;
+  x[0] = x[1] = tan[0] = tan[1] = 0.0;
+  for (int s = 0; s <= m; ++s) {
+    const int a = e == 0 ? 0 : e == 1 ? m : s;
+    const int b = e == 2 ? 0 : e == 3 ? m : s;
+    const double* X = ctrl_pt(ctrl, P.nx, m, cx, cy, a, b);
+    const double w = P.mq[q][s], dw = P.dmq[q][s];
+    x[0] = fma(w, X[0], x[0]);
+    x[1] = fma(w, X[1], x[1]);
+    tan[0] = fma(dw, X[0], tan[0]);
+    tan[1] = fma(dw, X[1], tan[1]);
+  }
 }
 
 __device__ inline double warp_sum(double v) {

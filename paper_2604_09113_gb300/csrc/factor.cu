@@ -206,16 +206,12 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   // edge geometry for the coarse functionals: x(t_q), j(t_q) and the midpoint
   for (int t = tid; t < 4 * (ROMB_NQ + 1); t += nt) {
     const int e = t / (ROMB_NQ + 1), qq = t % (ROMB_NQ + 1);
-    const double tt = qq < ROMB_NQ ? Pm.gq_x[qq] : 0.5;
-    const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : tt;
-    const double x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : tt;
-    double x[2], J[2][2];
-    map_eval(ctrl, Pm.nx, Pm.m, cx, cy, x1, x2, x, J);
-    const int dcol = e < 2 ? 1 : 0;
+    double x[2], tg[2];
+    edge_map_point(Pm, ctrl, cx, cy, e, qq, x, tg);
     if (qq < ROMB_NQ) {
       Ex[(e * ROMB_NQ + qq) * 3 + 0] = x[0];
       Ex[(e * ROMB_NQ + qq) * 3 + 1] = x[1];
-      Ex[(e * ROMB_NQ + qq) * 3 + 2] = hypot(J[0][dcol], J[1][dcol]);
+      Ex[(e * ROMB_NQ + qq) * 3 + 2] = hypot(tg[0], tg[1]);
     } else {
       Ex[4 * ROMB_NQ * 3 + 2 * e + 0] = x[0];
       Ex[4 * ROMB_NQ * 3 + 2 * e + 1] = x[1];
