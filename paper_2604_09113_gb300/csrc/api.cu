@@ -93,7 +93,12 @@ void romb_free_lattice(romb_ctx* c) {
   double* h_red = c->h_red;
   cudaEvent_t ev[16];
   for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
+  cudaStream_t side = c->side;
+  cudaEvent_t evfork = c->evfork, evjoin = c->evjoin;
   *c = romb_ctx();
+  c->side = side;
+  c->evfork = evfork;
+  c->evjoin = evjoin;
   for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->roms[i] = roms[i];
   c->rom_allocs = keep;
   c->stream = st;
@@ -140,6 +145,18 @@ extern "C" romb_status romb_create(romb_ctx** out, int device, size_t budget, vo
     c->own_stream = true;
   }
   for (auto& e : c->ev) cudaEventCreate(&e);
+  {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->evfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->evjoin, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      romb_set_error("romb_create: stream or event creation failed");
+      delete c;
+      return ROMB_E_CUDA;
+    }
+  }
   if (cudaMallocHost(&c->h_red, 64 * sizeof(double)) != cudaSuccess) {
     delete c;
     return ROMB_E_OOM;
@@ -158,6 +175,9 @@ extern "C" void romb_destroy(romb_ctx* c) {
   for (auto& e : c->ev) cudaEventDestroy(e);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->evfork) cudaEventDestroy(c->evfork);
+  if (c->evjoin) cudaEventDestroy(c->evjoin);
   delete c;
 }
 

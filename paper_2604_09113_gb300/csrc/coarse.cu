@@ -229,21 +229,12 @@ __global__ void __launch_bounds__(256) nd_assemble_inner_kernel(const FrontDev* 
   }
 }
 
-// Cholesky of the diagonal block [k0, k1) of each front (one CTA per front).
-__global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
-                                int k0, int32_t* __restrict__ bad) {
-  const FrontDev f = fr[level[blockIdx.x]];
-  if (k0 >= f.ns) return;
-  const int n = f.ns + f.nb;
-  const int nbk = min(ND_NB, f.ns - k0);
-  __shared__ double D[ND_NB][ND_NB + 1];
-  double* A = F + f.off;
-  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
-    const int i = t / nbk, j = t % nbk;
-    D[i][j] = A[(long long)(k0 + i) * n + (k0 + j)];
-  }
-  __syncthreads();
-  __shared__ double inv;
+// In-place Cholesky of the nbk x nbk block D (lower part used, zero padded to
+// ND_NB) and M = L^-1 (zero padded), by the whole CTA: right-looking with
+// reciprocal pivots; trailing updates over the lower triangle only.  (FP64
+// throughput is per SM sub-partition, so the CTA's warps share the work.)
+__device__ void nd_chol_inv_block(double (*D)[ND_NB + 1], double (*M)[ND_NB + 1], double* invd, int nbk,
+                                  int32_t* bad) {
   for (int k = 0; k < nbk; ++k) {
     if (threadIdx.x == 0) {
       double d = D[k][k];
@@ -253,65 +244,114 @@ __global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __re
       }
       d = sqrt(d);
       D[k][k] = d;
-      inv = 1.0 / d;
+      invd[k] = 1.0 / d;
     }
     __syncthreads();
+    const double inv = invd[k];
     for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) D[i][k] *= inv;
     __syncthreads();
     const int m = nbk - k - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      const int i = k + 1 + t / m, j = k + 1 + t % m;
-      if (j <= i) D[i][j] -= D[i][k] * D[j][k];
+    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
+      int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((i + 1) * (i + 2) / 2 <= t) ++i;
+      else if (i * (i + 1) / 2 > t) --i;
+      const int j = t - i * (i + 1) / 2;
+      D[k + 1 + i][k + 1 + j] = fma(-D[k + 1 + i][k], D[k + 1 + j][k], D[k + 1 + i][k + 1 + j]);
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
-    const int i = t / nbk, j = t % nbk;
-    if (j <= i) A[(long long)(k0 + i) * n + (k0 + j)] = D[i][j];
+  for (int t = threadIdx.x; t < ND_NB * ND_NB; t += blockDim.x) {
+    const int i = t / ND_NB, j = t % ND_NB;
+    M[i][j] = (i == j && i < nbk) ? invd[i] : 0.0;
+  }
+  __syncthreads();
+  for (int i = 0; i + 1 < nbk; ++i) {
+    const int w = i + 1, tot = (nbk - i - 1) * w;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int r = i + 1 + t / w, c = t % w;
+      double v = fma(-D[r][i], M[i][c], M[r][c]);
+      if (r == i + 1) v *= invd[r];
+      M[r][c] = v;
+    }
+    __syncthreads();
   }
 }
 
-// Panel: rows r >= k1 of columns [k0, k1): A[r, :] <- A[r, :] L_kk^-T.
-__global__ void nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
-                               int k0) {
+// Factor the diagonal block [k0, k0 + nbk) of front f in place and store
+// Linv = L_kk^-1 (ND_NB x ND_NB, zero padded) in slot `slot`.
+__device__ void nd_factor_diag(const FrontDev& f, double* __restrict__ F, int k0, int32_t* bad,
+                               double* __restrict__ Linv, int slot) {
+  __shared__ double D[ND_NB][ND_NB + 1];
+  __shared__ double M[ND_NB][ND_NB + 1];
+  __shared__ double invd[ND_NB];
+  const int n = f.ns + f.nb, nbk = min(ND_NB, f.ns - k0);
+  double* A = F + f.off;
+  for (int t = threadIdx.x; t < ND_NB * ND_NB; t += blockDim.x) {
+    const int i = t / ND_NB, j = t % ND_NB;
+    D[i][j] = (i < nbk && j <= i) ? A[(long long)(k0 + i) * n + (k0 + j)] : 0.0;
+  }
+  __syncthreads();
+  nd_chol_inv_block(D, M, invd, nbk, bad);
+  double* Li = Linv + (size_t)slot * ND_NB * ND_NB;
+  for (int t = threadIdx.x; t < ND_NB * ND_NB; t += blockDim.x) {
+    const int i = t / ND_NB, j = t % ND_NB;
+    Li[t] = M[i][j];
+    if (i < nbk && j <= i) A[(long long)(k0 + i) * n + (k0 + j)] = D[i][j];
+  }
+}
+
+// First diagonal block of every front of a level (one CTA per front); the
+// later blocks are factored by the trailing update that completes them.
+__global__ void nd_potrf_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level, double* __restrict__ F,
+                                int k0, int32_t* __restrict__ bad, double* __restrict__ Linv) {
+  const FrontDev f = fr[level[blockIdx.x]];
+  if (k0 >= f.ns) return;
+  nd_factor_diag(f, F, k0, bad, Linv, blockIdx.x);
+}
+
+// Panel: rows r >= k1 of columns [k0, k1): A[r, :] <- A[r, :] L_kk^-T, as the
+// product with Linv^T.  CTA = 32 rows of one front; thread = row x 4 columns
+// (j = g, g+8, g+16, g+24: equal work per thread).
+__global__ void __launch_bounds__(256) nd_trsm_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                                       double* __restrict__ F, int k0, const double* __restrict__ Linv) {
   const FrontDev f = fr[level[blockIdx.y]];
   if (k0 >= f.ns) return;
   const int n = f.ns + f.nb;
   const int nbk = min(ND_NB, f.ns - k0);
   const int k1 = k0 + nbk;
-  __shared__ double L[ND_NB][ND_NB + 1];
-  __shared__ double invd[ND_NB];
+  const int r0 = k1 + blockIdx.x * 32;
+  if (r0 >= n + f.ns) return;
+  __shared__ double Li[ND_NB][ND_NB + 1];
+  __shared__ double Ap[32][ND_NB + 1];
   double* A = F + f.off;
-  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
-    const int i = t / nbk, j = t % nbk;
-    L[i][j] = (j <= i) ? A[(long long)(k0 + i) * n + (k0 + j)] : 0.0;
+  const double* Lg = Linv + (size_t)blockIdx.y * ND_NB * ND_NB;
+  for (int t = threadIdx.x; t < ND_NB * ND_NB; t += blockDim.x) {
+    const int i = t / ND_NB, j = t % ND_NB;
+    Li[i][j] = Lg[t];
+    const int r = r0 + i;
+    Ap[i][j] = (r < n + f.ns && j < nbk) ? A[(long long)r * n + k0 + j] : 0.0;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < nbk; j += blockDim.x) invd[j] = 1.0 / L[j][j];
-  __syncthreads();
-  const int r = k1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n + f.ns) return;
-  double x[ND_NB];
-  double* row = A + (long long)r * n + k0;
+  const int rr = threadIdx.x >> 3, g = threadIdx.x & 7;
+  const int r = r0 + rr;
 #pragma unroll
-  for (int j = 0; j < ND_NB; ++j) {
-    if (j < nbk) {
-      double s = row[j];
-      for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
-      x[j] = s * invd[j];
-    }
+  for (int q = 0; q < 4; ++q) {
+    const int j = g + 8 * q;
+    double x = 0.0;
+    for (int tt = 0; tt <= j; ++tt) x = fma(Ap[rr][tt], Li[j][tt], x);
+    if (r < n + f.ns && j < nbk) A[(long long)r * n + k0 + j] = x;
   }
-#pragma unroll
-  for (int j = 0; j < ND_NB; ++j)
-    if (j < nbk) row[j] = x[j];
 }
 
 // Trailing update: A[i][j] -= sum_{t in [k0,k1)} A[i][t] A[j][t] for rows i >= k1,
 // columns k1 <= j < n with j <= i for front rows and every j < n for the rows
-// below the front, which end as B = [L11^-T | -(L21 L11^-1)^T] (ns x n).
-// 32 x 32 tiles, 256 threads (4 outputs each).
+// below the front, which end as B = [L11^-T | -(L21 L11^-1)^T].
+// 32 x 32 tiles, 256 threads (4 outputs each).  The CTA of the first tile
+// (the next diagonal block, complete after this update) then factors that
+// block and its inverse while the other tiles are still being updated.
 __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                                                       double* __restrict__ F, int k0) {
+                                                       double* __restrict__ F, int k0, int32_t* __restrict__ bad,
+                                                       double* __restrict__ Linv) {
   const FrontDev f = fr[level[blockIdx.y]];
   if (k0 >= f.ns) return;
   const int n = f.ns + f.nb;
@@ -335,18 +375,23 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   __syncthreads();
   const int lr = threadIdx.x / 8, lc0 = (threadIdx.x % 8) * 4;
   const int gi = r0 + lr;
-  if (gi >= n + f.ns) return;
-  double acc[4] = {0, 0, 0, 0};
-  for (int kk = 0; kk < nbk; ++kk) {
-    const double a = Pi[lr][kk];
+  if (gi < n + f.ns) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int kk = 0; kk < nbk; ++kk) {
+      const double a = Pi[lr][kk];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] = fma(a, Pj[lc0 + c][kk], acc[c]);
+      for (int c = 0; c < 4; ++c) acc[c] = fma(a, Pj[lc0 + c][kk], acc[c]);
+    }
+    const int jmax = gi < n ? gi : n - 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gj = c0 + lc0 + c;
+      if (gj < n && gj <= jmax) A[(long long)gi * n + gj] -= acc[c];
+    }
   }
-  const int jmax = gi < n ? gi : n - 1;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int gj = c0 + lc0 + c;
-    if (gj < n && gj <= jmax) A[(long long)gi * n + gj] -= acc[c];
+  if (tix == 0 && k1 < f.ns) {   // lookahead: the next diagonal block is final now
+    __syncthreads();
+    nd_factor_diag(f, F, k1, bad, Linv, blockIdx.y);
   }
 }
 
@@ -683,6 +728,7 @@ struct NdDevice {
   std::vector<int> level_count, level_maxns, level_maxn, level_maxtiles_trsm, level_maxtiles_syrk;
   int32_t* bad = nullptr;
   int* err = nullptr;   // set by a solve kernel whose staging copy timed out
+  double* linv = nullptr;   // [fronts of the widest level][32 x 32] inverses of the diagonal blocks
 };
 
 static std::unordered_map<const romb_ctx*, NdDevice> g_nd;
@@ -824,6 +870,11 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.counter, nf)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.err, 1)) != ROMB_OK) return s;
+  {
+    size_t widest = 1;
+    for (const auto& lv : plan.levels) widest = std::max(widest, lv.size());
+    if ((s = romb_alloc_t(c, &D.linv, widest * ND_NB * ND_NB)) != ROMB_OK) return s;
+  }
   ROMB_CUDA(cudaMemset(D.err, 0, 4));
   D.nfronts = nf;
   ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
@@ -921,15 +972,17 @@ romb_status coarse_factor(romb_ctx* c) {
     ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     const int mns = D.level_maxns[l], mn = D.level_maxn[l];
+    if (mns > 0) {
+      nd_potrf_kernel<<<nfl, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, 0, D.bad, D.linv); ++c->launches;
+    }
     for (int k0 = 0; k0 < mns; k0 += ND_NB) {
-      nd_potrf_kernel<<<nfl, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad); ++c->launches;
       const int rows = mn + mns - k0, cols = mn - k0;
       if (rows > 0 && cols > 0) {
-        dim3 g1((rows + 127) / 128, nfl);
-        nd_trsm_kernel<<<g1, 128, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0); ++c->launches;
+        dim3 g1((rows + 31) / 32, nfl);
+        nd_trsm_kernel<<<g1, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.linv); ++c->launches;
         const int ntr = (rows + 31) / 32, ntc = (cols + 31) / 32;
         dim3 g2(ntr * ntc, nfl);
-        nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0); ++c->launches;
+        nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad, D.linv); ++c->launches;
       }
       ROMB_CUDA(cudaGetLastError());
     }
@@ -963,10 +1016,10 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st) {
   NdDevice& D = g_nd[c];
-  ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, c->stream));
-  ROMB_CUDA(cudaMemsetAsync(D.counter, 0, 4 * (size_t)D.nfronts, c->stream));
+  ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, st));
+  ROMB_CUDA(cudaMemsetAsync(D.counter, 0, 4 * (size_t)D.nfronts, st));
   const int L = (int)D.level_ids.size();
   auto small_shape = [&](int l, int* stride, int* voff) {
     *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
@@ -977,12 +1030,12 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
       int stride, voff;
       small_shape(l, &stride, &voff);
       ROMB_CUDA(launch_pdl(nd_fwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
-                           8 * ND_WPC * (size_t)stride, c->stream, (const FrontDev*)D.fr,
+                           8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
                            (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
                            (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, stride, voff, D.err));
       ++c->launches;
     } else if (D.fwd_n[l]) {
-      ROMB_CUDA(launch_pdl(nd_fwd_tile_kernel, D.fwd_n[l], 256, 0, c->stream, (const FrontDev*)D.fr,
+      ROMB_CUDA(launch_pdl(nd_fwd_tile_kernel, D.fwd_n[l], 256, 0, st, (const FrontDev*)D.fr,
                            (const NdTile*)D.fwd_tiles[l], (const double*)D.F, (const int*)D.idx,
                            (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, D.zpart, D.counter, D.err));
       ++c->launches;
@@ -993,14 +1046,14 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out) {
       int stride, voff;
       small_shape(l, &stride, &voff);
       ROMB_CUDA(launch_pdl(nd_bwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
-                           8 * ND_WPC * (size_t)stride, c->stream, (const FrontDev*)D.fr,
+                           8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
                            (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
                            (const double*)D.sbuf, d_out, stride, voff, D.err));
       ++c->launches;
     } else if (D.bwd_n[l]) {
       const int rb = D.bwd_rpw[l], rstride = (D.level_maxn[l] + 2 + 1) & ~1;
       const size_t sm = 8 * ((size_t)rb * rstride + D.level_maxn[l]);
-      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, sm, c->stream, (const FrontDev*)D.fr,
+      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, sm, st, (const FrontDev*)D.fr,
                            (const NdRows*)D.bwd_rows[l], (const double*)D.F, (const int*)D.idx,
                            (const double*)D.sbuf, d_out, rb, rstride, D.err));
       ++c->launches;

@@ -68,52 +68,6 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
   }
 }
 
-// y_loc = M_c v_loc with M_c a dense symmetric nU x nU cell matrix (S or D F D),
-// v_loc gathered from the skeleton; optionally c_loc = Phi^T v_loc.
-// One half-warp per cell, 16 lanes over the rows (nU = 8p <= 64 rows).
-template <bool COARSE>
-__global__ void __launch_bounds__(256) cell_matvec_kernel(int ncells, int NU, const double* __restrict__ M,
-                                                           const int* __restrict__ umap, const double* __restrict__ v,
-                                                           double* __restrict__ yloc, const double* __restrict__ Phi,
-                                                           double* __restrict__ cloc) {
-  __shared__ double sv[16][64];
-  const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
-  const long long cell0 = (long long)blockIdx.x * 16 + slot;
-  const bool active = cell0 < ncells;
-  const long long cell = active ? cell0 : 0;
-  for (int u = hl; u < NU; u += 16) {
-    const int g = active ? umap[cell * NU + u] : -1;
-    sv[slot][u] = g >= 0 ? v[g] : 0.0;
-  }
-  __syncwarp();
-  if (!active) return;
-  const double* Mc = M + cell * NU * NU;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int nrow = (NU + 15 - hl) >> 4;   // rows hl, hl+16, ...
-#pragma unroll 4
-  for (int k = 0; k < NU; ++k) {
-    const double vk = sv[slot][k];
-    const double* col = Mc + k * NU + hl;   // symmetric: column k = row k
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i < nrow) acc[i] = fma(col[16 * i], vk, acc[i]);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (i < nrow) yloc[cell * NU + hl + 16 * i] = acc[i];
-  if (COARSE) {
-    const double* Pc = Phi + cell * NU * 20;
-    double a0 = 0.0, a1 = 0.0;
-    for (int u = 0; u < NU; ++u) {
-      const double vu = sv[slot][u];
-      a0 = fma(Pc[u * 20 + hl], vu, a0);
-      if (hl < 4) a1 = fma(Pc[u * 20 + 16 + hl], vu, a1);
-    }
-    cloc[cell * 20 + hl] = a0;
-    if (hl < 4) cloc[cell * 20 + 16 + hl] = a1;
-  }
-}
-
 // y_loc = M_c v_loc for every cell (M_c a dense symmetric nU x nU cell matrix:
 // S, or D F D), and with COARSE also c_loc = Phi_c^T v_loc.  Persistent CTAs
 // take the cells blockIdx.x, blockIdx.x + gridDim.x, ...; each streams its
@@ -123,19 +77,26 @@ __global__ void __launch_bounds__(256) cell_matvec_kernel(int ncells, int NU, co
 // FP64 instruction has all its lanes busy.  One barrier per cell releases the
 // stage and publishes the next cell's gathered v.
 #define CA_STAGES 3
+// modes: y = M v; y = M v and c = Phi^T v; c = Phi^T v only
+#define CA_MATVEC 0
+#define CA_BOTH 1
+#define CA_RESTRICT 2
 template <int P>
 struct CellApplyShape {
   static constexpr int NU = 8 * P, WARPS = (NU + 15) / 16, THREADS = 32 * WARPS;
-  static constexpr int stage_bytes(bool coarse) { return NU * NU * 8 + (coarse ? NU * 20 * 8 : 0) + NU * 4; }
+  static constexpr int stage_bytes(int mode) {
+    return (mode != CA_RESTRICT ? NU * NU * 8 : 0) + (mode != CA_MATVEC ? NU * 20 * 8 : 0) + NU * 4;
+  }
 };
 
-template <int P, bool COARSE>
+template <int P, int MODE>
 __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
     int ncells, const double* __restrict__ M, const int* __restrict__ umap, const double* __restrict__ v,
     double* __restrict__ yloc, const double* __restrict__ Phi, double* __restrict__ cloc, int* __restrict__ err) {
   using Sh = CellApplyShape<P>;
+  constexpr bool HAS_M = MODE != CA_RESTRICT, COARSE = MODE != CA_MATVEC;
   constexpr int NU = Sh::NU, H = NU / 2, NT = Sh::THREADS;
-  constexpr int MB = NU * NU * 8, PB = COARSE ? NU * 20 * 8 : 0, SB = MB + PB + NU * 4;
+  constexpr int MB = HAS_M ? NU * NU * 8 : 0, PB = COARSE ? NU * 20 * 8 : 0, SB = MB + PB + NU * 4;
   extern __shared__ __align__(16) unsigned char ring[];
   __shared__ uint64_t full[CA_STAGES];
   __shared__ double sv[2][NU];
@@ -148,7 +109,7 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
     unsigned char* st = ring + (size_t)(j % CA_STAGES) * SB;
     uint64_t* bar = &full[j % CA_STAGES];
     mbar_expect_tx(bar, SB);
-    bulk_g2s(st, M + cell * NU * NU, MB, bar);
+    if (HAS_M) bulk_g2s(st, M + cell * NU * NU, MB, bar);
     if (COARSE) bulk_g2s(st + MB, Phi + cell * NU * 20, PB, bar);
     bulk_g2s(st + MB + PB, umap + cell * NU, NU * 4, bar);
   };
@@ -178,14 +139,16 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
     const double* Ms = reinterpret_cast<const double*>(st);
     const double* x = sv[j & 1];
     // y = M_c v: lane (r, q) sums k in [q H, q H + H) of M[k][r] v[k] (M symmetric)
-    double acc = 0.0;
-    if (r < NU) {
-      const double* mk = Ms + q * H * NU + r;
+    if (HAS_M) {
+      double acc = 0.0;
+      if (r < NU) {
+        const double* mk = Ms + q * H * NU + r;
 #pragma unroll 8
-      for (int k = 0; k < H; ++k) acc = fma(mk[k * NU], x[q * H + k], acc);
+        for (int k = 0; k < H; ++k) acc = fma(mk[k * NU], x[q * H + k], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+      if (q == 0 && r < NU) yloc[cell * NU + r] = acc;
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-    if (q == 0 && r < NU) yloc[cell * NU + r] = acc;
     if (COARSE) {
       // c = Phi^T v: thread (j, part) sums a quarter of the slots
       const double* Ps = reinterpret_cast<const double*>(st + MB);
@@ -430,51 +393,59 @@ static int grid_for(const romb_ctx* c, long long n) {
 // z = S_BDDC^-1 r  (Algorithm 1)
 // prepare = true (outside stream capture): set the shared-memory limit and size
 // the persistent grid (resident CTAs per SM x SMs); prepare = false: launch.
-template <int P, bool COARSE>
+template <int P, int MODE>
 static romb_status cell_apply_p(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
-                                double* cloc) {
+                                double* cloc, int grid_override) {
   using Sh = CellApplyShape<P>;
-  const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(COARSE);
+  const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(MODE);
   if (prepare) {
-    ROMB_CUDA(cudaFuncSetAttribute(cell_apply_kernel<P, COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ROMB_CUDA(cudaFuncSetAttribute(cell_apply_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
     int per_sm = 0;
-    ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_apply_kernel<P, COARSE>, Sh::THREADS, smem));
-    c->ca_grid[COARSE] = std::max(1, std::min(c->ncells, std::max(1, per_sm) * c->sms));
+    ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_apply_kernel<P, MODE>, Sh::THREADS, smem));
+    c->ca_grid[MODE] = std::max(1, std::min(c->ncells, std::max(1, per_sm) * c->sms));
     return ROMB_OK;
   }
-  cell_apply_kernel<P, COARSE><<<c->ca_grid[COARSE], Sh::THREADS, smem, c->stream>>>(
+  const int grid = grid_override > 0 ? std::min(grid_override, c->ca_grid[MODE]) : c->ca_grid[MODE];
+  cell_apply_kernel<P, MODE><<<grid, Sh::THREADS, smem, c->stream>>>(
       c->ncells, M, c->d_ucell_map, v, yloc, c->d_Phi, cloc, c->d_pcg_err);
   ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
-template <bool COARSE>
+template <int MODE>
 static romb_status cell_apply(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
-                              double* cloc) {
+                              double* cloc, int grid_override = 0) {
   switch (c->p) {
-    case 3: return cell_apply_p<3, COARSE>(c, prepare, M, v, yloc, cloc);
-    case 4: return cell_apply_p<4, COARSE>(c, prepare, M, v, yloc, cloc);
-    case 5: return cell_apply_p<5, COARSE>(c, prepare, M, v, yloc, cloc);
-    case 6: return cell_apply_p<6, COARSE>(c, prepare, M, v, yloc, cloc);
-    case 7: return cell_apply_p<7, COARSE>(c, prepare, M, v, yloc, cloc);
-    case 8: return cell_apply_p<8, COARSE>(c, prepare, M, v, yloc, cloc);
+    case 3: return cell_apply_p<3, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 4: return cell_apply_p<4, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 5: return cell_apply_p<5, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 6: return cell_apply_p<6, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 7: return cell_apply_p<7, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 8: return cell_apply_p<8, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
   }
   return ROMB_E_ARG;
 }
 
 static romb_status precondition(romb_ctx* c, const CellParams& P, const double* r, double* z, double* yloc,
                                 double* cloc) {
-  const int cb = (c->ncells + 15) / 16;
-  romb_status s0 = cell_apply<true>(c, false, c->d_G, r, yloc, cloc);
-  if (s0 != ROMB_OK) return s0;
+  // restriction c = Phi^T r, then the coarse correction on the side stream
+  // while the fine part y = D F D r runs here; join before the prolongation
+  romb_status s = cell_apply<CA_RESTRICT>(c, false, nullptr, r, nullptr, cloc);
+  if (s != ROMB_OK) return s;
   double* zc = c->d_coarse;
   double* gc = c->d_coarse + c->ncoarse_all;
-  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->stream>>>(c->d_cowner, c->ncoarse_all, cloc, zc); ++c->launches;
+  ROMB_CUDA(cudaEventRecord(c->evfork, c->stream));
+  ROMB_CUDA(cudaStreamWaitEvent(c->side, c->evfork, 0));
+  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->side>>>(c->d_cowner, c->ncoarse_all, cloc, zc); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
-  romb_status s = coarse_solve(c, zc, gc);
-  if (s != ROMB_OK) return s;
+  if ((s = coarse_solve(c, zc, gc, c->side)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaEventRecord(c->evjoin, c->side));
+  // two CTAs per SM: the rest of each SM stays free for the coarse chain
+  if ((s = cell_apply<CA_MATVEC>(c, false, c->d_G, r, yloc, nullptr, 2 * c->sms)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaStreamWaitEvent(c->stream, c->evjoin, 0));
+  const int cb = (c->ncells + 15) / 16;
   cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc); ++c->launches;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, z); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
@@ -482,7 +453,7 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
 }
 
 static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
-  romb_status s0 = cell_apply<false>(c, false, c->d_S, v, yloc, nullptr);
+  romb_status s0 = cell_apply<CA_MATVEC>(c, false, c->d_S, v, yloc, nullptr);
   if (s0 != ROMB_OK) return s0;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
@@ -609,8 +580,8 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
     // the loop (or, where the driver cannot build it, one iteration) is captured
     // once per factorisation and replayed
     if (!c->pcg_graph) {
-      if ((s = cell_apply<true>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
-      if ((s = cell_apply<false>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<CA_MATVEC>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<CA_RESTRICT>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
       // ROMB_PCG_HOST_LOOP=1 keeps the loop on the host (one graph launch per
       // iteration): profilers cannot replay kernels inside conditional nodes.
       const char* hl = getenv("ROMB_PCG_HOST_LOOP");

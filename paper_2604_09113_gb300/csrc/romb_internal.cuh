@@ -159,7 +159,11 @@ struct romb_ctx {
   double* d_cloc = nullptr;     // [cells][20] coarse restriction Psi^T D r
   double* d_yloc = nullptr;     // [cells][nU] cell-local PCG scratch
   int* d_pcg_err = nullptr;     // set by a PCG cell kernel whose staging copy timed out
-  int ca_grid[2] = {0, 0};      // persistent grid of the cell operator kernels (S, D F D + Phi^T)
+  int ca_grid[3] = {0, 0, 0};   // persistent grid of the cell operator kernels per mode
+  // second stream (highest priority) for the coarse correction, which runs
+  // concurrently with the fine part of the preconditioner; fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t evfork = nullptr, evjoin = nullptr;
   cudaGraphExec_t pcg_graph = nullptr;   // captured PCG iteration (per factorisation)
   long long pcg_graph_launches = 0;
   bool pcg_device_loop = false;          // the graph holds the whole loop (conditional while node)
@@ -199,7 +203,7 @@ romb_status launch_assemble_tc(romb_ctx* c);
 romb_status launch_factor(romb_ctx* c);
 romb_status coarse_build(romb_ctx* c);      // symbolic (once per lattice shape)
 romb_status coarse_factor(romb_ctx* c);     // numeric
-romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out);
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st);
 romb_status coarse_solve_check(romb_ctx* c);   // staging timeouts of the solve kernels
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
