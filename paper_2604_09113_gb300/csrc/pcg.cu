@@ -442,8 +442,8 @@ static romb_status precondition(romb_ctx* c, const CellParams& P, const double* 
   ROMB_CUDA(cudaGetLastError());
   if ((s = coarse_solve(c, zc, gc, c->side)) != ROMB_OK) return s;
   ROMB_CUDA(cudaEventRecord(c->evjoin, c->side));
-  // two CTAs per SM: the rest of each SM stays free for the coarse chain
-  if ((s = cell_apply<CA_MATVEC>(c, false, c->d_G, r, yloc, nullptr, 2 * c->sms)) != ROMB_OK) return s;
+  // one CTA per SM: the rest of each SM stays free for the coarse chain
+  if ((s = cell_apply<CA_MATVEC>(c, false, c->d_G, r, yloc, nullptr, c->sms)) != ROMB_OK) return s;
   ROMB_CUDA(cudaStreamWaitEvent(c->stream, c->evjoin, 0));
   const int cb = (c->ncells + 15) / 16;
   cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc); ++c->launches;
