@@ -34,6 +34,9 @@ CONFIG = 3
 SAMPLE_NX = SAMPLE_NY = 16      # bounded CPU sample per reference-arm step
 BASE_NX = BASE_NY = 24          # bounded CPU sample of the cpu_baseline leg (~15 s)
 FP64_PEAK_GFLOPS = 1250.0       # nominal dense FP64 rate of GB300 (profiling recipe)
+# DRAM bytes (read + write) per cell of the local factor kernel, from an ncu
+# capture of the 132 x 132 p = 6 launch (profiles/factor_kernel_132x132_p6.md)
+FACTOR_TRAFFIC_PER_CELL = (692683520 + 1426905088) / 17424
 
 
 def args_parse():
@@ -188,6 +191,68 @@ def factor_flops(p: int) -> float:
     return f
 
 
+def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
+    """FP64 FMAs of one coarse solve: both sweeps apply every front's
+    B = [L11^-T | -(L21 L11^-1)^T] once (ns(ns+1)/2 + ns nb entries).  The
+    fronts are those of the library's geometric nested dissection: coarse DoFs
+    on vertices (2) and edges (3), rectangles bisected across the longer side
+    down to 2 x 2 cells; separator DoFs of a rectangle are eliminated there,
+    DoFs on its internal sides are its update rows; clamped DoFs are absent."""
+    def vdir(vx, vy):
+        return ((dmask & 1) and vx == 0) or ((dmask & 2) and vx == nx) or ((dmask & 4) and vy == 0) or \
+            ((dmask & 8) and vy == ny)
+
+    def groups(x0, x1, y0, y1):
+        out = []
+        for py in range(2 * y0, 2 * y1 + 1):
+            for px in range(2 * x0, 2 * x1 + 1):
+                ex, ey = px % 2 == 0, py % 2 == 0
+                if not ex and not ey:
+                    continue
+                if ex and ey:
+                    if not vdir(px // 2, py // 2):
+                        out.append((px, py, 2))
+                elif ey:
+                    vy = py // 2
+                    if not ((vy == 0 and dmask & 4) or (vy == ny and dmask & 8)):
+                        out.append((px, py, 3))
+                else:
+                    vx = px // 2
+                    if not ((vx == 0 and dmask & 1) or (vx == nx and dmask & 2)):
+                        out.append((px, py, 3))
+        return out
+
+    total = 0.0
+    stack = [(0, nx, 0, ny)]
+    while stack:
+        x0, x1, y0, y1 = stack.pop()
+        w, h = x1 - x0, y1 - y0
+        leaf = w <= 2 and h <= 2
+        xm = x0 + w // 2 if (not leaf and w >= h) else -1
+        ym = y0 + h // 2 if (not leaf and w < h) else -1
+        ns = nb = 0
+        for px, py, nd in groups(x0, x1, y0, y1):
+            if (px == 2 * x0 and x0 > 0) or (px == 2 * x1 and x1 < nx) or (py == 2 * y0 and y0 > 0) or \
+                    (py == 2 * y1 and y1 < ny):
+                nb += nd
+            elif leaf or (xm >= 0 and px == 2 * xm) or (ym >= 0 and py == 2 * ym):
+                ns += nd
+        total += 2.0 * (ns * (ns + 1) / 2 + ns * nb)
+        if not leaf:
+            if xm >= 0:
+                stack += [(x0, xm, y0, y1), (xm, x1, y0, y1)]
+            else:
+                stack += [(x0, x1, y0, ym), (x0, x1, ym, y1)]
+    return total
+
+
+def pcg_cell_fma(p: int) -> float:
+    """FP64 FMAs per cell and PCG iteration: S p (nU^2), D F D r on its non-zero
+    (nU-8)^2 block, Phi^T r and Phi g (2 nU 20)."""
+    NU = 8 * p
+    return NU * NU + (NU - 8) ** 2 + 2 * NU * 20
+
+
 def assembly_flops(p: int, n_r: int) -> float:
     nB = (p + 1) ** 2
     pairs = nB * (nB + 1) // 2
@@ -325,25 +390,26 @@ def run_ours(a):
         e2e = {"value": world * lat.ncells / (ems / 1e3), "unit": "cells/s", "ms_per_step": ems,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(u_host.nbytes)}
 
-    # dominant kernel and its roofline (measured phase times on the context stream)
+    # roofline of the dominant single kernel (the local factor kernel; the PCG
+    # phase is ~40 small kernels per iteration), from its CUDA-event time on the
+    # context stream, plus the PCG phase as a whole against the same FP64 peak
     names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery"]
-    dom = int(np.argmax(ph[:6]))
     n_r = max(s.n_r for s in LI.rom_specs(CONFIG))
-    roof = None
-    if names[dom] == "local_factor":
-        fl = factor_flops(lat.p) * lat.ncells
-        roof = {"kernel": "factor_kernel<6> (+ktot)", "bound": "alu", "achieved": fl / (ph[dom] / 1e3) / 1e9,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": None}
-    elif names[dom] == "contraction" and form == "fp64":
-        fl = assembly_flops(lat.p, n_r) * lat.ncells
-        roof = {"kernel": "assemble_fp64_kernel", "bound": "alu", "achieved": fl / (ph[dom] / 1e3) / 1e9,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": None}
-    else:
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s (FP64)", "traffic": None}
-    if roof["achieved"] is not None:
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["peak_source"] = "nominal FP64 rate of the profiling recipe"
+    fl = factor_flops(lat.p) * lat.ncells
+    roof = {"kernel": f"factor_kernel<{lat.p}>", "bound": "alu", "achieved": fl / (ph[2] / 1e3) / 1e9,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": (FACTOR_TRAFFIC_PER_CELL * lat.ncells
+                                                                         if FACTOR_TRAFFIC_PER_CELL else None),
+            "units": f"{lat.ncells} cells x {factor_flops(lat.p):.0f} flop", "peak_source":
+            "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64 rate of the profiling recipe)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    pcg_fl = iters[-1] * 2.0 * (pcg_cell_fma(lat.p) * lat.ncells +
+                                coarse_solve_fma(lat.nx, lat.ny, int(lat.dirichlet_mask)))
+    roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": pcg_fl / (ph[4] / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s (FP64)", "iterations": iters[-1]}
+    roof_pcg["frac"] = roof_pcg["achieved"] / roof_pcg["peak"]
+    if form == "fp64":
+        fa = assembly_flops(lat.p, n_r) * lat.ncells
+        roof_pcg["assembly_fp64"] = {"achieved": fa / (ph[1] / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
@@ -357,7 +423,7 @@ def run_ours(a):
             "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
                        "cells": lat.ncells, "p": lat.p, "assembly_form": form,
                        "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
-            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_pcg": roof_pcg,
             "cpu_baseline": cpu, "pcg_iters": iters[-1],
             "phase_ms": {n: float(v) for n, v in zip(names + ["copies", "total"], ph)},
             "offline_train_s": train_s, "accuracy": acc or None,
