@@ -106,6 +106,10 @@ __device__ inline float tf32_round_dev(float f) {
   return __uint_as_float(u);
 }
 
+// NS = ceil(n_r / 32) lane slots per reduced coefficient: FP64 instructions
+// with every lane predicated off still occupy the FP64 pipe, so the slot
+// count is a compile-time constant.
+template <int NS>
 __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, const int* __restrict__ list, int count,
                                                      const double* __restrict__ ctrl, const double* __restrict__ mu,
                                                      double* __restrict__ theta, double* __restrict__ chat,
@@ -135,32 +139,40 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
   __syncwarp();
   // lambda_t = sum_{g2 g3 g4} w2 w3 w4 (sum_{g1} w1[g1] At[g][t]): lanes over t
   const int nr = R.n_r;
-  double acc[4][TH_CELLS];
-  for (int s = 0; s < 4; ++s)
-    for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
-  const int n3 = n1 * n1 * n1;
-  for (int g234 = 0; g234 < n3; ++g234) {
-    const int g2 = g234 % n1, g3 = (g234 / n1) % n1, g4 = g234 / (n1 * n1);
-    double inner[4][TH_CELLS];
-    for (int s = 0; s < 4; ++s)
-      for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = 0.0;
-    for (int g1 = 0; g1 < n1; ++g1) {
-      const double* Ag = R.At + (long long)(g234 * n1 + g1) * nr;
+  double acc[NS][TH_CELLS];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int t = lane + 32 * s;
-        if (t < nr) {
-          const double a = __ldg(Ag + t);
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
+  const int n2 = n1 * n1;
+  for (int g34 = 0; g34 < n2; ++g34) {
+    const int g3 = g34 % n1, g4 = g34 / n1;
+    double w34[TH_CELLS];
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) w34[j] = wts[warp][j][2][g3] * wts[warp][j][3][g4];
+    for (int g2 = 0; g2 < n1; ++g2) {
+      const int g234 = g34 * n1 + g2;
+      double inner[NS][TH_CELLS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = 0.0;
+      for (int g1 = 0; g1 < n1; ++g1) {
+        const double* Ag = R.At + (long long)(g234 * n1 + g1) * nr;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const int t = lane + 32 * s;
+          const double a = t < nr ? __ldg(Ag + t) : 0.0;
 #pragma unroll
           for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = fma(a, wts[warp][j][0][g1], inner[s][j]);
         }
       }
-    }
 #pragma unroll
-    for (int j = 0; j < TH_CELLS; ++j) {
-      const double w234 = wts[warp][j][1][g2] * wts[warp][j][2][g3] * wts[warp][j][3][g4];
+      for (int j = 0; j < TH_CELLS; ++j) {
+        const double w234 = wts[warp][j][1][g2] * w34[j];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) acc[s][j] = fma(w234, inner[s][j], acc[s][j]);
+        for (int s = 0; s < NS; ++s) acc[s][j] = fma(w234, inner[s][j], acc[s][j]);
+      }
     }
   }
   for (int j = 0; j < TH_CELLS; ++j) {
@@ -170,7 +182,8 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
     float* hi = th_hi + 128 * (long long)c;
     float* lo = th_lo + 128 * (long long)c;
     if (lane == 0) th[0] = P.rho;
-    for (int s = 0; s < 4; ++s) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
       const int t = lane + 32 * s;
       if (t < nr) th[1 + t] = (1.0 - P.rho) * acc[s][j];
     }
@@ -355,9 +368,12 @@ romb_status launch_theta(romb_ctx* c) {
       gll_nodes01(Rr.r, g);
       for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
       const int per_block = 4 * TH_CELLS;
-      theta_kernel<<<(counts[f] + per_block - 1) / per_block, 128, 0, c->stream>>>(
-          P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat, c->d_theta_hi,
-          c->d_theta_lo, c->d_chat32, c->d_flags); ++c->launches;
+      const int grid = (counts[f] + per_block - 1) / per_block;
+      const int ns = (Rr.n_r + 31) / 32;
+      auto k = ns <= 1 ? theta_kernel<1> : ns == 2 ? theta_kernel<2> : ns == 3 ? theta_kernel<3> : theta_kernel<4>;
+      k<<<grid, 128, 0, c->stream>>>(P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat,
+                                     c->d_theta_hi, c->d_theta_lo, c->d_chat32, c->d_flags);
+      ++c->launches;
       ROMB_CUDA(cudaGetLastError());
     }
     start += counts[f];
