@@ -137,8 +137,7 @@ struct FrontDev {
   int ybuf_off;      // forward-solve update vector (nb)
   int wbuf_off;      // extend-add sources of each of the n rows (gsrc)
   int sbuf_off;      // forward result y_s = L11^-1 w_s (ns)
-  int ntiles;        // forward tiles of the front (tiled levels)
-  long long zoff;    // forward partial sums: [chunks][n]
+  long long bt_off;  // B^T (n x ns, row-major) of fronts on the row-kernel levels, -1 elsewhere
 };
 
 }  // namespace
@@ -404,12 +403,6 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
 // is x_s = B [y_s; x_b].  Both read the ns x n rows below the front once.
 // w is gathered from the right-hand side and the children's update vectors
 // through gsrc (up to two sources per row, in a fixed order).
-#define ND_RC 64   // rows (separator DoFs) per forward chunk
-#define ND_CT 64   // columns per forward tile
-
-struct NdTile {
-  int front, chunk, col0;
-};
 struct NdRows {
   int front, row0;
 };
@@ -432,7 +425,6 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 #define ND_WPC 4     // warps (fronts) per CTA in the small-front kernels
-#define ND_SROW 66   // shared row stride of a staged forward tile (64 + alignment slack, even)
 
 // Small fronts: one warp per front.  Shared memory per warp: `stride`
 // doubles = the B block (ns x n, contiguous in the front, staged by one bulk
@@ -467,12 +459,23 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
   int first = 0;
   if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
   __syncwarp();   // the barrier is initialised before any lane waits on it
+  // static gather indices before the wait: afterwards only the data loads remain
+  int pid[ND_SMALL_N / 32];
+  int2 pgs[ND_SMALL_N / 32];
+#pragma unroll
+  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
+    const int t = lane + 32 * k;
+    pid[k] = (has && t < ns) ? idx[f.idx_off + t] : -1;
+    pgs[k] = (has && t < n) ? gsrc[f.wbuf_off + t] : make_int2(-1, -1);
+  }
   pdl_trigger();
   pdl_wait();
   if (!has) return;
-  const int* id = idx + f.idx_off;
-  const int2* gs = gsrc + f.wbuf_off;
-  for (int t = lane; t < n; t += 32) w[t] = (t < ns ? rhs[id[t]] : 0.0) + nd_gather_row(gs[t], ybuf);
+#pragma unroll
+  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
+    const int t = lane + 32 * k;
+    if (t < n) w[t] = (pid[k] >= 0 ? rhs[pid[k]] : 0.0) + nd_gather_row(pgs[k], ybuf);
+  }
   const bool ok = mbar_wait(&bar[warp], 0);
   if (!__all_sync(0xffffffffu, ok)) {
     if (lane == 0) atomicExch(err, 1);
@@ -516,11 +519,21 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
   int first = 0;
   if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
   __syncwarp();   // the barrier is initialised before any lane waits on it
+  int pid[ND_SMALL_N / 32];
+#pragma unroll
+  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
+    const int c = lane + 32 * k;
+    pid[k] = (has && c < n) ? idx[f.idx_off + c] : 0;
+  }
   pdl_trigger();
   pdl_wait();
   if (!has) return;
   const int* id = idx + f.idx_off;
-  for (int c = lane; c < n; c += 32) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
+#pragma unroll
+  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
+    const int c = lane + 32 * k;
+    if (c < n) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[pid[k]];
+  }
   const bool ok = mbar_wait(&bar[warp], 0);
   if (!__all_sync(0xffffffffu, ok)) {
     if (lane == 0) atomicExch(err, 1);
@@ -543,164 +556,168 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
   }
 }
 
-// Tiled forward step: a CTA owns ND_RC rows x ND_CT columns of one front's B,
-// staged row by row (one bulk copy per row, issued by warp 0); thread =
-// column x row group (rows rg, rg+4, ...).  Fronts with one row chunk write y_s
-// and u_b directly; otherwise every CTA writes its partial z and the last CTA
-// of the front (counted with an atomic after a fence) sums the partials in
-// chunk order.
-__global__ void __launch_bounds__(256) nd_fwd_tile_kernel(const FrontDev* __restrict__ fr, const NdTile* __restrict__ tiles,
-                                                           const double* __restrict__ F, const int* __restrict__ idx,
-                                                           const int2* __restrict__ gsrc, const double* __restrict__ rhs,
-                                                           double* __restrict__ ybuf, double* __restrict__ sbuf,
-                                                           double* __restrict__ zpart, int* __restrict__ counter,
-                                                           int* __restrict__ err) {
-  __shared__ __align__(16) double S[ND_RC * ND_SROW];
-  __shared__ double ws[ND_RC];
-  __shared__ double red[4][ND_CT + 1];
-  __shared__ int first[ND_RC];
-  __shared__ uint64_t bar;
-  __shared__ int is_last;
-  const NdTile T = tiles[blockIdx.x];
-  const FrontDev f = fr[T.front];
+// ---- levels of wide fronts: row kernels over contiguous rows ----
+// Forward z = B^T w_s runs over the rows of B^T (n x ns, stored after the
+// factorisation), backward x_s = B [y_s; x_b] over the rows of B: a CTA owns
+// `rb` consecutive rows, staged by one bulk copy, and its 8 warps take R rows
+// each with P = 32 / R lanes per row (lane = row x column phase, phases summed
+// by shuffles), P chosen per level so that every lane has ~16 FMAs.
+struct NdRowShape {
+  int P, rb, ld;   // lanes per row, rows per CTA, shared row stride (doubles, even)
+};
+
+__global__ void nd_transpose_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
+                                    const double* __restrict__ F, double* __restrict__ BT) {
+  __shared__ double tile[32][33];
+  const FrontDev f = fr[level[blockIdx.z]];
   const int ns = f.ns, n = ns + f.nb;
-  const int e0 = T.chunk * ND_RC, ne = max(0, min(ND_RC, ns - e0));
-  const int nc = min(ND_CT, n - T.col0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    const double* B = F + f.off + (long long)(n + e0) * n + T.col0;
-    Span16 sp[2];
-    uint32_t mine = 0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int r = lane + 32 * k;
-      sp[k] = span16(B + (long long)r * n, r < ne ? nc : 0);
-      mine += sp[k].bytes;
-      if (r < ne) first[r] = sp[k].first;
-    }
-    const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
-    if (lane == 0) {
-      mbar_init(&bar, 1);
-      mbar_init_fence();
-      mbar_expect_tx(&bar, total);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (sp[k].bytes) bulk_g2s(S + (lane + 32 * k) * ND_SROW, sp[k].start, sp[k].bytes, &bar);
+  const int e0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  if (e0 >= ns || c0 >= n) return;
+  const double* B = F + f.off + (long long)n * n;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int e = e0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (e < ns && c < n) ? B[(long long)e * n + c] : 0.0;
   }
-  pdl_trigger();
-  pdl_wait();
-  const int col = threadIdx.x & (ND_CT - 1), rg = threadIdx.x / ND_CT;
-  const int c = T.col0 + col;
-  const int* id = idx + f.idx_off;
-  const int2* gs = gsrc + f.wbuf_off;
-  const int nch = max(1, (ns + ND_RC - 1) / ND_RC);
-  double wc = 0.0;   // w at this column's update row (single-chunk fronts)
-  if (nch == 1 && rg == 0 && c >= ns && c < n) wc = nd_gather_row(gs[c], ybuf);
-  for (int r = threadIdx.x; r < ne; r += blockDim.x) ws[r] = rhs[id[e0 + r]] + nd_gather_row(gs[e0 + r], ybuf);
-  __syncthreads();   // bar initialised, first[] and ws written
-  const bool ok = mbar_wait(&bar, 0);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-    return;
-  }
-  double z0 = 0.0, z1 = 0.0;
-  int r = rg;
-  for (; r + 4 < ne; r += 8) {
-    z0 = fma(S[r * ND_SROW + first[r] + col], ws[r], z0);
-    z1 = fma(S[(r + 4) * ND_SROW + first[r + 4] + col], ws[r + 4], z1);
-  }
-  if (r < ne) z0 = fma(S[r * ND_SROW + first[r] + col], ws[r], z0);
-  red[rg][col] = z0 + z1;
   __syncthreads();
-  double z = 0.0;
-  if (rg == 0) z = (red[0][col] + red[1][col]) + (red[2][col] + red[3][col]);
-  if (nch == 1) {
-    if (rg == 0 && c < n) {
-      if (c < ns) sbuf[f.sbuf_off + c] = z;
-      else ybuf[f.ybuf_off + c - ns] = wc + z;
-    }
-    return;
-  }
-  if (rg == 0 && c < n) zpart[f.zoff + (long long)T.chunk * n + c] = z;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(counter + T.front, 1) == f.ntiles - 1;
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < nch; ++k) s += __ldcg(zpart + f.zoff + (long long)k * n + cc);
-    if (cc < ns) sbuf[f.sbuf_off + cc] = s;
-    else ybuf[f.ybuf_off + cc - ns] = nd_gather_row(gs[cc], ybuf) + s;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, e = e0 + threadIdx.x;
+    if (c < n && e < ns) BT[f.bt_off + (long long)c * ns + e] = tile[threadIdx.x][i];
   }
 }
 
-// Tiled backward step: a CTA owns rb rows of one front's B (rb = 1, 2, 4 or 8;
-// 8 / rb warps per row, lanes over columns), staged by one bulk copy per row
-// into rows of `rstride` doubles; the columns left of the block's first row
-// are zero in L11^-T and skipped.
-__global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
-                                                           const double* __restrict__ F, const int* __restrict__ idx,
-                                                           const double* __restrict__ sbuf, double* __restrict__ x,
-                                                           int rb, int rstride, int* __restrict__ err) {
-  extern __shared__ __align__(16) double sh[];   // [rb][rstride] rows, then v [n]
-  __shared__ double red[8];
-  __shared__ int first[8];
+__device__ __forceinline__ void nd_stage_rows(const double* src, long long len, double* dst, uint64_t* bar, int* first) {
+  const Span16 sp = span16(src, len);
+  *first = sp.first;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    mbar_expect_tx(bar, sp.bytes);
+    if (sp.bytes) bulk_g2s(dst, sp.start, sp.bytes, bar);
+  }
+}
+
+__global__ void __launch_bounds__(256) nd_fwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
+                                                           NdRowShape sh_, const double* __restrict__ BT,
+                                                           const int* __restrict__ idx, const int2* __restrict__ gsrc,
+                                                           const double* __restrict__ rhs, double* __restrict__ ybuf,
+                                                           double* __restrict__ sbuf, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sh[];   // rows [rb][ns] (+slack), then w_s [ns]
   __shared__ uint64_t bar;
+  __shared__ int first_s;
   const NdRows it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int ns = f.ns, n = ns + f.nb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cs = it.row0 & ~31;
-  double* v = sh + (size_t)rb * rstride;
-  if (warp == 0) {
-    const int e = it.row0 + lane;
-    const bool mine_row = lane < rb && e < ns;
-    const Span16 sp = span16(F + f.off + (long long)(n + (mine_row ? e : 0)) * n + cs, mine_row ? n - cs : 0);
-    if (lane < rb) first[lane] = sp.first;
-    const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
-    if (lane == 0) {
-      mbar_init(&bar, 1);
-      mbar_init_fence();
-      mbar_expect_tx(&bar, total);
-    }
-    __syncwarp();
-    if (sp.bytes) bulk_g2s(sh + (size_t)lane * rstride, sp.start, sp.bytes, &bar);
+  const int nr = min(sh_.rb, n - it.row0);
+  double* ws = sh + ((((long long)nr * ns + 2) + 1) & ~1LL);
+  int first = 0;
+  nd_stage_rows(BT + f.bt_off + (long long)it.row0 * ns, (long long)nr * ns, sh, &bar, &first);
+  if (threadIdx.x == 0) first_s = first;
+  const int* id = idx + f.idx_off;
+  const int2* gs = gsrc + f.wbuf_off;
+  int pid[4];
+  int2 pgs[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    pid[k] = e < ns ? id[e] : 0;
+    pgs[k] = e < ns ? gs[e] : make_int2(-1, -1);
   }
+  const int P = sh_.P, R = 32 / P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane / P, h = lane % P;
+  const int j = warp * R + r;       // row within the CTA
+  const int c = it.row0 + j;        // row of B^T = column of B
+  const int2 gsc = (j < nr && h == 0 && c >= ns) ? gs[c] : make_int2(-1, -1);
   pdl_trigger();
   pdl_wait();
-  const int* id = idx + f.idx_off;
-  for (int c = cs + threadIdx.x; c < n; c += blockDim.x) v[c - cs] = c < ns ? sbuf[f.sbuf_off + c] : x[id[c]];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    if (e < ns) ws[e] = rhs[pid[k]] + nd_gather_row(pgs[k], ybuf);
+  }
+  for (int e = threadIdx.x + 1024; e < ns; e += blockDim.x) ws[e] = rhs[id[e]] + nd_gather_row(gs[e], ybuf);
+  const double wb = nd_gather_row(gsc, ybuf);
   __syncthreads();
   const bool ok = mbar_wait(&bar, 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
-  const int wpr = 8 / rb, j = warp / wpr, k = warp % wpr;
-  const int e = it.row0 + j;
-  double s0 = 0.0, s1 = 0.0;
-  if (e < ns) {
-    const double* row = sh + (size_t)j * rstride + first[j];
-    const int w = n - cs, step = 32 * wpr;
-    int cc = 32 * k + lane;
-    for (; cc + step < w; cc += 2 * step) {
-      s0 = fma(row[cc], v[cc], s0);
-      s1 = fma(row[cc + step], v[cc + step], s1);
+  double z = 0.0;
+  if (j < nr) {
+    const double* row = sh + first_s + (long long)j * ns;
+    const int emax = c < ns ? c : ns - 1;   // L11^-T is upper triangular: B^T row c < ns has e <= c
+    double z1 = 0.0;
+    int e = h;
+    for (; e + P <= emax; e += 2 * P) {
+      z = fma(row[e], ws[e], z);
+      z1 = fma(row[e + P], ws[e + P], z1);
     }
-    if (cc < w) s0 = fma(row[cc], v[cc], s0);
+    if (e <= emax) z = fma(row[e], ws[e], z);
+    z += z1;
   }
-  const double s = warp_sum(s0 + s1);
-  if (lane == 0) red[warp] = s;
+  for (int o = 1; o < P; o <<= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+  if (j < nr && h == 0) {
+    if (c < ns) sbuf[f.sbuf_off + c] = z;
+    else ybuf[f.ybuf_off + c - ns] = wb + z;
+  }
+}
+
+__global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
+                                                           NdRowShape sh_, const double* __restrict__ F,
+                                                           const int* __restrict__ idx, const double* __restrict__ sbuf,
+                                                           double* __restrict__ x, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sh[];   // rows [rb][n] (+slack), then v [n]
+  __shared__ uint64_t bar;
+  __shared__ int first_s;
+  const NdRows it = items[blockIdx.x];
+  const FrontDev f = fr[it.front];
+  const int ns = f.ns, n = ns + f.nb;
+  const int nr = min(sh_.rb, ns - it.row0);
+  double* v = sh + ((((long long)nr * n + 2) + 1) & ~1LL);
+  int first = 0;
+  nd_stage_rows(F + f.off + (long long)(n + it.row0) * n, (long long)nr * n, sh, &bar, &first);
+  if (threadIdx.x == 0) first_s = first;
+  const int* id = idx + f.idx_off;
+  int pid[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int cc = threadIdx.x + 256 * k;
+    pid[k] = (cc >= ns && cc < n) ? id[cc] : 0;
+  }
+  const int P = sh_.P, R = 32 / P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane / P, h = lane % P;
+  const int j = warp * R + r;
+  const int e = it.row0 + j;
+  pdl_trigger();
+  pdl_wait();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int cc = threadIdx.x + 256 * k;
+    if (cc < n) v[cc] = cc < ns ? sbuf[f.sbuf_off + cc] : x[pid[k]];
+  }
+  for (int cc = threadIdx.x + 1024; cc < n; cc += blockDim.x) v[cc] = cc < ns ? sbuf[f.sbuf_off + cc] : x[id[cc]];
   __syncthreads();
-  if (threadIdx.x < rb && it.row0 + threadIdx.x < ns) {
-    double t = 0.0;
-    for (int q = 0; q < wpr; ++q) t += red[threadIdx.x * wpr + q];
-    x[id[it.row0 + threadIdx.x]] = t;
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
   }
+  double s = 0.0;
+  if (j < nr) {
+    const double* row = sh + first_s + (long long)j * n;
+    double s1 = 0.0;
+    int cc = (e / P) * P + h;   // columns left of row e are zero in L11^-T
+    for (; cc + P < n; cc += 2 * P) {
+      s = fma(row[cc], v[cc], s);
+      s1 = fma(row[cc + P], v[cc + P], s1);
+    }
+    if (cc < n) s = fma(row[cc], v[cc], s);
+    s += s1;
+  }
+  for (int o = 1; o < P; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (j < nr && h == 0) x[id[e]] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -711,12 +728,12 @@ struct NdDevice {
   int2* gsrc = nullptr;
   int4* asrc = nullptr;
   double* sbuf = nullptr;
-  double* zpart = nullptr;
-  int* counter = nullptr;
+  double* BT = nullptr;       // B^T of the fronts on row-kernel levels
   int nfronts = 0;
-  std::vector<NdTile*> fwd_tiles;
-  std::vector<NdRows*> bwd_rows;
-  std::vector<int> fwd_n, bwd_n, bwd_rpw, level_small, level_maxb;
+  std::vector<NdRows*> fwd_rows, bwd_rows;
+  std::vector<int> fwd_n, bwd_n, level_small, level_maxb;
+  std::vector<NdRowShape> fwd_shape, bwd_shape;
+  std::vector<size_t> fwd_smem, bwd_smem;
   int* idx = nullptr;
   int* children = nullptr;
   int* emap = nullptr;
@@ -756,7 +773,7 @@ romb_status coarse_build(romb_ctx* c) {
   // host arrays
   std::vector<FrontDev> fd(nf);
   std::vector<int> idx, children, emap, cells, cell_pos((size_t)c->ncells * 20, -1);
-  long long off = 0, ztot = 0;
+  long long off = 0, bttot = 0;
   int ybuf = 0, wbuf_tot = 0, sbuf_tot = 0;
   for (int i = 0; i < nf; ++i) {
     const NdFront& F = plan.fronts[i];
@@ -781,9 +798,7 @@ romb_status coarse_build(romb_ctx* c) {
     d.sbuf_off = sbuf_tot;
     sbuf_tot += F.ns;
     d.emap_off = -1;
-    d.zoff = ztot;
-    ztot += (long long)std::max(1, (F.ns + ND_RC - 1) / ND_RC) * n;
-    d.ntiles = 0;
+    d.bt_off = -1;
   }
   // extend-add positions of each front's update rows in its parent
   for (int i = 0; i < nf; ++i) {
@@ -866,8 +881,7 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.gsrc, gsrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.asrc, asrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
-  if ((s = romb_alloc_t(c, &D.zpart, (size_t)std::max(1LL, ztot))) != ROMB_OK) return s;
-  if ((s = romb_alloc_t(c, &D.counter, nf)) != ROMB_OK) return s;
+
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.err, 1)) != ROMB_OK) return s;
   {
@@ -879,8 +893,6 @@ romb_status coarse_build(romb_ctx* c) {
   D.nfronts = nf;
   ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
   ROMB_CUDA(cudaMemcpy(D.asrc, asrc.data(), sizeof(int4) * asrc.size(), cudaMemcpyHostToDevice));
-  // partial sums of skipped (zero) tiles are never written: they stay 0
-  ROMB_CUDA(cudaMemset(D.zpart, 0, 8 * (size_t)std::max(1LL, ztot)));
   ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
   if (!children.empty())
     ROMB_CUDA(cudaMemcpy(D.children, children.data(), 4 * children.size(), cudaMemcpyHostToDevice));
@@ -904,54 +916,66 @@ romb_status coarse_build(romb_ctx* c) {
     for (int f : lv) mb = std::max(mb, plan.fronts[f].ns * (plan.fronts[f].ns + plan.fronts[f].nb));
     D.level_maxb.push_back(mb);
     D.level_small.push_back(mn <= ND_SMALL_N && mb + mn + 8 <= ND_SMALL_SMEM);
-    // backward rows per CTA: as many (<= 8) as keep the staged rows within 96 KB
-    int rpw = 8;
-    while (rpw > 1 && (size_t)rpw * (mn + 2) * 8 > 96 * 1024) rpw >>= 1;
-    D.bwd_rpw.push_back(rpw);
-    // work lists of the tiled solve kernels
-    std::vector<NdTile> ft;
-    std::vector<NdRows> br;
-    for (int f : lv) {
-      const NdFront& Fr = plan.fronts[f];
-      const int n = Fr.ns + Fr.nb, nch = std::max(1, (Fr.ns + ND_RC - 1) / ND_RC);
-      int cnt = 0;
-      for (int k = 0; k < nch; ++k)
-        for (int c0 = 0; c0 < n; c0 += ND_CT) {
-          if (c0 + ND_CT <= k * ND_RC) continue;   // below the diagonal of L11^-T: zero
-          ft.push_back({f, k, c0});
-          ++cnt;
-        }
-      fd[f].ntiles = cnt;
-      for (int e = 0; e < Fr.ns; e += rpw) br.push_back({f, e});
+    // row-kernel shapes: P lanes per row with ~16 FMAs each, 8 warps x 32/P rows per CTA
+    auto shape_for = [](int len, int width) {
+      NdRowShape q;
+      q.P = 1;
+      while (q.P < 32 && q.P * 16 < len) q.P <<= 1;
+      q.rb = 8 * (32 / q.P);
+      while (q.rb > 8 && (size_t)q.rb * width * 8 > 96 * 1024) q.rb >>= 1;
+      q.ld = width;
+      return q;
+    };
+    const NdRowShape fs = shape_for(mns, mns), bs = shape_for(mn, mn);
+    D.fwd_shape.push_back(fs);
+    D.bwd_shape.push_back(bs);
+    D.fwd_smem.push_back(8 * ((((size_t)fs.rb * mns + 2) + 1 & ~(size_t)1) + mns));
+    D.bwd_smem.push_back(8 * ((((size_t)bs.rb * mn + 2) + 1 & ~(size_t)1) + mn));
+    std::vector<NdRows> fr_items, br_items;
+    if (!D.level_small.back()) {
+      for (int f : lv) {
+        const NdFront& Fr = plan.fronts[f];
+        const int n = Fr.ns + Fr.nb;
+        fd[f].bt_off = bttot;
+        bttot += (long long)n * Fr.ns;
+        for (int r0 = 0; r0 < n; r0 += fs.rb) fr_items.push_back({f, r0});
+        for (int e0 = 0; e0 < Fr.ns; e0 += bs.rb) br_items.push_back({f, e0});
+      }
     }
-    NdTile* dt = nullptr;
-    NdRows* dr = nullptr;
-    if (!ft.empty()) {
-      if ((s = romb_alloc_t(c, &dt, ft.size())) != ROMB_OK) return s;
-      ROMB_CUDA(cudaMemcpy(dt, ft.data(), sizeof(NdTile) * ft.size(), cudaMemcpyHostToDevice));
+    for (auto* pr : {&fr_items, &br_items}) {
+      NdRows* dptr = nullptr;
+      if (!pr->empty()) {
+        if ((s = romb_alloc_t(c, &dptr, pr->size())) != ROMB_OK) return s;
+        ROMB_CUDA(cudaMemcpy(dptr, pr->data(), sizeof(NdRows) * pr->size(), cudaMemcpyHostToDevice));
+      }
+      if (pr == &fr_items) {
+        D.fwd_rows.push_back(dptr);
+        D.fwd_n.push_back((int)pr->size());
+      } else {
+        D.bwd_rows.push_back(dptr);
+        D.bwd_n.push_back((int)pr->size());
+      }
     }
-    if (!br.empty()) {
-      if ((s = romb_alloc_t(c, &dr, br.size())) != ROMB_OK) return s;
-      ROMB_CUDA(cudaMemcpy(dr, br.data(), sizeof(NdRows) * br.size(), cudaMemcpyHostToDevice));
-    }
-    D.fwd_tiles.push_back(dt);
-    D.fwd_n.push_back((int)ft.size());
-    D.bwd_rows.push_back(dr);
-    D.bwd_n.push_back((int)br.size());
   }
+  // B^T storage (+2 doubles: bulk copies read 16-byte aligned spans)
+  if ((s = romb_alloc_t(c, &D.BT, (size_t)bttot + 2)) != ROMB_OK) return s;
   // front descriptors last: they carry the tile counts
   ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
   const int small_smem = 8 * ND_WPC * ND_SMALL_SMEM;
-  size_t rows_smem = 0;   // staged rows + one vector of the widest tiled level
-  for (size_t l = 0; l < D.level_maxn.size(); ++l) {
-    const size_t rstride = (D.level_maxn[l] + 2 + 1) & ~1;
-    rows_smem = std::max(rows_smem, 8 * ((size_t)D.bwd_rpw[l] * rstride + D.level_maxn[l]));
-  }
-  if (rows_smem > 227 * 1024) {
-    romb_set_error("nested dissection: a coarse front is too wide for the staged backward solve");
+  size_t fmax = 0, bmax = 0;
+  for (size_t l = 0; l < D.level_small.size(); ++l)
+    if (!D.level_small[l]) {
+      fmax = std::max(fmax, D.fwd_smem[l]);
+      bmax = std::max(bmax, D.bwd_smem[l]);
+    }
+  if (fmax > 227 * 1024 || bmax > 227 * 1024) {
+    romb_set_error("nested dissection: a coarse front is too wide for the staged solve kernels");
     return ROMB_E_ARG;
   }
-  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(fmax, 16)));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(bmax, 16)));
   ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
   ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
   return ROMB_OK;
@@ -984,6 +1008,11 @@ romb_status coarse_factor(romb_ctx* c) {
         dim3 g2(ntr * ntc, nfl);
         nd_syrk_kernel<<<g2, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, k0, D.bad, D.linv); ++c->launches;
       }
+      ROMB_CUDA(cudaGetLastError());
+    }
+    if (!D.level_small[l] && mns > 0) {   // B^T for the forward row kernel
+      const dim3 gt((mn + 31) / 32, (mns + 31) / 32, nfl);
+      nd_transpose_kernel<<<gt, dim3(32, 8), 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.BT); ++c->launches;
       ROMB_CUDA(cudaGetLastError());
     }
   }
@@ -1019,7 +1048,6 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, st));
-  ROMB_CUDA(cudaMemsetAsync(D.counter, 0, 4 * (size_t)D.nfronts, st));
   const int L = (int)D.level_ids.size();
   auto small_shape = [&](int l, int* stride, int* voff) {
     *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
@@ -1035,9 +1063,9 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
                            (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, stride, voff, D.err));
       ++c->launches;
     } else if (D.fwd_n[l]) {
-      ROMB_CUDA(launch_pdl(nd_fwd_tile_kernel, D.fwd_n[l], 256, 0, st, (const FrontDev*)D.fr,
-                           (const NdTile*)D.fwd_tiles[l], (const double*)D.F, (const int*)D.idx,
-                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, D.zpart, D.counter, D.err));
+      ROMB_CUDA(launch_pdl(nd_fwd_rows_kernel, D.fwd_n[l], 256, D.fwd_smem[l], st, (const FrontDev*)D.fr,
+                           (const NdRows*)D.fwd_rows[l], D.fwd_shape[l], (const double*)D.BT, (const int*)D.idx,
+                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, D.err));
       ++c->launches;
     }
   }
@@ -1051,11 +1079,9 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
                            (const double*)D.sbuf, d_out, stride, voff, D.err));
       ++c->launches;
     } else if (D.bwd_n[l]) {
-      const int rb = D.bwd_rpw[l], rstride = (D.level_maxn[l] + 2 + 1) & ~1;
-      const size_t sm = 8 * ((size_t)rb * rstride + D.level_maxn[l]);
-      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, sm, st, (const FrontDev*)D.fr,
-                           (const NdRows*)D.bwd_rows[l], (const double*)D.F, (const int*)D.idx,
-                           (const double*)D.sbuf, d_out, rb, rstride, D.err));
+      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, D.bwd_smem[l], st, (const FrontDev*)D.fr,
+                           (const NdRows*)D.bwd_rows[l], D.bwd_shape[l], (const double*)D.F, (const int*)D.idx,
+                           (const double*)D.sbuf, d_out, D.err));
       ++c->launches;
     }
   }
