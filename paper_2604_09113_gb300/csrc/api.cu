@@ -240,6 +240,7 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   if (R.loaded) {
     romb_free_ptr(c, R.U64);
     romb_free_ptr(c, R.Utiles);
+    romb_free_ptr(c, R.Utiles16);
     romb_free_ptr(c, R.A);
     romb_free_ptr(c, R.At);
     R = RombRom();
@@ -263,6 +264,12 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
     tc_tile_rom(Uh, n_half, K, R.kpad, tiles, &R.ntiles);
     if ((s = romb_alloc_persist(c, (void**)&R.Utiles, 4 * tiles.size())) != ROMB_OK) return s;
     ROMB_CUDA(cudaMemcpy(R.Utiles, tiles.data(), 4 * tiles.size(), cudaMemcpyHostToDevice));
+    // and the BF16 hi / lo tiles of the same rows
+    R.kpad16 = (K + 15) / 16 * 16;
+    std::vector<uint16_t> t16;
+    tc_tile_rom_bf16(Uh, n_half, K, R.kpad16, t16);
+    if ((s = romb_alloc_persist(c, (void**)&R.Utiles16, 2 * t16.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(R.Utiles16, t16.data(), 2 * t16.size(), cudaMemcpyHostToDevice));
   }
   R.loaded = true;
   R.family = family;

@@ -19,6 +19,9 @@
 // the next tile.  Every wait is bounded: on timeout the kernel records an error
 // and all roles leave their loops; tensor memory is freed before exit.
 //
+// The BF16 form (kind::f16 with BF16 A and B, K = 16 per instruction) uses the
+// same pipeline and epilogue on BF16 hi / lo splits (~16-bit products).
+//
 // Roles (256 threads): warp 0 allocates tensor memory and issues the copies,
 // warp 1 issues the MMAs (one thread), warps 4-7 run the epilogue (TMEM lanes
 // 0-127 = the 128 cells of the tile).
@@ -86,6 +89,42 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// BF16 bits of f, round to nearest even (finite inputs)
+__host__ __device__ inline uint16_t bf16_bits(float f) {
+  uint32_t u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(f);
+#else
+  memcpy(&u, &f, 4);
+#endif
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+__host__ __device__ inline float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -157,8 +196,14 @@ __device__ __forceinline__ dfl df_from_double(double d) {
 __host__ __device__ inline uint32_t canon_off(int row, int k, int KT) {
   return (uint32_t)((row >> 3) * (KT * 32) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
+// the same for 16-bit elements: core matrices of 8 rows x 8 elements, SBO = KT * 16
+__host__ __device__ inline uint32_t canon_off16(int row, int k, int KT) {
+  return (uint32_t)((row >> 3) * (KT * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
 
+template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) {
+  constexpr uint32_t ES = BF ? 2 : 4;   // operand element size
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accfull[2], bar_accempty[2], bar_done;
   __shared__ uint32_t tmem_base_s;
@@ -166,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KT = P.KT;
-  const uint32_t a_bytes = TC_M * KT * 4, b_bytes = TC_N * KT * 4;
+  const uint32_t a_bytes = TC_M * KT * ES, b_bytes = TC_N * KT * ES;
   const uint32_t stage_bytes = 2 * b_bytes + 2 * TC_N * 8;
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* A_hi = base;
@@ -206,9 +251,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
       h = P.th_hi[cell * 128 + k];
       l = P.th_lo[cell * 128 + k];
     }
-    const uint32_t off = canon_off(row, k, KT);
-    *(float*)(A_hi + off) = h;
-    *(float*)(A_lo + off) = l;
+    if (BF) {
+      const float x = h + l;   // theta in TF32 hi + lo (zero padded), re-split into BF16
+      const uint16_t bh = bf16_bits(x), bl = bf16_bits(x - bf16_value(bh));
+      const uint32_t off = canon_off16(row, k, KT);
+      *(uint16_t*)(A_hi + off) = bh;
+      *(uint16_t*)(A_lo + off) = bl;
+    } else {
+      const uint32_t off = canon_off(row, k, KT);
+      *(float*)(A_hi + off) = h;
+      *(float*)(A_lo + off) = l;
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
@@ -238,8 +291,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(TC_M, TC_N);
-      const uint32_t sbo = (uint32_t)KT * 32, lbo = 128;
+      const uint32_t idesc = BF ? idesc_bf16(TC_M, TC_N) : idesc_tf32(TC_M, TC_N);
+      const uint32_t sbo = (uint32_t)KT * 8 * ES, lbo = 128;
       const uint32_t a_hi = smem_u32(A_hi), a_lo = smem_u32(A_lo);
       for (int t = 0; t < T && !s_abort; ++t) {
         const int s = t % S, b = t & 1;
@@ -256,11 +309,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         tc_fence_after();
         const uint32_t b_hi = smem_u32(Bst + (size_t)s * stage_bytes), b_lo = b_hi + b_bytes;
         const uint32_t d = tmem + (uint32_t)(b * TC_N);
-        for (int kk = 0; kk < KT / 8; ++kk) {
+        // one instruction covers two core matrices along K (32 bytes): 8 TF32 or 16 BF16
+        for (int kk = 0; kk < KT / (32 / (int)ES); ++kk) {
           const uint32_t ko = (uint32_t)kk * 256;
-          mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, kk > 0);
-          mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
-          mma_tf32(d, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+          if (BF) {
+            mma_bf16(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, kk > 0);
+            mma_bf16(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
+            mma_bf16(d, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+          } else {
+            mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, kk > 0);
+            mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
+            mma_tf32(d, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+          }
         }
         mma_commit(&bar_empty[s]);
         mma_commit(&bar_accfull[b]);
@@ -378,9 +438,41 @@ void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad
   }
 }
 
+// The same tiles with BF16 hi / lo of rows 2.. (16-bit canonical layout) and
+// rows 0 and 1 as float pairs; same byte layout per stage otherwise.
+void tc_tile_rom_bf16(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<uint16_t>& tiles) {
+  const int ncol_tile = TC_N;
+  const long long T = (n_half + ncol_tile - 1) / ncol_tile;
+  const size_t tile_elems = (size_t)ncol_tile * kpad;               // one BF16 tile
+  const size_t stage_elems = 2 * tile_elems + 2 * ncol_tile * 4;    // + 2 rows of float pairs (4 halves each)
+  tiles.assign((size_t)T * stage_elems, 0);
+  for (long long t = 0; t < T; ++t) {
+    uint16_t* base = tiles.data() + (size_t)t * stage_elems;
+    float* rows01 = (float*)(base + 2 * tile_elems);   // [2][TC_N][hi, lo]
+    for (int n = 0; n < ncol_tile; ++n) {
+      const long long col = t * ncol_tile + n;
+      if (col >= n_half) continue;
+      for (int rr = 0; rr < 2; ++rr) {
+        const double x = rr < K ? U[(size_t)rr * n_half + col] : 0.0;
+        const float h = (float)x;
+        rows01[2 * (rr * ncol_tile + n)] = h;
+        rows01[2 * (rr * ncol_tile + n) + 1] = (float)(x - (double)h);
+      }
+      for (int k = 2; k < K; ++k) {
+        const double x = U[(size_t)k * n_half + col];
+        const uint16_t h = bf16_bits((float)x);
+        const size_t off = canon_off16(n, k, kpad) / 2;
+        base[off] = h;
+        base[tile_elems + off] = bf16_bits((float)(x - (double)bf16_value(h)));
+      }
+    }
+  }
+}
+
 romb_status launch_assemble_tc(romb_ctx* c) {
-  if (c->prec != ROMB_FP32_SPLIT) {
-    romb_set_error("only the TF32 split form of the tensor-core assembly is available");
+  const bool bf = c->prec == ROMB_BF16_SPLIT;
+  if (c->prec != ROMB_FP32_SPLIT && !bf) {
+    romb_set_error("tensor-core assembly: unknown split form");
     return ROMB_E_ARG;
   }
   int* d_err = (int*)c->d_red + 32;
@@ -391,15 +483,16 @@ romb_status launch_assemble_tc(romb_ctx* c) {
   for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
+    const int kp = bf ? R.kpad16 : R.kpad;
     if (KT < 0) {
-      KT = R.kpad;
+      KT = kp;
       T = R.ntiles;
-    } else if (KT != R.kpad || T != R.ntiles) {
+    } else if (KT != kp || T != R.ntiles) {
       romb_set_error("tensor-core assembly: all reduced models of one lattice must share n_r");
       return ROMB_E_ARG;
     }
     TcFamily& F = P.fam[P.nfam++];
-    F.Utiles = R.Utiles;
+    F.Utiles = bf ? (const float*)R.Utiles16 : R.Utiles;
     F.list = c->d_famlist + c->famstart[f];
     F.count = c->famcount[f];
     F.mtile0 = grid;
@@ -417,7 +510,8 @@ romb_status launch_assemble_tc(romb_ctx* c) {
   P.pairs = c->d_pairs;
   P.npairs = c->nB * (c->nB + 1) / 2;
   P.err = d_err;
-  const size_t a_bytes = (size_t)TC_M * KT * 4, b_bytes = (size_t)TC_N * KT * 4;
+  const size_t es = bf ? 2 : 4;
+  const size_t a_bytes = (size_t)TC_M * KT * es, b_bytes = (size_t)TC_N * KT * es;
   const size_t stage_bytes = 2 * b_bytes + 2 * TC_N * 8;
   const size_t limit = 227 * 1024 - 1024 - 256;
   int stages = 2;
@@ -428,8 +522,9 @@ romb_status launch_assemble_tc(romb_ctx* c) {
   }
   P.stages = stages;
   const size_t smem = 1024 + 2 * a_bytes + (size_t)stages * stage_bytes;
-  ROMB_CUDA(cudaFuncSetAttribute(assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  assemble_tc_kernel<<<grid, TC_THREADS, smem, c->stream>>>(P); ++c->launches;
+  auto kern = bf ? assemble_tc_kernel<true> : assemble_tc_kernel<false>;
+  ROMB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, TC_THREADS, smem, c->stream>>>(P); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   int h_err = 0;
   ROMB_CUDA(cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, c->stream));

@@ -39,10 +39,10 @@ struct RombRom {
   double lo = 0, hi = 0;
   long long n_half = 0;        // pairs k1 <= k2 times 4 (q+1)^2 columns
   double* U64 = nullptr;       // [(n_r+1)][n_half]: row 0 = I_Pi, rows 1.. = U_r
-  float* Uhi = nullptr;        // unused (kept for layout compatibility)
-  float* Ulo = nullptr;        // unused
-  float* Utiles = nullptr;     // tensor-core operand: N-tiles of 144 columns, hi then lo, canonical layout
+  float* Utiles = nullptr;     // tensor-core operand: N-tiles of 144 columns, TF32 hi then lo, canonical layout
+  uint16_t* Utiles16 = nullptr;   // the same tiles with BF16 hi / lo (16-bit canonical layout)
   int ntiles = 0;
+  int kpad16 = 0;              // n_r+1 rounded up to the BF16 MMA K step (16)
   double* A = nullptr;         // [n_r][(r+1)^4]
   double* At = nullptr;        // [(r+1)^4][n_r]
   int kpad = 0;                // n_r+1 rounded up for the tensor-core K dimension
@@ -217,6 +217,7 @@ romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxi
 
 void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<float>& tiles,
                  int* ntiles);
+void tc_tile_rom_bf16(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<uint16_t>& tiles);
 
 // small host helpers
 inline long long tri(long long n) { return n * (n + 1) / 2; }

@@ -77,3 +77,38 @@ def test_tc_full_rank_model_from_library_trainer(tmp_path):
     print(f"rank 60: K rel error max {max(errs):.2e} median {np.median(errs):.2e}; displacement {derr:.2e}")
     assert max(errs) <= 1e-5
     assert derr <= 1e-5
+
+
+@pytest.mark.parametrize("n_r", [60])
+def test_bf16_split_form(tmp_path, n_r):
+    # kind::f16 with BF16 hi / lo splits (K = 16 per MMA): relative Frobenius
+    # error of every cell matrix <= 1e-3 against the FP64 form, and the FP64
+    # solve with those matrices converges to a displacement close to the FP64 one
+    # (weaker models than rank 60 at r = 2 give indefinite cells on this lattice
+    # in every form, FP64 included)
+    p = 6
+    paths = []
+    for fam, lo, hi in [(0, 0.18, 0.42), (1, 0.07, 0.21)]:
+        path = str(tmp_path / f"f{fam}.rom")
+        romb.romb_train(fam, 0, p, 2, n_r, lo, hi, LI.lhs(max(80, n_r + 4), lo, hi, seed=9 + fam), path)
+        paths.append(path)
+    lat = LI.lattice(20, 14, p, 4, seed=33, mu_mode="uniform", mu_range=(0.2, 0.4), cross_range=(0.08, 0.2),
+                     cross_fraction=0.5)
+    nodes = (p * lat.nx + 1) * (p * lat.ny + 1)
+    with romb.Context(0) as ctx:
+        for path in paths:
+            romb.romb_train_load(ctx.h, path)
+        K16 = _K(ctx, lat, romb.ROMB_BF16_SPLIT)
+        K64 = _K(ctx, lat, romb.ROMB_FP64)
+        errs = [_rel_fro(K16[c], K64[c]) for c in range(lat.ncells)]
+        print(f"bf16 n_r={n_r}: K rel error max {max(errs):.2e} median {np.median(errs):.2e}")
+        assert max(errs) <= 1e-3
+        assert 1e-9 < max(errs)          # a different (lower-precision) form, not the FP32 path
+        romb.romb_factor(ctx.h)
+        u64 = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-12, maxit=800)[0][0].copy()
+        _K(ctx, lat, romb.ROMB_BF16_SPLIT)
+        romb.romb_factor(ctx.h)
+        u16, its, _ = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-10, maxit=800)
+    derr = np.linalg.norm(u16[0] - u64) / np.linalg.norm(u64)
+    print(f"bf16 n_r={n_r}: displacement {derr:.2e}, iterations {its[0]}")
+    assert derr <= 1e-2
