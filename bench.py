@@ -45,7 +45,7 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32split"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32split", "bf16split"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -295,7 +295,8 @@ def run_ours(a):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MB > L2
 
     have_tc = a.precision != "fp64"
-    precisions = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT}
+    precisions = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT,
+                  "bf16split": romb.ROMB_BF16_SPLIT}
     if a.precision == "auto":
         try:
             romb.romb_assemble(ctx.h, lat, romb.ROMB_FP32_SPLIT, device_arrays=darr)
@@ -352,11 +353,20 @@ def run_ours(a):
     u_form = u_dev.clone()
     acc = {}
     if have_tc and not a.no_accuracy:
-        other = romb.ROMB_FP64 if form == "fp32split" else romb.ROMB_FP32_SPLIT
-        step(other)
-        num = torch.linalg.vector_norm(u_form - u_dev).item()
-        den = torch.linalg.vector_norm(u_dev if form == "fp32split" else u_form).item()
-        acc["disp_rel_l2_fp32split_vs_fp64"] = num / den
+        # every split form against the FP64 form, untimed, on the same lattice
+        if form == "fp64":
+            u_ref = u_form
+        else:
+            step(romb.ROMB_FP64)
+            u_ref = u_dev.clone()
+        den = torch.linalg.vector_norm(u_ref).item()
+        for name in ("fp32split", "bf16split"):
+            if name == form:
+                u_s = u_form
+            else:
+                step(precisions[name])
+                u_s = u_dev.clone()
+            acc["disp_rel_l2_%s_vs_fp64" % name] = torch.linalg.vector_norm(u_s - u_ref).item() / den
         step(prec)
 
     # end to end: pinned host inputs, host output, through the public API
@@ -419,7 +429,7 @@ def run_ours(a):
         line = {
             "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if form == "fp64" else "tf32x3+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32split": "tf32x3+f64", "bf16split": "bf16x3+f64"}[form], "data": "synthetic",
             "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
                        "cells": lat.ncells, "p": lat.p, "assembly_form": form,
                        "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
