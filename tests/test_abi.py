@@ -5,6 +5,8 @@ import importlib.util
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -41,3 +43,10 @@ def test_binding_imports_and_reports_status_strings():
             romb.romb_create(0)
         except romb.RombError as e:
             assert e.status == -2
+
+
+def test_autograd_binding_imports():
+    _build()
+    torch = pytest.importorskip("torch")
+    from paper_2604_09113_gb300.autograd import Compliance, compliance
+    assert issubclass(Compliance, torch.autograd.Function) and callable(compliance)
