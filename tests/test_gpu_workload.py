@@ -1,0 +1,155 @@
+"""The benchmarked workload at full size: 132 x 132 = 17,424 cells, p = 6,
+quartic maps, circle holes and crosses 50/50, rank-60 models per family
+trained by the library's trainer, run in the launch configuration the
+benchmark times (a caller-owned CUDA stream, lattice arrays resident on the
+device, displacement written to a device tensor, PCG rtol 1e-8).
+
+Checked against the oracle where it can compute outputs one by one, and by
+properties that hold at any size where it cannot:
+  * theta / Chat and cell matrices of a seeded sample of cells against the
+    oracle's MDEIM (Algorithm 5) and fast assembly (Algorithm 4);
+  * the ROM + fast-assembly matrices against the oracle's full trimmed
+    quadrature on a 0.1 % sample (Sec. 5 expects relative errors of order
+    1e-3 for q = 2);
+  * the split-form displacement against the FP64 form (<= 1e-6 relative L2),
+    both solved by the FP64 BDDC-PCG;
+  * global equilibrium f - K u of the returned displacement, with K the
+    library's FP64 cell matrices and f the oracle's loads, scattered here.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import lattice_inputs as LI
+from oracle import assembly, bddc as obddc, geometry as ogeo, pipeline, rom as orom
+
+from romb_testutil import unpack_upper
+
+pytestmark = pytest.mark.gpu
+romb = pytest.importorskip("paper_2604_09113_gb300")
+torch = pytest.importorskip("torch")
+
+WORKLOAD = 3          # the 132 x 132, p = 6 circle / cross lattice
+SAMPLE_SEED = 1003
+
+
+@pytest.fixture(scope="module")
+def run():
+    d = tempfile.mkdtemp(prefix="romb_full_")
+    paths, roms = [], {}
+    for spec in LI.rom_specs(WORKLOAD):
+        path = os.path.join(d, f"family{spec.family}.rom")
+        romb.romb_train(spec.family, 0, spec.p, spec.r, spec.n_r, spec.lo, spec.hi,
+                        LI.lhs(spec.n_s, spec.lo, spec.hi, seed=spec.seed), path)
+        paths.append(path)
+        R = orom.read(path)
+        roms[R.family] = R
+    lat = LI.config(WORKLOAD)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    out = {"lat": lat, "roms": roms, "nodes": nodes}
+    with torch.cuda.stream(stream):
+        darr = {"ctrl": torch.from_numpy(lat.ctrl).to(dev), "mu": torch.from_numpy(lat.mu).to(dev),
+                "family": torch.from_numpy(lat.family).to(dev),
+                "traction": torch.from_numpy(lat.traction.reshape(8).copy()).to(dev)}
+        u_dev = torch.zeros((1, nodes, 2), dtype=torch.float64, device=dev)
+        stream.synchronize()
+        with romb.Context(0, 0, stream.cuda_stream) as ctx:
+            for path in paths:
+                romb.romb_train_load(ctx.h, path)
+            for name, prec in (("split", romb.ROMB_FP32_SPLIT), ("fp64", romb.ROMB_FP64)):
+                romb.romb_assemble(ctx.h, lat, prec, device_arrays=darr)
+                romb.romb_factor(ctx.h)
+                _, its, rel = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-8, maxit=500, out=u_dev)
+                stream.synchronize()
+                out[name] = dict(u=u_dev[0].cpu().numpy().copy(), its=int(its[0]), rel=float(rel[0]),
+                                 K=romb.romb_read(ctx.h, "K").reshape(lat.ncells, -1))
+                if name == "split":
+                    out["theta"] = romb.romb_read(ctx.h, "theta").reshape(lat.ncells, -1)
+                    out["chat"] = romb.romb_read(ctx.h, "chat").reshape(lat.ncells, 9, 16)
+    return out
+
+
+def test_sampled_cells_match_oracle(run):
+    lat, roms = run["lat"], run["roms"]
+    nd = 2 * (lat.p + 1) ** 2
+    cells = LI.sample_cells(lat.ncells, 24 / lat.ncells, seed=SAMPLE_SEED)
+    Ko = pipeline.matrices_rom(lat, roms, cells=cells)
+    worst = {"split": 0.0, "fp64": 0.0, "theta": 0.0, "chat": 0.0}
+    for c in cells:
+        R = roms[int(lat.family[c])]
+        th = run["theta"][c]
+        assert th[0] == lat.rho
+        ref = (1 - lat.rho) * orom.reduced_vector(R, lat.mu[c])
+        worst["theta"] = max(worst["theta"], np.abs(th[1:1 + R.n_r] - ref).max() / np.abs(ref).max())
+        P = ogeo.cell_control_points(lat.ctrl, lat.nx, lat.m, c % lat.nx, c // lat.nx)
+        Cn = assembly.fa_coefficients(P, lat.E, lat.nu, 2).reshape(9, 16)
+        worst["chat"] = max(worst["chat"], np.abs(run["chat"][c] - Cn).max() / np.abs(Cn).max())
+        for form in ("split", "fp64"):
+            Kg = unpack_upper(run[form]["K"][c], nd)
+            worst[form] = max(worst[form], np.linalg.norm(Kg - Ko[c]) / np.linalg.norm(Ko[c]))
+    print("sampled cells, worst relative error vs oracle: " + ", ".join(f"{k} {v:.2e}" for k, v in worst.items()))
+    assert worst["theta"] <= 1e-12
+    # Chat = j J^-1 C J^-T at the interpolation nodes of quartic maps: both
+    # sides evaluate it in FP64 with different operation orders, and the
+    # Jacobian's conditioning amplifies the rounding to a few hundred ulps
+    assert worst["chat"] <= 1e-12
+    assert worst["fp64"] <= 1e-12
+    assert worst["split"] <= 1e-5
+
+
+def test_rom_against_full_quadrature(run):
+    lat = run["lat"]
+    nd = 2 * (lat.p + 1) ** 2
+    cells = LI.sample_cells(lat.ncells, 0.001, seed=SAMPLE_SEED)
+    Kf = pipeline.matrices_full(lat, cells=cells)
+    errs = [np.linalg.norm(unpack_upper(run["split"]["K"][c], nd) - Kf[c]) / np.linalg.norm(Kf[c])
+            for c in cells]
+    print(f"ROM + fast assembly vs full quadrature on {len(cells)} cells: median {np.median(errs):.2e}, "
+          f"max {max(errs):.2e}")
+    assert max(errs) <= 1e-3
+
+
+def test_split_form_displacement_within_1e6_of_fp64(run):
+    u32, u64 = run["split"]["u"], run["fp64"]["u"]
+    err = np.linalg.norm(u32 - u64) / np.linalg.norm(u64)
+    print(f"displacement: split vs FP64 form {err:.2e}; iterations {run['split']['its']} / {run['fp64']['its']}")
+    assert err <= 1e-6
+    assert run["split"]["rel"] <= 1e-8 and run["fp64"]["rel"] <= 1e-8
+    assert abs(run["split"]["its"] - run["fp64"]["its"]) <= 2
+
+
+def test_global_equilibrium(run):
+    lat = run["lat"]
+    p, nx, ny = lat.p, lat.nx, lat.ny
+    nB, nd = (p + 1) ** 2, 2 * (p + 1) ** 2
+    gnx = p * nx + 1
+    a, b = np.arange(nB) % (p + 1), np.arange(nB) // (p + 1)
+    cx, cy = np.arange(lat.ncells) % nx, np.arange(lat.ncells) // nx
+    gnode = (p * cx[:, None] + a[None, :]) + gnx * (p * cy[:, None] + b[None, :])      # [cells, nB]
+    gdof = np.stack([2 * gnode, 2 * gnode + 1], axis=2).reshape(lat.ncells, nd)          # local dof 2k + i
+    u = run["fp64"]["u"].reshape(-1)
+    ndof = u.size
+    iu = np.triu_indices(nd)
+    Ku = np.zeros(ndof)
+    for c0 in range(0, lat.ncells, 1024):
+        Kp = run["fp64"]["K"][c0:c0 + 1024]
+        Kc = np.zeros((len(Kp), nd, nd))
+        Kc[:, iu[0], iu[1]] = Kp
+        Kc[:, iu[1], iu[0]] = Kp
+        y = np.einsum("cij,cj->ci", Kc, u[gdof[c0:c0 + 1024]])
+        Ku += np.bincount(gdof[c0:c0 + 1024].ravel(), weights=y.ravel(), minlength=ndof)
+    f = np.bincount(gdof.ravel(), weights=obddc.lattice_loads(lat).ravel(), minlength=ndof)
+    gx, gy = np.arange(gnx * (p * ny + 1)) % gnx, np.arange(gnx * (p * ny + 1)) // gnx
+    m = lat.dirichlet_mask
+    clamped = ((m & 1) & (gx == 0)) | ((m >> 1 & 1) & (gx == p * nx)) | ((m >> 2 & 1) & (gy == 0)) \
+        | ((m >> 3 & 1) & (gy == p * ny))
+    free = np.repeat(~clamped.astype(bool), 2)
+    assert np.all(u.reshape(-1, 2)[clamped.astype(bool)] == 0.0)
+    res = np.linalg.norm((f - Ku)[free]) / np.linalg.norm(f[free])
+    print(f"global equilibrium: |f - K u| / |f| = {res:.2e} on {free.sum()} free DoFs")
+    # PCG stops at 1e-8 on the interface system; the interior recovery is exact
+    assert res <= 1e-7
