@@ -243,6 +243,7 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
     romb_free_ptr(c, R.Utiles16);
     romb_free_ptr(c, R.A);
     romb_free_ptr(c, R.At);
+    romb_free_ptr(c, R.At2);
     R = RombRom();
   }
   romb_status s;
@@ -256,6 +257,13 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
     for (long long g = 0; g < ngrid; ++g)
       for (int t = 0; t < n_r; ++t) At[(size_t)g * n_r + t] = A[(size_t)t * ngrid + g];
     ROMB_CUDA(cudaMemcpy(R.At, At.data(), 8 * At.size(), cudaMemcpyHostToDevice));
+    std::vector<float2> At2(At.size());
+    for (size_t i = 0; i < At.size(); ++i) {
+      const float h = (float)At[i];
+      At2[i] = make_float2(h, (float)(At[i] - (double)h));
+    }
+    if ((s = romb_alloc_persist(c, (void**)&R.At2, sizeof(float2) * At2.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(R.At2, At2.data(), sizeof(float2) * At2.size(), cudaMemcpyHostToDevice));
   }
   R.kpad = (K + 7) / 8 * 8;
   {

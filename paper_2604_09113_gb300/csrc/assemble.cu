@@ -19,6 +19,7 @@
 struct RomDev {
   const double* U64;     // [K][n_half]
   const double* At;      // [ngrid][n_r]  (transposed interpolation samples)
+  const float2* At2;     // the same as (hi, lo) FP32 pairs
   int n_r, r;
   double lo, hi;
   long long n_half;
@@ -106,16 +107,100 @@ __device__ inline float tf32_round_dev(float f) {
   return __uint_as_float(u);
 }
 
+// ---- double-float theta for the split assembly forms ----
+// The split forms consume theta rows 2.. as TF32 hi / lo pairs (~22 bits) and
+// rows 0-1 in double-float, so theta needs no more than double-float
+// precision (pairs of FP32, ~48-bit significands), which runs on the FP32
+// pipe (GB300 issues FP32 ~64x faster than FP64).  Products are error-free
+// (x.h y.h exactly as p + e via fmaf, plus the cross terms); sums are
+// compensated (two-sum, errors collected in the low word), the dot-product
+// scheme of Ogita, Rump and Oishi (2005).  __fmul_rn keeps the compiler from
+// contracting a product into a following add, which would break the
+// error-free transformations.
+struct DfPair {
+  float h, l;
+};
+__device__ __forceinline__ DfPair df_prod(float2 x, float2 y) {   // (x.x + x.y)(y.x + y.y), renormalised
+  const float p = __fmul_rn(x.x, y.x);
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  const float s = __fadd_rn(p, e);
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+// (h, l) += (a.x + a.y)(b.x + b.y), low word not renormalised
+__device__ __forceinline__ void df_dot_step(float& h, float& l, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(h, p), bb = __fsub_rn(s, h);
+  l = __fadd_rn(l, __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  h = s;
+}
+
+// lambda_t of TH_CELLS cells (lanes over t), the loop of the FP64 kernel in
+// double-float: inner sums over g1 per (g2, g3, g4), then the weighted outer sum.
+template <int NS>
+__device__ __forceinline__ void theta_contract_df(const float2* __restrict__ At2, const float2 (*wdf)[4][12],
+                                                  int lane, int n1, int nr, double (&lam)[NS][TH_CELLS]) {
+  float ah[NS][TH_CELLS], al[NS][TH_CELLS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) ah[s][j] = al[s][j] = 0.f;
+  const int n2 = n1 * n1;
+  for (int g34 = 0; g34 < n2; ++g34) {
+    const int g3 = g34 % n1, g4 = g34 / n1;
+    float2 w34[TH_CELLS];
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) {
+      const DfPair q = df_prod(wdf[j][2][g3], wdf[j][3][g4]);
+      w34[j] = make_float2(q.h, q.l);
+    }
+    for (int g2 = 0; g2 < n1; ++g2) {
+      const int g234 = g34 * n1 + g2;
+      float sh[NS][TH_CELLS], sc[NS][TH_CELLS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int j = 0; j < TH_CELLS; ++j) sh[s][j] = sc[s][j] = 0.f;
+      for (int g1 = 0; g1 < n1; ++g1) {
+        const float2* Ag = At2 + (long long)(g234 * n1 + g1) * nr;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const int t = lane + 32 * s;
+          const float2 a = t < nr ? __ldg(Ag + t) : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < TH_CELLS; ++j) df_dot_step(sh[s][j], sc[s][j], a, wdf[j][0][g1]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < TH_CELLS; ++j) {
+        const DfPair q = df_prod(wdf[j][1][g2], w34[j]);
+        const float2 w234 = make_float2(q.h, q.l);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) df_dot_step(ah[s][j], al[s][j], make_float2(sh[s][j], sc[s][j]), w234);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int j = 0; j < TH_CELLS; ++j) lam[s][j] = (double)ah[s][j] + (double)al[s][j];
+}
+
 // NS = ceil(n_r / 32) lane slots per reduced coefficient: FP64 instructions
 // with every lane predicated off still occupy the FP64 pipe, so the slot
 // count is a compile-time constant.
-template <int NS>
+template <int NS, bool DF>
 __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, const int* __restrict__ list, int count,
                                                      const double* __restrict__ ctrl, const double* __restrict__ mu,
                                                      double* __restrict__ theta, double* __restrict__ chat,
                                                      float* __restrict__ th_hi, float* __restrict__ th_lo,
                                                      float* __restrict__ chat32, int32_t* __restrict__ flags) {
   __shared__ double wts[4][TH_CELLS][4][12];   // [warp][cell][param][node]
+  __shared__ float2 wdf[DF ? 4 : 1][TH_CELLS][4][12];   // the same as (hi, lo) FP32 pairs (DF only)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int first = (blockIdx.x * 4 + warp) * TH_CELLS;
   const int r = R.r, n1 = r + 1;
@@ -135,45 +220,59 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
       for (int i = 0; i < n1; ++i) v[i] = 0.0;
     }
     for (int i = 0; i < n1; ++i) wts[warp][j][d][i] = v[i];
+    if constexpr (DF)
+      for (int i = 0; i < n1; ++i) {
+        const float h = (float)v[i];
+        wdf[warp][j][d][i] = make_float2(h, (float)(v[i] - (double)h));
+      }
   }
   __syncwarp();
   // lambda_t = sum_{g2 g3 g4} w2 w3 w4 (sum_{g1} w1[g1] At[g][t]): lanes over t
   const int nr = R.n_r;
-  double acc[NS][TH_CELLS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-#pragma unroll
-    for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
   const int n2 = n1 * n1;
-  for (int g34 = 0; g34 < n2; ++g34) {
-    const int g3 = g34 % n1, g4 = g34 / n1;
-    double w34[TH_CELLS];
+  double lam[NS][TH_CELLS];
+  if constexpr (!DF) {
+    double acc[NS][TH_CELLS];
 #pragma unroll
-    for (int j = 0; j < TH_CELLS; ++j) w34[j] = wts[warp][j][2][g3] * wts[warp][j][3][g4];
-    for (int g2 = 0; g2 < n1; ++g2) {
-      const int g234 = g34 * n1 + g2;
-      double inner[NS][TH_CELLS];
+    for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int s = 0; s < NS; ++s)
+      for (int j = 0; j < TH_CELLS; ++j) acc[s][j] = 0.0;
+    for (int g34 = 0; g34 < n2; ++g34) {
+      const int g3 = g34 % n1, g4 = g34 / n1;
+      double w34[TH_CELLS];
 #pragma unroll
-        for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = 0.0;
-      for (int g1 = 0; g1 < n1; ++g1) {
-        const double* Ag = R.At + (long long)(g234 * n1 + g1) * nr;
+      for (int j = 0; j < TH_CELLS; ++j) w34[j] = wts[warp][j][2][g3] * wts[warp][j][3][g4];
+      for (int g2 = 0; g2 < n1; ++g2) {
+        const int g234 = g34 * n1 + g2;
+        double inner[NS][TH_CELLS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const int t = lane + 32 * s;
-          const double a = t < nr ? __ldg(Ag + t) : 0.0;
+        for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = fma(a, wts[warp][j][0][g1], inner[s][j]);
+          for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = 0.0;
+        for (int g1 = 0; g1 < n1; ++g1) {
+          const double* Ag = R.At + (long long)(g234 * n1 + g1) * nr;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            const int t = lane + 32 * s;
+            const double a = t < nr ? __ldg(Ag + t) : 0.0;
+#pragma unroll
+            for (int j = 0; j < TH_CELLS; ++j) inner[s][j] = fma(a, wts[warp][j][0][g1], inner[s][j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < TH_CELLS; ++j) {
+          const double w234 = wts[warp][j][1][g2] * w34[j];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) acc[s][j] = fma(w234, inner[s][j], acc[s][j]);
         }
       }
-#pragma unroll
-      for (int j = 0; j < TH_CELLS; ++j) {
-        const double w234 = wts[warp][j][1][g2] * w34[j];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) acc[s][j] = fma(w234, inner[s][j], acc[s][j]);
-      }
     }
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int j = 0; j < TH_CELLS; ++j) lam[s][j] = acc[s][j];
+  } else {
+    theta_contract_df<NS>(R.At2, wdf[warp], lane, n1, nr, lam);
   }
   for (int j = 0; j < TH_CELLS; ++j) {
     const int c = cells[j];
@@ -185,7 +284,7 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const int t = lane + 32 * s;
-      if (t < nr) th[1 + t] = (1.0 - P.rho) * acc[s][j];
+      if (t < nr) th[1 + t] = (1.0 - P.rho) * lam[s][j];
     }
     __syncwarp();
     // TF32 hi / lo split of theta, zero padded to 128 slots
@@ -363,14 +462,18 @@ romb_status launch_theta(romb_ctx* c) {
     }
     if (counts[f] > 0) {
       const RombRom& Rr = c->roms[f];
-      RomDev R{Rr.U64, Rr.At, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
+      RomDev R{Rr.U64, Rr.At, Rr.At2, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
       double g[12];
       gll_nodes01(Rr.r, g);
       for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
       const int per_block = 4 * TH_CELLS;
       const int grid = (counts[f] + per_block - 1) / per_block;
       const int ns = (Rr.n_r + 31) / 32;
-      auto k = ns <= 1 ? theta_kernel<1> : ns == 2 ? theta_kernel<2> : ns == 3 ? theta_kernel<3> : theta_kernel<4>;
+      const bool df = c->prec != ROMB_FP64;   // split forms: theta in double-float
+      auto k = df ? (ns <= 1 ? theta_kernel<1, true> : ns == 2 ? theta_kernel<2, true> : ns == 3 ? theta_kernel<3, true>
+                                                                                   : theta_kernel<4, true>)
+                  : (ns <= 1 ? theta_kernel<1, false> : ns == 2 ? theta_kernel<2, false>
+                               : ns == 3 ? theta_kernel<3, false> : theta_kernel<4, false>);
       k<<<grid, 128, 0, c->stream>>>(P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat,
                                      c->d_theta_hi, c->d_theta_lo, c->d_chat32, c->d_flags);
       ++c->launches;

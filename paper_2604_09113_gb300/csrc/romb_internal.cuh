@@ -45,6 +45,7 @@ struct RombRom {
   int kpad16 = 0;              // n_r+1 rounded up to the BF16 MMA K step (16)
   double* A = nullptr;         // [n_r][(r+1)^4]
   double* At = nullptr;        // [(r+1)^4][n_r]
+  float2* At2 = nullptr;       // the same as (hi, lo) FP32 pairs, hi + lo = At to ~48 bits (double-float theta)
   int kpad = 0;                // n_r+1 rounded up for the tensor-core K dimension
 };
 

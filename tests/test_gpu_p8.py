@@ -86,6 +86,11 @@ def test_split_forms_p8(model):
         for prec, kbound, ubound in ((romb.ROMB_FP32_SPLIT, 1e-5, 1e-5), (romb.ROMB_BF16_SPLIT, 2.0 ** -14, 1e-2)):
             Kg = _K(ctx, lat, prec)
             worst = max(_rel(unpack_upper(Kg[c], nd), Ko[c]) for c in range(lat.ncells))
+            # split forms: theta interpolated in double-float (bound as at p = 6)
+            th = romb.romb_read(ctx.h, "theta").reshape(lat.ncells, -1)
+            for c in range(lat.ncells):
+                lam = (1 - lat.rho) * orom.reduced_vector(model["R"], lat.mu[c])
+                assert np.abs(th[c, 1:1 + model["R"].n_r] - lam).max() <= 1e-11 * np.abs(lam).max(), c
             romb.romb_factor(ctx.h)
             u, its, _ = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-12, maxit=400)
             err = np.linalg.norm(u[0] - ref["u"]) / np.linalg.norm(ref["u"])

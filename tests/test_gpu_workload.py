@@ -6,8 +6,9 @@ device, displacement written to a device tensor, PCG rtol 1e-8).
 
 Checked against the oracle where it can compute outputs one by one, and by
 properties that hold at any size where it cannot:
-  * theta / Chat and cell matrices of a seeded sample of cells against the
-    oracle's MDEIM (Algorithm 5) and fast assembly (Algorithm 4);
+  * theta (FP64 form and the split form's double-float theta) / Chat and cell
+    matrices of a seeded sample of cells against the oracle's MDEIM
+    (Algorithm 5) and fast assembly (Algorithm 4);
   * the ROM + fast-assembly matrices against the oracle's full trimmed
     quadrature on a 0.1 % sample (Sec. 5 expects relative errors of order
     1e-3 for q = 2);
@@ -67,8 +68,8 @@ def run():
                 stream.synchronize()
                 out[name] = dict(u=u_dev[0].cpu().numpy().copy(), its=int(its[0]), rel=float(rel[0]),
                                  K=romb.romb_read(ctx.h, "K").reshape(lat.ncells, -1))
+                out[name]["theta"] = romb.romb_read(ctx.h, "theta").reshape(lat.ncells, -1)
                 if name == "split":
-                    out["theta"] = romb.romb_read(ctx.h, "theta").reshape(lat.ncells, -1)
                     out["chat"] = romb.romb_read(ctx.h, "chat").reshape(lat.ncells, 9, 16)
     return out
 
@@ -78,13 +79,14 @@ def test_sampled_cells_match_oracle(run):
     nd = 2 * (lat.p + 1) ** 2
     cells = LI.sample_cells(lat.ncells, 24 / lat.ncells, seed=SAMPLE_SEED)
     Ko = pipeline.matrices_rom(lat, roms, cells=cells)
-    worst = {"split": 0.0, "fp64": 0.0, "theta": 0.0, "chat": 0.0}
+    worst = {"split": 0.0, "fp64": 0.0, "theta": 0.0, "theta_split": 0.0, "chat": 0.0}
     for c in cells:
         R = roms[int(lat.family[c])]
-        th = run["theta"][c]
-        assert th[0] == lat.rho
         ref = (1 - lat.rho) * orom.reduced_vector(R, lat.mu[c])
-        worst["theta"] = max(worst["theta"], np.abs(th[1:1 + R.n_r] - ref).max() / np.abs(ref).max())
+        for form, key in (("fp64", "theta"), ("split", "theta_split")):
+            th = run[form]["theta"][c]
+            assert th[0] == lat.rho
+            worst[key] = max(worst[key], np.abs(th[1:1 + R.n_r] - ref).max() / np.abs(ref).max())
         P = ogeo.cell_control_points(lat.ctrl, lat.nx, lat.m, c % lat.nx, c // lat.nx)
         Cn = assembly.fa_coefficients(P, lat.E, lat.nu, 2).reshape(9, 16)
         worst["chat"] = max(worst["chat"], np.abs(run["chat"][c] - Cn).max() / np.abs(Cn).max())
@@ -93,6 +95,10 @@ def test_sampled_cells_match_oracle(run):
             worst[form] = max(worst[form], np.linalg.norm(Kg - Ko[c]) / np.linalg.norm(Ko[c]))
     print("sampled cells, worst relative error vs oracle: " + ", ".join(f"{k} {v:.2e}" for k, v in worst.items()))
     assert worst["theta"] <= 1e-12
+    # the split forms interpolate theta in double-float arithmetic (pairs of
+    # FP32, ~2^-48 per operation, compensated sums over 2,744 steps): a few
+    # 1e-13 measured, 1e-11 allowed
+    assert worst["theta_split"] <= 1e-11
     # Chat = j J^-1 C J^-T at the interpolation nodes of quartic maps: both
     # sides evaluate it in FP64 with different operation orders, and the
     # Jacobian's conditioning amplifies the rounding to a few hundred ulps
