@@ -26,6 +26,14 @@ struct RomDev {
   double nodes[12];      // degree-r GLL nodes of [lo, hi]
 };
 
+// the families of one theta launch: family k owns CTAs [cta0[k], cta0[k+1])
+struct ThetaFams {
+  RomDev rom[ROMB_MAX_FAMILIES];
+  const int* list[ROMB_MAX_FAMILIES];
+  int count[ROMB_MAX_FAMILIES], cta0[ROMB_MAX_FAMILIES];
+  int nfam;
+};
+
 void fill_cell_params(const romb_ctx* c, CellParams* P) {
   memset(P, 0, sizeof(*P));
   P->p = c->p;
@@ -141,9 +149,12 @@ __device__ __forceinline__ void df_dot_step(float& h, float& l, float2 a, float2
 
 // lambda_t of TH_CELLS cells (lanes over t), the loop of the FP64 kernel in
 // double-float: inner sums over g1 per (g2, g3, g4), then the weighted outer sum.
-template <int NS>
+// N1 > 0: n1 = r + 1 as a compile-time constant, so that the n1 sample loads
+// of a (g2, g3, g4) step are all issued before its FP32 work.
+template <int NS, int N1>
 __device__ __forceinline__ void theta_contract_df(const float2* __restrict__ At2, const float2 (*wdf)[4][12],
-                                                  int lane, int n1, int nr, double (&lam)[NS][TH_CELLS]) {
+                                                  int lane, int n1_rt, int nr, double (&lam)[NS][TH_CELLS]) {
+  const int n1 = N1 > 0 ? N1 : n1_rt;
   float ah[NS][TH_CELLS], al[NS][TH_CELLS];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -165,14 +176,31 @@ __device__ __forceinline__ void theta_contract_df(const float2* __restrict__ At2
       for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int j = 0; j < TH_CELLS; ++j) sh[s][j] = sc[s][j] = 0.f;
-      for (int g1 = 0; g1 < n1; ++g1) {
-        const float2* Ag = At2 + (long long)(g234 * n1 + g1) * nr;
+      if constexpr (N1 > 0) {
+        float2 av[N1][NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const int t = lane + 32 * s;
-          const float2 a = t < nr ? __ldg(Ag + t) : make_float2(0.f, 0.f);
+        for (int g1 = 0; g1 < N1; ++g1)
 #pragma unroll
-          for (int j = 0; j < TH_CELLS; ++j) df_dot_step(sh[s][j], sc[s][j], a, wdf[j][0][g1]);
+          for (int s = 0; s < NS; ++s) {
+            const int t = lane + 32 * s;
+            av[g1][s] = t < nr ? __ldg(At2 + (long long)(g234 * N1 + g1) * nr + t) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int g1 = 0; g1 < N1; ++g1)
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int j = 0; j < TH_CELLS; ++j) df_dot_step(sh[s][j], sc[s][j], av[g1][s], wdf[j][0][g1]);
+      } else {
+        for (int g1 = 0; g1 < n1; ++g1) {
+          const float2* Ag = At2 + (long long)(g234 * n1 + g1) * nr;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            const int t = lane + 32 * s;
+            const float2 a = t < nr ? __ldg(Ag + t) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < TH_CELLS; ++j) df_dot_step(sh[s][j], sc[s][j], a, wdf[j][0][g1]);
+          }
         }
       }
 #pragma unroll
@@ -193,8 +221,8 @@ __device__ __forceinline__ void theta_contract_df(const float2* __restrict__ At2
 // NS = ceil(n_r / 32) lane slots per reduced coefficient: FP64 instructions
 // with every lane predicated off still occupy the FP64 pipe, so the slot
 // count is a compile-time constant.
-template <int NS, bool DF>
-__global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, const int* __restrict__ list, int count,
+template <int NS, bool DF, int N1 = 0>
+__global__ void __launch_bounds__(128) theta_kernel(CellParams P, ThetaFams F,
                                                      const double* __restrict__ ctrl, const double* __restrict__ mu,
                                                      double* __restrict__ theta, double* __restrict__ chat,
                                                      float* __restrict__ th_hi, float* __restrict__ th_lo,
@@ -202,7 +230,15 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
   __shared__ double wts[4][TH_CELLS][4][12];   // [warp][cell][param][node]
   __shared__ float2 wdf[DF ? 4 : 1][TH_CELLS][4][12];   // the same as (hi, lo) FP32 pairs (DF only)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int first = (blockIdx.x * 4 + warp) * TH_CELLS;
+  // the family of this CTA (families own consecutive CTA ranges)
+  int fi = 0;
+#pragma unroll
+  for (int k = 1; k < ROMB_MAX_FAMILIES; ++k)
+    if (k < F.nfam && (int)blockIdx.x >= F.cta0[k]) fi = k;
+  const RomDev& R = F.rom[fi];
+  const int* __restrict__ list = F.list[fi];
+  const int count = F.count[fi];
+  const int first = (((int)blockIdx.x - F.cta0[fi]) * 4 + warp) * TH_CELLS;
   const int r = R.r, n1 = r + 1;
   const double* nodes = R.nodes;
   int cells[TH_CELLS];
@@ -272,7 +308,7 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, RomDev R, cons
 #pragma unroll
       for (int j = 0; j < TH_CELLS; ++j) lam[s][j] = acc[s][j];
   } else {
-    theta_contract_df<NS>(R.At2, wdf[warp], lane, n1, nr, lam);
+    theta_contract_df<NS, N1>(R.At2, wdf[warp], lane, n1, nr, lam);
   }
   for (int j = 0; j < TH_CELLS; ++j) {
     const int c = cells[j];
@@ -456,30 +492,46 @@ romb_status launch_theta(romb_ctx* c) {
   for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
     c->famstart[f] = start;
     c->famcount[f] = counts[f];
-    if (counts[f] > 0 && !c->roms[f].loaded) {
-      // cells reference a family without a model: flag them via the family check
-      return ROMB_E_ARG;
-    }
-    if (counts[f] > 0) {
+    // cells that reference a family without a model
+    if (counts[f] > 0 && !c->roms[f].loaded) return ROMB_E_ARG;
+    start += counts[f];
+  }
+  // one launch per group of families that share the kernel's template
+  // arguments (lane slots per coefficient, compile-time r + 1)
+  const bool df = c->prec != ROMB_FP64;   // split forms: theta in double-float
+  bool done[ROMB_MAX_FAMILIES] = {false};
+  for (int f0 = 0; f0 < ROMB_MAX_FAMILIES; ++f0) {
+    if (done[f0] || counts[f0] == 0) continue;
+    const int ns = (c->roms[f0].n_r + 31) / 32;
+    const bool r6 = df && c->roms[f0].r == 6;
+    ThetaFams F;
+    memset(&F, 0, sizeof(F));
+    int grid = 0;
+    for (int f = f0; f < ROMB_MAX_FAMILIES; ++f) {
       const RombRom& Rr = c->roms[f];
-      RomDev R{Rr.U64, Rr.At, Rr.At2, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
+      if (done[f] || counts[f] == 0 || (Rr.n_r + 31) / 32 != ns || (df && Rr.r == 6) != r6) continue;
+      done[f] = true;
+      RomDev& R = F.rom[F.nfam];
+      R = RomDev{Rr.U64, Rr.At, Rr.At2, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
       double g[12];
       gll_nodes01(Rr.r, g);
       for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
-      const int per_block = 4 * TH_CELLS;
-      const int grid = (counts[f] + per_block - 1) / per_block;
-      const int ns = (Rr.n_r + 31) / 32;
-      const bool df = c->prec != ROMB_FP64;   // split forms: theta in double-float
-      auto k = df ? (ns <= 1 ? theta_kernel<1, true> : ns == 2 ? theta_kernel<2, true> : ns == 3 ? theta_kernel<3, true>
-                                                                                   : theta_kernel<4, true>)
-                  : (ns <= 1 ? theta_kernel<1, false> : ns == 2 ? theta_kernel<2, false>
-                               : ns == 3 ? theta_kernel<3, false> : theta_kernel<4, false>);
-      k<<<grid, 128, 0, c->stream>>>(P, R, c->d_famlist + start, counts[f], c->d_ctrl, c->d_mu, c->d_theta, c->d_chat,
-                                     c->d_theta_hi, c->d_theta_lo, c->d_chat32, c->d_flags);
-      ++c->launches;
-      ROMB_CUDA(cudaGetLastError());
+      F.list[F.nfam] = c->d_famlist + c->famstart[f];
+      F.count[F.nfam] = counts[f];
+      F.cta0[F.nfam] = grid;
+      grid += (counts[f] + 4 * TH_CELLS - 1) / (4 * TH_CELLS);
+      ++F.nfam;
     }
-    start += counts[f];
+    auto k = !df ? (ns <= 1 ? theta_kernel<1, false> : ns == 2 ? theta_kernel<2, false>
+                              : ns == 3 ? theta_kernel<3, false> : theta_kernel<4, false>)
+             : r6 ? (ns <= 1 ? theta_kernel<1, true, 7> : ns == 2 ? theta_kernel<2, true, 7>
+                     : ns == 3 ? theta_kernel<3, true, 7> : theta_kernel<4, true, 7>)
+                  : (ns <= 1 ? theta_kernel<1, true> : ns == 2 ? theta_kernel<2, true>
+                     : ns == 3 ? theta_kernel<3, true> : theta_kernel<4, true>);
+    k<<<grid, 128, 0, c->stream>>>(P, F, c->d_ctrl, c->d_mu, c->d_theta, c->d_chat, c->d_theta_hi, c->d_theta_lo,
+                                   c->d_chat32, c->d_flags);
+    ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
   }
   return ROMB_OK;
 }
