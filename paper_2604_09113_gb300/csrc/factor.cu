@@ -33,6 +33,20 @@ __device__ __forceinline__ void tri_ij(int t, int& i, int& j) {
   j = t - r * (r + 1) / 2;
 }
 
+// 1 / sqrt(d) for a pivot d > 0 by Newton's iteration for the reciprocal
+// square root, y <- y + y (1/2 - (d/2) y^2), started from the FP32 estimate
+// (relative error below 2^-22): the error squares with each step, so two
+// steps leave only FP64 rounding (a few ulp).  Pivots outside the FP32 range
+// use the FP64 square root and division.
+__device__ __forceinline__ double pivot_rsqrt(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  const double h = 0.5 * d;
+  double y = (double)rsqrtf((float)d);
+  y = fma(y, fma(-h, y * y, 0.5), y);
+  y = fma(y, fma(-h, y * y, 0.5), y);
+  return y;
+}
+
 // In-place right-looking Cholesky (lower) of the n x n row-major A (stride
 // lda); invd[k] = 1 / L_kk.  Trailing updates touch the lower triangle only.
 __device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
@@ -44,9 +58,9 @@ __device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
         *bad = 1;
         d = 1.0;
       }
-      d = sqrt(d);
-      A[k * lda + k] = d;
-      invd[k] = 1.0 / d;
+      const double y = pivot_rsqrt(d);
+      A[k * lda + k] = d * y;
+      invd[k] = y;
     }
     __syncthreads();
     const double inv = invd[k];
