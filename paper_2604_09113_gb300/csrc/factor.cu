@@ -336,35 +336,40 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     if (s_cmap[8 + a] < 0 || s_cmap[8 + b] < 0) acc = (a == b) ? 1.0 : 0.0;
     T[t] = acc;
   }
-  // Z = M^T Z1 = Shat^-1 fhat
-  for (int t = tid; t < NK * 20; t += nt) {
-    const int i = t / 20, j = t % 20;
-    double acc = 0.0;
-    for (int k = i; k < NK; ++k) acc = fma(M[k * NK + i], Z[k * 20 + j], acc);
-    Q[t] = acc;
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    // 12 x 12 Cholesky of That on one warp (lane = row, right-looking),
+    // while the other warps form Z
+    for (int k = 0; k < 12; ++k) {
+      if (lane == k) {
+        double d = T[k * 12 + k];
+        if (!(d > 0.0)) {
+          s_bad = 1;
+          d = 1.0;
+        }
+        const double y = pivot_rsqrt(d);
+        T[k * 12 + k] = d * y;
+        s_invT[k] = y;
+      }
+      __syncwarp();
+      if (lane > k && lane < 12) T[lane * 12 + k] *= s_invT[k];
+      __syncwarp();
+      if (lane > k && lane < 12)
+        for (int j = k + 1; j <= lane; ++j) T[lane * 12 + j] = fma(-T[lane * 12 + k], T[j * 12 + k], T[lane * 12 + j]);
+      __syncwarp();
+    }
+  } else {
+    // Z = M^T Z1 = Shat^-1 fhat
+    for (int t = tid - 32; t < NK * 20; t += nt - 32) {
+      const int i = t / 20, j = t % 20;
+      double acc = 0.0;
+      for (int k = i; k < NK; ++k) acc = fma(M[k * NK + i], Z[k * 20 + j], acc);
+      Q[t] = acc;
+    }
   }
   __syncthreads();
   for (int t = tid; t < NK * 20; t += nt) Z[t] = Q[t];
-  if (tid == 0) {
-    // 12 x 12 Cholesky of That (one thread)
-    for (int k = 0; k < 12; ++k) {
-      double d = T[k * 12 + k];
-      for (int j = 0; j < k; ++j) d -= T[k * 12 + j] * T[k * 12 + j];
-      if (!(d > 0.0)) {
-        s_bad = 1;
-        d = 1.0;
-      }
-      d = sqrt(d);
-      T[k * 12 + k] = d;
-      const double inv = 1.0 / d;
-      s_invT[k] = inv;
-      for (int i = k + 1; i < 12; ++i) {
-        double s = T[i * 12 + k];
-        for (int j = 0; j < k; ++j) s -= T[i * 12 + j] * T[k * 12 + j];
-        T[i * 12 + k] = s * inv;
-      }
-    }
-  }
   __syncthreads();
   // R = Chat Z - ghat ; ghat = -C[edge, corner_j] (vertex slots) or e_{j-8} (edge slots)
   double* R = Q;   // [12][20]
