@@ -48,15 +48,17 @@ __device__ __forceinline__ double pivot_rsqrt(double d) {
 }
 
 // In-place Cholesky (lower) of the n x n row-major A (stride lda); invd[k] =
-// 1 / L_kk.  Right-looking in blocks of 4 columns, three barriers per block:
-// thread 0 factors the 4 x 4 diagonal block, every row below solves its 4
-// entries against it, then a rank-4 update of the trailing lower triangle.
+// 1 / L_kk.  Right-looking in blocks of CB columns, three barriers per block:
+// thread 0 factors the CB x CB diagonal block, every row below solves its CB
+// entries against it, then a rank-CB update of the trailing lower triangle
+// (CB = 2 measured fastest: larger blocks lengthen thread 0's serial part).
 // Each entry receives the same FMAs in the same order as the column-by-column
 // algorithm.
 __device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int k0 = 0; k0 < n; k0 += 4) {
-    const int kb = min(4, n - k0);
+  constexpr int CB = 2;   // columns per block
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    const int kb = min(CB, n - k0);
     if (tid == 0) {
       for (int a = 0; a < kb; ++a) {
         const int k = k0 + a;
@@ -79,9 +81,9 @@ __device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
     __syncthreads();
     // panel: L[r][k0 + a] for rows r below the block (forward substitution)
     for (int r = k0 + kb + tid; r < n; r += nt) {
-      double l[4];
+      double l[CB];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      for (int a = 0; a < CB; ++a) {
         if (a < kb) {
           double v = A[r * lda + k0 + a];
 #pragma unroll
@@ -99,7 +101,7 @@ __device__ void chol_smem(double* A, int n, int lda, double* invd, int* bad) {
       const int i = k0 + kb + a, j = k0 + kb + b;
       double v = A[i * lda + j];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < CB; ++c)
         if (c < kb) v = fma(-A[i * lda + k0 + c], A[j * lda + k0 + c], v);
       A[i * lda + j] = v;
     }
