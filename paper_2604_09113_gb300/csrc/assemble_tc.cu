@@ -161,31 +161,27 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 struct dfl {
   float hi, lo;
 };
-__device__ __forceinline__ dfl df_quick(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
+// Compensated accumulation (h, l) += x * y: the product is error-free
+// (p + e via fmaf, plus the cross terms), the sum a two-sum whose error goes to
+// the low word, which is not renormalised until the end (the dot-product
+// scheme of Ogita, Rump and Oishi, 2005).  __fmul_rn keeps the compiler from
+// contracting the product into the following add.
+__device__ __forceinline__ void df_acc(float& h, float& l, dfl x, float2 y) {
+  const float p = __fmul_rn(x.hi, y.x);
+  float e = fmaf(x.hi, y.x, -p);
+  e = fmaf(x.hi, y.y, e);
+  e = fmaf(x.lo, y.x, e);
+  const float s = __fadd_rn(h, p), bb = __fsub_rn(s, h);
+  l = __fadd_rn(l, __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  h = s;
 }
-__device__ __forceinline__ dfl df_two_sum(float a, float b) {
-  const float s = a + b, bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
-  dfl s = df_two_sum(x.hi, y.hi);
-  s.lo += x.lo + y.lo;
-  return df_quick(s.hi, s.lo);
-}
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  return df_quick(p, e);
-}
-__device__ __forceinline__ dfl df_mul_f(dfl x, float c) {
-  const float p = x.hi * c;
-  float e = fmaf(x.hi, c, -p);
-  e = fmaf(x.lo, c, e);
-  return df_quick(p, e);
+__device__ __forceinline__ void df_acc_f(float& h, float& l, float xh, float xl, float c) {
+  const float p = __fmul_rn(xh, c);
+  float e = fmaf(xh, c, -p);
+  e = fmaf(xl, c, e);
+  const float s = __fadd_rn(h, p), bb = __fsub_rn(s, h);
+  l = __fadd_rn(l, __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  h = s;
 }
 __device__ __forceinline__ dfl df_from_double(double d) {
   const float h = (float)d;
@@ -367,7 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         const int pr = t * TC_PAIRS + pl;
         if (!valid || pr >= P.npairs) continue;
         const int2 kk = P.pairs[pr];
-        dfl v0 = {0.f, 0.f}, v1 = {0.f, 0.f};
+        float v0h = 0.f, v0l = 0.f, v1h = 0.f, v1l = 0.f;
 #pragma unroll
         for (int k3 = 0; k3 < 9; ++k3)
 #pragma unroll
@@ -375,16 +371,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
 #pragma unroll
             for (int j2 = 0; j2 < 2; ++j2) {
               const int e = k3 * 4 + 2 * j1 + j2;
-              const float2 u0 = U01[36 * pl + e], u1 = U01[TC_N + 36 * pl + e];
-              dfl Ie = df_add(df_mul(th0, {u0.x, u0.y}), df_mul(th1, {u1.x, u1.y}));
-              Ie = df_add(Ie, {acc[e], 0.f});
-              v0 = df_add(v0, df_mul_f(Ie, C[8 * k3 + 4 * j1 + j2]));       // i2 = 0
-              v1 = df_add(v1, df_mul_f(Ie, C[8 * k3 + 4 * j1 + 2 + j2]));   // i2 = 1
+              // I_e = theta_0 U'_0 + theta_1 U'_1 + (tensor-core rows 2..)
+              float ih = acc[e], il = 0.f;
+              df_acc(ih, il, th0, U01[36 * pl + e]);
+              df_acc(ih, il, th1, U01[TC_N + 36 * pl + e]);
+              df_acc_f(v0h, v0l, ih, il, C[8 * k3 + 4 * j1 + j2]);       // i2 = 0
+              df_acc_f(v1h, v1l, ih, il, C[8 * k3 + 4 * j1 + 2 + j2]);   // i2 = 1
             }
         const long long r = 2 * kk.x + g, q0 = 2 * kk.y;
         double* Kr = Kc + r * P.ndof - r * (r - 1) / 2 - r;
-        if (!(kk.x == kk.y && g == 1)) Kr[q0] = (double)v0.hi + (double)v0.lo;
-        Kr[q0 + 1] = (double)v1.hi + (double)v1.lo;
+        if (!(kk.x == kk.y && g == 1)) Kr[q0] = (double)v0h + (double)v0l;
+        Kr[q0 + 1] = (double)v1h + (double)v1l;
       }
       tc_fence_before();
       mbar_arrive(&bar_accempty[b]);
