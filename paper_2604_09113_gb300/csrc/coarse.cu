@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "bulk.cuh"
+#include "dense.cuh"
 #include "device.cuh"
 #include "tables.cuh"
 
@@ -229,51 +230,17 @@ __global__ void __launch_bounds__(256) nd_assemble_inner_kernel(const FrontDev* 
 }
 
 // In-place Cholesky of the nbk x nbk block D (lower part used, zero padded to
-// ND_NB) and M = L^-1 (zero padded), by the whole CTA: right-looking with
-// reciprocal pivots; trailing updates over the lower triangle only.  (FP64
-// throughput is per SM sub-partition, so the CTA's warps share the work.)
+// ND_NB) and M = L^-1 (zero padded), by the whole CTA with the blocked
+// shared-memory routines (Newton pivots, same FMA order as column by column).
 __device__ void nd_chol_inv_block(double (*D)[ND_NB + 1], double (*M)[ND_NB + 1], double* invd, int nbk,
                                   int32_t* bad) {
-  for (int k = 0; k < nbk; ++k) {
-    if (threadIdx.x == 0) {
-      double d = D[k][k];
-      if (!(d > 0.0)) {
-        *bad = 1;
-        d = 1.0;
-      }
-      d = sqrt(d);
-      D[k][k] = d;
-      invd[k] = 1.0 / d;
-    }
-    __syncthreads();
-    const double inv = invd[k];
-    for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) D[i][k] *= inv;
-    __syncthreads();
-    const int m = nbk - k - 1;
-    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
-      int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-      if ((i + 1) * (i + 2) / 2 <= t) ++i;
-      else if (i * (i + 1) / 2 > t) --i;
-      const int j = t - i * (i + 1) / 2;
-      D[k + 1 + i][k + 1 + j] = fma(-D[k + 1 + i][k], D[k + 1 + j][k], D[k + 1 + i][k + 1 + j]);
-    }
-    __syncthreads();
-  }
+  chol_smem(&D[0][0], nbk, ND_NB + 1, invd, bad);
+  tri_inverse(&D[0][0], nbk, ND_NB + 1, invd, &M[0][0], ND_NB + 1);
   for (int t = threadIdx.x; t < ND_NB * ND_NB; t += blockDim.x) {
     const int i = t / ND_NB, j = t % ND_NB;
-    M[i][j] = (i == j && i < nbk) ? invd[i] : 0.0;
+    if (i >= nbk || j >= nbk) M[i][j] = 0.0;
   }
   __syncthreads();
-  for (int i = 0; i + 1 < nbk; ++i) {
-    const int w = i + 1, tot = (nbk - i - 1) * w;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int r = i + 1 + t / w, c = t % w;
-      double v = fma(-D[r][i], M[i][c], M[r][c]);
-      if (r == i + 1) v *= invd[r];
-      M[r][c] = v;
-    }
-    __syncthreads();
-  }
 }
 
 // Factor the diagonal block [k0, k0 + nbk) of front f in place and store
