@@ -35,8 +35,10 @@ SAMPLE_NX = SAMPLE_NY = 16      # bounded CPU sample per reference-arm step
 BASE_NX = BASE_NY = 24          # bounded CPU sample of the cpu_baseline leg (~15 s)
 FP64_PEAK_GFLOPS = 1250.0       # nominal dense FP64 rate of GB300 (profiling recipe)
 # DRAM bytes (read + write) per cell of the local factor kernel, from an ncu
-# capture of the 132 x 132 p = 6 launch (profiles/factor_kernel_132x132_p6.md)
-FACTOR_TRAFFIC_PER_CELL = (692683520 + 1426905088) / 17424
+# capture of one launch on the first 66 x 66 cells of the 132 x 132 p = 6
+# workload (4,356 cells; per-cell traffic, scaled to the launch by the cell
+# count; profiles/factor_kernel_132x132_p6.md)
+FACTOR_TRAFFIC_PER_CELL = (172553984 + 312830976) / 4356
 
 
 def args_parse():
