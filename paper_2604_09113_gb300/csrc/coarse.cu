@@ -303,9 +303,10 @@ __global__ void __launch_bounds__(256) nd_trsm_kernel(const FrontDev* __restrict
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int j = g + 8 * q;
+    if (j >= nbk) continue;   // padding columns of a narrow last block: no work
     double x = 0.0;
     for (int tt = 0; tt <= j; ++tt) x = fma(Ap[rr][tt], Li[j][tt], x);
-    if (r < n + f.ns && j < nbk) A[(long long)r * n + k0 + j] = x;
+    if (r < n + f.ns) A[(long long)r * n + k0 + j] = x;
   }
 }
 
