@@ -505,7 +505,7 @@ __global__ void pcg_loop_check(cudaGraphConditionalHandle h, double* sc) {
 
 // The whole PCG loop as one graph: a conditional while node whose body is the
 // captured iteration followed by pcg_loop_check.  Returns false (with the
-// stream out of capture and no error pending) if the driver refuses any step.
+// stream out of capture and no error pending) if the CUDA driver refuses any step.
 static bool build_device_loop(romb_ctx* c, const CellParams& P, double* yloc, double* cloc) {
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return (void)cudaGetLastError(), false;
@@ -577,7 +577,7 @@ romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, dou
   if (nf > 0.0) {
     ROMB_CUDA(cudaMemcpyAsync(c->d_r, c->d_f, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
     ROMB_CUDA(cudaMemsetAsync(c->d_pv, 0, 8 * n, c->stream));
-    // the loop (or, where the driver cannot build it, one iteration) is captured
+    // the loop (or, where the CUDA driver cannot build it, one iteration) is captured
     // once per factorisation and replayed
     if (!c->pcg_graph) {
       if ((s = cell_apply<CA_MATVEC>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
