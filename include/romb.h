@@ -108,6 +108,10 @@ romb_status romb_train_load(romb_ctx* ctx, const char* rom_path, int* family_out
  * theta = ((1-rho) I_r(mu), rho) from the MDEIM interpolation of the cell's
  * family, Chat at the (q+1)^2 interpolation nodes (Eq. FAST interpolation), and
  * the contraction K = sum_{j1 j2 k3} [U_r I_r (1-rho) + rho I_Pi] C.
+ * prec = ROMB_FP64: everything in FP64.  The split forms interpolate theta in
+ * double-float arithmetic (FP32 pairs, ~48-bit significands; within ~1e-13
+ * of FP64) and run the contraction on the tensor cores with a compensated
+ * double-float epilogue; K stays FP64 in memory in every form.
  * Errors: ROMB_E_OUT_OF_BOX, ROMB_E_BAD_MAP (per-cell flags via romb_stats). */
 romb_status romb_assemble(romb_ctx* ctx, const romb_lattice* lat, romb_precision prec);
 
