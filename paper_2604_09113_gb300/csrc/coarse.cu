@@ -286,7 +286,10 @@ __global__ void __launch_bounds__(256) nd_trsm_kernel(const FrontDev* __restrict
   const int nbk = min(ND_NB, f.ns - k0);
   const int k1 = k0 + nbk;
   const int r0 = k1 + blockIdx.x * 32;
-  if (r0 >= n + f.ns) return;
+  // rows below the front: identity row n + e is still e_e until the panel
+  // holding column e, so rows n + e with e >= k1 are zero here: no work
+  const int rend = n + k1;
+  if (r0 >= rend) return;
   __shared__ double Li[ND_NB][ND_NB + 1];
   __shared__ double Ap[32][ND_NB + 1];
   double* A = F + f.off;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) nd_trsm_kernel(const FrontDev* __restrict
     const int i = t / ND_NB, j = t % ND_NB;
     Li[i][j] = Lg[t];
     const int r = r0 + i;
-    Ap[i][j] = (r < n + f.ns && j < nbk) ? A[(long long)r * n + k0 + j] : 0.0;
+    Ap[i][j] = (r < rend && j < nbk) ? A[(long long)r * n + k0 + j] : 0.0;
   }
   __syncthreads();
   const int rr = threadIdx.x >> 3, g = threadIdx.x & 7;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(256) nd_trsm_kernel(const FrontDev* __restrict
     if (j >= nbk) continue;   // padding columns of a narrow last block: no work
     double x = 0.0;
     for (int tt = 0; tt <= j; ++tt) x = fma(Ap[rr][tt], Li[j][tt], x);
-    if (r < n + f.ns) A[(long long)r * n + k0 + j] = x;
+    if (r < rend) A[(long long)r * n + k0 + j] = x;
   }
 }
 
@@ -329,6 +332,11 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   if (tix >= ntr * ntc) return;
   const int ti = tix / ntc, tj = tix % ntc;
   const int r0 = k1 + ti * 32, c0 = k1 + tj * 32;
+  // rows n + e with e >= k1 below the front are still e_e, zero in this panel:
+  // their update is exactly zero (the first tile, which carries the
+  // lookahead, starts at row k1 and is never skipped)
+  const int rend = n + k1;
+  if (r0 >= rend) return;
   // skip tiles with no valid output
   if (r0 < n && c0 > r0 + 31) return;
   __shared__ double Pi[32][ND_NB + 1], Pj[32][ND_NB + 1];
@@ -336,13 +344,13 @@ __global__ void __launch_bounds__(256) nd_syrk_kernel(const FrontDev* __restrict
   for (int t = threadIdx.x; t < 32 * ND_NB; t += blockDim.x) {
     const int rr = t / ND_NB, kk = t % ND_NB;
     const int ri = r0 + rr, rj = c0 + rr;
-    Pi[rr][kk] = (ri < n + f.ns && kk < nbk) ? A[(long long)ri * n + k0 + kk] : 0.0;
+    Pi[rr][kk] = (ri < rend && kk < nbk) ? A[(long long)ri * n + k0 + kk] : 0.0;
     Pj[rr][kk] = (rj < n && kk < nbk) ? A[(long long)rj * n + k0 + kk] : 0.0;
   }
   __syncthreads();
   const int lr = threadIdx.x / 8, lc0 = (threadIdx.x % 8) * 4;
   const int gi = r0 + lr;
-  if (gi < n + f.ns) {
+  if (gi < rend) {
     double acc[4] = {0, 0, 0, 0};
     for (int kk = 0; kk < nbk; ++kk) {
       const double a = Pi[lr][kk];
