@@ -193,13 +193,12 @@ def factor_flops(p: int) -> float:
     return f
 
 
-def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
-    """FP64 FMAs of one coarse solve: both sweeps apply every front's
-    B = [L11^-T | -(L21 L11^-1)^T] once (ns(ns+1)/2 + ns nb entries).  The
-    fronts are those of the library's geometric nested dissection: coarse DoFs
-    on vertices (2) and edges (3), rectangles bisected across the longer side
-    down to 2 x 2 cells; separator DoFs of a rectangle are eliminated there,
-    DoFs on its internal sides are its update rows; clamped DoFs are absent."""
+def nd_fronts(nx: int, ny: int, dmask: int) -> list:
+    """(ns, nb) of every front of the library's geometric nested dissection
+    of the coarse problem: coarse DoFs on vertices (2) and edges (3),
+    rectangles bisected across the longer side down to 2 x 2 cells; separator
+    DoFs of a rectangle are eliminated there (ns), DoFs on its internal sides
+    are its update rows (nb); clamped DoFs are absent."""
     def vdir(vx, vy):
         return ((dmask & 1) and vx == 0) or ((dmask & 2) and vx == nx) or ((dmask & 4) and vy == 0) or \
             ((dmask & 8) and vy == ny)
@@ -224,7 +223,7 @@ def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
                         out.append((px, py, 3))
         return out
 
-    total = 0.0
+    fronts = []
     stack = [(0, nx, 0, ny)]
     while stack:
         x0, x1, y0, y1 = stack.pop()
@@ -239,13 +238,19 @@ def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
                 nb += nd
             elif leaf or (xm >= 0 and px == 2 * xm) or (ym >= 0 and py == 2 * ym):
                 ns += nd
-        total += 2.0 * (ns * (ns + 1) / 2 + ns * nb)
+        fronts.append((ns, nb))
         if not leaf:
             if xm >= 0:
                 stack += [(x0, xm, y0, y1), (xm, x1, y0, y1)]
             else:
                 stack += [(x0, x1, y0, ym), (x0, x1, ym, y1)]
-    return total
+    return fronts
+
+
+def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
+    """FP64 FMAs of one coarse solve: both sweeps apply every front's
+    B = [L11^-T | -(L21 L11^-1)^T] once (ns(ns+1)/2 + ns nb entries)."""
+    return sum(2.0 * (ns * (ns + 1) / 2 + ns * nb) for ns, nb in nd_fronts(nx, ny, dmask))
 
 
 def pcg_cell_fma(p: int) -> float:
