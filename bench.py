@@ -266,6 +266,40 @@ def assembly_flops(p: int, n_r: int) -> float:
     return 2.0 * (n_r + 1) * 36 * pairs + 2.0 * 4 * 36 * pairs
 
 
+def tensor_peak_tflops(form: str):
+    """Dense tensor-core peak for the split form's operand type: the measured
+    bf16 burst rate of this machine (MEASURED_PEAKS.json), times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s) for the TF32 form."""
+    src = "measured bf16 burst (MEASURED_PEAKS.json)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        bf16, src = 1900.0, "fallback bf16 burst 1.9 PFLOP/s"
+    if form == "fp32split":
+        return bf16 * 1.1 / 2.25, src + " x 1.1/2.25 (nominal TF32/BF16)"
+    return bf16, src
+
+
+def assembly_report(phase_ms, ncells: int, p: int, n_r: int, form: str, world: int = 1) -> dict:
+    """Assembly alone (theta + contraction phases): cells/s, and the
+    contraction's algorithmic rate (assembly_flops per cell, K symmetry used)
+    against the tensor-core peak of its operand type, or against the FP64 rate
+    for the FP64 form."""
+    asm_ms = float(phase_ms[0] + phase_ms[1])
+    fl = assembly_flops(p, n_r) * ncells
+    out = {"cells_per_s": world * ncells / (asm_ms / 1e3), "ms": asm_ms,
+           "contraction_ms": float(phase_ms[1]),
+           "contraction_tflops": fl / (float(phase_ms[1]) / 1e3) / 1e12,
+           "units": f"{ncells} cells x {assembly_flops(p, n_r):.0f} flop"}
+    if form == "fp64":
+        out["peak_tflops"], out["peak_source"] = FP64_PEAK_GFLOPS / 1e3, "nominal FP64 rate"
+    else:
+        out["peak_tflops"], out["peak_source"] = tensor_peak_tflops(form)
+    out["frac"] = out["contraction_tflops"] / out["peak_tflops"]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -424,9 +458,7 @@ def run_ours(a):
     roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": pcg_fl / (ph[4] / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s (FP64)", "iterations": iters[-1]}
     roof_pcg["frac"] = roof_pcg["achieved"] / roof_pcg["peak"]
-    if form == "fp64":
-        fa = assembly_flops(lat.p, n_r) * lat.ncells
-        roof_pcg["assembly_fp64"] = {"achieved": fa / (ph[1] / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS}
+    asm = assembly_report(ph, lat.ncells, lat.p, n_r, form, world)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
@@ -441,6 +473,7 @@ def run_ours(a):
                        "cells": lat.ncells, "p": lat.p, "assembly_form": form,
                        "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_pcg": roof_pcg,
+            "assembly": asm,
             "cpu_baseline": cpu, "pcg_iters": iters[-1],
             "phase_ms": {n: float(v) for n, v in zip(names + ["copies", "total"], ph)},
             "offline_train_s": train_s, "accuracy": acc or None,

@@ -36,3 +36,19 @@ def test_coarse_solve_count_of_the_benchmarked_lattice():
     entries = sum(ns * (ns + 1) / 2 + ns * nb for ns, nb in fronts)
     assert bench.coarse_solve_fma(132, 132, 1) == 2 * entries
     assert sum(ns for ns, _ in fronts) == 140052
+
+
+def test_assembly_report_arithmetic():
+    # phase times of a recorded run (theta, contraction, ... in ms)
+    ph = [1.90, 3.13, 14.78, 11.57, 48.37, 0.93, 0.05, 80.69]
+    # K symmetry: nB(nB+1)/2 pairs, 36 (j1 j2 k3) terms, n_r + 1 rows of U' plus the 4 C products
+    assert bench.assembly_flops(6, 60) == 2 * 61 * 36 * 1225 + 2 * 4 * 36 * 1225
+    for form in ("fp32split", "bf16split", "fp64"):
+        r = bench.assembly_report(ph, 17424, 6, 60, form)
+        assert r["cells_per_s"] == pytest.approx(17424 / 5.03e-3)
+        assert r["contraction_tflops"] == pytest.approx(bench.assembly_flops(6, 60) * 17424 / 3.13e-3 / 1e12)
+        assert r["frac"] == pytest.approx(r["contraction_tflops"] / r["peak_tflops"])
+        assert 0 < r["peak_tflops"] < 5000
+    tf32, _ = bench.tensor_peak_tflops("fp32split")
+    bf16, _ = bench.tensor_peak_tflops("bf16split")
+    assert tf32 == pytest.approx(bf16 * 1.1 / 2.25)
