@@ -69,7 +69,7 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
 }
 
 // y_loc = M_c v_loc for every cell (M_c a dense symmetric nU x nU cell matrix:
-// S, or D F D), and with COARSE also c_loc = Phi_c^T v_loc.  Persistent CTAs
+// S, or D F D), or c_loc = Phi_c^T v_loc (COARSE).  Persistent CTAs
 // take the cells blockIdx.x, blockIdx.x + gridDim.x, ...; each streams its
 // cells' M_c (and Phi_c) and index rows through a CA_STAGES-deep shared ring
 // filled by bulk copies, so the HBM stream overlaps the FP64 work.  Row r of
@@ -77,9 +77,8 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
 // FP64 instruction has all its lanes busy.  One barrier per cell releases the
 // stage and publishes the next cell's gathered v.
 #define CA_STAGES 3
-// modes: y = M v; y = M v and c = Phi^T v; c = Phi^T v only
+// modes: y = M v (the operators S and D F D); c = Phi^T v (coarse restriction)
 #define CA_MATVEC 0
-#define CA_BOTH 1
 #define CA_RESTRICT 2
 template <int P>
 struct CellApplyShape {
