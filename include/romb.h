@@ -171,11 +171,13 @@ romb_status romb_compliance_grad(romb_ctx* ctx, double* compliance, double* dc_d
  * alignment, e.g. 10.7 MB for 64 x 64 cells at m = 3 and roughly 5,800 cells
  * at m = 4; larger problems return ROMB_E_SCRATCH and change nothing.
  *
- * Set-up: the first call on a device (with that device current) looks up the
- * array's device address with cudaGetSymbolAddress, which may load the
- * library's device code and its static memory.  Make that first call before
- * any stream capture, at a point where that one-time load is acceptable.
- * Every call clears the part of the array it uses before using it.
+ * Set-up: every call, with the context's device current, looks up the
+ * array's device address with cudaGetSymbolAddress (so a reset or re-created
+ * device context never leaves a stale address behind).  The first call on a
+ * device may load the library's device code and its static memory: make it
+ * before any stream capture, at a point where that one-time load is
+ * acceptable.  Every call clears the part of the array it uses before using
+ * it, and synchronises the context's stream before it returns.
  *
  * The array is shared by every context on the device: calls that overlap in
  * time on one device (from several host threads, or from contexts on

@@ -12,8 +12,6 @@
 // that never make that call.  The paper has no counterpart of this call.
 #include <stdio.h>
 
-#include <mutex>
-
 #include "device.cuh"
 
 // One per device, shared by every context on that device.
@@ -24,21 +22,16 @@ __global__ void sum4_kernel(const double* __restrict__ dmu, long long n, double*
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_grad_scratch on `device`, which the caller has made
-// current.  Looked up on the first call per device and remembered.
-romb_status scratch_address(int device, unsigned char** out) {
-  if (device < 0 || device >= kMaxDevices) return ROMB_E_ARG;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    ROMB_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
-    g_scratch_addr[device] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[device];
+// Device address of g_grad_scratch in the current device's context.  Looked
+// up on every call rather than remembered: an address kept across calls would
+// go stale if the device's primary context were reset or released and
+// retained again, while the lookup itself allocates nothing once the
+// library's device code is loaded (the first call on a device may load it).
+romb_status scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  ROMB_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
+  if (!p) return ROMB_E_CUDA;
+  *out = static_cast<unsigned char*>(p);
   return ROMB_OK;
 }
 
@@ -66,7 +59,7 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
   if (used > ROMB_NOALLOC_SCRATCH_BYTES) return ROMB_E_SCRATCH;
   ROMB_CUDA(cudaSetDevice(c->device));
   unsigned char* base = nullptr;
-  romb_status s = scratch_address(c->device, &base);
+  romb_status s = scratch_address(&base);
   if (s != ROMB_OK) return s;
   double* W = reinterpret_cast<double*>(base + oW);
   double* Q = reinterpret_cast<double*>(base + oQ);

@@ -24,6 +24,31 @@ def test_magic_points_first_is_argmax(small_rom):
     assert small_rom.magic[0] == np.argmax(np.abs(small_rom.U[:, 0]))
 
 
+def test_magic_points_hand_worked_example():
+    # Algorithm 3 on a 6 x 3 integer matrix, worked by hand with the
+    # interpolatory residual (the empirical interpolation step):
+    #   u1 = (0, 0, -3, -2, -2, 2): |u1| peaks at row 2            -> m1 = 2
+    #   u2 - (u2[2] / u1[2]) u1 = u2 - u1/3
+    #      = (2, -1, 0, -4/3, 5/3, -2/3): peak |2| at row 0       -> m2 = 0
+    #   [u1 u2] at rows (2, 0) = [[-3, -1], [0, 2]], u3 there = (3, 1)
+    #      -> c = (-7/6, 1/2); u3 + 7/6 u1 - 1/2 u2
+    #      = (0, -5/2, 0, -10/3, -17/6, 13/3): peak 13/3 at row 5 -> m3 = 5
+    # Readings this rules out: the orthogonal projection on span{u1, u2}
+    # picks (2, 0, 2), projecting with only the first column and point at
+    # every step picks (2, 0, 3), and no projection at all picks (2, 0, 1).
+    U = np.array([[0, 2, 1], [0, -1, -3], [-3, -1, 3], [-2, -2, -2], [-2, 1, 0], [2, 0, 2]], dtype=float)
+    assert rom.magic_points(U).tolist() == [2, 0, 5]
+
+
+def test_magic_points_tie_goes_to_lowest_index():
+    # equal peaks |u1| = 2 at rows 1 and 3: the lowest index wins
+    U = np.array([[1.0, 0.0], [-2.0, 1.0], [0.5, 3.0], [2.0, 1.0]])
+    m = rom.magic_points(U)
+    assert m[0] == 1
+    # u2 - (u2[1] / u1[1]) u1 = u2 + u1/2 = (1/2, 0, 13/4, 2): peak at row 2
+    assert m[1] == 2
+
+
 def test_interpolation_exact_at_grid_nodes(small_rom):
     # at a GLL grid node the online interpolant returns the offline I_r, which
     # matches the exact I at the magic points (Sec. 4.2.3)
