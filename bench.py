@@ -13,7 +13,8 @@ set-up + coarse Cholesky) -> romb_bddc_solve (PCG + interior recovery).
 displacement inside the timed region.  L2 is flushed (a 512 MB write) between
 timed steps, outside the timed events.
 
---impl reference times the CPU oracle on a bounded sample of the same workload.
+--impl reference times the CPU oracle on bounded samples of the same workload
+(independent tiles, one per host core), with models trained by the oracle.
 """
 from __future__ import annotations
 
@@ -31,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cells/s assembled+solved at 17,424 cells p=6; FP32 vs FP64 form at ≤1e-6 error"
 CONFIG = 3
-SAMPLE_NX = SAMPLE_NY = 16      # bounded CPU sample per reference-arm step
+SAMPLE_NX = SAMPLE_NY = 12      # tile of the reference arm (one per host core per step)
 BASE_NX = BASE_NY = 24          # bounded CPU sample of the cpu_baseline leg (~15 s)
 FP64_PEAK_GFLOPS = 1250.0       # nominal dense FP64 rate of GB300 (profiling recipe)
 # DRAM bytes (read + write) per cell of the local factor kernel, from an ncu
@@ -51,10 +52,12 @@ def args_parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--sub", type=int, default=0,
                     help="profiling only: run the first N x N cells of the workload")
     ap.add_argument("--cpu-sample-json", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--rom-dir", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--small-models", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -77,38 +80,101 @@ def train_models(rom_dir: str):
 
 
 def sub_lattice(lat, sx: int, sy: int):
-    """The first sx x sy cells of a lattice (same maps, thresholds, families)."""
-    import numpy as np
     import lattice_inputs as LI
-    m = lat.m
-    G = lat.ctrl.reshape(m * lat.ny + 1, m * lat.nx + 1, 2)[: m * sy + 1, : m * sx + 1]
-    cells = (np.arange(sy)[:, None] * lat.nx + np.arange(sx)[None, :]).ravel()
-    return LI.Lattice(nx=sx, ny=sy, p=lat.p, m=m, basis=lat.basis, ctrl=np.ascontiguousarray(G.reshape(-1, 2)),
-                      mu=lat.mu[cells].copy(), family=lat.family[cells].copy(), E=lat.E, nu=lat.nu, rho=lat.rho,
-                      dirichlet_mask=lat.dirichlet_mask, traction=lat.traction.copy(), name=lat.name + "-sample")
+    return LI.sub_lattice(lat, sx, sy)
 
 
-def oracle_sample_seconds(rom_paths, steps: int = 1, nx: int = SAMPLE_NX, ny: int = SAMPLE_NY):
-    """Time the oracle's online phase (MDEIM assembly, BDDC set-up, PCG,
-    recovery) on a bounded sample; returns (seconds per step, cells)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+_TILE_ROMS = {}
+
+
+def _oracle_tile_job(args):
+    """One independent tile of the workload through the oracle's online phase
+    (MDEIM assembly, BDDC set-up, PCG rtol 1e-8, recovery); runs in a pool
+    worker.  Returns (seconds, cells)."""
+    rom_paths, x0, y0, sx, sy = args
     import lattice_inputs as LI
     from oracle import bddc as obddc, pipeline, rom as orom
-    lat = sub_lattice(LI.config(CONFIG), nx, ny)
-    roms = {}
-    for p in rom_paths:
-        R = orom.read(p)
-        roms[R.family] = R
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        K = pipeline.matrices_rom(lat, roms)
-        pipeline.solve(lat, K, obddc.lattice_loads(lat), rtol=1e-8)
-        times.append(time.perf_counter() - t0)
-    return times, lat.ncells
+    key = tuple(rom_paths)
+    if key not in _TILE_ROMS:
+        _TILE_ROMS[key] = {R.family: R for R in (orom.read(p) for p in rom_paths)}
+    lat = LI.tile_lattice(LI.config(CONFIG), x0, y0, sx, sy)
+    t0 = time.perf_counter()
+    K = pipeline.matrices_rom(lat, _TILE_ROMS[key])
+    pipeline.solve(lat, K, obddc.lattice_loads(lat), rtol=1e-8)
+    return time.perf_counter() - t0, lat.ncells
+
+
+def tiles(count: int, size: int):
+    """`count` tiles of size x size cells of the 132 x 132 workload, row by row
+    (repeated when the workload has fewer)."""
+    per = 132 // size
+    return [((k % (per * per)) % per * size, (k % (per * per)) // per * size) for k in range(count)]
+
+
+def spawn_pool(n: int):
+    """Process pool started with spawn (safe after CUDA initialisation), one
+    single-threaded worker per core."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(n)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def oracle_tiles_seconds(pool, rom_paths, count: int, size: int):
+    """Wall time of `count` independent tiles run concurrently by the pool."""
+    jobs = [(list(rom_paths), x0, y0, size, size) for x0, y0 in tiles(count, size)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_tile_job, jobs, chunksize=1)
+    return time.perf_counter() - t0, sum(c for _, c in res)
+
+
+def oracle_models(train: bool, small: bool = False):
+    """Oracle-trained models of the workload (cached per machine); None when
+    train is False and they are not cached.  small: the rank-60 models on 80
+    samples with r = 2 (for a quick check of the line's format only; weaker
+    models leave some cells of this lattice indefinite)."""
+    import dataclasses
+    import lattice_inputs as LI
+    from oracle import offline
+    specs = LI.rom_specs(CONFIG)
+    if small:
+        specs = [dataclasses.replace(s, n_s=80, r=2) for s in specs]
+    return offline.workload_models(specs, lambda n, lo, hi, seed: LI.lhs(n, lo, hi, seed=seed), train=train)
 
 
 def cpu_baseline(rom_paths):
-    """The oracle, single-threaded, in a child process (threads fixed before numpy loads)."""
+    """The oracle on the host cores, in a child process (threads fixed before
+    numpy loads): one 24 x 24 tile single-threaded, then one tile per core
+    run concurrently.  Uses the oracle-trained models when a reference-arm
+    run on this machine has cached them, else the benchmark's model files
+    (the timing does not depend on the model's values)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     with tempfile.NamedTemporaryFile(suffix=".json", delete=False) as f:
         out = f.name
@@ -120,6 +186,28 @@ def cpu_baseline(rom_paths):
     d = json.load(open(out))
     os.unlink(out)
     return d
+
+
+def cpu_sample(rom_dir: str, out: str):
+    """Body of the cpu_baseline child process."""
+    models = oracle_models(train=False)
+    src = "oracle-trained models"
+    if models is None:
+        models = sorted(os.path.join(rom_dir, f) for f in os.listdir(rom_dir) if f.endswith(".rom"))
+        src = "the benchmark's model files"
+    nproc = os.cpu_count() or 1
+    single, cells1 = _oracle_tile_job((models, 0, 0, BASE_NX, BASE_NY))
+    with spawn_pool(nproc) as pool:
+        oracle_tiles_seconds(pool, models, nproc, 8)          # workers import numpy / scipy
+        wall, cells_all = oracle_tiles_seconds(pool, models, nproc, BASE_NX)
+    json.dump({"value": cells1 / single, "unit": "cells/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cells1} cells: first {BASE_NX}x{BASE_NY} cells of the workload, MDEIM assembly + "
+                         f"BDDC set-up + PCG + recovery, single thread ({src})",
+               "seconds": single, "cpu_model": cpu_model(), "nproc": nproc,
+               "all_cores": {"value": cells_all / wall, "unit": "cells/s", "cores": nproc, "seconds": wall,
+                             "sample": f"{nproc} independent {BASE_NX}x{BASE_NY} tiles of the workload, one "
+                                       f"single-threaded process per core, run concurrently"}},
+              open(out, "w"))
 
 
 # ---------------------------------------------------------------------------
@@ -281,7 +369,38 @@ def tensor_peak_tflops(form: str):
     return bf16, src
 
 
-def assembly_report(phase_ms, ncells: int, p: int, n_r: int, form: str, world: int = 1) -> dict:
+def fma_rates(romb, torch, stream, sms: int) -> dict:
+    """FP64 and FP32 FMA issue rates of this GPU, measured by the library's
+    probe kernel (8 independent FMA chains per thread, 8 warps per block,
+    8 blocks per SM) on the benchmark's stream with CUDA events, best of 5
+    launches of ~20 ms after a warm-up launch."""
+    out = {}
+    blocks, threads = 8 * sms, 256
+    for name, prec, dt in (("fp64_gflops", 0, torch.float64), ("fp32_gflops", 1, torch.float32)):
+        buf = torch.empty(blocks * threads, dtype=dt, device=torch.device("cuda", torch.cuda.current_device()))
+        iters = 64
+        best = 0.0
+        for rep in range(7):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = romb.romb_fma_probe(prec, blocks, threads, iters, stream.cuda_stream, buf)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if rep == 0:           # size the launches for ~20 ms
+                iters = max(16, int(iters * 20.0 / max(ms, 1e-3)))
+                continue
+            if rep >= 2:
+                best = max(best, fl / (ms / 1e3) / 1e9)
+        out[name] = best
+    out["how"] = (f"romb_fma_probe: {blocks} blocks x {threads} threads x 8 independent FMA chains, "
+                  "best of 5 launches of ~20 ms, CUDA events on the benchmark stream")
+    return out
+
+
+def assembly_report(phase_ms, ncells: int, p: int, n_r: int, form: str, world: int = 1,
+                    fp64_gflops: float = FP64_PEAK_GFLOPS) -> dict:
     """Assembly alone (theta + contraction phases): cells/s, and the
     contraction's algorithmic rate (assembly_flops per cell, K symmetry used)
     against the tensor-core peak of its operand type, or against the FP64 rate
@@ -293,7 +412,7 @@ def assembly_report(phase_ms, ncells: int, p: int, n_r: int, form: str, world: i
            "contraction_tflops": fl / (float(phase_ms[1]) / 1e3) / 1e12,
            "units": f"{ncells} cells x {assembly_flops(p, n_r):.0f} flop"}
     if form == "fp64":
-        out["peak_tflops"], out["peak_source"] = FP64_PEAK_GFLOPS / 1e3, "nominal FP64 rate"
+        out["peak_tflops"], out["peak_source"] = fp64_gflops / 1e3, "measured FP64 FMA rate (fma_rates)"
     else:
         out["peak_tflops"], out["peak_source"] = tensor_peak_tflops(form)
     out["frac"] = out["contraction_tflops"] / out["peak_tflops"]
@@ -367,6 +486,9 @@ def run_ours(a):
     for _ in range(a.warmup):
         step(prec)
     barrier()
+    rates = fma_rates(romb, torch, stream, torch.cuda.get_device_properties(dev).multi_processor_count)
+    peak64 = rates["fp64_gflops"] or FP64_PEAK_GFLOPS
+    barrier()
     clocks = Clocks(local)
     clocks.start()
     l0 = romb.romb_launch_count(ctx.h)
@@ -393,6 +515,32 @@ def run_ours(a):
     # accuracy of the split form against the FP64 form (same device, same inputs)
     u_form = u_dev.clone()
     acc = {}
+    fp64_form = None
+    names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery"]
+    if form != "fp64" and not a.no_fp64_form:
+        # the all-FP64 GPU form on the same lattice, timed like the chosen form
+        # (L2 flushed between steps; fewer steps: it is ~2.5x slower)
+        step(romb.ROMB_FP64)
+        k64 = max(1, min(a.steps, 5))
+        t64, ph64, it64 = [], [], []
+        for _ in range(k64):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, _ = step(romb.ROMB_FP64)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+            ph64.append(romb.romb_stats(ctx.h)[0].copy())
+            it64.append(it)
+        ms64, _ = aggregate(sum(t64), lat.ncells, world, dev)
+        ms64 /= k64
+        p64 = np.mean(np.array(ph64), axis=0)
+        fp64_form = {"value": world * lat.ncells / (ms64 / 1e3), "unit": "cells/s", "ms_per_step": ms64,
+                     "steps": k64, "pcg_iters": it64[-1],
+                     "phase_ms": {n: float(v) for n, v in zip(names + ["copies", "total"], p64)},
+                     "speedup_of_chosen_form": ms64 / ms}
     if have_tc and not a.no_accuracy:
         # every split form against the FP64 form, untimed, on the same lattice
         if form == "fp64":
@@ -444,21 +592,20 @@ def run_ours(a):
     # roofline of the dominant single kernel (the local factor kernel; the PCG
     # phase is ~40 small kernels per iteration), from its CUDA-event time on the
     # context stream, plus the PCG phase as a whole against the same FP64 peak
-    names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery"]
     n_r = max(s.n_r for s in LI.rom_specs(CONFIG))
     fl = factor_flops(lat.p) * lat.ncells
     roof = {"kernel": f"factor_kernel<{lat.p}>", "bound": "alu", "achieved": fl / (ph[2] / 1e3) / 1e9,
-            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "traffic": (FACTOR_TRAFFIC_PER_CELL * lat.ncells
+            "peak": peak64, "unit": "GFLOP/s (FP64)", "traffic": (FACTOR_TRAFFIC_PER_CELL * lat.ncells
                                                                          if FACTOR_TRAFFIC_PER_CELL else None),
-            "units": f"{lat.ncells} cells x {factor_flops(lat.p):.0f} flop", "peak_source":
-            "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64 rate of the profiling recipe)"}
+            "units": f"{lat.ncells} cells x {factor_flops(lat.p):.0f} flop",
+            "peak_source": "measured FP64 FMA rate of this GPU (fma_rates: romb_fma_probe)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     pcg_fl = iters[-1] * 2.0 * (pcg_cell_fma(lat.p) * lat.ncells +
                                 coarse_solve_fma(lat.nx, lat.ny, int(lat.dirichlet_mask)))
-    roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": pcg_fl / (ph[4] / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+    roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": pcg_fl / (ph[4] / 1e3) / 1e9, "peak": peak64,
                 "unit": "GFLOP/s (FP64)", "iterations": iters[-1]}
     roof_pcg["frac"] = roof_pcg["achieved"] / roof_pcg["peak"]
-    asm = assembly_report(ph, lat.ncells, lat.p, n_r, form, world)
+    asm = assembly_report(ph, lat.ncells, lat.p, n_r, form, world, peak64)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
@@ -476,7 +623,8 @@ def run_ours(a):
             "assembly": asm,
             "cpu_baseline": cpu, "pcg_iters": iters[-1],
             "phase_ms": {n: float(v) for n, v in zip(names + ["copies", "total"], ph)},
-            "offline_train_s": train_s, "accuracy": acc or None,
+            "offline_train_s": train_s, "accuracy": acc or None, "fp64_form": fp64_form,
+            "fma_rates": rates,
         }
         print(json.dumps(line))
     ctx.close()
@@ -488,22 +636,33 @@ def run_ours(a):
 # reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def run_reference(a):
+    """The oracle on the host cores: every step runs one 16 x 16 tile of the
+    workload per core, concurrently (independent sub-problems, oracle-trained
+    models; training is not timed)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
-    paths, _ = train_models(rom_dir)
-    oracle_sample_seconds(paths, steps=min(a.warmup, 1))
-    times, cells = oracle_sample_seconds(paths, steps=a.steps)
+    paths = oracle_models(train=True, small=a.small_models)
+    nproc = os.cpu_count() or 1
+    with spawn_pool(nproc) as pool:
+        for _ in range(max(1, min(a.warmup, 1))):
+            oracle_tiles_seconds(pool, paths, nproc, SAMPLE_NX)
+        times = []
+        for _ in range(a.steps):
+            t, cells = oracle_tiles_seconds(pool, paths, nproc, SAMPLE_NX)
+            times.append(t)
     s = sum(times) / len(times)
     v = cells / s
+    sample = (f"{nproc} independent {SAMPLE_NX}x{SAMPLE_NY} tiles of the workload per step ({cells} cells), one "
+              f"single-threaded oracle process per core; oracle-trained models"
+              + (" (reduced: 80 samples, r = 2, format check only)" if a.small_models else ""))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
-                       "sample": f"first {SAMPLE_NX}x{SAMPLE_NY} cells of the workload per step"},
-            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{cells} cells ({SAMPLE_NX}x{SAMPLE_NY}) per step"},
+                       "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": nproc, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -511,12 +670,7 @@ def run_reference(a):
 def main():
     a = args_parse()
     if a.cpu_sample_json:
-        paths = sorted(os.path.join(a.rom_dir, f) for f in os.listdir(a.rom_dir) if f.endswith(".rom"))
-        times, cells = oracle_sample_seconds(paths, steps=1, nx=BASE_NX, ny=BASE_NY)
-        json.dump({"value": cells / times[0], "unit": "cells/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{cells} cells: first {BASE_NX}x{BASE_NY} cells of the workload, "
-                             f"MDEIM assembly + BDDC set-up + PCG + recovery, single thread",
-                   "seconds": times[0]}, open(a.cpu_sample_json, "w"))
+        cpu_sample(a.rom_dir, a.cpu_sample_json)
         return
     if a.impl == "reference":
         run_reference(a)

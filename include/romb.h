@@ -185,6 +185,18 @@ romb_status romb_compliance_grad(romb_ctx* ctx, double* compliance, double* dc_d
 romb_status romb_compliance_grad_noalloc(romb_ctx* ctx, double* compliance, double* dc_dctrl, double* dc_dR,
                                          double* dc_dmu);
 
+/* FMA issue rate of this GPU (a measurement utility; the paper has no
+ * counterpart): enqueues on `cuda_stream` (a cudaStream_t, NULL: the legacy
+ * default stream) one kernel of `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 256), each running 8 independent chains of
+ * 16 * iters dependent FMAs in FP64 (precision 0) or FP32 (precision 1).
+ * `out` is device memory of blocks * threads elements of that type (written,
+ * so the chains are kept); *flops receives the floating-point operations the
+ * launch performs (2 per FMA).  The caller times the launch on its stream.
+ * Errors: ROMB_E_ARG, ROMB_E_CUDA. */
+romb_status romb_fma_probe(int precision, int blocks, int threads, int iters, void* cuda_stream, void* out,
+                           double* flops);
+
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
  * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits

@@ -187,6 +187,24 @@ def config(k: int) -> Lattice:
     raise ValueError(k)
 
 
+def tile_lattice(lat: Lattice, x0: int, y0: int, sx: int, sy: int) -> Lattice:
+    """The sx x sy cells of a lattice starting at cell (x0, y0): the same maps,
+    thresholds, families and material, with the lattice's constraints and
+    loads applied on the tile's own boundary edges."""
+    m = lat.m
+    G = lat.ctrl.reshape(m * lat.ny + 1, m * lat.nx + 1, 2)[m * y0: m * (y0 + sy) + 1, m * x0: m * (x0 + sx) + 1]
+    cells = ((y0 + np.arange(sy))[:, None] * lat.nx + (x0 + np.arange(sx))[None, :]).ravel()
+    return Lattice(nx=sx, ny=sy, p=lat.p, m=m, basis=lat.basis, ctrl=np.ascontiguousarray(G.reshape(-1, 2)),
+                   mu=lat.mu[cells].copy(), family=lat.family[cells].copy(), E=lat.E, nu=lat.nu, rho=lat.rho,
+                   dirichlet_mask=lat.dirichlet_mask, traction=lat.traction.copy(),
+                   name=f"{lat.name}-tile-{x0}-{y0}-{sx}x{sy}")
+
+
+def sub_lattice(lat: Lattice, sx: int, sy: int) -> Lattice:
+    """The first sx x sy cells of a lattice (tile_lattice at cell (0, 0))."""
+    return tile_lattice(lat, 0, 0, sx, sy)
+
+
 def rom_specs(k: int) -> list[RomSpec]:
     """ROM training recipes of each workload (one cluster per family)."""
     s = 2000 + k

@@ -127,17 +127,31 @@ def grid_points(lo: float, hi: float, r: int) -> np.ndarray:
     return np.stack([G1.ravel(), G2.ravel(), G3.ravel(), G4.ravel()], axis=1)
 
 
+def _snapshot_job(args):
+    return snapshot(*args)
+
+
+def _entries_job(args):
+    return entries(*args)
+
+
 def train(family: int, kind: int, p: int, q: int, r: int, n_r: int, lo: float, hi: float,
-          samples: np.ndarray, n_v: int | None = None) -> Rom:
-    """Offline phase of Sec. 4.4 for one family and one cluster."""
-    S = np.stack([snapshot(family, mu, kind, p, q) for mu in samples], axis=1)
+          samples: np.ndarray, n_v: int | None = None, pmap=map) -> Rom:
+    """Offline phase of Sec. 4.4 for one family and one cluster.
+
+    ``pmap`` maps a function over the independent quadratures (one per
+    snapshot, one per grid node); the builtin ``map`` runs them one after
+    another, a process pool's ``map`` spreads them over cores with the same
+    results."""
+    S = np.stack(list(pmap(_snapshot_job, [(family, mu, kind, p, q) for mu in samples])), axis=1)
     U, _ = svd_basis(S, n_r)
     magic = magic_points(U)
     G = grid_points(lo, hi, r)
     Um = U[magic, :]
     A = np.empty((n_r, len(G)))
-    for g, mu in enumerate(G):
-        A[:, g] = np.linalg.solve(Um, entries(family, mu, kind, p, q, magic))
+    E = list(pmap(_entries_job, [(family, mu, kind, p, q, magic) for mu in G]))
+    for g in range(len(G)):
+        A[:, g] = np.linalg.solve(Um, E[g])
     I_pi = assembly.fa_tensor_untrimmed(kind, p, q)
     return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic)
 

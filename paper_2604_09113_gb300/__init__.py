@@ -65,6 +65,7 @@ def _load():
         "romb_compliance_grad": ([P, P, P, P, P], I),
         "romb_compliance_grad_noalloc": ([P, P, P, P, P], I),
         "romb_train_snapshot": ([ctypes.POINTER(RombTrainSpec), P, P], I),
+        "romb_fma_probe": ([I, I, I, I, P, P, ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +189,16 @@ def romb_compliance_grad_noalloc(ctx, n_ctrl: int, ncells: int):
     _check(_lib.romb_compliance_grad_noalloc(ctx, ctypes.byref(c), dx.ctypes.data, dR.ctypes.data,
                                              dmu.ctypes.data), "romb_compliance_grad_noalloc")
     return c.value, dx, dR, dmu
+
+
+def romb_fma_probe(precision: int, blocks: int, threads: int, iters: int, cuda_stream, out) -> float:
+    """Enqueue the FMA-rate probe (precision 0 FP64, 1 FP32) on a stream;
+    ``out`` is a CUDA tensor of blocks * threads elements.  Returns the
+    launch's floating-point operations (the caller times the launch)."""
+    fl = ctypes.c_double()
+    _check(_lib.romb_fma_probe(precision, blocks, threads, iters, cuda_stream, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.byref(fl)), "romb_fma_probe")
+    return fl.value
 
 
 def romb_launch_count(ctx) -> int:

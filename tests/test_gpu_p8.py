@@ -3,19 +3,16 @@ the 256 x 256 graded-circle workload: the CUDA path against the oracle on a
 small lattice with quartic maps, for the FP64 form and both tensor-core split
 forms, with several seeded load sets sharing one factorisation.
 
-The reduced model (rank 40, r = 2) is trained by the library's trainer over a
-narrow parameter box so that every cell matrix is positive semi-definite with
+The reduced model (rank 40, r = 2) is trained by the oracle over a narrow
+parameter box so that every cell matrix is positive semi-definite with
 exactly the three rigid-body zero modes (weaker models give indefinite cells
-at p = 8 in every form, FP64 included); the oracle reads the same model file.
+at p = 8 in every form, FP64 included); the GPU loads the same model file.
 """
-import os
-import tempfile
-
 import numpy as np
 import pytest
 
 import lattice_inputs as LI
-from oracle import assembly, bddc as obddc, geometry as ogeo, pipeline, rom as orom
+from oracle import assembly, bddc as obddc, geometry as ogeo, offline, pipeline, rom as orom
 
 from romb_testutil import unpack_upper
 
@@ -28,8 +25,8 @@ LO, HI = 0.22, 0.34
 
 @pytest.fixture(scope="module")
 def model():
-    path = os.path.join(tempfile.mkdtemp(prefix="romb_p8_"), "circle_p8.rom")
-    romb.romb_train(0, 0, P, 2, 40, LO, HI, LI.lhs(48, LO, HI, seed=81), path)
+    spec = LI.RomSpec(LI.FAMILY_CIRCLE, LO, HI, p=P, r=2, n_r=40, n_s=48, seed=81)
+    path = offline.trained_model(spec, LI.lhs(spec.n_s, LO, HI, seed=spec.seed))
     R = orom.read(path)
     lat = LI.lattice(4, 3, P, 4, seed=61, mu_mode="uniform", mu_range=(LO + 0.01, HI - 0.01), rho=5e-4)
     return dict(path=path, R=R, lat=lat, K=pipeline.matrices_rom(lat, {0: R}))
@@ -83,7 +80,7 @@ def test_split_forms_p8(model):
     ref = pipeline.solve(lat, Ko, obddc.lattice_loads(lat), rtol=1e-12)
     with romb.Context(0) as ctx:
         romb.romb_train_load(ctx.h, model["path"])
-        for prec, kbound, ubound in ((romb.ROMB_FP32_SPLIT, 1e-5, 1e-5), (romb.ROMB_BF16_SPLIT, 2.0 ** -14, 1e-2)):
+        for prec, kbound, ubound in ((romb.ROMB_FP32_SPLIT, 1e-5, 1e-6), (romb.ROMB_BF16_SPLIT, 2.0 ** -14, 1e-2)):
             Kg = _K(ctx, lat, prec)
             worst = max(_rel(unpack_upper(Kg[c], nd), Ko[c]) for c in range(lat.ncells))
             # split forms: theta interpolated in double-float (bound as at p = 6)

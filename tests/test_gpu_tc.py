@@ -2,8 +2,8 @@
 hi / lo splits) against the FP64 GPU form and the oracle.  Bar for the TF32
 form: relative Frobenius error of every cell matrix <= 1e-5 (FP32 split with
 FP32 accumulation; K dimension <= 64 terms, 36-term FP32 epilogue: a few 1e-7
-expected), and the displacement of the FP64 solve with the split-form matrices
-close to the oracle's.  The BF16 form's bound is derived in its test."""
+expected), and the displacement of the FP64 solve with the split-form
+matrices within 1e-6 (relative L2) of the oracle's.  The BF16 form's bound is derived in its test."""
 import numpy as np
 import pytest
 
@@ -49,7 +49,8 @@ def test_tc_matches_fp64_and_oracle(n_r):
     ref = pipeline.solve(lat, Ko, obddc.lattice_loads(lat), rtol=1e-12)
     err = np.linalg.norm(u32[0] - ref["u"]) / np.linalg.norm(ref["u"])
     print(f"n_r={n_r}: worst K rel {worst:.2e}, displacement rel {err:.2e}, iters {its[0]} / {ref['iters']}")
-    assert err < 1e-5
+    # the displacement bar of the split form: 1e-6 relative L2 from the oracle
+    assert err <= 1e-6
 
 
 def test_tc_full_rank_model_from_library_trainer(tmp_path):
@@ -77,7 +78,7 @@ def test_tc_full_rank_model_from_library_trainer(tmp_path):
     derr = np.linalg.norm(u["split"] - u["fp64"]) / np.linalg.norm(u["fp64"])
     print(f"rank 60: K rel error max {max(errs):.2e} median {np.median(errs):.2e}; displacement {derr:.2e}")
     assert max(errs) <= 1e-5
-    assert derr <= 1e-5
+    assert derr <= 1e-6
 
 
 @pytest.mark.parametrize("n_r", [60])

@@ -1,7 +1,8 @@
 """The benchmarked workload at full size: 132 x 132 = 17,424 cells, p = 6,
 quartic maps, circle holes and crosses 50/50, rank-60 models per family
-trained by the library's trainer, run in the launch configuration the
-benchmark times (a caller-owned CUDA stream, lattice arrays resident on the
+trained by the oracle (Sec. 4.2, on the workload's 400 seeded Latin hypercube
+samples; the GPU loads the same model files), run in the launch
+configuration the benchmark times (a caller-owned CUDA stream, lattice arrays resident on the
 device, displacement written to a device tensor, PCG rtol 1e-8).
 
 Checked against the oracle where it can compute outputs one by one, and by
@@ -14,6 +15,10 @@ properties that hold at any size where it cannot:
     1e-3 for q = 2);
   * the split-form displacement against the FP64 form (<= 1e-6 relative L2),
     both solved by the FP64 BDDC-PCG;
+  * on the first 24 x 24 cells of the workload (the same maps, thresholds
+    and models), the whole path against the oracle's: the split form's
+    displacement within 1e-6 and the FP64 form's within 1e-8 of the oracle's
+    FP64 BDDC-PCG solution, iteration counts within one;
   * global equilibrium f - K u of the returned displacement, with K the
     library's FP64 cell matrices and f the oracle's loads, scattered here.
 """
@@ -24,7 +29,7 @@ import numpy as np
 import pytest
 
 import lattice_inputs as LI
-from oracle import assembly, bddc as obddc, geometry as ogeo, pipeline, rom as orom
+from oracle import assembly, bddc as obddc, geometry as ogeo, offline, pipeline, rom as orom
 
 from romb_testutil import unpack_upper
 
@@ -37,16 +42,19 @@ SAMPLE_SEED = 1003
 
 
 @pytest.fixture(scope="module")
-def run():
-    d = tempfile.mkdtemp(prefix="romb_full_")
-    paths, roms = [], {}
-    for spec in LI.rom_specs(WORKLOAD):
-        path = os.path.join(d, f"family{spec.family}.rom")
-        romb.romb_train(spec.family, 0, spec.p, spec.r, spec.n_r, spec.lo, spec.hi,
-                        LI.lhs(spec.n_s, spec.lo, spec.hi, seed=spec.seed), path)
-        paths.append(path)
+def models():
+    """Oracle-trained rank-60 models of both families (cached per machine)."""
+    paths = offline.workload_models(LI.rom_specs(WORKLOAD), lambda n, lo, hi, seed: LI.lhs(n, lo, hi, seed=seed))
+    roms = {}
+    for path in paths:
         R = orom.read(path)
         roms[R.family] = R
+    return paths, roms
+
+
+@pytest.fixture(scope="module")
+def run(models):
+    paths, roms = models
     lat = LI.config(WORKLOAD)
     nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
     dev = torch.device("cuda", 0)
@@ -159,3 +167,46 @@ def test_global_equilibrium(run):
     print(f"global equilibrium: |f - K u| / |f| = {res:.2e} on {free.sum()} free DoFs")
     # PCG stops at 1e-8 on the interface system; the interior recovery is exact
     assert res <= 1e-7
+
+
+@pytest.fixture(scope="module")
+def mid(models):
+    """The first 24 x 24 cells of the workload: GPU (both forms, the bench's
+    launch configuration) and oracle, all solved to rtol 1e-10."""
+    paths, roms = models
+    lat = LI.sub_lattice(LI.config(WORKLOAD), 24, 24)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        darr = {"ctrl": torch.from_numpy(lat.ctrl).to(dev), "mu": torch.from_numpy(lat.mu).to(dev),
+                "family": torch.from_numpy(lat.family).to(dev),
+                "traction": torch.from_numpy(lat.traction.reshape(8).copy()).to(dev)}
+        u_dev = torch.zeros((1, nodes, 2), dtype=torch.float64, device=dev)
+        stream.synchronize()
+        with romb.Context(0, 0, stream.cuda_stream) as ctx:
+            for path in paths:
+                romb.romb_train_load(ctx.h, path)
+            for name, prec in (("split", romb.ROMB_FP32_SPLIT), ("fp64", romb.ROMB_FP64)):
+                romb.romb_assemble(ctx.h, lat, prec, device_arrays=darr)
+                romb.romb_factor(ctx.h)
+                _, its, rel = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-10, maxit=800, out=u_dev)
+                stream.synchronize()
+                out[name] = dict(u=u_dev[0].cpu().numpy().copy(), its=int(its[0]), rel=float(rel[0]))
+    K = pipeline.matrices_rom(lat, roms)
+    out["oracle"] = pipeline.solve(lat, K, obddc.lattice_loads(lat), rtol=1e-10, maxit=800)
+    return out
+
+
+def test_mid_size_sub_lattice_against_oracle(mid):
+    ref = mid["oracle"]
+    nrm = np.linalg.norm(ref["u"])
+    e32 = np.linalg.norm(mid["split"]["u"] - ref["u"]) / nrm
+    e64 = np.linalg.norm(mid["fp64"]["u"] - ref["u"]) / nrm
+    print(f"24 x 24 cells of the workload vs oracle: split {e32:.2e}, fp64 {e64:.2e}; iterations "
+          f"{mid['split']['its']} / {mid['fp64']['its']} / oracle {ref['iters']}")
+    assert e32 <= 1e-6
+    assert e64 <= 1e-8
+    assert abs(mid["fp64"]["its"] - ref["iters"]) <= 1
+    assert abs(mid["split"]["its"] - ref["iters"]) <= 1
