@@ -615,7 +615,7 @@ def run_ours(a):
         line = {
             "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32split": "tf32x3+f64", "bf16split": "bf16x3+f64"}[form], "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32split": "tf32x3+f64", "bf16split": "bf16x10+f64"}[form], "data": "synthetic",
             "config": {"workload": "132x132 lattice, p=6, quartic maps, circle/cross 50/50, n_r=60 per family",
                        "cells": lat.ncells, "p": lat.p, "assembly_form": form,
                        "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},

@@ -63,7 +63,7 @@ typedef enum {
 typedef enum {
   ROMB_FP64 = 0,        /* assembly contraction in FP64 on the CUDA cores          */
   ROMB_FP32_SPLIT = 1,  /* tcgen05 kind::tf32, 3-term hi/lo split, FP32 accumulate */
-  ROMB_BF16_SPLIT = 2   /* tcgen05 kind::f16 (bf16), 3-term split, FP32 accumulate */
+  ROMB_BF16_SPLIT = 2   /* tcgen05 kind::f16 (bf16), 4-part split, 10 products     */
 } romb_precision;
 
 typedef enum { ROMB_MEM_HOST = 0, ROMB_MEM_DEVICE = 1 } romb_mem;

@@ -323,9 +323,10 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, ThetaFams F,
       if (t < nr) th[1 + t] = (1.0 - P.rho) * lam[s][j];
     }
     __syncwarp();
-    // TF32 hi / lo split of theta, zero padded to 128 slots
+    // TF32 hi / lo split of the tensor-core slots of theta (0 and 2..; slot 1
+    // is applied in the epilogue), zero padded to 128 slots
     for (int t = lane; t < 128; t += 32) {
-      const double v = (t >= 2 && t <= nr) ? th[t] : 0.0;
+      const double v = (t == 0 || (t >= 2 && t <= nr)) ? th[t] : 0.0;
       const float h = tf32_round_dev((float)v);
       hi[t] = h;
       lo[t] = tf32_round_dev((float)(v - (double)h));

@@ -71,16 +71,16 @@ def test_fp64_form_matches_oracle_with_load_sets(model):
 
 
 def test_split_forms_p8(model):
-    # bounds as at p = 6: TF32 split 1e-5 (FP32 accumulation), BF16 split 2^-14
-    # (16 significant bits per operand, three products, factor 2 for cancellation);
-    # the FP64 solve with the split-form matrices against the oracle's displacement
+    # bounds as at p = 6: cell matrices within 1e-5 (FP32 accumulation of the
+    # tensor-core rows) in both split forms, and the FP64 solve with the
+    # split-form matrices within the 1e-6 bar of the oracle's displacement
     lat, Ko = model["lat"], model["K"]
     nd = 2 * (P + 1) ** 2
     nodes = (P * lat.nx + 1) * (P * lat.ny + 1)
     ref = pipeline.solve(lat, Ko, obddc.lattice_loads(lat), rtol=1e-12)
     with romb.Context(0) as ctx:
         romb.romb_train_load(ctx.h, model["path"])
-        for prec, kbound, ubound in ((romb.ROMB_FP32_SPLIT, 1e-5, 1e-6), (romb.ROMB_BF16_SPLIT, 2.0 ** -14, 1e-2)):
+        for prec, kbound, ubound in ((romb.ROMB_FP32_SPLIT, 1e-5, 1e-6), (romb.ROMB_BF16_SPLIT, 1e-5, 1e-6)):
             Kg = _K(ctx, lat, prec)
             worst = max(_rel(unpack_upper(Kg[c], nd), Ko[c]) for c in range(lat.ncells))
             # split forms: theta interpolated in double-float (bound as at p = 6)
