@@ -53,6 +53,9 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
+                    help="3: the headline (132 x 132, p = 6); 4: the compliance gradient on 64 x 64 cells; "
+                         "5: 256 x 256 cells, p = 8, 16 load sets sharing one factorisation")
     ap.add_argument("--sub", type=int, default=0,
                     help="profiling only: run the first N x N cells of the workload")
     ap.add_argument("--cpu-sample-json", default=None, help=argparse.SUPPRESS)
@@ -633,6 +636,186 @@ def run_ours(a):
 
 
 # ---------------------------------------------------------------------------
+# the other two workloads (opt-in lines; the headline is workload 3)
+# ---------------------------------------------------------------------------
+def _setup(a, k: int):
+    import torch
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
+    t0 = time.time()
+    paths = []
+    for spec in LI.rom_specs(k):
+        path = os.path.join(rom_dir, f"w{k}_family{spec.family}.rom")
+        if not os.path.exists(path):
+            romb.romb_train(spec.family, 0, spec.p, spec.r, spec.n_r, spec.lo, spec.hi,
+                            LI.lhs(spec.n_s, spec.lo, spec.hi, seed=spec.seed), path)
+        paths.append(path)
+    train_s = time.time() - t0
+    lat = LI.config(k)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    ctx = romb.Context(0, 0, stream.cuda_stream)
+    for p_ in paths:
+        romb.romb_train_load(ctx.h, p_)
+    darr = {"ctrl": torch.from_numpy(lat.ctrl).to(dev), "mu": torch.from_numpy(lat.mu).to(dev),
+            "family": torch.from_numpy(lat.family).to(dev),
+            "traction": torch.from_numpy(lat.traction.reshape(8).copy()).to(dev)}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MB > L2
+    return dev, stream, ctx, lat, darr, flush, train_s, free0
+
+
+def _timed(torch, stream, flush, steps: int, fn):
+    times, out = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        out.append(r)
+    return times, out
+
+
+def run_workload5(a):
+    """256 x 256 cells, p = 8, quartic maps, graded circle holes, rank-80 model,
+    split-precision assembly (BF16 form unless --precision says otherwise),
+    16 seeded load sets sharing one factorisation; one step = assembly,
+    factor, and the 16 solves."""
+    import numpy as np
+    import torch
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+    dev, stream, ctx, lat, darr, flush, train_s, free0 = _setup(a, 5)
+    nrhs = 16
+    tr = torch.from_numpy(LI.traction_sets(nrhs, seed=1005).reshape(nrhs, 8)).to(dev)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    u = torch.zeros((nrhs, nodes, 2), dtype=torch.float64, device=dev)
+    forms = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT, "bf16split": romb.ROMB_BF16_SPLIT}
+    form = "bf16split" if a.precision == "auto" else a.precision
+
+    def step(pr, k=nrhs):
+        romb.romb_assemble(ctx.h, lat, pr, device_arrays=darr)
+        romb.romb_factor(ctx.h)
+        _, its, rel = romb.romb_bddc_solve(ctx.h, nodes, nrhs=k, traction_sets=tr[:k], rtol=1e-8, maxit=800,
+                                          out=u[:k])
+        return its.tolist()
+
+    for _ in range(a.warmup):
+        step(forms[form])
+    torch.cuda.synchronize(dev)
+    held = free0 - torch.cuda.mem_get_info(dev)[0]
+    clocks = Clocks(0)
+    clocks.start()
+    times, its = _timed(torch, stream, flush, a.steps, lambda: (step(forms[form]), romb.romb_stats(ctx.h)[0].copy()))
+    clk = clocks.stop()
+    ms = sum(times) / len(times)
+    ph = np.mean(np.array([p for _, p in its]), axis=0)
+    names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery", "copies", "total"]
+    acc = {}
+    if not a.no_accuracy:
+        ref = None
+        for name in ("fp64", "fp32split", "bf16split"):
+            step(forms[name], 2)
+            v = u[:2].clone()
+            if ref is None:
+                ref = v
+                continue
+            acc[f"disp_rel_l2_{name}_vs_fp64"] = [
+                (torch.linalg.vector_norm(v[k] - ref[k]) / torch.linalg.vector_norm(ref[k])).item() for k in range(2)]
+    line = {"metric": "cells/s assembled+solved at 65,536 cells p=8, 16 load sets sharing one factorisation",
+            "value": lat.ncells / (ms / 1e3), "unit": "cells/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32split": "tf32x3+f64", "bf16split": "bf16x10+f64"}[form],
+            "data": "synthetic",
+            "config": {"workload": "256x256 lattice, p=8, quartic maps, graded circle holes 0.2-0.42, n_r=80",
+                       "cells": lat.ncells, "p": lat.p, "assembly_form": form, "load_sets": nrhs,
+                       "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
+            "clocks": clk, "pcg_iters": its[-1][0], "phase_ms": {n: float(v) for n, v in zip(names, ph)},
+            "device_bytes_held": int(held), "offline_train_s": train_s, "accuracy": acc or None}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_workload4(a):
+    """The compliance gradient workload: 64 x 64 cells, cubic maps, one hole
+    radius per cell, p = 6, rank-40 model; one step = FP64-form assembly,
+    factor, solve and the adjoint gradient with respect to every control
+    point and radius (device outputs).  Untimed: central differences of the
+    compliance along seeded directions against the adjoint gradient."""
+    import numpy as np
+    import torch
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+    import ctypes
+    dev, stream, ctx, lat, darr, flush, train_s, free0 = _setup(a, 4)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    u = torch.zeros((1, nodes, 2), dtype=torch.float64, device=dev)
+    gx = torch.zeros(lat.ctrl.shape, dtype=torch.float64, device=dev)
+    gR = torch.zeros(lat.ncells, dtype=torch.float64, device=dev)
+    cval = ctypes.c_double()
+    ev = {}
+
+    def step(lt=None, darr_=None):
+        romb.romb_assemble(ctx.h, lt or lat, romb.ROMB_FP64, device_arrays=darr_ or darr)
+        romb.romb_factor(ctx.h)
+        romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-12, maxit=1000, out=u)
+        ev["g0"] = torch.cuda.Event(enable_timing=True)
+        ev["g1"] = torch.cuda.Event(enable_timing=True)
+        ev["g0"].record(stream)
+        st = romb._lib.romb_compliance_grad(ctx.h, ctypes.byref(cval), ctypes.c_void_p(gx.data_ptr()),
+                                            ctypes.c_void_p(gR.data_ptr()), None)
+        ev["g1"].record(stream)
+        if st != 0:
+            raise romb.RombError(st, "romb_compliance_grad")
+        return cval.value
+
+    for _ in range(a.warmup):
+        step()
+    times, gms = [], []
+    for _ in range(a.steps):
+        t, _ = _timed(torch, stream, flush, 1, step)
+        times += t
+        gms.append(ev["g0"].elapsed_time(ev["g1"]))
+    ms = sum(times) / len(times)
+    c0 = step()
+    g_ctrl, g_R = gx.cpu().numpy().copy(), gR.cpu().numpy().copy()
+    nfd = 20
+    V = LI.directions(nfd, lat.ctrl.size + lat.ncells, seed=1000 + 4)
+    gnorm = float(np.sqrt((g_ctrl ** 2).sum() + (g_R ** 2).sum()))
+    worst, h = 0.0, 1e-6
+    for v in V:
+        vx, vr = v[:lat.ctrl.size].reshape(lat.ctrl.shape), v[lat.ctrl.size:]
+        cs = []
+        for sgn in (1, -1):
+            lp = LI.Lattice(**{**lat.__dict__, "ctrl": lat.ctrl + sgn * h * vx, "mu": lat.mu + sgn * h * vr[:, None]})
+            dp = {"ctrl": torch.from_numpy(lp.ctrl).to(dev), "mu": torch.from_numpy(lp.mu).to(dev),
+                  "family": darr["family"], "traction": darr["traction"]}
+            cs.append(step(lp, dp))
+        fd = (cs[0] - cs[1]) / (2 * h)
+        worst = max(worst, abs(fd - ((g_ctrl * vx).sum() + (g_R * vr).sum())) / gnorm)
+    line = {"metric": "compliance gradients/s at 4,096 cells p=6 (adjoint, all control points and radii)",
+            "value": 1e3 / ms, "unit": "gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "64x64 lattice, p=6, cubic maps, circle hole radius per cell, n_r=40",
+                       "cells": lat.ncells, "control_points": len(lat.ctrl), "pcg_rtol": 1e-12,
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "step": "FP64 assembly + factor + solve + adjoint gradient"},
+            "grad_ms": float(np.mean(gms)), "compliance": c0,
+            "fd_check": {"directions": nfd, "h": h, "worst_abs_err_over_grad_norm": worst},
+            "offline_train_s": train_s}
+    print(json.dumps(line))
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def run_reference(a):
@@ -674,6 +857,10 @@ def main():
         return
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == 5:
+        run_workload5(a)
+    elif a.workload == 4:
+        run_workload4(a)
     else:
         run_ours(a)
 

@@ -95,8 +95,12 @@ def reduced_vector_derivative(R, mu4, d):
     return R.A @ w
 
 
-def compliance_gradient(lat, roms: dict, rtol: float = 1e-13):
-    """Returns (c, dc/dctrl [n_ctrl, 2], dc/dmu [cells, 4], u nodal)."""
+def compliance_gradient(lat, roms: dict, rtol: float = 1e-13, cells=None):
+    """Returns (c, dc/dctrl [n_ctrl, 2], dc/dmu [cells, 4], u nodal).
+
+    ``cells``: if given, only these cells' terms are accumulated (the solve
+    still covers the whole lattice); c and dc/dctrl are then partial sums,
+    complete for the control points that no other cell shares."""
     nB = (lat.p + 1) ** 2
     K = pipeline.matrices_rom(lat, roms)
     f = bddc.lattice_loads(lat)
@@ -108,9 +112,12 @@ def compliance_gradient(lat, roms: dict, rtol: float = 1e-13):
     c = 0.0
     dctrl = np.zeros_like(lat.ctrl)
     dmu = np.zeros((lat.ncells, 4))
+    want = None if cells is None else set(int(k) for k in cells)
     for cy in range(lat.ny):
         for cx in range(lat.nx):
             cell = cx + lat.nx * cy
+            if want is not None and cell not in want:
+                continue
             R = roms[int(lat.family[cell])]
             g = L.cell_global_nodes(cx, cy)
             ui = u[g].ravel()                      # local DoF 2k + i

@@ -210,16 +210,16 @@ __host__ __device__ inline uint32_t canon_off16(int row, int k, int KT) {
   return (uint32_t)((row >> 3) * (KT * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Operand parts of the split forms: TF32 hi + lo (products hi hi, hi lo,
-// lo hi), BF16 b0 + b1 + b2 + b3 (~32 significant bits; the ten products
-// b_i b_j with i + j <= 3, smallest first).
+// Operand parts of the split forms: TF32 hi + lo (products lo hi, hi lo,
+// hi hi), BF16 b0 + b1 + b2 + b3 (~32 significant bits; the ten products
+// b_i b_j with i + j <= 3); both lists smallest first.
 template <bool BF>
 struct TcSplit {
   static constexpr int NPART = BF ? 4 : 2;
   static constexpr int NPROD = BF ? 10 : 3;
 };
 __constant__ int8_t c_tc_prod[2][10][2] = {
-    {{0, 0}, {0, 1}, {1, 0}},
+    {{1, 0}, {0, 1}, {0, 0}},
     {{3, 0}, {2, 1}, {1, 2}, {0, 3}, {2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}}};
 
 // BF16 parts of x: b0 = bf16(x), b1 = bf16(x - b0), ... (residuals exact in FP64)
@@ -362,12 +362,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) assemble_tc_kernel(TcParams P) 
         tc_fence_after();
         const uint32_t b0 = smem_u32(Bst + (size_t)s * stage_bytes);
         const uint32_t d = tmem + (uint32_t)(b * TC_N);
-        // one instruction covers two core matrices along K (32 bytes): 8 TF32 or 16 BF16
-        for (int kk = 0; kk < KT / (32 / (int)ES); ++kk) {
-          const uint32_t ko = (uint32_t)kk * 256;
-#pragma unroll
-          for (int m = 0; m < Sp::NPROD; ++m) {
-            const int ia = c_tc_prod[BF][m][0], ib = c_tc_prod[BF][m][1];
+        // One instruction covers two core matrices along K (32 bytes): 8 TF32
+        // or 16 BF16.  Every instruction rounds the FP32 accumulator, so the
+        // small correction products go first, over all of K, while the
+        // accumulator is still small; the leading products come last and
+        // round the full-size sum only KT / 8 (TF32) or KT / 16 (BF16) times.
+        const int nk = KT / (32 / (int)ES);
+#pragma unroll 1
+        for (int m = 0; m < Sp::NPROD; ++m) {
+          const int ia = c_tc_prod[BF][m][0], ib = c_tc_prod[BF][m][1];
+          for (int kk = 0; kk < nk; ++kk) {
+            const uint32_t ko = (uint32_t)kk * 256;
             const uint64_t ad = smem_desc(a0 + ia * a_bytes + ko, lbo, sbo);
             const uint64_t bd = smem_desc(b0 + ib * b_bytes + ko, lbo, sbo);
             if (BF) mma_bf16(d, ad, bd, idesc, (kk > 0 || m > 0) ? 1u : 0u);

@@ -1,0 +1,51 @@
+"""BDDC-PCG iteration counts of the GPU against the oracle's on lattices shaped
+like the benchmark workload (p = 6, quartic maps, circle holes, crosses and
+both mixed, two stabilisation factors, 4 x 4 to 32 x 32 cells), with the
+workload's oracle-trained rank-60 models.  The expected counts are the
+oracle's own, written by tests/golden/make_pcg_iterations.py; the GPU's
+count may differ by one (rounding decides the last iteration)."""
+import os
+
+import pytest
+
+import lattice_inputs as LI
+from oracle import offline
+
+pytestmark = pytest.mark.gpu
+romb = pytest.importorskip("paper_2604_09113_gb300")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FRAC = {"circle": 0.0, "cross": 1.0, "mixed": 0.5}
+
+
+def _rows():
+    path = os.path.join(HERE, "golden", "pcg_iterations_p6.txt")
+    out = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            n, mix, rho, its, _ = line.split()
+            out.append((int(n), mix, float(rho), int(its)))
+    return out
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    paths = offline.workload_models(LI.rom_specs(3), lambda k, lo, hi, seed: LI.lhs(k, lo, hi, seed=seed))
+    c = romb.Context(0)
+    for path in paths:
+        romb.romb_train_load(c.h, path)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,mix,rho,its", _rows())
+def test_iterations_match_oracle(ctx, n, mix, rho, its):
+    lat = LI.lattice(n, n, 6, 4, seed=1003, mu_mode="uniform", mu_range=(0.2, 0.4), cross_range=(0.08, 0.2),
+                     cross_fraction=FRAC[mix], rho=rho)
+    romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
+    romb.romb_factor(ctx.h)
+    nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+    _, got, rel = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-8, maxit=2000)
+    print(f"{n} x {n} {mix} rho {rho:g}: GPU {got[0]} / oracle {its}")
+    assert rel[0] <= 1e-8
+    assert abs(int(got[0]) - its) <= 1
