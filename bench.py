@@ -789,7 +789,7 @@ def run_workload4(a):
     nfd = 20
     V = LI.directions(nfd, lat.ctrl.size + lat.ncells, seed=1000 + 4)
     gnorm = float(np.sqrt((g_ctrl ** 2).sum() + (g_R ** 2).sum()))
-    worst, h = 0.0, 1e-6
+    worst, h = 0.0, 2e-5
     for v in V:
         vx, vr = v[:lat.ctrl.size].reshape(lat.ctrl.shape), v[lat.ctrl.size:]
         cs = []

@@ -146,13 +146,16 @@ def romb_factor(ctx) -> None:
 def romb_bddc_solve(ctx, nodes: int, nrhs: int = 1, traction_sets=None, rtol: float = 1e-8, maxit: int = 500,
                     out=None, allow_not_converged: bool = False):
     """Returns (u [nrhs, nodes, 2], iterations [nrhs], relative residuals [nrhs]).
-    ``out`` may be a CUDA tensor of that shape (device output, when the
-    lattice was passed as device tensors)."""
+    ``out`` may be a CUDA tensor of that shape, and ``traction_sets`` a CUDA
+    tensor [nrhs, 8] (device memory, when the lattice was passed as device
+    tensors)."""
     keep = []
     if out is None:
         out = np.zeros((nrhs, nodes, 2))
     up, _ = _ptr(out, keep)
-    tp, _ = _ptr(None if traction_sets is None else np.asarray(traction_sets, dtype=np.float64), keep)
+    if traction_sets is not None and not getattr(traction_sets, "is_cuda", False):
+        traction_sets = np.asarray(traction_sets, dtype=np.float64)
+    tp, _ = _ptr(traction_sets, keep)
     its = np.zeros(nrhs, dtype=np.int32)
     rel = np.zeros(nrhs)
     st = _lib.romb_bddc_solve(ctx, nrhs, tp, rtol, maxit, up, its.ctypes.data, rel.ctypes.data)
