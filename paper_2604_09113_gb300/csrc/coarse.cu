@@ -801,13 +801,20 @@ __device__ void nd_dag_fwd_small(const NdDagArgs& A, int f, double* w, int lane)
       const int c = c0 + lane;
       const int emax = min(ns, c0 + 32);   // rows e > c of L11^-T are zero
       if (c < n) {
+        // B is read straight from L2 / HBM: eight independent loads in flight
         double z0 = 0.0, z1 = 0.0;
         int e = 0;
-        for (; e + 1 < emax; e += 2) {
-          z0 = fma(__ldg(Bs + (long long)e * n + c), w[e], z0);
-          z1 = fma(__ldg(Bs + (long long)(e + 1) * n + c), w[e + 1], z1);
+        for (; e + 8 <= emax; e += 8) {
+          double b[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) b[u] = __ldg(Bs + (long long)(e + u) * n + c);
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            z0 = fma(b[u], w[e + u], z0);
+            z1 = fma(b[u + 1], w[e + u + 1], z1);
+          }
         }
-        if (e < emax) z0 = fma(__ldg(Bs + (long long)e * n + c), w[e], z0);
+        for (; e < emax; ++e) z0 = fma(__ldg(Bs + (long long)e * n + c), w[e], z0);
         const double z = z0 + z1;
         if (c < ns) A.sbuf[fd.sbuf_off + c] = z;
         else A.ybuf[fd.ybuf_off + c - ns] = w[c] + z;
@@ -841,7 +848,16 @@ __device__ void nd_dag_bwd_small(const NdDagArgs& A, int f, double* v, int lane)
       double s = 0.0;
       if (e < ns) {
         const double* row = Bs + (long long)e * n;
-        for (int c = (e0 / P) * P + h; c < n; c += P) s = fma(__ldg(row + c), v[c], s);
+        int c = (e0 / P) * P + h;
+        for (; c + 3 * P < n; c += 4 * P) {
+          const double b0 = __ldg(row + c), b1 = __ldg(row + c + P), b2 = __ldg(row + c + 2 * P),
+                       b3 = __ldg(row + c + 3 * P);
+          s = fma(b0, v[c], s);
+          s = fma(b1, v[c + P], s);
+          s = fma(b2, v[c + 2 * P], s);
+          s = fma(b3, v[c + 3 * P], s);
+        }
+        for (; c < n; c += P) s = fma(__ldg(row + c), v[c], s);
       }
       for (int o = R; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (h == 0 && e < ns) A.x[id[e]] = s;
@@ -852,8 +868,9 @@ __device__ void nd_dag_bwd_small(const NdDagArgs& A, int f, double* v, int lane)
 }
 
 __global__ void __launch_bounds__(256) nd_solve_dag_kernel(NdDagArgs A) {
+  // dynamic shared memory: a row chunk and its vector, or (small fronts) one
+  // vector of up to ND_SMALL_N per warp
   extern __shared__ __align__(16) double sh[];
-  __shared__ double wsm[8][ND_SMALL_N];
   __shared__ uint64_t bar;
   __shared__ int s_item, s_first, s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -869,8 +886,8 @@ __global__ void __launch_bounds__(256) nd_solve_dag_kernel(NdDagArgs A) {
     if (it.kind == 0 || it.kind == 2) {
       if (warp < it.b) {
         const int f = A.small_list[it.a + warp];
-        if (it.kind == 0) nd_dag_fwd_small(A, f, wsm[warp], lane);
-        else nd_dag_bwd_small(A, f, wsm[warp], lane);
+        if (it.kind == 0) nd_dag_fwd_small(A, f, sh + warp * ND_SMALL_N, lane);
+        else nd_dag_bwd_small(A, f, sh + warp * ND_SMALL_N, lane);
       }
       continue;
     }
@@ -1229,15 +1246,16 @@ romb_status coarse_build(romb_ctx* c) {
   // B^T storage (+2 doubles: bulk copies read 16-byte aligned spans)
   if ((s = romb_alloc_t(c, &D.BT, (size_t)bttot + 2)) != ROMB_OK) return s;
   // one-launch solve: work items in topological order (forward by level from
-  // the leaves, backward from the root), row chunks of at most 40 KB so that
-  // several CTAs share an SM; every front has at least one item per sweep
+  // the leaves, backward from the root), row chunks of at most 24 KB so that
+  // several CTAs share an SM (also beside the fine preconditioner product);
+  // every front has at least one item per sweep
   {
     auto dag_shape = [](int len, int width) {
       NdRowShape q;
       q.P = 1;
       while (q.P < 32 && q.P * 16 < len) q.P <<= 1;
       q.rb = 8 * (32 / q.P);
-      while (q.rb > 8 && (size_t)q.rb * width * 8 > 40 * 1024) q.rb >>= 1;
+      while (q.rb > 1 && (size_t)q.rb * width * 8 > 24 * 1024) q.rb >>= 1;
       q.ld = width;
       return q;
     };
@@ -1249,7 +1267,7 @@ romb_status coarse_build(romb_ctx* c) {
     std::vector<int> small;
     std::vector<NdRowShape> fsh, bsh;
     std::vector<int> small_off(L, -1);
-    size_t smem = 16;
+    size_t smem = (size_t)8 * ND_SMALL_N * 8;   // the small-front vectors of 8 warps
     for (int l = 0; l < L; ++l) {
       fsh.push_back(dag_shape(D.level_maxns[l], D.level_maxns[l]));
       bsh.push_back(dag_shape(D.level_maxn[l], D.level_maxn[l]));
