@@ -15,8 +15,6 @@
 // Solve: forward (leaves -> root) and backward (root -> leaves) substitution,
 // one GEMV with B per front and sweep, one launch per level and sweep.
 #include <stdio.h>
-#include <stdlib.h>
-#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -141,9 +139,6 @@ struct FrontDev {
   int wbuf_off;      // extend-add sources of each of the n rows (gsrc)
   int sbuf_off;      // forward result y_s = L11^-1 w_s (ns)
   long long bt_off;  // B^T (n x ns, row-major) of fronts on the row-kernel levels, -1 elsewhere
-  int parent;        // parent front (-1 at the root)
-  int fwd_chunks;    // work items of the forward / backward step of this front in the
-  int bwd_chunks;    // one-launch solve (1 for small fronts, row chunks otherwise)
 };
 
 }  // namespace
@@ -701,297 +696,6 @@ __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __rest
   if (j < nr && h == 0) x[id[e]] = s;
 }
 
-// ---- the whole solve in one launch, driven by dependencies ----
-// The forward steps of all fronts (leaves first) and then the backward steps
-// (root first) form one queue of work items in topological order: a group of
-// up to 8 small fronts (one warp each) or a chunk of rows of one large front
-// (the whole CTA, as in the row kernels above).  Persistent CTAs take items
-// from the queue in order (an atomic counter); an item waits until the
-// fronts it reads from are complete: in the forward sweep its children (all
-// their chunks), in the backward sweep its parent (whose completion implies
-// every ancestor's and, through the root, every forward step).  Every item a
-// CTA waits for was taken earlier by a running CTA and itself waits only for
-// earlier items, so the waits always end and no co-residency is required.
-// Completion is published with a release (fence + atomic add per item) and
-// read with acquire loads; data produced inside the launch is read through
-// L2 (ld.global.cg).  The static B rows of a row chunk are copied into shared
-// memory before the wait, so the copy overlaps it (the staging barrier is
-// initialised afresh for every chunk, so its phase parity is always 0).  Every wait is bounded; on
-// a timeout the kernel records *err and all later waits give up at once.
-struct NdDagItem {
-  int kind;   // 0 forward small fronts, 1 forward rows, 2 backward small fronts, 3 backward rows
-  int a;      // small: first entry in the small-front list; rows: the front
-  int b;      // small: number of fronts (<= 8); rows: first row of the chunk
-  int lvl;    // level (row-chunk shape)
-};
-
-__device__ __forceinline__ int nd_ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// wait until *p >= target (bounded); false on timeout or after an error
-__device__ bool nd_dag_wait(const int* p, int target, int* err) {
-  if (target <= 0) return true;
-  const long long t0 = clock64();
-  while (nd_ld_acquire(p) < target) {
-    if (*(volatile int*)err) return false;
-    if (clock64() - t0 > ROMB_WAIT_CYCLES) {
-      atomicExch(err, 2);
-      return false;
-    }
-    __nanosleep(64);
-  }
-  return true;
-}
-
-__device__ __forceinline__ void nd_dag_publish(int* p) {
-  __threadfence();
-  atomicAdd(p, 1);
-}
-
-__device__ __forceinline__ double nd_gather_row_cg(const int2 s, const double* __restrict__ ybuf) {
-  double v = 0.0;
-  if (s.x >= 0) v += __ldcg(ybuf + s.x);
-  if (s.y >= 0) v += __ldcg(ybuf + s.y);
-  return v;
-}
-
-struct NdDagArgs {
-  const FrontDev* fr;
-  const NdDagItem* items;
-  int nitems;
-  const int* small_list;
-  const NdRowShape* fshape;
-  const NdRowShape* bshape;
-  const double* F;
-  const double* BT;
-  const int* idx;
-  const int2* gsrc;
-  const int* children;
-  const double* rhs;
-  double* ybuf;
-  double* sbuf;
-  double* x;
-  int* ctr;    // [0] queue head, [1 + f] forward items done, [1 + nfronts + f] backward items done
-  int nfronts;
-  int root;
-  int* err;
-};
-
-// forward step of one small front by one warp: z = B^T w_s (B read from L2 / HBM)
-__device__ void nd_dag_fwd_small(const NdDagArgs& A, int f, double* w, int lane) {
-  const FrontDev fd = A.fr[f];
-  const int ns = fd.ns, n = ns + fd.nb;
-  int* fdone = A.ctr + 1;
-  bool ok = true;
-  if (lane == 0)
-    for (int k = 0; k < fd.nchild; ++k) {
-      const int ch = A.children[fd.child_off + k];
-      ok = ok && nd_dag_wait(fdone + ch, A.fr[ch].fwd_chunks, A.err);
-    }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (ok) {
-    for (int t = lane; t < n; t += 32)
-      w[t] = (t < ns ? __ldg(A.rhs + A.idx[fd.idx_off + t]) : 0.0) + nd_gather_row_cg(A.gsrc[fd.wbuf_off + t], A.ybuf);
-    __syncwarp();
-    const double* Bs = A.F + fd.off + (long long)n * n;
-    for (int c0 = 0; c0 < n; c0 += 32) {
-      const int c = c0 + lane;
-      const int emax = min(ns, c0 + 32);   // rows e > c of L11^-T are zero
-      if (c < n) {
-        // B is read straight from L2 / HBM: eight independent loads in flight
-        double z0 = 0.0, z1 = 0.0;
-        int e = 0;
-        for (; e + 8 <= emax; e += 8) {
-          double b[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) b[u] = __ldg(Bs + (long long)(e + u) * n + c);
-#pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            z0 = fma(b[u], w[e + u], z0);
-            z1 = fma(b[u + 1], w[e + u + 1], z1);
-          }
-        }
-        for (; e < emax; ++e) z0 = fma(__ldg(Bs + (long long)e * n + c), w[e], z0);
-        const double z = z0 + z1;
-        if (c < ns) A.sbuf[fd.sbuf_off + c] = z;
-        else A.ybuf[fd.ybuf_off + c - ns] = w[c] + z;
-      }
-    }
-  }
-  __syncwarp();
-  if (lane == 0) nd_dag_publish(fdone + f);
-}
-
-// backward step of one small front by one warp: x_s = B [y_s; x_b]
-__device__ void nd_dag_bwd_small(const NdDagArgs& A, int f, double* v, int lane) {
-  const FrontDev fd = A.fr[f];
-  const int ns = fd.ns, n = ns + fd.nb;
-  int* bdone = A.ctr + 1 + A.nfronts;
-  bool ok = true;
-  if (lane == 0)
-    ok = fd.parent >= 0 ? nd_dag_wait(bdone + fd.parent, A.fr[fd.parent].bwd_chunks, A.err)
-                        : nd_dag_wait(A.ctr + 1 + f, fd.fwd_chunks, A.err);
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (ok && ns > 0) {
-    const int* id = A.idx + fd.idx_off;
-    for (int c = lane; c < n; c += 32) v[c] = c < ns ? __ldcg(A.sbuf + fd.sbuf_off + c) : __ldcg(A.x + id[c]);
-    __syncwarp();
-    const double* Bs = A.F + fd.off + (long long)n * n;
-    int R = 1;
-    while (R < ns && R < 32) R <<= 1;
-    const int P = 32 / R, r = lane & (R - 1), h = lane / R;
-    for (int e0 = 0; e0 < ns; e0 += R) {
-      const int e = e0 + r;
-      double s = 0.0;
-      if (e < ns) {
-        const double* row = Bs + (long long)e * n;
-        int c = (e0 / P) * P + h;
-        for (; c + 3 * P < n; c += 4 * P) {
-          const double b0 = __ldg(row + c), b1 = __ldg(row + c + P), b2 = __ldg(row + c + 2 * P),
-                       b3 = __ldg(row + c + 3 * P);
-          s = fma(b0, v[c], s);
-          s = fma(b1, v[c + P], s);
-          s = fma(b2, v[c + 2 * P], s);
-          s = fma(b3, v[c + 3 * P], s);
-        }
-        for (; c < n; c += P) s = fma(__ldg(row + c), v[c], s);
-      }
-      for (int o = R; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (h == 0 && e < ns) A.x[id[e]] = s;
-    }
-  }
-  __syncwarp();
-  if (lane == 0) nd_dag_publish(bdone + f);
-}
-
-__global__ void __launch_bounds__(256) nd_solve_dag_kernel(NdDagArgs A) {
-  // dynamic shared memory: a row chunk and its vector, or (small fronts) one
-  // vector of up to ND_SMALL_N per warp
-  extern __shared__ __align__(16) double sh[];
-  __shared__ uint64_t bar;
-  __shared__ int s_item, s_first, s_ok;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int* fdone = A.ctr + 1;
-  int* bdone = A.ctr + 1 + A.nfronts;
-  while (true) {
-    if (tid == 0) s_item = atomicAdd(A.ctr, 1);
-    __syncthreads();
-    const int ii = s_item;
-    __syncthreads();
-    if (ii >= A.nitems) break;
-    const NdDagItem it = A.items[ii];
-    if (it.kind == 0 || it.kind == 2) {
-      if (warp < it.b) {
-        const int f = A.small_list[it.a + warp];
-        if (it.kind == 0) nd_dag_fwd_small(A, f, sh + warp * ND_SMALL_N, lane);
-        else nd_dag_bwd_small(A, f, sh + warp * ND_SMALL_N, lane);
-      }
-      continue;
-    }
-    const FrontDev f = A.fr[it.a];
-    const int ns = f.ns, n = ns + f.nb;
-    const int* id = A.idx + f.idx_off;
-    if (it.kind == 1) {
-      // forward rows [row0, row0 + nr) of B^T: z_c = sum_e B^T[c][e] w_e
-      const NdRowShape sh_ = A.fshape[it.lvl];
-      const int nr = min(sh_.rb, n - it.b);
-      double* ws = sh + ((((long long)nr * ns + 2) + 1) & ~1LL);
-      int first = 0;
-      nd_stage_rows(A.BT + f.bt_off + (long long)it.b * ns, (long long)nr * ns, sh, &bar, &first);
-      if (tid == 0) {
-        s_first = first;
-        bool ok = true;
-        for (int k = 0; k < f.nchild; ++k) {
-          const int ch = A.children[f.child_off + k];
-          ok = ok && nd_dag_wait(fdone + ch, A.fr[ch].fwd_chunks, A.err);
-        }
-        s_ok = ok;
-      }
-      __syncthreads();
-      const int2* gs = A.gsrc + f.wbuf_off;
-      for (int e = tid; e < ns; e += blockDim.x) ws[e] = __ldg(A.rhs + id[e]) + nd_gather_row_cg(gs[e], A.ybuf);
-      const int P = sh_.P, R = 32 / P;
-      const int r = lane / P, h = lane % P;
-      const int j = warp * R + r;
-      const int c = it.b + j;
-      const double wb = (j < nr && h == 0 && c >= ns) ? nd_gather_row_cg(gs[c], A.ybuf) : 0.0;
-      __syncthreads();
-      // the staging copy is waited for even after an error elsewhere: no
-      // copy may still be in flight when the CTA moves on or exits
-      const bool okc = mbar_wait(&bar, 0, nullptr);
-      if (__syncthreads_or(!okc || !s_ok)) {
-        if (tid == 0 && !okc) atomicExch(A.err, 1);
-      } else {
-        double z = 0.0;
-        if (j < nr) {
-          const double* row = sh + s_first + (long long)j * ns;
-          const int emax = c < ns ? c : ns - 1;
-          double z1 = 0.0;
-          int e = h;
-          for (; e + P <= emax; e += 2 * P) {
-            z = fma(row[e], ws[e], z);
-            z1 = fma(row[e + P], ws[e + P], z1);
-          }
-          if (e <= emax) z = fma(row[e], ws[e], z);
-          z += z1;
-        }
-        for (int o = 1; o < P; o <<= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-        if (j < nr && h == 0) {
-          if (c < ns) A.sbuf[f.sbuf_off + c] = z;
-          else A.ybuf[f.ybuf_off + c - ns] = wb + z;
-        }
-      }
-      __syncthreads();
-      if (tid == 0) nd_dag_publish(fdone + it.a);
-    } else {
-      // backward rows [row0, row0 + nr) of B: x_e = sum_c B[e][c] v_c
-      const NdRowShape sh_ = A.bshape[it.lvl];
-      const int nr = min(sh_.rb, ns - it.b);
-      double* v = sh + ((((long long)nr * n + 2) + 1) & ~1LL);
-      int first = 0;
-      nd_stage_rows(A.F + f.off + (long long)(n + it.b) * n, (long long)nr * n, sh, &bar, &first);
-      if (tid == 0) {
-        s_first = first;
-        s_ok = f.parent >= 0 ? nd_dag_wait(bdone + f.parent, A.fr[f.parent].bwd_chunks, A.err)
-                             : nd_dag_wait(fdone + it.a, f.fwd_chunks, A.err);
-      }
-      __syncthreads();
-      for (int cc = tid; cc < n; cc += blockDim.x) v[cc] = cc < ns ? __ldcg(A.sbuf + f.sbuf_off + cc) : __ldcg(A.x + id[cc]);
-      const int P = sh_.P, R = 32 / P;
-      const int r = lane / P, h = lane % P;
-      const int j = warp * R + r;
-      const int e = it.b + j;
-      __syncthreads();
-      // the staging copy is waited for even after an error elsewhere: no
-      // copy may still be in flight when the CTA moves on or exits
-      const bool okc = mbar_wait(&bar, 0, nullptr);
-      if (__syncthreads_or(!okc || !s_ok)) {
-        if (tid == 0 && !okc) atomicExch(A.err, 1);
-      } else {
-        double s = 0.0;
-        if (j < nr) {
-          const double* row = sh + s_first + (long long)j * n;
-          double s1 = 0.0;
-          int cc = (e / P) * P + h;
-          for (; cc + P < n; cc += 2 * P) {
-            s = fma(row[cc], v[cc], s);
-            s1 = fma(row[cc + P], v[cc + P], s1);
-          }
-          if (cc < n) s = fma(row[cc], v[cc], s);
-          s += s1;
-        }
-        for (int o = 1; o < P; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (j < nr && h == 0) A.x[id[e]] = s;
-      }
-      __syncthreads();
-      if (tid == 0) nd_dag_publish(bdone + it.a);
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1018,18 +722,6 @@ struct NdDevice {
   int32_t* bad = nullptr;
   int* err = nullptr;   // set by a solve kernel whose staging copy timed out
   double* linv = nullptr;   // [fronts of the widest level][32 x 32] inverses of the diagonal blocks
-  // one-launch solve
-  bool dag = false;
-  NdDagItem* dag_items = nullptr;
-  int dag_nitems = 0;
-  int* dag_small = nullptr;
-  NdRowShape* dag_fshape = nullptr;
-  NdRowShape* dag_bshape = nullptr;
-  int* dag_ctr = nullptr;      // [1 + 2 nfronts]
-  size_t dag_smem = 0;
-  int dag_grid = 0;
-  int root = 0;
-  std::vector<FrontDev> fd_host;
 };
 
 static std::unordered_map<const romb_ctx*, NdDevice> g_nd;
@@ -1045,6 +737,7 @@ romb_status coarse_build(romb_ctx* c) {
   B.NCH = 3LL * c->nx * (c->ny + 1);
   B.fronts = &plan.fronts;
   const int root = B.build(0, c->nx, 0, c->ny);
+  (void)root;
   const int nf = (int)plan.fronts.size();
   int maxd = 0;
   for (int d : B.depth) maxd = std::max(maxd, d);
@@ -1082,8 +775,6 @@ romb_status coarse_build(romb_ctx* c) {
     sbuf_tot += F.ns;
     d.emap_off = -1;
     d.bt_off = -1;
-    d.parent = F.parent;
-    d.fwd_chunks = d.bwd_chunks = 1;
   }
   // extend-add positions of each front's update rows in its parent
   for (int i = 0; i < nf; ++i) {
@@ -1176,7 +867,6 @@ romb_status coarse_build(romb_ctx* c) {
   }
   ROMB_CUDA(cudaMemset(D.err, 0, 4));
   D.nfronts = nf;
-  D.root = root;
   ROMB_CUDA(cudaMemcpy(D.gsrc, gsrc.data(), sizeof(int2) * gsrc.size(), cudaMemcpyHostToDevice));
   ROMB_CUDA(cudaMemcpy(D.asrc, asrc.data(), sizeof(int4) * asrc.size(), cudaMemcpyHostToDevice));
   ROMB_CUDA(cudaMemcpy(D.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice));
@@ -1245,78 +935,6 @@ romb_status coarse_build(romb_ctx* c) {
   }
   // B^T storage (+2 doubles: bulk copies read 16-byte aligned spans)
   if ((s = romb_alloc_t(c, &D.BT, (size_t)bttot + 2)) != ROMB_OK) return s;
-  // one-launch solve: work items in topological order (forward by level from
-  // the leaves, backward from the root), row chunks of at most 24 KB so that
-  // several CTAs share an SM (also beside the fine preconditioner product);
-  // every front has at least one item per sweep
-  {
-    auto dag_shape = [](int len, int width) {
-      NdRowShape q;
-      q.P = 1;
-      while (q.P < 32 && q.P * 16 < len) q.P <<= 1;
-      q.rb = 8 * (32 / q.P);
-      while (q.rb > 1 && (size_t)q.rb * width * 8 > 24 * 1024) q.rb >>= 1;
-      q.ld = width;
-      return q;
-    };
-    auto stage_bytes = [](int rb, int width) {
-      return 8 * (((((size_t)rb * width + 2) + 1) & ~(size_t)1) + (size_t)width);
-    };
-    const int L = (int)plan.levels.size();
-    std::vector<NdDagItem> items;
-    std::vector<int> small;
-    std::vector<NdRowShape> fsh, bsh;
-    std::vector<int> small_off(L, -1);
-    size_t smem = (size_t)8 * ND_SMALL_N * 8;   // the small-front vectors of 8 warps
-    for (int l = 0; l < L; ++l) {
-      fsh.push_back(dag_shape(D.level_maxns[l], D.level_maxns[l]));
-      bsh.push_back(dag_shape(D.level_maxn[l], D.level_maxn[l]));
-      if (D.level_small[l]) {
-        small_off[l] = (int)small.size();
-        small.insert(small.end(), plan.levels[l].begin(), plan.levels[l].end());
-      } else {
-        smem = std::max(smem, stage_bytes(fsh[l].rb, D.level_maxns[l]));
-        smem = std::max(smem, stage_bytes(bsh[l].rb, D.level_maxn[l]));
-      }
-    }
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k = 0; k < L; ++k) {
-        const int l = pass == 0 ? k : L - 1 - k;
-        const std::vector<int>& lv = plan.levels[l];
-        if (D.level_small[l]) {
-          for (size_t i = 0; i < lv.size(); i += 8)
-            items.push_back({pass == 0 ? 0 : 2, small_off[l] + (int)i, (int)std::min<size_t>(8, lv.size() - i), l});
-          continue;
-        }
-        for (int f : lv) {
-          const int ns = plan.fronts[f].ns, n = ns + plan.fronts[f].nb;
-          const int len = pass == 0 ? n : ns, rb = pass == 0 ? fsh[l].rb : bsh[l].rb;
-          int cnt = 0;
-          for (int r0 = 0; r0 < std::max(len, 1); r0 += rb, ++cnt) items.push_back({pass == 0 ? 1 : 3, f, r0, l});
-          (pass == 0 ? fd[f].fwd_chunks : fd[f].bwd_chunks) = cnt;
-        }
-      }
-    const char* sel = getenv("ROMB_COARSE_SOLVE");
-    D.dag = !(sel && strcmp(sel, "levels") == 0) && smem <= 160 * 1024;
-    if (D.dag) {
-      if ((s = romb_alloc_t(c, &D.dag_items, items.size())) != ROMB_OK) return s;
-      if ((s = romb_alloc_t(c, &D.dag_small, std::max<size_t>(1, small.size()))) != ROMB_OK) return s;
-      if ((s = romb_alloc_t(c, &D.dag_fshape, (size_t)L)) != ROMB_OK) return s;
-      if ((s = romb_alloc_t(c, &D.dag_bshape, (size_t)L)) != ROMB_OK) return s;
-      if ((s = romb_alloc_t(c, &D.dag_ctr, (size_t)1 + 2 * (size_t)nf)) != ROMB_OK) return s;
-      ROMB_CUDA(cudaMemcpy(D.dag_items, items.data(), sizeof(NdDagItem) * items.size(), cudaMemcpyHostToDevice));
-      if (!small.empty())
-        ROMB_CUDA(cudaMemcpy(D.dag_small, small.data(), 4 * small.size(), cudaMemcpyHostToDevice));
-      ROMB_CUDA(cudaMemcpy(D.dag_fshape, fsh.data(), sizeof(NdRowShape) * L, cudaMemcpyHostToDevice));
-      ROMB_CUDA(cudaMemcpy(D.dag_bshape, bsh.data(), sizeof(NdRowShape) * L, cudaMemcpyHostToDevice));
-      D.dag_nitems = (int)items.size();
-      D.dag_smem = smem;
-      ROMB_CUDA(cudaFuncSetAttribute(nd_solve_dag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int per_sm = 0;
-      ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nd_solve_dag_kernel, 256, smem));
-      D.dag_grid = std::max(1, per_sm) * c->sms;
-    }
-  }
   // front descriptors last: they carry the tile counts
   ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
   const int small_smem = 8 * ND_WPC * ND_SMALL_SMEM;
@@ -1406,33 +1024,6 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, st));
-  if (D.dag) {
-    ROMB_CUDA(cudaMemsetAsync(D.dag_ctr, 0, 4 * (1 + 2 * (size_t)D.nfronts), st));
-    NdDagArgs A;
-    A.fr = D.fr;
-    A.items = D.dag_items;
-    A.nitems = D.dag_nitems;
-    A.small_list = D.dag_small;
-    A.fshape = D.dag_fshape;
-    A.bshape = D.dag_bshape;
-    A.F = D.F;
-    A.BT = D.BT;
-    A.idx = D.idx;
-    A.gsrc = D.gsrc;
-    A.children = D.children;
-    A.rhs = d_in;
-    A.ybuf = D.ybuf;
-    A.sbuf = D.sbuf;
-    A.x = d_out;
-    A.ctr = D.dag_ctr;
-    A.nfronts = D.nfronts;
-    A.root = D.root;
-    A.err = D.err;
-    nd_solve_dag_kernel<<<D.dag_grid, 256, D.dag_smem, st>>>(A);
-    ++c->launches;
-    ROMB_CUDA(cudaGetLastError());
-    return ROMB_OK;
-  }
   const int L = (int)D.level_ids.size();
   auto small_shape = [&](int l, int* stride, int* voff) {
     *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
