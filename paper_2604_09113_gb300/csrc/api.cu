@@ -72,10 +72,11 @@ static void romb_free_ptr(romb_ctx* c, void* p) {
 
 // Free every lattice-dependent buffer (the loaded ROMs stay).
 void romb_free_lattice(romb_ctx* c) {
-  if (c->pcg_graph) {
-    cudaGraphExecDestroy(c->pcg_graph);
-    c->pcg_graph = nullptr;
-  }
+  for (PcgLane& L : c->lane)
+    if (L.graph) {
+      cudaGraphExecDestroy(L.graph);
+      L.graph = nullptr;
+    }
   for (void* p : c->allocs) {
     cudaFree(p);
     c->sizes.erase(p);
@@ -93,12 +94,24 @@ void romb_free_lattice(romb_ctx* c) {
   double* h_red = c->h_red;
   cudaEvent_t ev[16];
   for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
-  cudaStream_t side = c->side;
-  cudaEvent_t evfork = c->evfork, evjoin = c->evjoin;
+  // lanes keep their streams, events and pinned words; their device buffers
+  // went with the lattice
+  PcgLane lanes[ROMB_MAX_LANES];
+  for (int k = 0; k < ROMB_MAX_LANES; ++k) {
+    const PcgLane& o = c->lane[k];
+    PcgLane& L = lanes[k];
+    L.stream = o.stream;
+    L.side = o.side;
+    L.evfork = o.evfork;
+    L.evjoin = o.evjoin;
+    L.ev0 = o.ev0;
+    L.ev1 = o.ev1;
+    L.have_streams = o.have_streams;
+    L.own_stream = o.own_stream;
+    L.h_red = o.h_red;
+  }
   *c = romb_ctx();
-  c->side = side;
-  c->evfork = evfork;
-  c->evjoin = evjoin;
+  for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
   for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->roms[i] = roms[i];
   c->rom_allocs = keep;
   c->stream = st;
@@ -145,17 +158,12 @@ extern "C" romb_status romb_create(romb_ctx** out, int device, size_t budget, vo
     c->own_stream = true;
   }
   for (auto& e : c->ev) cudaEventCreate(&e);
-  {
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->evfork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->evjoin, cudaEventDisableTiming) != cudaSuccess) {
-      (void)cudaGetLastError();
-      romb_set_error("romb_create: stream or event creation failed");
-      delete c;
-      return ROMB_E_CUDA;
-    }
+  if (pcg_lane_streams(c, c->lane[0], true) != ROMB_OK) {
+    (void)cudaGetLastError();
+    romb_set_error("romb_create: stream or event creation failed");
+    pcg_lane_destroy(c->lane[0]);
+    delete c;
+    return ROMB_E_CUDA;
   }
   if (cudaMallocHost(&c->h_red, 64 * sizeof(double)) != cudaSuccess) {
     delete c;
@@ -169,15 +177,15 @@ extern "C" void romb_destroy(romb_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
+  for (PcgLane& L : c->lane) {
+    if (L.have_streams && L.own_stream) cudaStreamSynchronize(L.stream);
+    pcg_lane_destroy(L);
+  }
   romb_free_all(c);
   for (int l = 0; l < (int)c->nd.d_level_fronts.size(); ++l) c->nd.d_level_fronts[l] = nullptr;
   for (auto& e : c->ev) cudaEventDestroy(e);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->own_stream) cudaStreamDestroy(c->stream);
-  if (c->side) cudaStreamDestroy(c->side);
-  if (c->evfork) cudaEventDestroy(c->evfork);
-  if (c->evjoin) cudaEventDestroy(c->evjoin);
   delete c;
 }
 
@@ -385,6 +393,36 @@ static romb_status build_tables(romb_ctx* c) {
   return ROMB_OK;
 }
 
+// Device buffers of one PCG lane for the current lattice (lane 0 with the
+// lattice, further lanes on the first solve with several load sets).
+static romb_status lane_buffers(romb_ctx* c, PcgLane& L) {
+  if (L.have_bufs) return ROMB_OK;
+  const long long cells = c->ncells;
+  const long long nodes = (long long)(c->p * c->nx + 1) * (c->p * c->ny + 1);
+  romb_status s;
+#define A_(ptr, n)                                               \
+  do {                                                           \
+    if ((s = romb_alloc_t(c, &(ptr), (size_t)(n))) != ROMB_OK) return s; \
+  } while (0)
+  A_(L.d_f, c->nskel);
+  A_(L.d_x, c->nskel);
+  A_(L.d_r, c->nskel);
+  A_(L.d_z, c->nskel);
+  A_(L.d_pv, c->nskel);
+  A_(L.d_q, c->nskel);
+  A_(L.d_red, 4096);
+  A_(L.d_fU, cells * c->nU);
+  A_(L.d_cloc, cells * ROMB_NSLOT);
+  A_(L.d_yloc, cells * c->nU);
+  A_(L.d_u, 2 * nodes);
+  A_(L.d_traction, 8 * 64);
+  A_(L.d_coarse, 2 * c->ncoarse_all);
+#undef A_
+  if (&L != &c->lane[0] && (s = coarse_lane_buffers(c, &L.nd_ybuf, &L.nd_sbuf)) != ROMB_OK) return s;
+  L.have_bufs = true;
+  return ROMB_OK;
+}
+
 static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   romb_status s;
   c->nx = L->nx;
@@ -433,24 +471,14 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_islot, c->nI);
   A_(c->d_uslot, c->nU);
   A_(c->d_cmap, cells * ROMB_NSLOT);
-  A_(c->d_f, c->nskel);
-  A_(c->d_x, c->nskel);
-  A_(c->d_r, c->nskel);
-  A_(c->d_z, c->nskel);
-  A_(c->d_pv, c->nskel);
-  A_(c->d_q, c->nskel);
   A_(c->d_red, 4096);
   A_(c->d_fI, cells * c->nI);
-  A_(c->d_fU, cells * c->nU);
-  A_(c->d_cloc, cells * ROMB_NSLOT);
-  A_(c->d_yloc, cells * c->nU);
-  A_(c->d_u, 2 * nodes);
-  A_(c->d_traction, 8 * 64);
   A_(c->d_pcg_err, 1);
 #undef A_
   ROMB_CUDA(cudaMemsetAsync(c->d_pcg_err, 0, 4, c->stream));
   const long long ncoarse = 2LL * (nx + 1) * (ny + 1) + 3LL * nx * (ny + 1) + 3LL * (nx + 1) * ny;
-  if ((s = romb_alloc_t(c, &c->d_coarse, 2 * ncoarse)) != ROMB_OK) return s;
+  c->ncoarse_all = ncoarse;
+  if ((s = lane_buffers(c, c->lane[0])) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &c->d_cowner, 4 * ncoarse)) != ROMB_OK) return s;
   if ((s = build_tables(c)) != ROMB_OK) return s;
   c->have_lattice = true;
@@ -478,16 +506,11 @@ static romb_status load_lattice(romb_ctx* c, const romb_lattice* L) {
   ROMB_CUDA(cudaMemcpyAsync(c->d_ctrl, L->ctrl, 16 * nctrl, kind, c->stream));
   ROMB_CUDA(cudaMemcpyAsync(c->d_mu, L->mu, 32 * cells, kind, c->stream));
   ROMB_CUDA(cudaMemcpyAsync(c->d_family, L->family, 4 * cells, kind, c->stream));
-  if (L->traction) {
-    if (L->mem == ROMB_MEM_DEVICE) {
-      ROMB_CUDA(cudaMemcpyAsync(c->d_traction, L->traction, 64, cudaMemcpyDeviceToDevice, c->stream));
-      ROMB_CUDA(cudaMemcpyAsync(c->traction, L->traction, 64, cudaMemcpyDeviceToHost, c->stream));
-      ROMB_CUDA(cudaStreamSynchronize(c->stream));
-    } else {
-      ROMB_CUDA(cudaMemcpyAsync(c->d_traction, c->traction, 64, cudaMemcpyHostToDevice, c->stream));
-    }
-  } else {
-    ROMB_CUDA(cudaMemsetAsync(c->d_traction, 0, 64, c->stream));
+  // the lattice's own traction is kept on the host (each solve copies its
+  // load set to its lane)
+  if (L->traction && L->mem == ROMB_MEM_DEVICE) {
+    ROMB_CUDA(cudaMemcpyAsync(c->traction, L->traction, 64, cudaMemcpyDeviceToHost, c->stream));
+    ROMB_CUDA(cudaStreamSynchronize(c->stream));
   }
   cudaEventRecord(c->ev[13], c->stream);
   ROMB_CUDA(cudaMemsetAsync(c->d_flags, 0, 4 * cells, c->stream));
@@ -578,10 +601,11 @@ extern "C" romb_status romb_factor(romb_ctx* c) {
   if (!c->assembled) return ROMB_E_STATE;
   ROMB_CUDA(cudaSetDevice(c->device));
   romb_status s;
-  if (c->pcg_graph) {
-    cudaGraphExecDestroy(c->pcg_graph);
-    c->pcg_graph = nullptr;
-  }
+  for (PcgLane& L : c->lane)   // the captured PCG loops hold this factorisation's launch shapes
+    if (L.graph) {
+      cudaGraphExecDestroy(L.graph);
+      L.graph = nullptr;
+    }
   cudaEventRecord(c->ev[3], c->stream);
   if ((s = launch_ktot(c)) != ROMB_OK) return s;
   if ((s = launch_factor(c)) != ROMB_OK) return s;
@@ -602,44 +626,68 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
   if (!c->factored) return ROMB_E_STATE;
   ROMB_CUDA(cudaSetDevice(c->device));
   const long long nodes = (long long)(c->p * c->nx + 1) * (c->p * c->ny + 1);
-  romb_status worst = ROMB_OK;
-  double pcg_ms = 0.0, rec_ms = 0.0;
-  c->phase_ms[6] = 0.0;
-  // the last set solved is the first: the compliance gradient reads its state
-  for (int k = nrhs - 1; k >= 0; --k) {
-    double tr[8];
-    if (traction_sets) {
-      if (c->mem == ROMB_MEM_HOST) memcpy(tr, traction_sets + 8 * k, 64);
-      else {
-        ROMB_CUDA(cudaMemcpyAsync(tr, traction_sets + 8 * k, 64, cudaMemcpyDeviceToHost, c->stream));
-        ROMB_CUDA(cudaStreamSynchronize(c->stream));
-      }
-    } else {
-      memcpy(tr, c->traction, 64);
-    }
-    int it = 0;
-    double rel = 0;
-    cudaEventRecord(c->ev[6], c->stream);
-    romb_status s = pcg_solve(c, tr, rtol, maxit, c->d_u, &it, &rel);
-    if (s != ROMB_OK && s != ROMB_E_NOT_CONVERGED) return s;
-    if (s == ROMB_E_NOT_CONVERGED) worst = s;
-    cudaEventRecord(c->ev[7], c->stream);
-    double* dst = u_out + 2 * nodes * k;
-    ROMB_CUDA(cudaMemcpyAsync(dst, c->d_u, 16 * nodes,
-                              c->mem == ROMB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                              c->stream));
-    cudaEventRecord(c->ev[8], c->stream);
-    ROMB_CUDA(cudaStreamSynchronize(c->stream));
-    if (iters_out) iters_out[k] = it;
-    if (relres_out) relres_out[k] = rel;
-    pcg_ms += ms_between(c->ev[6], c->ev[7]) - c->phase_ms[5];   // pcg_solve times its recovery itself
-    rec_ms += c->phase_ms[5];
-    c->phase_ms[6] += ms_between(c->ev[7], c->ev[8]);
+  const bool dev = c->mem == ROMB_MEM_DEVICE;
+  romb_status s;
+  // Load sets run concurrently on up to ROMB_MAX_LANES lanes (each its own
+  // streams, vectors and captured PCG loop, all reading the one factorisation),
+  // in waves; set k goes to lane k % nl, and the waves run from the last to
+  // the first, so that lane 0 ends on set 0, whose state the compliance
+  // gradient reads.  Two host synchronisations per wave: after ||f|| and at
+  // the end.
+  const int nl = std::min(nrhs, ROMB_MAX_LANES);
+  for (int k = 1; k < nl; ++k) {
+    if ((s = pcg_lane_streams(c, c->lane[k], false)) != ROMB_OK) return s;
+    if ((s = lane_buffers(c, c->lane[k])) != ROMB_OK) return s;
   }
-  c->phase_ms[4] = pcg_ms;
+  romb_status worst = ROMB_OK;
+  double rec_ms = 0.0;
+  c->phase_ms[6] = 0.0;
+  cudaEventRecord(c->ev[6], c->stream);
+  const int nwaves = (nrhs + nl - 1) / nl;
+  for (int w = nwaves - 1; w >= 0; --w) {
+    const int k0 = w * nl, kn = std::min(nrhs, k0 + nl) - k0;
+    for (int j = 0; j < kn; ++j) {
+      PcgLane& L = c->lane[j];
+      if (j > 0) {   // lanes start after everything before this call on the context stream
+        ROMB_CUDA(cudaEventRecord(c->ev[14], c->stream));
+        ROMB_CUDA(cudaStreamWaitEvent(L.stream, c->ev[14], 0));
+      }
+      const double* tr = traction_sets ? traction_sets + 8 * (k0 + j) : c->traction;
+      if ((s = pcg_begin(c, L, tr, traction_sets && dev)) != ROMB_OK) return s;
+    }
+    for (int j = 0; j < kn; ++j) ROMB_CUDA(cudaStreamSynchronize(c->lane[j].stream));
+    for (int j = 0; j < kn; ++j) {
+      PcgLane& L = c->lane[j];
+      L.nf = sqrt(L.h_red[1]);
+      if ((s = pcg_finish(c, L, rtol, maxit)) != ROMB_OK) return s;
+      double* dst = u_out + 2 * nodes * (k0 + j);
+      ROMB_CUDA(cudaMemcpyAsync(dst, L.d_u, 16 * nodes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                L.stream));
+    }
+    for (int j = 0; j < kn; ++j) {
+      PcgLane& L = c->lane[j];
+      ROMB_CUDA(cudaStreamSynchronize(L.stream));
+      int it = 0;
+      double rel = 0.0;
+      s = pcg_result(c, L, rtol, maxit, &it, &rel);
+      if (s != ROMB_OK && s != ROMB_E_NOT_CONVERGED) return s;
+      if (s == ROMB_E_NOT_CONVERGED) worst = s;
+      if (iters_out) iters_out[k0 + j] = it;
+      if (relres_out) relres_out[k0 + j] = rel;
+      rec_ms += ms_between(L.ev0, L.ev1);
+    }
+  }
+  // the lanes' work is complete (synchronised above); the end event on the
+  // context stream closes the wall time of the whole call
+  cudaEventRecord(c->ev[7], c->stream);
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  // [4]: wall time of the solves (loads, PCG, recovery, output copies) of all
+  // load sets; [5]: the recoveries' own time (summed over sets when nrhs = 1
+  // this is one recovery)
   c->phase_ms[5] = rec_ms;
+  c->phase_ms[4] = ms_between(c->ev[6], c->ev[7]) - (nrhs == 1 ? rec_ms : 0.0);
   c->phase_ms[7] = c->phase_ms[0] + c->phase_ms[1] + c->phase_ms[2] + c->phase_ms[3] + c->phase_ms[4] +
-                   c->phase_ms[5];
+                   (nrhs == 1 ? c->phase_ms[5] : 0.0);
   c->solved = true;
   return worst;
 }
@@ -661,7 +709,7 @@ extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, dou
     if ((s = romb_alloc_t(c, &c->d_gdctrl, 2 * (size_t)nctrl)) != ROMB_OK) return s;
   }
   // c = f^T u on the skeleton (no interior forces)
-  if ((s = romb_dot(c, c->d_f, c->d_x, c->nskel, c->d_red + 8)) != ROMB_OK) return s;
+  if ((s = romb_dot(c, c->lane[0].d_f, c->lane[0].d_x, c->nskel, c->d_red + 8)) != ROMB_OK) return s;
   ROMB_CUDA(cudaMemcpyAsync(c->h_red + 2, c->d_red + 8, 8, cudaMemcpyDeviceToHost, c->stream));
   const bool dev = c->mem == ROMB_MEM_DEVICE;
   double* d_ctrl_out = dev ? dc_dctrl : c->d_gdctrl;

@@ -722,6 +722,7 @@ struct NdDevice {
   int32_t* bad = nullptr;
   int* err = nullptr;   // set by a solve kernel whose staging copy timed out
   double* linv = nullptr;   // [fronts of the widest level][32 x 32] inverses of the diagonal blocks
+  int ybuf_n = 0, sbuf_n = 0;   // sizes of the per-solve buffers (one pair per PCG lane)
 };
 
 static std::unordered_map<const romb_ctx*, NdDevice> g_nd;
@@ -857,6 +858,10 @@ romb_status coarse_build(romb_ctx* c) {
   if ((s = romb_alloc_t(c, &D.gsrc, gsrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.asrc, asrc.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.sbuf, std::max(1, sbuf_tot))) != ROMB_OK) return s;
+  D.ybuf_n = std::max(1, ybuf);
+  D.sbuf_n = std::max(1, sbuf_tot);
+  c->lane[0].nd_ybuf = D.ybuf;
+  c->lane[0].nd_sbuf = D.sbuf;
 
   if ((s = romb_alloc_t(c, &D.bad, 1)) != ROMB_OK) return s;
   if ((s = romb_alloc_t(c, &D.err, 1)) != ROMB_OK) return s;
@@ -1021,7 +1026,16 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st) {
+// Per-solve buffers of the coarse solve for an additional PCG lane.
+romb_status coarse_lane_buffers(romb_ctx* c, double** ybuf, double** sbuf) {
+  NdDevice& D = g_nd[c];
+  romb_status s;
+  if ((s = romb_alloc_t(c, ybuf, (size_t)D.ybuf_n)) != ROMB_OK) return s;
+  return romb_alloc_t(c, sbuf, (size_t)D.sbuf_n);
+}
+
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st, double* ybuf,
+                         double* sbuf) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, st));
   const int L = (int)D.level_ids.size();
@@ -1036,12 +1050,12 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
       ROMB_CUDA(launch_pdl(nd_fwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
                            8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
                            (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
-                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, stride, voff, D.err));
+                           (const int2*)D.gsrc, d_in, ybuf, sbuf, stride, voff, D.err));
       ++c->launches;
     } else if (D.fwd_n[l]) {
       ROMB_CUDA(launch_pdl(nd_fwd_rows_kernel, D.fwd_n[l], 256, D.fwd_smem[l], st, (const FrontDev*)D.fr,
                            (const NdRows*)D.fwd_rows[l], D.fwd_shape[l], (const double*)D.BT, (const int*)D.idx,
-                           (const int2*)D.gsrc, d_in, D.ybuf, D.sbuf, D.err));
+                           (const int2*)D.gsrc, d_in, ybuf, sbuf, D.err));
       ++c->launches;
     }
   }
@@ -1052,12 +1066,12 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
       ROMB_CUDA(launch_pdl(nd_bwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
                            8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
                            (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
-                           (const double*)D.sbuf, d_out, stride, voff, D.err));
+                           (const double*)sbuf, d_out, stride, voff, D.err));
       ++c->launches;
     } else if (D.bwd_n[l]) {
       ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, D.bwd_smem[l], st, (const FrontDev*)D.fr,
                            (const NdRows*)D.bwd_rows[l], D.bwd_shape[l], (const double*)D.F, (const int*)D.idx,
-                           (const double*)D.sbuf, d_out, D.err));
+                           (const double*)sbuf, d_out, D.err));
       ++c->launches;
     }
   }

@@ -279,7 +279,7 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
     ROMB_CUDA(cudaFuncSetAttribute(grad_wq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     grad_wq_kernel<<<(c->famcount[f] + GW_CELLS - 1) / GW_CELLS, 512, smem, c->stream>>>(
         P, R.U64, R.n_half, K, c->d_famlist + c->famstart[f], c->famcount[f], c->d_pairs, npairs, c->d_theta,
-        c->d_chat, c->d_u, c->d_gW, c->d_gQ); ++c->launches;
+        c->d_chat, c->lane[0].d_u, c->d_gW, c->d_gQ); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     if (d_dmu) {
       double nodes[12], g1[12];
@@ -294,7 +294,7 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
     }
   }
   grad_chain_kernel<<<(c->ncells + 127) / 128, 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, c->d_gW,
-                                                                     c->d_u, c->d_traction, c->d_gloc); ++c->launches;
+                                                                     c->lane[0].d_u, c->lane[0].d_traction, c->d_gloc); ++c->launches;
   grad_gather_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, c->d_gloc, d_dctrl); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
@@ -318,7 +318,7 @@ romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc,
     ROMB_CUDA(cudaFuncSetAttribute(grad_wq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     grad_wq_kernel<<<(c->famcount[f] + GW_CELLS - 1) / GW_CELLS, 512, smem, c->stream>>>(
         P, R.U64, R.n_half, K, c->d_famlist + c->famstart[f], c->famcount[f], c->d_pairs, npairs, c->d_theta,
-        c->d_chat, c->d_u, W, Q); ++c->launches;
+        c->d_chat, c->lane[0].d_u, W, Q); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     double nodes[16] = {0.0}, g1[12] = {0.0};
     gll_nodes01(R.r, g1);
@@ -331,8 +331,8 @@ romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc,
     ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
-  grad_chain_kernel<<<(c->ncells + 127) / 128, 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, W, c->d_u,
-                                                                     c->d_traction, gloc); ++c->launches;
+  grad_chain_kernel<<<(c->ncells + 127) / 128, 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, W, c->lane[0].d_u,
+                                                                     c->lane[0].d_traction, gloc); ++c->launches;
   grad_gather_kernel<<<4 * c->sms, 256, 0, c->stream>>>(P, gloc, d_dctrl); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;

@@ -71,7 +71,7 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
   // nothing left by an earlier call (of any context on this device) is read
   ROMB_CUDA(cudaMemsetAsync(base, 0, used, c->stream));
   // c = f^T u on the skeleton, into the context's reduction slots
-  if ((s = romb_dot(c, c->d_f, c->d_x, c->nskel, c->d_red + 8)) != ROMB_OK) return s;
+  if ((s = romb_dot(c, c->lane[0].d_f, c->lane[0].d_x, c->nskel, c->d_red + 8)) != ROMB_OK) return s;
   ROMB_CUDA(cudaMemcpyAsync(c->h_red + 2, c->d_red + 8, 8, cudaMemcpyDeviceToHost, c->stream));
   const bool dev = c->mem == ROMB_MEM_DEVICE;
   double* x_out = dev ? dc_dctrl : dX;

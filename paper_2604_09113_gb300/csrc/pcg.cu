@@ -371,14 +371,20 @@ __global__ void skel_to_nodes_kernel(CellParams P, long long nnodes, const doubl
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
-static romb_status dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) { return romb_dot(c, a, b, n, out); }
-romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
-  double* part = c->d_red + 64;
-  dot_partial_kernel<<<RED_BLOCKS, 256, 0, c->stream>>>(a, b, n, part); ++c->launches;
-  dot_final_kernel<<<1, 256, 0, c->stream>>>(part, RED_BLOCKS, out); ++c->launches;
+static romb_status dot_on(romb_ctx* c, cudaStream_t st, double* red, const double* a, const double* b, long long n,
+                          double* out) {
+  double* part = red + 64;
+  dot_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, part); ++c->launches;
+  dot_final_kernel<<<1, 256, 0, st>>>(part, RED_BLOCKS, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
+}
+// context-level dot product (the compliance), on the context's stream
+romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out) {
+  return dot_on(c, c->stream, c->d_red, a, b, n, out);
+}
+static romb_status dot(romb_ctx* c, PcgLane& L, const double* a, const double* b, long long n, double* out) {
+  return dot_on(c, L.stream, L.d_red, a, b, n, out);
 }
 
 static int grid_for(const romb_ctx* c, long long n) {
@@ -393,8 +399,8 @@ static int grid_for(const romb_ctx* c, long long n) {
 // prepare = true (outside stream capture): set the shared-memory limit and size
 // the persistent grid (resident CTAs per SM x SMs); prepare = false: launch.
 template <int P, int MODE>
-static romb_status cell_apply_p(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
-                                double* cloc, int grid_override) {
+static romb_status cell_apply_p(romb_ctx* c, cudaStream_t st, bool prepare, const double* M, const double* v,
+                                double* yloc, double* cloc, int grid_override) {
   using Sh = CellApplyShape<P>;
   const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(MODE);
   if (prepare) {
@@ -406,55 +412,55 @@ static romb_status cell_apply_p(romb_ctx* c, bool prepare, const double* M, cons
     return ROMB_OK;
   }
   const int grid = grid_override > 0 ? std::min(grid_override, c->ca_grid[MODE]) : c->ca_grid[MODE];
-  cell_apply_kernel<P, MODE><<<grid, Sh::THREADS, smem, c->stream>>>(
-      c->ncells, M, c->d_ucell_map, v, yloc, c->d_Phi, cloc, c->d_pcg_err);
+  cell_apply_kernel<P, MODE><<<grid, Sh::THREADS, smem, st>>>(c->ncells, M, c->d_ucell_map, v, yloc, c->d_Phi, cloc,
+                                                              c->d_pcg_err);
   ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
 template <int MODE>
-static romb_status cell_apply(romb_ctx* c, bool prepare, const double* M, const double* v, double* yloc,
-                              double* cloc, int grid_override = 0) {
+static romb_status cell_apply(romb_ctx* c, cudaStream_t st, bool prepare, const double* M, const double* v,
+                              double* yloc, double* cloc, int grid_override = 0) {
   switch (c->p) {
-    case 3: return cell_apply_p<3, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
-    case 4: return cell_apply_p<4, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
-    case 5: return cell_apply_p<5, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
-    case 6: return cell_apply_p<6, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
-    case 7: return cell_apply_p<7, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
-    case 8: return cell_apply_p<8, MODE>(c, prepare, M, v, yloc, cloc, grid_override);
+    case 3: return cell_apply_p<3, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 4: return cell_apply_p<4, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 5: return cell_apply_p<5, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 6: return cell_apply_p<6, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 7: return cell_apply_p<7, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 8: return cell_apply_p<8, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
   }
   return ROMB_E_ARG;
 }
 
-static romb_status precondition(romb_ctx* c, const CellParams& P, const double* r, double* z, double* yloc,
-                                double* cloc) {
+static romb_status precondition(romb_ctx* c, PcgLane& L, const CellParams& P, const double* r, double* z) {
   // restriction c = Phi^T r, then the coarse correction on the side stream
   // while the fine part y = D F D r runs here; join before the prolongation
-  romb_status s = cell_apply<CA_RESTRICT>(c, false, nullptr, r, nullptr, cloc);
+  romb_status s = cell_apply<CA_RESTRICT>(c, L.stream, false, nullptr, r, nullptr, L.d_cloc);
   if (s != ROMB_OK) return s;
-  double* zc = c->d_coarse;
-  double* gc = c->d_coarse + c->ncoarse_all;
-  ROMB_CUDA(cudaEventRecord(c->evfork, c->stream));
-  ROMB_CUDA(cudaStreamWaitEvent(c->side, c->evfork, 0));
-  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, c->side>>>(c->d_cowner, c->ncoarse_all, cloc, zc); ++c->launches;
+  double* zc = L.d_coarse;
+  double* gc = L.d_coarse + c->ncoarse_all;
+  ROMB_CUDA(cudaEventRecord(L.evfork, L.stream));
+  ROMB_CUDA(cudaStreamWaitEvent(L.side, L.evfork, 0));
+  coarse_gather_kernel<<<grid_for(c, c->ncoarse_all), 256, 0, L.side>>>(c->d_cowner, c->ncoarse_all, L.d_cloc, zc);
+  ++c->launches;
   ROMB_CUDA(cudaGetLastError());
-  if ((s = coarse_solve(c, zc, gc, c->side)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaEventRecord(c->evjoin, c->side));
+  if ((s = coarse_solve(c, zc, gc, L.side, L.nd_ybuf, L.nd_sbuf)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaEventRecord(L.evjoin, L.side));
   // one CTA per SM: the rest of each SM stays free for the coarse chain
-  if ((s = cell_apply<CA_MATVEC>(c, false, c->d_G, r, yloc, nullptr, c->sms)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaStreamWaitEvent(c->stream, c->evjoin, 0));
+  if ((s = cell_apply<CA_MATVEC>(c, L.stream, false, c->d_G, r, L.d_yloc, nullptr, c->sms)) != ROMB_OK) return s;
+  ROMB_CUDA(cudaStreamWaitEvent(L.stream, L.evjoin, 0));
   const int cb = (c->ncells + 15) / 16;
-  cell_prolong_kernel<<<cb, 256, 0, c->stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, yloc); ++c->launches;
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, z); ++c->launches;
+  cell_prolong_kernel<<<cb, 256, 0, L.stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, L.d_yloc); ++c->launches;
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_yloc, c->nskel_nodes, z); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
-static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, double* out, double* yloc) {
-  romb_status s0 = cell_apply<CA_MATVEC>(c, false, c->d_S, v, yloc, nullptr);
+static romb_status apply_S(romb_ctx* c, PcgLane& L, const CellParams& P, const double* v, double* out) {
+  romb_status s0 = cell_apply<CA_MATVEC>(c, L.stream, false, c->d_S, v, L.d_yloc, nullptr);
   if (s0 != ROMB_OK) return s0;
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, yloc, c->nskel_nodes, out); ++c->launches;
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_yloc, c->nskel_nodes, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
@@ -463,20 +469,20 @@ static romb_status apply_S(romb_ctx* c, const CellParams& P, const double* v, do
 //   z = M r; rz' = r.z; p = z + (rz'/rz) p; rz = rz'; q = S p; pq = p.q;
 //   x += (rz/pq) p; r -= (rz/pq) q; rr = r.r -> pinned host word.
 // With p = 0 and rz = 1 on entry the first iteration is the same body.
-static romb_status pcg_body(romb_ctx* c, const CellParams& P, double* yloc, double* cloc, bool host_copy) {
+static romb_status pcg_body(romb_ctx* c, PcgLane& L, const CellParams& P, bool host_copy) {
   romb_status s;
   const long long n = c->nskel;
   const int g = grid_for(c, n);
-  double* sc = c->d_red;
-  if ((s = precondition(c, P, c->d_r, c->d_z, yloc, cloc)) != ROMB_OK) return s;
-  if ((s = dot(c, c->d_r, c->d_z, n, sc + 2)) != ROMB_OK) return s;
-  pcg_update_p<<<g, 256, 0, c->stream>>>(n, sc, c->d_pv, c->d_z); ++c->launches;
-  pcg_shift_scalars<<<1, 32, 0, c->stream>>>(sc); ++c->launches;
-  if ((s = apply_S(c, P, c->d_pv, c->d_q, yloc)) != ROMB_OK) return s;
-  if ((s = dot(c, c->d_pv, c->d_q, n, sc + 1)) != ROMB_OK) return s;
-  pcg_update_x_r<<<g, 256, 0, c->stream>>>(n, sc, c->d_x, c->d_r, c->d_pv, c->d_q); ++c->launches;
-  if ((s = dot(c, c->d_r, c->d_r, n, sc + 3)) != ROMB_OK) return s;
-  if (host_copy) ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
+  double* sc = L.d_red;
+  if ((s = precondition(c, L, P, L.d_r, L.d_z)) != ROMB_OK) return s;
+  if ((s = dot(c, L, L.d_r, L.d_z, n, sc + 2)) != ROMB_OK) return s;
+  pcg_update_p<<<g, 256, 0, L.stream>>>(n, sc, L.d_pv, L.d_z); ++c->launches;
+  pcg_shift_scalars<<<1, 32, 0, L.stream>>>(sc); ++c->launches;
+  if ((s = apply_S(c, L, P, L.d_pv, L.d_q)) != ROMB_OK) return s;
+  if ((s = dot(c, L, L.d_pv, L.d_q, n, sc + 1)) != ROMB_OK) return s;
+  pcg_update_x_r<<<g, 256, 0, L.stream>>>(n, sc, L.d_x, L.d_r, L.d_pv, L.d_q); ++c->launches;
+  if ((s = dot(c, L, L.d_r, L.d_r, n, sc + 3)) != ROMB_OK) return s;
+  if (host_copy) ROMB_CUDA(cudaMemcpyAsync(L.h_red, sc + 3, 8, cudaMemcpyDeviceToHost, L.stream));
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
@@ -505,7 +511,7 @@ __global__ void pcg_loop_check(cudaGraphConditionalHandle h, double* sc) {
 // The whole PCG loop as one graph: a conditional while node whose body is the
 // captured iteration followed by pcg_loop_check.  Returns false (with the
 // stream out of capture and no error pending) if the CUDA driver refuses any step.
-static bool build_device_loop(romb_ctx* c, const CellParams& P, double* yloc, double* cloc) {
+static bool build_device_loop(romb_ctx* c, PcgLane& L, const CellParams& P) {
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return (void)cudaGetLastError(), false;
   bool ok = false;
@@ -518,16 +524,16 @@ static bool build_device_loop(romb_ctx* c, const CellParams& P, double* yloc, do
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess &&
-        cudaStreamBeginCaptureToGraph(c->stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+        cudaStreamBeginCaptureToGraph(L.stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       const long long l0 = c->launches;
-      romb_status s = pcg_body(c, P, yloc, cloc, false);
-      pcg_loop_check<<<1, 32, 0, c->stream>>>(h, c->d_red);
+      romb_status s = pcg_body(c, L, P, false);
+      pcg_loop_check<<<1, 32, 0, L.stream>>>(h, L.d_red);
       ++c->launches;
       cudaGraph_t body = nullptr;
-      const cudaError_t e = cudaStreamEndCapture(c->stream, &body);
-      if (s == ROMB_OK && e == cudaSuccess && cudaGraphInstantiate(&c->pcg_graph, g, 0) == cudaSuccess) {
-        c->pcg_graph_launches = c->launches - l0;
+      const cudaError_t e = cudaStreamEndCapture(L.stream, &body);
+      if (s == ROMB_OK && e == cudaSuccess && cudaGraphInstantiate(&L.graph, g, 0) == cudaSuccess) {
+        L.graph_launches = c->launches - l0;
         ok = true;
       }
       c->launches = l0;
@@ -536,8 +542,8 @@ static bool build_device_loop(romb_ctx* c, const CellParams& P, double* yloc, do
   cudaGraphDestroy(g);
   if (!ok) {
     (void)cudaGetLastError();
-    if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
-    c->pcg_graph = nullptr;
+    if (L.graph) cudaGraphExecDestroy(L.graph);
+    L.graph = nullptr;
   }
   return ok;
 }
@@ -546,109 +552,152 @@ __global__ void pcg_init_scalars(double* sc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = 1.0;
 }
 
-romb_status pcg_solve(romb_ctx* c, const double* tr, double rtol, int maxit, double* d_u, int* iters,
-                      double* relres) {
+// Streams and events of a lane (created once, kept across lattices).
+romb_status pcg_lane_streams(romb_ctx* c, PcgLane& L, bool main_is_context_stream) {
+  if (L.have_streams) return ROMB_OK;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (main_is_context_stream) {
+    L.stream = c->stream;
+    L.own_stream = false;
+  } else {
+    ROMB_CUDA(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
+    L.own_stream = true;
+  }
+  ROMB_CUDA(cudaStreamCreateWithPriority(&L.side, cudaStreamNonBlocking, hi));
+  ROMB_CUDA(cudaEventCreateWithFlags(&L.evfork, cudaEventDisableTiming));
+  ROMB_CUDA(cudaEventCreateWithFlags(&L.evjoin, cudaEventDisableTiming));
+  ROMB_CUDA(cudaEventCreate(&L.ev0));
+  ROMB_CUDA(cudaEventCreate(&L.ev1));
+  if (cudaMallocHost(&L.h_red, 64 * sizeof(double)) != cudaSuccess) return ROMB_E_OOM;
+  L.have_streams = true;
+  return ROMB_OK;
+}
+
+void pcg_lane_destroy(PcgLane& L) {
+  if (L.graph) cudaGraphExecDestroy(L.graph);
+  L.graph = nullptr;
+  if (!L.have_streams) return;
+  if (L.own_stream && L.stream) cudaStreamDestroy(L.stream);
+  if (L.side) cudaStreamDestroy(L.side);
+  for (cudaEvent_t e : {L.evfork, L.evjoin, L.ev0, L.ev1})
+    if (e) cudaEventDestroy(e);
+  if (L.h_red) cudaFreeHost(L.h_red);
+  L = PcgLane();
+}
+
+// Loads -> f and ||f||^2 into L.h_red[1] (read after synchronising L.stream).
+romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* tr, bool tr_on_device) {
+  CellParams P;
+  fill_cell_params(c, &P);
+  ROMB_CUDA(cudaMemcpyAsync(L.d_traction, tr, 64, tr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            L.stream));
+  ROMB_CUDA(cudaMemsetAsync(L.d_fU, 0, 8 * (size_t)c->ncells * c->nU, L.stream));
+  {
+    const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
+    loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, L.stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, L.d_traction,
+                                                                   L.d_fU); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
+  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_fU, c->nskel_nodes, L.d_f); ++c->launches;
+  if (romb_status s = dot(c, L, L.d_f, L.d_f, c->nskel, L.d_red + 4); s != ROMB_OK) return s;
+  ROMB_CUDA(cudaMemcpyAsync(L.h_red + 1, L.d_red + 4, 8, cudaMemcpyDeviceToHost, L.stream));
+  return ROMB_OK;
+}
+
+// The PCG loop (x0 = 0) and the recovery into L.d_u; the caller has read
+// ||f|| into L.nf.  With the device-side loop nothing here waits for the GPU.
+romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit) {
   CellParams P;
   fill_cell_params(c, &P);
   romb_status s;
   const long long n = c->nskel;
-  double* yloc = c->d_yloc;
-  double* cloc = c->d_cloc;
-  // loads -> f
-  ROMB_CUDA(cudaMemcpyAsync(c->d_traction, tr, 64, cudaMemcpyHostToDevice, c->stream));
-  ROMB_CUDA(cudaMemsetAsync(c->d_fU, 0, 8 * (size_t)c->ncells * c->nU, c->stream));
-  {
-    const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
-    loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family,
-                                                                    c->d_traction, c->d_fU); ++c->launches;
-    ROMB_CUDA(cudaGetLastError());
-  }
-  skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->d_fU, c->nskel_nodes, c->d_f); ++c->launches;
-  double* sc = c->d_red;   // scalars: [0] rz, [1] pq, [2] rz_new, [3] rr, [4] ff
-  if ((s = dot(c, c->d_f, c->d_f, n, sc + 4)) != ROMB_OK) return s;
-  ROMB_CUDA(cudaMemcpyAsync(c->h_red + 1, sc + 4, 8, cudaMemcpyDeviceToHost, c->stream));
-  ROMB_CUDA(cudaStreamSynchronize(c->stream));
-  const double nf = sqrt(c->h_red[1]);
-  ROMB_CUDA(cudaMemsetAsync(c->d_x, 0, 8 * n, c->stream));
-  *iters = 0;
-  *relres = 0.0;
-  romb_status result = ROMB_OK;
-  if (nf > 0.0) {
-    ROMB_CUDA(cudaMemcpyAsync(c->d_r, c->d_f, 8 * n, cudaMemcpyDeviceToDevice, c->stream));
-    ROMB_CUDA(cudaMemsetAsync(c->d_pv, 0, 8 * n, c->stream));
+  double* sc = L.d_red;   // scalars: [0] rz, [1] pq, [2] rz_new, [3] rr, [4] ff
+  ROMB_CUDA(cudaMemsetAsync(L.d_x, 0, 8 * n, L.stream));
+  L.h_red[0] = 0.0;
+  L.h_red[3] = 0.0;
+  if (L.nf > 0.0) {
+    ROMB_CUDA(cudaMemcpyAsync(L.d_r, L.d_f, 8 * n, cudaMemcpyDeviceToDevice, L.stream));
+    ROMB_CUDA(cudaMemsetAsync(L.d_pv, 0, 8 * n, L.stream));
     // the loop (or, where the CUDA driver cannot build it, one iteration) is captured
-    // once per factorisation and replayed
-    if (!c->pcg_graph) {
-      if ((s = cell_apply<CA_MATVEC>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
-      if ((s = cell_apply<CA_RESTRICT>(c, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+    // once per factorisation and lane and replayed
+    if (!L.graph) {
+      if ((s = cell_apply<CA_MATVEC>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<CA_RESTRICT>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
       // ROMB_PCG_HOST_LOOP=1 keeps the loop on the host (one graph launch per
       // iteration): profilers cannot replay kernels inside conditional nodes.
       const char* hl = getenv("ROMB_PCG_HOST_LOOP");
-      c->pcg_device_loop = !(hl && hl[0] == '1') && build_device_loop(c, P, yloc, cloc);
-      if (!c->pcg_device_loop) {
+      L.device_loop = !(hl && hl[0] == '1') && build_device_loop(c, L, P);
+      if (!L.device_loop) {
         const long long l0 = c->launches;
-        ROMB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        s = pcg_body(c, P, yloc, cloc, true);
+        ROMB_CUDA(cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal));
+        s = pcg_body(c, L, P, true);
         cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        const cudaError_t e = cudaStreamEndCapture(L.stream, &graph);
         if (s != ROMB_OK) return s;
         ROMB_CUDA(e);
-        ROMB_CUDA(cudaGraphInstantiate(&c->pcg_graph, graph, 0));
+        ROMB_CUDA(cudaGraphInstantiate(&L.graph, graph, 0));
         cudaGraphDestroy(graph);
-        c->pcg_graph_launches = c->launches - l0;
+        L.graph_launches = c->launches - l0;
         c->launches = l0;
       }
     }
-    int it = 0;
-    double rel = 1.0;
-    if (c->pcg_device_loop && maxit > 0) {   // the while body runs at least once
-      const double thr = rtol * nf;
-      pcg_loop_init<<<1, 32, 0, c->stream>>>(sc, thr * thr, maxit); ++c->launches;
-      ROMB_CUDA(cudaGraphLaunch(c->pcg_graph, c->stream));
-      ROMB_CUDA(cudaMemcpyAsync(c->h_red, sc + 3, 8, cudaMemcpyDeviceToHost, c->stream));
-      ROMB_CUDA(cudaMemcpyAsync(c->h_red + 3, sc + 18, 8, cudaMemcpyDeviceToHost, c->stream));
-      ROMB_CUDA(cudaStreamSynchronize(c->stream));
-      it = (int)c->h_red[3];
-      c->launches += (long long)it * c->pcg_graph_launches;
-      rel = sqrt(c->h_red[0]) / nf;
-      if (!(rel == rel)) result = ROMB_E_NAN;
-    }
-    if (!c->pcg_device_loop) pcg_init_scalars<<<1, 32, 0, c->stream>>>(sc), ++c->launches;
-    while (!c->pcg_device_loop && it < maxit) {
-      ROMB_CUDA(cudaGraphLaunch(c->pcg_graph, c->stream));
-      c->launches += c->pcg_graph_launches;
-      ROMB_CUDA(cudaStreamSynchronize(c->stream));
-      ++it;
-      rel = sqrt(c->h_red[0]) / nf;
-      if (!(rel == rel)) {
-        result = ROMB_E_NAN;
-        break;
+    if (L.device_loop) {   // the while body runs at least once
+      const double thr = rtol * L.nf;
+      pcg_loop_init<<<1, 32, 0, L.stream>>>(sc, thr * thr, maxit); ++c->launches;
+      ROMB_CUDA(cudaGraphLaunch(L.graph, L.stream));
+      ROMB_CUDA(cudaMemcpyAsync(L.h_red, sc + 3, 8, cudaMemcpyDeviceToHost, L.stream));
+      ROMB_CUDA(cudaMemcpyAsync(L.h_red + 3, sc + 18, 8, cudaMemcpyDeviceToHost, L.stream));
+    } else {
+      // host-driven loop: one graph launch and one synchronisation per iteration
+      pcg_init_scalars<<<1, 32, 0, L.stream>>>(sc); ++c->launches;
+      int it = 0;
+      while (it < maxit) {
+        ROMB_CUDA(cudaGraphLaunch(L.graph, L.stream));
+        c->launches += L.graph_launches;
+        ROMB_CUDA(cudaStreamSynchronize(L.stream));
+        ++it;
+        const double rel = sqrt(L.h_red[0]) / L.nf;
+        if (!(rel == rel) || rel <= rtol) break;
       }
-      if (rel <= rtol) break;
+      L.h_red[3] = (double)it;
     }
-    *iters = it;
-    *relres = rel;
-    if ((s = coarse_solve_check(c)) != ROMB_OK) return s;
-    {
-      int e = 0;
-      ROMB_CUDA(cudaMemcpy(&e, c->d_pcg_err, 4, cudaMemcpyDeviceToHost));
-      if (e) {
-        ROMB_CUDA(cudaMemset(c->d_pcg_err, 0, 4));
-        romb_set_error("PCG: a cell-operator staging copy did not complete in time");
-        return ROMB_E_CUDA;
-      }
-    }
-    if (result == ROMB_OK && rel > rtol) result = ROMB_E_NOT_CONVERGED;
   }
   // recovery + nodal output
-  cudaEventRecord(c->ev[9], c->stream);
-  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, c->stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, c->d_x, d_u); ++c->launches;
-  skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, c->stream>>>(P, c->nskel_nodes, c->d_x, d_u); ++c->launches;
+  cudaEventRecord(L.ev0, L.stream);
+  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, L.stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, L.d_x, L.d_u);
+  ++c->launches;
+  skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, c->nskel_nodes, L.d_x, L.d_u);
+  ++c->launches;
   ROMB_CUDA(cudaGetLastError());
-  cudaEventRecord(c->ev[10], c->stream);
-  ROMB_CUDA(cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->ev[9], c->ev[10]);
-  c->phase_ms[5] = ms;
+  cudaEventRecord(L.ev1, L.stream);
+  return ROMB_OK;
+}
+
+// Iterations and relative residual of the lane's last solve (its stream has
+// been synchronised); device-side error reports of the solve kernels.
+romb_status pcg_result(romb_ctx* c, PcgLane& L, double rtol, int maxit, int* iters, double* relres) {
+  romb_status result = ROMB_OK;
+  int it = 0;
+  double rel = 0.0;
+  if (L.nf > 0.0) {
+    it = (int)L.h_red[3];
+    rel = sqrt(L.h_red[0]) / L.nf;
+    if (L.device_loop) c->launches += (long long)it * L.graph_launches;
+    if (!(rel == rel)) result = ROMB_E_NAN;
+    else if (rel > rtol) result = ROMB_E_NOT_CONVERGED;
+  }
+  (void)maxit;
+  *iters = it;
+  *relres = rel;
+  romb_status s;
+  if ((s = coarse_solve_check(c)) != ROMB_OK) return s;
+  int e = 0;
+  ROMB_CUDA(cudaMemcpy(&e, c->d_pcg_err, 4, cudaMemcpyDeviceToHost));
+  if (e) {
+    ROMB_CUDA(cudaMemset(c->d_pcg_err, 0, 4));
+    romb_set_error("PCG: a cell-operator staging copy did not complete in time");
+    return ROMB_E_CUDA;
+  }
   return result;
 }

@@ -88,6 +88,36 @@ struct NdPlan {
   int max_ns_small = 0;
 };
 
+// State of one PCG solve (Algorithm 1 inside CG) and its interior recovery:
+// the streams it runs on, its skeleton vectors and cell-local scratch, the
+// coarse-solve buffers and the captured iteration graph.  romb_bddc_solve
+// runs several load sets at once on separate lanes; lane 0 runs on the
+// context's stream and holds the state the compliance gradient reads.
+#define ROMB_MAX_LANES 16
+struct PcgLane {
+  cudaStream_t stream = nullptr;   // main stream (lane 0: the context's stream)
+  cudaStream_t side = nullptr;     // highest priority: coarse correction
+  cudaEvent_t evfork = nullptr, evjoin = nullptr, ev0 = nullptr, ev1 = nullptr;
+  bool have_streams = false, own_stream = false;
+  double* h_red = nullptr;         // pinned: [0] r.r, [1] f.f, [3] iterations
+  // lattice-dependent device buffers (freed with the lattice)
+  bool have_bufs = false;
+  double *d_f = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr;
+  double* d_red = nullptr;         // scalars and reduction partials
+  double* d_fU = nullptr;          // [cells][nU] skeleton-slot forces
+  double* d_cloc = nullptr;        // [cells][20] coarse restriction
+  double* d_yloc = nullptr;        // [cells][nU] cell-local scratch
+  double* d_coarse = nullptr;      // [2][ncoarse_all] coarse right-hand side and solution
+  double* d_u = nullptr;           // nodal output [nodes][2]
+  double* d_traction = nullptr;    // [4][2]
+  double* nd_ybuf = nullptr;       // coarse-solve update vectors
+  double* nd_sbuf = nullptr;       // coarse-solve forward results
+  cudaGraphExec_t graph = nullptr; // the captured PCG loop (per factorisation)
+  long long graph_launches = 0;
+  bool device_loop = false;
+  double nf = 0.0;                 // ||f|| of the lane's current load set
+};
+
 struct romb_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -150,27 +180,14 @@ struct romb_ctx {
   int* d_cnum = nullptr;        // [ncoarse_all] -> ND unknown (-1 Dirichlet)
   NdPlan nd;
 
-  // PCG work vectors (skeleton length)
-  double *d_f = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr;
-  double* d_coarse = nullptr;   // [ncoarse_all]
-  double* d_red = nullptr;      // reduction scratch
+  // reduction scratch of the assembly, the factor checks and the compliance
+  double* d_red = nullptr;
   double* h_red = nullptr;      // pinned host copy
   double* d_fI = nullptr;       // [cells][nI] interior forces
-  double* d_fU = nullptr;       // [cells][nU] skeleton-slot forces
-  double* d_cloc = nullptr;     // [cells][20] coarse restriction Psi^T D r
-  double* d_yloc = nullptr;     // [cells][nU] cell-local PCG scratch
   int* d_pcg_err = nullptr;     // set by a PCG cell kernel whose staging copy timed out
   int ca_grid[3] = {0, 0, 0};   // persistent grid of the cell operator kernels per mode
-  // second stream (highest priority) for the coarse correction, which runs
-  // concurrently with the fine part of the preconditioner; fork/join events
-  cudaStream_t side = nullptr;
-  cudaEvent_t evfork = nullptr, evjoin = nullptr;
-  cudaGraphExec_t pcg_graph = nullptr;   // captured PCG iteration (per factorisation)
-  long long pcg_graph_launches = 0;
-  bool pcg_device_loop = false;          // the graph holds the whole loop (conditional while node)
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
-  double* d_u = nullptr;        // nodal output [nodes][2]
-  double* d_traction = nullptr;
+  PcgLane lane[ROMB_MAX_LANES]; // PCG solves (see PcgLane)
 
   // gradient
   bool solved = false, assembled_rom = false;
@@ -204,7 +221,9 @@ romb_status launch_assemble_tc(romb_ctx* c);
 romb_status launch_factor(romb_ctx* c);
 romb_status coarse_build(romb_ctx* c);      // symbolic (once per lattice shape)
 romb_status coarse_factor(romb_ctx* c);     // numeric
-romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st);
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st, double* ybuf,
+                         double* sbuf);
+romb_status coarse_lane_buffers(romb_ctx* c, double** ybuf, double** sbuf);   // sized like lane 0's
 romb_status coarse_solve_check(romb_ctx* c);   // staging timeouts of the solve kernels
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
@@ -213,8 +232,16 @@ romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc,
                                 double* d_dmu);
 romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
-romb_status pcg_solve(romb_ctx* c, const double* traction, double rtol, int maxit, double* d_u_out,
-                      int* iters, double* relres);
+// A PCG solve on lane L in two halves: pcg_begin enqueues the loads and
+// ||f||^2 (read by the host after a stream synchronisation); pcg_finish
+// enqueues the PCG loop, the recovery into L.d_u and the copy of the
+// iteration count and residual to L.h_red; pcg_result reads them after the
+// lane's stream has been synchronised.
+romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* traction_dev_or_host, bool traction_on_device);
+romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit);
+romb_status pcg_result(romb_ctx* c, PcgLane& L, double rtol, int maxit, int* iters, double* relres);
+romb_status pcg_lane_streams(romb_ctx* c, PcgLane& L, bool main_is_context_stream);
+void pcg_lane_destroy(PcgLane& L);
 
 void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<float>& tiles,
                  int* ntiles);
