@@ -239,6 +239,23 @@ typedef struct {
 } romb_train_spec;
 romb_status romb_train(const romb_train_spec* spec, const double* samples, int n_s, const char* rom_path);
 
+/* The same training on the GPU `device`: the snapshot moments and
+ * snapshots (one CTA per parameter point, the adaptive panel quadrature of
+ * the host trainer), the snapshot Gram matrix and U_r (FP64 GEMM kernels;
+ * the n_s x n_s eigenvectors on the host), U_r orthonormalised by two passes
+ * of Cholesky QR, the magic points of Algorithm 3 (residual and arg-max on
+ * the device, ties to the lowest index) and the I_r samples on the
+ * (r+1)^4 grid (moments and magic-point entries on the device).  Same file
+ * format; spec->n_threads is ignored.  Allocates and frees its own device
+ * memory.  Errors: ROMB_E_ARG, ROMB_E_NAN, ROMB_E_CUDA. */
+romb_status romb_train_gpu(int device, const romb_train_spec* spec, const double* samples, int n_s,
+                           const char* rom_path);
+
+/* Snapshots I(mu_k) (Eq. MDEIM I) of n threshold points mu [n][4] (host) by
+ * the GPU trainer's quadrature: I_out [n][n_i] host array. */
+romb_status romb_train_snapshots_gpu(int device, const romb_train_spec* spec, const double* mu, int n,
+                                     double* I_out);
+
 /* One fast-assembly snapshot I(mu) (Eq. MDEIM I) by the trainer's quadrature:
  * I_out[n_i], n_i = (p+1)^4 (q+1)^2 4, layout as in the ROM file. */
 romb_status romb_train_snapshot(const romb_train_spec* spec, const double* mu4, double* I_out);

@@ -66,6 +66,8 @@ def _load():
         "romb_compliance_grad_noalloc": ([P, P, P, P, P], I),
         "romb_train_snapshot": ([ctypes.POINTER(RombTrainSpec), P, P], I),
         "romb_fma_probe": ([I, I, I, I, P, P, ctypes.POINTER(D)], I),
+        "romb_train_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
+        "romb_train_snapshots_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -248,6 +250,25 @@ def romb_train(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi:
     smp = np.ascontiguousarray(samples, dtype=np.float64)
     spec = RombTrainSpec(family, basis, p, q, r, n_r, n_threads, lo, hi)
     _check(_lib.romb_train(ctypes.byref(spec), smp.ctypes.data, len(smp), path.encode()), "romb_train")
+
+
+def romb_train_gpu(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi: float, samples, path: str,
+                   q: int = 2, device: int = 0) -> None:
+    """Offline training on the GPU (see include/romb.h); same model file format."""
+    smp = np.ascontiguousarray(samples, dtype=np.float64)
+    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi)
+    _check(_lib.romb_train_gpu(device, ctypes.byref(spec), smp.ctypes.data, len(smp), path.encode()),
+           "romb_train_gpu")
+
+
+def romb_train_snapshots_gpu(family: int, basis: int, p: int, mus, q: int = 2, device: int = 0) -> np.ndarray:
+    """Snapshots I(mu) of Eq. (MDEIM I) at the rows of mus [n, 4], computed on the GPU: [n, n_i]."""
+    mu = np.ascontiguousarray(mus, dtype=np.float64).reshape(-1, 4)
+    spec = RombTrainSpec(family, basis, p, q, 1, 1, 0, 0.0, 1.0)
+    out = np.zeros((len(mu), (p + 1) ** 4 * (q + 1) ** 2 * 4))
+    _check(_lib.romb_train_snapshots_gpu(device, ctypes.byref(spec), mu.ctypes.data, len(mu), out.ctypes.data),
+           "romb_train_snapshots_gpu")
+    return out
 
 
 def romb_train_snapshot(family: int, basis: int, p: int, mu4, q: int = 2) -> np.ndarray:

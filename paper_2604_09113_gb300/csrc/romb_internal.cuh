@@ -243,6 +243,11 @@ romb_status pcg_result(romb_ctx* c, PcgLane& L, double rtol, int maxit, int* ite
 romb_status pcg_lane_streams(romb_ctx* c, PcgLane& L, bool main_is_context_stream);
 void pcg_lane_destroy(PcgLane& L);
 
+// host-trainer pieces the GPU trainer reuses (train.cu)
+romb_status train_host_tables(const romb_train_spec* sp, std::vector<double>& F, int* D, int* nF,
+                              std::vector<double>& gx, std::vector<double>& gw, std::vector<double>& Ipi);
+void train_jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V);
+
 void tc_tile_rom(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<float>& tiles,
                  int* ntiles);
 void tc_tile_rom_bf16(const std::vector<double>& U, long long n_half, int K, int kpad, std::vector<uint16_t>& tiles);

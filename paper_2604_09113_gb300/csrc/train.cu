@@ -25,88 +25,9 @@
 
 #include "romb_internal.cuh"
 #include "tables.cuh"
+#include "trim.cuh"
 
 namespace {
-
-// Legendre P_0..P_n at t in [-1, 1]
-inline void legendre(int n, double t, double* P) {
-  P[0] = 1.0;
-  if (n >= 1) P[1] = t;
-  for (int k = 2; k <= n; ++k) P[k] = ((2 * k - 1) * t * P[k - 1] - (k - 1) * P[k - 2]) / k;
-}
-
-// int_0^y P_b(2s - 1) ds for b = 0..n  (needs P up to n+1)
-inline void legendre_antideriv(int n, double y, double* out) {
-  double P[64];
-  const double t = 2.0 * y - 1.0;
-  legendre(n + 1, t, P);
-  out[0] = y;
-  for (int b = 1; b <= n; ++b) out[b] = 0.5 * (P[b + 1] - P[b - 1]) / (2 * b + 1);
-}
-
-// solid intervals of [0,1] in xi2 at xi1 = x (bilinear threshold)
-int solid_y(int family, const double* mu, double x, double* lo, double* hi) {
-  const double a = mu[0] * (1.0 - x) + mu[1] * x;
-  const double b = (mu[2] - mu[0]) * (1.0 - x) + (mu[3] - mu[1]) * x;
-  int n = 0;
-  if (family == 0) {
-    const double A = 1.0 - b * b, B = -1.0 - 2.0 * a * b, C = (x - 0.5) * (x - 0.5) + 0.25 - a * a;
-    const double disc = B * B - 4.0 * A * C;
-    if (disc <= 0.0) {
-      lo[0] = 0.0;
-      hi[0] = 1.0;
-      return 1;
-    }
-    const double s = sqrt(disc), r1 = (-B - s) / (2.0 * A), r2 = (-B + s) / (2.0 * A);
-    if (r1 > 0.0 && fmin(r1, 1.0) > 0.0) {
-      lo[n] = 0.0;
-      hi[n++] = fmin(r1, 1.0);
-    }
-    if (r2 < 1.0 && fmax(r2, 0.0) < 1.0) {
-      lo[n] = fmax(r2, 0.0);
-      hi[n++] = 1.0;
-    }
-    return n;
-  }
-  double L[2], H[2];
-  int m = 0;
-  const double t = fabs(x - 0.5) - a;
-  double l1 = 0, h1 = 0;
-  bool has1 = true;
-  if (b > 0.0) {
-    l1 = t / b;
-    h1 = 2.0;
-  } else if (b < 0.0) {
-    l1 = -1.0;
-    h1 = t / b;
-  } else if (t < 0.0) {
-    l1 = -1.0;
-    h1 = 2.0;
-  } else {
-    has1 = false;
-  }
-  if (has1 && fmin(h1, 1.0) > fmax(l1, 0.0)) {
-    L[m] = fmax(l1, 0.0);
-    H[m++] = fmin(h1, 1.0);
-  }
-  const double l2 = (0.5 - a) / (1.0 + b), h2 = (0.5 + a) / (1.0 - b);
-  if (fmin(h2, 1.0) > fmax(l2, 0.0)) {
-    L[m] = fmax(l2, 0.0);
-    H[m++] = fmin(h2, 1.0);
-  }
-  if (m == 2 && L[1] < L[0]) {
-    std::swap(L[0], L[1]);
-    std::swap(H[0], H[1]);
-  }
-  for (int i = 0; i < m; ++i) {
-    if (n > 0 && L[i] <= hi[n - 1]) hi[n - 1] = fmax(hi[n - 1], H[i]);
-    else {
-      lo[n] = L[i];
-      hi[n++] = H[i];
-    }
-  }
-  return n;
-}
 
 struct Trainer {
   int family, kind, p, q, r, n_r;
@@ -377,6 +298,29 @@ struct LU {
 };
 
 }  // namespace
+
+// Tables shared with the GPU trainer: the Legendre coefficients F of the 1D
+// factor products, the Gauss rule of one panel, and I_Pi (the untrimmed
+// tensor, from the moments e_0 e_0^T).
+romb_status train_host_tables(const romb_train_spec* sp, std::vector<double>& F, int* D, int* nF,
+                              std::vector<double>& gx, std::vector<double>& gw, std::vector<double>& Ipi) {
+  Trainer T;
+  T.setup(*sp);
+  F = T.F;
+  *D = T.D;
+  *nF = T.nF;
+  gx = T.gx;
+  gw = T.gw;
+  Ipi.assign(T.n_i, 0.0);
+  std::vector<double> M((size_t)(T.D + 1) * (T.D + 1), 0.0);
+  M[0] = 1.0;
+  T.snapshot_from_moments(M.data(), Ipi.data());
+  return ROMB_OK;
+}
+
+void train_jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
+  jacobi_eig(n, A, w, V);
+}
 
 extern "C" romb_status romb_train_snapshot(const romb_train_spec* sp, const double* mu4, double* I_out) {
   if (!sp || !mu4 || !I_out || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family != 0 && sp->family != 1))
