@@ -96,10 +96,14 @@ void romb_destroy(romb_ctx* ctx);
 const char* romb_strerror(romb_status s);
 
 /* Load one trained reduced model (Sec. 4.2, offline phase of Sec. 4.4) and keep
- * it resident in HBM.  File format: 128-byte header "ROMBDDC1", int32 version 1,
- * family, basis, p, q, r, n_r, n_k=1, float64 lo, hi, int64 n_i; then float64
- * I_Pi[n_i], U_r[n_r][n_i], A[n_r][(r+1)^4] (I_r at the tensor GLL nodes of
- * [lo,hi]^4, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64 magic[n_r].
+ * it resident in HBM.  File format: 128-byte header "ROMBDDC1", int32 version
+ * (1 or 2), family, basis, p, q, r, n_r, n_k=1, float64 lo, hi, int64 n_i; then
+ * float64 I_Pi[n_i], U_r[n_r][n_i], A[n_r][(r+1)^4] (I_r at the tensor GLL nodes
+ * of [lo,hi]^4, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64
+ * magic[n_r]; version 2 adds the reduced model of the force integrals
+ * J[e][s][k] (edge e, edge node s, edge interpolation node k; see
+ * romb_set_load_form): int64 n_f = 4 (p+1)(q+1), r_f, float64 U_f[r_f][n_f],
+ * A_f[r_f][(r+1)^4], int64 magic_f[r_f].  The trainers write version 2.
  * The fast-assembly vector is I[((k1*nB+k2)*nL+k3)*4 + 2*j1 + j2] (Eq. MDEIM I).
  * *family_out receives the file's family id.  Errors: ROMB_E_FORMAT. */
 romb_status romb_train_load(romb_ctx* ctx, const char* rom_path, int* family_out);
@@ -197,6 +201,20 @@ romb_status romb_compliance_grad_noalloc(romb_ctx* ctx, double* compliance, doub
 romb_status romb_fma_probe(int precision, int blocks, int threads, int iters, void* cuda_stream, void* out,
                            double* flops);
 
+/* How romb_bddc_solve forms the traction loads (Eq. ELA constitutive on the
+ * conformal part of the loaded edges, Sec. 2.2.3):
+ *   ROMB_LOADS_QUADRATURE (default): Gauss quadrature of j t b_s on the solid
+ *     intervals of every loaded cell edge;
+ *   ROMB_LOADS_REDUCED: the reduced model of the force integrals (Eq. SPEED
+ *     L ext, reduced as in Sec. 4.2): J_e(mu) = U_f theta_f(mu) with theta_f
+ *     interpolated like I_r (Algorithm 5), contracted with t_hat = j t at the
+ *     q+1 GLL nodes of the edge.  Needs cell matrices from romb_assemble and
+ *     models of file version 2 (else a solve returns ROMB_E_STATE before
+ *     enqueuing any work).
+ * The choice stays with the context.  Errors: ROMB_E_ARG. */
+enum { ROMB_LOADS_QUADRATURE = 0, ROMB_LOADS_REDUCED = 1 };
+romb_status romb_set_load_form(romb_ctx* ctx, int form);
+
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
  * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits
@@ -217,7 +235,9 @@ typedef enum {
   ROMB_FIELD_SC_LOCAL = 5, /* [cells][20][20] f64: Psi^T S Psi                       */
   ROMB_FIELD_D = 6,        /* [cells][nU] f64: partition of unity                    */
   ROMB_FIELD_FINE = 7,     /* [cells][nU*(nU+1)/2] f64: D F D, packed                */
-  ROMB_FIELD_FLAGS = 8     /* [cells] int32                                          */
+  ROMB_FIELD_FLAGS = 8,    /* [cells] int32                                          */
+  ROMB_FIELD_LOADS = 9     /* [cells][nU] f64: traction loads of the first set of the
+                              last romb_bddc_solve on the skeleton slots            */
 } romb_field;
 size_t romb_field_bytes(romb_ctx* ctx, int field);
 romb_status romb_read(romb_ctx* ctx, int field, void* out, size_t bytes);

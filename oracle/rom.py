@@ -32,6 +32,11 @@ ROM file format (little endian), one family / one cluster per file:
       float64  U_r[n_r][n_i]        (basis vector j contiguous)
       float64  A[n_r][(r+1)^4]      (I_r at grid node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4)))
       int64    magic[n_r]
+  version 2 only, the reduced model of the force integrals J(mu) (module
+  ``force_rom``), on the same box and grid:
+      int64    n_f = 4 (p+1) (q+1), r_f
+      float64  U_f[r_f][n_f], A_f[r_f][(r+1)^4]
+      int64    magic_f[r_f]
 """
 from __future__ import annotations
 
@@ -47,6 +52,14 @@ HEADER = 128
 
 
 @dataclass
+class ForceRom:
+    """Reduced model of the force integrals J(mu) (see ``force_rom``)."""
+    U: np.ndarray        # [n_f, r_f]
+    A: np.ndarray        # [r_f, (r+1)^4]
+    magic: np.ndarray    # [r_f]
+
+
+@dataclass
 class Rom:
     family: int
     kind: int
@@ -59,6 +72,7 @@ class Rom:
     U: np.ndarray             # [n_i, n_r]
     A: np.ndarray             # [n_r, (r+1)^4]
     magic: np.ndarray         # [n_r]
+    force: ForceRom | None = None
 
     @property
     def n_r(self) -> int:
@@ -180,7 +194,8 @@ def mdeim(rom: Rom, mu4: np.ndarray) -> np.ndarray:
 
 def write(rom: Rom, path: str) -> None:
     n_i = rom.U.shape[0]
-    hdr = MAGIC + struct.pack("<8i", 1, rom.family, rom.kind, rom.p, rom.q, rom.r, rom.n_r, 1)
+    version = 1 if rom.force is None else 2
+    hdr = MAGIC + struct.pack("<8i", version, rom.family, rom.kind, rom.p, rom.q, rom.r, rom.n_r, 1)
     hdr += struct.pack("<ddq", rom.lo, rom.hi, n_i)
     hdr += b"\0" * (HEADER - len(hdr))
     with open(path, "wb") as f:
@@ -189,6 +204,12 @@ def write(rom: Rom, path: str) -> None:
         f.write(np.ascontiguousarray(rom.U.T, dtype="<f8").tobytes())
         f.write(np.ascontiguousarray(rom.A, dtype="<f8").tobytes())
         f.write(np.ascontiguousarray(rom.magic, dtype="<i8").tobytes())
+        if rom.force is not None:
+            n_f, r_f = rom.force.U.shape
+            f.write(struct.pack("<qq", n_f, r_f))
+            f.write(np.ascontiguousarray(rom.force.U.T, dtype="<f8").tobytes())
+            f.write(np.ascontiguousarray(rom.force.A, dtype="<f8").tobytes())
+            f.write(np.ascontiguousarray(rom.force.magic, dtype="<i8").tobytes())
 
 
 def read(path: str) -> Rom:
@@ -198,12 +219,19 @@ def read(path: str) -> Rom:
         raise ValueError("not a ROM file")
     version, family, kind, p, q, r, n_r, n_k = struct.unpack_from("<8i", buf, 8)
     lo, hi, n_i = struct.unpack_from("<ddq", buf, 40)
-    if version != 1 or n_k != 1:
+    if version not in (1, 2) or n_k != 1:
         raise ValueError("unsupported ROM file")
     o = HEADER
     I_pi = np.frombuffer(buf, "<f8", n_i, o).copy(); o += 8 * n_i
     U = np.frombuffer(buf, "<f8", n_r * n_i, o).reshape(n_r, n_i).T.copy(); o += 8 * n_r * n_i
     ng = (r + 1) ** 4
     A = np.frombuffer(buf, "<f8", n_r * ng, o).reshape(n_r, ng).copy(); o += 8 * n_r * ng
-    magic = np.frombuffer(buf, "<i8", n_r, o).copy()
-    return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic)
+    magic = np.frombuffer(buf, "<i8", n_r, o).copy(); o += 8 * n_r
+    force = None
+    if version == 2:
+        n_f, r_f = struct.unpack_from("<qq", buf, o); o += 16
+        Uf = np.frombuffer(buf, "<f8", r_f * n_f, o).reshape(r_f, n_f).T.copy(); o += 8 * r_f * n_f
+        Af = np.frombuffer(buf, "<f8", r_f * ng, o).reshape(r_f, ng).copy(); o += 8 * r_f * ng
+        mf = np.frombuffer(buf, "<i8", r_f, o).copy()
+        force = ForceRom(Uf, Af, mf)
+    return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic, force)

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libromb.so")
 
 ROMB_FP64, ROMB_FP32_SPLIT, ROMB_BF16_SPLIT = 0, 1, 2
 ROMB_MEM_HOST, ROMB_MEM_DEVICE = 0, 1
-FIELDS = {"chat": 0, "theta": 1, "K": 2, "S": 3, "psi": 4, "sc_local": 5, "D": 6, "fine": 7, "flags": 8}
+ROMB_LOADS_QUADRATURE, ROMB_LOADS_REDUCED = 0, 1
+FIELDS = {"chat": 0, "theta": 1, "K": 2, "S": 3, "psi": 4, "sc_local": 5, "D": 6, "fine": 7, "flags": 8, "loads": 9}
 STATUS = {0: "ROMB_OK", -1: "ROMB_E_ARG", -2: "ROMB_E_CUDA", -3: "ROMB_E_OOM", -4: "ROMB_E_OUT_OF_BOX",
           -5: "ROMB_E_BAD_MAP", -6: "ROMB_E_NOT_SPD", -7: "ROMB_E_NOT_CONVERGED", -8: "ROMB_E_NAN",
           -9: "ROMB_E_FORMAT", -10: "ROMB_E_STATE", -11: "ROMB_E_SCRATCH"}
@@ -68,6 +69,7 @@ def _load():
         "romb_fma_probe": ([I, I, I, I, P, P, ctypes.POINTER(D)], I),
         "romb_train_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
         "romb_train_snapshots_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, P], I),
+        "romb_set_load_form": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -164,6 +166,12 @@ def romb_bddc_solve(ctx, nodes: int, nrhs: int = 1, traction_sets=None, rtol: fl
     if not (allow_not_converged and st == -7):
         _check(st, "romb_bddc_solve")
     return out, its, rel
+
+
+def romb_set_load_form(ctx, form: int) -> None:
+    """ROMB_LOADS_QUADRATURE (edge quadrature) or ROMB_LOADS_REDUCED (the
+    reduced model of the force integrals of version-2 model files)."""
+    _check(_lib.romb_set_load_form(ctx, form), "romb_set_load_form")
 
 
 def romb_stats(ctx, ncells: int | None = None):

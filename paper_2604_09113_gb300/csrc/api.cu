@@ -96,6 +96,7 @@ void romb_free_lattice(romb_ctx* c) {
   for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
   // lanes keep their streams, events and pinned words; their device buffers
   // went with the lattice
+  const int load_form = c->load_form;
   PcgLane lanes[ROMB_MAX_LANES];
   for (int k = 0; k < ROMB_MAX_LANES; ++k) {
     const PcgLane& o = c->lane[k];
@@ -112,6 +113,7 @@ void romb_free_lattice(romb_ctx* c) {
   }
   *c = romb_ctx();
   for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
+  c->load_form = load_form;
   for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->roms[i] = roms[i];
   c->rom_allocs = keep;
   c->stream = st;
@@ -213,7 +215,7 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   const int version = iv[0], family = iv[1], kind = iv[2], p = iv[3], q = iv[4], r = iv[5], n_r = iv[6],
             n_k = iv[7];
   const int nB = (p + 1) * (p + 1), nL = (q + 1) * (q + 1);
-  if (version != 1 || n_k != 1 || family < 0 || family >= ROMB_MAX_FAMILIES || p < 3 || p > ROMB_MAX_P ||
+  if ((version != 1 && version != 2) || n_k != 1 || family < 0 || family >= ROMB_MAX_FAMILIES || p < 3 || p > ROMB_MAX_P ||
       q != 2 || r < 1 || r > 10 || n_r < 1 || n_r > 127 || n_i != (int64_t)nB * nB * nL * 4 ||
       !(lohi[1] > lohi[0])) {
     fclose(f);
@@ -225,6 +227,19 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   std::vector<double> Ipi(n_i), U((size_t)n_r * n_i), A((size_t)n_r * ngrid);
   bool ok = rd(f, Ipi.data(), 8 * n_i) && rd(f, U.data(), 8 * (size_t)n_r * n_i) &&
             rd(f, A.data(), 8 * (size_t)n_r * ngrid);
+  // version 2: the reduced model of the force integrals J(mu) follows the magic points
+  int64_t fhdr[2] = {0, 0};
+  std::vector<double> Uf, Af;
+  if (ok && version == 2) {
+    std::vector<int64_t> magic(n_r);
+    ok = rd(f, magic.data(), 8 * (size_t)n_r) && rd(f, fhdr, 16) && fhdr[0] == 4LL * (p + 1) * (q + 1) &&
+         fhdr[1] >= 1 && fhdr[1] <= fhdr[0];
+    if (ok) {
+      Uf.resize((size_t)fhdr[1] * fhdr[0]);
+      Af.resize((size_t)fhdr[1] * ngrid);
+      ok = rd(f, Uf.data(), 8 * Uf.size()) && rd(f, Af.data(), 8 * Af.size());
+    }
+  }
   fclose(f);
   if (!ok) return ROMB_E_FORMAT;
 
@@ -252,9 +267,22 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
     romb_free_ptr(c, R.A);
     romb_free_ptr(c, R.At);
     romb_free_ptr(c, R.At2);
+    romb_free_ptr(c, R.force_U);
+    romb_free_ptr(c, R.force_At);
     R = RombRom();
   }
   romb_status s;
+  if (!Uf.empty()) {   // force model: U_f [r_f][n_f] and A_f transposed [grid][r_f]
+    R.force_nf = (int)fhdr[0];
+    R.force_rf = (int)fhdr[1];
+    std::vector<double> Aft(Af.size());
+    for (long long g = 0; g < ngrid; ++g)
+      for (int t = 0; t < R.force_rf; ++t) Aft[(size_t)g * R.force_rf + t] = Af[(size_t)t * ngrid + g];
+    if ((s = romb_alloc_persist(c, (void**)&R.force_U, 8 * Uf.size())) != ROMB_OK) return s;
+    if ((s = romb_alloc_persist(c, (void**)&R.force_At, 8 * Aft.size())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaMemcpy(R.force_U, Uf.data(), 8 * Uf.size(), cudaMemcpyHostToDevice));
+    ROMB_CUDA(cudaMemcpy(R.force_At, Aft.data(), 8 * Aft.size(), cudaMemcpyHostToDevice));
+  }
   if ((s = romb_alloc_persist(c, (void**)&R.U64, 8 * Uh.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_persist(c, (void**)&R.A, 8 * A.size())) != ROMB_OK) return s;
   if ((s = romb_alloc_persist(c, (void**)&R.At, 8 * A.size())) != ROMB_OK) return s;
@@ -624,6 +652,17 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
   if (!c || !u_out || nrhs < 1 || !(rtol > 0) || maxit < 1) return ROMB_E_ARG;
   if (!traction_sets && nrhs != 1) return ROMB_E_ARG;
   if (!c->factored) return ROMB_E_STATE;
+  if (c->load_form == ROMB_LOADS_REDUCED) {   // checked before any work is enqueued
+    if (!c->assembled_rom) {
+      romb_set_error("reduced loads: the cell matrices were not assembled from the reduced models");
+      return ROMB_E_STATE;
+    }
+    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f)
+      if (c->famcount[f] > 0 && !c->roms[f].force_U) {
+        romb_set_error("reduced loads: the reduced model of a family in use has no force model");
+        return ROMB_E_STATE;
+      }
+  }
   ROMB_CUDA(cudaSetDevice(c->device));
   const long long nodes = (long long)(c->p * c->nx + 1) * (c->p * c->ny + 1);
   const bool dev = c->mem == ROMB_MEM_DEVICE;
@@ -736,6 +775,12 @@ extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, dou
   return ROMB_OK;
 }
 
+extern "C" romb_status romb_set_load_form(romb_ctx* c, int form) {
+  if (!c || (form != ROMB_LOADS_QUADRATURE && form != ROMB_LOADS_REDUCED)) return ROMB_E_ARG;
+  c->load_form = form;
+  return ROMB_OK;
+}
+
 extern "C" romb_status romb_stats(romb_ctx* c, double* phase_ms, int* flags_out) {
   if (!c) return ROMB_E_ARG;
   if (phase_ms) memcpy(phase_ms, c->phase_ms, sizeof(c->phase_ms));
@@ -766,6 +811,7 @@ extern "C" size_t romb_field_bytes(romb_ctx* c, int field) {
     case ROMB_FIELD_D: return cells * nU * 8;
     case ROMB_FIELD_FINE: return cells * tri(nU) * 8;
     case ROMB_FIELD_FLAGS: return cells * 4;
+    case ROMB_FIELD_LOADS: return c->lane[0].d_fU ? cells * nU * 8 : 0;
   }
   return 0;
 }
@@ -802,6 +848,7 @@ extern "C" romb_status romb_read(romb_ctx* c, int field, void* out, size_t bytes
     case ROMB_FIELD_SC_LOCAL: ROMB_CUDA(cudaMemcpy(out, c->d_SCl, bytes, cudaMemcpyDeviceToHost)); break;
     case ROMB_FIELD_D: ROMB_CUDA(cudaMemcpy(out, c->d_D, bytes, cudaMemcpyDeviceToHost)); break;
     case ROMB_FIELD_FLAGS: ROMB_CUDA(cudaMemcpy(out, c->d_flags, bytes, cudaMemcpyDeviceToHost)); break;
+    case ROMB_FIELD_LOADS: ROMB_CUDA(cudaMemcpy(out, c->lane[0].d_fU, bytes, cudaMemcpyDeviceToHost)); break;
     default: return ROMB_E_ARG;
   }
   return ROMB_OK;

@@ -15,8 +15,6 @@
 // Solve: forward (leaves -> root) and backward (root -> leaves) substitution,
 // one GEMV with B per front and sweep, one launch per level and sweep.
 #include <stdio.h>
-#include <stdlib.h>
-#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -476,117 +474,6 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
       if (c < ns) sbuf[f.sbuf_off + c] = z;
       else ybuf[f.ybuf_off + c - ns] = w[c] + z;
     }
-  }
-}
-
-// Small fronts without staging: one warp per front, eight per CTA, B read
-// straight from L2 / HBM (eight independent loads in flight per lane) and
-// only the vector in shared memory, so that many more fronts stream at once
-// than the staged kernels' shared-memory regions allow.
-#define ND_WPC_D 8
-__global__ void __launch_bounds__(32 * ND_WPC_D) nd_fwd_small_direct_kernel(
-    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
-    const int* __restrict__ idx, const int2* __restrict__ gsrc, const double* __restrict__ rhs,
-    double* __restrict__ ybuf, double* __restrict__ sbuf) {
-  __shared__ double wsh[ND_WPC_D][ND_SMALL_N];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int fi = blockIdx.x * ND_WPC_D + warp;
-  const bool has = fi < nfronts;
-  const FrontDev f = fr[level[has ? fi : 0]];
-  const int ns = f.ns, n = ns + f.nb;
-  double* w = wsh[warp];
-  int pid[ND_SMALL_N / 32];
-  int2 pgs[ND_SMALL_N / 32];
-#pragma unroll
-  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
-    const int t = lane + 32 * k;
-    pid[k] = (has && t < ns) ? idx[f.idx_off + t] : -1;
-    pgs[k] = (has && t < n) ? gsrc[f.wbuf_off + t] : make_int2(-1, -1);
-  }
-  pdl_trigger();
-  pdl_wait();
-  if (!has) return;
-#pragma unroll
-  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
-    const int t = lane + 32 * k;
-    if (t < n) w[t] = (pid[k] >= 0 ? rhs[pid[k]] : 0.0) + nd_gather_row(pgs[k], ybuf);
-  }
-  __syncwarp();
-  const double* Bs = F + f.off + (long long)n * n;
-  for (int c0 = 0; c0 < n; c0 += 32) {
-    const int c = c0 + lane;
-    const int emax = min(ns, c0 + 32);   // rows e > c of L11^-T are zero
-    if (c < n) {
-      double z0 = 0.0, z1 = 0.0;
-      int e = 0;
-      for (; e + 8 <= emax; e += 8) {
-        double b[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) b[u] = __ldg(Bs + (long long)(e + u) * n + c);
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          z0 = fma(b[u], w[e + u], z0);
-          z1 = fma(b[u + 1], w[e + u + 1], z1);
-        }
-      }
-      for (; e < emax; ++e) z0 = fma(__ldg(Bs + (long long)e * n + c), w[e], z0);
-      const double z = z0 + z1;
-      if (c < ns) sbuf[f.sbuf_off + c] = z;
-      else ybuf[f.ybuf_off + c - ns] = w[c] + z;
-    }
-  }
-}
-
-// x_s = B [y_s; x_b] without staging (see nd_fwd_small_direct_kernel): lanes =
-// (row r, column phase h), R rows x P phases; phases combined by shuffles.
-__global__ void __launch_bounds__(32 * ND_WPC_D) nd_bwd_small_direct_kernel(
-    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
-    const int* __restrict__ idx, const double* __restrict__ sbuf, double* __restrict__ x) {
-  __shared__ double vsh[ND_WPC_D][ND_SMALL_N];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int fi = blockIdx.x * ND_WPC_D + warp;
-  const bool has = fi < nfronts;
-  const FrontDev f = fr[level[has ? fi : 0]];
-  const int ns = f.ns, n = ns + f.nb;
-  double* v = vsh[warp];
-  int pid[ND_SMALL_N / 32];
-#pragma unroll
-  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
-    const int c = lane + 32 * k;
-    pid[k] = (has && c < n) ? idx[f.idx_off + c] : 0;
-  }
-  pdl_trigger();
-  pdl_wait();
-  if (!has) return;
-  const int* id = idx + f.idx_off;
-#pragma unroll
-  for (int k = 0; k < ND_SMALL_N / 32; ++k) {
-    const int c = lane + 32 * k;
-    if (c < n) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[pid[k]];
-  }
-  __syncwarp();
-  const double* Bs = F + f.off + (long long)n * n;
-  int R = 1;
-  while (R < ns && R < 32) R <<= 1;
-  const int P = 32 / R, r = lane & (R - 1), h = lane / R;
-  for (int e0 = 0; e0 < ns; e0 += R) {
-    const int e = e0 + r;
-    double s = 0.0;
-    if (e < ns) {
-      const double* row = Bs + (long long)e * n;
-      int c = (e0 / P) * P + h;
-      for (; c + 3 * P < n; c += 4 * P) {
-        const double b0 = __ldg(row + c), b1 = __ldg(row + c + P), b2 = __ldg(row + c + 2 * P),
-                     b3 = __ldg(row + c + 3 * P);
-        s = fma(b0, v[c], s);
-        s = fma(b1, v[c + P], s);
-        s = fma(b2, v[c + 2 * P], s);
-        s = fma(b3, v[c + 3 * P], s);
-      }
-      for (; c < n; c += P) s = fma(__ldg(row + c), v[c], s);
-    }
-    for (int o = R; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (h == 0 && e < ns) x[id[e]] = s;
   }
 }
 
@@ -1156,17 +1043,8 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
     *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
     *stride = (*voff + D.level_maxn[l] + 1) & ~1;       // + one vector, even (16-byte regions)
   };
-  static const bool staged = [] {
-    const char* e = getenv("ROMB_COARSE_SMALL");
-    return e && strcmp(e, "staged") == 0;
-  }();
   for (int l = 0; l < L; ++l) {
-    if (D.level_small[l] && !staged) {
-      ROMB_CUDA(launch_pdl(nd_fwd_small_direct_kernel, (D.level_count[l] + ND_WPC_D - 1) / ND_WPC_D, 32 * ND_WPC_D,
-                           0, st, (const FrontDev*)D.fr, (const int*)D.level_ids[l], D.level_count[l],
-                           (const double*)D.F, (const int*)D.idx, (const int2*)D.gsrc, d_in, ybuf, sbuf));
-      ++c->launches;
-    } else if (D.level_small[l]) {
+    if (D.level_small[l]) {
       int stride, voff;
       small_shape(l, &stride, &voff);
       ROMB_CUDA(launch_pdl(nd_fwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
@@ -1182,12 +1060,7 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
     }
   }
   for (int l = L - 1; l >= 0; --l) {
-    if (D.level_small[l] && !staged) {
-      ROMB_CUDA(launch_pdl(nd_bwd_small_direct_kernel, (D.level_count[l] + ND_WPC_D - 1) / ND_WPC_D, 32 * ND_WPC_D,
-                           0, st, (const FrontDev*)D.fr, (const int*)D.level_ids[l], D.level_count[l],
-                           (const double*)D.F, (const int*)D.idx, (const double*)sbuf, d_out));
-      ++c->launches;
-    } else if (D.level_small[l]) {
+    if (D.level_small[l]) {
       int stride, voff;
       small_shape(l, &stride, &voff);
       ROMB_CUDA(launch_pdl(nd_bwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,

@@ -312,6 +312,99 @@ __global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, cons
   }
 }
 
+// Traction loads through the reduced model of the force integrals (Eq. SPEED
+// L ext with the ROM of Sec. 4.2): per loaded boundary edge of a cell,
+// theta_f by tensor Lagrange interpolation of the grid coefficients at the
+// cell's thresholds (Algorithm 5), J_e = U_f theta_f, and the load of edge
+// node s, f_s = t sum_k J_e[s][k] j(t_k), with j the edge Jacobian at the
+// q+1 GLL nodes t_k of the edge (t_hat = j t interpolated there).  One warp
+// per (cell, edge).
+struct ForceRomDev {
+  const double* U;    // [r_f][n_f]
+  const double* At;   // [(r+1)^4][r_f]
+  int rf, nf, r;
+  double nodes[12];   // the GLL nodes of the threshold box, degree r
+};
+struct ForceRomSet {
+  ForceRomDev f[ROMB_MAX_FAMILIES];
+  double qnodes[8];   // GLL nodes of degree q on [0, 1]
+};
+#define LR_WARPS 4
+__global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, ForceRomSet FS,
+                                                                   const double* __restrict__ ctrl,
+                                                                   const double* __restrict__ mu,
+                                                                   const int32_t* __restrict__ family,
+                                                                   const double* __restrict__ trac,
+                                                                   double* __restrict__ fU) {
+  __shared__ double wts[LR_WARPS][4][12];
+  __shared__ double th[LR_WARPS][128];
+  __shared__ double Jv[LR_WARPS][(ROMB_MAX_P + 1) * 8];
+  __shared__ double jk[LR_WARPS][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int ncell_e[4] = {P.ny, P.ny, P.nx, P.nx};
+  int e = 0;
+  while (e < 4 && t >= ncell_e[e]) {
+    t -= ncell_e[e];
+    ++e;
+  }
+  if (e >= 4) return;
+  const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
+  if (t0 == 0.0 && t1 == 0.0) return;
+  const int p = P.p, q = P.q, nx = P.nx, ny = P.ny;
+  const int j = (int)t;
+  const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
+  const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
+  const long long cell = cx + (long long)nx * cy;
+  const ForceRomDev F = FS.f[family[cell]];
+  const int r = F.r, n1 = r + 1, rf = F.rf;
+  if (lane < 4) lagrange1d(r, F.nodes, mu[4 * cell + lane], wts[warp][lane], nullptr);
+  __syncwarp();
+  // theta_f = A_f w(mu), the grid node g = g1 + n1 (g2 + n1 (g3 + n1 g4))
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int ng = n1 * n1 * n1 * n1;
+  for (int g = 0; g < ng; ++g) {
+    const int g1 = g % n1, g2 = (g / n1) % n1, g3 = (g / (n1 * n1)) % n1, g4 = g / (n1 * n1 * n1);
+    const double w = wts[warp][0][g1] * wts[warp][1][g2] * wts[warp][2][g3] * wts[warp][3][g4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jj = lane + 32 * u;
+      if (jj < rf) acc[u] = fma(w, F.At[(long long)g * rf + jj], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (lane + 32 * u < rf) th[warp][lane + 32 * u] = acc[u];
+  // edge Jacobian at the q+1 interpolation nodes of the edge
+  if (lane <= q) {
+    const double tk = FS.qnodes[lane];
+    const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : tk, x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : tk;
+    double x[2], J[2][2];
+    map_eval(ctrl, nx, P.m, cx, cy, x1, x2, x, J);
+    const int dc = e < 2 ? 1 : 0;
+    jk[warp][lane] = hypot(J[0][dc], J[1][dc]);
+  }
+  __syncwarp();
+  // J_e[s][k] = sum_t U_f[t][(e (p+1) + s)(q+1) + k] theta_f[t]
+  const int ne = (p + 1) * (q + 1);
+  for (int i = lane; i < ne; i += 32) {
+    const int col = e * ne + i;
+    double sum = 0.0;
+    for (int tt = 0; tt < rf; ++tt) sum = fma(F.U[(long long)tt * F.nf + col], th[warp][tt], sum);
+    Jv[warp][i] = sum;
+  }
+  __syncwarp();
+  if (lane <= p) {
+    const int s_ = lane;
+    double gsum = 0.0;
+    for (int k = 0; k <= q; ++k) gsum = fma(Jv[warp][s_ * (q + 1) + k], jk[warp][k], gsum);
+    const int k_ = e == 0 ? (p + 1) * s_ : e == 1 ? p + (p + 1) * s_ : e == 2 ? s_ : s_ + (p + 1) * p;
+    const int u = 2 * P.uslot_of_node[k_];
+    atomicAdd(&fU[cell * P.nU + u], gsum * t0);
+    atomicAdd(&fU[cell * P.nU + u + 1], gsum * t1);
+  }
+}
+
 // Interior recovery and nodal output: u_I = -L^-T W u_loc (f_I = 0: no body force),
 // one warp per cell.
 __global__ void recover_kernel(CellParams P, const double* __restrict__ LII, const double* __restrict__ W,
@@ -593,7 +686,33 @@ romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* tr, bool tr_on_devi
   ROMB_CUDA(cudaMemcpyAsync(L.d_traction, tr, 64, tr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                             L.stream));
   ROMB_CUDA(cudaMemsetAsync(L.d_fU, 0, 8 * (size_t)c->ncells * c->nU, L.stream));
-  {
+  if (c->load_form == ROMB_LOADS_REDUCED) {
+    ForceRomSet FS;
+    memset(&FS, 0, sizeof(FS));
+    gll_nodes01(c->q, FS.qnodes);
+    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+      if (c->famcount[f] == 0) continue;
+      const RombRom& R = c->roms[f];
+      if (!R.force_U) {
+        romb_set_error("reduced loads: the reduced model of a family in use has no force model");
+        return ROMB_E_STATE;
+      }
+      ForceRomDev& D = FS.f[f];
+      D.U = R.force_U;
+      D.At = R.force_At;
+      D.rf = R.force_rf;
+      D.nf = R.force_nf;
+      D.r = R.r;
+      double g1[12];
+      gll_nodes01(R.r, g1);
+      for (int i = 0; i <= R.r; ++i) D.nodes[i] = R.lo + (R.hi - R.lo) * g1[i];
+      if (D.rf > 128) return ROMB_E_ARG;
+    }
+    const long long nwarps = 2LL * c->ny + 2LL * c->nx;
+    loads_rom_kernel<<<(int)((nwarps + LR_WARPS - 1) / LR_WARPS), 32 * LR_WARPS, 0, L.stream>>>(
+        P, FS, c->d_ctrl, c->d_mu, c->d_family, L.d_traction, L.d_fU); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  } else {
     const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
     loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, L.stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, L.d_traction,
                                                                    L.d_fU); ++c->launches;

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <string>
 #include <unordered_map>
@@ -47,6 +48,10 @@ struct RombRom {
   double* At = nullptr;        // [(r+1)^4][n_r]
   float2* At2 = nullptr;       // the same as (hi, lo) FP32 pairs, hi + lo = At to ~48 bits (double-float theta)
   int kpad = 0;                // n_r+1 rounded up for the tensor-core K dimension
+  // reduced model of the force integrals J(mu) (file version 2; absent: null)
+  int force_nf = 0, force_rf = 0;
+  double* force_U = nullptr;   // [r_f][n_f], n_f = 4 (p+1) (q+1): J[e][s][k]
+  double* force_At = nullptr;  // [(r+1)^4][r_f]
 };
 
 // Nested-dissection coarse solver (a5): symbolic tree built on the host from
@@ -140,6 +145,7 @@ struct romb_ctx {
   unsigned dmask = 0;
   double traction[8] = {0};
   int prec = 0;
+  int load_form = 0;            // 0 direct edge quadrature, 1 reduced force model (romb_set_load_form)
 
   double* d_ctrl = nullptr;
   double* d_mu = nullptr;
@@ -242,6 +248,16 @@ romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit);
 romb_status pcg_result(romb_ctx* c, PcgLane& L, double rtol, int maxit, int* iters, double* relres);
 romb_status pcg_lane_streams(romb_ctx* c, PcgLane& L, bool main_is_context_stream);
 void pcg_lane_destroy(PcgLane& L);
+
+// reduced model of the force integrals J(mu) (train.cu; file format version 2)
+struct RombForceModel {
+  int n_f = 0, r_f = 0;
+  std::vector<double> U;          // [r_f][n_f]
+  std::vector<double> A;          // [r_f][(r+1)^4]
+  std::vector<long long> magic;   // [r_f]
+};
+romb_status train_force_model(const romb_train_spec* sp, const double* samples, int n_s, RombForceModel* out);
+bool write_force_section(FILE* f, const RombForceModel& m);
 
 // host-trainer pieces the GPU trainer reuses (train.cu)
 romb_status train_host_tables(const romb_train_spec* sp, std::vector<double>& F, int* D, int* nF,

@@ -297,6 +297,40 @@ struct LU {
   }
 };
 
+// ---- reduced model of the force integrals (Sec. 4.2 applied to Eq. SPEED L ext) ----
+// J(mu)[e][s][k] = int over the solid part of cell edge e of b_s(t) l_k(t) dt,
+// e = 0..3 (left, right, bottom, top), s along the edge, l_k the degree-q
+// Lagrange polynomials on the edge's GLL nodes.  Solid intervals of a
+// vertical edge are those of xi2 at xi1 = 0 / 1; a horizontal edge uses the
+// same function with mu_2 and mu_3 exchanged (both families are symmetric
+// under swapping xi1 and xi2 once the corners are swapped accordingly).
+void edge_load_tensor(const romb_train_spec& sp, const double* mu, double* J) {
+  const int p = sp.p, q = sp.q, nf = 4 * (p + 1) * (q + 1);
+  for (int i = 0; i < nf; ++i) J[i] = 0.0;
+  double gx[24], gw[24], gll[ROMB_MAX_P + 1], qn[8];
+  gauss01(24, gx, gw);
+  gll_nodes01(p, gll);
+  gll_nodes01(q, qn);
+  for (int e = 0; e < 4; ++e) {
+    const double mt[4] = {mu[0], mu[2], mu[1], mu[3]};
+    const double* me = e < 2 ? mu : mt;
+    double lo[4], hi[4];
+    const int ni = solid_y(sp.family, me, (e == 1 || e == 3) ? 1.0 : 0.0, lo, hi);
+    for (int iv = 0; iv < ni; ++iv) {
+      const double len = hi[iv] - lo[iv];
+      for (int g = 0; g < 24; ++g) {
+        const double t = lo[iv] + len * gx[g], w = len * gw[g];
+        double bv[ROMB_MAX_P + 1], bd[ROMB_MAX_P + 1], lv[8];
+        if (sp.basis == 0) Trainer::lagrange1d_host(p, gll, t, bv, bd);
+        else Trainer::bernstein1d_host(p, t, bv, bd);
+        Trainer::lagrange1d_host(q, qn, t, lv, nullptr);
+        for (int si = 0; si <= p; ++si)
+          for (int k = 0; k <= q; ++k) J[(e * (p + 1) + si) * (q + 1) + k] += w * bv[si] * lv[k];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // Tables shared with the GPU trainer: the Legendre coefficients F of the 1D
@@ -320,6 +354,91 @@ romb_status train_host_tables(const romb_train_spec* sp, std::vector<double>& F,
 
 void train_jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
   jacobi_eig(n, A, w, V);
+}
+
+// The force model of a spec on the samples: U_f (eigenvectors of the
+// n_f x n_f matrix S S^T of the J snapshots, those with singular values above
+// 1e-7 of the largest), magic points (Algorithm 3), grid coefficients.
+romb_status train_force_model(const romb_train_spec* sp, const double* samples, int n_s, RombForceModel* out) {
+  const int nf = 4 * (sp->p + 1) * (sp->q + 1);
+  std::vector<double> S((size_t)n_s * nf);
+  for (int si = 0; si < n_s; ++si) edge_load_tensor(*sp, samples + 4 * si, &S[(size_t)si * nf]);
+  std::vector<double> C((size_t)nf * nf, 0.0), w, V;
+  for (int a = 0; a < nf; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double sum = 0.0;
+      for (int si = 0; si < n_s; ++si) sum += S[(size_t)si * nf + a] * S[(size_t)si * nf + b];
+      C[(size_t)a * nf + b] = C[(size_t)b * nf + a] = sum;
+    }
+  jacobi_eig(nf, C, w, V);
+  std::vector<int> order(nf);
+  for (int i = 0; i < nf; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+  int rf = 0;
+  const double wmax = w[order[0]];
+  if (!(wmax > 0.0)) return ROMB_E_NAN;
+  while (rf < nf && rf < n_s && w[order[rf]] > 1e-14 * wmax) ++rf;   // singular values above 1e-7 of the largest
+  std::vector<double> U((size_t)rf * nf);
+  for (int k = 0; k < rf; ++k)
+    for (int a = 0; a < nf; ++a) U[(size_t)k * nf + a] = V[(size_t)a * nf + order[k]];
+  std::vector<long long> magic(rf);
+  {
+    std::vector<double> res(nf);
+    for (int j = 0; j < rf; ++j) {
+      std::vector<double> c(std::max(1, j));
+      if (j > 0) {
+        std::vector<double> A((size_t)j * j);
+        for (int a = 0; a < j; ++a) {
+          for (int b = 0; b < j; ++b) A[(size_t)a * j + b] = U[(size_t)b * nf + magic[a]];
+          c[a] = U[(size_t)j * nf + magic[a]];
+        }
+        LU lu;
+        if (!lu.factor(j, A)) return ROMB_E_NAN;
+        lu.solve(c.data());
+      }
+      int m = 0;
+      for (int e = 0; e < nf; ++e) {
+        double v = U[(size_t)j * nf + e];
+        for (int b = 0; b < j; ++b) v -= U[(size_t)b * nf + e] * c[b];
+        res[e] = v;
+        if (fabs(res[e]) > fabs(res[m])) m = e;
+      }
+      magic[j] = m;
+    }
+  }
+  const int n1 = sp->r + 1, ng = n1 * n1 * n1 * n1;
+  double g1d[12];
+  gll_nodes01(sp->r, g1d);
+  std::vector<double> Um((size_t)rf * rf);
+  for (int a = 0; a < rf; ++a)
+    for (int b = 0; b < rf; ++b) Um[(size_t)a * rf + b] = U[(size_t)b * nf + magic[a]];
+  LU lu;
+  if (!lu.factor(rf, Um)) return ROMB_E_NAN;
+  std::vector<double> A((size_t)rf * ng), J(nf), bb(rf);
+  for (int g = 0; g < ng; ++g) {
+    const int ii[4] = {g % n1, (g / n1) % n1, (g / (n1 * n1)) % n1, g / (n1 * n1 * n1)};
+    double mu[4];
+    for (int d = 0; d < 4; ++d) mu[d] = sp->lo + (sp->hi - sp->lo) * g1d[ii[d]];
+    edge_load_tensor(*sp, mu, J.data());
+    for (int a = 0; a < rf; ++a) bb[a] = J[magic[a]];
+    lu.solve(bb.data());
+    for (int a = 0; a < rf; ++a) A[(size_t)a * ng + g] = bb[a];
+  }
+  out->n_f = nf;
+  out->r_f = rf;
+  out->U = std::move(U);
+  out->A = std::move(A);
+  out->magic = std::move(magic);
+  return ROMB_OK;
+}
+
+bool write_force_section(FILE* f, const RombForceModel& m) {
+  const int64_t hdr[2] = {m.n_f, m.r_f};
+  bool ok = fwrite(hdr, 8, 2, f) == 2;
+  ok = ok && fwrite(m.U.data(), 8, m.U.size(), f) == m.U.size();
+  ok = ok && fwrite(m.A.data(), 8, m.A.size(), f) == m.A.size();
+  ok = ok && fwrite(m.magic.data(), 8, m.magic.size(), f) == m.magic.size();
+  return ok;
 }
 
 extern "C" romb_status romb_train_snapshot(const romb_train_spec* sp, const double* mu4, double* I_out) {
@@ -448,12 +567,14 @@ extern "C" romb_status romb_train(const romb_train_spec* sp, const double* sampl
     M[0] = 1.0;
     T.snapshot_from_moments(M.data(), Ipi.data());
   }
+  RombForceModel force;
+  if (romb_status fs = train_force_model(sp, samples, n_s, &force); fs != ROMB_OK) return fs;
   FILE* f = fopen(path, "wb");
   if (!f) return ROMB_E_ARG;
   unsigned char hdr[128];
   memset(hdr, 0, sizeof(hdr));
   memcpy(hdr, "ROMBDDC1", 8);
-  const int32_t iv[8] = {1, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
+  const int32_t iv[8] = {2, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
   memcpy(hdr + 8, iv, 32);
   const double lohi[2] = {sp->lo, sp->hi};
   memcpy(hdr + 40, lohi, 16);
@@ -464,6 +585,7 @@ extern "C" romb_status romb_train(const romb_train_spec* sp, const double* sampl
   ok = ok && fwrite(U.data(), 8, U.size(), f) == U.size();
   ok = ok && fwrite(A.data(), 8, A.size(), f) == A.size();
   ok = ok && fwrite(magic.data(), 8, n_r, f) == (size_t)n_r;
+  ok = ok && write_force_section(f, force);
   fclose(f);
   return ok ? ROMB_OK : ROMB_E_ARG;
 }

@@ -620,12 +620,14 @@ extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, con
     lu.solve(b.data());
     for (int a = 0; a < n_r; ++a) A[(size_t)a * ng + g] = b[a];
   }
+  RombForceModel force;   // J(mu) is small (n_f = 4 (p+1) (q+1)): trained on the host
+  if ((s = train_force_model(sp, samples, n_s, &force)) != ROMB_OK) return s;
   FILE* f = fopen(path, "wb");
   if (!f) return ROMB_E_ARG;
   unsigned char hdr[128];
   memset(hdr, 0, sizeof(hdr));
   memcpy(hdr, "ROMBDDC1", 8);
-  const int32_t iv[8] = {1, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
+  const int32_t iv[8] = {2, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
   memcpy(hdr + 8, iv, 32);
   const double lohi[2] = {sp->lo, sp->hi};
   memcpy(hdr + 40, lohi, 16);
@@ -636,6 +638,7 @@ extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, con
   ok = ok && fwrite(U.data(), 8, U.size(), f) == U.size();
   ok = ok && fwrite(A.data(), 8, A.size(), f) == A.size();
   ok = ok && fwrite(magic.data(), 8, n_r, f) == (size_t)n_r;
+  ok = ok && write_force_section(f, force);
   fclose(f);
   return ok ? ROMB_OK : ROMB_E_ARG;
 }
