@@ -78,3 +78,8 @@ def test_gpu_trainer_at_benchmark_size_against_host_trainer(tmp_path):
     assert len(set(Rg.magic.tolist())) == spec.n_r
     for e_gpu, e_host in errs:
         assert e_gpu < 2 * e_host + 1e-10
+    # both trainers form the force model (Eq. SPEED L ext) by the same host
+    # routine on the same samples
+    assert Rg.force is not None and Rh.force is not None
+    assert np.array_equal(Rg.force.U, Rh.force.U) and np.array_equal(Rg.force.A, Rh.force.A)
+    assert np.array_equal(Rg.force.magic, Rh.force.magic)

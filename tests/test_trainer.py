@@ -58,3 +58,33 @@ def test_trained_model_properties(tmp_path):
         e_lib = np.abs(orom.mdeim(R, mu) - I).max() / np.abs(I).max()
         e_orc = np.abs(orom.mdeim(Ro, mu) - I).max() / np.abs(I).max()
         assert e_lib < 2 * e_orc + 1e-10
+
+
+def test_trained_force_model(tmp_path):
+    # the trainer's reduced model of the force integrals (Eq. SPEED L ext,
+    # reduced as in Sec. 4.2) against the oracle's edge integrals J(mu): an
+    # orthonormal basis, distinct magic entries reproduced exactly at the
+    # grid nodes, and held-out accuracy like the oracle-trained force model
+    from oracle import force_rom
+    romb = _lib()
+    p, lo, hi = 4, 0.07, 0.21
+    S = LI.lhs(30, lo, hi, seed=9)
+    path = str(tmp_path / "x.rom")
+    romb.romb_train(1, 0, p, 2, 8, lo, hi, S, path)
+    F = orom.read(path).force
+    assert F is not None and F.U.shape[0] == 4 * (p + 1) * 3
+    rf = F.U.shape[1]
+    assert 4 < rf <= 30
+    assert np.abs(F.U.T @ F.U - np.eye(rf)).max() < 1e-12
+    assert len(set(F.magic.tolist())) == rf
+    R = orom.read(path)
+    G = orom.grid_points(lo, hi, 2)
+    for g in (0, 40, 80):
+        J = force_rom.edge_load_tensor(1, G[g], 0, p, 2)
+        assert np.abs(force_rom.force_vector(F, R, G[g])[F.magic] - J[F.magic]).max() <= 1e-12 * np.abs(J).max()
+    Fo = force_rom.train_force(1, 0, p, 2, 2, lo, hi, S, max_rank=30)
+    for mu in LI.uniform_box(3, lo, hi, seed=10):
+        J = force_rom.edge_load_tensor(1, mu, 0, p, 2)
+        e_lib = np.abs(force_rom.force_vector(F, R, mu) - J).max() / np.abs(J).max()
+        e_orc = np.abs(force_rom.force_vector(Fo, R, mu) - J).max() / np.abs(J).max()
+        assert e_lib < 2 * e_orc + 1e-10, (e_lib, e_orc)
