@@ -658,8 +658,9 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
       return ROMB_E_STATE;
     }
     for (int f = 0; f < ROMB_MAX_FAMILIES; ++f)
-      if (c->famcount[f] > 0 && !c->roms[f].force_U) {
-        romb_set_error("reduced loads: the reduced model of a family in use has no force model");
+      if (c->famcount[f] > 0 &&
+          (!c->roms[f].force_U || c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) || c->roms[f].force_rf > 128)) {
+        romb_set_error("reduced loads: the reduced model of a family in use has no force model of this degree");
         return ROMB_E_STATE;
       }
   }

@@ -336,10 +336,21 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
                                                                    const int32_t* __restrict__ family,
                                                                    const double* __restrict__ trac,
                                                                    double* __restrict__ fU) {
+  // the family descriptors and edge nodes are copied to shared memory with
+  // static indices once per block; the warps then index them by family
+  __shared__ ForceRomDev sF[ROMB_MAX_FAMILIES];
+  __shared__ double sq[8];
   __shared__ double wts[LR_WARPS][4][12];
   __shared__ double th[LR_WARPS][128];
   __shared__ double Jv[LR_WARPS][(ROMB_MAX_P + 1) * 8];
   __shared__ double jk[LR_WARPS][8];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) sF[f] = FS.f[f];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sq[k] = FS.qnodes[k];
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int ncell_e[4] = {P.ny, P.ny, P.nx, P.nx};
@@ -351,12 +362,12 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
   if (e >= 4) return;
   const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
   if (t0 == 0.0 && t1 == 0.0) return;
-  const int p = P.p, q = P.q, nx = P.nx, ny = P.ny;
+  const int p = P.p, q = P.q, nx = P.nx, ny = P.ny, m = P.m;
   const int j = (int)t;
   const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
   const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
   const long long cell = cx + (long long)nx * cy;
-  const ForceRomDev F = FS.f[family[cell]];
+  const ForceRomDev& F = sF[family[cell]];
   const int r = F.r, n1 = r + 1, rf = F.rf;
   if (lane < 4) lagrange1d(r, F.nodes, mu[4 * cell + lane], wts[warp][lane], nullptr);
   __syncwarp();
@@ -375,14 +386,22 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     if (lane + 32 * u < rf) th[warp][lane + 32 * u] = acc[u];
-  // edge Jacobian at the q+1 interpolation nodes of the edge
+  // edge Jacobian j = |dx/dt| at the q+1 interpolation nodes of the edge: on
+  // an edge one factor of the tensor map basis is a Kronecker delta, so the
+  // tangent is the derivative of the 1D map basis against the m+1 control
+  // points of that edge
   if (lane <= q) {
-    const double tk = FS.qnodes[lane];
-    const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : tk, x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : tk;
-    double x[2], J[2][2];
-    map_eval(ctrl, nx, P.m, cx, cy, x1, x2, x, J);
-    const int dc = e < 2 ? 1 : 0;
-    jk[warp][lane] = hypot(J[0][dc], J[1][dc]);
+    double v[5], d[5];
+    map_basis1d(m, sq[lane], v, d);
+    double tx = 0.0, ty = 0.0;
+    for (int s = 0; s <= m; ++s) {
+      const int a = e == 0 ? 0 : e == 1 ? m : s;
+      const int b = e == 2 ? 0 : e == 3 ? m : s;
+      const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
+      tx = fma(d[s], X[0], tx);
+      ty = fma(d[s], X[1], ty);
+    }
+    jk[warp][lane] = hypot(tx, ty);
   }
   __syncwarp();
   // J_e[s][k] = sum_t U_f[t][(e (p+1) + s)(q+1) + k] theta_f[t]
