@@ -7,11 +7,18 @@
 * Threshold mu(xi) = sum_i l_i(xi) mu_i with first-degree Lagrange l_i and
   mu_i at the bottom-left, bottom-right, top-left, top-right corners
   (Sec. 2.1.2).
-* Trimmed domain Omega = {phi0 < mu} (Sec. 2.1.2).  Two families:
+* Trimmed domain Omega = {phi0 < mu} (Sec. 2.1.2).  Families:
   - circle hole, solid where |xi - (1/2,1/2)| > mu(xi)
     (phi = mu - |xi - c| < 0);
   - cross bars, solid where min(|xi1-1/2|, |xi2-1/2|) < mu(xi)
-    (phi = min(...) - mu < 0).
+    (phi = min(...) - mu < 0);
+  - the four 2D TPMS level sets phi0 of Table GEO tpms (Schwarz Diamond,
+    Schwarz Primitive, Schoen FRD, Schoen IWP), solid where phi0 < mu
+    (phi = phi0 - mu < 0).  The Schoen FRD takes the opposite sign of the
+    table's expression: the table's form ranges over [-2, 7], where the
+    paper's FRD threshold boxes [-6.5, 0.5] and [-7, 0.5] would give empty
+    cells below -2; its negative ranges over [-7, 2] and the boxes fit (the
+    caption states that the FRD sign is flipped).
 """
 from __future__ import annotations
 
@@ -21,6 +28,42 @@ from . import basis
 
 FAMILY_CIRCLE = 0
 FAMILY_CROSS = 1
+FAMILY_SCHWARZ_D = 2
+FAMILY_SCHWARZ_P = 3
+FAMILY_SCHOEN_FRD = 4
+FAMILY_SCHOEN_IWP = 5
+TPMS_FAMILIES = (FAMILY_SCHWARZ_D, FAMILY_SCHWARZ_P, FAMILY_SCHOEN_FRD, FAMILY_SCHOEN_IWP)
+
+
+def tpms_phi0(family: int, xi1, xi2):
+    """phi0 of Table GEO tpms (the 2D sections of the TPMS)."""
+    c1, c2 = np.cos(2 * np.pi * xi1), np.cos(2 * np.pi * xi2)
+    if family == FAMILY_SCHWARZ_D:
+        return c1 * c2
+    if family == FAMILY_SCHWARZ_P:
+        return c1 + c2 - 1.0
+    d1, d2 = np.cos(4 * np.pi * xi1), np.cos(4 * np.pi * xi2)
+    if family == FAMILY_SCHOEN_FRD:
+        return 4.0 * c1 * c2 - d1 * d2 - d2 - d1
+    if family == FAMILY_SCHOEN_IWP:
+        return 2.0 * (c1 * c2 + c2 + c1) - d1 - d2 - 1.0
+    raise ValueError(family)
+
+
+def tpms_line_coeffs(family: int, xi1: float):
+    """phi0 restricted to the line xi1 = const, written as
+    alpha cos(2 pi xi2) + beta cos(4 pi xi2) + gamma (collecting the terms of
+    Table GEO tpms by their xi2 dependence)."""
+    c1, d1 = np.cos(2 * np.pi * xi1), np.cos(4 * np.pi * xi1)
+    if family == FAMILY_SCHWARZ_D:
+        return c1, 0.0, 0.0
+    if family == FAMILY_SCHWARZ_P:
+        return 1.0, 0.0, c1 - 1.0
+    if family == FAMILY_SCHOEN_FRD:
+        return 4.0 * c1, -(d1 + 1.0), -d1
+    if family == FAMILY_SCHOEN_IWP:
+        return 2.0 * (c1 + 1.0), -1.0, 2.0 * c1 - d1 - 1.0
+    raise ValueError(family)
 
 
 def threshold(mu4: np.ndarray, xi1, xi2):
@@ -40,7 +83,7 @@ def level_set(family: int, mu4: np.ndarray, xi1, xi2):
         return mu - np.hypot(xi1 - 0.5, xi2 - 0.5)
     if family == FAMILY_CROSS:
         return np.minimum(np.abs(xi1 - 0.5), np.abs(xi2 - 0.5)) - mu
-    raise ValueError(family)
+    return tpms_phi0(family, xi1, xi2) - mu
 
 
 def cell_control_points(ctrl: np.ndarray, nx: int, m: int, cx: int, cy: int) -> np.ndarray:

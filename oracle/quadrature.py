@@ -16,6 +16,21 @@ between the panel and its two halves, which bounds the error of every
 polynomial integrand of that degree (the fast-assembly integrands are such
 polynomials).  The base panels are split at xi1 = 1/2 where the cross family
 has a kink.
+
+For the TPMS families of Table GEO tpms the roots along xi2 have no closed
+form.  On a line xi1 = x the level set is g(y) = alpha cos(2 pi y) +
+beta cos(4 pi y) + gamma - (a + b y), whose second derivative is bounded by
+M2 = (2 pi)^2 |alpha| + (4 pi)^2 |beta|.  Its sign changes on [0, 1] are
+isolated with that bound as a certificate: an interval with the same sign at
+both ends and min |g| > M2 h^2 / 8 holds no root (g stays within M2 h^2 / 8
+of its chord), an interval with a sign change and |g'| > M2 h at an end holds
+exactly one (g is monotone on it), and any other interval is halved.  Each
+certified root is then bisected to machine precision.  Halving stops at
+intervals of 1e-10: an uncertified one there counts one root if its end
+signs differ and none otherwise, and two roots closer than 1e-10 cancel.
+Such a pair only occurs where the line touches the level set tangentially,
+where rounding makes the sign of g noisy; the solid length it stands for is
+below 1e-10.
 """
 from __future__ import annotations
 
@@ -26,7 +41,60 @@ import numpy as np
 from numpy.polynomial import legendre as npleg
 
 from . import basis
-from .geometry import FAMILY_CIRCLE, FAMILY_CROSS
+from .geometry import FAMILY_CIRCLE, FAMILY_CROSS, TPMS_FAMILIES, tpms_line_coeffs
+
+
+def _bisect(g, u, v, neg_u):
+    """The sign change of g in (u, v] to machine precision; neg_u: g(u) < 0."""
+    while True:
+        m = 0.5 * (u + v)
+        if m <= u or m >= v:
+            return m
+        if (g(m) < 0.0) == neg_u:
+            u = m
+        else:
+            v = m
+
+
+def tpms_roots(family: int, a: float, b: float, x: float, n_grid: int = 32, h_min: float = 1e-10):
+    """Sign changes of g(y) = phi0(x, y) - (a + b y) in (0, 1), increasing,
+    and whether g(0) < 0 (the line starts in the solid)."""
+    al, be, ga = (float(v) for v in tpms_line_coeffs(family, x))
+    w = 2.0 * math.pi
+    g = lambda y: al * math.cos(w * y) + be * math.cos(2.0 * w * y) + ga - a - b * y
+    dg = lambda y: -w * al * math.sin(w * y) - 2.0 * w * be * math.sin(2.0 * w * y) - b
+    M2 = w * w * abs(al) + 4.0 * w * w * abs(be)
+    if M2 == 0.0:                  # g is linear in y
+        roots = []
+        if b != 0.0:
+            y0 = (ga - a) / b
+            if 0.0 < y0 < 1.0:
+                roots.append(y0)
+        return roots, g(0.0) < 0.0
+    roots = []
+    ys = [i / n_grid for i in range(n_grid + 1)]
+    gs = [g(y) for y in ys]
+    stack = [(ys[i], ys[i + 1], gs[i], gs[i + 1]) for i in range(n_grid - 1, -1, -1)]
+    while stack:
+        u, v, gu, gv = stack.pop()
+        h = v - u
+        if (gu < 0.0) != (gv < 0.0):
+            if abs(dg(u)) > M2 * h or abs(dg(v)) > M2 * h or h < h_min:
+                roots.append(_bisect(g, u, v, gu < 0.0))
+                continue
+        elif min(abs(gu), abs(gv)) > M2 * h * h / 8.0 or h < h_min:
+            continue
+        m = 0.5 * (u + v)
+        gm = g(m)
+        stack.append((m, v, gm, gv))
+        stack.append((u, m, gu, gm))
+    out = []
+    for y in roots:                 # increasing; cancel pairs closer than h_min
+        if out and y - out[-1] < h_min:
+            out.pop()
+        else:
+            out.append(y)
+    return out, gs[0] < 0.0
 
 
 def solid_intervals(family: int, mu4: np.ndarray, x: float):
@@ -75,6 +143,15 @@ def solid_intervals(family: int, mu4: np.ndarray, x: float):
             else:
                 merged.append((u, v))
         return merged
+    if family in TPMS_FAMILIES:
+        # solid where phi0(x, y) < a + b y; each root toggles the state
+        roots, solid = tpms_roots(family, a, b, x)
+        out = []
+        for u, v in zip([0.0] + roots, roots + [1.0]):
+            if solid and v > u:
+                out.append((u, v))
+            solid = not solid
+        return out
     raise ValueError(family)
 
 
@@ -145,7 +222,7 @@ def edge_solid_intervals(family: int, mu4: np.ndarray, edge: int):
     xi2 for vertical edges and along xi1 for horizontal ones."""
     if edge in (0, 1):
         return solid_intervals(family, mu4, float(edge == 1))
-    # swap the roles of xi1 and xi2: both families are symmetric under the
+    # swap the roles of xi1 and xi2: every family is symmetric under the
     # swap once mu_2 and mu_3 are exchanged
     mu_t = np.array([mu4[0], mu4[2], mu4[1], mu4[3]])
     return solid_intervals(family, mu_t, float(edge == 3))
