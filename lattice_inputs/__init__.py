@@ -18,7 +18,8 @@ Geometry conventions (shared by every consumer):
   bottom-right, top-left and top-right corners (Sec. 2.1.2, bilinear
   threshold).
 * ``family[c]``: 0 = circular hole of radius mu centred in the cell,
-  1 = solid cross of half-width mu.
+  1 = solid cross of half-width mu, 2..5 = the TPMS level sets Schwarz
+  Diamond, Schwarz Primitive, Schoen FRD and Schoen IWP (Table GEO tpms).
 * Edges of the lattice boundary are numbered 0 left, 1 right, 2 bottom, 3 top;
   ``dirichlet_mask`` bit e clamps edge e, ``traction[e]`` is the physical
   traction per unit length applied on edge e.
@@ -32,6 +33,7 @@ import numpy as np
 
 FAMILY_CIRCLE = 0
 FAMILY_CROSS = 1
+FAMILY_SCHWARZ_D, FAMILY_SCHWARZ_P, FAMILY_SCHOEN_FRD, FAMILY_SCHOEN_IWP = 2, 3, 4, 5
 
 EDGE_LEFT, EDGE_RIGHT, EDGE_BOTTOM, EDGE_TOP = 0, 1, 2, 3
 
@@ -163,6 +165,33 @@ def lattice(nx: int, ny: int, p: int, m: int, *, seed: int, basis: int = 0,
     return Lattice(nx=nx, ny=ny, p=p, m=m, basis=basis, ctrl=np.ascontiguousarray(ctrl),
                    mu=np.ascontiguousarray(mu, dtype=np.float64), family=family,
                    E=E, nu=nu, rho=rho, dirichlet_mask=dirichlet_mask, name=name)
+
+
+def quarter_annulus(nx: int, ny: int, p: int = 8, m: int = 4, r0: float = 0.6, r1: float = 1.0,
+                    rho: float = 5e-4, name: str = "") -> Lattice:
+    """The benchmark lattice of Sec. 5.2 (Eq. RES multi map): nx x ny cells of
+    the auxiliary square, mapped onto the quarter annulus r0 <= r <= r1 by
+    x = r sin(pi/2 s), y = -r cos(pi/2 s), Schwarz Diamond cells with the
+    vertex thresholds 0.9 - 0.8 s (s the first auxiliary coordinate), E = 5,
+    nu = 0.25, the edge s = 0 clamped and a downward traction of 0.1 on the
+    edge s = 1.  The radius runs r = r1 - (r1 - r0) t in the second auxiliary
+    coordinate t (the printed map with t -> 1 - t): the same domain, cells
+    and thresholds, with a positive Jacobian determinant; the Schwarz
+    Diamond is symmetric under xi2 -> 1 - xi2 inside each cell, so the
+    trimmed geometry is unchanged.  The cell maps are the degree-m
+    interpolants of this map on the shared control grid."""
+    X = reference_grid(nx, ny, m)
+    s, t = X[:, 0] / nx, X[:, 1] / ny
+    r = r1 - (r1 - r0) * t
+    ctrl = np.stack([r * np.sin(0.5 * math.pi * s), -r * np.cos(0.5 * math.pi * s)], axis=1)
+    vx = np.tile(np.arange(nx + 1), ny + 1).astype(np.float64) / nx
+    mu = vertex_values_to_cells(0.9 - 0.8 * vx, nx, ny)
+    tr = np.zeros((4, 2))
+    tr[EDGE_RIGHT] = [0.0, -0.1]
+    return Lattice(nx=nx, ny=ny, p=p, m=m, basis=0, ctrl=np.ascontiguousarray(ctrl),
+                   mu=np.ascontiguousarray(mu, dtype=np.float64),
+                   family=np.full(nx * ny, FAMILY_SCHWARZ_D, dtype=np.int32), E=5.0, nu=0.25, rho=rho,
+                   dirichlet_mask=1 << EDGE_LEFT, traction=tr, name=name or f"quarter-annulus-{nx}x{ny}-p{p}")
 
 
 def config(k: int) -> Lattice:

@@ -10,8 +10,13 @@ Neumann edges included) and internal (the 2(p-1)^2 interior DoFs of a cell).
 
 Coarse DoFs (Sec. 3.3.1): two per non-Dirichlet cross point (the displacement
 components) and three per non-Dirichlet cell edge: the integrals of u_1 and
-u_2 over the whole physical edge and the moment int f.u with
-f = (x2 - xbar2, xbar1 - x1), xbar = F(parametric midpoint of the edge).
+u_2 over the edge of the trimmed domain (the solid part of the physical edge)
+and the moment int f.u over the same part with f = (x2 - xbar2, xbar1 - x1),
+xbar = F(parametric midpoint of the edge).  Both cells of an edge must use
+one functional, so the solid part is the union of what either cell sees as
+solid there (the two agree when the trimmed compatibility condition holds);
+where that union is shorter than 1e-3 of the edge parameter the whole edge
+is used (three functionals over a vanishing part become dependent).
 Global coarse numbering: vertex (vx, vy) first, then horizontal edges
 (cx, vy), then vertical edges (vx, cy); Dirichlet ones are skipped.
 Local coarse slots of a cell: 2v + c for corner v (bl, br, tl, tr), then
@@ -152,31 +157,62 @@ class Lattice:
         return out
 
 
-def coarse_functionals(kind: int, p: int, P: np.ndarray, nq: int = 32) -> np.ndarray:
+EDGE_MIN_SOLID = 1e-3
+
+
+def _merge(ivs):
+    out = []
+    for u, v in sorted(ivs):
+        if out and u <= out[-1][1]:
+            out[-1] = (out[-1][0], max(out[-1][1], v))
+        else:
+            out.append((u, v))
+    return out
+
+
+def constraint_intervals(lat, cx: int, cy: int, e: int):
+    """The part of edge e of cell (cx, cy), in its edge parameter, over which
+    the edge's coarse functionals integrate: the union of the solid parts
+    seen by the cell and by its neighbour across the edge (the whole edge if
+    that union is shorter than EDGE_MIN_SOLID)."""
+    c = cx + lat.nx * cy
+    ivs = list(quadrature.edge_solid_intervals(int(lat.family[c]), lat.mu[c], e))
+    nb = {EDGE_LEFT: (cx - 1, cy, EDGE_RIGHT), EDGE_RIGHT: (cx + 1, cy, EDGE_LEFT),
+          EDGE_BOTTOM: (cx, cy - 1, EDGE_TOP), EDGE_TOP: (cx, cy + 1, EDGE_BOTTOM)}[e]
+    if 0 <= nb[0] < lat.nx and 0 <= nb[1] < lat.ny:
+        n = nb[0] + lat.nx * nb[1]
+        ivs += list(quadrature.edge_solid_intervals(int(lat.family[n]), lat.mu[n], nb[2]))
+    ivs = _merge(ivs)
+    if sum(v - u for u, v in ivs) < EDGE_MIN_SOLID:
+        return [(0.0, 1.0)]
+    return ivs
+
+
+def coarse_functionals(kind: int, p: int, P: np.ndarray, intervals=None, nq: int = 32) -> np.ndarray:
     """The 20 coarse-DoF functionals of one cell as rows over its full local
     DoF vector (Sec. 3.3.1): corner values, then per edge the integrals of u_1
-    and u_2 and the moment, all over the whole untrimmed physical edge."""
+    and u_2 and the moment over the given parts of the edge
+    (``intervals[e]``, in the edge parameter; the whole edge if None)."""
     ndof = 2 * (p + 1) ** 2
     Q = np.zeros((20, ndof))
     for v, k in enumerate([0, p, (p + 1) * p, (p + 1) * p + p]):
         Q[2 * v, 2 * k] = 1.0
         Q[2 * v + 1, 2 * k + 1] = 1.0
-    t, wt = basis.gauss_legendre(nq)
-    bt, _ = basis.basis_1d(kind, p, t)                   # [nq, p+1]
     for e in range(4):
         nodes = edge_local_nodes(p, e)
-        x, j = edge_tangent_length(P, e, t)
         m1, m2 = edge_point(e, np.array([0.5]))
         xbar, _ = geometry.map_eval(P, m1, m2)
         xbar = xbar[0]
-        avg = (wt * j) @ bt                              # int b_s j dt
-        mom1 = (wt * j * (x[:, 1] - xbar[1])) @ bt       # int b_s (x2 - xbar2) j dt
-        mom2 = (wt * j * (xbar[0] - x[:, 0])) @ bt       # int b_s (xbar1 - x1) j dt
         r = 8 + 3 * e
-        Q[r, 2 * nodes] = avg
-        Q[r + 1, 2 * nodes + 1] = avg
-        Q[r + 2, 2 * nodes] = mom1
-        Q[r + 2, 2 * nodes + 1] = mom2
+        for (u, w) in ([(0.0, 1.0)] if intervals is None else intervals[e]):
+            t, wt = basis.gauss_legendre(nq, u, w)
+            bt, _ = basis.basis_1d(kind, p, t)               # [nq, p+1]
+            x, j = edge_tangent_length(P, e, t)
+            avg = (wt * j) @ bt                              # int b_s j dt
+            Q[r, 2 * nodes] += avg
+            Q[r + 1, 2 * nodes + 1] += avg
+            Q[r + 2, 2 * nodes] += (wt * j * (x[:, 1] - xbar[1])) @ bt      # int b_s (x2 - xbar2) j dt
+            Q[r + 2, 2 * nodes + 1] += (wt * j * (xbar[0] - x[:, 0])) @ bt  # int b_s (xbar1 - x1) j dt
     return Q
 
 
@@ -265,7 +301,7 @@ class Bddc:
         L, lat = self.L, self.lat
         cx, cy = cell["cx"], cell["cy"]
         P = geometry.cell_control_points(lat.ctrl, lat.nx, lat.m, cx, cy)
-        Qfull = coarse_functionals(lat.basis, lat.p, P)
+        Qfull = coarse_functionals(lat.basis, lat.p, P, [constraint_intervals(lat, cx, cy, e) for e in range(4)])
         slots_g = L.cell_coarse(cx, cy)
         have = np.nonzero(slots_g >= 0)[0]
         U = cell["U"]

@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import assembly, bddc, geometry, rom as romlib
+from . import assembly, bddc, geometry, quadrature, rom as romlib
 
 
 def cell_maps(lat):
@@ -35,6 +35,32 @@ def theta(lat, roms: dict, q: int = 2):
         Cn[c] = assembly.fa_coefficients(P, lat.E, lat.nu, q)
         lam[c] = romlib.reduced_vector(roms[int(lat.family[c])], lat.mu[c])
     return Cn, lam
+
+
+def fa_tensors(lat, q: int = 2, pmap=map) -> dict:
+    """The exact fast-assembly tensors I(mu) of Sec. 4.1 by full trimmed
+    quadrature, one per distinct (family, thresholds) of the lattice."""
+    keys = sorted({(int(lat.family[c]),) + tuple(float(v) for v in lat.mu[c]) for c in range(lat.ncells)})
+    out = list(pmap(_fa_job, [(lat.basis, lat.p, q, k) for k in keys]))
+    return dict(zip(keys, out))
+
+
+def _fa_job(args):
+    kind, p, q, key = args
+    return assembly.fa_tensor(kind, p, q, quadrature.trimmed_rule(key[0], np.array(key[1:])))
+
+
+def matrices_fa(lat, tensors: dict, q: int = 2) -> np.ndarray:
+    """Cell matrices by fast assembly (Algorithm 4) with the exact tensors
+    I(mu) (no ROM)."""
+    nB = (lat.p + 1) ** 2
+    I_pi = assembly.fa_tensor_untrimmed(lat.basis, lat.p, q)
+    K = np.zeros((lat.ncells, 2 * nB, 2 * nB))
+    for c, P in cell_maps(lat):
+        key = (int(lat.family[c]),) + tuple(float(v) for v in lat.mu[c])
+        Cn = assembly.fa_coefficients(P, lat.E, lat.nu, q)
+        K[c] = assembly.local_stiffness(tensors[key], I_pi, Cn, lat.rho, nB)
+    return K
 
 
 def matrices_rom(lat, roms: dict, cells=None) -> np.ndarray:
