@@ -67,10 +67,11 @@ def _force_job(args):
 
 def force_vector(fr: ForceRom, rom: romlib.Rom, mu4: np.ndarray) -> np.ndarray:
     """J(mu) by the reduced model: U_f times the tensor Lagrange interpolant of
-    the grid coefficients (Algorithm 5, with the stiffness model's box and grid)."""
+    the grid coefficients (Algorithm 5, with the stiffness model's box and
+    grid; ``rom`` is the cluster model that holds mu)."""
     romlib.find_cluster(rom, mu4)
-    nodes = romlib.mu_nodes(rom.lo, rom.hi, rom.r)
-    l = [basis.lagrange(nodes, np.array([mu4[d]]))[0][0] for d in range(4)]
+    nodes = romlib.param_nodes(rom)
+    l = [basis.lagrange(nodes[d], np.array([mu4[d]]))[0][0] for d in range(4)]
     w = np.einsum("d,c,b,a->dcba", l[3], l[2], l[1], l[0]).ravel()
     return fr.U @ (fr.A @ w)
 
@@ -108,7 +109,7 @@ def lattice_loads_rom(lat, roms: dict, traction=None) -> np.ndarray:
                 continue
             c = cx + nx * cy
             fam = int(lat.family[c])
-            R = roms[fam]
+            R = romlib.model_for(roms[fam], lat.mu[c])
             P = geometry.cell_control_points(lat.ctrl, nx, m, cx, cy)
             J = force_vector(R.force, R, lat.mu[c])
             out[c] = cell_loads_fast(lat.basis, p, R.q, P, J, traction, edges)

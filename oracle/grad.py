@@ -86,10 +86,11 @@ def _cell_edges(lat, cx, cy):
 
 def reduced_vector_derivative(R, mu4, d):
     """dI_r/dmu_d: the tensor Lagrange interpolant with the d-th factor differentiated."""
-    nodes = romlib.mu_nodes(R.lo, R.hi, R.r)
+    R = romlib.model_for(R, mu4)
+    nodes = romlib.param_nodes(R)
     fac = []
     for k in range(4):
-        v, dv = basis.lagrange(nodes, np.array([mu4[k]]))
+        v, dv = basis.lagrange(nodes[k], np.array([mu4[k]]))
         fac.append(dv[0] if k == d else v[0])
     w = np.einsum("d,c,b,a->dcba", fac[3], fac[2], fac[1], fac[0]).ravel()
     return R.A @ w
@@ -142,7 +143,7 @@ def compliance_gradient(lat, roms: dict, rtol: float = 1e-13, cells=None):
                         dctrl[(m * cy + b) * gnx + (m * cx + a), comp] += val
             Cn = assembly.fa_coefficients(P, lat.E, lat.nu, R.q)
             for d in range(4):
-                dI = (1.0 - lat.rho) * (R.U @ reduced_vector_derivative(R, lat.mu[cell], d))
+                dI = (1.0 - lat.rho) * (romlib.model_for(R, lat.mu[cell]).U @ reduced_vector_derivative(R, lat.mu[cell], d))
                 dK = assembly.contract(dI, Cn, nB)
                 dmu[cell, d] = -ui @ dK @ ui
     return c, dctrl, dmu, u

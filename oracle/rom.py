@@ -13,7 +13,14 @@ Offline, per level-set family and parameter box M = [lo, hi]^4 (one cluster):
 Online (Algorithm 5): I(mu) = U_r I_r(mu), with I_r interpolated by degree-r
 tensor Lagrange polynomials on those GLL nodes.
 
-ROM file format (little endian), one family / one cluster per file:
+Clusters (Sec. 4.2.1): the box is split into n_k equal subintervals per
+parameter, n_K = n_k^4 cluster boxes, cluster k = k1 + n_k (k2 + n_k (k3 +
+n_k k4)) with k_d the subinterval of mu_d (FindCluster: k_d = floor((mu_d -
+lo) / h) capped at n_k - 1, so an interior subinterval boundary belongs to
+the upper cluster); each cluster is an independent model on its own box and
+GLL grid.
+
+ROM file format (little endian), one family per file:
 
   0   char[8]  "ROMBDDC1"
   8   int32    version = 1
@@ -23,17 +30,19 @@ ROM file format (little endian), one family / one cluster per file:
   24  int32    q
   28  int32    r
   32  int32    n_r
-  36  int32    n_k (clusters per parameter; 1)
+  36  int32    n_k (clusters per parameter)
   40  float64  lo
   48  float64  hi
   56  int64    n_i
   64  reserved (zeros) up to byte 128
   128 float64  I_Pi[n_i]
+  then per cluster, in cluster order:
       float64  U_r[n_r][n_i]        (basis vector j contiguous)
-      float64  A[n_r][(r+1)^4]      (I_r at grid node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4)))
+      float64  A[n_r][(r+1)^4]      (I_r at grid node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))
+                                     of the cluster's box)
       int64    magic[n_r]
-  version 2 only, the reduced model of the force integrals J(mu) (module
-  ``force_rom``), on the same box and grid:
+    version 2 only, the reduced model of the force integrals J(mu) (module
+    ``force_rom``), on the same box and grid:
       int64    n_f = 4 (p+1) (q+1), r_f
       float64  U_f[r_f][n_f], A_f[r_f][(r+1)^4]
       int64    magic_f[r_f]
@@ -61,13 +70,15 @@ class ForceRom:
 
 @dataclass
 class Rom:
+    """One cluster: the box is [lo, hi]^4, or per parameter [lo_d, hi_d]
+    when lo and hi are arrays of four."""
     family: int
     kind: int
     p: int
     q: int
     r: int
-    lo: float
-    hi: float
+    lo: float | np.ndarray
+    hi: float | np.ndarray
     I_pi: np.ndarray          # [n_i]
     U: np.ndarray             # [n_i, n_r]
     A: np.ndarray             # [n_r, (r+1)^4]
@@ -77,6 +88,58 @@ class Rom:
     @property
     def n_r(self) -> int:
         return self.U.shape[1]
+
+    def bounds(self):
+        return (np.broadcast_to(np.asarray(self.lo, dtype=np.float64), (4,)),
+                np.broadcast_to(np.asarray(self.hi, dtype=np.float64), (4,)))
+
+
+@dataclass
+class ClusteredRom:
+    """n_k^4 clusters of one family on the box [lo, hi]^4 (Sec. 4.2.1)."""
+    family: int
+    kind: int
+    p: int
+    q: int
+    r: int
+    n_k: int
+    lo: float
+    hi: float
+    I_pi: np.ndarray
+    clusters: list
+
+    def cluster_index(self, mu4: np.ndarray) -> int:
+        """FindCluster of Algorithm 5."""
+        mu4 = np.asarray(mu4, dtype=np.float64)
+        if np.any(mu4 < self.lo) or np.any(mu4 > self.hi):
+            raise ValueError(f"threshold {mu4} outside the trained box [{self.lo}, {self.hi}]")
+        h = (self.hi - self.lo) / self.n_k
+        k = [min(int((mu4[d] - self.lo) / h), self.n_k - 1) for d in range(4)]
+        return k[0] + self.n_k * (k[1] + self.n_k * (k[2] + self.n_k * k[3]))
+
+    def cluster(self, mu4: np.ndarray) -> Rom:
+        return self.clusters[self.cluster_index(mu4)]
+
+
+def cluster_box(lo: float, hi: float, n_k: int, k: int):
+    """Per-parameter bounds of cluster k."""
+    h = (hi - lo) / n_k
+    kd = [(k // n_k ** d) % n_k for d in range(4)]
+    return np.array([lo + h * i for i in kd]), np.array([lo + h * (i + 1) for i in kd])
+
+
+def model_for(rom, mu4: np.ndarray) -> Rom:
+    """The cluster model that serves mu4 (FindCluster, then its Rom)."""
+    if isinstance(rom, ClusteredRom):
+        return rom.cluster(mu4)
+    find_cluster(rom, mu4)
+    return rom
+
+
+def param_nodes(rom: Rom) -> list:
+    """The degree-r GLL nodes of each parameter's interval of the model's box."""
+    lo, hi = rom.bounds()
+    return [mu_nodes(lo[d], hi[d], rom.r) for d in range(4)]
 
 
 def snapshot(family: int, mu4: np.ndarray, kind: int, p: int, q: int) -> np.ndarray:
@@ -134,10 +197,13 @@ def mu_nodes(lo: float, hi: float, r: int) -> np.ndarray:
     return lo + (hi - lo) * basis.gll_nodes(r)
 
 
-def grid_points(lo: float, hi: float, r: int) -> np.ndarray:
-    """The (r+1)^4 tensor grid, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))."""
-    n = mu_nodes(lo, hi, r)
-    G4, G3, G2, G1 = np.meshgrid(n, n, n, n, indexing="ij")
+def grid_points(lo, hi, r: int) -> np.ndarray:
+    """The (r+1)^4 tensor grid, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4));
+    lo and hi scalar or per parameter."""
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (4,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (4,))
+    n = [mu_nodes(lo[d], hi[d], r) for d in range(4)]
+    G4, G3, G2, G1 = np.meshgrid(n[3], n[2], n[1], n[0], indexing="ij")
     return np.stack([G1.ravel(), G2.ravel(), G3.ravel(), G4.ravel()], axis=1)
 
 
@@ -170,68 +236,101 @@ def train(family: int, kind: int, p: int, q: int, r: int, n_r: int, lo: float, h
     return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic)
 
 
-def find_cluster(rom: Rom, mu4: np.ndarray) -> int:
-    """FindCluster of Algorithm 5 for a single cluster: parameters outside the
-    trained box are rejected (the surrogate is only queried inside it)."""
-    if np.any(mu4 < rom.lo) or np.any(mu4 > rom.hi):
+def train_clustered(family: int, kind: int, p: int, q: int, r: int, n_r: int, lo: float, hi: float, n_k: int,
+                    samples: list, pmap=map) -> ClusteredRom:
+    """Sec. 4.2.1-4.2.3 per cluster: samples[k] are the snapshot parameters
+    drawn in cluster k's box; each cluster is trained as its own model."""
+    clusters = []
+    for k in range(n_k ** 4):
+        clo, chi = cluster_box(lo, hi, n_k, k)
+        clusters.append(train(family, kind, p, q, r, n_r, clo, chi, samples[k], pmap=pmap))
+    return ClusteredRom(family, kind, p, q, r, n_k, lo, hi, clusters[0].I_pi, clusters)
+
+
+def find_cluster(rom, mu4: np.ndarray) -> int:
+    """FindCluster of Algorithm 5: parameters outside the trained box are
+    rejected (the surrogate is only queried inside it)."""
+    if isinstance(rom, ClusteredRom):
+        return rom.cluster_index(mu4)
+    lo, hi = rom.bounds()
+    if np.any(mu4 < lo) or np.any(mu4 > hi):
         raise ValueError(f"threshold {mu4} outside the trained box [{rom.lo}, {rom.hi}]")
     return 0
 
 
-def reduced_vector(rom: Rom, mu4: np.ndarray) -> np.ndarray:
-    """I_r(mu) by tensor degree-r Lagrange interpolation on the GLL grid."""
-    find_cluster(rom, mu4)
-    nodes = mu_nodes(rom.lo, rom.hi, rom.r)
-    l = [basis.lagrange(nodes, np.array([mu4[d]]))[0][0] for d in range(4)]
+def reduced_vector(rom, mu4: np.ndarray) -> np.ndarray:
+    """I_r(mu) by tensor degree-r Lagrange interpolation on the GLL grid of
+    the cluster that holds mu."""
+    R = model_for(rom, mu4)
+    nodes = param_nodes(R)
+    l = [basis.lagrange(nodes[d], np.array([mu4[d]]))[0][0] for d in range(4)]
     w = np.einsum("d,c,b,a->dcba", l[3], l[2], l[1], l[0]).ravel()
-    return rom.A @ w
+    return R.A @ w
 
 
-def mdeim(rom: Rom, mu4: np.ndarray) -> np.ndarray:
-    """Algorithm 5: I(mu) ~ U_r I_r(mu)."""
-    return rom.U @ reduced_vector(rom, mu4)
+def mdeim(rom, mu4: np.ndarray) -> np.ndarray:
+    """Algorithm 5: I(mu) ~ U_r I_r(mu) with the cluster's basis."""
+    return model_for(rom, mu4).U @ reduced_vector(rom, mu4)
 
 
-def write(rom: Rom, path: str) -> None:
-    n_i = rom.U.shape[0]
-    version = 1 if rom.force is None else 2
-    hdr = MAGIC + struct.pack("<8i", version, rom.family, rom.kind, rom.p, rom.q, rom.r, rom.n_r, 1)
-    hdr += struct.pack("<ddq", rom.lo, rom.hi, n_i)
+def write(rom, path: str) -> None:
+    cl = rom.clusters if isinstance(rom, ClusteredRom) else [rom]
+    n_k = rom.n_k if isinstance(rom, ClusteredRom) else 1
+    lo = float(rom.lo if isinstance(rom, ClusteredRom) else np.min(rom.lo))
+    hi = float(rom.hi if isinstance(rom, ClusteredRom) else np.max(rom.hi))
+    forced = [R.force is not None for R in cl]
+    if any(forced) and not all(forced):
+        raise ValueError("either every cluster has a force model or none")
+    n_i = cl[0].U.shape[0]
+    version = 2 if forced[0] else 1
+    hdr = MAGIC + struct.pack("<8i", version, rom.family, rom.kind, rom.p, rom.q, rom.r, cl[0].n_r, n_k)
+    hdr += struct.pack("<ddq", lo, hi, n_i)
     hdr += b"\0" * (HEADER - len(hdr))
     with open(path, "wb") as f:
         f.write(hdr)
         f.write(np.ascontiguousarray(rom.I_pi, dtype="<f8").tobytes())
-        f.write(np.ascontiguousarray(rom.U.T, dtype="<f8").tobytes())
-        f.write(np.ascontiguousarray(rom.A, dtype="<f8").tobytes())
-        f.write(np.ascontiguousarray(rom.magic, dtype="<i8").tobytes())
-        if rom.force is not None:
-            n_f, r_f = rom.force.U.shape
-            f.write(struct.pack("<qq", n_f, r_f))
-            f.write(np.ascontiguousarray(rom.force.U.T, dtype="<f8").tobytes())
-            f.write(np.ascontiguousarray(rom.force.A, dtype="<f8").tobytes())
-            f.write(np.ascontiguousarray(rom.force.magic, dtype="<i8").tobytes())
+        for R in cl:
+            f.write(np.ascontiguousarray(R.U.T, dtype="<f8").tobytes())
+            f.write(np.ascontiguousarray(R.A, dtype="<f8").tobytes())
+            f.write(np.ascontiguousarray(R.magic, dtype="<i8").tobytes())
+            if R.force is not None:
+                n_f, r_f = R.force.U.shape
+                f.write(struct.pack("<qq", n_f, r_f))
+                f.write(np.ascontiguousarray(R.force.U.T, dtype="<f8").tobytes())
+                f.write(np.ascontiguousarray(R.force.A, dtype="<f8").tobytes())
+                f.write(np.ascontiguousarray(R.force.magic, dtype="<i8").tobytes())
 
 
-def read(path: str) -> Rom:
+def read(path: str):
+    """A Rom (n_k = 1) or a ClusteredRom."""
     with open(path, "rb") as f:
         buf = f.read()
     if buf[:8] != MAGIC:
         raise ValueError("not a ROM file")
     version, family, kind, p, q, r, n_r, n_k = struct.unpack_from("<8i", buf, 8)
     lo, hi, n_i = struct.unpack_from("<ddq", buf, 40)
-    if version not in (1, 2) or n_k != 1:
+    if version not in (1, 2) or n_k < 1:
         raise ValueError("unsupported ROM file")
     o = HEADER
     I_pi = np.frombuffer(buf, "<f8", n_i, o).copy(); o += 8 * n_i
-    U = np.frombuffer(buf, "<f8", n_r * n_i, o).reshape(n_r, n_i).T.copy(); o += 8 * n_r * n_i
     ng = (r + 1) ** 4
-    A = np.frombuffer(buf, "<f8", n_r * ng, o).reshape(n_r, ng).copy(); o += 8 * n_r * ng
-    magic = np.frombuffer(buf, "<i8", n_r, o).copy(); o += 8 * n_r
-    force = None
-    if version == 2:
-        n_f, r_f = struct.unpack_from("<qq", buf, o); o += 16
-        Uf = np.frombuffer(buf, "<f8", r_f * n_f, o).reshape(r_f, n_f).T.copy(); o += 8 * r_f * n_f
-        Af = np.frombuffer(buf, "<f8", r_f * ng, o).reshape(r_f, ng).copy(); o += 8 * r_f * ng
-        mf = np.frombuffer(buf, "<i8", r_f, o).copy()
-        force = ForceRom(Uf, Af, mf)
-    return Rom(family, kind, p, q, r, lo, hi, I_pi, U, A, magic, force)
+    clusters = []
+    for k in range(n_k ** 4):
+        U = np.frombuffer(buf, "<f8", n_r * n_i, o).reshape(n_r, n_i).T.copy(); o += 8 * n_r * n_i
+        A = np.frombuffer(buf, "<f8", n_r * ng, o).reshape(n_r, ng).copy(); o += 8 * n_r * ng
+        magic = np.frombuffer(buf, "<i8", n_r, o).copy(); o += 8 * n_r
+        force = None
+        if version == 2:
+            n_f, r_f = struct.unpack_from("<qq", buf, o); o += 16
+            Uf = np.frombuffer(buf, "<f8", r_f * n_f, o).reshape(r_f, n_f).T.copy(); o += 8 * r_f * n_f
+            Af = np.frombuffer(buf, "<f8", r_f * ng, o).reshape(r_f, ng).copy(); o += 8 * r_f * ng
+            mf = np.frombuffer(buf, "<i8", r_f, o).copy(); o += 8 * r_f
+            force = ForceRom(Uf, Af, mf)
+        if n_k == 1:
+            clo, chi = lo, hi
+        else:
+            clo, chi = cluster_box(lo, hi, n_k, k)
+        clusters.append(Rom(family, kind, p, q, r, clo, chi, I_pi, U, A, magic, force))
+    if n_k == 1:
+        return clusters[0]
+    return ClusteredRom(family, kind, p, q, r, n_k, lo, hi, I_pi, clusters)

@@ -96,3 +96,48 @@ def test_full_rank_rom_is_exact_on_training_snapshots():
     I = rom.snapshot(0, S[2], 0, 2, 2)
     Ir = np.linalg.solve(R.U[R.magic], I[R.magic])
     assert np.abs(R.U @ Ir - I).max() < 1e-12 * np.abs(I).max()
+
+
+def test_find_cluster_rule():
+    # Sec. 4.2.1: n_k equal subintervals per parameter, cluster
+    # k = k1 + n_k (k2 + n_k (k3 + n_k k4)); an interior boundary belongs to the
+    # upper subinterval, the top of the box to the last one
+    lo, hi, n_k = 0.1, 0.9, 2
+    C = rom.ClusteredRom(2, 0, 3, 2, 1, n_k, lo, hi, np.zeros(1), [None] * 16)
+    assert C.cluster_index(np.array([0.1, 0.1, 0.1, 0.1])) == 0
+    assert C.cluster_index(np.array([0.5, 0.1, 0.1, 0.1])) == 1
+    assert C.cluster_index(np.array([0.49, 0.6, 0.1, 0.1])) == 2
+    assert C.cluster_index(np.array([0.2, 0.2, 0.2, 0.9])) == 8
+    assert C.cluster_index(np.array([0.9, 0.9, 0.9, 0.9])) == 15
+    with pytest.raises(ValueError):
+        C.cluster_index(np.array([0.05, 0.5, 0.5, 0.5]))
+    lo4, hi4 = rom.cluster_box(lo, hi, n_k, 6)          # k = (0, 1, 1, 0)
+    assert np.allclose(lo4, [0.1, 0.5, 0.5, 0.1]) and np.allclose(hi4, [0.5, 0.9, 0.9, 0.5])
+
+
+def test_clustered_model(tmp_path):
+    # n_k = 2 (16 clusters) of the Schwarz Diamond at p = 3: every cluster
+    # reproduces the exact entries at its magic points on its own grid nodes,
+    # each threshold is served by the cluster whose box holds it, and the
+    # file round trip keeps every cluster
+    from oracle import offline
+    lo, hi, n_k, r, n_r = 0.1, 0.9, 2, 1, 4
+    samples = [LI.lhs(6, *rom.cluster_box(lo, hi, n_k, k), seed=100 + k) for k in range(16)]
+    with offline._pool(None) as pool:
+        C = rom.train_clustered(2, 0, 3, 2, r, n_r, lo, hi, n_k, samples, pmap=pool.map)
+    for k in (0, 5, 15):
+        R = C.clusters[k]
+        clo, chi = rom.cluster_box(lo, hi, n_k, k)
+        G = rom.grid_points(clo, chi, r)
+        assert np.all(G >= clo - 1e-15) and np.all(G <= chi + 1e-15)
+        for g in (0, 7, 15):
+            mu = G[g] if k == 15 else np.minimum(G[g], chi - 1e-12)   # inside the half-open box
+            I = rom.snapshot(2, mu, 0, 3, 2)
+            assert C.cluster_index(mu) == k
+            assert np.abs(rom.mdeim(C, mu)[R.magic] - I[R.magic]).max() < 1e-9 * np.abs(I).max()
+    path = str(tmp_path / "c.rom")
+    rom.write(C, path)
+    C2 = rom.read(path)
+    assert isinstance(C2, rom.ClusteredRom) and C2.n_k == 2 and len(C2.clusters) == 16
+    mu = np.array([0.3, 0.7, 0.45, 0.62])
+    assert np.array_equal(rom.mdeim(C2, mu), rom.mdeim(C, mu))
