@@ -250,7 +250,7 @@ romb_status romb_read(romb_ctx* ctx, int field, void* out, size_t bytes);
  * [n_s][4] host array; n_threads host threads (0: all cores).
  * Errors: ROMB_E_ARG (bad spec, n_r > n_s, unwritable path), ROMB_E_NAN. */
 typedef struct {
-  int family;     /* 0 circle hole, 1 cross                   */
+  int family;     /* 0 circle hole, 1 cross, 2..5 TPMS (Table GEO tpms) */
   int basis;      /* 0 GLL Lagrange, 1 Bernstein              */
   int p, q, r;    /* cell degree (3..8), q = 2, grid degree r */
   int n_r;        /* reduced basis size                       */

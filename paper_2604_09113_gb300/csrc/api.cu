@@ -84,8 +84,10 @@ void romb_free_lattice(romb_ctx* c) {
   c->allocs.clear();
   auto sizes = c->sizes;
   const size_t rom_bytes = c->rom_bytes;
-  RombRom roms[ROMB_MAX_FAMILIES];
-  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) roms[i] = c->roms[i];
+  std::vector<RombRom> roms(c->roms, c->roms + ROMB_MAX_MODELS);
+  RombCtxFamilies fams[ROMB_MAX_FAMILIES];
+  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) fams[i] = c->fams[i];
+  const int nslots = c->nslots;
   std::vector<void*> keep = c->rom_allocs;
   cudaStream_t st = c->stream;
   bool own = c->own_stream;
@@ -114,7 +116,9 @@ void romb_free_lattice(romb_ctx* c) {
   *c = romb_ctx();
   for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
   c->load_form = load_form;
-  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->roms[i] = roms[i];
+  for (int i = 0; i < ROMB_MAX_MODELS; ++i) c->roms[i] = roms[i];
+  for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->fams[i] = fams[i];
+  c->nslots = nslots;
   c->rom_allocs = keep;
   c->stream = st;
   c->own_stream = own;
@@ -196,53 +200,27 @@ extern "C" void romb_destroy(romb_ctx* c) {
 // ---------------------------------------------------------------------------
 static bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
 
-extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* family_out) {
-  if (!c || !path) return ROMB_E_ARG;
-  ROMB_CUDA(cudaSetDevice(c->device));
-  FILE* f = fopen(path, "rb");
-  if (!f) return ROMB_E_ARG;
-  unsigned char hdr[128];
-  if (!rd(f, hdr, 128) || memcmp(hdr, "ROMBDDC1", 8) != 0) {
-    fclose(f);
-    return ROMB_E_FORMAT;
+// Release the device arrays of one model slot.
+static void free_model(romb_ctx* c, RombRom& R) {
+  if (R.loaded) {
+    romb_free_ptr(c, R.U64);
+    romb_free_ptr(c, R.Utiles);
+    romb_free_ptr(c, R.Utiles16);
+    romb_free_ptr(c, R.A);
+    romb_free_ptr(c, R.At);
+    romb_free_ptr(c, R.At2);
+    romb_free_ptr(c, R.force_U);
+    romb_free_ptr(c, R.force_At);
   }
-  int32_t iv[8];
-  double lohi[2];
-  int64_t n_i;
-  memcpy(iv, hdr + 8, 32);
-  memcpy(lohi, hdr + 40, 16);
-  memcpy(&n_i, hdr + 56, 8);
-  const int version = iv[0], family = iv[1], kind = iv[2], p = iv[3], q = iv[4], r = iv[5], n_r = iv[6],
-            n_k = iv[7];
-  const int nB = (p + 1) * (p + 1), nL = (q + 1) * (q + 1);
-  if ((version != 1 && version != 2) || n_k != 1 || family < 0 || family >= ROMB_MAX_FAMILIES || p < 3 || p > ROMB_MAX_P ||
-      q != 2 || r < 1 || r > 10 || n_r < 1 || n_r > 127 || n_i != (int64_t)nB * nB * nL * 4 ||
-      !(lohi[1] > lohi[0])) {
-    fclose(f);
-    return ROMB_E_FORMAT;
-  }
-  const long long ng = 1;
-  long long ngrid = ng;
-  for (int d = 0; d < 4; ++d) ngrid *= (r + 1);
-  std::vector<double> Ipi(n_i), U((size_t)n_r * n_i), A((size_t)n_r * ngrid);
-  bool ok = rd(f, Ipi.data(), 8 * n_i) && rd(f, U.data(), 8 * (size_t)n_r * n_i) &&
-            rd(f, A.data(), 8 * (size_t)n_r * ngrid);
-  // version 2: the reduced model of the force integrals J(mu) follows the magic points
-  int64_t fhdr[2] = {0, 0};
-  std::vector<double> Uf, Af;
-  if (ok && version == 2) {
-    std::vector<int64_t> magic(n_r);
-    ok = rd(f, magic.data(), 8 * (size_t)n_r) && rd(f, fhdr, 16) && fhdr[0] == 4LL * (p + 1) * (q + 1) &&
-         fhdr[1] >= 1 && fhdr[1] <= fhdr[0];
-    if (ok) {
-      Uf.resize((size_t)fhdr[1] * fhdr[0]);
-      Af.resize((size_t)fhdr[1] * ngrid);
-      ok = rd(f, Uf.data(), 8 * Uf.size()) && rd(f, Af.data(), 8 * Af.size());
-    }
-  }
-  fclose(f);
-  if (!ok) return ROMB_E_FORMAT;
+  R = RombRom();
+}
 
+// Convert one cluster's model to the device layouts and install it in R.
+static romb_status install_model(romb_ctx* c, RombRom& R, int family, int kind, int p, int q, int r, int n_r,
+                                 long long n_i, long long ngrid, const std::vector<double>& Ipi,
+                                 const std::vector<double>& U, const std::vector<double>& A,
+                                 const std::vector<double>& Uf, const std::vector<double>& Af, const int64_t* fhdr) {
+  const int nB = (p + 1) * (p + 1), nL = (q + 1) * (q + 1);
   // Rearrange into the pair-major half layout used by the contraction: row t of
   // U' is I_Pi (t = 0) or U_r column t-1; column (pair(k1<=k2), k3, j1, j2).
   const long long npairs = (long long)nB * (nB + 1) / 2;
@@ -259,18 +237,7 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
         for (int t = 0; t < n_r; ++t) Uh[(size_t)(t + 1) * n_half + dst] = U[(size_t)t * n_i + src];
       }
 
-  RombRom& R = c->roms[family];
-  if (R.loaded) {
-    romb_free_ptr(c, R.U64);
-    romb_free_ptr(c, R.Utiles);
-    romb_free_ptr(c, R.Utiles16);
-    romb_free_ptr(c, R.A);
-    romb_free_ptr(c, R.At);
-    romb_free_ptr(c, R.At2);
-    romb_free_ptr(c, R.force_U);
-    romb_free_ptr(c, R.force_At);
-    R = RombRom();
-  }
+  free_model(c, R);
   romb_status s;
   if (!Uf.empty()) {   // force model: U_f [r_f][n_f] and A_f transposed [grid][r_f]
     R.force_nf = (int)fhdr[0];
@@ -322,9 +289,95 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
   R.q = q;
   R.r = r;
   R.n_r = n_r;
-  R.lo = lohi[0];
-  R.hi = lohi[1];
   R.n_half = n_half;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* family_out) {
+  if (!c || !path) return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(c->device));
+  FILE* f = fopen(path, "rb");
+  if (!f) return ROMB_E_ARG;
+  unsigned char hdr[128];
+  if (!rd(f, hdr, 128) || memcmp(hdr, "ROMBDDC1", 8) != 0) {
+    fclose(f);
+    return ROMB_E_FORMAT;
+  }
+  int32_t iv[8];
+  double lohi[2];
+  int64_t n_i;
+  memcpy(iv, hdr + 8, 32);
+  memcpy(lohi, hdr + 40, 16);
+  memcpy(&n_i, hdr + 56, 8);
+  const int version = iv[0], family = iv[1], kind = iv[2], p = iv[3], q = iv[4], r = iv[5], n_r = iv[6],
+            n_k = iv[7];
+  const int nB = (p + 1) * (p + 1), nL = (q + 1) * (q + 1);
+  if ((version != 1 && version != 2) || n_k < 1 || n_k > ROMB_MAX_NK || family < 0 || family >= ROMB_MAX_FAMILIES || p < 3 || p > ROMB_MAX_P ||
+      q != 2 || r < 1 || r > 10 || n_r < 1 || n_r > 127 || n_i != (int64_t)nB * nB * nL * 4 ||
+      !(lohi[1] > lohi[0])) {
+    fclose(f);
+    return ROMB_E_FORMAT;
+  }
+  long long ngrid = 1;
+  for (int d = 0; d < 4; ++d) ngrid *= (r + 1);
+  int nK = 1;
+  for (int d = 0; d < 4; ++d) nK *= n_k;
+  std::vector<double> Ipi(n_i);
+  if (!rd(f, Ipi.data(), 8 * n_i)) {
+    fclose(f);
+    return ROMB_E_FORMAT;
+  }
+  // model slots of the family: reused when the cluster count is unchanged
+  RombCtxFamilies& F = c->fams[family];
+  for (int k = 0; k < F.n_k * F.n_k * F.n_k * F.n_k; ++k) free_model(c, c->roms[F.slot0 + k]);
+  if (F.n_k != n_k) {
+    if (c->nslots + nK > ROMB_MAX_MODELS) {
+      F = RombCtxFamilies();
+      fclose(f);
+      romb_set_error("romb_train_load: more than 64 resident models");
+      return ROMB_E_ARG;
+    }
+    F.slot0 = c->nslots;
+    c->nslots += nK;
+  }
+  F.n_k = 0;   // not usable until every cluster is in
+  const double h = (lohi[1] - lohi[0]) / n_k;
+  std::vector<double> U((size_t)n_r * n_i), A((size_t)n_r * ngrid), Uf, Af;
+  std::vector<int64_t> magic(n_r);
+  for (int k = 0; k < nK; ++k) {
+    bool ok = rd(f, U.data(), 8 * U.size()) && rd(f, A.data(), 8 * A.size()) && rd(f, magic.data(), 8 * magic.size());
+    // version 2: the reduced model of the force integrals J(mu) follows the magic points
+    int64_t fhdr[2] = {0, 0};
+    Uf.clear();
+    Af.clear();
+    if (ok && version == 2) {
+      ok = rd(f, fhdr, 16) && fhdr[0] == 4LL * (p + 1) * (q + 1) && fhdr[1] >= 1 && fhdr[1] <= fhdr[0];
+      if (ok) {
+        Uf.resize((size_t)fhdr[1] * fhdr[0]);
+        Af.resize((size_t)fhdr[1] * ngrid);
+        std::vector<int64_t> mf(fhdr[1]);
+        ok = rd(f, Uf.data(), 8 * Uf.size()) && rd(f, Af.data(), 8 * Af.size()) && rd(f, mf.data(), 8 * mf.size());
+      }
+    }
+    romb_status s = ok ? install_model(c, c->roms[F.slot0 + k], family, kind, p, q, r, n_r, n_i, ngrid, Ipi, U, A, Uf,
+                                       Af, fhdr)
+                       : ROMB_E_FORMAT;
+    if (s != ROMB_OK) {
+      for (int k2 = 0; k2 <= k; ++k2) free_model(c, c->roms[F.slot0 + k2]);
+      fclose(f);
+      return s;
+    }
+    RombRom& R = c->roms[F.slot0 + k];
+    R.cluster = k;
+    for (int d = 0, kk = k; d < 4; ++d, kk /= n_k) {
+      R.lo4[d] = lohi[0] + h * (kk % n_k);
+      R.hi4[d] = lohi[0] + h * (kk % n_k + 1);
+    }
+  }
+  fclose(f);
+  F.n_k = n_k;
+  F.lo = lohi[0];
+  F.hi = lohi[1];
   if (family_out) *family_out = family;
   return ROMB_OK;
 }
@@ -484,6 +537,7 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_theta_hi, cells * 128);
   A_(c->d_theta_lo, cells * 128);
   A_(c->d_famlist, cells);
+  A_(c->d_slot, cells);
   A_(c->d_K, cells * c->kpack);
   A_(c->d_kdiag, cells * c->nU);
   A_(c->d_ktot, c->nskel);
@@ -495,6 +549,7 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_Psi, cells * (long long)c->nU * ROMB_NSLOT);
   A_(c->d_SCl, cells * ROMB_NSLOT * ROMB_NSLOT);
   A_(c->d_D, cells * c->nU);
+  A_(c->d_efun, cells * 12LL * (c->p + 1));
   A_(c->d_ucell_map, cells * c->nU);
   A_(c->d_islot, c->nI);
   A_(c->d_uslot, c->nU);
@@ -657,7 +712,7 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
       romb_set_error("reduced loads: the cell matrices were not assembled from the reduced models");
       return ROMB_E_STATE;
     }
-    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f)
+    for (int f = 0; f < ROMB_MAX_MODELS; ++f)
       if (c->famcount[f] > 0 &&
           (!c->roms[f].force_U || c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) || c->roms[f].force_rf > 128)) {
         romb_set_error("reduced loads: the reduced model of a family in use has no force model of this degree");

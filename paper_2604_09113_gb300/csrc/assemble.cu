@@ -21,18 +21,59 @@ struct RomDev {
   const double* At;      // [ngrid][n_r]  (transposed interpolation samples)
   const float2* At2;     // the same as (hi, lo) FP32 pairs
   int n_r, r;
-  double lo, hi;
+  double lo4[4], hi4[4]; // the cluster's box per threshold
   long long n_half;
-  double nodes[12];      // degree-r GLL nodes of [lo, hi]
+  double g01[12];        // degree-r GLL nodes of [0, 1]; node i of threshold d is lo4 + (hi4 - lo4) g01[i]
 };
 
-// the families of one theta launch: family k owns CTAs [cta0[k], cta0[k+1])
+// the models of one theta launch: model k owns CTAs [cta0[k], cta0[k+1])
 struct ThetaFams {
-  RomDev rom[ROMB_MAX_FAMILIES];
-  const int* list[ROMB_MAX_FAMILIES];
-  int count[ROMB_MAX_FAMILIES], cta0[ROMB_MAX_FAMILIES];
+  RomDev rom[ROMB_MAX_MODELS];
+  const int* list[ROMB_MAX_MODELS];
+  int count[ROMB_MAX_MODELS], cta0[ROMB_MAX_MODELS];
   int nfam;
 };
+
+// FindCluster (Algorithm 5, Sec. 4.2.1): the model slot of each cell, from its
+// family's cluster table: k_d = floor((mu_d - lo) / h) capped at n_k - 1
+// (an interior subinterval boundary belongs to the upper cluster).  Cells
+// outside their family's box are flagged and kept in the nearest cluster;
+// cells of a family without models get slot -1.
+struct FamTab {
+  int n_k[ROMB_MAX_FAMILIES], slot0[ROMB_MAX_FAMILIES];
+  double lo[ROMB_MAX_FAMILIES], hi[ROMB_MAX_FAMILIES];
+};
+__global__ void cell_model_kernel(FamTab T, const int32_t* __restrict__ family, const double* __restrict__ mu,
+                                  int ncells, int32_t* __restrict__ slot, int32_t* __restrict__ flags) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int f = family[c];
+  int nk = 0, s0 = -1;
+  double lo = 0.0, hi = 0.0;
+#pragma unroll
+  for (int k = 0; k < ROMB_MAX_FAMILIES; ++k)
+    if (k == f) {
+      nk = T.n_k[k];
+      s0 = T.slot0[k];
+      lo = T.lo[k];
+      hi = T.hi[k];
+    }
+  if (nk == 0) {
+    slot[c] = -1;
+    return;
+  }
+  const double h = (hi - lo) / nk;
+  int k = 0, stride = 1;
+  for (int d = 0; d < 4; ++d) {
+    const double m = mu[4 * c + d];
+    if (!(m >= lo && m <= hi)) atomicOr(&flags[c], ROMB_FLAG_OUT_OF_BOX);
+    int kd = (int)floor((m - lo) / h);
+    kd = kd < 0 ? 0 : kd > nk - 1 ? nk - 1 : kd;
+    k += kd * stride;
+    stride *= nk;
+  }
+  slot[c] = s0 + k;
+}
 
 void fill_cell_params(const romb_ctx* c, CellParams* P) {
   memset(P, 0, sizeof(*P));
@@ -232,15 +273,13 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, ThetaFams F,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // the family of this CTA (families own consecutive CTA ranges)
   int fi = 0;
-#pragma unroll
-  for (int k = 1; k < ROMB_MAX_FAMILIES; ++k)
-    if (k < F.nfam && (int)blockIdx.x >= F.cta0[k]) fi = k;
+  for (int k = 1; k < F.nfam; ++k)
+    if ((int)blockIdx.x >= F.cta0[k]) fi = k;
   const RomDev& R = F.rom[fi];
   const int* __restrict__ list = F.list[fi];
   const int count = F.count[fi];
   const int first = (((int)blockIdx.x - F.cta0[fi]) * 4 + warp) * TH_CELLS;
   const int r = R.r, n1 = r + 1;
-  const double* nodes = R.nodes;
   int cells[TH_CELLS];
   for (int j = 0; j < TH_CELLS; ++j) cells[j] = (first + j < count) ? list[first + j] : -1;
   // 1D interpolation weights: lane = (cell j, parameter d)
@@ -250,7 +289,9 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, ThetaFams F,
     double v[12];
     if (c >= 0) {
       const double m = mu[4 * (long long)c + d];
-      if (!(m >= R.lo && m <= R.hi)) atomicOr(&flags[c], ROMB_FLAG_OUT_OF_BOX);
+      if (!(m >= R.lo4[d] && m <= R.hi4[d])) atomicOr(&flags[c], ROMB_FLAG_OUT_OF_BOX);
+      double nodes[12];
+      for (int i = 0; i < n1; ++i) nodes[i] = R.lo4[d] + (R.hi4[d] - R.lo4[d]) * R.g01[i];
       lagrange1d(r, nodes, m, v, nullptr);
     } else {
       for (int i = 0; i < n1; ++i) v[i] = 0.0;
@@ -480,43 +521,65 @@ static romb_status ensure_pairs(romb_ctx* c) {
 romb_status launch_theta(romb_ctx* c) {
   romb_status s;
   if ((s = ensure_pairs(c)) != ROMB_OK) return s;
-  int* d_counts = (int*)c->d_red + 16;
-  family_list_kernel<<<1, 1024, 0, c->stream>>>(c->d_family, c->ncells, ROMB_MAX_FAMILIES, c->d_famlist, d_counts,
+  // the model slot of every cell, then the cells grouped by slot
+  {
+    FamTab T;
+    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+      T.n_k[f] = c->fams[f].n_k;
+      T.slot0[f] = c->fams[f].slot0;
+      T.lo[f] = c->fams[f].lo;
+      T.hi[f] = c->fams[f].hi;
+    }
+    cell_model_kernel<<<(c->ncells + 255) / 256, 256, 0, c->stream>>>(T, c->d_family, c->d_mu, c->ncells, c->d_slot,
+                                                                      c->d_flags); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
+  int* d_counts = (int*)(c->d_red + 64);
+  family_list_kernel<<<1, 1024, 0, c->stream>>>(c->d_slot, c->ncells, c->nslots, c->d_famlist, d_counts,
                                                 c->d_flags); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
-  int counts[ROMB_MAX_FAMILIES];
-  ROMB_CUDA(cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, c->stream));
+  int counts[ROMB_MAX_MODELS] = {0};
+  if (c->nslots > 0)
+    ROMB_CUDA(cudaMemcpyAsync(counts, d_counts, sizeof(int) * c->nslots, cudaMemcpyDeviceToHost, c->stream));
   ROMB_CUDA(cudaStreamSynchronize(c->stream));
   CellParams P;
   fill_cell_params(c, &P);
   int start = 0;
-  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+  for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
     c->famstart[f] = start;
     c->famcount[f] = counts[f];
-    // cells that reference a family without a model
-    if (counts[f] > 0 && !c->roms[f].loaded) return ROMB_E_ARG;
     start += counts[f];
   }
+  // cells of a family without models (slot -1) fall in no group
+  if (start != c->ncells) return ROMB_E_ARG;
   // one launch per group of families that share the kernel's template
   // arguments (lane slots per coefficient, compile-time r + 1)
   const bool df = c->prec != ROMB_FP64;   // split forms: theta in double-float
-  bool done[ROMB_MAX_FAMILIES] = {false};
-  for (int f0 = 0; f0 < ROMB_MAX_FAMILIES; ++f0) {
+  bool done[ROMB_MAX_MODELS] = {false};
+  for (int f0 = 0; f0 < ROMB_MAX_MODELS; ++f0) {
     if (done[f0] || counts[f0] == 0) continue;
     const int ns = (c->roms[f0].n_r + 31) / 32;
     const bool r6 = df && c->roms[f0].r == 6;
     ThetaFams F;
     memset(&F, 0, sizeof(F));
     int grid = 0;
-    for (int f = f0; f < ROMB_MAX_FAMILIES; ++f) {
+    for (int f = f0; f < ROMB_MAX_MODELS; ++f) {
       const RombRom& Rr = c->roms[f];
       if (done[f] || counts[f] == 0 || (Rr.n_r + 31) / 32 != ns || (df && Rr.r == 6) != r6) continue;
       done[f] = true;
       RomDev& R = F.rom[F.nfam];
-      R = RomDev{Rr.U64, Rr.At, Rr.At2, Rr.n_r, Rr.r, Rr.lo, Rr.hi, Rr.n_half, {0}};
-      double g[12];
-      gll_nodes01(Rr.r, g);
-      for (int i = 0; i <= Rr.r; ++i) R.nodes[i] = Rr.lo + (Rr.hi - Rr.lo) * g[i];
+      memset(&R, 0, sizeof(R));
+      R.U64 = Rr.U64;
+      R.At = Rr.At;
+      R.At2 = Rr.At2;
+      R.n_r = Rr.n_r;
+      R.r = Rr.r;
+      for (int d = 0; d < 4; ++d) {
+        R.lo4[d] = Rr.lo4[d];
+        R.hi4[d] = Rr.hi4[d];
+      }
+      R.n_half = Rr.n_half;
+      gll_nodes01(Rr.r, R.g01);
       F.list[F.nfam] = c->d_famlist + c->famstart[f];
       F.count[F.nfam] = counts[f];
       F.cta0[F.nfam] = grid;
@@ -539,7 +602,7 @@ romb_status launch_theta(romb_ctx* c) {
 
 romb_status launch_assemble_fp64(romb_ctx* c) {
   const int npairs = c->nB * (c->nB + 1) / 2;
-  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+  for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
     const int K = R.n_r + 1;

@@ -55,7 +55,7 @@ struct TcFamily {
 };
 
 struct TcParams {
-  TcFamily fam[ROMB_MAX_FAMILIES];
+  TcFamily fam[ROMB_MAX_MODELS];
   int nfam;
   const double* theta;     // [cells][128] f64 (slots 0, 1 applied exactly in the epilogue)
   int ntiles, KT;
@@ -570,7 +570,7 @@ romb_status launch_assemble_tc(romb_ctx* c) {
   TcParams P;
   memset(&P, 0, sizeof(P));
   int KT = -1, T = -1, grid = 0;
-  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+  for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
     const int kp = bf ? R.kpad16 : R.kpad;

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "romb_internal.cuh"
+#include "trim.cuh"
 
 #define ROMB_NQ 24   // Gauss points per edge for the coarse functionals
 
@@ -128,86 +129,18 @@ __device__ inline double warp_sum(double v) {
 }
 
 // Solid sub-intervals [lo, hi] of cell edge e (0 left, 1 right, 2 bottom, 3 top)
-// in the edge parameter, from the closed-form roots of the level set on the
-// edge (bilinear threshold).  Returns the number of intervals (<= 2).
+// in the edge parameter: the trimmed line of a vertical edge is the line
+// xi1 = 0 or 1; a horizontal edge is the same line of the cell with xi1 and
+// xi2 exchanged, i.e. with mu_2 and mu_3 exchanged (every family is symmetric
+// under the exchange).  Returns the number of intervals (<= ROMB_MAX_IV).
 __device__ inline int edge_solid_dev(int family, const double* mu4, int e, double* lo, double* hi) {
-  // parameter t along the edge; fixed coordinate c0
   const double c0 = (e == 1 || e == 3) ? 1.0 : 0.0;
-  double a, b;
-  if (e < 2) {   // vertical edge: mu(c0, t)
-    a = mu4[0] * (1.0 - c0) + mu4[1] * c0;
-    b = (mu4[2] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[1]) * c0;
-  } else {       // horizontal edge: mu(t, c0)
-    a = mu4[0] * (1.0 - c0) + mu4[2] * c0;
-    b = (mu4[1] - mu4[0]) * (1.0 - c0) + (mu4[3] - mu4[2]) * c0;
+  double m[4] = {mu4[0], mu4[1], mu4[2], mu4[3]};
+  if (e >= 2) {
+    m[1] = mu4[2];
+    m[2] = mu4[1];
   }
-  int n = 0;
-  if (family == 0) {   // solid outside |xi - c| = mu
-    const double A = 1.0 - b * b, B = -1.0 - 2.0 * a * b, C = (c0 - 0.5) * (c0 - 0.5) + 0.25 - a * a;
-    const double disc = B * B - 4.0 * A * C;
-    if (disc <= 0.0) {
-      lo[0] = 0.0;
-      hi[0] = 1.0;
-      return 1;
-    }
-    const double s = sqrt(disc), r1 = (-B - s) / (2.0 * A), r2 = (-B + s) / (2.0 * A);
-    if (r1 > 0.0) {
-      lo[n] = 0.0;
-      hi[n] = fmin(r1, 1.0);
-      if (hi[n] > lo[n]) ++n;
-    }
-    if (r2 < 1.0) {
-      lo[n] = fmax(r2, 0.0);
-      hi[n] = 1.0;
-      if (hi[n] > lo[n]) ++n;
-    }
-    return n;
-  }
-  // cross: |c0 - 1/2| < a + b t  or  |t - 1/2| < a + b t
-  double l1, h1;
-  const double tt = fabs(c0 - 0.5) - a;
-  bool has1 = true;
-  if (b > 0.0) {
-    l1 = tt / b;
-    h1 = 1e300;
-  } else if (b < 0.0) {
-    l1 = -1e300;
-    h1 = tt / b;
-  } else if (tt < 0.0) {
-    l1 = -1e300;
-    h1 = 1e300;
-  } else {
-    has1 = false;
-    l1 = h1 = 0.0;
-  }
-  const double l2 = (0.5 - a) / (1.0 + b), h2 = (0.5 + a) / (1.0 - b);
-  double L[2], H[2];
-  int m = 0;
-  if (has1) {
-    L[m] = fmax(l1, 0.0);
-    H[m] = fmin(h1, 1.0);
-    if (H[m] > L[m]) ++m;
-  }
-  L[m] = fmax(l2, 0.0);
-  H[m] = fmin(h2, 1.0);
-  if (H[m] > L[m]) ++m;
-  if (m == 2 && L[1] < L[0]) {
-    double t = L[0];
-    L[0] = L[1];
-    L[1] = t;
-    t = H[0];
-    H[0] = H[1];
-    H[1] = t;
-  }
-  for (int i = 0; i < m; ++i) {
-    if (n > 0 && L[i] <= hi[n - 1]) hi[n - 1] = fmax(hi[n - 1], H[i]);
-    else {
-      lo[n] = L[i];
-      hi[n] = H[i];
-      ++n;
-    }
-  }
-  return n;
+  return solid_y(family, m, c0, lo, hi);
 }
 
 // Host helper: fill a CellParams from the context.

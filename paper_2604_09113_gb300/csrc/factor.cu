@@ -3,7 +3,8 @@
 //  (Sec. 3.2)   K_II = L L^T,  W = L^-1 K_IU,  S = K_UU - W^T W
 //  (Sec. 3.3.3) D_jj = K_jj / K^tot_j  (stiffness-weighted partition of unity)
 //  (Sec. 3.3.1) coarse functionals: corner values, per edge int u_1, int u_2 and
-//               int f.u over the whole physical edge, f = (x2 - xbar2, xbar1 - x1)
+//               int f.u over the edge of the trimmed domain, f = (x2 - xbar2,
+//               xbar1 - x1) (edge_functional_kernel)
 //  (Alg. 2)     cross-point DoFs removed: Shat = S minus corners, Chat = edge rows,
 //               That = Chat Shat^-1 Chat^T
 //  (Eq. BDDC local basis) Psi column per local coarse DoF, corner values moved
@@ -35,7 +36,7 @@ struct FactorDims {
   static constexpr int NB = (P + 1) * (P + 1), ND = 2 * NB, NI = 2 * (P - 1) * (P - 1), NU = 8 * P, NK = NU - 8;
   // phase 1 (doubles)
   static constexpr int oAII = 0, oAIU = oAII + NI * NI, oAUU = oAIU + NI * NU, oCr = oAUU + NU * NU,
-                       oKd = oCr + 20 * NU, oDv = oKd + NU, oEx = oDv + NU, oEnd1 = oEx + 4 * ROMB_NQ * 3 + 8;
+                       oKd = oCr + 20 * NU, oDv = oKd + NU, oEnd1 = oDv + NU;
   // phase 2 reuses [oAII, oAUU) when it fits there (S stays in place), else
   // it goes after the phase-1 arrays
   static constexpr int size2 = NK * NK + NK * 12 + 144 + NK * 20 + NU * 20 + NK * 20;
@@ -45,9 +46,100 @@ struct FactorDims {
   static constexpr int total = oEnd2 > oEnd1 ? oEnd2 : oEnd1;
 };
 
+// The edge functionals of Sec. 3.3.1 on the skeleton nodes of every cell
+// edge: a_s = int b_s j dt, m1_s = int b_s (x2 - xbar2) j dt and
+// m2_s = int b_s (xbar1 - x1) j dt (j = |dx/dt|, xbar the image of the edge
+// midpoint) over the edge of the trimmed domain: where both cells sharing the
+// edge are solid (the skeleton of Omega), the cell's own solid part on the
+// lattice boundary, the whole edge where that part is shorter than
+// ROMB_EDGE_MIN_SOLID; each interval by the ROMB_NQ-point Gauss rule.  One
+// warp per (cell, edge); out[cell][e][s][3].
+#define ROMB_EDGE_MIN_SOLID 1e-3
+__global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, const double* __restrict__ ctrl,
+                                                              const double* __restrict__ mu,
+                                                              const int32_t* __restrict__ family,
+                                                              double* __restrict__ out) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= 4LL * P.ncells) return;
+  const long long cell = w >> 2;
+  const int e = (int)(w & 3), p = P.p, m = P.m, nx = P.nx, ny = P.ny;
+  const int cx = (int)(cell % nx), cy = (int)(cell / nx);
+  // intervals: where this cell and its neighbour across the edge are both
+  // solid (the cell's own solid part on the lattice boundary)
+  double lo[ROMB_MAX_IV * ROMB_MAX_IV], hi[ROMB_MAX_IV * ROMB_MAX_IV];
+  double ol[ROMB_MAX_IV], oh[ROMB_MAX_IV];
+  int nm = edge_solid_dev(family[cell], mu + 4 * cell, e, ol, oh);
+  for (int i = 0; i < nm; ++i) {
+    lo[i] = ol[i];
+    hi[i] = oh[i];
+  }
+  const int ncx = e == 0 ? cx - 1 : e == 1 ? cx + 1 : cx, ncy = e == 2 ? cy - 1 : e == 3 ? cy + 1 : cy;
+  if (ncx >= 0 && ncx < nx && ncy >= 0 && ncy < ny) {
+    const long long nb = ncx + (long long)nx * ncy;
+    double bl[ROMB_MAX_IV], bh[ROMB_MAX_IV];
+    const int n2 = edge_solid_dev(family[nb], mu + 4 * nb, e ^ 1, bl, bh);
+    const int n1 = nm;
+    nm = 0;
+    for (int i = 0; i < n1; ++i)    // both lists are sorted and disjoint: so is the result
+      for (int k = 0; k < n2; ++k) {
+        const double u = fmax(ol[i], bl[k]), v = fmin(oh[i], bh[k]);
+        if (v > u) {
+          lo[nm] = u;
+          hi[nm++] = v;
+        }
+      }
+  }
+  double len = 0.0;
+  for (int i = 0; i < nm; ++i) len += hi[i] - lo[i];
+  if (len < ROMB_EDGE_MIN_SOLID) {
+    nm = 1;
+    lo[0] = 0.0;
+    hi[0] = 1.0;
+  }
+  // the edge's m+1 map control points (a Kronecker delta in the other direction)
+  auto edge_pt = [&](double t, double* x, double* tg) {
+    double v[5], d[5];
+    map_basis1d(m, t, v, d);
+    x[0] = x[1] = tg[0] = tg[1] = 0.0;
+    for (int q = 0; q <= m; ++q) {
+      const int a = e == 0 ? 0 : e == 1 ? m : q;
+      const int b = e == 2 ? 0 : e == 3 ? m : q;
+      const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
+      x[0] = fma(v[q], X[0], x[0]);
+      x[1] = fma(v[q], X[1], x[1]);
+      tg[0] = fma(d[q], X[0], tg[0]);
+      tg[1] = fma(d[q], X[1], tg[1]);
+    }
+  };
+  double xb[2], tb[2];
+  edge_pt(0.5, xb, tb);
+  double acc[3 * (ROMB_MAX_P + 1)];
+  for (int i = 0; i < 3 * (p + 1); ++i) acc[i] = 0.0;
+  for (int t = lane; t < nm * ROMB_NQ; t += 32) {
+    const int iv = t / ROMB_NQ, qq = t % ROMB_NQ;
+    const double L = hi[iv] - lo[iv], tt = lo[iv] + L * P.gq_x[qq];
+    double x[2], tg[2], bv[ROMB_MAX_P + 1];
+    edge_pt(tt, x, tg);
+    cell_basis1d(P, tt, bv, nullptr);
+    const double wj = L * P.gq_w[qq] * hypot(tg[0], tg[1]);
+    for (int s_ = 0; s_ <= p; ++s_) {
+      const double wb = wj * bv[s_];
+      acc[3 * s_] += wb;
+      acc[3 * s_ + 1] += wb * (x[1] - xb[1]);
+      acc[3 * s_ + 2] += wb * (xb[0] - x[0]);
+    }
+  }
+  double* o = out + (cell * 4 + e) * (p + 1) * 3;
+  for (int i = 0; i < 3 * (p + 1); ++i) {
+    const double v = warp_sum(acc[i]);
+    if (lane == 0) o[i] = v;
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double* __restrict__ Kp,
-                                                      const double* __restrict__ ctrl, const int* __restrict__ umap,
+                                                      const double* __restrict__ efun, const int* __restrict__ umap,
                                                       const int* __restrict__ cmap, const double* __restrict__ ktot,
                                                       double* __restrict__ LII_out, double* __restrict__ W_out,
                                                       double* __restrict__ S_out, double* __restrict__ G_out,
@@ -63,7 +155,6 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
   double* Cr = sm + Dm::oCr;
   double* kd = sm + Dm::oKd;
   double* Dv = sm + Dm::oDv;
-  double* Ex = sm + Dm::oEx;   // per edge and Gauss point: x1, x2, j ; then xbar
   __shared__ int s_umap[NU], s_cmap[20], s_keep[NK], s_cu[8], s_islot[NI], s_uslot[NU], s_bad;
   __shared__ double s_rs[ND][2];   // row sums over each displacement component (translation test)
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -121,20 +212,6 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     if (s_umap[u] < 0 || s_umap[v] < 0) val = (u == v) ? 1.0 : 0.0;
     S[t] = val;
   }
-  // edge geometry for the coarse functionals: x(t_q), j(t_q) and the midpoint
-  for (int t = tid; t < 4 * (ROMB_NQ + 1); t += nt) {
-    const int e = t / (ROMB_NQ + 1), qq = t % (ROMB_NQ + 1);
-    double x[2], tg[2];
-    edge_map_point(Pm, ctrl, cx, cy, e, qq, x, tg);
-    if (qq < ROMB_NQ) {
-      Ex[(e * ROMB_NQ + qq) * 3 + 0] = x[0];
-      Ex[(e * ROMB_NQ + qq) * 3 + 1] = x[1];
-      Ex[(e * ROMB_NQ + qq) * 3 + 2] = hypot(tg[0], tg[1]);
-    } else {
-      Ex[4 * ROMB_NQ * 3 + 2 * e + 0] = x[0];
-      Ex[4 * ROMB_NQ * 3 + 2 * e + 1] = x[1];
-    }
-  }
   for (int t = tid; t < 20 * NU; t += nt) Cr[t] = 0.0;
   __syncthreads();
   // ---- coarse functionals ----
@@ -145,15 +222,8 @@ __global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double
     const int e = t / (P + 1), s = t % (P + 1);
     const int k = e == 0 ? (P + 1) * s : e == 1 ? P + (P + 1) * s : e == 2 ? s : s + (P + 1) * P;
     const int u0 = 2 * Pm.uslot_of_node[k];
-    const double xb1 = Ex[4 * ROMB_NQ * 3 + 2 * e], xb2 = Ex[4 * ROMB_NQ * 3 + 2 * e + 1];
-    double a = 0.0, m1 = 0.0, m2 = 0.0;
-    for (int qq = 0; qq < ROMB_NQ; ++qq) {
-      const double* ex = Ex + (e * ROMB_NQ + qq) * 3;
-      const double wj = Pm.gq_w[qq] * ex[2] * Pm.bq[qq][s];
-      a += wj;
-      m1 += wj * (ex[1] - xb2);
-      m2 += wj * (xb1 - ex[0]);
-    }
+    const double* ef = efun + ((cell * 4 + e) * (P + 1) + s) * 3;
+    const double a = ef[0], m1 = ef[1], m2 = ef[2];
     const int r = 8 + 3 * e;
     if (s_cmap[r] >= 0) {
       if (s_umap[u0] >= 0) {
@@ -433,7 +503,7 @@ template <int P>
 static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
   const size_t smem = sizeof(double) * FactorDims<P>::total;
   ROMB_CUDA(cudaFuncSetAttribute(factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  factor_kernel<P><<<c->ncells, 256, smem, c->stream>>>(Pm, c->d_K, c->d_ctrl, c->d_ucell_map, c->d_cmap, c->d_ktot,
+  factor_kernel<P><<<c->ncells, 256, smem, c->stream>>>(Pm, c->d_K, c->d_efun, c->d_ucell_map, c->d_cmap, c->d_ktot,
                                                         c->d_LII, c->d_W, c->d_S, c->d_G, c->d_Phi, c->d_Psi,
                                                         c->d_SCl, c->d_D, c->d_flags,
                                                         c->assembled_split ? 1 : 0); ++c->launches;
@@ -444,6 +514,12 @@ static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
 romb_status launch_factor(romb_ctx* c) {
   CellParams Pm;
   fill_cell_params(c, &Pm);
+  {
+    const long long nw = 4LL * c->ncells;
+    edge_functional_kernel<<<(int)((nw + 3) / 4), 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family,
+                                                                       c->d_efun); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
   switch (c->p) {
     case 3: return launch_factor_p<3>(c, Pm);
     case 4: return launch_factor_p<4>(c, Pm);

@@ -169,7 +169,7 @@ __global__ void grad_chain_kernel(CellParams P, const double* __restrict__ ctrl,
     const bool on = (e == 0 && cx == 0) || (e == 1 && cx == nx - 1) || (e == 2 && cy == 0) || (e == 3 && cy == P.ny - 1);
     const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
     if (!on || (t0 == 0.0 && t1 == 0.0)) continue;
-    double lo[3], hi[3];
+    double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
     const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
     for (int iv = 0; iv < nint; ++iv) {
       const double len = hi[iv] - lo[iv];
@@ -207,17 +207,23 @@ __global__ void grad_chain_kernel(CellParams P, const double* __restrict__ ctrl,
 }
 
 // dc/dmu_d = -(1 - rho) sum_t dI_r,t/dmu_d Q[t+1]: one warp per cell, lanes over the grid.
-__global__ void grad_mu_kernel(CellParams P, const double* __restrict__ A, int n_r, int r, const double* nodes_in,
-                               double lo, double hi, const int* __restrict__ list, int count,
-                               const double* __restrict__ mu, const double* __restrict__ Q, double* __restrict__ dmu) {
+struct GradNodes {
+  double nd[4][12];   // the GLL nodes of each threshold's interval of the model's box
+};
+__global__ void grad_mu_kernel(CellParams P, const double* __restrict__ A, int n_r, int r, GradNodes N,
+                               const int* __restrict__ list, int count, const double* __restrict__ mu,
+                               const double* __restrict__ Q, double* __restrict__ dmu) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ci = blockIdx.x * (blockDim.x >> 5) + warp;
   if (ci >= count) return;
   const long long cell = list[ci];
   const int n1 = r + 1;
   double nodes[12], v[4][12], d[4][12];
-  for (int i = 0; i < n1; ++i) nodes[i] = nodes_in[i];
-  for (int k = 0; k < 4; ++k) lagrange1d(r, nodes, mu[4 * cell + k], v[k], d[k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    for (int i = 0; i < n1; ++i) nodes[i] = N.nd[k][i];
+    lagrange1d(r, nodes, mu[4 * cell + k], v[k], d[k]);
+  }
   const double* Qc = Q + cell * 128 + 1;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   const int ng = n1 * n1 * n1 * n1;
@@ -258,6 +264,17 @@ __global__ void grad_gather_kernel(CellParams P, const double* __restrict__ gloc
   }
 }
 
+// The per-threshold GLL nodes of a model's box (as the theta kernel forms them).
+static GradNodes grad_nodes(const RombRom& R) {
+  GradNodes N;
+  memset(&N, 0, sizeof(N));
+  double g1[12];
+  gll_nodes01(R.r, g1);
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i <= R.r; ++i) N.nd[k][i] = R.lo4[k] + (R.hi4[k] - R.lo4[k]) * g1[i];
+  return N;
+}
+
 romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
   CellParams P;
   fill_cell_params(c, &P);
@@ -267,10 +284,9 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
     if ((s = romb_alloc_t(c, &c->d_gQ, (size_t)c->ncells * 128)) != ROMB_OK) return s;
     const int ncp = (c->m + 1) * (c->m + 1);
     if ((s = romb_alloc_t(c, &c->d_gloc, (size_t)c->ncells * ncp * 2)) != ROMB_OK) return s;
-    if ((s = romb_alloc_t(c, &c->d_gnodes, 16)) != ROMB_OK) return s;
   }
   const int npairs = c->nB * (c->nB + 1) / 2;
-  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+  for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
     const int K = R.n_r + 1;
@@ -282,15 +298,10 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
         c->d_chat, c->lane[0].d_u, c->d_gW, c->d_gQ); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
     if (d_dmu) {
-      double nodes[12], g1[12];
-      gll_nodes01(R.r, g1);
-      for (int i = 0; i <= R.r; ++i) nodes[i] = R.lo + (R.hi - R.lo) * g1[i];
-      ROMB_CUDA(cudaMemcpyAsync(c->d_gnodes, nodes, 8 * 12, cudaMemcpyHostToDevice, c->stream));
       grad_mu_kernel<<<(c->famcount[f] + 7) / 8, 256, 0, c->stream>>>(
-          P, R.A, R.n_r, R.r, c->d_gnodes, R.lo, R.hi, c->d_famlist + c->famstart[f], c->famcount[f], c->d_mu,
-          c->d_gQ, d_dmu); ++c->launches;
+          P, R.A, R.n_r, R.r, grad_nodes(R), c->d_famlist + c->famstart[f], c->famcount[f], c->d_mu, c->d_gQ,
+          d_dmu); ++c->launches;
       ROMB_CUDA(cudaGetLastError());
-      ROMB_CUDA(cudaStreamSynchronize(c->stream));   // d_gnodes is reused by the next family
     }
   }
   grad_chain_kernel<<<(c->ncells + 127) / 128, 128, 0, c->stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, c->d_gW,
@@ -304,12 +315,11 @@ romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu) {
 // [cells][144], Q [cells][128], gloc [cells][2 (m+1)^2] and one 16-double
 // node table per family (nodes_dev + 16 f), so that families need no stream
 // synchronisation between them.  Used by the no-allocation gradient.
-romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* nodes_dev, double* d_dctrl,
-                                double* d_dmu) {
+romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* d_dctrl, double* d_dmu) {
   CellParams P;
   fill_cell_params(c, &P);
   const int npairs = c->nB * (c->nB + 1) / 2;
-  for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+  for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
     if (c->famcount[f] == 0) continue;
     const RombRom& R = c->roms[f];
     const int K = R.n_r + 1;
@@ -320,14 +330,8 @@ romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc,
         P, R.U64, R.n_half, K, c->d_famlist + c->famstart[f], c->famcount[f], c->d_pairs, npairs, c->d_theta,
         c->d_chat, c->lane[0].d_u, W, Q); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
-    double nodes[16] = {0.0}, g1[12] = {0.0};
-    gll_nodes01(R.r, g1);
-    for (int i = 0; i <= R.r; ++i) nodes[i] = R.lo + (R.hi - R.lo) * g1[i];
-    double* nd = nodes_dev + 16 * f;
-    // pageable source: the call returns once `nodes` has been staged
-    ROMB_CUDA(cudaMemcpyAsync(nd, nodes, sizeof(nodes), cudaMemcpyHostToDevice, c->stream));
     grad_mu_kernel<<<(c->famcount[f] + 7) / 8, 256, 0, c->stream>>>(
-        P, R.A, R.n_r, R.r, nd, R.lo, R.hi, c->d_famlist + c->famstart[f], c->famcount[f], c->d_mu, Q, d_dmu);
+        P, R.A, R.n_r, R.r, grad_nodes(R), c->d_famlist + c->famstart[f], c->famcount[f], c->d_mu, Q, d_dmu);
     ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }

@@ -55,7 +55,6 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
   size_t used = 0;
   const size_t oW = take(used, cells * 144), oQ = take(used, cells * 128), oL = take(used, cells * 2 * ncp);
   const size_t oM = take(used, 4 * cells), oR = take(used, cells), oX = take(used, 2 * nctrl);
-  const size_t oN = take(used, 16 * ROMB_MAX_FAMILIES);
   if (used > ROMB_NOALLOC_SCRATCH_BYTES) return ROMB_E_SCRATCH;
   ROMB_CUDA(cudaSetDevice(c->device));
   unsigned char* base = nullptr;
@@ -67,7 +66,6 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
   double* dmu = reinterpret_cast<double*>(base + oM);
   double* dR = reinterpret_cast<double*>(base + oR);
   double* dX = reinterpret_cast<double*>(base + oX);
-  double* nodes = reinterpret_cast<double*>(base + oN);
   // nothing left by an earlier call (of any context on this device) is read
   ROMB_CUDA(cudaMemsetAsync(base, 0, used, c->stream));
   // c = f^T u on the skeleton, into the context's reduction slots
@@ -76,7 +74,7 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
   const bool dev = c->mem == ROMB_MEM_DEVICE;
   double* x_out = dev ? dc_dctrl : dX;
   double* mu_out = (dev && dc_dmu) ? dc_dmu : dmu;
-  if ((s = launch_grad_scratch(c, W, Q, gloc, nodes, x_out, mu_out)) != ROMB_OK) return s;
+  if ((s = launch_grad_scratch(c, W, Q, gloc, x_out, mu_out)) != ROMB_OK) return s;
   if (dc_dR) {
     sum4_kernel<<<c->sms, 256, 0, c->stream>>>(mu_out, c->ncells, dev ? dc_dR : dR); ++c->launches;
     ROMB_CUDA(cudaGetLastError());

@@ -288,7 +288,7 @@ __global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, cons
     const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
     const long long cell = cx + (long long)nx * cy;
     const int k = e == 0 ? (p + 1) * s : e == 1 ? p + (p + 1) * s : e == 2 ? s : s + (p + 1) * p;
-    double lo[3], hi[3];
+    double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
     const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
     double acc = 0.0;
     for (int iv = 0; iv < nint; ++iv) {
@@ -323,22 +323,22 @@ struct ForceRomDev {
   const double* U;    // [r_f][n_f]
   const double* At;   // [(r+1)^4][r_f]
   int rf, nf, r;
-  double nodes[12];   // the GLL nodes of the threshold box, degree r
+  double lo4[4], hi4[4];   // the model's (cluster's) box per threshold
+  double g01[12];     // degree-r GLL nodes of [0, 1]
 };
-struct ForceRomSet {
-  ForceRomDev f[ROMB_MAX_FAMILIES];
-  double qnodes[8];   // GLL nodes of degree q on [0, 1]
+struct QNodes {
+  double n[8];        // GLL nodes of degree q on [0, 1]
 };
 #define LR_WARPS 4
-__global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, ForceRomSet FS,
+__global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, QNodes QN,
+                                                                   const ForceRomDev* __restrict__ tab,
+                                                                   const int32_t* __restrict__ slot,
                                                                    const double* __restrict__ ctrl,
                                                                    const double* __restrict__ mu,
-                                                                   const int32_t* __restrict__ family,
                                                                    const double* __restrict__ trac,
                                                                    double* __restrict__ fU) {
-  // the family descriptors and edge nodes are copied to shared memory with
-  // static indices once per block; the warps then index them by family
-  __shared__ ForceRomDev sF[ROMB_MAX_FAMILIES];
+  // the edge nodes are copied to shared memory with static indices; the
+  // model descriptors are read from the table in global memory by slot
   __shared__ double sq[8];
   __shared__ double wts[LR_WARPS][4][12];
   __shared__ double th[LR_WARPS][128];
@@ -346,9 +346,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
   __shared__ double jk[LR_WARPS][8];
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) sF[f] = FS.f[f];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sq[k] = FS.qnodes[k];
+    for (int k = 0; k < 8; ++k) sq[k] = QN.n[k];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -367,9 +365,13 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
   const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
   const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
   const long long cell = cx + (long long)nx * cy;
-  const ForceRomDev& F = sF[family[cell]];
+  const ForceRomDev& F = tab[slot[cell]];
   const int r = F.r, n1 = r + 1, rf = F.rf;
-  if (lane < 4) lagrange1d(r, F.nodes, mu[4 * cell + lane], wts[warp][lane], nullptr);
+  if (lane < 4) {
+    double nodes[12];
+    for (int i = 0; i < n1; ++i) nodes[i] = F.lo4[lane] + (F.hi4[lane] - F.lo4[lane]) * F.g01[i];
+    lagrange1d(r, nodes, mu[4 * cell + lane], wts[warp][lane], nullptr);
+  }
   __syncwarp();
   // theta_f = A_f w(mu), the grid node g = g1 + n1 (g2 + n1 (g3 + n1 g4))
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -706,30 +708,42 @@ romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* tr, bool tr_on_devi
                             L.stream));
   ROMB_CUDA(cudaMemsetAsync(L.d_fU, 0, 8 * (size_t)c->ncells * c->nU, L.stream));
   if (c->load_form == ROMB_LOADS_REDUCED) {
-    ForceRomSet FS;
-    memset(&FS, 0, sizeof(FS));
-    gll_nodes01(c->q, FS.qnodes);
-    for (int f = 0; f < ROMB_MAX_FAMILIES; ++f) {
+    QNodes QN;
+    memset(&QN, 0, sizeof(QN));
+    gll_nodes01(c->q, QN.n);
+    std::vector<ForceRomDev> tab(ROMB_MAX_MODELS);
+    memset(tab.data(), 0, sizeof(ForceRomDev) * tab.size());
+    for (int f = 0; f < ROMB_MAX_MODELS; ++f) {
       if (c->famcount[f] == 0) continue;
       const RombRom& R = c->roms[f];
       if (!R.force_U) {
         romb_set_error("reduced loads: the reduced model of a family in use has no force model");
         return ROMB_E_STATE;
       }
-      ForceRomDev& D = FS.f[f];
+      ForceRomDev& D = tab[f];
       D.U = R.force_U;
       D.At = R.force_At;
       D.rf = R.force_rf;
       D.nf = R.force_nf;
       D.r = R.r;
-      double g1[12];
-      gll_nodes01(R.r, g1);
-      for (int i = 0; i <= R.r; ++i) D.nodes[i] = R.lo + (R.hi - R.lo) * g1[i];
+      for (int d = 0; d < 4; ++d) {
+        D.lo4[d] = R.lo4[d];
+        D.hi4[d] = R.hi4[d];
+      }
+      gll_nodes01(R.r, D.g01);
       if (D.rf > 128) return ROMB_E_ARG;
     }
+    if (!L.d_forcetab) {
+      romb_status s = romb_alloc_t(c, &L.d_forcetab, sizeof(ForceRomDev) * ROMB_MAX_MODELS);
+      if (s != ROMB_OK) return s;
+    }
+    // pageable source: the call returns once the table has been staged
+    ROMB_CUDA(cudaMemcpyAsync(L.d_forcetab, tab.data(), sizeof(ForceRomDev) * ROMB_MAX_MODELS,
+                              cudaMemcpyHostToDevice, L.stream));
     const long long nwarps = 2LL * c->ny + 2LL * c->nx;
     loads_rom_kernel<<<(int)((nwarps + LR_WARPS - 1) / LR_WARPS), 32 * LR_WARPS, 0, L.stream>>>(
-        P, FS, c->d_ctrl, c->d_mu, c->d_family, L.d_traction, L.d_fU); ++c->launches;
+        P, QN, reinterpret_cast<const ForceRomDev*>(L.d_forcetab), c->d_slot, c->d_ctrl, c->d_mu, L.d_traction,
+        L.d_fU); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   } else {
     const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);

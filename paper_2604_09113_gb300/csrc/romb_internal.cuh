@@ -12,7 +12,9 @@
 
 #include "../../include/romb.h"
 
-#define ROMB_MAX_FAMILIES 4
+#define ROMB_MAX_FAMILIES 8
+#define ROMB_MAX_MODELS 64   // resident reduced models: one per (family, cluster)
+#define ROMB_MAX_NK 2        // clusters per threshold parameter (n_k^4 models per family)
 #define ROMB_MAX_P 8
 #define ROMB_NSLOT 20      // local coarse slots: 4 corners x 2 + 4 edges x 3
 
@@ -33,11 +35,12 @@
 
 void romb_set_error(const std::string& s);
 
-// One loaded reduced model (Sec. 4.2), resident in HBM.
+// One loaded reduced model (Sec. 4.2) of one family and one cluster (Sec.
+// 4.2.1), resident in HBM.  Its box is [lo4[d], hi4[d]] per threshold.
 struct RombRom {
   bool loaded = false;
-  int family = -1, kind = 0, p = 0, q = 0, r = 0, n_r = 0;
-  double lo = 0, hi = 0;
+  int family = -1, kind = 0, p = 0, q = 0, r = 0, n_r = 0, cluster = 0;
+  double lo4[4] = {0, 0, 0, 0}, hi4[4] = {0, 0, 0, 0};
   long long n_half = 0;        // pairs k1 <= k2 times 4 (q+1)^2 columns
   double* U64 = nullptr;       // [(n_r+1)][n_half]: row 0 = I_Pi, rows 1.. = U_r
   float* Utiles = nullptr;     // tensor-core operand: N-tiles of 144 columns, TF32 hi then lo, canonical layout
@@ -52,6 +55,13 @@ struct RombRom {
   int force_nf = 0, force_rf = 0;
   double* force_U = nullptr;   // [r_f][n_f], n_f = 4 (p+1) (q+1): J[e][s][k]
   double* force_At = nullptr;  // [(r+1)^4][r_f]
+};
+
+// The models of one family: slots [slot0, slot0 + n_k^4), cluster
+// k = k1 + n_k (k2 + n_k (k3 + n_k k4)) on the box [lo, hi]^4 (n_k = 0: none).
+struct RombCtxFamilies {
+  int n_k = 0, slot0 = -1;
+  double lo = 0, hi = 0;
 };
 
 // Nested-dissection coarse solver (a5): symbolic tree built on the host from
@@ -115,6 +125,7 @@ struct PcgLane {
   double* d_coarse = nullptr;      // [2][ncoarse_all] coarse right-hand side and solution
   double* d_u = nullptr;           // nodal output [nodes][2]
   double* d_traction = nullptr;    // [4][2]
+  unsigned char* d_forcetab = nullptr;   // reduced force models by slot (loads_rom_kernel)
   double* nd_ybuf = nullptr;       // coarse-solve update vectors
   double* nd_sbuf = nullptr;       // coarse-solve forward results
   cudaGraphExec_t graph = nullptr; // the captured PCG loop (per factorisation)
@@ -133,7 +144,9 @@ struct romb_ctx {
   std::vector<void*> rom_allocs;   // loaded reduced models
   std::unordered_map<void*, size_t> sizes;
 
-  RombRom roms[ROMB_MAX_FAMILIES];
+  RombRom roms[ROMB_MAX_MODELS];   // by model slot
+  RombCtxFamilies fams[ROMB_MAX_FAMILIES];
+  int nslots = 0;
 
   // lattice
   bool have_lattice = false, assembled = false, factored = false;
@@ -158,10 +171,11 @@ struct romb_ctx {
   double* d_theta = nullptr;    // [cells][kmax]
   float* d_theta_hi = nullptr;  // [cells][kpad] tensor-core operand (hi)
   float* d_theta_lo = nullptr;  // [cells][kpad] (lo)
-  int* d_famlist = nullptr;     // cells grouped by family
+  int32_t* d_slot = nullptr;    // [cells] model slot of each cell (FindCluster of its family)
+  int* d_famlist = nullptr;     // cells grouped by model slot
   int2* d_pairs = nullptr;      // (k1, k2), k1 <= k2, in pair order
-  int famcount[ROMB_MAX_FAMILIES] = {0};
-  int famstart[ROMB_MAX_FAMILIES] = {0};
+  int famcount[ROMB_MAX_MODELS] = {0};   // cells per model slot
+  int famstart[ROMB_MAX_MODELS] = {0};
   double* d_K = nullptr;        // [cells][kpack]
   double* d_kdiag = nullptr;    // [cells][nU] diagonal of K at the skeleton slots
   double* d_ktot = nullptr;     // [skeleton DoFs] sum of the diagonals of sharing cells
@@ -173,6 +187,7 @@ struct romb_ctx {
   double* d_Psi = nullptr;      // [cells][nU][20]
   double* d_SCl = nullptr;      // [cells][20][20]
   double* d_D = nullptr;        // [cells][nU]
+  double* d_efun = nullptr;     // [cells][4][p+1][3] edge functionals (a, m1, m2) of the coarse DoFs
 
   // skeleton
   long long nskel_nodes = 0, nskel = 0;   // nodes / DoFs (Dirichlet ones included, masked)
@@ -200,7 +215,6 @@ struct romb_ctx {
   double* d_gW = nullptr;       // [cells][144] sum_{k1 k2} u u I'
   double* d_gQ = nullptr;       // [cells][128] u^T dK/dtheta_t u
   double* d_gloc = nullptr;     // [cells][(m+1)^2][2] local control-point gradient
-  double* d_gnodes = nullptr;
   double* d_gdmu = nullptr;     // [cells][4]
   double* d_gdctrl = nullptr;   // [ctrl][2]
 
@@ -234,8 +248,7 @@ romb_status coarse_solve_check(romb_ctx* c);   // staging timeouts of the solve 
 romb_status launch_ktot(romb_ctx* c);
 romb_status launch_flag_or(romb_ctx* c, int* d_any);
 romb_status launch_grad(romb_ctx* c, double* d_dctrl, double* d_dmu);
-romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* nodes_dev, double* d_dctrl,
-                                double* d_dmu);
+romb_status launch_grad_scratch(romb_ctx* c, double* W, double* Q, double* gloc, double* d_dctrl, double* d_dmu);
 romb_status romb_dot(romb_ctx* c, const double* a, const double* b, long long n, double* out);
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense);
 // A PCG solve on lane L in two halves: pcg_begin enqueues the loads and

@@ -442,7 +442,7 @@ bool write_force_section(FILE* f, const RombForceModel& m) {
 }
 
 extern "C" romb_status romb_train_snapshot(const romb_train_spec* sp, const double* mu4, double* I_out) {
-  if (!sp || !mu4 || !I_out || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family != 0 && sp->family != 1))
+  if (!sp || !mu4 || !I_out || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family < 0 || sp->family > 5))
     return ROMB_E_ARG;
   Trainer T;
   T.setup(*sp);
@@ -455,7 +455,7 @@ extern "C" romb_status romb_train_snapshot(const romb_train_spec* sp, const doub
 extern "C" romb_status romb_train(const romb_train_spec* sp, const double* samples, int n_s, const char* path) {
   if (!sp || !samples || !path || n_s < 1 || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || sp->r < 1 ||
       sp->r > 10 || sp->n_r < 1 || sp->n_r > 127 || sp->n_r > n_s || !(sp->hi > sp->lo) ||
-      (sp->family != 0 && sp->family != 1) || (sp->basis != 0 && sp->basis != 1))
+      (sp->family < 0 || sp->family > 5) || (sp->basis != 0 && sp->basis != 1))
     return ROMB_E_ARG;
   Trainer T;
   T.setup(*sp);

@@ -410,7 +410,7 @@ struct HostLU {
 };
 
 romb_status check_spec(const romb_train_spec* sp) {
-  if (!sp || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family != 0 && sp->family != 1) ||
+  if (!sp || sp->p < 3 || sp->p > ROMB_MAX_P || sp->q != 2 || (sp->family < 0 || sp->family > 5) ||
       (sp->basis != 0 && sp->basis != 1))
     return ROMB_E_ARG;
   return ROMB_OK;

@@ -59,15 +59,22 @@ def test_constraint_intervals():
     iv = bddc.constraint_intervals(lat, 1, 0, bddc.EDGE_LEFT)
     assert len(iv) == 1 and np.allclose(iv[0], (t0, 1 - t0), atol=1e-14)
     assert np.allclose(bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_RIGHT), iv, atol=0)
-    # crosses of different widths: the union, i.e. the wider bar's part
+    # crosses of different widths: where both are solid, the narrower bar's part
     lat = LI.lattice(2, 1, 4, 1, seed=3, mu_mode="uniform", cross_fraction=1.0, cross_range=(0.1, 0.1))
-    lat.mu[0] = 0.1
-    lat.mu[1] = 0.15
+    lat.mu[0] = 0.15
+    lat.mu[1] = 0.1
     iv = bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_RIGHT)
-    assert len(iv) == 1 and np.allclose(iv[0], (0.35, 0.65), atol=1e-14)
+    assert len(iv) == 1 and np.allclose(iv[0], (0.4, 0.6), atol=1e-14)
+    assert np.allclose(bddc.constraint_intervals(lat, 1, 0, bddc.EDGE_LEFT), iv, atol=0)
     # a boundary edge: the cell's own solid part
-    assert np.allclose(bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_LEFT)[0], (0.4, 0.6), atol=1e-14)
-    # an edge that is void on both sides: the whole edge
+    assert np.allclose(bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_LEFT)[0], (0.35, 0.65), atol=1e-14)
+    # a circle (solid edge) next to a cross: the cross bar's part
+    lat = LI.lattice(2, 1, 4, 1, seed=3, mu_mode="uniform", cross_fraction=0.0)
+    lat.family[1] = 1
+    lat.mu[0] = 0.3
+    lat.mu[1] = 0.12
+    assert np.allclose(bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_RIGHT)[0], (0.38, 0.62), atol=1e-14)
+    # an edge whose solid part vanishes: the whole edge
     lat = LI.quarter_annulus(2, 1, p=4)
     lat.mu[:] = -0.9999999
     assert bddc.constraint_intervals(lat, 0, 0, bddc.EDGE_RIGHT) == [(0.0, 1.0)]

@@ -35,6 +35,20 @@ def test_snapshot_matches_oracle(family, mu, p, kind):
     assert np.abs(I - Io).max() <= 1e-12 * np.abs(Io).max()
 
 
+@pytest.mark.parametrize("family,mu", [(2, [0.5, 0.45, 0.5, 0.45]), (2, [0.85, 0.3, 0.2, 0.6]), (3, [-0.4, 0.5, 0.1, -0.2]),
+                                       (4, [-3.0, -1.0, -2.0, 0.2]), (5, [0.5, -1.2, 1.0, -2.0])])
+def test_tpms_snapshot_matches_oracle(family, mu):
+    # the trainer's TPMS lines (certified root isolation in trim.cuh) against
+    # the oracle's independent quadrature of the same trimmed cell; both
+    # adaptive rules stop at ~1e-15 per panel, and the many panels around the
+    # TPMS critical lines add up to a few 1e-12
+    romb = _lib()
+    mu4 = np.array(mu)
+    I = romb.romb_train_snapshot(family, 0, 4, mu4)
+    Io = assembly.fa_tensor(0, 4, 2, quadrature.trimmed_rule(family, mu4))
+    assert np.abs(I - Io).max() <= 5e-12 * np.abs(Io).max()
+
+
 def test_trained_model_properties(tmp_path):
     romb = _lib()
     p, lo, hi = 3, 0.2, 0.36
