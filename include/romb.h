@@ -95,15 +95,22 @@ romb_status romb_create(romb_ctx** ctx, int device, size_t mem_budget_bytes, voi
 void romb_destroy(romb_ctx* ctx);
 const char* romb_strerror(romb_status s);
 
-/* Load one trained reduced model (Sec. 4.2, offline phase of Sec. 4.4) and keep
- * it resident in HBM.  File format: 128-byte header "ROMBDDC1", int32 version
- * (1 or 2), family, basis, p, q, r, n_r, n_k=1, float64 lo, hi, int64 n_i; then
- * float64 I_Pi[n_i], U_r[n_r][n_i], A[n_r][(r+1)^4] (I_r at the tensor GLL nodes
- * of [lo,hi]^4, node g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64
- * magic[n_r]; version 2 adds the reduced model of the force integrals
- * J[e][s][k] (edge e, edge node s, edge interpolation node k; see
- * romb_set_load_form): int64 n_f = 4 (p+1)(q+1), r_f, float64 U_f[r_f][n_f],
- * A_f[r_f][(r+1)^4], int64 magic_f[r_f].  The trainers write version 2.
+/* Load the trained reduced models of one family (Sec. 4.2, offline phase of
+ * Sec. 4.4) and keep them resident in HBM.  File format: 128-byte header
+ * "ROMBDDC1", int32 version (1 or 2), family, basis, p, q, r, n_r, n_k (1 or
+ * 2), float64 lo, hi, int64 n_i; then float64 I_Pi[n_i]; then, for each of the
+ * n_k^4 clusters of the box [lo,hi]^4 in cluster order (Sec. 4.2.1, see
+ * romb_train_gpu_clustered): float64 U_r[n_r][n_i], A[n_r][(r+1)^4] (I_r at
+ * the tensor GLL nodes of the cluster's box, node
+ * g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64 magic[n_r]; version 2
+ * adds to each cluster the reduced model of the force integrals J[e][s][k]
+ * (edge e, edge node s, edge interpolation node k; see romb_set_load_form):
+ * int64 n_f = 4 (p+1)(q+1), r_f, float64 U_f[r_f][n_f], A_f[r_f][(r+1)^4],
+ * int64 magic_f[r_f].  The trainers write version 2.  At most 64 models are
+ * resident (a family reloaded with another n_k takes new slots); a file that
+ * fails to load leaves its family without models.  Assembly finds each
+ * cell's cluster from its thresholds (FindCluster of Algorithm 5; an interior
+ * subinterval boundary belongs to the upper cluster).
  * The fast-assembly vector is I[((k1*nB+k2)*nL+k3)*4 + 2*j1 + j2] (Eq. MDEIM I).
  * *family_out receives the file's family id.  Errors: ROMB_E_FORMAT. */
 romb_status romb_train_load(romb_ctx* ctx, const char* rom_path, int* family_out);
@@ -270,6 +277,17 @@ romb_status romb_train(const romb_train_spec* spec, const double* samples, int n
  * memory.  Errors: ROMB_E_ARG, ROMB_E_NAN, ROMB_E_CUDA. */
 romb_status romb_train_gpu(int device, const romb_train_spec* spec, const double* samples, int n_s,
                            const char* rom_path);
+
+/* Clustered training (Sec. 4.2.1): the box [lo, hi]^4 is split into n_k
+ * equal subintervals per threshold (n_k = 1 or 2), cluster
+ * k = k1 + n_k (k2 + n_k (k3 + n_k k4)) with k_d the subinterval of mu_d, and
+ * each cluster is trained as romb_train_gpu trains one box, on its own
+ * samples and its own (r+1)^4 GLL grid.  samples: [n_k^4][n_s][4] host array,
+ * block k drawn in cluster k's box.  One file with n_k in its header and the
+ * clusters' sections in cluster order (format above).  Errors as
+ * romb_train_gpu. */
+romb_status romb_train_gpu_clustered(int device, const romb_train_spec* spec, int n_k, const double* samples,
+                                     int n_s, const char* rom_path);
 
 /* Snapshots I(mu_k) (Eq. MDEIM I) of n threshold points mu [n][4] (host) by
  * the GPU trainer's quadrature: I_out [n][n_i] host array. */

@@ -258,6 +258,18 @@ def lhs(n_s: int, lo: float, hi: float, seed: int, dim: int = 4) -> np.ndarray:
     return lo + (hi - lo) * out
 
 
+def cluster_samples(n_s: int, lo: float, hi: float, n_k: int, seed: int) -> np.ndarray:
+    """[n_k^4, n_s, 4]: a Latin hypercube of n_s points in each of the n_k^4
+    equal sub-boxes of [lo, hi]^4, sub-box k = k1 + n_k (k2 + n_k (k3 + n_k k4))
+    spanning [lo + k_d h, lo + (k_d + 1) h] in parameter d, h = (hi - lo) / n_k."""
+    h = (hi - lo) / n_k
+    out = np.empty((n_k ** 4, n_s, 4))
+    for k in range(n_k ** 4):
+        kd = np.array([(k // n_k ** d) % n_k for d in range(4)])
+        out[k] = lhs(n_s, lo + h * kd, lo + h * (kd + 1), seed=seed + k)
+    return out
+
+
 def uniform_box(n: int, lo: float, hi: float, seed: int, dim: int = 4) -> np.ndarray:
     """n independent uniform points in [lo, hi]^dim (held-out test samples)."""
     return _rng(seed, STREAM_SAMPLE).uniform(lo, hi, size=(n, dim))

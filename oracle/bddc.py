@@ -12,11 +12,13 @@ Coarse DoFs (Sec. 3.3.1): two per non-Dirichlet cross point (the displacement
 components) and three per non-Dirichlet cell edge: the integrals of u_1 and
 u_2 over the edge of the trimmed domain (the solid part of the physical edge)
 and the moment int f.u over the same part with f = (x2 - xbar2, xbar1 - x1),
-xbar = F(parametric midpoint of the edge).  Both cells of an edge must use
-one functional, so the solid part is the union of what either cell sees as
-solid there (the two agree when the trimmed compatibility condition holds);
-where that union is shorter than 1e-3 of the edge parameter the whole edge
-is used (three functionals over a vanishing part become dependent).
+xbar = F(parametric midpoint of the edge).  An edge of the internal
+skeleton of Omega is where the material of both cells meets, so both cells
+integrate over the part that both see as solid (the intersection; the two
+parts agree when the trimmed compatibility condition holds), a lattice
+boundary edge over the cell's own solid part; where that part is shorter
+than 1e-3 of the edge parameter the whole edge is used (three functionals
+over a vanishing part become dependent).
 Global coarse numbering: vertex (vx, vy) first, then horizontal edges
 (cx, vy), then vertical edges (vx, cy); Dirichlet ones are skipped.
 Local coarse slots of a cell: 2v + c for corner v (bl, br, tl, tr), then
@@ -160,29 +162,29 @@ class Lattice:
 EDGE_MIN_SOLID = 1e-3
 
 
-def _merge(ivs):
+def _intersect(a, b):
     out = []
-    for u, v in sorted(ivs):
-        if out and u <= out[-1][1]:
-            out[-1] = (out[-1][0], max(out[-1][1], v))
-        else:
-            out.append((u, v))
-    return out
+    for u1, v1 in a:
+        for u2, v2 in b:
+            u, v = max(u1, u2), min(v1, v2)
+            if v > u:
+                out.append((u, v))
+    return sorted(out)
 
 
 def constraint_intervals(lat, cx: int, cy: int, e: int):
     """The part of edge e of cell (cx, cy), in its edge parameter, over which
-    the edge's coarse functionals integrate: the union of the solid parts
-    seen by the cell and by its neighbour across the edge (the whole edge if
-    that union is shorter than EDGE_MIN_SOLID)."""
+    the edge's coarse functionals integrate: the intersection of the solid
+    parts seen by the cell and by its neighbour across the edge, the cell's
+    own solid part on the lattice boundary (the whole edge if that part is
+    shorter than EDGE_MIN_SOLID)."""
     c = cx + lat.nx * cy
     ivs = list(quadrature.edge_solid_intervals(int(lat.family[c]), lat.mu[c], e))
     nb = {EDGE_LEFT: (cx - 1, cy, EDGE_RIGHT), EDGE_RIGHT: (cx + 1, cy, EDGE_LEFT),
           EDGE_BOTTOM: (cx, cy - 1, EDGE_TOP), EDGE_TOP: (cx, cy + 1, EDGE_BOTTOM)}[e]
     if 0 <= nb[0] < lat.nx and 0 <= nb[1] < lat.ny:
         n = nb[0] + lat.nx * nb[1]
-        ivs += list(quadrature.edge_solid_intervals(int(lat.family[n]), lat.mu[n], nb[2]))
-    ivs = _merge(ivs)
+        ivs = _intersect(ivs, list(quadrature.edge_solid_intervals(int(lat.family[n]), lat.mu[n], nb[2])))
     if sum(v - u for u, v in ivs) < EDGE_MIN_SOLID:
         return [(0.0, 1.0)]
     return ivs

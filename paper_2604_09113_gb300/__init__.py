@@ -70,6 +70,7 @@ def _load():
         "romb_train_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
         "romb_train_snapshots_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, P], I),
         "romb_set_load_form": ([P, I], I),
+        "romb_train_gpu_clustered": ([I, ctypes.POINTER(RombTrainSpec), I, P, I, ctypes.c_char_p], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +268,18 @@ def romb_train_gpu(family: int, basis: int, p: int, r: int, n_r: int, lo: float,
     spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi)
     _check(_lib.romb_train_gpu(device, ctypes.byref(spec), smp.ctypes.data, len(smp), path.encode()),
            "romb_train_gpu")
+
+
+def romb_train_gpu_clustered(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi: float, n_k: int,
+                             samples, path: str, q: int = 2, device: int = 0) -> None:
+    """Clustered offline training on the GPU (Sec. 4.2.1): samples [n_k^4, n_s, 4],
+    block k in cluster k's box (see include/romb.h)."""
+    smp = np.ascontiguousarray(samples, dtype=np.float64)
+    if smp.ndim != 3 or smp.shape[0] != n_k ** 4 or smp.shape[2] != 4:
+        raise ValueError("samples must be [n_k^4, n_s, 4]")
+    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi)
+    _check(_lib.romb_train_gpu_clustered(device, ctypes.byref(spec), n_k, smp.ctypes.data, smp.shape[1],
+                                         path.encode()), "romb_train_gpu_clustered")
 
 
 def romb_train_snapshots_gpu(family: int, basis: int, p: int, mus, q: int = 2, device: int = 0) -> np.ndarray:

@@ -71,11 +71,23 @@ __host__ __device__ inline void cell_basis1d(const CellParams& P, double t, doub
   else bernstein1d(P.p, t, v, d);
 }
 
-// Equispaced map nodes a/m.
+// The order-m Lagrange basis on the equispaced map nodes a/m, values and
+// derivatives at t (the arithmetic of lagrange1d with the nodes formed in
+// place, no local node table).
 __host__ __device__ inline void map_basis1d(int m, double t, double* v, double* d) {
-  double nodes[5];
-  for (int a = 0; a <= m; ++a) nodes[a] = (double)a / m;
-  lagrange1d(m, nodes, t, v, d);
+  for (int i = 0; i <= m; ++i) {
+    const double ni = (double)i / m;
+    double den = 1.0, val = 1.0, der = 0.0;
+    for (int j = 0; j <= m; ++j) {
+      if (j == i) continue;
+      const double nj = (double)j / m;
+      den *= ni - nj;
+      der = der * (t - nj) + val;
+      val *= t - nj;
+    }
+    v[i] = val / den;
+    if (d) d[i] = der / den;
+  }
 }
 
 // Map control point (a, b) of cell (cx, cy) from the shared grid.

@@ -175,12 +175,18 @@ __global__ void grad_chain_kernel(CellParams P, const double* __restrict__ ctrl,
       const double len = hi[iv] - lo[iv];
       for (int qq = 0; qq < ROMB_NQ; ++qq) {
         const double t = lo[iv] + len * P.gq_x[qq];
-        const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : t;
-        const double x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : t;
-        double xx[2], J[2][2];
-        map_eval(ctrl, nx, m, cx, cy, x1, x2, xx, J);
-        const int dc = e < 2 ? 1 : 0;
-        const double jj = hypot(J[0][dc], J[1][dc]);
+        // the edge tangent dx/dt: on the edge one factor of the tensor map basis
+        // is a Kronecker delta, so only the edge's m+1 control points vary
+        double vs[5], ds[5];
+        map_basis1d(m, t, vs, ds);
+        double tg[2] = {0.0, 0.0};
+        for (int s2 = 0; s2 <= m; ++s2) {
+          const int ea = e == 0 ? 0 : e == 1 ? m : s2, eb = e == 2 ? 0 : e == 3 ? m : s2;
+          const double* X = ctrl_pt(ctrl, nx, m, cx, cy, ea, eb);
+          tg[0] = fma(ds[s2], X[0], tg[0]);
+          tg[1] = fma(ds[s2], X[1], tg[1]);
+        }
+        const double jj = hypot(tg[0], tg[1]);
         double bv[ROMB_MAX_P + 1];
         cell_basis1d(P, t, bv, nullptr);
         // u . (b t) along the edge
@@ -191,16 +197,12 @@ __global__ void grad_chain_kernel(CellParams P, const double* __restrict__ ctrl,
           const long long node = (long long)(p * cy + bb) * gnx + (p * cx + a);
           ub += bv[s] * (unodal[2 * node] * t0 + unodal[2 * node + 1] * t1);
         }
-        double v1[5], d1[5], v2[5], d2[5];
-        map_basis1d(m, x1, v1, d1);
-        map_basis1d(m, x2, v2, d2);
         const double wq = len * P.gq_w[qq];
-        for (int b = 0; b <= m; ++b)
-          for (int a = 0; a <= m; ++a) {
-            const double dNt = dc == 1 ? v1[a] * d2[b] : d1[a] * v2[b];   // d N / dt along the edge
-            for (int comp = 0; comp < 2; ++comp)
-              out[2 * (b * (m + 1) + a) + comp] += 2.0 * wq * ub * J[comp][dc] * dNt / jj;
-          }
+        for (int s2 = 0; s2 <= m; ++s2) {   // d N / dt along the edge: ds for the edge's control points
+          const int ea = e == 0 ? 0 : e == 1 ? m : s2, eb = e == 2 ? 0 : e == 3 ? m : s2;
+          for (int comp = 0; comp < 2; ++comp)
+            out[2 * (eb * (m + 1) + ea) + comp] += 2.0 * wq * ub * tg[comp] * ds[s2] / jj;
+        }
       }
     }
   }

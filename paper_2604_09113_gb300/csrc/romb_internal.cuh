@@ -270,6 +270,9 @@ struct RombForceModel {
   std::vector<long long> magic;   // [r_f]
 };
 romb_status train_force_model(const romb_train_spec* sp, const double* samples, int n_s, RombForceModel* out);
+// The same on the box [lo4[d], hi4[d]] per threshold (one cluster).
+romb_status train_force_model_box(const romb_train_spec* sp, const double* lo4, const double* hi4,
+                                  const double* samples, int n_s, RombForceModel* out);
 bool write_force_section(FILE* f, const RombForceModel& m);
 
 // host-trainer pieces the GPU trainer reuses (train.cu)

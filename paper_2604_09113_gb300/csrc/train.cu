@@ -360,6 +360,12 @@ void train_jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std
 // n_f x n_f matrix S S^T of the J snapshots, those with singular values above
 // 1e-7 of the largest), magic points (Algorithm 3), grid coefficients.
 romb_status train_force_model(const romb_train_spec* sp, const double* samples, int n_s, RombForceModel* out) {
+  const double lo4[4] = {sp->lo, sp->lo, sp->lo, sp->lo}, hi4[4] = {sp->hi, sp->hi, sp->hi, sp->hi};
+  return train_force_model_box(sp, lo4, hi4, samples, n_s, out);
+}
+
+romb_status train_force_model_box(const romb_train_spec* sp, const double* lo4, const double* hi4,
+                                  const double* samples, int n_s, RombForceModel* out) {
   const int nf = 4 * (sp->p + 1) * (sp->q + 1);
   std::vector<double> S((size_t)n_s * nf);
   for (int si = 0; si < n_s; ++si) edge_load_tensor(*sp, samples + 4 * si, &S[(size_t)si * nf]);
@@ -418,7 +424,7 @@ romb_status train_force_model(const romb_train_spec* sp, const double* samples, 
   for (int g = 0; g < ng; ++g) {
     const int ii[4] = {g % n1, (g / n1) % n1, (g / (n1 * n1)) % n1, g / (n1 * n1 * n1)};
     double mu[4];
-    for (int d = 0; d < 4; ++d) mu[d] = sp->lo + (sp->hi - sp->lo) * g1d[ii[d]];
+    for (int d = 0; d < 4; ++d) mu[d] = lo4[d] + (hi4[d] - lo4[d]) * g1d[ii[d]];
     edge_load_tensor(*sp, mu, J.data());
     for (int a = 0; a < rf; ++a) bb[a] = J[magic[a]];
     lu.solve(bb.data());

@@ -484,17 +484,18 @@ extern "C" romb_status romb_train_snapshots_gpu(int device, const romb_train_spe
   return ROMB_OK;
 }
 
-extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, const double* samples, int n_s,
-                                      const char* path) {
+namespace {
+// One model (one cluster) on the box [lo4[d], hi4[d]]: U_r [n_r][n_i], A
+// [n_r][(r+1)^4], the magic points and the force model, in host arrays.
+struct TgModel {
+  std::vector<double> U, A;
+  std::vector<long long> magic;
+  RombForceModel force;
+};
+romb_status tg_train_box(const romb_train_spec* sp, const TgSetup& T, const double* lo4, const double* hi4,
+                         const double* samples, int n_s, TgModel* out) {
   romb_status s;
-  if ((s = check_spec(sp)) != ROMB_OK) return s;
-  if (!samples || !path || n_s < 1 || sp->r < 1 || sp->r > 10 || sp->n_r < 1 || sp->n_r > 127 || sp->n_r > n_s ||
-      !(sp->hi > sp->lo))
-    return ROMB_E_ARG;
-  ROMB_CUDA(cudaSetDevice(device));
-  DevBufs buf;
-  TgSetup T;
-  if ((s = T.init(sp, buf)) != ROMB_OK) return s;
+  DevBufs buf;   // this model's device buffers, freed on return
   const long long ni = T.S.n_i;
   const int nm = T.Q.nm, n_r = sp->n_r;
   // snapshots S [n_s][n_i]
@@ -556,7 +557,8 @@ extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, con
   ROMB_CUDA(buf.get(&dc, (size_t)n_r));
   ROMB_CUDA(buf.get(&dcol, (size_t)n_r));
   ROMB_CUDA(buf.get(&dmagic, (size_t)n_r));
-  std::vector<long long> magic(n_r);
+  std::vector<long long>& magic = out->magic;
+  magic.assign(n_r, 0);
   std::vector<double> Um((size_t)n_r * n_r);   // Um[a][b] = U[b][magic[a]]
   std::vector<double> pv(nblk), col(n_r);
   std::vector<long long> pi(nblk);
@@ -595,7 +597,7 @@ extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, con
   for (int g = 0; g < ng; ++g) {
     const int i1 = g % n1, i2 = (g / n1) % n1, i3 = (g / (n1 * n1)) % n1, i4 = g / (n1 * n1 * n1);
     const int ii[4] = {i1, i2, i3, i4};
-    for (int d = 0; d < 4; ++d) gmu[4 * (size_t)g + d] = sp->lo + (sp->hi - sp->lo) * g1d[ii[d]];
+    for (int d = 0; d < 4; ++d) gmu[4 * (size_t)g + d] = lo4[d] + (hi4[d] - lo4[d]) * g1d[ii[d]];
   }
   double *dgmu = nullptr, *dgM = nullptr, *dB = nullptr;
   ROMB_CUDA(buf.get(&dgmu, gmu.size()));
@@ -609,36 +611,81 @@ extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, con
     tg_entries_kernel<<<(int)((tot + 255) / 256), 256>>>(T.S, T.dF, dgM, dmagic, n_r, ng, dB);
     ROMB_CUDA(cudaGetLastError());
   }
-  std::vector<double> Bm((size_t)n_r * ng), U((size_t)n_r * ni);
+  std::vector<double> Bm((size_t)n_r * ng);
+  std::vector<double>& U = out->U;
+  U.resize((size_t)n_r * ni);
   ROMB_CUDA(cudaMemcpy(Bm.data(), dB, 8 * Bm.size(), cudaMemcpyDeviceToHost));
   ROMB_CUDA(cudaMemcpy(U.data(), dU, 8 * U.size(), cudaMemcpyDeviceToHost));
   HostLU lu;
   if (!lu.factor(n_r, Um)) return ROMB_E_NAN;
-  std::vector<double> A((size_t)n_r * ng), b(n_r);
+  std::vector<double>& A = out->A;
+  A.resize((size_t)n_r * ng);
+  std::vector<double> b(n_r);
   for (int g = 0; g < ng; ++g) {
     for (int a = 0; a < n_r; ++a) b[a] = Bm[(size_t)a * ng + g];
     lu.solve(b.data());
     for (int a = 0; a < n_r; ++a) A[(size_t)a * ng + g] = b[a];
   }
-  RombForceModel force;   // J(mu) is small (n_f = 4 (p+1) (q+1)): trained on the host
-  if ((s = train_force_model(sp, samples, n_s, &force)) != ROMB_OK) return s;
-  FILE* f = fopen(path, "wb");
-  if (!f) return ROMB_E_ARG;
+  // J(mu) is small (n_f = 4 (p+1) (q+1)): trained on the host
+  return train_force_model_box(sp, lo4, hi4, samples, n_s, &out->force);
+}
+
+bool tg_write_header(FILE* f, const romb_train_spec* sp, int n_k, long long ni, const std::vector<double>& Ipi) {
   unsigned char hdr[128];
   memset(hdr, 0, sizeof(hdr));
   memcpy(hdr, "ROMBDDC1", 8);
-  const int32_t iv[8] = {2, sp->family, sp->basis, sp->p, sp->q, sp->r, n_r, 1};
+  const int32_t iv[8] = {2, sp->family, sp->basis, sp->p, sp->q, sp->r, sp->n_r, n_k};
   memcpy(hdr + 8, iv, 32);
   const double lohi[2] = {sp->lo, sp->hi};
   memcpy(hdr + 40, lohi, 16);
   const int64_t ni64 = ni;
   memcpy(hdr + 56, &ni64, 8);
   bool ok = fwrite(hdr, 1, 128, f) == 128;
-  ok = ok && fwrite(T.Ipi.data(), 8, (size_t)ni, f) == (size_t)ni;
-  ok = ok && fwrite(U.data(), 8, U.size(), f) == U.size();
-  ok = ok && fwrite(A.data(), 8, A.size(), f) == A.size();
-  ok = ok && fwrite(magic.data(), 8, n_r, f) == (size_t)n_r;
-  ok = ok && write_force_section(f, force);
+  return ok && fwrite(Ipi.data(), 8, (size_t)ni, f) == (size_t)ni;
+}
+
+bool tg_write_model(FILE* f, const TgModel& M) {
+  bool ok = fwrite(M.U.data(), 8, M.U.size(), f) == M.U.size();
+  ok = ok && fwrite(M.A.data(), 8, M.A.size(), f) == M.A.size();
+  ok = ok && fwrite(M.magic.data(), 8, M.magic.size(), f) == M.magic.size();
+  return ok && write_force_section(f, M.force);
+}
+}  // namespace
+
+extern "C" romb_status romb_train_gpu(int device, const romb_train_spec* sp, const double* samples, int n_s,
+                                      const char* path) {
+  return romb_train_gpu_clustered(device, sp, 1, samples, n_s, path);
+}
+
+extern "C" romb_status romb_train_gpu_clustered(int device, const romb_train_spec* sp, int n_k, const double* samples,
+                                                int n_s, const char* path) {
+  romb_status s;
+  if ((s = check_spec(sp)) != ROMB_OK) return s;
+  if (!samples || !path || n_s < 1 || n_k < 1 || n_k > 2 || sp->r < 1 || sp->r > 10 || sp->n_r < 1 ||
+      sp->n_r > 127 || sp->n_r > n_s || !(sp->hi > sp->lo))
+    return ROMB_E_ARG;
+  ROMB_CUDA(cudaSetDevice(device));
+  DevBufs buf;
+  TgSetup T;
+  if ((s = T.init(sp, buf)) != ROMB_OK) return s;
+  FILE* f = fopen(path, "wb");
+  if (!f) return ROMB_E_ARG;
+  bool ok = tg_write_header(f, sp, n_k, T.S.n_i, T.Ipi);
+  const int nK = n_k * n_k * n_k * n_k;
+  const double h = (sp->hi - sp->lo) / n_k;
+  for (int k = 0; k < nK && ok; ++k) {
+    double lo4[4], hi4[4];
+    for (int d = 0, kk = k; d < 4; ++d, kk /= n_k) {
+      lo4[d] = sp->lo + h * (kk % n_k);
+      hi4[d] = sp->lo + h * (kk % n_k + 1);
+    }
+    TgModel M;
+    if ((s = tg_train_box(sp, T, lo4, hi4, samples + 4 * (size_t)n_s * k, n_s, &M)) != ROMB_OK) {
+      fclose(f);
+      return s;
+    }
+    ok = tg_write_model(f, M);
+  }
   fclose(f);
   return ok ? ROMB_OK : ROMB_E_ARG;
 }
