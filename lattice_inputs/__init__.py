@@ -185,7 +185,8 @@ def quarter_annulus(nx: int, ny: int, p: int = 8, m: int = 4, r0: float = 0.6, r
     r = r1 - (r1 - r0) * t
     ctrl = np.stack([r * np.sin(0.5 * math.pi * s), -r * np.cos(0.5 * math.pi * s)], axis=1)
     vx = np.tile(np.arange(nx + 1), ny + 1).astype(np.float64) / nx
-    mu = vertex_values_to_cells(0.9 - 0.8 * vx, nx, ny)
+    # 0.9 - 0.8 s, kept inside [0.1, 0.9] against rounding (0.9 - 0.8 = 0.09999...)
+    mu = vertex_values_to_cells(np.clip(0.9 - 0.8 * vx, 0.1, 0.9), nx, ny)
     tr = np.zeros((4, 2))
     tr[EDGE_RIGHT] = [0.0, -0.1]
     return Lattice(nx=nx, ny=ny, p=p, m=m, basis=0, ctrl=np.ascontiguousarray(ctrl),

@@ -95,6 +95,18 @@ void fill_cell_params(const romb_ctx* c, CellParams* P) {
   P->lam = c->E * c->nu / (1.0 - c->nu * c->nu);
   P->mu = c->E / (2.0 * (1.0 + c->nu));
   gll_nodes01(c->p, P->gll);
+  for (int i = 0; i <= c->p; ++i) {
+    double den = 1.0;
+    for (int j = 0; j <= c->p; ++j)
+      if (j != i) den *= P->gll[i] - P->gll[j];
+    P->bw[i] = 1.0 / den;
+  }
+  for (int i = 0; i <= c->m; ++i) {
+    double den = 1.0;
+    for (int j = 0; j <= c->m; ++j)
+      if (j != i) den *= (double)i / c->m - (double)j / c->m;
+    P->mw[i] = 1.0 / den;
+  }
   gauss01(ROMB_NQ, P->gq_x, P->gq_w);
   for (int i = 0; i < ROMB_NQ; ++i) cell_basis1d(*P, P->gq_x[i], P->bq[i], nullptr);
   for (int i = 0; i <= ROMB_NQ; ++i) map_basis1d(c->m, i < ROMB_NQ ? P->gq_x[i] : 0.5, P->mq[i], P->dmq[i]);

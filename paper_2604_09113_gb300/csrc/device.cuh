@@ -15,6 +15,8 @@ struct CellParams {
   unsigned dmask;
   double E, nu, rho, lam, mu;   // plane-stress Lame parameters
   double gll[ROMB_MAX_P + 1];   // degree-p GLL nodes of the cell basis
+  double bw[ROMB_MAX_P + 1];    // their barycentric weights 1 / prod_{j != i} (gll_i - gll_j)
+  double mw[5];                 // the same for the equispaced map nodes a/m
   double gq_x[ROMB_NQ], gq_w[ROMB_NQ];
   double bq[ROMB_NQ][ROMB_MAX_P + 1];        // cell basis (1D) at the Gauss points
   int uslot[8 * ROMB_MAX_P];

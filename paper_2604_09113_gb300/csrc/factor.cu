@@ -55,6 +55,7 @@ struct FactorDims {
 // ROMB_EDGE_MIN_SOLID; each interval by the ROMB_NQ-point Gauss rule.  One
 // warp per (cell, edge); out[cell][e][s][3].
 #define ROMB_EDGE_MIN_SOLID 1e-3
+template <int PD>
 __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, const double* __restrict__ ctrl,
                                                               const double* __restrict__ mu,
                                                               const int32_t* __restrict__ family,
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
   const int lane = threadIdx.x & 31;
   if (w >= 4LL * P.ncells) return;
   const long long cell = w >> 2;
-  const int e = (int)(w & 3), p = P.p, m = P.m, nx = P.nx, ny = P.ny;
+  const int e = (int)(w & 3), m = P.m, nx = P.nx, ny = P.ny;
   const int cx = (int)(cell % nx), cy = (int)(cell / nx);
   // intervals: where this cell and its neighbour across the edge are both
   // solid (the cell's own solid part on the lattice boundary)
@@ -97,41 +98,75 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
     lo[0] = 0.0;
     hi[0] = 1.0;
   }
-  // the edge's m+1 map control points (a Kronecker delta in the other direction)
+  // the edge's m+1 map control points (a Kronecker delta in the other
+  // direction); the map basis and its derivative in barycentric form with the
+  // weights of the equispaced nodes (P.mw), no division
+  double Xe[5][2];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if (q > m) break;
+    const int a = e == 0 ? 0 : e == 1 ? m : q;
+    const int b = e == 2 ? 0 : e == 3 ? m : q;
+    const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
+    Xe[q][0] = X[0];
+    Xe[q][1] = X[1];
+  }
   auto edge_pt = [&](double t, double* x, double* tg) {
-    double v[5], d[5];
-    map_basis1d(m, t, v, d);
     x[0] = x[1] = tg[0] = tg[1] = 0.0;
-    for (int q = 0; q <= m; ++q) {
-      const int a = e == 0 ? 0 : e == 1 ? m : q;
-      const int b = e == 2 ? 0 : e == 3 ? m : q;
-      const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
-      x[0] = fma(v[q], X[0], x[0]);
-      x[1] = fma(v[q], X[1], x[1]);
-      tg[0] = fma(d[q], X[0], tg[0]);
-      tg[1] = fma(d[q], X[1], tg[1]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (q > m) break;
+      double val = 1.0, der = 0.0;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        if (j > m) break;
+        if (j == q) continue;
+        const double dt = t - (double)j / m;
+        der = der * dt + val;
+        val *= dt;
+      }
+      val *= P.mw[q];
+      der *= P.mw[q];
+      x[0] = fma(val, Xe[q][0], x[0]);
+      x[1] = fma(val, Xe[q][1], x[1]);
+      tg[0] = fma(der, Xe[q][0], tg[0]);
+      tg[1] = fma(der, Xe[q][1], tg[1]);
     }
   };
   double xb[2], tb[2];
   edge_pt(0.5, xb, tb);
-  double acc[3 * (ROMB_MAX_P + 1)];
-  for (int i = 0; i < 3 * (p + 1); ++i) acc[i] = 0.0;
+  double acc[3 * (PD + 1)];
+#pragma unroll
+  for (int i = 0; i < 3 * (PD + 1); ++i) acc[i] = 0.0;
   for (int t = lane; t < nm * ROMB_NQ; t += 32) {
     const int iv = t / ROMB_NQ, qq = t % ROMB_NQ;
     const double L = hi[iv] - lo[iv], tt = lo[iv] + L * P.gq_x[qq];
-    double x[2], tg[2], bv[ROMB_MAX_P + 1];
+    double x[2], tg[2], bv[PD + 1];
     edge_pt(tt, x, tg);
-    cell_basis1d(P, tt, bv, nullptr);
+    if (P.basis == 0) {   // GLL Lagrange: barycentric weights P.bw
+#pragma unroll
+      for (int s_ = 0; s_ <= PD; ++s_) {
+        double val = P.bw[s_];
+#pragma unroll
+        for (int j = 0; j <= PD; ++j)
+          if (j != s_) val *= tt - P.gll[j];
+        bv[s_] = val;
+      }
+    } else {
+      bernstein1d(PD, tt, bv, nullptr);
+    }
     const double wj = L * P.gq_w[qq] * hypot(tg[0], tg[1]);
-    for (int s_ = 0; s_ <= p; ++s_) {
+#pragma unroll
+    for (int s_ = 0; s_ <= PD; ++s_) {
       const double wb = wj * bv[s_];
       acc[3 * s_] += wb;
       acc[3 * s_ + 1] += wb * (x[1] - xb[1]);
       acc[3 * s_ + 2] += wb * (xb[0] - x[0]);
     }
   }
-  double* o = out + (cell * 4 + e) * (p + 1) * 3;
-  for (int i = 0; i < 3 * (p + 1); ++i) {
+  double* o = out + (cell * 4 + e) * (PD + 1) * 3;
+#pragma unroll
+  for (int i = 0; i < 3 * (PD + 1); ++i) {
     const double v = warp_sum(acc[i]);
     if (lane == 0) o[i] = v;
   }
@@ -516,8 +551,11 @@ romb_status launch_factor(romb_ctx* c) {
   fill_cell_params(c, &Pm);
   {
     const long long nw = 4LL * c->ncells;
-    edge_functional_kernel<<<(int)((nw + 3) / 4), 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family,
-                                                                       c->d_efun); ++c->launches;
+    const int nb = (int)((nw + 3) / 4);
+    auto k = c->p == 3 ? edge_functional_kernel<3> : c->p == 4 ? edge_functional_kernel<4>
+             : c->p == 5 ? edge_functional_kernel<5> : c->p == 6 ? edge_functional_kernel<6>
+             : c->p == 7 ? edge_functional_kernel<7> : edge_functional_kernel<8>;
+    k<<<nb, 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family, c->d_efun); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
   switch (c->p) {
