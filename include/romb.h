@@ -222,7 +222,8 @@ romb_status romb_fma_probe(int precision, int blocks, int threads, int iters, vo
 enum { ROMB_LOADS_QUADRATURE = 0, ROMB_LOADS_REDUCED = 1 };
 romb_status romb_set_load_form(romb_ctx* ctx, int form);
 
-/* Phase timings (ms, CUDA events) of the last calls: [0] theta, [1] contraction,
+/* Phase timings (ms, CUDA events) of the last calls: [0] theta, Chat and the
+ * coarse DoFs' edge functionals, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
  * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits
  * (1 out of box, 2 bad map, 4 not SPD, 8 non-finite); either may be NULL. */

@@ -642,7 +642,10 @@ extern "C" romb_status romb_assemble(romb_ctx* c, const romb_lattice* L, romb_pr
   c->assembled_split = prec != ROMB_FP64;
   c->assembled_rom = true;
   cudaEventRecord(c->ev[0], c->stream);
+  c->efun_ready = false;
   if ((s = launch_theta(c)) != ROMB_OK) return s;
+  // the coarse DoFs' edge functionals depend on the geometry only
+  if ((s = launch_edge_functionals(c)) != ROMB_OK) return s;
   cudaEventRecord(c->ev[1], c->stream);
   if (prec == ROMB_FP64) s = launch_assemble_fp64(c);
   else s = launch_assemble_tc(c);
@@ -664,6 +667,7 @@ extern "C" romb_status romb_assemble_host_K(romb_ctx* c, const romb_lattice* L, 
   c->assembled = c->factored = c->solved = false;
   c->assembled_split = false;
   c->assembled_rom = false;
+  c->efun_ready = false;
   // pack the dense matrices on the device (upper triangle, row-major)
   double* dense = nullptr;
   const size_t nd = (size_t)c->ndof;

@@ -546,17 +546,26 @@ static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
   return ROMB_OK;
 }
 
+romb_status launch_edge_functionals(romb_ctx* c) {
+  CellParams Pm;
+  fill_cell_params(c, &Pm);
+  const long long nw = 4LL * c->ncells;
+  const int nb = (int)((nw + 3) / 4);
+  auto k = c->p == 3 ? edge_functional_kernel<3> : c->p == 4 ? edge_functional_kernel<4>
+           : c->p == 5 ? edge_functional_kernel<5> : c->p == 6 ? edge_functional_kernel<6>
+           : c->p == 7 ? edge_functional_kernel<7> : edge_functional_kernel<8>;
+  k<<<nb, 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family, c->d_efun); ++c->launches;
+  ROMB_CUDA(cudaGetLastError());
+  c->efun_ready = true;
+  return ROMB_OK;
+}
+
 romb_status launch_factor(romb_ctx* c) {
   CellParams Pm;
   fill_cell_params(c, &Pm);
-  {
-    const long long nw = 4LL * c->ncells;
-    const int nb = (int)((nw + 3) / 4);
-    auto k = c->p == 3 ? edge_functional_kernel<3> : c->p == 4 ? edge_functional_kernel<4>
-             : c->p == 5 ? edge_functional_kernel<5> : c->p == 6 ? edge_functional_kernel<6>
-             : c->p == 7 ? edge_functional_kernel<7> : edge_functional_kernel<8>;
-    k<<<nb, 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family, c->d_efun); ++c->launches;
-    ROMB_CUDA(cudaGetLastError());
+  if (!c->efun_ready) {   // cell matrices given by the caller: no assembly computed them
+    romb_status s = launch_edge_functionals(c);
+    if (s != ROMB_OK) return s;
   }
   switch (c->p) {
     case 3: return launch_factor_p<3>(c, Pm);

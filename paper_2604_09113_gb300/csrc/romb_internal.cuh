@@ -188,6 +188,7 @@ struct romb_ctx {
   double* d_SCl = nullptr;      // [cells][20][20]
   double* d_D = nullptr;        // [cells][nU]
   double* d_efun = nullptr;     // [cells][4][p+1][3] edge functionals (a, m1, m2) of the coarse DoFs
+  bool efun_ready = false;      // d_efun holds this lattice's functionals
 
   // skeleton
   long long nskel_nodes = 0, nskel = 0;   // nodes / DoFs (Dirichlet ones included, masked)
@@ -236,6 +237,7 @@ void romb_free_all(romb_ctx* c);
 
 // kernel launchers (each returns ROMB_OK or ROMB_E_CUDA)
 romb_status launch_theta(romb_ctx* c);
+romb_status launch_edge_functionals(romb_ctx* c);
 romb_status launch_assemble_fp64(romb_ctx* c);
 romb_status launch_assemble_tc(romb_ctx* c);
 romb_status launch_factor(romb_ctx* c);
