@@ -89,3 +89,51 @@ def test_reduced_force_model():
     for mu in LI.uniform_box(3, lo, hi, seed=7):
         Jex = force_rom.edge_load_tensor(1, mu, 0, 4, 2)
         assert np.abs(force_rom.force_vector(fx, R, mu) - Jex).max() <= 1e-3 * np.abs(Jex).max()
+
+
+@pytest.mark.parametrize("family,mu", [(0, 0.3), (1, 0.13), (2, 0.4)])
+def test_body_loads_total_force_closed_forms(family, mu):
+    # sum_k B_k = 1 (partition of unity), so the total body force on a cell is
+    # b times its physical trimmed area; on an affine map A that is |det A|
+    # times the parametric solid area: 1 - pi R^2 (circle, R < 1/2),
+    # 4 w - 4 w^2 (cross); the Schwarz Diamond's parametric area is the
+    # oracle quadrature's own, pinned in tests/test_oracle_tpms.py
+    Aff = np.array([[1.3, 0.2], [-0.1, 0.9]])
+    P = np.zeros((3, 3, 2))
+    for b in range(3):
+        for a in range(3):
+            P[b, a] = Aff @ np.array([a / 2, b / 2]) + np.array([0.4, -0.2])
+    mu4 = np.full(4, mu)
+    body = np.array([0.7, -1.9])
+    area = {0: 1 - np.pi * mu ** 2, 1: 4 * mu - 4 * mu ** 2}.get(family)
+    if area is None:
+        area = rom.quadrature.trimmed_rule(family, mu4)[2].sum()
+    f = force_rom.cell_body_loads(0, 5, P, family, mu4, body)
+    assert np.allclose([f[0::2].sum(), f[1::2].sum()], abs(np.linalg.det(Aff)) * area * body, rtol=1e-13)
+    # with an affine map det J is constant: the interpolated form is exact
+    V = force_rom.volume_load_tensor(family, mu4, 0, 5, 2)
+    ff = force_rom.cell_body_loads_fast(0, 5, 2, P, V, body)
+    assert np.abs(ff - f).max() <= 1e-13 * np.abs(f).max()
+
+
+def test_body_loads_on_curved_maps_and_condensation():
+    # curved quartic maps: the interpolated det J differs from the exact one by
+    # the interpolation error only; and the BDDC solve of a body-loaded lattice
+    # (interior loads condensed onto the skeleton, Sec. 3.2) equals the direct
+    # solve of the assembled system
+    lat = LI.lattice(3, 2, 4, 4, seed=23, mu_mode="uniform", mu_range=(0.22, 0.34), cross_range=(0.1, 0.16),
+                     cross_fraction=0.5)
+    body = np.array([0.0, -2.0])
+    f = bddc.lattice_loads(lat)
+    for c in range(lat.ncells):
+        P = geometry.cell_control_points(lat.ctrl, lat.nx, lat.m, c % lat.nx, c // lat.nx)
+        fam, mu4 = int(lat.family[c]), lat.mu[c]
+        fb = force_rom.cell_body_loads(0, 4, P, fam, mu4, body)
+        fbf = force_rom.cell_body_loads_fast(0, 4, 2, P, force_rom.volume_load_tensor(fam, mu4, 0, 4, 2), body)
+        assert 0 < np.abs(fbf - fb).max() <= 1e-3 * np.abs(fb).max()
+        f[c] += fb
+    from oracle import pipeline
+    K = pipeline.matrices_full(lat)
+    ref = bddc.direct_solve(lat, K, f)
+    sol = pipeline.solve(lat, K, f, rtol=1e-12)
+    assert np.linalg.norm(sol["u"] - ref) <= 1e-9 * np.linalg.norm(ref)
