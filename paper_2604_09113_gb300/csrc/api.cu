@@ -550,6 +550,7 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_SCl, cells * ROMB_NSLOT * ROMB_NSLOT);
   A_(c->d_D, cells * c->nU);
   A_(c->d_efun, cells * 12LL * (c->p + 1));
+  A_(c->d_eiv, cells * 4LL * (1 + 2 * ROMB_MAX_IV));
   A_(c->d_ucell_map, cells * c->nU);
   A_(c->d_islot, c->nI);
   A_(c->d_uslot, c->nU);

@@ -55,10 +55,27 @@ struct FactorDims {
 // ROMB_EDGE_MIN_SOLID; each interval by the ROMB_NQ-point Gauss rule.  One
 // warp per (cell, edge); out[cell][e][s][3].
 #define ROMB_EDGE_MIN_SOLID 1e-3
+#define ROMB_EIV (1 + 2 * ROMB_MAX_IV)   // per (cell, edge): count, then lo/hi pairs
+
+// The solid intervals of every cell edge (edge_solid_dev), one thread each.
+__global__ void edge_interval_kernel(int ncells, const double* __restrict__ mu, const int32_t* __restrict__ family,
+                                     double* __restrict__ eiv) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 4LL * ncells) return;
+  const long long cell = t >> 2;
+  double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
+  const int n = edge_solid_dev(family[cell], mu + 4 * cell, (int)(t & 3), lo, hi);
+  double* o = eiv + t * ROMB_EIV;
+  o[0] = n;
+  for (int i = 0; i < n; ++i) {
+    o[1 + 2 * i] = lo[i];
+    o[2 + 2 * i] = hi[i];
+  }
+}
+
 template <int PD>
 __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, const double* __restrict__ ctrl,
-                                                              const double* __restrict__ mu,
-                                                              const int32_t* __restrict__ family,
+                                                              const double* __restrict__ eiv,
                                                               double* __restrict__ out) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -69,22 +86,20 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
   // intervals: where this cell and its neighbour across the edge are both
   // solid (the cell's own solid part on the lattice boundary)
   double lo[ROMB_MAX_IV * ROMB_MAX_IV], hi[ROMB_MAX_IV * ROMB_MAX_IV];
-  double ol[ROMB_MAX_IV], oh[ROMB_MAX_IV];
-  int nm = edge_solid_dev(family[cell], mu + 4 * cell, e, ol, oh);
+  const double* own = eiv + (cell * 4 + e) * ROMB_EIV;
+  int nm = (int)own[0];
   for (int i = 0; i < nm; ++i) {
-    lo[i] = ol[i];
-    hi[i] = oh[i];
+    lo[i] = own[1 + 2 * i];
+    hi[i] = own[2 + 2 * i];
   }
   const int ncx = e == 0 ? cx - 1 : e == 1 ? cx + 1 : cx, ncy = e == 2 ? cy - 1 : e == 3 ? cy + 1 : cy;
   if (ncx >= 0 && ncx < nx && ncy >= 0 && ncy < ny) {
-    const long long nb = ncx + (long long)nx * ncy;
-    double bl[ROMB_MAX_IV], bh[ROMB_MAX_IV];
-    const int n2 = edge_solid_dev(family[nb], mu + 4 * nb, e ^ 1, bl, bh);
-    const int n1 = nm;
+    const double* nbv = eiv + ((ncx + (long long)nx * ncy) * 4 + (e ^ 1)) * ROMB_EIV;
+    const int n1 = nm, n2 = (int)nbv[0];
     nm = 0;
     for (int i = 0; i < n1; ++i)    // both lists are sorted and disjoint: so is the result
       for (int k = 0; k < n2; ++k) {
-        const double u = fmax(ol[i], bl[k]), v = fmin(oh[i], bh[k]);
+        const double u = fmax(own[1 + 2 * i], nbv[1 + 2 * k]), v = fmin(own[2 + 2 * i], nbv[2 + 2 * k]);
         if (v > u) {
           lo[nm] = u;
           hi[nm++] = v;
@@ -172,8 +187,15 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
   }
 }
 
+// Threads per cell: at p = 8 one cell's working set (167 KB) allows one CTA
+// per SM, which 256 threads leave short of warps to hide the FP64 latency.
 template <int P>
-__global__ void __launch_bounds__(256) factor_kernel(CellParams Pm, const double* __restrict__ Kp,
+struct FactorThreads {
+  static constexpr int value = P >= 8 ? 512 : 256;
+};
+
+template <int P>
+__global__ void __launch_bounds__(FactorThreads<P>::value) factor_kernel(CellParams Pm, const double* __restrict__ Kp,
                                                       const double* __restrict__ efun, const int* __restrict__ umap,
                                                       const int* __restrict__ cmap, const double* __restrict__ ktot,
                                                       double* __restrict__ LII_out, double* __restrict__ W_out,
@@ -538,7 +560,7 @@ template <int P>
 static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
   const size_t smem = sizeof(double) * FactorDims<P>::total;
   ROMB_CUDA(cudaFuncSetAttribute(factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  factor_kernel<P><<<c->ncells, 256, smem, c->stream>>>(Pm, c->d_K, c->d_efun, c->d_ucell_map, c->d_cmap, c->d_ktot,
+  factor_kernel<P><<<c->ncells, FactorThreads<P>::value, smem, c->stream>>>(Pm, c->d_K, c->d_efun, c->d_ucell_map, c->d_cmap, c->d_ktot,
                                                         c->d_LII, c->d_W, c->d_S, c->d_G, c->d_Phi, c->d_Psi,
                                                         c->d_SCl, c->d_D, c->d_flags,
                                                         c->assembled_split ? 1 : 0); ++c->launches;
@@ -554,7 +576,9 @@ romb_status launch_edge_functionals(romb_ctx* c) {
   auto k = c->p == 3 ? edge_functional_kernel<3> : c->p == 4 ? edge_functional_kernel<4>
            : c->p == 5 ? edge_functional_kernel<5> : c->p == 6 ? edge_functional_kernel<6>
            : c->p == 7 ? edge_functional_kernel<7> : edge_functional_kernel<8>;
-  k<<<nb, 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_mu, c->d_family, c->d_efun); ++c->launches;
+  edge_interval_kernel<<<(int)((nw + 255) / 256), 256, 0, c->stream>>>(c->ncells, c->d_mu, c->d_family, c->d_eiv);
+  ++c->launches;
+  k<<<nb, 128, 0, c->stream>>>(Pm, c->d_ctrl, c->d_eiv, c->d_efun); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   c->efun_ready = true;
   return ROMB_OK;

@@ -15,6 +15,7 @@
 #define ROMB_MAX_FAMILIES 8
 #define ROMB_MAX_MODELS 64   // resident reduced models: one per (family, cluster)
 #define ROMB_MAX_NK 2        // clusters per threshold parameter (n_k^4 models per family)
+#define ROMB_MAX_IV 4        // solid intervals of one trimmed line, at most (trim.cuh)
 #define ROMB_MAX_P 8
 #define ROMB_NSLOT 20      // local coarse slots: 4 corners x 2 + 4 edges x 3
 
@@ -189,6 +190,7 @@ struct romb_ctx {
   double* d_D = nullptr;        // [cells][nU]
   double* d_efun = nullptr;     // [cells][4][p+1][3] edge functionals (a, m1, m2) of the coarse DoFs
   bool efun_ready = false;      // d_efun holds this lattice's functionals
+  double* d_eiv = nullptr;      // [cells][4][1 + 2 ROMB_MAX_IV] solid intervals of each cell edge
 
   // skeleton
   long long nskel_nodes = 0, nskel = 0;   // nodes / DoFs (Dirichlet ones included, masked)

@@ -27,7 +27,9 @@ ROMB_HD inline void legendre_antideriv(int n, double y, double* out) {
   for (int b = 1; b <= n; ++b) out[b] = 0.5 * (P[b + 1] - P[b - 1]) / (2 * b + 1);
 }
 
+#ifndef ROMB_MAX_IV
 #define ROMB_MAX_IV 4   // solid intervals of one line, at most
+#endif
 
 // The TPMS level sets of Table GEO tpms (families 2..5: Schwarz Diamond,
 // Schwarz Primitive, Schoen FRD with the sign flipped, Schoen IWP) on the line
@@ -51,8 +53,10 @@ ROMB_HD inline void tpms_line(int family, double x, double* al, double* be, doub
 // equal end signs and min |g| > M2 h^2 / 8 holds no root, one with a sign
 // change and |g'| > M2 h at an end holds exactly one, others are halved down
 // to TPMS_HMIN (there: one root if the end signs differ, none otherwise);
-// roots are bisected to machine precision and pairs closer than TPMS_HMIN
-// cancel (a tangential touch, where rounding makes the sign noisy).
+// each root is found to machine precision by Newton steps kept inside its
+// bracket (a step that leaves the bracket or shrinks it by less than half
+// is replaced by bisection), and pairs closer than TPMS_HMIN cancel (a
+// tangential touch, where rounding makes the sign noisy).
 #define TPMS_HMIN 1e-10
 ROMB_HD inline int tpms_solid_y(int family, double a, double b, double x, double* lo, double* hi) {
   double al, be, ga;
@@ -86,13 +90,21 @@ ROMB_HD inline int tpms_solid_y(int family, double a, double b, double x, double
           if (fabs(dg(u)) > M2 * h || fabs(dg(v)) > M2 * h || h < TPMS_HMIN) {
             double l = u, r = v;
             const bool neg = gu < 0.0;
+            double y = 0.5 * (l + r);
             for (int it = 0; it < 200; ++it) {
-              const double m = 0.5 * (l + r);
-              if (m <= l || m >= r) break;
-              if ((g(m) < 0.0) == neg) l = m;
-              else r = m;
+              const double gy = g(y);
+              if (gy == 0.0) {
+                l = r = y;
+                break;
+              }
+              if ((gy < 0.0) == neg) l = y;
+              else r = y;
+              const double w0 = r - l, d = dg(y);
+              double yn = d != 0.0 ? y - gy / d : 0.5 * (l + r);
+              if (!(yn > l && yn < r) || (it > 0 && fabs(yn - y) > 0.5 * w0)) yn = 0.5 * (l + r);
+              if (yn <= l || yn >= r || yn == y) break;
+              y = yn;
             }
-            const double y = 0.5 * (l + r);
             if (nr > 0 && y - roots[nr - 1] < TPMS_HMIN) --nr;
             else if (nr < 16) roots[nr++] = y;
             continue;
