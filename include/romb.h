@@ -105,8 +105,10 @@ const char* romb_strerror(romb_status s);
  * g = g1 + (r+1)(g2 + (r+1)(g3 + (r+1) g4))), int64 magic[n_r]; version 2
  * adds to each cluster the reduced model of the force integrals J[e][s][k]
  * (edge e, edge node s, edge interpolation node k; see romb_set_load_form):
- * int64 n_f = 4 (p+1)(q+1), r_f, float64 U_f[r_f][n_f], A_f[r_f][(r+1)^4],
- * int64 magic_f[r_f].  The trainers write version 2.  At most 64 models are
+ * int64 n_f = 4 (p+1)(q+1) (tractions) or 4 (p+1)(q+1) + (p+1)^2 (q+1)^2
+ * (tractions, then V[k][k3] for body forces), r_f <= 128, float64
+ * U_f[r_f][n_f], A_f[r_f][(r+1)^4], int64 magic_f[r_f].  The trainers write
+ * version 2.  At most 64 models are
  * resident (a family reloaded with another n_k takes new slots); a file that
  * fails to load leaves its family without models.  Assembly finds each
  * cell's cluster from its thresholds (FindCluster of Algorithm 5; an interior
@@ -222,6 +224,19 @@ romb_status romb_fma_probe(int precision, int blocks, int threads, int iters, vo
 enum { ROMB_LOADS_QUADRATURE = 0, ROMB_LOADS_REDUCED = 1 };
 romb_status romb_set_load_form(romb_ctx* ctx, int form);
 
+/* A constant body force (bx, by) per unit physical area on the solid part of
+ * every cell (the volume term of Eq. SPEED L ext): with b_hat = det J b at the
+ * (q+1)^2 interpolation nodes (Eq. FAST b interpolation) and the reduced
+ * volume integrals V[k][k3] = int over the trimmed cell of B_k L_k3, node k
+ * carries sum_k3 V[k][k3] b_hat(xi_k3).  The interior loads are condensed on
+ * the skeleton and enter the recovery (Sec. 3.2).  Needs ROMB_LOADS_REDUCED
+ * and force models trained with a volume part (romb_train_spec.body; else a
+ * solve returns ROMB_E_STATE before enqueuing any work); (0, 0) switches it
+ * off.  The compliance gradient covers the quadrature traction loads only
+ * and returns ROMB_E_STATE after a solve with body forces or reduced loads.
+ * The setting stays with the context.  Errors: ROMB_E_ARG (non-finite). */
+romb_status romb_set_body_force(romb_ctx* ctx, double bx, double by);
+
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, Chat and the
  * coarse DoFs' edge functionals, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
@@ -264,6 +279,8 @@ typedef struct {
   int n_r;        /* reduced basis size                       */
   int n_threads;
   double lo, hi;  /* parameter box [lo, hi]^4                 */
+  int body;       /* nonzero: the force model also reduces the volume integrals of
+                     body forces (Eq. SPEED L ext, romb_set_body_force)            */
 } romb_train_spec;
 romb_status romb_train(const romb_train_spec* spec, const double* samples, int n_s, const char* rom_path);
 

@@ -33,7 +33,7 @@ class RombError(RuntimeError):
 class RombTrainSpec(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int), ("basis", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
                 ("r", ctypes.c_int), ("n_r", ctypes.c_int), ("n_threads", ctypes.c_int),
-                ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
+                ("lo", ctypes.c_double), ("hi", ctypes.c_double), ("body", ctypes.c_int)]
 
 
 class RombLattice(ctypes.Structure):
@@ -70,6 +70,7 @@ def _load():
         "romb_train_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, ctypes.c_char_p], I),
         "romb_train_snapshots_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, P], I),
         "romb_set_load_form": ([P, I], I),
+        "romb_set_body_force": ([P, D, D], I),
         "romb_train_gpu_clustered": ([I, ctypes.POINTER(RombTrainSpec), I, P, I, ctypes.c_char_p], I),
     }
     for name, (args, res) in sig.items():
@@ -175,6 +176,12 @@ def romb_set_load_form(ctx, form: int) -> None:
     _check(_lib.romb_set_load_form(ctx, form), "romb_set_load_form")
 
 
+def romb_set_body_force(ctx, bx: float, by: float) -> None:
+    """A constant body force per unit area (needs ROMB_LOADS_REDUCED and force
+    models with a volume part; (0, 0) switches it off)."""
+    _check(_lib.romb_set_body_force(ctx, bx, by), "romb_set_body_force")
+
+
 def romb_stats(ctx, ncells: int | None = None):
     ms = np.zeros(8)
     flags = np.zeros(ncells, dtype=np.int32) if ncells else None
@@ -254,30 +261,31 @@ class Context:
 
 
 def romb_train(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi: float, samples, path: str,
-               q: int = 2, n_threads: int = 0) -> None:
-    """Offline training on the host CPU (see include/romb.h)."""
+               q: int = 2, n_threads: int = 0, body: bool = False) -> None:
+    """Offline training on the host CPU (see include/romb.h); body: the force
+    model also reduces the body-force volume integrals."""
     smp = np.ascontiguousarray(samples, dtype=np.float64)
-    spec = RombTrainSpec(family, basis, p, q, r, n_r, n_threads, lo, hi)
+    spec = RombTrainSpec(family, basis, p, q, r, n_r, n_threads, lo, hi, int(body))
     _check(_lib.romb_train(ctypes.byref(spec), smp.ctypes.data, len(smp), path.encode()), "romb_train")
 
 
 def romb_train_gpu(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi: float, samples, path: str,
-                   q: int = 2, device: int = 0) -> None:
+                   q: int = 2, device: int = 0, body: bool = False) -> None:
     """Offline training on the GPU (see include/romb.h); same model file format."""
     smp = np.ascontiguousarray(samples, dtype=np.float64)
-    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi)
+    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi, int(body))
     _check(_lib.romb_train_gpu(device, ctypes.byref(spec), smp.ctypes.data, len(smp), path.encode()),
            "romb_train_gpu")
 
 
 def romb_train_gpu_clustered(family: int, basis: int, p: int, r: int, n_r: int, lo: float, hi: float, n_k: int,
-                             samples, path: str, q: int = 2, device: int = 0) -> None:
+                             samples, path: str, q: int = 2, device: int = 0, body: bool = False) -> None:
     """Clustered offline training on the GPU (Sec. 4.2.1): samples [n_k^4, n_s, 4],
     block k in cluster k's box (see include/romb.h)."""
     smp = np.ascontiguousarray(samples, dtype=np.float64)
     if smp.ndim != 3 or smp.shape[0] != n_k ** 4 or smp.shape[2] != 4:
         raise ValueError("samples must be [n_k^4, n_s, 4]")
-    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi)
+    spec = RombTrainSpec(family, basis, p, q, r, n_r, 0, lo, hi, int(body))
     _check(_lib.romb_train_gpu_clustered(device, ctypes.byref(spec), n_k, smp.ctypes.data, smp.shape[1],
                                          path.encode()), "romb_train_gpu_clustered")
 

@@ -1,6 +1,7 @@
 // C-ABI entry points of romb: context, memory, ROM loading, lattice set-up and
 // the orchestration of the online phase (Sec. 4.4): assemble -> factor -> solve.
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -99,6 +100,7 @@ void romb_free_lattice(romb_ctx* c) {
   // lanes keep their streams, events and pinned words; their device buffers
   // went with the lattice
   const int load_form = c->load_form;
+  const double body[2] = {c->body[0], c->body[1]};
   PcgLane lanes[ROMB_MAX_LANES];
   for (int k = 0; k < ROMB_MAX_LANES; ++k) {
     const PcgLane& o = c->lane[k];
@@ -116,6 +118,8 @@ void romb_free_lattice(romb_ctx* c) {
   *c = romb_ctx();
   for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
   c->load_form = load_form;
+  c->body[0] = body[0];
+  c->body[1] = body[1];
   for (int i = 0; i < ROMB_MAX_MODELS; ++i) c->roms[i] = roms[i];
   for (int i = 0; i < ROMB_MAX_FAMILIES; ++i) c->fams[i] = fams[i];
   c->nslots = nslots;
@@ -351,7 +355,9 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
     Uf.clear();
     Af.clear();
     if (ok && version == 2) {
-      ok = rd(f, fhdr, 16) && fhdr[0] == 4LL * (p + 1) * (q + 1) && fhdr[1] >= 1 && fhdr[1] <= fhdr[0];
+      const long long ne = 4LL * (p + 1) * (q + 1), nv = (long long)nB * nL;
+      ok = rd(f, fhdr, 16) && (fhdr[0] == ne || fhdr[0] == ne + nv) && fhdr[1] >= 1 && fhdr[1] <= fhdr[0] &&
+           fhdr[1] <= 128;
       if (ok) {
         Uf.resize((size_t)fhdr[1] * fhdr[0]);
         Af.resize((size_t)fhdr[1] * ngrid);
@@ -493,6 +499,7 @@ static romb_status lane_buffers(romb_ctx* c, PcgLane& L) {
   A_(L.d_q, c->nskel);
   A_(L.d_red, 4096);
   A_(L.d_fU, cells * c->nU);
+  A_(L.d_fI, cells * c->nI);
   A_(L.d_cloc, cells * ROMB_NSLOT);
   A_(L.d_yloc, cells * c->nU);
   A_(L.d_u, 2 * nodes);
@@ -556,7 +563,6 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_uslot, c->nU);
   A_(c->d_cmap, cells * ROMB_NSLOT);
   A_(c->d_red, 4096);
-  A_(c->d_fI, cells * c->nI);
   A_(c->d_pcg_err, 1);
 #undef A_
   ROMB_CUDA(cudaMemsetAsync(c->d_pcg_err, 0, 4, c->stream));
@@ -712,6 +718,17 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
   if (!c || !u_out || nrhs < 1 || !(rtol > 0) || maxit < 1) return ROMB_E_ARG;
   if (!traction_sets && nrhs != 1) return ROMB_E_ARG;
   if (!c->factored) return ROMB_E_STATE;
+  if (c->body[0] != 0.0 || c->body[1] != 0.0) {   // body forces need the volume part of the force models
+    if (c->load_form != ROMB_LOADS_REDUCED) {
+      romb_set_error("body forces: select ROMB_LOADS_REDUCED (romb_set_load_form)");
+      return ROMB_E_STATE;
+    }
+    for (int f = 0; f < ROMB_MAX_MODELS; ++f)
+      if (c->famcount[f] > 0 && c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) + c->nB * c->nL) {
+        romb_set_error("body forces: a reduced model in use has no volume part in its force model");
+        return ROMB_E_STATE;
+      }
+  }
   if (c->load_form == ROMB_LOADS_REDUCED) {   // checked before any work is enqueued
     if (!c->assembled_rom) {
       romb_set_error("reduced loads: the cell matrices were not assembled from the reduced models");
@@ -719,7 +736,9 @@ extern "C" romb_status romb_bddc_solve(romb_ctx* c, int nrhs, const double* trac
     }
     for (int f = 0; f < ROMB_MAX_MODELS; ++f)
       if (c->famcount[f] > 0 &&
-          (!c->roms[f].force_U || c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) || c->roms[f].force_rf > 128)) {
+          (!c->roms[f].force_U || c->roms[f].force_rf > 128 ||
+           (c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) &&
+            c->roms[f].force_nf != 4 * (c->p + 1) * (c->q + 1) + c->nB * c->nL))) {
         romb_set_error("reduced loads: the reduced model of a family in use has no force model of this degree");
         return ROMB_E_STATE;
       }
@@ -801,6 +820,10 @@ extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, dou
                                             double* dc_dmu) {
   if (!c || !compliance || !dc_dctrl) return ROMB_E_ARG;
   if (!c->solved || !c->assembled_rom) return ROMB_E_STATE;
+  if (c->lane[0].body_on || c->load_form != ROMB_LOADS_QUADRATURE) {
+    romb_set_error("compliance gradient: only for the quadrature traction loads without body forces");
+    return ROMB_E_STATE;
+  }
   ROMB_CUDA(cudaSetDevice(c->device));
   romb_status s;
   const long long nctrl = (long long)(c->m * c->nx + 1) * (c->m * c->ny + 1);
@@ -833,6 +856,13 @@ extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, dou
   }
   ROMB_CUDA(cudaStreamSynchronize(c->stream));
   *compliance = c->h_red[2];
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_set_body_force(romb_ctx* c, double bx, double by) {
+  if (!c || !std::isfinite(bx) || !std::isfinite(by)) return ROMB_E_ARG;
+  c->body[0] = bx;
+  c->body[1] = by;
   return ROMB_OK;
 }
 

@@ -426,10 +426,125 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
   }
 }
 
+// Body-force loads through the reduced model of the external-force
+// integrals (volume term of Eq. SPEED L ext): per cell, theta_f at the cell's
+// thresholds, V[k][k3] = (U_f theta_f) over the volume rows, b_hat = det J b
+// at the (q+1)^2 interpolation nodes (Eq. FAST b interpolation), and the load
+// of node k, g_k b with g_k = sum_k3 V[k][k3] det J(xi_k3).  Boundary nodes
+// add to the skeleton loads fU; interior nodes write f_I.  One warp per cell.
+#define BL_WARPS 4
+__global__ void __launch_bounds__(32 * BL_WARPS) body_loads_kernel(CellParams P, QNodes QN,
+                                                                    const ForceRomDev* __restrict__ tab,
+                                                                    const int32_t* __restrict__ slot,
+                                                                    const double* __restrict__ ctrl,
+                                                                    const double* __restrict__ mu, double bx,
+                                                                    double by, double* __restrict__ fU,
+                                                                    double* __restrict__ fI) {
+  __shared__ double sq[8];
+  __shared__ double wts[BL_WARPS][4][12];
+  __shared__ double th[BL_WARPS][128];
+  __shared__ double dj[BL_WARPS][64];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sq[k] = QN.n[k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * BL_WARPS + warp;
+  if (cell >= P.ncells) return;
+  const int p = P.p, q = P.q, nx = P.nx, m = P.m, nq = q + 1, nL = nq * nq, nB = (p + 1) * (p + 1);
+  const int cx = (int)(cell % nx), cy = (int)(cell / nx);
+  const ForceRomDev& F = tab[slot[cell]];
+  const int r = F.r, n1 = r + 1, rf = F.rf, ne = 4 * (p + 1) * nq;
+  if (lane < 4) {
+    double nodes[12];
+    for (int i = 0; i < n1; ++i) nodes[i] = F.lo4[lane] + (F.hi4[lane] - F.lo4[lane]) * F.g01[i];
+    lagrange1d(r, nodes, mu[4 * cell + lane], wts[warp][lane], nullptr);
+  }
+  // det J at the interpolation nodes (coordinates read from shared memory)
+  for (int k3 = lane; k3 < nL; k3 += 32) {
+    double x[2], J[2][2];
+    map_eval(ctrl, nx, m, cx, cy, sq[k3 % nq], sq[k3 / nq], x, J);
+    dj[warp][k3] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  }
+  __syncwarp();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int ng = n1 * n1 * n1 * n1;
+  for (int g = 0; g < ng; ++g) {
+    const int g1 = g % n1, g2 = (g / n1) % n1, g3 = (g / (n1 * n1)) % n1, g4 = g / (n1 * n1 * n1);
+    const double w = wts[warp][0][g1] * wts[warp][1][g2] * wts[warp][2][g3] * wts[warp][3][g4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jj = lane + 32 * u;
+      if (jj < rf) acc[u] = fma(w, F.At[(long long)g * rf + jj], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (lane + 32 * u < rf) th[warp][lane + 32 * u] = acc[u];
+  __syncwarp();
+  for (int k = lane; k < nB; k += 32) {
+    double gk = 0.0;
+    for (int k3 = 0; k3 < nL; ++k3) {
+      const long long col = ne + (long long)k * nL + k3;
+      double v = 0.0;
+      for (int t = 0; t < rf; ++t) v = fma(F.U[(long long)t * F.nf + col], th[warp][t], v);
+      gk = fma(v, dj[warp][k3], gk);
+    }
+    const int us = P.uslot_of_node[k];
+    if (us >= 0) {
+      atomicAdd(&fU[cell * P.nU + 2 * us], gk * bx);
+      atomicAdd(&fU[cell * P.nU + 2 * us + 1], gk * by);
+    }
+  }
+  // interior DoFs in islot order
+  for (int i = lane; i < P.nI; i += 32) {
+    const int dof = P.islot[i], k = dof / 2, comp = dof % 2;
+    double gk = 0.0;
+    for (int k3 = 0; k3 < nL; ++k3) {
+      const long long col = ne + (long long)k * nL + k3;
+      double v = 0.0;
+      for (int t = 0; t < rf; ++t) v = fma(F.U[(long long)t * F.nf + col], th[warp][t], v);
+      gk = fma(v, dj[warp][k3], gk);
+    }
+    fI[cell * P.nI + i] = gk * (comp == 0 ? bx : by);
+  }
+}
+
+// Static condensation of the interior loads (Sec. 3.2): y = L^-1 f_I (kept in
+// fI for the recovery) and f_U -= W^T y, W = L^-1 K_IU.  One warp per cell.
+__global__ void condense_kernel(CellParams P, const double* __restrict__ LII, const double* __restrict__ W,
+                                double* __restrict__ fI, double* __restrict__ fU) {
+  __shared__ double sy[4][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * 4 + warp;
+  if (cell >= P.ncells) return;
+  const int NI = P.nI, NU = P.nU;
+  for (int i = lane; i < NI; i += 32) sy[warp][i] = fI[cell * NI + i];
+  __syncwarp();
+  const double* L = LII + cell * (NI * (NI + 1) / 2);
+  // forward substitution L y = f_I, one row at a time, dot over lanes
+  for (int i = 0; i < NI; ++i) {
+    double s = 0.0;
+    for (int k = lane; k < i; k += 32) s += L[(long long)i * (i + 1) / 2 + k] * sy[warp][k];
+    s = warp_sum(s);
+    if (lane == 0) sy[warp][i] = (sy[warp][i] - s) / L[(long long)i * (i + 1) / 2 + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < NI; i += 32) fI[cell * NI + i] = sy[warp][i];
+  const double* Wc = W + cell * NI * NU;
+  for (int u = lane; u < NU; u += 32) {
+    double acc = 0.0;
+    for (int i = 0; i < NI; ++i) acc = fma(Wc[i * NU + u], sy[warp][i], acc);
+    fU[cell * NU + u] -= acc;
+  }
+}
+
 // Interior recovery and nodal output: u_I = -L^-T W u_loc (f_I = 0: no body force),
 // one warp per cell.
 __global__ void recover_kernel(CellParams P, const double* __restrict__ LII, const double* __restrict__ W,
-                               const int* __restrict__ umap, const double* __restrict__ x, double* __restrict__ u) {
+                               const int* __restrict__ umap, const double* __restrict__ x,
+                               const double* __restrict__ yI, double* __restrict__ u) {
   __shared__ double sv[4][64];
   __shared__ double sy[4][128];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -445,7 +560,7 @@ __global__ void recover_kernel(CellParams P, const double* __restrict__ LII, con
   for (int i = lane; i < NI; i += 32) {
     double acc = 0.0;
     for (int t = 0; t < NU; ++t) acc = fma(Wc[i * NU + t], sv[warp][t], acc);
-    sy[warp][i] = -acc;   // L^-1 f_I - W u with f_I = 0
+    sy[warp][i] = (yI ? yI[cell * NI + i] : 0.0) - acc;   // L^-1 f_I - W u (f_I = 0 without body forces)
   }
   __syncwarp();
   const double* L = LII + cell * (NI * (NI + 1) / 2);
@@ -751,6 +866,17 @@ romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* tr, bool tr_on_devi
                                                                    L.d_fU); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
+  L.body_on = c->body[0] != 0.0 || c->body[1] != 0.0;
+  if (L.body_on) {   // the reduced form's table was filled above (the solve checked the form)
+    QNodes QN;
+    memset(&QN, 0, sizeof(QN));
+    gll_nodes01(c->q, QN.n);
+    body_loads_kernel<<<(c->ncells + BL_WARPS - 1) / BL_WARPS, 32 * BL_WARPS, 0, L.stream>>>(
+        P, QN, reinterpret_cast<const ForceRomDev*>(L.d_forcetab), c->d_slot, c->d_ctrl, c->d_mu, c->body[0],
+        c->body[1], L.d_fU, L.d_fI); ++c->launches;
+    condense_kernel<<<(c->ncells + 3) / 4, 128, 0, L.stream>>>(P, c->d_LII, c->d_W, L.d_fI, L.d_fU); ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_fU, c->nskel_nodes, L.d_f); ++c->launches;
   if (romb_status s = dot(c, L, L.d_f, L.d_f, c->nskel, L.d_red + 4); s != ROMB_OK) return s;
   ROMB_CUDA(cudaMemcpyAsync(L.h_red + 1, L.d_red + 4, 8, cudaMemcpyDeviceToHost, L.stream));
@@ -817,7 +943,8 @@ romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit) {
   }
   // recovery + nodal output
   cudaEventRecord(L.ev0, L.stream);
-  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, L.stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, L.d_x, L.d_u);
+  recover_kernel<<<(c->ncells + 3) / 4, 128, 0, L.stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, L.d_x,
+                                                            L.body_on ? L.d_fI : nullptr, L.d_u);
   ++c->launches;
   skel_to_nodes_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, c->nskel_nodes, L.d_x, L.d_u);
   ++c->launches;

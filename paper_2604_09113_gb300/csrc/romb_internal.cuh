@@ -127,6 +127,8 @@ struct PcgLane {
   double* d_u = nullptr;           // nodal output [nodes][2]
   double* d_traction = nullptr;    // [4][2]
   unsigned char* d_forcetab = nullptr;   // reduced force models by slot (loads_rom_kernel)
+  double* d_fI = nullptr;       // [cells][nI] interior body loads, then L^-1 f_I (recovery)
+  bool body_on = false;         // this solve carries body forces
   double* nd_ybuf = nullptr;       // coarse-solve update vectors
   double* nd_sbuf = nullptr;       // coarse-solve forward results
   cudaGraphExec_t graph = nullptr; // the captured PCG loop (per factorisation)
@@ -160,6 +162,7 @@ struct romb_ctx {
   double traction[8] = {0};
   int prec = 0;
   int load_form = 0;            // 0 direct edge quadrature, 1 reduced force model (romb_set_load_form)
+  double body[2] = {0.0, 0.0};  // constant body force per unit area (romb_set_body_force)
 
   double* d_ctrl = nullptr;
   double* d_mu = nullptr;
@@ -207,7 +210,6 @@ struct romb_ctx {
   // reduction scratch of the assembly, the factor checks and the compliance
   double* d_red = nullptr;
   double* h_red = nullptr;      // pinned host copy
-  double* d_fI = nullptr;       // [cells][nI] interior forces
   int* d_pcg_err = nullptr;     // set by a PCG cell kernel whose staging copy timed out
   int ca_grid[3] = {0, 0, 0};   // persistent grid of the cell operator kernels per mode
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)

@@ -34,6 +34,7 @@ struct Trainer {
   double lo, hi;
   int nB, nL, D, n_i, nF;
   std::vector<double> F;    // [nF][D+1] Legendre coefficients of the xi1 factors (= xi2 factors)
+  std::vector<double> Fv;   // [(p+1)(q+1)][D+1] the same for the value products b_a l_c
   std::vector<double> gx, gw;   // outer Gauss rule on [0,1]
 
   void setup(const romb_train_spec& s) {
@@ -78,9 +79,45 @@ struct Trainer {
                 for (int a = 0; a <= D; ++a) F[(size_t)f * (D + 1) + a] += (2 * a + 1) * w[g] * v * P[a];
               }
     }
+    // 1D value products b_a l_c for the body-force volume integrals, index a (q+1) + c
+    Fv.assign((size_t)(p + 1) * (q + 1) * (D + 1), 0.0);
+    for (int g = 0; g < ng; ++g) {
+      double bv[ROMB_MAX_P + 1], bd[ROMB_MAX_P + 1], lv[8], P[64];
+      if (kind == 0) lagrange1d_host(p, gll, x[g], bv, bd);
+      else bernstein1d_host(p, x[g], bv, bd);
+      lagrange1d_host(q, qn, x[g], lv, nullptr);
+      legendre(D, 2.0 * x[g] - 1.0, P);
+      for (int a = 0; a <= p; ++a)
+        for (int cc = 0; cc <= q; ++cc)
+          for (int al = 0; al <= D; ++al)
+            Fv[((size_t)a * (q + 1) + cc) * (D + 1) + al] += (2 * al + 1) * w[g] * bv[a] * lv[cc] * P[al];
+    }
     gx.resize(20);
     gw.resize(20);
     gauss01(20, gx.data(), gw.data());
+  }
+
+  // V[k][k3] = int over the trimmed cell of B_k L_k3 from the moment matrix
+  // (the volume part of the external-force integrals), k = ax + (p+1) ay,
+  // k3 = cx + (q+1) cy
+  void volume_from_moments(const double* M, double* V) const {
+    const int n = D + 1, nv = (p + 1) * (q + 1);
+    std::vector<double> H((size_t)n * nv);   // H[al][g] = sum_be M[al][be] Fv[g][be]
+    for (int al = 0; al < n; ++al)
+      for (int g = 0; g < nv; ++g) {
+        double sum = 0.0;
+        for (int be = 0; be < n; ++be) sum += M[al * n + be] * Fv[(size_t)g * n + be];
+        H[(size_t)al * nv + g] = sum;
+      }
+    for (int ay = 0; ay <= p; ++ay)
+      for (int ax = 0; ax <= p; ++ax)
+        for (int cy = 0; cy <= q; ++cy)
+          for (int cx = 0; cx <= q; ++cx) {
+            const int f = ax * (q + 1) + cx, g = ay * (q + 1) + cy;
+            double sum = 0.0;
+            for (int al = 0; al < n; ++al) sum += Fv[(size_t)f * n + al] * H[(size_t)al * nv + g];
+            V[(size_t)(ax + (p + 1) * ay) * nL + cx + (q + 1) * cy] = sum;
+          }
   }
 
   static void lagrange1d_host(int n, const double* nodes, double t, double* v, double* d) {
@@ -331,6 +368,18 @@ void edge_load_tensor(const romb_train_spec& sp, const double* mu, double* J) {
   }
 }
 
+// J(mu) with the volume part when the spec asks for body forces: the edge
+// integrals, then V[k][k3] = int over the trimmed cell of B_k L_k3 (from the
+// Legendre moments of the trimmed cell, as the stiffness snapshots).
+void external_tensor(const Trainer& T, const romb_train_spec& sp, const double* mu, double* J) {
+  const int ne = 4 * (sp.p + 1) * (sp.q + 1);
+  edge_load_tensor(sp, mu, J);
+  if (!sp.body) return;
+  std::vector<double> M((size_t)(T.D + 1) * (T.D + 1));
+  T.moments(mu, M.data());
+  T.volume_from_moments(M.data(), J + ne);
+}
+
 }  // namespace
 
 // Tables shared with the GPU trainer: the Legendre coefficients F of the 1D
@@ -366,27 +415,65 @@ romb_status train_force_model(const romb_train_spec* sp, const double* samples, 
 
 romb_status train_force_model_box(const romb_train_spec* sp, const double* lo4, const double* hi4,
                                   const double* samples, int n_s, RombForceModel* out) {
-  const int nf = 4 * (sp->p + 1) * (sp->q + 1);
+  const int nf = 4 * (sp->p + 1) * (sp->q + 1) + (sp->body ? (sp->p + 1) * (sp->p + 1) * (sp->q + 1) * (sp->q + 1) : 0);
+  const int nth = sp->n_threads > 0 ? sp->n_threads : std::max(1u, std::thread::hardware_concurrency());
+  Trainer T;
+  T.setup(*sp);
   std::vector<double> S((size_t)n_s * nf);
-  for (int si = 0; si < n_s; ++si) edge_load_tensor(*sp, samples + 4 * si, &S[(size_t)si * nf]);
-  std::vector<double> C((size_t)nf * nf, 0.0), w, V;
-  for (int a = 0; a < nf; ++a)
+  parallel_for(n_s, nth, [&](int si) { external_tensor(T, *sp, samples + 4 * si, &S[(size_t)si * nf]); });
+  // U_f: the leading left singular vectors of the snapshots, from the smaller
+  // of the two Gram matrices (n_f x n_f, or n_s x n_s by the method of
+  // snapshots), those with singular values above 1e-7 of the largest
+  const bool by_snap = n_s < nf;
+  const int ng_ = by_snap ? n_s : nf;
+  std::vector<double> C((size_t)ng_ * ng_, 0.0), w, V;
+  for (int a = 0; a < ng_; ++a)
     for (int b = 0; b <= a; ++b) {
       double sum = 0.0;
-      for (int si = 0; si < n_s; ++si) sum += S[(size_t)si * nf + a] * S[(size_t)si * nf + b];
-      C[(size_t)a * nf + b] = C[(size_t)b * nf + a] = sum;
+      if (by_snap)
+        for (int e = 0; e < nf; ++e) sum += S[(size_t)a * nf + e] * S[(size_t)b * nf + e];
+      else
+        for (int si = 0; si < n_s; ++si) sum += S[(size_t)si * nf + a] * S[(size_t)si * nf + b];
+      C[(size_t)a * ng_ + b] = C[(size_t)b * ng_ + a] = sum;
     }
-  jacobi_eig(nf, C, w, V);
-  std::vector<int> order(nf);
-  for (int i = 0; i < nf; ++i) order[i] = i;
+  jacobi_eig(ng_, C, w, V);
+  std::vector<int> order(ng_);
+  for (int i = 0; i < ng_; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
   int rf = 0;
   const double wmax = w[order[0]];
   if (!(wmax > 0.0)) return ROMB_E_NAN;
   while (rf < nf && rf < n_s && w[order[rf]] > 1e-14 * wmax) ++rf;   // singular values above 1e-7 of the largest
   std::vector<double> U((size_t)rf * nf);
-  for (int k = 0; k < rf; ++k)
-    for (int a = 0; a < nf; ++a) U[(size_t)k * nf + a] = V[(size_t)a * nf + order[k]];
+  if (!by_snap) {
+    for (int k = 0; k < rf; ++k)
+      for (int a = 0; a < nf; ++a) U[(size_t)k * nf + a] = V[(size_t)a * nf + order[k]];
+  } else {
+    // U_k = S^T v_k / sqrt(lambda_k), then two passes of modified Gram-Schmidt
+    for (int k = 0; k < rf; ++k) {
+      const double sc = 1.0 / sqrt(w[order[k]]);
+      for (int e = 0; e < nf; ++e) {
+        double sum = 0.0;
+        for (int si = 0; si < n_s; ++si) sum += S[(size_t)si * nf + e] * V[(size_t)si * ng_ + order[k]];
+        U[(size_t)k * nf + e] = sum * sc;
+      }
+    }
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 0; k < rf; ++k) {
+        double* uk = &U[(size_t)k * nf];
+        for (int j = 0; j < k; ++j) {
+          const double* uj = &U[(size_t)j * nf];
+          double d = 0.0;
+          for (int e = 0; e < nf; ++e) d += uj[e] * uk[e];
+          for (int e = 0; e < nf; ++e) uk[e] -= d * uj[e];
+        }
+        double nrm = 0.0;
+        for (int e = 0; e < nf; ++e) nrm += uk[e] * uk[e];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0)) return ROMB_E_NAN;
+        for (int e = 0; e < nf; ++e) uk[e] /= nrm;
+      }
+  }
   std::vector<long long> magic(rf);
   {
     std::vector<double> res(nf);
@@ -420,16 +507,17 @@ romb_status train_force_model_box(const romb_train_spec* sp, const double* lo4, 
     for (int b = 0; b < rf; ++b) Um[(size_t)a * rf + b] = U[(size_t)b * nf + magic[a]];
   LU lu;
   if (!lu.factor(rf, Um)) return ROMB_E_NAN;
-  std::vector<double> A((size_t)rf * ng), J(nf), bb(rf);
-  for (int g = 0; g < ng; ++g) {
+  std::vector<double> A((size_t)rf * ng);
+  parallel_for(ng, nth, [&](int g) {
     const int ii[4] = {g % n1, (g / n1) % n1, (g / (n1 * n1)) % n1, g / (n1 * n1 * n1)};
     double mu[4];
     for (int d = 0; d < 4; ++d) mu[d] = lo4[d] + (hi4[d] - lo4[d]) * g1d[ii[d]];
-    edge_load_tensor(*sp, mu, J.data());
+    std::vector<double> J(nf), bb(rf);
+    external_tensor(T, *sp, mu, J.data());
     for (int a = 0; a < rf; ++a) bb[a] = J[magic[a]];
     lu.solve(bb.data());
     for (int a = 0; a < rf; ++a) A[(size_t)a * ng + g] = bb[a];
-  }
+  });
   out->n_f = nf;
   out->r_f = rf;
   out->U = std::move(U);

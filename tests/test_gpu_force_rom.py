@@ -116,3 +116,57 @@ def test_load_form_errors(models):
         romb.romb_set_load_form(ctx.h, romb.ROMB_LOADS_QUADRATURE)
         u, its, rel = romb.romb_bddc_solve(ctx.h, nodes, traction_sets=_traction(), rtol=1e-10, maxit=300)
         assert rel[0] <= 1e-10 and np.all(np.isfinite(u))
+
+
+@pytest.fixture(scope="module")
+def body_models(tmp_path_factory):
+    """The same stiffness models with force models that also reduce the
+    body-force volume integrals (volume term of Eq. SPEED L ext)."""
+    d = tmp_path_factory.mktemp("force_rom_body")
+    p, q, r = 4, 2, 2
+    out = {"p": p, "roms": {}, "paths": []}
+    for fam, (lo, hi) in BOXES.items():
+        R, _ = small_rom(fam, p, lo, hi, 20, 12, r, seed=1 + fam)
+        S = LI.lhs(30, lo, hi, seed=50 + fam)
+        R2 = orom.Rom(R.family, R.kind, R.p, R.q, R.r, R.lo, R.hi, R.I_pi, R.U, R.A, R.magic,
+                      force_rom.train_force(fam, 0, p, q, r, lo, hi, S, max_rank=40, body=True))
+        path = os.path.join(str(d), f"f{fam}_body.rom")
+        orom.write(R2, path)
+        out["roms"][fam] = R2
+        out["paths"].append(path)
+    return out
+
+
+def test_body_forces_against_oracle(body_models):
+    # a downward body force plus the tractions: loads formed by the reduced
+    # model, interior loads condensed on the skeleton and restored in the
+    # recovery; the displacement against the oracle's BDDC-PCG solve of the
+    # same loads (1e-8), and the compliance gradient refused
+    p = body_models["p"]
+    lat = _lattice(6, 5, p, 34)
+    tr = _traction()
+    body = np.array([0.3, -1.5])
+    nodes = (p * lat.nx + 1) * (p * lat.ny + 1)
+    with romb.Context(0) as ctx:
+        for path in body_models["paths"]:
+            romb.romb_train_load(ctx.h, path)
+        romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
+        romb.romb_factor(ctx.h)
+        romb.romb_set_body_force(ctx.h, *body)
+        with pytest.raises(romb.RombError) as e:   # body forces need the reduced load form
+            romb.romb_bddc_solve(ctx.h, nodes, traction_sets=tr, rtol=1e-12, maxit=300)
+        assert e.value.status == -10
+        romb.romb_set_load_form(ctx.h, romb.ROMB_LOADS_REDUCED)
+        u, its, _ = romb.romb_bddc_solve(ctx.h, nodes, traction_sets=tr, rtol=1e-12, maxit=300)
+        with pytest.raises(romb.RombError):
+            romb.romb_compliance_grad(ctx.h, len(lat.ctrl), lat.ncells)
+        romb.romb_set_body_force(ctx.h, 0.0, 0.0)
+        u0, _, _ = romb.romb_bddc_solve(ctx.h, nodes, traction_sets=tr, rtol=1e-12, maxit=300)
+    fo = force_rom.lattice_loads_rom(lat, body_models["roms"], tr[0], body)
+    K = pipeline.matrices_rom(lat, body_models["roms"])
+    ref = pipeline.solve(lat, K, fo, rtol=1e-12)
+    err = np.linalg.norm(u[0] - ref["u"]) / np.linalg.norm(ref["u"])
+    assert err < 1e-8, (err, its, ref["iters"])
+    # and without the body force the tractions alone
+    ref0 = pipeline.solve(lat, K, force_rom.lattice_loads_rom(lat, body_models["roms"], tr[0]), rtol=1e-12)
+    assert np.linalg.norm(u0[0] - ref0["u"]) / np.linalg.norm(ref0["u"]) < 1e-8

@@ -102,3 +102,28 @@ def test_trained_force_model(tmp_path):
         e_lib = np.abs(force_rom.force_vector(F, R, mu) - J).max() / np.abs(J).max()
         e_orc = np.abs(force_rom.force_vector(Fo, R, mu) - J).max() / np.abs(J).max()
         assert e_lib < 2 * e_orc + 1e-10, (e_lib, e_orc)
+
+
+def test_trained_force_model_with_body_part(tmp_path):
+    # the trainer's volume integrals V[k][k3] = int B_k L_k3 over the trimmed
+    # cell (from the Legendre moments of the trimmed cell) against the
+    # oracle's direct quadrature, through the trained model at its grid nodes
+    from oracle import force_rom
+    romb = _lib()
+    p, lo, hi = 4, 0.07, 0.21
+    S = LI.lhs(20, lo, hi, seed=19)
+    path = str(tmp_path / "xb.rom")
+    romb.romb_train(1, 0, p, 2, 6, lo, hi, S, path, body=True)
+    R = orom.read(path)
+    F = R.force
+    ne, nv = 4 * (p + 1) * 3, (p + 1) ** 2 * 9
+    assert F.U.shape[0] == ne + nv
+    assert np.abs(F.U.T @ F.U - np.eye(F.U.shape[1])).max() < 1e-12
+    G = orom.grid_points(lo, hi, 2)
+    for g in (3, 50):
+        J = force_rom.external_tensor(1, G[g], 0, p, 2)
+        Jr = force_rom.force_vector(F, R, G[g])
+        assert np.abs(Jr[F.magic] - J[F.magic]).max() <= 1e-11 * np.abs(J).max()
+    for mu in LI.uniform_box(2, lo, hi, seed=20):
+        J = force_rom.external_tensor(1, mu, 0, p, 2)
+        assert np.abs(force_rom.force_vector(F, R, mu) - J).max() <= 1e-3 * np.abs(J).max()
