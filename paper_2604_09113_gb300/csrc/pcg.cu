@@ -267,48 +267,99 @@ __global__ void pcg_shift_scalars(double* sc) {
 }
 
 // Traction loads on the solid part of the loaded lattice edges (Eq. ELA
-// constitutive: that = j t), one thread per (cell, edge node).
-__global__ void loads_kernel(CellParams P, const double* __restrict__ ctrl, const double* __restrict__ mu,
-                             const int32_t* __restrict__ family, const double* __restrict__ trac,
-                             double* __restrict__ fU) {
-  const int p = P.p, nx = P.nx, ny = P.ny;
-  // tasks: for each lattice edge e, its cells, each edge node s
-  const int ncell_e[4] = {ny, ny, nx, nx};
-  long long task = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (int e = 0; e < 4; ++e) {
-    const long long ntask = (long long)ncell_e[e] * (p + 1);
-    if (task >= ntask) {
-      task -= ntask;
-      continue;
-    }
-    const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
-    if (t0 == 0.0 && t1 == 0.0) return;
-    const int j = (int)(task / (p + 1)), s = (int)(task % (p + 1));
-    const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
-    const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
-    const long long cell = cx + (long long)nx * cy;
-    const int k = e == 0 ? (p + 1) * s : e == 1 ? p + (p + 1) * s : e == 2 ? s : s + (p + 1) * p;
-    double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
-    const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
-    double acc = 0.0;
-    for (int iv = 0; iv < nint; ++iv) {
-      const double len = hi[iv] - lo[iv];
-      for (int qq = 0; qq < ROMB_NQ; ++qq) {
-        const double t = lo[iv] + len * P.gq_x[qq];
-        const double x1 = e == 0 ? 0.0 : e == 1 ? 1.0 : t;
-        const double x2 = e == 2 ? 0.0 : e == 3 ? 1.0 : t;
-        double x[2], J[2][2];
-        map_eval(ctrl, nx, P.m, cx, cy, x1, x2, x, J);
-        const int dc = e < 2 ? 1 : 0;
-        double bv[ROMB_MAX_P + 1];
-        cell_basis1d(P, t, bv, nullptr);
-        acc += len * P.gq_w[qq] * hypot(J[0][dc], J[1][dc]) * bv[s];
+// constitutive: that = j t): per (cell, edge), f_s = t int b_s j dt over the
+// edge's solid intervals by the ROMB_NQ-point Gauss rule, lanes over the
+// Gauss points; j from the edge's own m+1 control points (the other factor of
+// the tensor map basis is a Kronecker delta on the edge), b_s in barycentric
+// form.  One warp per (cell, edge).
+#define LQ_WARPS 4
+__global__ void __launch_bounds__(32 * LQ_WARPS) loads_kernel(CellParams P, const double* __restrict__ ctrl,
+                                                               const double* __restrict__ mu,
+                                                               const int32_t* __restrict__ family,
+                                                               const double* __restrict__ trac,
+                                                               double* __restrict__ fU) {
+  const int lane = threadIdx.x & 31;
+  long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int ncell_e[4] = {P.ny, P.ny, P.nx, P.nx};
+  int e = 0;
+  while (e < 4 && t >= ncell_e[e]) {
+    t -= ncell_e[e];
+    ++e;
+  }
+  if (e >= 4) return;
+  const double t0 = trac[2 * e], t1 = trac[2 * e + 1];
+  if (t0 == 0.0 && t1 == 0.0) return;
+  const int p = P.p, nx = P.nx, ny = P.ny, m = P.m;
+  const int j = (int)t;
+  const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
+  const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
+  const long long cell = cx + (long long)nx * cy;
+  double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
+  const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
+  double Xe[5][2];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if (q > m) break;
+    const int a = e == 0 ? 0 : e == 1 ? m : q;
+    const int b = e == 2 ? 0 : e == 3 ? m : q;
+    const double* X = ctrl_pt(ctrl, nx, m, cx, cy, a, b);
+    Xe[q][0] = X[0];
+    Xe[q][1] = X[1];
+  }
+  double acc[ROMB_MAX_P + 1];
+#pragma unroll
+  for (int s_ = 0; s_ <= ROMB_MAX_P; ++s_) acc[s_] = 0.0;
+  for (int k = lane; k < nint * ROMB_NQ; k += 32) {
+    const int iv = k / ROMB_NQ, qq = k % ROMB_NQ;
+    const double len = hi[iv] - lo[iv], tt = lo[iv] + len * P.gq_x[qq];
+    double tg0 = 0.0, tg1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (q > m) break;
+      double val = 1.0, der = 0.0;
+#pragma unroll
+      for (int jn = 0; jn < 5; ++jn) {
+        if (jn > m) break;
+        if (jn == q) continue;
+        const double dt = tt - (double)jn / m;
+        der = der * dt + val;
+        val *= dt;
       }
+      der *= P.mw[q];
+      tg0 = fma(der, Xe[q][0], tg0);
+      tg1 = fma(der, Xe[q][1], tg1);
     }
-    const int u = 2 * P.uslot_of_node[k];
-    atomicAdd(&fU[cell * P.nU + u], acc * t0);
-    atomicAdd(&fU[cell * P.nU + u + 1], acc * t1);
-    return;
+    const double wj = len * P.gq_w[qq] * hypot(tg0, tg1);
+    if (P.basis == 0) {
+#pragma unroll
+      for (int s_ = 0; s_ <= ROMB_MAX_P; ++s_) {
+        if (s_ > p) break;
+        double val = P.bw[s_];
+#pragma unroll
+        for (int jn = 0; jn <= ROMB_MAX_P; ++jn) {
+          if (jn > p) break;
+          if (jn != s_) val *= tt - P.gll[jn];
+        }
+        acc[s_] = fma(wj, val, acc[s_]);
+      }
+    } else {
+      double bv[ROMB_MAX_P + 1];
+      bernstein1d(p, tt, bv, nullptr);
+#pragma unroll
+      for (int s_ = 0; s_ <= ROMB_MAX_P; ++s_)
+        if (s_ <= p) acc[s_] = fma(wj, bv[s_], acc[s_]);
+    }
+  }
+#pragma unroll
+  for (int s_ = 0; s_ <= ROMB_MAX_P; ++s_) {
+    if (s_ > p) break;
+    const double v = warp_sum(acc[s_]);
+    if (lane == 0) {
+      const int k = e == 0 ? (p + 1) * s_ : e == 1 ? p + (p + 1) * s_ : e == 2 ? s_ : s_ + (p + 1) * p;
+      const int u = 2 * P.uslot_of_node[k];
+      atomicAdd(&fU[cell * P.nU + u], v * t0);
+      atomicAdd(&fU[cell * P.nU + u + 1], v * t1);
+    }
   }
 }
 
@@ -861,9 +912,9 @@ romb_status pcg_begin(romb_ctx* c, PcgLane& L, const double* tr, bool tr_on_devi
         L.d_fU); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   } else {
-    const long long ntask = (2LL * c->ny + 2LL * c->nx) * (c->p + 1);
-    loads_kernel<<<(int)((ntask + 127) / 128), 128, 0, L.stream>>>(P, c->d_ctrl, c->d_mu, c->d_family, L.d_traction,
-                                                                   L.d_fU); ++c->launches;
+    const long long nwarps = 2LL * c->ny + 2LL * c->nx;
+    loads_kernel<<<(int)((nwarps + LQ_WARPS - 1) / LQ_WARPS), 32 * LQ_WARPS, 0, L.stream>>>(
+        P, c->d_ctrl, c->d_mu, c->d_family, L.d_traction, L.d_fU); ++c->launches;
     ROMB_CUDA(cudaGetLastError());
   }
   L.body_on = c->body[0] != 0.0 || c->body[1] != 0.0;
