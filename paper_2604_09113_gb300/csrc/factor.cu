@@ -77,12 +77,30 @@ template <int PD>
 __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, const double* __restrict__ ctrl,
                                                               const double* __restrict__ eiv,
                                                               double* __restrict__ out) {
+  // one warp per lattice edge: vertical edges (vx, cy) first, then horizontal
+  // (cx, vy); the edge is computed from one of its cells (edge e) and written
+  // for both (the other sees it as edge e ^ 1, same parameter and nodes)
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= 4LL * P.ncells) return;
-  const long long cell = w >> 2;
-  const int e = (int)(w & 3), m = P.m, nx = P.nx, ny = P.ny;
-  const int cx = (int)(cell % nx), cy = (int)(cell / nx);
+  const int lane = threadIdx.x & 31, m = P.m, nx = P.nx, ny = P.ny;
+  const long long nV = (long long)(nx + 1) * ny, nH = (long long)nx * (ny + 1);
+  if (w >= nV + nH) return;
+  int cx, cy, e;
+  long long cell2 = -1;
+  if (w < nV) {
+    const int vx = (int)(w % (nx + 1));
+    cy = (int)(w / (nx + 1));
+    cx = vx < nx ? vx : nx - 1;
+    e = vx < nx ? 0 : 1;
+    if (vx > 0 && vx < nx) cell2 = (vx - 1) + (long long)nx * cy;
+  } else {
+    const long long wh = w - nV;
+    const int vy = (int)(wh / nx);
+    cx = (int)(wh % nx);
+    cy = vy < ny ? vy : ny - 1;
+    e = vy < ny ? 2 : 3;
+    if (vy > 0 && vy < ny) cell2 = cx + (long long)nx * (vy - 1);
+  }
+  const long long cell = cx + (long long)nx * cy;
   // intervals: where this cell and its neighbour across the edge are both
   // solid (the cell's own solid part on the lattice boundary)
   double lo[ROMB_MAX_IV * ROMB_MAX_IV], hi[ROMB_MAX_IV * ROMB_MAX_IV];
@@ -180,10 +198,14 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
     }
   }
   double* o = out + (cell * 4 + e) * (PD + 1) * 3;
+  double* o2 = cell2 >= 0 ? out + (cell2 * 4 + (e ^ 1)) * (PD + 1) * 3 : nullptr;
 #pragma unroll
   for (int i = 0; i < 3 * (PD + 1); ++i) {
     const double v = warp_sum(acc[i]);
-    if (lane == 0) o[i] = v;
+    if (lane == 0) {
+      o[i] = v;
+      if (o2) o2[i] = v;
+    }
   }
 }
 
@@ -571,8 +593,9 @@ static romb_status launch_factor_p(romb_ctx* c, const CellParams& Pm) {
 romb_status launch_edge_functionals(romb_ctx* c) {
   CellParams Pm;
   fill_cell_params(c, &Pm);
-  const long long nw = 4LL * c->ncells;
-  const int nb = (int)((nw + 3) / 4);
+  const long long nw = 4LL * c->ncells;   // cell edges (interval kernel)
+  const long long ne = (long long)(c->nx + 1) * c->ny + (long long)c->nx * (c->ny + 1);   // lattice edges
+  const int nb = (int)((ne + 3) / 4);
   auto k = c->p == 3 ? edge_functional_kernel<3> : c->p == 4 ? edge_functional_kernel<4>
            : c->p == 5 ? edge_functional_kernel<5> : c->p == 6 ? edge_functional_kernel<6>
            : c->p == 7 ? edge_functional_kernel<7> : edge_functional_kernel<8>;
