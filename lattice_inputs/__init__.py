@@ -23,6 +23,11 @@ Geometry conventions (shared by every consumer):
 * Edges of the lattice boundary are numbered 0 left, 1 right, 2 bottom, 3 top;
   ``dirichlet_mask`` bit e clamps edge e, ``traction[e]`` is the physical
   traction per unit length applied on edge e.
+* Layouts that are not a full rectangle of cells (Sec. 5.2.2, the lattice
+  wrench): ``present[c]`` false removes cell c (its edges next to present
+  cells become free boundary), and ``edge_clamped[c, e]`` true clamps edge e
+  (0 left, 1 right, 2 bottom, 3 top) of cell c, end points included.  Both
+  default to None: every cell present, no clamped cell edge.
 """
 from __future__ import annotations
 
@@ -55,10 +60,19 @@ class Lattice:
     traction: np.ndarray = field(default_factory=lambda: np.array(
         [[0.0, 0.0], [0.0, -1.0], [0.0, 0.0], [0.0, 0.0]]))
     name: str = ""
+    present: np.ndarray | None = None        # [nx*ny] bool, None: every cell
+    edge_clamped: np.ndarray | None = None   # [nx*ny, 4] bool, None: none
 
     @property
     def ncells(self) -> int:
         return self.nx * self.ny
+
+    @property
+    def present_cells(self) -> np.ndarray:
+        """Indices of the present cells, increasing."""
+        if self.present is None:
+            return np.arange(self.nx * self.ny)
+        return np.nonzero(self.present)[0]
 
 
 @dataclass
@@ -195,6 +209,65 @@ def quarter_annulus(nx: int, ny: int, p: int = 8, m: int = 4, r0: float = 0.6, r
                    dirichlet_mask=1 << EDGE_LEFT, traction=tr, name=name or f"quarter-annulus-{nx}x{ny}-p{p}")
 
 
+def wrench(scale: int = 1, p: int = 8, m: int = 2, seed: int = 0, mu_box=(-2.5, 2.5),
+           cell_mm: float = 7.5, name: str = "") -> Lattice:
+    """A wrench-like layout of Schoen IWP cells (Sec. 5.2.2): a round head of
+    8 x 8 cells with a 2 x 2-cell hole in its middle and a handle of 10 x 3
+    cells on its left, 90 cells at scale 1 (every cell split into
+    scale x scale at larger scales: 7,290 cells at scale 9), on an 18 x 8
+    grid of which the other cells are absent.  The edges of the cells around
+    the hole are clamped (the grip on the bolt); a downward traction of
+    1 N/mm acts on the left end of the handle.  E = 5 N/mm, nu = 0.25,
+    rho = 5e-4; each cell draws its four corner thresholds independently
+    and uniformly from mu_box.  The map: the head square is blended half way
+    towards a disc (the elliptical square-to-disc map), the handle follows
+    the head's left side over its last three base cells; a base cell is
+    cell_mm millimetres wide."""
+    s = int(scale)
+    nx, ny = 18 * s, 8 * s
+    cx, cy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    bx, by = (cx // s).ravel(), (cy // s).ravel()          # base cell of every cell
+    head = bx >= 10
+    hole = (bx >= 13) & (bx <= 14) & (by >= 3) & (by <= 4)
+    handle = (bx < 10) & (by >= 2) & (by <= 4)
+    present = (head & ~hole) | handle
+    # clamped edges: edges of present cells that face a hole cell
+    clamped = np.zeros((nx * ny, 4), dtype=bool)
+    holeg = hole.reshape(ny, nx)
+    X, Y = cx.ravel(), cy.ravel()
+    for e, (dx, dy) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+        nxp, nyp = X + dx, Y + dy
+        ok = (nxp >= 0) & (nxp < nx) & (nyp >= 0) & (nyp < ny)
+        face = np.zeros(nx * ny, dtype=bool)
+        face[ok] = holeg[nyp[ok], nxp[ok]]
+        clamped[:, e] = present & face
+    # map, in base-cell units, then millimetres
+    G = reference_grid(nx, ny, m) / s
+    x, y = G[:, 0].copy(), G[:, 1].copy()
+
+    def head_map(x, y):
+        u, v = (x - 14.0) / 4.0, (y - 4.0) / 4.0
+        du = u * np.sqrt(np.maximum(0.0, 1.0 - 0.5 * v * v))
+        dv = v * np.sqrt(np.maximum(0.0, 1.0 - 0.5 * u * u))
+        return 14.0 + 4.0 * (0.5 * u + 0.5 * du), 4.0 + 4.0 * (0.5 * v + 0.5 * dv)
+
+    hx, hy = head_map(x, y)
+    ex, ey = head_map(np.full_like(y, 10.0), y)              # the head's left side at the same y
+    w = np.clip((x - 7.0) / 3.0, 0.0, 1.0)
+    w = w * w * (3.0 - 2.0 * w)
+    px = np.where(x >= 10.0, hx, x + w * (ex - 10.0))
+    py = np.where(x >= 10.0, hy, y + w * (ey - y))
+    ctrl = np.stack([px, py], axis=1) * cell_mm
+    g = _rng(seed, STREAM_MU)
+    mu = g.uniform(mu_box[0], mu_box[1], size=(nx * ny, 4))
+    tr = np.zeros((4, 2))
+    tr[EDGE_LEFT] = [0.0, -1.0]
+    return Lattice(nx=nx, ny=ny, p=p, m=m, basis=0, ctrl=np.ascontiguousarray(ctrl),
+                   mu=np.ascontiguousarray(mu), family=np.full(nx * ny, FAMILY_SCHOEN_IWP, dtype=np.int32),
+                   E=5.0, nu=0.25, rho=5e-4, dirichlet_mask=0, traction=tr,
+                   name=name or f"wrench-{int(present.sum())}-p{p}", present=present, edge_clamped=clamped)
+
+
 def config(k: int) -> Lattice:
     """The five synthetic workloads (seed 1000 + k)."""
     s = 1000 + k
@@ -227,7 +300,9 @@ def tile_lattice(lat: Lattice, x0: int, y0: int, sx: int, sy: int) -> Lattice:
     return Lattice(nx=sx, ny=sy, p=lat.p, m=m, basis=lat.basis, ctrl=np.ascontiguousarray(G.reshape(-1, 2)),
                    mu=lat.mu[cells].copy(), family=lat.family[cells].copy(), E=lat.E, nu=lat.nu, rho=lat.rho,
                    dirichlet_mask=lat.dirichlet_mask, traction=lat.traction.copy(),
-                   name=f"{lat.name}-tile-{x0}-{y0}-{sx}x{sy}")
+                   name=f"{lat.name}-tile-{x0}-{y0}-{sx}x{sy}",
+                   present=None if lat.present is None else lat.present[cells].copy(),
+                   edge_clamped=None if lat.edge_clamped is None else lat.edge_clamped[cells].copy())
 
 
 def sub_lattice(lat: Lattice, sx: int, sy: int) -> Lattice:

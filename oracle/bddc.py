@@ -1,12 +1,17 @@
 """BDDC domain decomposition, one subdomain per cell (Sec. 3, Algorithms 1-2).
 
-Structured ``nx x ny`` lattices.  Global nodes form the grid
+Lattices of ``nx x ny`` cells, some of which may be absent (``present``):
+the subdomains are the present cells, the edges they share are the internal
+skeleton, their other edges are the boundary of Omega (Sec. 5.2.2 uses such
+a layout).  Global nodes form the grid
 (p*nx+1) x (p*ny+1), node n = gx + (p*nx+1) gy; cell (cx, cy) owns nodes
 (p*cx + a, p*cy + b) with local node k = a + (p+1) b and local DoF 2k + i.
 
-DoF classes (Sec. 3.1): Dirichlet (nodes on clamped lattice edges, strong
-u = 0), skeleton (every other DoF of a node on a cell boundary, external
-Neumann edges included) and internal (the 2(p-1)^2 interior DoFs of a cell).
+DoF classes (Sec. 3.1): Dirichlet (nodes of present cells on clamped
+lattice edges or on clamped cell edges, strong u = 0), skeleton (every other
+DoF of a node on the boundary of a present cell, external Neumann edges
+included) and internal (the 2(p-1)^2 interior DoFs of a cell).  Nodes that
+no present cell touches carry no DoF.
 
 Coarse DoFs (Sec. 3.3.1): two per non-Dirichlet cross point (the displacement
 components) and three per non-Dirichlet cell edge: the integrals of u_1 and
@@ -20,7 +25,8 @@ boundary edge over the cell's own solid part; where that part is shorter
 than 1e-3 of the edge parameter the whole edge is used (three functionals
 over a vanishing part become dependent).
 Global coarse numbering: vertex (vx, vy) first, then horizontal edges
-(cx, vy), then vertical edges (vx, cy); Dirichlet ones are skipped.
+(cx, vy), then vertical edges (vx, cy); Dirichlet ones and those of no
+present cell are skipped.
 Local coarse slots of a cell: 2v + c for corner v (bl, br, tl, tr), then
 8 + 3e + t for edge e (left, right, bottom, top), t = average u1, average
 u2, moment.
@@ -70,7 +76,7 @@ def edge_tangent_length(P: np.ndarray, e: int, t):
 
 
 class Lattice:
-    """DoF classification and numbering of a structured lattice (Sec. 3.1)."""
+    """DoF classification and numbering of a lattice layout (Sec. 3.1)."""
 
     def __init__(self, lat):
         self.lat = lat
@@ -79,14 +85,33 @@ class Lattice:
         self.nB = (p + 1) ** 2
         self.ndof = 2 * self.nB
         self.gnx, self.gny = p * nx + 1, p * ny + 1
+        self.present = np.ones(nx * ny, dtype=bool) if getattr(lat, "present", None) is None \
+            else np.asarray(lat.present, dtype=bool)
+        self.cells = np.nonzero(self.present)[0]
+        a, b = np.meshgrid(np.arange(p + 1), np.arange(p + 1), indexing="xy")
+        self.loc_a, self.loc_b = a.ravel(), b.ravel()
+        self.loc_boundary = (self.loc_a % p == 0) | (self.loc_b % p == 0)
+        self.corner_nodes = np.array([0, p, (p + 1) * p, (p + 1) * p + p])
+
         gx, gy = np.meshgrid(np.arange(self.gnx), np.arange(self.gny), indexing="xy")
         gx, gy = gx.ravel(), gy.ravel()
         mask = lat.dirichlet_mask
-        self.dirichlet_node = (((mask >> 0) & 1) & (gx == 0)) | (((mask >> 1) & 1) & (gx == p * nx)) \
+        side = (((mask >> 0) & 1) & (gx == 0)) | (((mask >> 1) & 1) & (gx == p * nx)) \
             | (((mask >> 2) & 1) & (gy == 0)) | (((mask >> 3) & 1) & (gy == p * ny))
-        self.dirichlet_node = self.dirichlet_node.astype(bool)
+        # nodes of present cells, and the nodes of their clamped edges
+        self.touched = np.zeros(self.gnx * self.gny, dtype=bool)
+        clamped_node = np.zeros(self.gnx * self.gny, dtype=bool)
+        ec = getattr(lat, "edge_clamped", None)
+        for c in self.cells:
+            g = self.cell_global_nodes(c % nx, c // nx)
+            self.touched[g] = True
+            if ec is not None:
+                for e in range(4):
+                    if ec[c, e]:
+                        clamped_node[g[edge_local_nodes(p, e)]] = True
+        self.dirichlet_node = (side.astype(bool) | clamped_node) & self.touched
         on_skel = (gx % p == 0) | (gy % p == 0)
-        skel_node = on_skel & ~self.dirichlet_node
+        skel_node = on_skel & self.touched & ~self.dirichlet_node
         # skeleton numbering: increasing (node, component)
         self.skel_of = -np.ones((self.gnx * self.gny, 2), dtype=np.int64)
         ids = np.nonzero(skel_node)[0]
@@ -94,34 +119,27 @@ class Lattice:
         self.skel_of[ids, 1] = 2 * np.arange(len(ids)) + 1
         self.n_U = 2 * len(ids)
 
-        a, b = np.meshgrid(np.arange(p + 1), np.arange(p + 1), indexing="xy")
-        self.loc_a, self.loc_b = a.ravel(), b.ravel()
-        self.loc_boundary = (self.loc_a % p == 0) | (self.loc_b % p == 0)
-        self.corner_nodes = np.array([0, p, (p + 1) * p, (p + 1) * p + p])
-
-        # coarse numbering
+        # coarse numbering: a vertex or edge of a present cell whose nodes are
+        # not clamped (an edge is clamped where its interior nodes are)
+        free = self.touched & ~self.dirichlet_node
         nv = (nx + 1) * (ny + 1)
         vgx = p * (np.arange(nv) % (nx + 1))
         vgy = p * (np.arange(nv) // (nx + 1))
-        v_dir = self.dirichlet_node[vgx + self.gnx * vgy]
+        v_ok = free[vgx + self.gnx * vgy]
         self.coarse_vertex = -np.ones(nv, dtype=np.int64)
-        ok = np.nonzero(~v_dir)[0]
+        ok = np.nonzero(v_ok)[0]
         self.coarse_vertex[ok] = 2 * np.arange(len(ok))
         base = 2 * len(ok)
-        # horizontal edges (cx, vy) and vertical edges (vx, cy); an edge is
-        # Dirichlet when it lies on a clamped lattice edge
         self.coarse_hedge = -np.ones(nx * (ny + 1), dtype=np.int64)
         for vy in range(ny + 1):
-            clamped = (vy == 0 and mask & 4) or (vy == ny and mask & 8)
             for cx in range(nx):
-                if not clamped:
+                if free[p * cx + 1 + self.gnx * (p * vy)]:
                     self.coarse_hedge[cx + nx * vy] = base
                     base += 3
         self.coarse_vedge = -np.ones((nx + 1) * ny, dtype=np.int64)
         for cy in range(ny):
             for vx in range(nx + 1):
-                clamped = (vx == 0 and mask & 1) or (vx == nx and mask & 2)
-                if not clamped:
+                if free[p * vx + self.gnx * (p * cy + 1)]:
                     self.coarse_vedge[vx + (nx + 1) * cy] = base
                     base += 3
         self.n_C = base
@@ -176,14 +194,16 @@ def constraint_intervals(lat, cx: int, cy: int, e: int):
     """The part of edge e of cell (cx, cy), in its edge parameter, over which
     the edge's coarse functionals integrate: the intersection of the solid
     parts seen by the cell and by its neighbour across the edge, the cell's
-    own solid part on the lattice boundary (the whole edge if that part is
-    shorter than EDGE_MIN_SOLID)."""
+    own solid part on the boundary of Omega: the lattice boundary and the
+    edges next to absent cells (the whole edge if that part is shorter than
+    EDGE_MIN_SOLID)."""
     c = cx + lat.nx * cy
     ivs = list(quadrature.edge_solid_intervals(int(lat.family[c]), lat.mu[c], e))
     nb = {EDGE_LEFT: (cx - 1, cy, EDGE_RIGHT), EDGE_RIGHT: (cx + 1, cy, EDGE_LEFT),
           EDGE_BOTTOM: (cx, cy - 1, EDGE_TOP), EDGE_TOP: (cx, cy + 1, EDGE_BOTTOM)}[e]
-    if 0 <= nb[0] < lat.nx and 0 <= nb[1] < lat.ny:
-        n = nb[0] + lat.nx * nb[1]
+    present = getattr(lat, "present", None)
+    n = nb[0] + lat.nx * nb[1]
+    if 0 <= nb[0] < lat.nx and 0 <= nb[1] < lat.ny and (present is None or present[n]):
         ivs = _intersect(ivs, list(quadrature.edge_solid_intervals(int(lat.family[n]), lat.mu[n], nb[2])))
     if sum(v - u for u, v in ivs) < EDGE_MIN_SOLID:
         return [(0.0, 1.0)]
@@ -241,12 +261,16 @@ def cell_loads(kind: int, p: int, P: np.ndarray, family: int, mu4: np.ndarray,
 
 
 def lattice_loads(lat, traction=None) -> np.ndarray:
-    """[ncells, ndof] external forces for tractions on the lattice boundary edges."""
+    """[ncells, ndof] external forces for tractions on the lattice boundary
+    edges (of the present cells; rows of absent cells stay zero)."""
     traction = lat.traction if traction is None else traction
     p, m, nx, ny = lat.p, lat.m, lat.nx, lat.ny
     out = np.zeros((nx * ny, 2 * (p + 1) ** 2))
+    present = getattr(lat, "present", None)
     for cy in range(ny):
         for cx in range(nx):
+            if present is not None and not present[cx + nx * cy]:
+                continue
             edges = [e for e, on in ((EDGE_LEFT, cx == 0), (EDGE_RIGHT, cx == nx - 1),
                                      (EDGE_BOTTOM, cy == 0), (EDGE_TOP, cy == ny - 1)) if on]
             if not edges:
@@ -266,21 +290,20 @@ class Bddc:
         p, nx, ny = lat.p, lat.nx, lat.ny
         self.cells = []
         diagU = np.zeros(L.n_U)
-        for cy in range(ny):
-            for cx in range(nx):
-                c = cx + nx * cy
-                I, U, D, Ug = L.cell_classes(cx, cy)
-                Kc = K[c]
-                K_II, K_IU, K_UU = Kc[np.ix_(I, I)], Kc[np.ix_(I, U)], Kc[np.ix_(U, U)]
-                # Sec. 3.2: local Schur complement and condensed force (u_D = 0)
-                X = np.linalg.solve(K_II, K_IU)
-                S = K_UU - K_IU.T @ X
-                fI, fU = fstar[c][I], fstar[c][U]
-                f = fU - K_IU.T @ np.linalg.solve(K_II, fI)
-                cell = dict(cx=cx, cy=cy, I=I, U=U, Ug=Ug, K_II=K_II, K_IU=K_IU, S=S, f=f,
-                            fI=fI, kdiag=np.diag(Kc)[U])
-                np.add.at(diagU, Ug, cell["kdiag"])
-                self.cells.append(cell)
+        for c in L.cells:
+            cx, cy = int(c % nx), int(c // nx)
+            I, U, D, Ug = L.cell_classes(cx, cy)
+            Kc = K[c]
+            K_II, K_IU, K_UU = Kc[np.ix_(I, I)], Kc[np.ix_(I, U)], Kc[np.ix_(U, U)]
+            # Sec. 3.2: local Schur complement and condensed force (u_D = 0)
+            X = np.linalg.solve(K_II, K_IU)
+            S = K_UU - K_IU.T @ X
+            fI, fU = fstar[c][I], fstar[c][U]
+            f = fU - K_IU.T @ np.linalg.solve(K_II, fI)
+            cell = dict(cx=cx, cy=cy, I=I, U=U, Ug=Ug, K_II=K_II, K_IU=K_IU, S=S, f=f,
+                        fI=fI, kdiag=np.diag(Kc)[U])
+            np.add.at(diagU, Ug, cell["kdiag"])
+            self.cells.append(cell)
         self.f = np.zeros(L.n_U)
         for cell in self.cells:
             np.add.at(self.f, cell["Ug"], cell["f"])
@@ -402,7 +425,8 @@ class Bddc:
 
     def recover(self, u: np.ndarray) -> np.ndarray:
         """Interior DoFs u_I = K_II^-1 (f_I - K_IU u^(i)) and the nodal
-        displacement field [(p nx + 1)(p ny + 1), 2] (Dirichlet nodes are 0)."""
+        displacement field [(p nx + 1)(p ny + 1), 2] (Dirichlet nodes, and
+        nodes of no present cell, are 0)."""
         L = self.L
         out = np.zeros((L.gnx * L.gny, 2))
         for cell in self.cells:
@@ -417,22 +441,21 @@ class Bddc:
 def direct_solve(lat, K: np.ndarray, fstar: np.ndarray) -> np.ndarray:
     """Brute force: assemble the global stiffness over all non-Dirichlet DoFs
     (the system of Eq. BDDC full system before condensation) and solve it
-    directly.  Returns the nodal displacement field."""
+    directly.  Returns the nodal displacement field (zero at the nodes of no
+    present cell)."""
     L = Lattice(lat)
     ndof_g = 2 * L.gnx * L.gny
     rows, cols, vals = [], [], []
     f = np.zeros(ndof_g)
-    for cy in range(lat.ny):
-        for cx in range(lat.nx):
-            c = cx + lat.nx * cy
-            g = L.cell_global_nodes(cx, cy)
-            gd = (2 * g[:, None] + np.arange(2)[None, :]).ravel()
-            rr, cc = np.meshgrid(gd, gd, indexing="ij")
-            rows.append(rr.ravel()); cols.append(cc.ravel()); vals.append(K[c].ravel())
-            np.add.at(f, gd, fstar[c])
+    for c in L.cells:
+        g = L.cell_global_nodes(c % lat.nx, c // lat.nx)
+        gd = (2 * g[:, None] + np.arange(2)[None, :]).ravel()
+        rr, cc = np.meshgrid(gd, gd, indexing="ij")
+        rows.append(rr.ravel()); cols.append(cc.ravel()); vals.append(K[c].ravel())
+        np.add.at(f, gd, fstar[c])
     A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(ndof_g, ndof_g))
-    free = ~np.repeat(L.dirichlet_node, 2)
+    free = np.repeat(L.touched & ~L.dirichlet_node, 2)
     u = np.zeros(ndof_g)
     u[free] = spla.spsolve(A[free][:, free], f[free])
     return u.reshape(-1, 2)

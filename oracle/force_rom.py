@@ -160,16 +160,20 @@ def cell_body_loads(kind: int, p: int, P: np.ndarray, family: int, mu4: np.ndarr
 def lattice_loads_rom(lat, roms: dict, traction=None, body=None) -> np.ndarray:
     """[ncells, ndof] forces of the lattice boundary tractions (and of a
     constant body force ``body`` per unit area, if given) with J from the
-    force models that the reduced models ``roms`` (family -> Rom) carry."""
+    force models that the reduced models ``roms`` (family -> Rom) carry;
+    rows of absent cells stay zero."""
     traction = lat.traction if traction is None else traction
     p, m, nx, ny = lat.p, lat.m, lat.nx, lat.ny
     out = np.zeros((nx * ny, 2 * (p + 1) ** 2))
+    present = getattr(lat, "present", None)
     for cy in range(ny):
         for cx in range(nx):
             edges = [e for e, on in ((0, cx == 0), (1, cx == nx - 1), (2, cy == 0), (3, cy == ny - 1)) if on]
             if not edges and body is None:
                 continue
             c = cx + nx * cy
+            if present is not None and not present[c]:
+                continue
             fam = int(lat.family[c])
             R = romlib.model_for(roms[fam], lat.mu[c])
             P = geometry.cell_control_points(lat.ctrl, nx, m, cx, cy)

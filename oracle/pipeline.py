@@ -6,10 +6,16 @@ import numpy as np
 from . import assembly, bddc, geometry, quadrature, rom as romlib
 
 
+def present_cells(lat) -> np.ndarray:
+    """The subdomains of the layout: every cell, or the present ones."""
+    pr = getattr(lat, "present", None)
+    return np.arange(lat.ncells) if pr is None else np.nonzero(pr)[0]
+
+
 def cell_maps(lat):
-    for cy in range(lat.ny):
-        for cx in range(lat.nx):
-            yield cx + lat.nx * cy, geometry.cell_control_points(lat.ctrl, lat.nx, lat.m, cx, cy)
+    for c in present_cells(lat):
+        cx, cy = int(c % lat.nx), int(c // lat.nx)
+        yield int(c), geometry.cell_control_points(lat.ctrl, lat.nx, lat.m, cx, cy)
 
 
 def matrices_full(lat, cells=None) -> np.ndarray:
@@ -40,7 +46,7 @@ def theta(lat, roms: dict, q: int = 2):
 def fa_tensors(lat, q: int = 2, pmap=map) -> dict:
     """The exact fast-assembly tensors I(mu) of Sec. 4.1 by full trimmed
     quadrature, one per distinct (family, thresholds) of the lattice."""
-    keys = sorted({(int(lat.family[c]),) + tuple(float(v) for v in lat.mu[c]) for c in range(lat.ncells)})
+    keys = sorted({(int(lat.family[c]),) + tuple(float(v) for v in lat.mu[c]) for c in present_cells(lat)})
     out = list(pmap(_fa_job, [(lat.basis, lat.p, q, k) for k in keys]))
     return dict(zip(keys, out))
 
