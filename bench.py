@@ -53,10 +53,11 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5, 6],
+    ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5, 6, 7],
                     help="3: the headline (132 x 132, p = 6); 4: the compliance gradient on 64 x 64 cells; "
                          "5: 256 x 256 cells, p = 8, 16 load sets sharing one factorisation; "
-                         "6: the quarter-annulus Schwarz Diamond benchmark, p = 8, 16 clusters")
+                         "6: the quarter-annulus Schwarz Diamond benchmark, p = 8, 16 clusters; "
+                         "7: the wrench-like layout of Schoen IWP cells, 90 and 7,290 cells, p = 8")
     ap.add_argument("--sub", type=int, default=0,
                     help="profiling only: run the first N x N cells of the workload")
     ap.add_argument("--cpu-sample-json", default=None, help=argparse.SUPPRESS)
@@ -669,6 +670,8 @@ def _setup(a, k: int):
         paths.append(path)
     train_s = time.time() - t0
     lat = LI.config(k)
+    if a.sub:
+        lat = LI.sub_lattice(lat, a.sub, a.sub)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     free0 = torch.cuda.mem_get_info(dev)[0]
@@ -833,6 +836,86 @@ def run_workload6(a):
     print(json.dumps(line))
 
 
+def run_workload7(a):
+    """The lattice-wrench application (Sec. 5.2.2) on a wrench-like layout:
+    a round head with a clamped hole and a handle loaded at its end, cells of
+    an 18 x 8 (x scale) grid of which the others are absent, Schoen IWP cells
+    with thresholds drawn per cell from [-2.5, 2.5]^4, p = 8, E = 5,
+    nu = 0.25, rho = 5e-4; a reduced model with n_k = 2 (16 clusters),
+    n_r = 40, r = 6 and 100 samples per cluster, trained on the GPU.  One
+    step = assembly, factor and solve to 1e-8, at 90 cells (scale 1) and
+    7,290 cells (scale 9), the paper's two wrench lattices (15 and 18
+    iterations there, on its own geometry)."""
+    import numpy as np
+    import torch
+    import lattice_inputs as LI
+    import paper_2604_09113_gb300 as romb
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rom_dir = a.rom_dir or tempfile.mkdtemp(prefix="romb_models_")
+    path = os.path.join(rom_dir, "w7_schoen_iwp_nk2.rom")
+    t0 = time.time()
+    if not os.path.exists(path):
+        romb.romb_train_gpu_clustered(LI.FAMILY_SCHOEN_IWP, 0, 8, 6, 40, -2.5, 2.5, 2,
+                                      LI.cluster_samples(100, -2.5, 2.5, 2, seed=2007), path)
+    train_s = time.time() - t0
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MB > L2
+    forms = {"fp64": romb.ROMB_FP64, "fp32split": romb.ROMB_FP32_SPLIT, "bf16split": romb.ROMB_BF16_SPLIT}
+    form = "fp32split" if a.precision == "auto" else a.precision
+    names = ["theta", "contraction", "local_factor", "coarse_factor", "pcg", "recovery", "copies", "total"]
+    sizes = {}
+    clocks = Clocks(0)
+    clocks.start()
+    for scale, paper_its in ((1, 15), (9, 18)):
+        lat = LI.wrench(scale, p=8)
+        cells = int(lat.present.sum())
+        nodes = (lat.p * lat.nx + 1) * (lat.p * lat.ny + 1)
+        ctx = romb.Context(0, 0, stream.cuda_stream)
+        romb.romb_train_load(ctx.h, path)
+        darr = {"ctrl": torch.from_numpy(lat.ctrl).to(dev), "mu": torch.from_numpy(lat.mu).to(dev),
+                "family": torch.from_numpy(lat.family).to(dev),
+                "traction": torch.from_numpy(lat.traction.reshape(8).copy()).to(dev),
+                "present": torch.from_numpy(lat.present.astype(np.uint8)).to(dev),
+                "edge_clamped": torch.from_numpy(lat.edge_clamped.astype(np.uint8).reshape(-1)).to(dev)}
+        u = torch.zeros((1, nodes, 2), dtype=torch.float64, device=dev)
+
+        def step(pr):
+            romb.romb_assemble(ctx.h, lat, pr, device_arrays=darr)
+            romb.romb_factor(ctx.h)
+            _, its, rel = romb.romb_bddc_solve(ctx.h, nodes, rtol=1e-8, maxit=500, out=u)
+            return int(its[0])
+
+        for _ in range(a.warmup):
+            step(forms[form])
+        torch.cuda.synchronize(dev)
+        times, its = _timed(torch, stream, flush, a.steps, lambda: (step(forms[form]), romb.romb_stats(ctx.h)[0].copy()))
+        ms = sum(times) / len(times)
+        ph = np.mean(np.array([p_ for _, p_ in its]), axis=0)
+        entry = {"cells": cells, "grid": f"{lat.nx}x{lat.ny}", "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
+                 "pcg_iters": its[-1][0], "paper_iters": paper_its,
+                 "phase_ms": {n: float(v) for n, v in zip(names, ph)}}
+        if not a.no_accuracy:
+            v = u.clone()
+            step(romb.ROMB_FP64)
+            entry["disp_rel_l2_vs_fp64"] = (torch.linalg.vector_norm(v - u) / torch.linalg.vector_norm(u)).item()
+        sizes[str(cells)] = entry
+        ctx.close()
+    clk = clocks.stop()
+    big = sizes["7290"]
+    line = {"metric": "cells/s assembled+solved, wrench-like layout of Schoen IWP cells, p=8, 16 clusters",
+            "value": big["cells_per_s"], "unit": "cells/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": big["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32split": "tf32x3+f64", "bf16split": "bf16x10+f64"}[form],
+            "data": "synthetic",
+            "config": {"workload": "wrench-like layout (round head with a clamped hole, loaded handle), Schoen IWP, "
+                                   "thresholds U[-2.5,2.5]^4 per cell, p=8, n_k=2, n_r=40, r=6",
+                       "assembly_form": form, "l2": "flushed (512 MB write) between timed steps", "pcg_rtol": 1e-8},
+            "clocks": clk, "sizes": sizes, "offline_train_s": train_s}
+    print(json.dumps(line))
+
+
 def run_workload4(a):
     """The compliance gradient workload: 64 x 64 cells, cubic maps, one hole
     radius per cell, p = 6, rank-40 model; one step = FP64-form assembly,
@@ -953,6 +1036,8 @@ def main():
         run_workload4(a)
     elif a.workload == 6:
         run_workload6(a)
+    elif a.workload == 7:
+        run_workload7(a)
     else:
         run_ours(a)
 

@@ -86,6 +86,19 @@ typedef struct {
   unsigned dirichlet_mask; /* bit e: lattice edge e clamped (u = 0, strong)      */
   const double* traction;  /* [4][2] physical traction per unit length per edge, */
                            /* applied on the solid (conformal) part of the edge  */
+  /* Layouts that are not a full rectangle of cells (the lattice wrench of
+   * Sec. 5.2.2): the subdomains are the present cells of the nx x ny grid.
+   * Edges that a present cell shares with an absent one are free boundary;
+   * dirichlet_mask and traction act on the present cells' edges on the
+   * grid's sides.  Per-cell results (romb_read, the per-cell flags) list the
+   * present cells in increasing grid index c = cx + nx cy; mu and family
+   * keep one entry per grid cell, absent ones unread; the nodal output keeps
+   * the full grid, zero at nodes of no present cell.  The compliance
+   * gradient needs the full rectangle (ROMB_E_STATE otherwise). */
+  const uint8_t* cell_present;  /* [nx*ny] nonzero: cell present; NULL: all     */
+  const uint8_t* edge_clamped;  /* [nx*ny][4] nonzero: edge e (0 left, 1 right, */
+                                /* 2 bottom, 3 top) of that present cell clamped, */
+                                /* end points included; NULL: none              */
 } romb_lattice;
 
 /* Create a context on `device`.  `cuda_stream` is a cudaStream_t owned by the
@@ -129,8 +142,9 @@ romb_status romb_train_load(romb_ctx* ctx, const char* rom_path, int* family_out
 romb_status romb_assemble(romb_ctx* ctx, const romb_lattice* lat, romb_precision prec);
 
 /* As romb_assemble, but with caller-supplied dense cell matrices
- * K[nx*ny][ndof][ndof] (ndof = 2 (p+1)^2, local DoF 2k+i), e.g. from full
- * trimmed quadrature (the unaccelerated baseline of Sec. 5.1). */
+ * K[ncells][ndof][ndof] (ndof = 2 (p+1)^2, local DoF 2k+i; ncells = nx*ny,
+ * or the present cells in increasing grid index), e.g. from full trimmed
+ * quadrature (the unaccelerated baseline of Sec. 5.1). */
 romb_status romb_assemble_host_K(romb_ctx* ctx, const romb_lattice* lat, const double* K);
 
 /* BDDC set-up (Sec. 3): per cell the Cholesky factor of K_II and the Schur

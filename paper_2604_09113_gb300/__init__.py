@@ -41,7 +41,8 @@ class RombLattice(ctypes.Structure):
                 ("basis", ctypes.c_int), ("mem", ctypes.c_int),
                 ("ctrl", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("family", ctypes.c_void_p),
                 ("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double),
-                ("dirichlet_mask", ctypes.c_uint), ("traction", ctypes.c_void_p)]
+                ("dirichlet_mask", ctypes.c_uint), ("traction", ctypes.c_void_p),
+                ("cell_present", ctypes.c_void_p), ("edge_clamped", ctypes.c_void_p)]
 
 
 def _load():
@@ -103,7 +104,9 @@ def _ptr(a, keep: list):
 def make_lattice(lat, keep: list, device_arrays: dict | None = None) -> RombLattice:
     """Marshal a lattice description (an object with the fields of
     ``romb_lattice``) into the C struct.  ``device_arrays`` may map 'ctrl',
-    'mu', 'family', 'traction' to CUDA tensors that are passed in place."""
+    'mu', 'family', 'traction' (and 'present', 'edge_clamped', uint8) to CUDA
+    tensors that are passed in place; ``lat.present`` / ``lat.edge_clamped``
+    (None: every cell, no clamped cell edge) give the layout."""
     dev = device_arrays or {}
     ctrl, d1 = _ptr(dev.get("ctrl", np.asarray(lat.ctrl, dtype=np.float64)), keep)
     mu, d2 = _ptr(dev.get("mu", np.asarray(lat.mu, dtype=np.float64)), keep)
@@ -111,8 +114,24 @@ def make_lattice(lat, keep: list, device_arrays: dict | None = None) -> RombLatt
     tr, d4 = _ptr(dev.get("traction", np.asarray(lat.traction, dtype=np.float64).reshape(8)), keep)
     if len({d1, d2, d3, d4}) != 1:
         raise ValueError("lattice arrays must all be host arrays or all device tensors")
+    # layout arrays (absent cells, clamped cell edges): uint8, in the same memory
+    ptrs = []
+    for name in ("present", "edge_clamped"):
+        a = getattr(lat, name, None)
+        if name in dev:
+            a = dev[name]
+        elif a is not None:
+            a = np.asarray(a).astype(np.uint8).reshape(-1)
+            if d1:
+                import torch
+                a = torch.from_numpy(a).to(dev["ctrl"].device)
+        q, dq = _ptr(a, keep)
+        if q is not None and dq != d1:
+            raise ValueError("layout arrays must live where the other lattice arrays do")
+        ptrs.append(q)
     L = RombLattice(lat.nx, lat.ny, lat.p, lat.m, lat.basis, ROMB_MEM_DEVICE if d1 else ROMB_MEM_HOST,
-                    ctrl, mu, fam, float(lat.E), float(lat.nu), float(lat.rho), int(lat.dirichlet_mask), tr)
+                    ctrl, mu, fam, float(lat.E), float(lat.nu), float(lat.rho), int(lat.dirichlet_mask), tr,
+                    ptrs[0], ptrs[1])
     return L
 
 

@@ -391,7 +391,29 @@ extern "C" romb_status romb_train_load(romb_ctx* c, const char* path, int* famil
 // ---------------------------------------------------------------------------
 // Lattice set-up: copies inputs, builds structural index tables
 // ---------------------------------------------------------------------------
-static romb_status setup_lattice(romb_ctx* c, const romb_lattice* L) {
+// The layout arrays of L on the host (empty when not given).
+static romb_status read_layout(romb_ctx* c, const romb_lattice* L, std::vector<uint8_t>& pres,
+                               std::vector<uint8_t>& clamp) {
+  const size_t cells = (size_t)L->nx * L->ny;
+  pres.clear();
+  clamp.clear();
+  const cudaMemcpyKind kind = L->mem == ROMB_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+  if (L->cell_present) {
+    pres.resize(cells);
+    ROMB_CUDA(cudaMemcpy(pres.data(), L->cell_present, cells, kind));
+    for (uint8_t& v : pres) v = v ? 1 : 0;
+  }
+  if (L->edge_clamped) {
+    clamp.resize(4 * cells);
+    ROMB_CUDA(cudaMemcpy(clamp.data(), L->edge_clamped, 4 * cells, kind));
+    for (uint8_t& v : clamp) v = v ? 1 : 0;
+  }
+  (void)c;
+  return ROMB_OK;
+}
+
+static romb_status setup_lattice(romb_ctx* c, const romb_lattice* L, const std::vector<uint8_t>& pres,
+                                 const std::vector<uint8_t>& clamp) {
   if (!L || L->nx < 1 || L->ny < 1 || L->p < 3 || L->p > ROMB_MAX_P || L->map_order < 1 ||
       L->map_order > 4 || (L->basis != 0 && L->basis != 1) || !L->ctrl || !L->mu || !L->family ||
       (L->mem != ROMB_MEM_HOST && L->mem != ROMB_MEM_DEVICE) || !(L->rho >= 0.0) || !(L->E > 0) ||
@@ -399,8 +421,13 @@ static romb_status setup_lattice(romb_ctx* c, const romb_lattice* L) {
     return ROMB_E_ARG;
   const long long cells = (long long)L->nx * L->ny;
   if (cells > (1LL << 22)) return ROMB_E_ARG;
+  if (!pres.empty() && std::find(pres.begin(), pres.end(), (uint8_t)1) == pres.end()) {
+    romb_set_error("lattice layout: no present cell");
+    return ROMB_E_ARG;
+  }
   const bool same = c->have_lattice && c->nx == L->nx && c->ny == L->ny && c->p == L->p &&
-                    c->m == L->map_order && c->dmask == L->dirichlet_mask;
+                    c->m == L->map_order && c->dmask == L->dirichlet_mask && c->h_present == pres &&
+                    c->h_clamped == clamp;
   if (!same) {
     romb_free_lattice(c);
     return ROMB_E_STATE;
@@ -419,21 +446,71 @@ static romb_status build_tables(romb_ctx* c) {
   // skeleton map per cell, coarse map per cell
   std::vector<int> umap((size_t)cells * nU), cmap((size_t)cells * ROMB_NSLOT);
   const long long NH = (long long)(ny + 1) * (p * nx + 1);
+  auto skel_id = [&](int gx, int gy) -> long long {   // grid node on a cell boundary -> skeleton node
+    if (gy % p == 0) return (long long)(gy / p) * (p * nx + 1) + gx;
+    return NH + ((long long)(gy / p) * (nx + 1) + gx / p) * (p - 1) + (gy % p - 1);
+  };
+  auto grid_xy = [&](long long cell, int* cx, int* cy) {
+    const long long g = c->layout ? c->h_cell_grid[cell] : cell;
+    *cx = (int)(g % nx);
+    *cy = (int)(g / nx);
+  };
+  // layouts: the skeleton nodes that carry no unknown (clamped by the mask or
+  // by a clamped cell edge, or on no present cell)
+  std::vector<uint8_t> fixed;
+  if (c->layout) {
+    fixed.assign((size_t)c->nskel_nodes, 1);
+    std::vector<uint8_t> clamped((size_t)c->nskel_nodes, 0);
+    for (long long cell = 0; cell < cells; ++cell) {
+      int cx, cy;
+      grid_xy(cell, &cx, &cy);
+      for (int u = 0; u < nU; u += 2) {
+        const int k = T.uslot[u] / 2, a = k % (p + 1), b = k / (p + 1);
+        fixed[skel_id(p * cx + a, p * cy + b)] = 0;
+      }
+      if (!c->h_clamped.empty())
+        for (int e = 0; e < 4; ++e) {
+          if (!c->h_clamped[4 * (size_t)(c->h_cell_grid[cell]) + e]) continue;
+          for (int t = 0; t <= p; ++t) {
+            const int a = e == 0 ? 0 : e == 1 ? p : t, b = e == 2 ? 0 : e == 3 ? p : t;
+            clamped[skel_id(p * cx + a, p * cy + b)] = 1;
+          }
+        }
+    }
+    for (long long id = 0; id < c->nskel_nodes; ++id) {
+      if (fixed[id]) continue;
+      int gx, gy;
+      if (id < NH) {
+        gy = p * (int)(id / (p * nx + 1));
+        gx = (int)(id % (p * nx + 1));
+      } else {
+        long long t = id - NH;
+        const int b = (int)(t % (p - 1)) + 1;
+        t /= (p - 1);
+        gx = p * (int)(t % (nx + 1));
+        gy = p * (int)(t / (nx + 1)) + b;
+      }
+      const bool side = ((c->dmask & 1) && gx == 0) || ((c->dmask & 2) && gx == p * nx) ||
+                        ((c->dmask & 4) && gy == 0) || ((c->dmask & 8) && gy == p * ny);
+      fixed[id] = side || clamped[id];
+    }
+    ROMB_CUDA(cudaMemcpy(c->d_node_fixed, fixed.data(), fixed.size(), cudaMemcpyHostToDevice));
+  }
   auto dir_node = [&](int gx, int gy) {
+    if (c->layout) return fixed[skel_id(gx, gy)] != 0;
     return ((c->dmask & 1) && gx == 0) || ((c->dmask & 2) && gx == p * nx) || ((c->dmask & 4) && gy == 0) ||
            ((c->dmask & 8) && gy == p * ny);
   };
   const long long NCV = 2LL * (nx + 1) * (ny + 1), NCH = 3LL * nx * (ny + 1);
-  for (int cy = 0; cy < ny; ++cy)
-    for (int cx = 0; cx < nx; ++cx) {
-      const long long cell = cx + (long long)nx * cy;
+  for (long long cell = 0; cell < cells; ++cell) {
+    int cx, cy;
+    grid_xy(cell, &cx, &cy);
+    {
       for (int u = 0; u < nU; ++u) {
         const int k = T.uslot[u] / 2, comp = T.uslot[u] % 2;
         const int a = k % (p + 1), b = k / (p + 1);
         const int gx = p * cx + a, gy = p * cy + b;
-        long long id;
-        if (gy % p == 0) id = (long long)(gy / p) * (p * nx + 1) + gx;
-        else id = NH + ((long long)cy * (nx + 1) + gx / p) * (p - 1) + (b - 1);
+        const long long id = skel_id(gx, gy);
         umap[cell * nU + u] = dir_node(gx, gy) ? -1 : (int)(2 * id + comp);
       }
       int* cm = &cmap[cell * ROMB_NSLOT];
@@ -444,22 +521,27 @@ static romb_status build_tables(romb_ctx* c) {
         cm[2 * v] = d ? -1 : (int)base;
         cm[2 * v + 1] = d ? -1 : (int)(base + 1);
       }
-      // edges: left (vx=cx), right (vx=cx+1), bottom (vy=cy), top (vy=cy+1)
+      // edges: left (vx=cx), right (vx=cx+1), bottom (vy=cy), top (vy=cy+1);
+      // an edge is clamped where its interior nodes are
       for (int e = 0; e < 4; ++e) {
         long long base;
         bool d;
         if (e < 2) {
           const int vx = cx + e;
-          d = (vx == 0 && (c->dmask & 1)) || (vx == nx && (c->dmask & 2));
+          d = c->layout ? dir_node(p * vx, p * cy + 1)
+                        : (vx == 0 && (c->dmask & 1)) || (vx == nx && (c->dmask & 2));
           base = NCV + NCH + 3LL * ((long long)cy * (nx + 1) + vx);
         } else {
           const int vy = cy + (e - 2);
-          d = (vy == 0 && (c->dmask & 4)) || (vy == ny && (c->dmask & 8));
+          d = c->layout ? dir_node(p * cx + 1, p * vy)
+                        : (vy == 0 && (c->dmask & 4)) || (vy == ny && (c->dmask & 8));
           base = NCV + 3LL * ((long long)vy * nx + cx);
         }
         for (int t = 0; t < 3; ++t) cm[8 + 3 * e + t] = d ? -1 : (int)(base + t);
       }
     }
+  }
+  (void)nB;
   ROMB_CUDA(cudaMemcpy(c->d_ucell_map, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice));
   ROMB_CUDA(cudaMemcpy(c->d_cmap, cmap.data(), sizeof(int) * cmap.size(), cudaMemcpyHostToDevice));
   c->ncoarse_all = NCV + NCH + 3LL * (nx + 1) * ny;
@@ -511,7 +593,8 @@ static romb_status lane_buffers(romb_ctx* c, PcgLane& L) {
   return ROMB_OK;
 }
 
-static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
+static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L, std::vector<uint8_t>& pres,
+                                 std::vector<uint8_t>& clamp) {
   romb_status s;
   c->nx = L->nx;
   c->ny = L->ny;
@@ -519,6 +602,20 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   c->m = L->map_order;
   c->dmask = L->dirichlet_mask;
   c->ncells = L->nx * L->ny;
+  c->layout = !pres.empty() || !clamp.empty();
+  c->h_present.swap(pres);
+  c->h_clamped.swap(clamp);
+  std::vector<int> grid_cell;
+  if (c->layout) {
+    grid_cell.assign((size_t)c->ncells, -1);
+    c->h_cell_grid.clear();
+    for (int g = 0; g < c->ncells; ++g)
+      if (c->h_present.empty() || c->h_present[g]) {
+        grid_cell[g] = (int)c->h_cell_grid.size();
+        c->h_cell_grid.push_back(g);
+      }
+    c->ncells = (int)c->h_cell_grid.size();
+  }
   c->nB = (c->p + 1) * (c->p + 1);
   c->ndof = 2 * c->nB;
   c->nI = 2 * (c->p - 1) * (c->p - 1);
@@ -564,7 +661,18 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   A_(c->d_cmap, cells * ROMB_NSLOT);
   A_(c->d_red, 4096);
   A_(c->d_pcg_err, 1);
+  if (c->layout) {
+    const long long grid = (long long)nx * ny;
+    A_(c->d_cell_grid, cells);
+    A_(c->d_grid_cell, grid);
+    A_(c->d_node_fixed, c->nskel_nodes);
+    A_(c->d_stage, 4 * grid + (grid + 1) / 2);   // grid-indexed mu, then family
+  }
 #undef A_
+  if (c->layout) {
+    ROMB_CUDA(cudaMemcpy(c->d_cell_grid, c->h_cell_grid.data(), 4 * (size_t)cells, cudaMemcpyHostToDevice));
+    ROMB_CUDA(cudaMemcpy(c->d_grid_cell, grid_cell.data(), 4 * grid_cell.size(), cudaMemcpyHostToDevice));
+  }
   ROMB_CUDA(cudaMemsetAsync(c->d_pcg_err, 0, 4, c->stream));
   const long long ncoarse = 2LL * (nx + 1) * (ny + 1) + 3LL * nx * (ny + 1) + 3LL * (nx + 1) * ny;
   c->ncoarse_all = ncoarse;
@@ -575,13 +683,28 @@ static romb_status alloc_lattice(romb_ctx* c, const romb_lattice* L) {
   return ROMB_OK;
 }
 
+// The present cells' thresholds and families out of the grid-indexed inputs.
+__global__ void gather_present_kernel(long long n, const int* __restrict__ cell_grid, const double* __restrict__ mu_g,
+                                      const int32_t* __restrict__ fam_g, double* __restrict__ mu,
+                                      int32_t* __restrict__ fam) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = cell_grid[i];
+    fam[i] = fam_g[g];
+    for (int k = 0; k < 4; ++k) mu[4 * i + k] = mu_g[4 * g + k];
+  }
+}
+
 // Copy (or reference) the lattice inputs and validate families.
 static romb_status load_lattice(romb_ctx* c, const romb_lattice* L) {
-  romb_status s = setup_lattice(c, L);
+  if (!L) return ROMB_E_ARG;
+  std::vector<uint8_t> pres, clamp;
+  romb_status s = read_layout(c, L, pres, clamp);
+  if (s != ROMB_OK) return s;
+  s = setup_lattice(c, L, pres, clamp);
   if (s == ROMB_E_ARG) return s;
   if (s == ROMB_E_STATE) {
     c->have_lattice = false;
-    if ((s = alloc_lattice(c, L)) != ROMB_OK) return s;
+    if ((s = alloc_lattice(c, L, pres, clamp)) != ROMB_OK) return s;
   }
   c->basis = L->basis;
   c->mem = L->mem;
@@ -594,8 +717,20 @@ static romb_status load_lattice(romb_ctx* c, const romb_lattice* L) {
   const cudaMemcpyKind kind = L->mem == ROMB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaEventRecord(c->ev[12], c->stream);
   ROMB_CUDA(cudaMemcpyAsync(c->d_ctrl, L->ctrl, 16 * nctrl, kind, c->stream));
-  ROMB_CUDA(cudaMemcpyAsync(c->d_mu, L->mu, 32 * cells, kind, c->stream));
-  ROMB_CUDA(cudaMemcpyAsync(c->d_family, L->family, 4 * cells, kind, c->stream));
+  if (!c->layout) {
+    ROMB_CUDA(cudaMemcpyAsync(c->d_mu, L->mu, 32 * cells, kind, c->stream));
+    ROMB_CUDA(cudaMemcpyAsync(c->d_family, L->family, 4 * cells, kind, c->stream));
+  } else {
+    // grid-indexed inputs through the staging buffer, then the present cells'
+    const long long grid = (long long)c->nx * c->ny;
+    int32_t* fam_g = reinterpret_cast<int32_t*>(c->d_stage + 4 * grid);
+    ROMB_CUDA(cudaMemcpyAsync(c->d_stage, L->mu, 32 * grid, kind, c->stream));
+    ROMB_CUDA(cudaMemcpyAsync(fam_g, L->family, 4 * grid, kind, c->stream));
+    gather_present_kernel<<<c->sms, 256, 0, c->stream>>>(cells, c->d_cell_grid, c->d_stage, fam_g, c->d_mu,
+                                                         c->d_family);
+    ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
+  }
   // the lattice's own traction is kept on the host (each solve copies its
   // load set to its lane)
   if (L->traction && L->mem == ROMB_MEM_DEVICE) {
@@ -822,6 +957,10 @@ extern "C" romb_status romb_compliance_grad(romb_ctx* c, double* compliance, dou
   if (!c->solved || !c->assembled_rom) return ROMB_E_STATE;
   if (c->lane[0].body_on || c->load_form != ROMB_LOADS_QUADRATURE) {
     romb_set_error("compliance gradient: only for the quadrature traction loads without body forces");
+    return ROMB_E_STATE;
+  }
+  if (c->layout) {
+    romb_set_error("compliance gradient: only for the full rectangle of cells");
     return ROMB_E_STATE;
   }
   ROMB_CUDA(cudaSetDevice(c->device));

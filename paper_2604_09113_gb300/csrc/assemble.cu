@@ -86,6 +86,11 @@ void fill_cell_params(const romb_ctx* c, CellParams* P) {
   P->nx = c->nx;
   P->ny = c->ny;
   P->ncells = c->ncells;
+  if (c->layout) {
+    P->cell_grid = c->d_cell_grid;
+    P->grid_cell = c->d_grid_cell;
+    P->node_fixed = c->d_node_fixed;
+  }
   P->q = c->q;
   P->nL = c->nL;
   P->dmask = c->dmask;
@@ -390,7 +395,8 @@ __global__ void __launch_bounds__(128) theta_kernel(CellParams P, ThetaFams F,
     const int j = task / 9, k3 = task % 9;
     const int c = cells[j];
     if (c < 0) continue;
-    const int cx = c % P.nx, cy = c / P.nx;
+    int cx, cy;
+    cell_xy(P, c, &cx, &cy);
     const double qn[3] = {0.0, 0.5, 1.0};
     double x[2], J[2][2];
     map_eval(ctrl, P.nx, P.m, cx, cy, qn[k3 % 3], qn[k3 / 3], x, J);

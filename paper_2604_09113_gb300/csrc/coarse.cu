@@ -42,6 +42,11 @@ struct Builder {
   int nx, ny;
   unsigned dmask;
   long long NCV, NCH;
+  // layouts with absent cells or clamped cell edges (empty for the full
+  // rectangle): the coarse DoFs some present cell holds, and the cell number
+  // of every grid position (-1 absent)
+  std::vector<char> used;
+  std::vector<int> grid_cell;
   std::vector<NdFront>* fronts;
   std::vector<std::vector<int>> rows;        // per front: global coarse DoFs (sep first)
   std::vector<std::vector<int>> leaf_cells;  // per front (leaves only)
@@ -57,19 +62,22 @@ struct Builder {
       for (int px = 2 * x0; px <= 2 * x1; ++px) {
         const bool ex = (px & 1) == 0, ey = (py & 1) == 0;
         if (!ex && !ey) continue;   // cell centre
+        Group g;
         if (ex && ey) {
           const int vx = px / 2, vy = py / 2;
           if (vertex_dir(vx, vy)) continue;
-          out.push_back({px, py, 2, (int)(2LL * ((long long)vy * (nx + 1) + vx))});
+          g = {px, py, 2, (int)(2LL * ((long long)vy * (nx + 1) + vx))};
         } else if (ey) {   // horizontal edge (cx, vy)
           const int cx = px / 2, vy = py / 2;
           if ((vy == 0 && (dmask & 4)) || (vy == ny && (dmask & 8))) continue;
-          out.push_back({px, py, 3, (int)(NCV + 3LL * ((long long)vy * nx + cx))});
+          g = {px, py, 3, (int)(NCV + 3LL * ((long long)vy * nx + cx))};
         } else {           // vertical edge (vx, cy)
           const int vx = px / 2, cy = py / 2;
           if ((vx == 0 && (dmask & 1)) || (vx == nx && (dmask & 2))) continue;
-          out.push_back({px, py, 3, (int)(NCV + NCH + 3LL * ((long long)cy * (nx + 1) + vx))});
+          g = {px, py, 3, (int)(NCV + NCH + 3LL * ((long long)cy * (nx + 1) + vx))};
         }
+        if (!used.empty() && !used[g.base]) continue;
+        out.push_back(g);
       }
   }
   bool internal_side(const Group& g, int x0, int x1, int y0, int y1) const {
@@ -116,7 +124,11 @@ struct Builder {
     std::vector<int> cells;
     if (leaf)
       for (int cy = y0; cy < y1; ++cy)
-        for (int cx = x0; cx < x1; ++cx) cells.push_back(cx + nx * cy);
+        for (int cx = x0; cx < x1; ++cx) {
+          const int g = cx + nx * cy;
+          const int cell = grid_cell.empty() ? g : grid_cell[g];
+          if (cell >= 0) cells.push_back(cell);
+        }
     leaf_cells.push_back(cells);
     int d = 0;
     for (int k : kids) {
@@ -737,6 +749,15 @@ romb_status coarse_build(romb_ctx* c) {
   B.NCV = 2LL * (c->nx + 1) * (c->ny + 1);
   B.NCH = 3LL * c->nx * (c->ny + 1);
   B.fronts = &plan.fronts;
+  std::vector<int> cmap((size_t)c->ncells * 20);
+  ROMB_CUDA(cudaMemcpy(cmap.data(), c->d_cmap, 4 * cmap.size(), cudaMemcpyDeviceToHost));
+  if (c->layout) {
+    B.used.assign((size_t)c->ncoarse_all, 0);
+    for (int g : cmap)
+      if (g >= 0) B.used[g] = 1;
+    B.grid_cell.assign((size_t)c->nx * c->ny, -1);
+    for (int i = 0; i < c->ncells; ++i) B.grid_cell[c->h_cell_grid[i]] = i;
+  }
   const int root = B.build(0, c->nx, 0, c->ny);
   (void)root;
   const int nf = (int)plan.fronts.size();
@@ -821,8 +842,6 @@ romb_status coarse_build(romb_ctx* c) {
     }
   }
   // cell -> leaf-front row of each local coarse slot
-  std::vector<int> cmap((size_t)c->ncells * 20);
-  ROMB_CUDA(cudaMemcpy(cmap.data(), c->d_cmap, 4 * cmap.size(), cudaMemcpyDeviceToHost));
   for (int i = 0; i < nf; ++i) {
     if (B.leaf_cells[i].empty()) continue;
     std::unordered_map<int, int> pos;
@@ -972,6 +991,7 @@ romb_status coarse_factor(romb_ctx* c) {
                                                      D.cell_pos, c->d_SCl);
     } else {
       const dim3 ga((D.level_maxn[l] + D.level_maxns[l] + 7) / 8, nfl);
+      if (ga.x == 0) continue;   // every front of the level empty (layouts with absent cells)
       nd_assemble_inner_kernel<<<ga, 256, 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.asrc);
     }
     ++c->launches;

@@ -13,6 +13,10 @@
 struct CellParams {
   int p, m, basis, nB, nI, nU, nx, ny, ncells, q, nL;
   unsigned dmask;
+  // layouts with absent cells or clamped cell edges (null for the full rectangle)
+  const int* cell_grid;         // [ncells] grid index c = cx + nx cy of each cell
+  const int* grid_cell;         // [nx*ny] cell of each grid position, -1 absent
+  const uint8_t* node_fixed;    // [skeleton nodes] clamped, or of no present cell
   double E, nu, rho, lam, mu;   // plane-stress Lame parameters
   double gll[ROMB_MAX_P + 1];   // degree-p GLL nodes of the cell basis
   double bw[ROMB_MAX_P + 1];    // their barycentric weights 1 / prod_{j != i} (gll_i - gll_j)
@@ -135,6 +139,20 @@ __device__ inline void edge_map_point(const CellParams& P, const double* ctrl, i
     tan[0] = fma(dw, X[0], tan[0]);
     tan[1] = fma(dw, X[1], tan[1]);
   }
+}
+
+// Grid position of cell `cell` (the cells are the present ones of the grid).
+__device__ inline void cell_xy(const CellParams& P, long long cell, int* cx, int* cy) {
+  const long long g = P.cell_grid ? P.cell_grid[cell] : cell;
+  *cx = (int)(g % P.nx);
+  *cy = (int)(g / P.nx);
+}
+
+// Cell at grid position (cx, cy): -1 outside the grid or absent.
+__device__ inline long long cell_at(const CellParams& P, int cx, int cy) {
+  if (cx < 0 || cy < 0 || cx >= P.nx || cy >= P.ny) return -1;
+  const long long g = cx + (long long)P.nx * cy;
+  return P.grid_cell ? P.grid_cell[g] : g;
 }
 
 __device__ inline double warp_sum(double v) {

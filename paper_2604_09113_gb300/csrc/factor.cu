@@ -78,31 +78,38 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
                                                               const double* __restrict__ eiv,
                                                               double* __restrict__ out) {
   // one warp per lattice edge: vertical edges (vx, cy) first, then horizontal
-  // (cx, vy); the edge is computed from one of its cells (edge e) and written
-  // for both (the other sees it as edge e ^ 1, same parameter and nodes)
+  // (cx, vy); the edge is computed from one of its present cells (edge e) and
+  // written for both (the other sees it as edge e ^ 1, same parameter and nodes)
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, m = P.m, nx = P.nx, ny = P.ny;
   const long long nV = (long long)(nx + 1) * ny, nH = (long long)nx * (ny + 1);
   if (w >= nV + nH) return;
-  int cx, cy, e;
-  long long cell2 = -1;
+  int cx, cy, e, cx2, cy2;
   if (w < nV) {
     const int vx = (int)(w % (nx + 1));
-    cy = (int)(w / (nx + 1));
-    cx = vx < nx ? vx : nx - 1;
-    e = vx < nx ? 0 : 1;
-    if (vx > 0 && vx < nx) cell2 = (vx - 1) + (long long)nx * cy;
+    cy = cy2 = (int)(w / (nx + 1));
+    cx = vx;         // the cell right of the edge sees it as its left edge
+    cx2 = vx - 1;    // the cell left of it, as its right edge
+    e = 0;
   } else {
     const long long wh = w - nV;
     const int vy = (int)(wh / nx);
-    cx = (int)(wh % nx);
-    cy = vy < ny ? vy : ny - 1;
-    e = vy < ny ? 2 : 3;
-    if (vy > 0 && vy < ny) cell2 = cx + (long long)nx * (vy - 1);
+    cx = cx2 = (int)(wh % nx);
+    cy = vy;         // the cell above, bottom edge
+    cy2 = vy - 1;    // the cell below, top edge
+    e = 2;
   }
-  const long long cell = cx + (long long)nx * cy;
+  long long cell = cell_at(P, cx, cy), cell2 = cell_at(P, cx2, cy2);
+  if (cell < 0) {   // computed from the other cell
+    cell = cell2;
+    cell2 = -1;
+    cx = cx2;
+    cy = cy2;
+    e ^= 1;
+  }
+  if (cell < 0) return;   // no present cell on this edge
   // intervals: where this cell and its neighbour across the edge are both
-  // solid (the cell's own solid part on the lattice boundary)
+  // solid (the cell's own solid part on the boundary of the domain)
   double lo[ROMB_MAX_IV * ROMB_MAX_IV], hi[ROMB_MAX_IV * ROMB_MAX_IV];
   const double* own = eiv + (cell * 4 + e) * ROMB_EIV;
   int nm = (int)own[0];
@@ -110,9 +117,8 @@ __global__ void __launch_bounds__(128) edge_functional_kernel(CellParams P, cons
     lo[i] = own[1 + 2 * i];
     hi[i] = own[2 + 2 * i];
   }
-  const int ncx = e == 0 ? cx - 1 : e == 1 ? cx + 1 : cx, ncy = e == 2 ? cy - 1 : e == 3 ? cy + 1 : cy;
-  if (ncx >= 0 && ncx < nx && ncy >= 0 && ncy < ny) {
-    const double* nbv = eiv + ((ncx + (long long)nx * ncy) * 4 + (e ^ 1)) * ROMB_EIV;
+  if (cell2 >= 0) {
+    const double* nbv = eiv + (cell2 * 4 + (e ^ 1)) * ROMB_EIV;
     const int n1 = nm, n2 = (int)nbv[0];
     nm = 0;
     for (int i = 0; i < n1; ++i)    // both lists are sorted and disjoint: so is the result
@@ -558,9 +564,10 @@ __global__ void ktot_kernel(CellParams P, const double* __restrict__ Kp, long lo
     for (int dy = (gy % p == 0) ? -1 : 0; dy <= 0; ++dy)
       for (int dx = (gx % p == 0) ? -1 : 0; dx <= 0; ++dx) {
         const int cx = cx1 + dx, cy = cy1 + dy;
-        if (cx < 0 || cy < 0 || cx >= nx || cy >= ny) continue;
+        const long long cell = cell_at(P, cx, cy);
+        if (cell < 0) continue;
         const int k = (gx - p * cx) + (p + 1) * (gy - p * cy);
-        const double* Kc = Kp + ((long long)cy * nx + cx) * kp;
+        const double* Kc = Kp + cell * kp;
         const long long r0 = 2 * k, r1 = 2 * k + 1;
         s0 += Kc[r0 * ND - r0 * (r0 - 1) / 2];
         s1 += Kc[r1 * ND - r1 * (r1 - 1) / 2];

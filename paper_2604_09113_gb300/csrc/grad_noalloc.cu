@@ -49,7 +49,7 @@ extern "C" romb_status romb_compliance_grad_noalloc(romb_ctx* c, double* complia
                                                     double* dc_dR, double* dc_dmu) {
   if (!c || !compliance || !dc_dctrl) return ROMB_E_ARG;
   if (!c->solved || !c->assembled_rom) return ROMB_E_STATE;
-  if (c->lane[0].body_on || c->load_form != ROMB_LOADS_QUADRATURE) return ROMB_E_STATE;
+  if (c->lane[0].body_on || c->load_form != ROMB_LOADS_QUADRATURE || c->layout) return ROMB_E_STATE;
   const size_t cells = (size_t)c->ncells;
   const size_t ncp = (size_t)(c->m + 1) * (c->m + 1);
   const size_t nctrl = (size_t)(c->m * c->nx + 1) * (c->m * c->ny + 1);

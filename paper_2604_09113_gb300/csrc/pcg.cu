@@ -35,7 +35,10 @@ __device__ inline void skel_node_xy(long long id, int p, int nx, long long NH, i
   }
 }
 
-__device__ inline bool dir_node(const CellParams& P, int gx, int gy) {
+// skeleton node `id` at grid node (gx, gy) carries no unknown: clamped (or,
+// in layouts with absent cells, clamped or of no present cell)
+__device__ inline bool dir_node(const CellParams& P, long long id, int gx, int gy) {
+  if (P.node_fixed) return P.node_fixed[id] != 0;
   return ((P.dmask & 1) && gx == 0) || ((P.dmask & 2) && gx == P.p * P.nx) || ((P.dmask & 4) && gy == 0) ||
          ((P.dmask & 8) && gy == P.p * P.ny);
 }
@@ -50,15 +53,16 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
     int gx, gy;
     skel_node_xy(id, p, nx, NH, &gx, &gy);
     double s0 = 0.0, s1 = 0.0;
-    if (!dir_node(P, gx, gy)) {
+    if (!dir_node(P, id, gx, gy)) {
       const int cx1 = gx / p, cy1 = gy / p;
       for (int dy = (gy % p == 0) ? -1 : 0; dy <= 0; ++dy)
         for (int dx = (gx % p == 0) ? -1 : 0; dx <= 0; ++dx) {
           const int cx = cx1 + dx, cy = cy1 + dy;
-          if (cx < 0 || cy < 0 || cx >= nx || cy >= ny) continue;
+          const long long cell = cell_at(P, cx, cy);
+          if (cell < 0) continue;
           const int k = (gx - p * cx) + (p + 1) * (gy - p * cy);
           const int u = 2 * P.uslot_of_node[k];
-          const double* l = loc + ((long long)cy * nx + cx) * NU;
+          const double* l = loc + cell * NU;
           s0 += l[u];
           s1 += l[u + 1];
         }
@@ -293,7 +297,8 @@ __global__ void __launch_bounds__(32 * LQ_WARPS) loads_kernel(CellParams P, cons
   const int j = (int)t;
   const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
   const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
-  const long long cell = cx + (long long)nx * cy;
+  const long long cell = cell_at(P, cx, cy);
+  if (cell < 0) return;   // absent cell: no edge here
   double lo[ROMB_MAX_IV], hi[ROMB_MAX_IV];
   const int nint = edge_solid_dev(family[cell], mu + 4 * cell, e, lo, hi);
   double Xe[5][2];
@@ -415,7 +420,8 @@ __global__ void __launch_bounds__(32 * LR_WARPS) loads_rom_kernel(CellParams P, 
   const int j = (int)t;
   const int cx = e == 0 ? 0 : e == 1 ? nx - 1 : j;
   const int cy = e == 2 ? 0 : e == 3 ? ny - 1 : j;
-  const long long cell = cx + (long long)nx * cy;
+  const long long cell = cell_at(P, cx, cy);
+  if (cell < 0) return;   // absent cell: no edge here
   const ForceRomDev& F = tab[slot[cell]];
   const int r = F.r, n1 = r + 1, rf = F.rf;
   if (lane < 4) {
@@ -504,7 +510,8 @@ __global__ void __launch_bounds__(32 * BL_WARPS) body_loads_kernel(CellParams P,
   const long long cell = (long long)blockIdx.x * BL_WARPS + warp;
   if (cell >= P.ncells) return;
   const int p = P.p, q = P.q, nx = P.nx, m = P.m, nq = q + 1, nL = nq * nq, nB = (p + 1) * (p + 1);
-  const int cx = (int)(cell % nx), cy = (int)(cell / nx);
+  int cx, cy;
+  cell_xy(P, cell, &cx, &cy);
   const ForceRomDev& F = tab[slot[cell]];
   const int r = F.r, n1 = r + 1, rf = F.rf, ne = 4 * (p + 1) * nq;
   if (lane < 4) {
@@ -623,7 +630,8 @@ __global__ void recover_kernel(CellParams P, const double* __restrict__ LII, con
     if (lane == 0) sy[warp][i] = (sy[warp][i] - s) / L[(long long)i * (i + 1) / 2 + i];
     __syncwarp();
   }
-  const int cx = (int)(cell % P.nx), cy = (int)(cell / P.nx);
+  int cx, cy;
+  cell_xy(P, cell, &cx, &cy);
   const long long gnx = (long long)p * P.nx + 1;
   for (int i = lane; i < NI; i += 32) {
     const int dof = P.islot[i], k = dof / 2, comp = dof % 2;
@@ -642,7 +650,7 @@ __global__ void skel_to_nodes_kernel(CellParams P, long long nnodes, const doubl
        id += (long long)gridDim.x * blockDim.x) {
     int gx, gy;
     skel_node_xy(id, p, nx, NH, &gx, &gy);
-    const bool d = dir_node(P, gx, gy);
+    const bool d = dir_node(P, id, gx, gy);
     u[2 * (gy * gnx + gx)] = d ? 0.0 : x[2 * id];
     u[2 * (gy * gnx + gx) + 1] = d ? 0.0 : x[2 * id + 1];
   }
@@ -994,6 +1002,8 @@ romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit) {
   }
   // recovery + nodal output
   cudaEventRecord(L.ev0, L.stream);
+  if (c->layout)   // nodes of no present cell are written by no kernel below
+    ROMB_CUDA(cudaMemsetAsync(L.d_u, 0, 16LL * (c->p * c->nx + 1) * (c->p * c->ny + 1), L.stream));
   recover_kernel<<<(c->ncells + 3) / 4, 128, 0, L.stream>>>(P, c->d_LII, c->d_W, c->d_ucell_map, L.d_x,
                                                             L.body_on ? L.d_fI : nullptr, L.d_u);
   ++c->launches;

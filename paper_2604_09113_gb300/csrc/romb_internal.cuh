@@ -169,6 +169,18 @@ struct romb_ctx {
   int32_t* d_family = nullptr;
   int32_t* d_flags = nullptr;
 
+  // layout of the present cells (Sec. 5.2.2); cells are numbered 0..ncells-1
+  // in increasing grid index c = cx + nx cy, and every per-cell array below
+  // is in that order
+  bool layout = false;               // cell_present or edge_clamped given
+  std::vector<uint8_t> h_present;    // [nx*ny] as given (empty: every cell)
+  std::vector<uint8_t> h_clamped;    // [nx*ny][4] as given (empty: none)
+  std::vector<int> h_cell_grid;      // [ncells] grid index of each present cell
+  int* d_cell_grid = nullptr;        // [ncells]
+  int* d_grid_cell = nullptr;        // [nx*ny] present-cell number, -1 absent
+  uint8_t* d_node_fixed = nullptr;   // [skeleton nodes] clamped or of no present cell
+  double* d_stage = nullptr;         // [nx*ny][4] grid-indexed inputs on their way to d_mu
+
   // per-cell arrays
   double* d_chat = nullptr;     // [cells][nL][16]
   float* d_chat32 = nullptr;    // [cells][144] FP32 copy for the tensor-core epilogue
