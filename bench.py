@@ -354,14 +354,15 @@ def nd_fronts(nx: int, ny: int, dmask: int) -> list:
 
 
 def coarse_solve_fma(nx: int, ny: int, dmask: int) -> float:
-    """FP64 FMAs of one coarse solve: both sweeps apply every front's
+    """FMAs of one coarse solve (FP32 in the split forms): both sweeps apply every front's
     B = [L11^-T | -(L21 L11^-1)^T] once (ns(ns+1)/2 + ns nb entries)."""
     return sum(2.0 * (ns * (ns + 1) / 2 + ns * nb) for ns, nb in nd_fronts(nx, ny, dmask))
 
 
 def pcg_cell_fma(p: int) -> float:
-    """FP64 FMAs per cell and PCG iteration: S p (nU^2), D F D r on its non-zero
-    (nU-8)^2 block, Phi^T r and Phi g (2 nU 20)."""
+    """FMAs per cell and PCG iteration: S p (nU^2), D F D r on its non-zero
+    (nU-8)^2 block, Phi^T r and Phi g (2 nU 20); all FP64 in the FP64 form,
+    all but S p FP32 in the split forms (the preconditioner)."""
     NU = 8 * p
     return NU * NU + (NU - 8) ** 2 + 2 * NU * 20
 
@@ -618,10 +619,24 @@ def run_ours(a):
             "units": f"{lat.ncells} cells x {factor_flops(lat.p):.0f} flop",
             "peak_source": "measured FP64 FMA rate of this GPU (fma_rates: romb_fma_probe)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    pcg_fl = iters[-1] * 2.0 * (pcg_cell_fma(lat.p) * lat.ncells +
-                                coarse_solve_fma(lat.nx, lat.ny, int(lat.dirichlet_mask)))
-    roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": pcg_fl / (ph[4] / 1e3) / 1e9, "peak": peak64,
-                "unit": "GFLOP/s (FP64)", "iterations": iters[-1]}
+    # the split forms apply the preconditioner in FP32 (D F D, Phi, the coarse
+    # substitutions); S p stays FP64
+    NU = 8 * lat.p
+    pre_fma = (pcg_cell_fma(lat.p) - NU * NU) * lat.ncells + coarse_solve_fma(lat.nx, lat.ny,
+                                                                             int(lat.dirichlet_mask))
+    sp_fma = NU * NU * lat.ncells
+    pcg_s = ph[4] / 1e3
+    if form == "fp64":
+        roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": iters[-1] * 2.0 * (sp_fma + pre_fma) / pcg_s / 1e9,
+                    "peak": peak64, "unit": "GFLOP/s (FP64)", "iterations": iters[-1]}
+    else:
+        peak32 = rates.get("fp32_gflops") or None
+        roof_pcg = {"phase": "pcg", "bound": "alu", "achieved": iters[-1] * 2.0 * sp_fma / pcg_s / 1e9,
+                    "peak": peak64, "unit": "GFLOP/s (FP64: S p)", "iterations": iters[-1],
+                    "fp32_preconditioner": {"achieved": iters[-1] * 2.0 * pre_fma / pcg_s / 1e9, "peak": peak32,
+                                            "unit": "GFLOP/s (FP32: D F D, Phi, coarse substitutions)"}}
+        if peak32:
+            roof_pcg["fp32_preconditioner"]["frac"] = roof_pcg["fp32_preconditioner"]["achieved"] / peak32
     roof_pcg["frac"] = roof_pcg["achieved"] / roof_pcg["peak"]
     asm = assembly_report(ph, lat.ncells, lat.p, n_r, form, world, peak64)
 

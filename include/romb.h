@@ -238,6 +238,18 @@ romb_status romb_fma_probe(int precision, int blocks, int threads, int iters, vo
 enum { ROMB_LOADS_QUADRATURE = 0, ROMB_LOADS_REDUCED = 1 };
 romb_status romb_set_load_form(romb_ctx* ctx, int form);
 
+/* Precision in which the BDDC preconditioner (Algorithm 1) is applied: its
+ * fine operator D F D, the restriction and prolongation Phi and the coarse
+ * substitutions with the factor of S_C.  ROMB_PRECOND_AUTO (default): FP32
+ * after a split-precision assembly, FP64 otherwise; ROMB_PRECOND_FP64 /
+ * ROMB_PRECOND_FP32 force one.  The factorisations, the operator S, the PCG
+ * vectors, dot products and the stopping test stay FP64 in every case: the
+ * iterate converges to the same solution and only the preconditioner (an
+ * SPD operator up to FP32 rounding) changes.  Takes effect at the next
+ * romb_factor.  Errors: ROMB_E_ARG for another value. */
+enum { ROMB_PRECOND_AUTO = -1, ROMB_PRECOND_FP64 = 0, ROMB_PRECOND_FP32 = 1 };
+romb_status romb_set_precond_precision(romb_ctx* ctx, int mode);
+
 /* A constant body force (bx, by) per unit physical area on the solid part of
  * every cell (the volume term of Eq. SPEED L ext): with b_hat = det J b at the
  * (q+1)^2 interpolation nodes (Eq. FAST b interpolation) and the reduced

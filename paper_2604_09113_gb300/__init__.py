@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libromb.so")
 ROMB_FP64, ROMB_FP32_SPLIT, ROMB_BF16_SPLIT = 0, 1, 2
 ROMB_MEM_HOST, ROMB_MEM_DEVICE = 0, 1
 ROMB_LOADS_QUADRATURE, ROMB_LOADS_REDUCED = 0, 1
+ROMB_PRECOND_AUTO, ROMB_PRECOND_FP64, ROMB_PRECOND_FP32 = -1, 0, 1
 FIELDS = {"chat": 0, "theta": 1, "K": 2, "S": 3, "psi": 4, "sc_local": 5, "D": 6, "fine": 7, "flags": 8, "loads": 9}
 STATUS = {0: "ROMB_OK", -1: "ROMB_E_ARG", -2: "ROMB_E_CUDA", -3: "ROMB_E_OOM", -4: "ROMB_E_OUT_OF_BOX",
           -5: "ROMB_E_BAD_MAP", -6: "ROMB_E_NOT_SPD", -7: "ROMB_E_NOT_CONVERGED", -8: "ROMB_E_NAN",
@@ -72,6 +73,7 @@ def _load():
         "romb_train_snapshots_gpu": ([I, ctypes.POINTER(RombTrainSpec), P, I, P], I),
         "romb_set_load_form": ([P, I], I),
         "romb_set_body_force": ([P, D, D], I),
+        "romb_set_precond_precision": ([P, I], I),
         "romb_train_gpu_clustered": ([I, ctypes.POINTER(RombTrainSpec), I, P, I, ctypes.c_char_p], I),
     }
     for name, (args, res) in sig.items():
@@ -193,6 +195,13 @@ def romb_set_load_form(ctx, form: int) -> None:
     """ROMB_LOADS_QUADRATURE (edge quadrature) or ROMB_LOADS_REDUCED (the
     reduced model of the force integrals of version-2 model files)."""
     _check(_lib.romb_set_load_form(ctx, form), "romb_set_load_form")
+
+
+def romb_set_precond_precision(ctx, mode: int) -> None:
+    """ROMB_PRECOND_AUTO (FP32 after a split-precision assembly), ROMB_PRECOND_FP64
+    or ROMB_PRECOND_FP32: the precision of the preconditioner's operators from
+    the next romb_factor on."""
+    _check(_lib.romb_set_precond_precision(ctx, int(mode)), "romb_set_precond_precision")
 
 
 def romb_set_body_force(ctx, bx: float, by: float) -> None:

@@ -99,7 +99,7 @@ void romb_free_lattice(romb_ctx* c) {
   for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
   // lanes keep their streams, events and pinned words; their device buffers
   // went with the lattice
-  const int load_form = c->load_form;
+  const int load_form = c->load_form, precond_mode = c->precond_mode;
   const double body[2] = {c->body[0], c->body[1]};
   PcgLane lanes[ROMB_MAX_LANES];
   for (int k = 0; k < ROMB_MAX_LANES; ++k) {
@@ -118,6 +118,7 @@ void romb_free_lattice(romb_ctx* c) {
   *c = romb_ctx();
   for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
   c->load_form = load_form;
+  c->precond_mode = precond_mode;
   c->body[0] = body[0];
   c->body[1] = body[1];
   for (int i = 0; i < ROMB_MAX_MODELS; ++i) c->roms[i] = roms[i];
@@ -825,6 +826,11 @@ extern "C" romb_status romb_assemble_host_K(romb_ctx* c, const romb_lattice* L, 
   return ROMB_OK;
 }
 
+__global__ void to_f32_kernel(long long n, const double* __restrict__ src, float* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 extern "C" romb_status romb_factor(romb_ctx* c) {
   if (!c) return ROMB_E_ARG;
   if (!c->assembled) return ROMB_E_STATE;
@@ -835,11 +841,23 @@ extern "C" romb_status romb_factor(romb_ctx* c) {
       cudaGraphExecDestroy(L.graph);
       L.graph = nullptr;
     }
+  // the split-precision forms apply the preconditioner in FP32 (the operator
+  // S and the PCG vectors stay FP64): D F D, Phi and the coarse solve's B
+  c->pre32 = c->precond_mode < 0 ? c->assembled_split : c->precond_mode == 1;
   cudaEventRecord(c->ev[3], c->stream);
   if ((s = launch_ktot(c)) != ROMB_OK) return s;
   if ((s = launch_factor(c)) != ROMB_OK) return s;
   cudaEventRecord(c->ev[4], c->stream);
   if ((s = coarse_factor(c)) != ROMB_OK) return s;
+  if (c->pre32) {
+    const long long nG = (long long)c->ncells * c->nU * c->nU, nP = (long long)c->ncells * c->nU * ROMB_NSLOT;
+    if (!c->d_G32 && (s = romb_alloc_t(c, &c->d_G32, (size_t)nG)) != ROMB_OK) return s;
+    if (!c->d_Phi32 && (s = romb_alloc_t(c, &c->d_Phi32, (size_t)nP)) != ROMB_OK) return s;
+    to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nG, c->d_G, c->d_G32);
+    to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nP, c->d_Phi, c->d_Phi32);
+    c->launches += 2;
+    ROMB_CUDA(cudaGetLastError());
+  }
   cudaEventRecord(c->ev[5], c->stream);
   if ((s = check_flags(c, ROMB_FLAG_NOT_SPD | ROMB_FLAG_NAN)) != ROMB_OK) return s;
   c->phase_ms[2] = ms_between(c->ev[3], c->ev[4]);
@@ -1008,6 +1026,12 @@ extern "C" romb_status romb_set_body_force(romb_ctx* c, double bx, double by) {
 extern "C" romb_status romb_set_load_form(romb_ctx* c, int form) {
   if (!c || (form != ROMB_LOADS_QUADRATURE && form != ROMB_LOADS_REDUCED)) return ROMB_E_ARG;
   c->load_form = form;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_set_precond_precision(romb_ctx* c, int mode) {
+  if (!c || mode < ROMB_PRECOND_AUTO || mode > ROMB_PRECOND_FP32) return ROMB_E_ARG;
+  c->precond_mode = mode;
   return ROMB_OK;
 }
 

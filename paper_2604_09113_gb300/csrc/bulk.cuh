@@ -74,3 +74,17 @@ __device__ __forceinline__ Span16 span16(const double* src, long long len) {
   s.first = (int)((a - a0) >> 3);
   return s;
 }
+
+// The same for an array of T (4 or 8 bytes): the span may reach 16 - sizeof(T)
+// bytes before src and after src + len; first < 16 / sizeof(T).
+template <typename T>
+__device__ __forceinline__ Span16 span16t(const T* src, long long len) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+  const uintptr_t a0 = a & ~uintptr_t(15);
+  const uintptr_t e = (a + sizeof(T) * (uintptr_t)len + 15u) & ~uintptr_t(15);
+  Span16 s;
+  s.start = reinterpret_cast<const void*>(a0);
+  s.bytes = len > 0 ? (uint32_t)(e - a0) : 0u;
+  s.first = (int)((a - a0) / sizeof(T));
+  return s;
+}

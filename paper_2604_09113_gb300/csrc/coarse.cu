@@ -151,7 +151,16 @@ struct FrontDev {
   int wbuf_off;      // extend-add sources of each of the n rows (gsrc)
   int sbuf_off;      // forward result y_s = L11^-1 w_s (ns)
   long long bt_off;  // B^T (n x ns, row-major) of fronts on the row-kernel levels, -1 elsewhere
+  long long bf_off;  // B (ns x n) in the FP32 copy of the split-precision forms
 };
+
+// The front's B = [L11^-T | -(L21 L11^-1)^T] (ns x n, row-major): the rows
+// below the front in the FP64 pool, or its FP32 copy.
+__device__ __forceinline__ const double* front_B(const FrontDev& f, const double* F) {
+  const long long n = f.ns + f.nb;
+  return F + f.off + n * n;
+}
+__device__ __forceinline__ const float* front_B(const FrontDev& f, const float* BF) { return BF + f.bf_off; }
 
 }  // namespace
 
@@ -417,10 +426,11 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Small fronts: one warp per front.  Shared memory per warp: `stride`
 // doubles = the B block (ns x n, contiguous in the front, staged by one bulk
 // copy) at offset 0 and a vector of n at offset `voff`.
-__device__ __forceinline__ bool nd_stage_block(const FrontDev& f, const double* __restrict__ F, double* region,
+template <typename T, typename S>
+__device__ __forceinline__ bool nd_stage_block(const FrontDev& f, const S* __restrict__ Bsrc, T* region,
                                                uint64_t* bar, int lane, int* first) {
   const int n = f.ns + f.nb;
-  const Span16 sp = span16(F + f.off + (long long)n * n, (long long)f.ns * n);
+  const Span16 sp = span16t(front_B(f, Bsrc), (long long)f.ns * n);
   *first = sp.first;
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -431,21 +441,24 @@ __device__ __forceinline__ bool nd_stage_block(const FrontDev& f, const double* 
   return true;
 }
 
+// T = double: B from the FP64 pool (Bsrc = F); T = float: from its FP32 copy.
+template <typename T>
 __global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
-    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
+    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const T* __restrict__ Bsrc,
     const int* __restrict__ idx, const int2* __restrict__ gsrc, const double* __restrict__ rhs,
     double* __restrict__ ybuf, double* __restrict__ sbuf, int stride, int voff, int* __restrict__ err) {
-  extern __shared__ __align__(16) double sh[];
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
   __shared__ uint64_t bar[ND_WPC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int fi = blockIdx.x * ND_WPC + warp;
   const bool has = fi < nfronts;
   const FrontDev f = fr[level[has ? fi : 0]];
   const int ns = f.ns, n = ns + f.nb;
-  double* region = sh + (size_t)warp * stride;
-  double* w = region + voff;
+  T* region = sh + (size_t)warp * stride;
+  T* w = region + voff;
   int first = 0;
-  if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
+  if (has) nd_stage_block(f, Bsrc, region, &bar[warp], lane, &first);
   __syncwarp();   // the barrier is initialised before any lane waits on it
   // static gather indices before the wait: afterwards only the data loads remain
   int pid[ND_SMALL_N / 32];
@@ -462,7 +475,7 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
 #pragma unroll
   for (int k = 0; k < ND_SMALL_N / 32; ++k) {
     const int t = lane + 32 * k;
-    if (t < n) w[t] = (pid[k] >= 0 ? rhs[pid[k]] : 0.0) + nd_gather_row(pgs[k], ybuf);
+    if (t < n) w[t] = (T)((pid[k] >= 0 ? rhs[pid[k]] : 0.0) + nd_gather_row(pgs[k], ybuf));
   }
   const bool ok = mbar_wait(&bar[warp], 0);
   if (!__all_sync(0xffffffffu, ok)) {
@@ -470,42 +483,44 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_fwd_small_kernel(
     return;
   }
   __syncwarp();
-  const double* Bs = region + first;
+  const T* Bs = region + first;
   for (int c0 = 0; c0 < n; c0 += 32) {
     const int c = c0 + lane;
     const int emax = min(ns, c0 + 32);   // rows e > c of L11^-T are zero
     if (c < n) {
-      double z0 = 0.0, z1 = 0.0;
+      T z0 = 0, z1 = 0;
       int e = 0;
       for (; e + 1 < emax; e += 2) {
         z0 = fma(Bs[e * n + c], w[e], z0);
         z1 = fma(Bs[(e + 1) * n + c], w[e + 1], z1);
       }
       if (e < emax) z0 = fma(Bs[e * n + c], w[e], z0);
-      const double z = z0 + z1;
+      const double z = (double)(z0 + z1);
       if (c < ns) sbuf[f.sbuf_off + c] = z;
-      else ybuf[f.ybuf_off + c - ns] = w[c] + z;
+      else ybuf[f.ybuf_off + c - ns] = (double)w[c] + z;
     }
   }
 }
 
 // x_s = B [y_s; x_b]: lanes = (row r, column phase h) with R rows x P phases,
 // R the smallest power of two >= min(ns, 32); phases combined by shuffles.
+template <typename T>
 __global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
-    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const double* __restrict__ F,
+    const FrontDev* __restrict__ fr, const int* __restrict__ level, int nfronts, const T* __restrict__ Bsrc,
     const int* __restrict__ idx, const double* __restrict__ sbuf, double* __restrict__ x, int stride, int voff,
     int* __restrict__ err) {
-  extern __shared__ __align__(16) double sh[];
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
   __shared__ uint64_t bar[ND_WPC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int fi = blockIdx.x * ND_WPC + warp;
   const bool has = fi < nfronts;
   const FrontDev f = fr[level[has ? fi : 0]];
   const int ns = f.ns, n = ns + f.nb;
-  double* region = sh + (size_t)warp * stride;
-  double* v = region + voff;
+  T* region = sh + (size_t)warp * stride;
+  T* v = region + voff;
   int first = 0;
-  if (has) nd_stage_block(f, F, region, &bar[warp], lane, &first);
+  if (has) nd_stage_block(f, Bsrc, region, &bar[warp], lane, &first);
   __syncwarp();   // the barrier is initialised before any lane waits on it
   int pid[ND_SMALL_N / 32];
 #pragma unroll
@@ -520,7 +535,7 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
 #pragma unroll
   for (int k = 0; k < ND_SMALL_N / 32; ++k) {
     const int c = lane + 32 * k;
-    if (c < n) v[c] = c < ns ? sbuf[f.sbuf_off + c] : x[pid[k]];
+    if (c < n) v[c] = (T)(c < ns ? sbuf[f.sbuf_off + c] : x[pid[k]]);
   }
   const bool ok = mbar_wait(&bar[warp], 0);
   if (!__all_sync(0xffffffffu, ok)) {
@@ -528,19 +543,19 @@ __global__ void __launch_bounds__(32 * ND_WPC) nd_bwd_small_kernel(
     return;
   }
   __syncwarp();
-  const double* Bs = region + first;
+  const T* Bs = region + first;
   int R = 1;
   while (R < ns && R < 32) R <<= 1;
   const int P = 32 / R, r = lane & (R - 1), h = lane / R;
   for (int e0 = 0; e0 < ns; e0 += R) {
     const int e = e0 + r;
-    double s = 0.0;
+    T s = 0;
     if (e < ns) {
-      const double* row = Bs + e * n;
+      const T* row = Bs + e * n;
       for (int c = (e0 / P) * P + h; c < n; c += P) s = fma(row[c], v[c], s);
     }
     for (int o = R; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (h == 0 && e < ns) x[id[e]] = s;
+    if (h == 0 && e < ns) x[id[e]] = (double)s;
   }
 }
 
@@ -554,8 +569,10 @@ struct NdRowShape {
   int P, rb, ld;   // lanes per row, rows per CTA, shared row stride (doubles, even)
 };
 
+// B^T of the fronts on the row-kernel levels (T = float: the FP32 copy).
+template <typename T>
 __global__ void nd_transpose_kernel(const FrontDev* __restrict__ fr, const int* __restrict__ level,
-                                    const double* __restrict__ F, double* __restrict__ BT) {
+                                    const double* __restrict__ F, T* __restrict__ BT) {
   __shared__ double tile[32][33];
   const FrontDev f = fr[level[blockIdx.z]];
   const int ns = f.ns, n = ns + f.nb;
@@ -569,12 +586,24 @@ __global__ void nd_transpose_kernel(const FrontDev* __restrict__ fr, const int* 
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, e = e0 + threadIdx.x;
-    if (c < n && e < ns) BT[f.bt_off + (long long)c * ns + e] = tile[threadIdx.x][i];
+    if (c < n && e < ns) BT[f.bt_off + (long long)c * ns + e] = (T)tile[threadIdx.x][i];
   }
 }
 
-__device__ __forceinline__ void nd_stage_rows(const double* src, long long len, double* dst, uint64_t* bar, int* first) {
-  const Span16 sp = span16(src, len);
+// The FP32 copy of every front's B (one CTA per front).
+__global__ void nd_copy_b32_kernel(const FrontDev* __restrict__ fr, int nfronts, const double* __restrict__ F,
+                                   float* __restrict__ BF) {
+  for (int fi = blockIdx.x; fi < nfronts; fi += gridDim.x) {
+    const FrontDev f = fr[fi];
+    const long long len = (long long)f.ns * (f.ns + f.nb);
+    const double* src = front_B(f, F);
+    for (long long t = threadIdx.x; t < len; t += blockDim.x) BF[f.bf_off + t] = (float)src[t];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void nd_stage_rows(const T* src, long long len, T* dst, uint64_t* bar, int* first) {
+  const Span16 sp = span16t(src, len);
   *first = sp.first;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -584,19 +613,29 @@ __device__ __forceinline__ void nd_stage_rows(const double* src, long long len, 
   }
 }
 
+// Offset of the vector behind the staged rows: len elements and the span's
+// slack, rounded up to a 16-byte boundary.
+template <typename T>
+__device__ __forceinline__ long long nd_vec_offset(long long len) {
+  constexpr long long g = 16 / sizeof(T);
+  return (len + 2 * (g - 1) + (g - 1)) & ~(g - 1);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) nd_fwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
-                                                           NdRowShape sh_, const double* __restrict__ BT,
+                                                           NdRowShape sh_, const T* __restrict__ BT,
                                                            const int* __restrict__ idx, const int2* __restrict__ gsrc,
                                                            const double* __restrict__ rhs, double* __restrict__ ybuf,
                                                            double* __restrict__ sbuf, int* __restrict__ err) {
-  extern __shared__ __align__(16) double sh[];   // rows [rb][ns] (+slack), then w_s [ns]
+  extern __shared__ __align__(16) unsigned char sh_raw[];   // rows [rb][ns] (+slack), then w_s [ns]
+  T* sh = reinterpret_cast<T*>(sh_raw);
   __shared__ uint64_t bar;
   __shared__ int first_s;
   const NdRows it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int ns = f.ns, n = ns + f.nb;
   const int nr = min(sh_.rb, n - it.row0);
-  double* ws = sh + ((((long long)nr * ns + 2) + 1) & ~1LL);
+  T* ws = sh + nd_vec_offset<T>((long long)nr * ns);
   int first = 0;
   nd_stage_rows(BT + f.bt_off + (long long)it.row0 * ns, (long long)nr * ns, sh, &bar, &first);
   if (threadIdx.x == 0) first_s = first;
@@ -621,9 +660,9 @@ __global__ void __launch_bounds__(256) nd_fwd_rows_kernel(const FrontDev* __rest
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int e = threadIdx.x + 256 * k;
-    if (e < ns) ws[e] = rhs[pid[k]] + nd_gather_row(pgs[k], ybuf);
+    if (e < ns) ws[e] = (T)(rhs[pid[k]] + nd_gather_row(pgs[k], ybuf));
   }
-  for (int e = threadIdx.x + 1024; e < ns; e += blockDim.x) ws[e] = rhs[id[e]] + nd_gather_row(gs[e], ybuf);
+  for (int e = threadIdx.x + 1024; e < ns; e += blockDim.x) ws[e] = (T)(rhs[id[e]] + nd_gather_row(gs[e], ybuf));
   const double wb = nd_gather_row(gsc, ybuf);
   __syncthreads();
   const bool ok = mbar_wait(&bar, 0);
@@ -631,11 +670,11 @@ __global__ void __launch_bounds__(256) nd_fwd_rows_kernel(const FrontDev* __rest
     if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
-  double z = 0.0;
+  T z = 0;
   if (j < nr) {
-    const double* row = sh + first_s + (long long)j * ns;
+    const T* row = sh + first_s + (long long)j * ns;
     const int emax = c < ns ? c : ns - 1;   // L11^-T is upper triangular: B^T row c < ns has e <= c
-    double z1 = 0.0;
+    T z1 = 0;
     int e = h;
     for (; e + P <= emax; e += 2 * P) {
       z = fma(row[e], ws[e], z);
@@ -646,25 +685,27 @@ __global__ void __launch_bounds__(256) nd_fwd_rows_kernel(const FrontDev* __rest
   }
   for (int o = 1; o < P; o <<= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
   if (j < nr && h == 0) {
-    if (c < ns) sbuf[f.sbuf_off + c] = z;
-    else ybuf[f.ybuf_off + c - ns] = wb + z;
+    if (c < ns) sbuf[f.sbuf_off + c] = (double)z;
+    else ybuf[f.ybuf_off + c - ns] = wb + (double)z;
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __restrict__ fr, const NdRows* __restrict__ items,
-                                                           NdRowShape sh_, const double* __restrict__ F,
+                                                           NdRowShape sh_, const T* __restrict__ Bsrc,
                                                            const int* __restrict__ idx, const double* __restrict__ sbuf,
                                                            double* __restrict__ x, int* __restrict__ err) {
-  extern __shared__ __align__(16) double sh[];   // rows [rb][n] (+slack), then v [n]
+  extern __shared__ __align__(16) unsigned char sh_raw[];   // rows [rb][n] (+slack), then v [n]
+  T* sh = reinterpret_cast<T*>(sh_raw);
   __shared__ uint64_t bar;
   __shared__ int first_s;
   const NdRows it = items[blockIdx.x];
   const FrontDev f = fr[it.front];
   const int ns = f.ns, n = ns + f.nb;
   const int nr = min(sh_.rb, ns - it.row0);
-  double* v = sh + ((((long long)nr * n + 2) + 1) & ~1LL);
+  T* v = sh + nd_vec_offset<T>((long long)nr * n);
   int first = 0;
-  nd_stage_rows(F + f.off + (long long)(n + it.row0) * n, (long long)nr * n, sh, &bar, &first);
+  nd_stage_rows(front_B(f, Bsrc) + (long long)it.row0 * n, (long long)nr * n, sh, &bar, &first);
   if (threadIdx.x == 0) first_s = first;
   const int* id = idx + f.idx_off;
   int pid[4];
@@ -683,19 +724,20 @@ __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __rest
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int cc = threadIdx.x + 256 * k;
-    if (cc < n) v[cc] = cc < ns ? sbuf[f.sbuf_off + cc] : x[pid[k]];
+    if (cc < n) v[cc] = (T)(cc < ns ? sbuf[f.sbuf_off + cc] : x[pid[k]]);
   }
-  for (int cc = threadIdx.x + 1024; cc < n; cc += blockDim.x) v[cc] = cc < ns ? sbuf[f.sbuf_off + cc] : x[id[cc]];
+  for (int cc = threadIdx.x + 1024; cc < n; cc += blockDim.x)
+    v[cc] = (T)(cc < ns ? sbuf[f.sbuf_off + cc] : x[id[cc]]);
   __syncthreads();
   const bool ok = mbar_wait(&bar, 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
-  double s = 0.0;
+  T s = 0;
   if (j < nr) {
-    const double* row = sh + first_s + (long long)j * n;
-    double s1 = 0.0;
+    const T* row = sh + first_s + (long long)j * n;
+    T s1 = 0;
     int cc = (e / P) * P + h;   // columns left of row e are zero in L11^-T
     for (; cc + P < n; cc += 2 * P) {
       s = fma(row[cc], v[cc], s);
@@ -705,7 +747,7 @@ __global__ void __launch_bounds__(256) nd_bwd_rows_kernel(const FrontDev* __rest
     s += s1;
   }
   for (int o = 1; o < P; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (j < nr && h == 0) x[id[e]] = s;
+  if (j < nr && h == 0) x[id[e]] = (double)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -717,6 +759,9 @@ struct NdDevice {
   int4* asrc = nullptr;
   double* sbuf = nullptr;
   double* BT = nullptr;       // B^T of the fronts on row-kernel levels
+  float* BF = nullptr;        // FP32 copies of every front's B and of B^T (split-precision
+  float* BTF = nullptr;       // forms, allocated on their first factorisation)
+  long long bf_n = 0, bt_n = 0;
   int nfronts = 0;
   std::vector<NdRows*> fwd_rows, bwd_rows;
   std::vector<int> fwd_n, bwd_n, level_small, level_maxb;
@@ -771,7 +816,7 @@ romb_status coarse_build(romb_ctx* c) {
   // host arrays
   std::vector<FrontDev> fd(nf);
   std::vector<int> idx, children, emap, cells, cell_pos((size_t)c->ncells * 20, -1);
-  long long off = 0, bttot = 0;
+  long long off = 0, bttot = 0, bftot = 0;
   int ybuf = 0, wbuf_tot = 0, sbuf_tot = 0;
   for (int i = 0; i < nf; ++i) {
     const NdFront& F = plan.fronts[i];
@@ -797,6 +842,8 @@ romb_status coarse_build(romb_ctx* c) {
     sbuf_tot += F.ns;
     d.emap_off = -1;
     d.bt_off = -1;
+    d.bf_off = bftot;
+    bftot += (long long)F.ns * n;
   }
   // extend-add positions of each front's update rows in its parent
   for (int i = 0; i < nf; ++i) {
@@ -959,6 +1006,8 @@ romb_status coarse_build(romb_ctx* c) {
   }
   // B^T storage (+2 doubles: bulk copies read 16-byte aligned spans)
   if ((s = romb_alloc_t(c, &D.BT, (size_t)bttot + 2)) != ROMB_OK) return s;
+  D.bf_n = bftot;
+  D.bt_n = bttot;
   // front descriptors last: they carry the tile counts
   ROMB_CUDA(cudaMemcpy(D.fr, fd.data(), sizeof(FrontDev) * nf, cudaMemcpyHostToDevice));
   const int small_smem = 8 * ND_WPC * ND_SMALL_SMEM;
@@ -972,17 +1021,28 @@ romb_status coarse_build(romb_ctx* c) {
     romb_set_error("nested dissection: a coarse front is too wide for the staged solve kernels");
     return ROMB_E_ARG;
   }
-  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(fmax, 16)));
-  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(bmax, 16)));
-  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
-  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(fmax, 16)));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(bmax, 16)));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_fwd_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
+  ROMB_CUDA(cudaFuncSetAttribute(nd_bwd_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem));
   return ROMB_OK;
 }
 
 romb_status coarse_factor(romb_ctx* c) {
   NdDevice& D = g_nd[c];
+  if (c->pre32 && !D.BF) {   // +4 floats: bulk copies read 16-byte aligned spans
+    romb_status s;
+    if ((s = romb_alloc_t(c, &D.BF, (size_t)D.bf_n + 4)) != ROMB_OK) return s;
+    if ((s = romb_alloc_t(c, &D.BTF, (size_t)D.bt_n + 4)) != ROMB_OK) return s;
+  }
   ROMB_CUDA(cudaMemsetAsync(D.bad, 0, 4, c->stream));
   for (size_t l = 0; l < D.level_ids.size(); ++l) {
     const int nfl = D.level_count[l];
@@ -1013,9 +1073,18 @@ romb_status coarse_factor(romb_ctx* c) {
     }
     if (!D.level_small[l] && mns > 0) {   // B^T for the forward row kernel
       const dim3 gt((mn + 31) / 32, (mns + 31) / 32, nfl);
-      nd_transpose_kernel<<<gt, dim3(32, 8), 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.BT); ++c->launches;
+      if (c->pre32)
+        nd_transpose_kernel<float><<<gt, dim3(32, 8), 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.BTF);
+      else
+        nd_transpose_kernel<double><<<gt, dim3(32, 8), 0, c->stream>>>(D.fr, D.level_ids[l], D.F, D.BT);
+      ++c->launches;
       ROMB_CUDA(cudaGetLastError());
     }
+  }
+  if (c->pre32) {   // the solves of the split-precision forms read B in FP32
+    nd_copy_b32_kernel<<<std::min(D.nfronts, 8 * c->sms), 256, 0, c->stream>>>(D.fr, D.nfronts, D.F, D.BF);
+    ++c->launches;
+    ROMB_CUDA(cudaGetLastError());
   }
   int bad = 0;
   ROMB_CUDA(cudaMemcpyAsync(&bad, D.bad, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1054,27 +1123,29 @@ romb_status coarse_lane_buffers(romb_ctx* c, double** ybuf, double** sbuf) {
   return romb_alloc_t(c, sbuf, (size_t)D.sbuf_n);
 }
 
-romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st, double* ybuf,
-                         double* sbuf) {
+template <typename T>
+static romb_status coarse_solve_t(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st, double* ybuf,
+                                  double* sbuf, const T* Bsrc, const T* BTsrc) {
   NdDevice& D = g_nd[c];
   ROMB_CUDA(cudaMemsetAsync(d_out, 0, 8 * c->ncoarse_all, st));
   const int L = (int)D.level_ids.size();
+  constexpr int g = 16 / (int)sizeof(T);   // elements per 16 bytes
   auto small_shape = [&](int l, int* stride, int* voff) {
-    *voff = (D.level_maxb[l] + 2 + 1) & ~1;             // B block + alignment slack, even
-    *stride = (*voff + D.level_maxn[l] + 1) & ~1;       // + one vector, even (16-byte regions)
+    *voff = (D.level_maxb[l] + 2 * (g - 1) + (g - 1)) & ~(g - 1);   // B block + span slack, 16-byte aligned
+    *stride = (*voff + D.level_maxn[l] + (g - 1)) & ~(g - 1);       // + one vector (16-byte regions)
   };
   for (int l = 0; l < L; ++l) {
     if (D.level_small[l]) {
       int stride, voff;
       small_shape(l, &stride, &voff);
-      ROMB_CUDA(launch_pdl(nd_fwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
-                           8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
-                           (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
+      ROMB_CUDA(launch_pdl(nd_fwd_small_kernel<T>, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
+                           sizeof(T) * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
+                           (const int*)D.level_ids[l], D.level_count[l], Bsrc, (const int*)D.idx,
                            (const int2*)D.gsrc, d_in, ybuf, sbuf, stride, voff, D.err));
       ++c->launches;
     } else if (D.fwd_n[l]) {
-      ROMB_CUDA(launch_pdl(nd_fwd_rows_kernel, D.fwd_n[l], 256, D.fwd_smem[l], st, (const FrontDev*)D.fr,
-                           (const NdRows*)D.fwd_rows[l], D.fwd_shape[l], (const double*)D.BT, (const int*)D.idx,
+      ROMB_CUDA(launch_pdl(nd_fwd_rows_kernel<T>, D.fwd_n[l], 256, D.fwd_smem[l], st, (const FrontDev*)D.fr,
+                           (const NdRows*)D.fwd_rows[l], D.fwd_shape[l], BTsrc, (const int*)D.idx,
                            (const int2*)D.gsrc, d_in, ybuf, sbuf, D.err));
       ++c->launches;
     }
@@ -1083,20 +1154,29 @@ romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStr
     if (D.level_small[l]) {
       int stride, voff;
       small_shape(l, &stride, &voff);
-      ROMB_CUDA(launch_pdl(nd_bwd_small_kernel, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
-                           8 * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
-                           (const int*)D.level_ids[l], D.level_count[l], (const double*)D.F, (const int*)D.idx,
+      ROMB_CUDA(launch_pdl(nd_bwd_small_kernel<T>, (D.level_count[l] + ND_WPC - 1) / ND_WPC, 32 * ND_WPC,
+                           sizeof(T) * ND_WPC * (size_t)stride, st, (const FrontDev*)D.fr,
+                           (const int*)D.level_ids[l], D.level_count[l], Bsrc, (const int*)D.idx,
                            (const double*)sbuf, d_out, stride, voff, D.err));
       ++c->launches;
     } else if (D.bwd_n[l]) {
-      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel, D.bwd_n[l], 256, D.bwd_smem[l], st, (const FrontDev*)D.fr,
-                           (const NdRows*)D.bwd_rows[l], D.bwd_shape[l], (const double*)D.F, (const int*)D.idx,
+      ROMB_CUDA(launch_pdl(nd_bwd_rows_kernel<T>, D.bwd_n[l], 256, D.bwd_smem[l], st, (const FrontDev*)D.fr,
+                           (const NdRows*)D.bwd_rows[l], D.bwd_shape[l], Bsrc, (const int*)D.idx,
                            (const double*)sbuf, d_out, D.err));
       ++c->launches;
     }
   }
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
+}
+
+// out = S_C^-1 in over the coarse DoFs that exist (the others of out are 0);
+// the split-precision forms run the substitutions in FP32.
+romb_status coarse_solve(romb_ctx* c, const double* d_in, double* d_out, cudaStream_t st, double* ybuf,
+                         double* sbuf) {
+  NdDevice& D = g_nd[c];
+  if (c->pre32) return coarse_solve_t<float>(c, d_in, d_out, st, ybuf, sbuf, (const float*)D.BF, (const float*)D.BTF);
+  return coarse_solve_t<double>(c, d_in, d_out, st, ybuf, sbuf, (const double*)D.F, (const double*)D.BT);
 }
 
 // Reports (and clears) a staging timeout of the solve kernels since the last call.

@@ -84,26 +84,29 @@ __global__ void skel_gather_kernel(CellParams P, const double* __restrict__ loc,
 // modes: y = M v (the operators S and D F D); c = Phi^T v (coarse restriction)
 #define CA_MATVEC 0
 #define CA_RESTRICT 2
+// The element type T of M and Phi: double, or float for the preconditioner's
+// operators (D F D and Phi) of the split-precision forms; v, y and c stay
+// double in memory, the products and sums run in T.
 template <int P>
 struct CellApplyShape {
   static constexpr int NU = 8 * P, WARPS = (NU + 15) / 16, THREADS = 32 * WARPS;
-  static constexpr int stage_bytes(int mode) {
-    return (mode != CA_RESTRICT ? NU * NU * 8 : 0) + (mode != CA_MATVEC ? NU * 20 * 8 : 0) + NU * 4;
+  static constexpr int stage_bytes(int mode, int esize) {
+    return (mode != CA_RESTRICT ? NU * NU * esize : 0) + (mode != CA_MATVEC ? NU * 20 * esize : 0) + NU * 4;
   }
 };
 
-template <int P, int MODE>
+template <int P, int MODE, typename T>
 __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
-    int ncells, const double* __restrict__ M, const int* __restrict__ umap, const double* __restrict__ v,
-    double* __restrict__ yloc, const double* __restrict__ Phi, double* __restrict__ cloc, int* __restrict__ err) {
+    int ncells, const T* __restrict__ M, const int* __restrict__ umap, const double* __restrict__ v,
+    double* __restrict__ yloc, const T* __restrict__ Phi, double* __restrict__ cloc, int* __restrict__ err) {
   using Sh = CellApplyShape<P>;
   constexpr bool HAS_M = MODE != CA_RESTRICT, COARSE = MODE != CA_MATVEC;
-  constexpr int NU = Sh::NU, H = NU / 2, NT = Sh::THREADS;
-  constexpr int MB = HAS_M ? NU * NU * 8 : 0, PB = COARSE ? NU * 20 * 8 : 0, SB = MB + PB + NU * 4;
+  constexpr int NU = Sh::NU, H = NU / 2, NT = Sh::THREADS, ES = (int)sizeof(T);
+  constexpr int MB = HAS_M ? NU * NU * ES : 0, PB = COARSE ? NU * 20 * ES : 0, SB = MB + PB + NU * 4;
   extern __shared__ __align__(16) unsigned char ring[];
   __shared__ uint64_t full[CA_STAGES];
-  __shared__ double sv[2][NU];
-  __shared__ double cpart[2][4][20];
+  __shared__ T sv[2][NU];
+  __shared__ T cpart[2][4][20];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmine = blockIdx.x < ncells ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   auto cell_of = [&](int j) { return (long long)blockIdx.x + (long long)j * gridDim.x; };
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
     mbar_expect_tx(bar, SB);
     if (HAS_M) bulk_g2s(st, M + cell * NU * NU, MB, bar);
     if (COARSE) bulk_g2s(st + MB, Phi + cell * NU * 20, PB, bar);
+    static_assert(MB % 16 == 0 && PB % 16 == 0 && (NU * 4) % 16 == 0, "bulk copies of whole 16-byte units");
     bulk_g2s(st + MB + PB, umap + cell * NU, NU * 4, bar);
   };
   if (tid == 0) {
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
     ok = mbar_wait(&full[0], 0);
     if (ok) {
       const int* us = reinterpret_cast<const int*>(ring + MB + PB);
-      for (int u = tid; u < NU; u += NT) sv[0][u] = us[u] >= 0 ? v[us[u]] : 0.0;
+      for (int u = tid; u < NU; u += NT) sv[0][u] = us[u] >= 0 ? (T)v[us[u]] : (T)0;
     }
   }
   if (__syncthreads_or(!ok)) {
@@ -139,25 +143,25 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
   for (int j = 0; j < nmine; ++j) {
     const long long cell = cell_of(j);
     const unsigned char* st = ring + (size_t)(j % CA_STAGES) * SB;
-    const double* Ms = reinterpret_cast<const double*>(st);
-    const double* x = sv[j & 1];
+    const T* Ms = reinterpret_cast<const T*>(st);
+    const T* x = sv[j & 1];
     // y = M_c v: lane (r, q) sums k in [q H, q H + H) of M[k][r] v[k] (M symmetric)
     if (HAS_M) {
-      double acc = 0.0;
+      T acc = 0;
       if (r < NU) {
-        const double* mk = Ms + q * H * NU + r;
+        const T* mk = Ms + q * H * NU + r;
 #pragma unroll 8
         for (int k = 0; k < H; ++k) acc = fma(mk[k * NU], x[q * H + k], acc);
       }
       acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-      if (q == 0 && r < NU) yloc[cell * NU + r] = acc;
+      if (q == 0 && r < NU) yloc[cell * NU + r] = (double)acc;
     }
     if (COARSE) {
       // c = Phi^T v: thread (j, part) sums a quarter of the slots
-      const double* Ps = reinterpret_cast<const double*>(st + MB);
+      const T* Ps = reinterpret_cast<const T*>(st + MB);
       for (int t = tid; t < 80; t += NT) {
         const int jj = t % 20, part = t / 20;
-        double a = 0.0;
+        T a = 0;
         for (int u = part * (NU / 4); u < (part + 1) * (NU / 4); ++u) a = fma(Ps[u * 20 + jj], x[u], a);
         cpart[j & 1][part][jj] = a;
       }
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
       ok = mbar_wait(&full[(j + 1) % CA_STAGES], (uint32_t)(((j + 1) / CA_STAGES) & 1));
       if (ok) {
         const int* us = reinterpret_cast<const int*>(ring + (size_t)((j + 1) % CA_STAGES) * SB + MB + PB);
-        for (int u = tid; u < NU; u += NT) sv[(j + 1) & 1][u] = us[u] >= 0 ? v[us[u]] : 0.0;
+        for (int u = tid; u < NU; u += NT) sv[(j + 1) & 1][u] = us[u] >= 0 ? (T)v[us[u]] : (T)0;
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -175,32 +179,42 @@ __global__ void __launch_bounds__(CellApplyShape<P>::THREADS) cell_apply_kernel(
       return;
     }
     if (COARSE && tid < 20)
-      cloc[cell * 20 + tid] = (cpart[j & 1][0][tid] + cpart[j & 1][1][tid]) + (cpart[j & 1][2][tid] + cpart[j & 1][3][tid]);
+      cloc[cell * 20 + tid] =
+          (double)((cpart[j & 1][0][tid] + cpart[j & 1][1][tid]) + (cpart[j & 1][2][tid] + cpart[j & 1][3][tid]));
     if (tid == 0 && j + CA_STAGES < nmine) issue(j + CA_STAGES);   // stage j % CA_STAGES is free
   }
 }
 
-// y_loc += Phi g_loc  (coarse prolongation, Algorithm 1); half-warp per cell
-__global__ void __launch_bounds__(256) cell_prolong_kernel(int ncells, int NU, const double* __restrict__ Phi,
+// y_loc += Phi g_loc  (coarse prolongation, Algorithm 1); half-warp per cell.
+// T = float (the split-precision forms): Phi g summed in FP32, then added.
+template <typename T>
+__global__ void __launch_bounds__(256) cell_prolong_kernel(int ncells, int NU, const T* __restrict__ Phi,
                                                             const int* __restrict__ cmap, const double* __restrict__ g,
                                                             double* __restrict__ yloc) {
-  __shared__ double sg[16][20];
+  __shared__ T sg[16][20];
   const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
   const long long cell0 = (long long)blockIdx.x * 16 + slot;
   const bool active = cell0 < ncells;
   const long long cell = active ? cell0 : 0;
   for (int j = hl; j < 20; j += 16) {
     const int k = active ? cmap[cell * 20 + j] : -1;
-    sg[slot][j] = k >= 0 ? g[k] : 0.0;
+    sg[slot][j] = k >= 0 ? (T)g[k] : (T)0;
   }
   __syncwarp();
   if (!active) return;
-  const double* Pc = Phi + cell * NU * 20;
+  const T* Pc = Phi + cell * NU * 20;
   for (int u = hl; u < NU; u += 16) {
-    double acc = yloc[cell * NU + u];
+    if constexpr (sizeof(T) == 8) {
+      double acc = yloc[cell * NU + u];
 #pragma unroll
-    for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[slot][j], acc);
-    yloc[cell * NU + u] = acc;
+      for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[slot][j], acc);
+      yloc[cell * NU + u] = acc;
+    } else {
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < 20; ++j) acc = fma(Pc[u * 20 + j], sg[slot][j], acc);
+      yloc[cell * NU + u] += (double)acc;
+    }
   }
 }
 
@@ -686,37 +700,39 @@ static int grid_for(const romb_ctx* c, long long n) {
 // z = S_BDDC^-1 r  (Algorithm 1)
 // prepare = true (outside stream capture): set the shared-memory limit and size
 // the persistent grid (resident CTAs per SM x SMs); prepare = false: launch.
-template <int P, int MODE>
-static romb_status cell_apply_p(romb_ctx* c, cudaStream_t st, bool prepare, const double* M, const double* v,
-                                double* yloc, double* cloc, int grid_override) {
+template <int P, int MODE, typename T>
+static romb_status cell_apply_p(romb_ctx* c, cudaStream_t st, bool prepare, const T* M, const double* v,
+                                double* yloc, double* cloc, int grid_override, const T* Phi) {
   using Sh = CellApplyShape<P>;
-  const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(MODE);
+  const size_t smem = (size_t)CA_STAGES * Sh::stage_bytes(MODE, (int)sizeof(T));
+  const int gi = MODE + (sizeof(T) == 4 ? 1 : 0);   // persistent grid per mode and element type
   if (prepare) {
-    ROMB_CUDA(cudaFuncSetAttribute(cell_apply_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ROMB_CUDA(cudaFuncSetAttribute(cell_apply_kernel<P, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
     int per_sm = 0;
-    ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_apply_kernel<P, MODE>, Sh::THREADS, smem));
-    c->ca_grid[MODE] = std::max(1, std::min(c->ncells, std::max(1, per_sm) * c->sms));
+    ROMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_apply_kernel<P, MODE, T>, Sh::THREADS,
+                                                            smem));
+    c->ca_grid[gi] = std::max(1, std::min(c->ncells, std::max(1, per_sm) * c->sms));
     return ROMB_OK;
   }
-  const int grid = grid_override > 0 ? std::min(grid_override, c->ca_grid[MODE]) : c->ca_grid[MODE];
-  cell_apply_kernel<P, MODE><<<grid, Sh::THREADS, smem, st>>>(c->ncells, M, c->d_ucell_map, v, yloc, c->d_Phi, cloc,
-                                                              c->d_pcg_err);
+  const int grid = grid_override > 0 ? std::min(grid_override, c->ca_grid[gi]) : c->ca_grid[gi];
+  cell_apply_kernel<P, MODE, T><<<grid, Sh::THREADS, smem, st>>>(c->ncells, M, c->d_ucell_map, v, yloc, Phi, cloc,
+                                                                 c->d_pcg_err);
   ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
-template <int MODE>
-static romb_status cell_apply(romb_ctx* c, cudaStream_t st, bool prepare, const double* M, const double* v,
-                              double* yloc, double* cloc, int grid_override = 0) {
+template <int MODE, typename T = double>
+static romb_status cell_apply(romb_ctx* c, cudaStream_t st, bool prepare, const T* M, const double* v,
+                              double* yloc, double* cloc, int grid_override = 0, const T* Phi = nullptr) {
   switch (c->p) {
-    case 3: return cell_apply_p<3, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
-    case 4: return cell_apply_p<4, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
-    case 5: return cell_apply_p<5, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
-    case 6: return cell_apply_p<6, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
-    case 7: return cell_apply_p<7, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
-    case 8: return cell_apply_p<8, MODE>(c, st, prepare, M, v, yloc, cloc, grid_override);
+    case 3: return cell_apply_p<3, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
+    case 4: return cell_apply_p<4, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
+    case 5: return cell_apply_p<5, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
+    case 6: return cell_apply_p<6, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
+    case 7: return cell_apply_p<7, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
+    case 8: return cell_apply_p<8, MODE, T>(c, st, prepare, M, v, yloc, cloc, grid_override, Phi);
   }
   return ROMB_E_ARG;
 }
@@ -724,7 +740,9 @@ static romb_status cell_apply(romb_ctx* c, cudaStream_t st, bool prepare, const 
 static romb_status precondition(romb_ctx* c, PcgLane& L, const CellParams& P, const double* r, double* z) {
   // restriction c = Phi^T r, then the coarse correction on the side stream
   // while the fine part y = D F D r runs here; join before the prolongation
-  romb_status s = cell_apply<CA_RESTRICT>(c, L.stream, false, nullptr, r, nullptr, L.d_cloc);
+  romb_status s = c->pre32 ? cell_apply<CA_RESTRICT, float>(c, L.stream, false, nullptr, r, nullptr, L.d_cloc, 0,
+                                                             c->d_Phi32)
+                           : cell_apply<CA_RESTRICT, double>(c, L.stream, false, nullptr, r, nullptr, L.d_cloc, 0, c->d_Phi);
   if (s != ROMB_OK) return s;
   double* zc = L.d_coarse;
   double* gc = L.d_coarse + c->ncoarse_all;
@@ -736,17 +754,23 @@ static romb_status precondition(romb_ctx* c, PcgLane& L, const CellParams& P, co
   if ((s = coarse_solve(c, zc, gc, L.side, L.nd_ybuf, L.nd_sbuf)) != ROMB_OK) return s;
   ROMB_CUDA(cudaEventRecord(L.evjoin, L.side));
   // one CTA per SM: the rest of each SM stays free for the coarse chain
-  if ((s = cell_apply<CA_MATVEC>(c, L.stream, false, c->d_G, r, L.d_yloc, nullptr, c->sms)) != ROMB_OK) return s;
+  s = c->pre32 ? cell_apply<CA_MATVEC, float>(c, L.stream, false, c->d_G32, r, L.d_yloc, nullptr, c->sms)
+               : cell_apply<CA_MATVEC, double>(c, L.stream, false, c->d_G, r, L.d_yloc, nullptr, c->sms);
+  if (s != ROMB_OK) return s;
   ROMB_CUDA(cudaStreamWaitEvent(L.stream, L.evjoin, 0));
   const int cb = (c->ncells + 15) / 16;
-  cell_prolong_kernel<<<cb, 256, 0, L.stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, L.d_yloc); ++c->launches;
+  if (c->pre32)
+    cell_prolong_kernel<float><<<cb, 256, 0, L.stream>>>(c->ncells, c->nU, c->d_Phi32, c->d_cmap, gc, L.d_yloc);
+  else
+    cell_prolong_kernel<double><<<cb, 256, 0, L.stream>>>(c->ncells, c->nU, c->d_Phi, c->d_cmap, gc, L.d_yloc);
+  ++c->launches;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_yloc, c->nskel_nodes, z); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
   return ROMB_OK;
 }
 
 static romb_status apply_S(romb_ctx* c, PcgLane& L, const CellParams& P, const double* v, double* out) {
-  romb_status s0 = cell_apply<CA_MATVEC>(c, L.stream, false, c->d_S, v, L.d_yloc, nullptr);
+  romb_status s0 = cell_apply<CA_MATVEC, double>(c, L.stream, false, c->d_S, v, L.d_yloc, nullptr);
   if (s0 != ROMB_OK) return s0;
   skel_gather_kernel<<<grid_for(c, c->nskel_nodes), 256, 0, L.stream>>>(P, L.d_yloc, c->nskel_nodes, out); ++c->launches;
   ROMB_CUDA(cudaGetLastError());
@@ -959,8 +983,14 @@ romb_status pcg_finish(romb_ctx* c, PcgLane& L, double rtol, int maxit) {
     // the loop (or, where the CUDA driver cannot build it, one iteration) is captured
     // once per factorisation and lane and replayed
     if (!L.graph) {
-      if ((s = cell_apply<CA_MATVEC>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
-      if ((s = cell_apply<CA_RESTRICT>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<CA_MATVEC, double>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if ((s = cell_apply<CA_RESTRICT, double>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK) return s;
+      if (c->pre32) {
+        if ((s = cell_apply<CA_MATVEC, float>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK)
+          return s;
+        if ((s = cell_apply<CA_RESTRICT, float>(c, L.stream, true, nullptr, nullptr, nullptr, nullptr)) != ROMB_OK)
+          return s;
+      }
       // ROMB_PCG_HOST_LOOP=1 keeps the loop on the host (one graph launch per
       // iteration): profilers cannot replay kernels inside conditional nodes.
       const char* hl = getenv("ROMB_PCG_HOST_LOOP");

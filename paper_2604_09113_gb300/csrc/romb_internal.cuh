@@ -223,7 +223,13 @@ struct romb_ctx {
   double* d_red = nullptr;
   double* h_red = nullptr;      // pinned host copy
   int* d_pcg_err = nullptr;     // set by a PCG cell kernel whose staging copy timed out
-  int ca_grid[3] = {0, 0, 0};   // persistent grid of the cell operator kernels per mode
+  int ca_grid[4] = {0, 0, 0, 0};   // persistent grid of the cell operator kernels per mode (+1: FP32)
+  // split-precision forms: the preconditioner's operators D F D and Phi (and
+  // the coarse solve's B) in FP32, set by romb_factor
+  bool pre32 = false;
+  int precond_mode = -1;        // romb_set_precond_precision (survives a new lattice)
+  float* d_G32 = nullptr;       // [cells][nU][nU]
+  float* d_Phi32 = nullptr;     // [cells][nU][20]
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
   PcgLane lane[ROMB_MAX_LANES]; // PCG solves (see PcgLane)
 
