@@ -908,8 +908,10 @@ def run_workload7(a):
         times, its = _timed(torch, stream, flush, a.steps, lambda: (step(forms[form]), romb.romb_stats(ctx.h)[0].copy()))
         ms = sum(times) / len(times)
         ph = np.mean(np.array([p_ for _, p_ in its]), axis=0)
+        _, flags = romb.romb_stats(ctx.h, cells)
         entry = {"cells": cells, "grid": f"{lat.nx}x{lat.ny}", "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
                  "pcg_iters": its[-1][0], "paper_iters": paper_its,
+                 "exact_fallback_cells": int(np.count_nonzero(flags & 16)),
                  "phase_ms": {n: float(v) for n, v in zip(names, ph)}}
         if not a.no_accuracy:
             v = u.clone()

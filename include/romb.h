@@ -266,9 +266,22 @@ romb_status romb_set_body_force(romb_ctx* ctx, double bx, double by);
 /* Phase timings (ms, CUDA events) of the last calls: [0] theta, Chat and the
  * coarse DoFs' edge functionals, [1] contraction,
  * [2] local factor, [3] coarse assembly + factor, [4] PCG, [5] recovery,
- * [6] host<->device copies, [7] total.  flags_out: [nx*ny] per-cell error bits
- * (1 out of box, 2 bad map, 4 not SPD, 8 non-finite); either may be NULL. */
+ * [6] host<->device copies, [7] total.  flags_out: [ncells] per-cell bits
+ * (1 out of box, 2 bad map, 4 not SPD, 8 non-finite, 16 assembled by the
+ * exact fallback of romb_set_exact_fallback); either may be NULL. */
 romb_status romb_stats(romb_ctx* ctx, double* phase_ms, int* flags_out);
+
+/* Fallback for cells whose reduced-model stiffness is not positive definite
+ * (the MDEIM error of a nearly void cell can exceed the alpha-stabilisation
+ * rho I_Pi; Sec. 4.3 asks to retrain such models).  On (default), when
+ * romb_factor meets a non-positive pivot in at most max_cells cells of a
+ * reduced-model assembly, it integrates those cells' tensors I(mu) exactly
+ * (the trimmed quadrature of the GPU trainer), forms their K by Algorithm 4
+ * in FP64 (theta of the cell set to (rho, 1 - rho) against [I_Pi; I(mu)]),
+ * marks them with flag 16 and factorises again; a second failure returns
+ * ROMB_E_NOT_SPD.  Off (max_cells = 0): the failure is returned at once.
+ * Errors: ROMB_E_ARG (max_cells < 0). */
+romb_status romb_set_exact_fallback(romb_ctx* ctx, int max_cells);
 
 /* Number of CUDA kernels this context has launched since romb_create. */
 long long romb_launch_count(romb_ctx* ctx);

@@ -74,6 +74,7 @@ def _load():
         "romb_set_load_form": ([P, I], I),
         "romb_set_body_force": ([P, D, D], I),
         "romb_set_precond_precision": ([P, I], I),
+        "romb_set_exact_fallback": ([P, I], I),
         "romb_train_gpu_clustered": ([I, ctypes.POINTER(RombTrainSpec), I, P, I, ctypes.c_char_p], I),
     }
     for name, (args, res) in sig.items():
@@ -202,6 +203,13 @@ def romb_set_precond_precision(ctx, mode: int) -> None:
     or ROMB_PRECOND_FP32: the precision of the preconditioner's operators from
     the next romb_factor on."""
     _check(_lib.romb_set_precond_precision(ctx, int(mode)), "romb_set_precond_precision")
+
+
+def romb_set_exact_fallback(ctx, max_cells: int) -> None:
+    """Cells (at most max_cells; 0: off) whose reduced-model stiffness is not
+    positive definite are assembled from their exact tensors and factorised
+    again (per-cell flag 16)."""
+    _check(_lib.romb_set_exact_fallback(ctx, int(max_cells)), "romb_set_exact_fallback")
 
 
 def romb_set_body_force(ctx, bx: float, by: float) -> None:

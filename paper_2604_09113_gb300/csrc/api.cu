@@ -99,7 +99,7 @@ void romb_free_lattice(romb_ctx* c) {
   for (int i = 0; i < 16; ++i) ev[i] = c->ev[i];
   // lanes keep their streams, events and pinned words; their device buffers
   // went with the lattice
-  const int load_form = c->load_form, precond_mode = c->precond_mode;
+  const int load_form = c->load_form, precond_mode = c->precond_mode, fallback_max = c->fallback_max;
   const double body[2] = {c->body[0], c->body[1]};
   PcgLane lanes[ROMB_MAX_LANES];
   for (int k = 0; k < ROMB_MAX_LANES; ++k) {
@@ -119,6 +119,7 @@ void romb_free_lattice(romb_ctx* c) {
   for (int k = 0; k < ROMB_MAX_LANES; ++k) c->lane[k] = lanes[k];
   c->load_form = load_form;
   c->precond_mode = precond_mode;
+  c->fallback_max = fallback_max;
   c->body[0] = body[0];
   c->body[1] = body[1];
   for (int i = 0; i < ROMB_MAX_MODELS; ++i) c->roms[i] = roms[i];
@@ -831,6 +832,82 @@ __global__ void to_f32_kernel(long long n, const double* __restrict__ src, float
     dst[i] = (float)src[i];
 }
 
+// Cells flagged not positive definite after a reduced-model assembly (at most
+// fallback_max): their tensors I(mu) by the trainer's exact trimmed
+// quadrature, K by the FP64 contraction against U' = [I_Pi; I(mu)] with theta
+// = (rho, 1 - rho), flag NOT_SPD replaced by EXACT.  *applied: cells were redone.
+static romb_status exact_fallback(romb_ctx* c, bool* applied) {
+  *applied = false;
+  if (c->fallback_max <= 0 || !c->assembled_rom) return ROMB_OK;
+  const long long n = c->ncells;
+  std::vector<int32_t> flags((size_t)n);
+  ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  ROMB_CUDA(cudaMemcpy(flags.data(), c->d_flags, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  std::vector<int> bad;
+  for (long long i = 0; i < n; ++i)
+    if ((flags[i] & ROMB_FLAG_NOT_SPD) && !(flags[i] & ROMB_FLAG_EXACT)) bad.push_back((int)i);
+  if (bad.empty() || (int)bad.size() > c->fallback_max) return ROMB_OK;
+  std::vector<double> mu(4 * (size_t)n);
+  std::vector<int32_t> slot((size_t)n);
+  ROMB_CUDA(cudaMemcpy(mu.data(), c->d_mu, 32 * (size_t)n, cudaMemcpyDeviceToHost));
+  ROMB_CUDA(cudaMemcpy(slot.data(), c->d_slot, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  romb_status s;
+  double* dU = nullptr;
+  int* dlist = nullptr;
+  long long dU_n = 0;
+  if ((s = romb_alloc_t(c, &dlist, 1)) != ROMB_OK) return s;
+  for (int b : bad) {
+    const RombRom& R = c->roms[slot[b]];
+    romb_train_spec sp = {};
+    sp.family = R.family;
+    sp.basis = R.kind;
+    sp.p = R.p;
+    sp.q = R.q;
+    sp.r = R.r;
+    sp.n_r = R.n_r;
+    sp.lo = R.lo4[0];
+    sp.hi = R.hi4[0];
+    const int nB = (R.p + 1) * (R.p + 1), nL = (R.q + 1) * (R.q + 1);
+    const long long n_i = (long long)nB * nB * nL * 4;
+    std::vector<double> I((size_t)n_i);
+    if ((s = romb_train_snapshots_gpu(c->device, &sp, &mu[4 * (size_t)b], 1, I.data())) != ROMB_OK) return s;
+    ROMB_CUDA(cudaSetDevice(c->device));
+    if (dU_n < 2 * R.n_half) {
+      if (dU) romb_free_ptr(c, dU);
+      if ((s = romb_alloc_t(c, &dU, 2 * (size_t)R.n_half)) != ROMB_OK) return s;
+      dU_n = 2 * R.n_half;
+    }
+    // row 1 of U': I(mu) in the pair-major half layout (row 0: the model's I_Pi)
+    std::vector<double> row((size_t)R.n_half);
+    long long pr = 0;
+    for (int k1 = 0; k1 < nB; ++k1)
+      for (int k2 = k1; k2 < nB; ++k2, ++pr)
+        for (int e = 0; e < nL * 4; ++e) row[(size_t)(pr * nL * 4 + e)] = I[(size_t)(((long long)k1 * nB + k2) * nL * 4 + e)];
+    std::vector<double> th(128, 0.0);
+    th[0] = c->rho;
+    th[1] = 1.0 - c->rho;
+    ROMB_CUDA(cudaMemcpy(dU, R.U64, 8 * (size_t)R.n_half, cudaMemcpyDeviceToDevice));
+    ROMB_CUDA(cudaMemcpy(dU + R.n_half, row.data(), 8 * (size_t)R.n_half, cudaMemcpyHostToDevice));
+    ROMB_CUDA(cudaMemcpy(c->d_theta + 128 * (size_t)b, th.data(), 8 * 128, cudaMemcpyHostToDevice));
+    ROMB_CUDA(cudaMemcpy(dlist, &b, 4, cudaMemcpyHostToDevice));
+    if ((s = launch_assemble_cells_fp64(c, dU, R.n_half, 2, dlist, 1)) != ROMB_OK) return s;
+    ROMB_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  if (dU) romb_free_ptr(c, dU);
+  romb_free_ptr(c, dlist);
+  for (long long i = 0; i < n; ++i) flags[i] &= ~ROMB_FLAG_NOT_SPD;
+  for (int b : bad) flags[b] |= ROMB_FLAG_EXACT;
+  ROMB_CUDA(cudaMemcpy(c->d_flags, flags.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+  *applied = true;
+  return ROMB_OK;
+}
+
+extern "C" romb_status romb_set_exact_fallback(romb_ctx* c, int max_cells) {
+  if (!c || max_cells < 0) return ROMB_E_ARG;
+  c->fallback_max = max_cells;
+  return ROMB_OK;
+}
+
 extern "C" romb_status romb_factor(romb_ctx* c) {
   if (!c) return ROMB_E_ARG;
   if (!c->assembled) return ROMB_E_STATE;
@@ -844,22 +921,32 @@ extern "C" romb_status romb_factor(romb_ctx* c) {
   // the split-precision forms apply the preconditioner in FP32 (the operator
   // S and the PCG vectors stay FP64): D F D, Phi and the coarse solve's B
   c->pre32 = c->precond_mode < 0 ? c->assembled_split : c->precond_mode == 1;
-  cudaEventRecord(c->ev[3], c->stream);
-  if ((s = launch_ktot(c)) != ROMB_OK) return s;
-  if ((s = launch_factor(c)) != ROMB_OK) return s;
-  cudaEventRecord(c->ev[4], c->stream);
-  if ((s = coarse_factor(c)) != ROMB_OK) return s;
-  if (c->pre32) {
-    const long long nG = (long long)c->ncells * c->nU * c->nU, nP = (long long)c->ncells * c->nU * ROMB_NSLOT;
-    if (!c->d_G32 && (s = romb_alloc_t(c, &c->d_G32, (size_t)nG)) != ROMB_OK) return s;
-    if (!c->d_Phi32 && (s = romb_alloc_t(c, &c->d_Phi32, (size_t)nP)) != ROMB_OK) return s;
-    to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nG, c->d_G, c->d_G32);
-    to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nP, c->d_Phi, c->d_Phi32);
-    c->launches += 2;
-    ROMB_CUDA(cudaGetLastError());
+  for (int attempt = 0;; ++attempt) {
+    cudaEventRecord(c->ev[3], c->stream);
+    if ((s = launch_ktot(c)) != ROMB_OK) return s;
+    if ((s = launch_factor(c)) != ROMB_OK) return s;
+    cudaEventRecord(c->ev[4], c->stream);
+    s = coarse_factor(c);
+    if (s == ROMB_OK && c->pre32) {
+      const long long nG = (long long)c->ncells * c->nU * c->nU, nP = (long long)c->ncells * c->nU * ROMB_NSLOT;
+      if (!c->d_G32 && (s = romb_alloc_t(c, &c->d_G32, (size_t)nG)) != ROMB_OK) return s;
+      if (!c->d_Phi32 && (s = romb_alloc_t(c, &c->d_Phi32, (size_t)nP)) != ROMB_OK) return s;
+      to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nG, c->d_G, c->d_G32);
+      to_f32_kernel<<<4 * c->sms, 256, 0, c->stream>>>(nP, c->d_Phi, c->d_Phi32);
+      c->launches += 2;
+      ROMB_CUDA(cudaGetLastError());
+    }
+    cudaEventRecord(c->ev[5], c->stream);
+    if (s == ROMB_OK) s = check_flags(c, ROMB_FLAG_NOT_SPD | ROMB_FLAG_NAN);
+    if (s == ROMB_E_NOT_SPD && attempt == 0) {   // cells whose reduced K lost definiteness
+      bool applied = false;
+      romb_status s2 = exact_fallback(c, &applied);
+      if (s2 != ROMB_OK) return s2;
+      if (applied) continue;
+    }
+    if (s != ROMB_OK) return s;
+    break;
   }
-  cudaEventRecord(c->ev[5], c->stream);
-  if ((s = check_flags(c, ROMB_FLAG_NOT_SPD | ROMB_FLAG_NAN)) != ROMB_OK) return s;
   c->phase_ms[2] = ms_between(c->ev[3], c->ev[4]);
   c->phase_ms[3] = ms_between(c->ev[4], c->ev[5]);
   c->factored = true;

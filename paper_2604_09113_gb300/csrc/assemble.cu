@@ -639,6 +639,21 @@ romb_status launch_assemble_fp64(romb_ctx* c) {
   return ROMB_OK;
 }
 
+// The FP64 contraction for a list of cells against a given U' (K rows, half
+// layout) and the cells' own theta rows.
+romb_status launch_assemble_cells_fp64(romb_ctx* c, const double* U, long long n_half, int K, const int* d_list,
+                                       int count) {
+  const int npairs = c->nB * (c->nB + 1) / 2;
+  const size_t smem = 8 * ((size_t)K * A64_PAIRS * 36 + A64_CELLS * (K | 1) + A64_CELLS * 145);
+  ROMB_CUDA(cudaFuncSetAttribute(assemble_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  dim3 grid((count + A64_CELLS - 1) / A64_CELLS, (npairs + A64_PAIRS - 1) / A64_PAIRS);
+  assemble_fp64_kernel<<<grid, 128, smem, c->stream>>>(U, n_half, K, d_list, count, c->d_pairs, npairs, c->ndof,
+                                                       c->d_theta, c->d_chat, c->d_K);
+  ++c->launches;
+  ROMB_CUDA(cudaGetLastError());
+  return ROMB_OK;
+}
+
 romb_status launch_pack_dense(romb_ctx* c, const double* d_dense) {
   pack_dense_kernel<<<4 * c->sms, 256, 0, c->stream>>>(d_dense, c->ndof, c->ncells, c->d_K); ++c->launches;
   ROMB_CUDA(cudaGetLastError());

@@ -24,6 +24,7 @@
 #define ROMB_FLAG_BAD_MAP 2
 #define ROMB_FLAG_NOT_SPD 4
 #define ROMB_FLAG_NAN 8
+#define ROMB_FLAG_EXACT 16   // K of the cell from the exact tensor (romb_set_exact_fallback)
 
 #define ROMB_CUDA(call)                                                     \
   do {                                                                      \
@@ -228,6 +229,7 @@ struct romb_ctx {
   // the coarse solve's B) in FP32, set by romb_factor
   bool pre32 = false;
   int precond_mode = -1;        // romb_set_precond_precision (survives a new lattice)
+  int fallback_max = 64;        // romb_set_exact_fallback (survives a new lattice)
   float* d_G32 = nullptr;       // [cells][nU][nU]
   float* d_Phi32 = nullptr;     // [cells][nU][20]
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
@@ -260,6 +262,8 @@ void romb_free_all(romb_ctx* c);
 // kernel launchers (each returns ROMB_OK or ROMB_E_CUDA)
 romb_status launch_theta(romb_ctx* c);
 romb_status launch_edge_functionals(romb_ctx* c);
+romb_status launch_assemble_cells_fp64(romb_ctx* c, const double* U, long long n_half, int K,
+                                      const int* d_list, int count);
 romb_status launch_assemble_fp64(romb_ctx* c);
 romb_status launch_assemble_tc(romb_ctx* c);
 romb_status launch_factor(romb_ctx* c);

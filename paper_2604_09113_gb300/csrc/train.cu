@@ -20,6 +20,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -385,19 +388,54 @@ void external_tensor(const Trainer& T, const romb_train_spec& sp, const double* 
 // Tables shared with the GPU trainer: the Legendre coefficients F of the 1D
 // factor products, the Gauss rule of one panel, and I_Pi (the untrimmed
 // tensor, from the moments e_0 e_0^T).
+// The tables depend on (family, basis, p, q) only; they are built once per
+// process and key (the exact fallback of romb_factor asks for them on every
+// factorisation that needs it).
+namespace {
+struct HostTables {
+  std::vector<double> F, gx, gw, Ipi;
+  int D = 0, nF = 0;
+};
+std::mutex g_tables_mu;
+std::map<std::tuple<int, int, int, int>, HostTables> g_tables;
+}  // namespace
+
 romb_status train_host_tables(const romb_train_spec* sp, std::vector<double>& F, int* D, int* nF,
                               std::vector<double>& gx, std::vector<double>& gw, std::vector<double>& Ipi) {
+  const auto key = std::make_tuple(sp->family, sp->basis, sp->p, sp->q);
+  {
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) {
+      F = it->second.F;
+      *D = it->second.D;
+      *nF = it->second.nF;
+      gx = it->second.gx;
+      gw = it->second.gw;
+      Ipi = it->second.Ipi;
+      return ROMB_OK;
+    }
+  }
   Trainer T;
   T.setup(*sp);
-  F = T.F;
-  *D = T.D;
-  *nF = T.nF;
-  gx = T.gx;
-  gw = T.gw;
-  Ipi.assign(T.n_i, 0.0);
+  HostTables H;
+  H.F = T.F;
+  H.D = T.D;
+  H.nF = T.nF;
+  H.gx = T.gx;
+  H.gw = T.gw;
+  H.Ipi.assign(T.n_i, 0.0);
   std::vector<double> M((size_t)(T.D + 1) * (T.D + 1), 0.0);
   M[0] = 1.0;
-  T.snapshot_from_moments(M.data(), Ipi.data());
+  T.snapshot_from_moments(M.data(), H.Ipi.data());
+  F = H.F;
+  *D = H.D;
+  *nF = H.nF;
+  gx = H.gx;
+  gw = H.gw;
+  Ipi = H.Ipi;
+  std::lock_guard<std::mutex> lk(g_tables_mu);
+  g_tables.emplace(key, std::move(H));
   return ROMB_OK;
 }
 

@@ -16,7 +16,9 @@ Checked against the oracle (tests/test_oracle_layout.py pins it):
     16-cluster model trained on the GPU, against the oracle's solve with the
     exact fast-assembly tensors: displacement within the ROM error (1e-2),
     iteration count within two (the paper's 15 for its own wrench geometry,
-    Sec. 5.2.2, is context: that geometry is not published).
+    Sec. 5.2.2, is context: that geometry is not published);
+  * at 7,290 cells, the exact fallback for a cell whose reduced stiffness is
+    indefinite: its K against the oracle's Algorithm 4 with the exact I(mu).
 """
 import os
 
@@ -172,13 +174,20 @@ def test_layout_errors(rom_paths):
         assert e.value.status == -10
 
 
-def test_wrench_p8_against_exact_fast_assembly(tmp_path):
-    path = os.path.join(str(tmp_path), "iwp.rom")
+@pytest.fixture(scope="module")
+def iwp_model(tmp_path_factory):
+    """The wrench's 16-cluster Schoen IWP model (n_r = 40, r = 6, 100 samples
+    per cluster on [-2.5, 2.5]^4), trained on the GPU."""
+    path = os.path.join(str(tmp_path_factory.mktemp("iwp")), "iwp.rom")
     romb.romb_train_gpu_clustered(LI.FAMILY_SCHOEN_IWP, 0, 8, 6, 40, -2.5, 2.5, 2,
                                   LI.cluster_samples(100, -2.5, 2.5, 2, seed=2007), path)
+    return path
+
+
+def test_wrench_p8_against_exact_fast_assembly(iwp_model):
     lat = LI.wrench(1, p=8)
     with romb.Context(0) as ctx:
-        romb.romb_train_load(ctx.h, path)
+        romb.romb_train_load(ctx.h, iwp_model)
         romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
         romb.romb_factor(ctx.h)
         u, its, rel = romb.romb_bddc_solve(ctx.h, _nodes(lat), rtol=1e-8, maxit=500)
@@ -192,3 +201,51 @@ def test_wrench_p8_against_exact_fast_assembly(tmp_path):
     ref = pipeline.solve(lat, K, rtol=1e-10, maxit=300)
     err = np.linalg.norm(u[0] - ref["u"]) / np.linalg.norm(ref["u"])
     assert err < 1e-2, (err, int(its[0]), ref["iters"])
+
+
+def test_wrench_7290_exact_fallback(iwp_model):
+    # at 7,290 cells the model's MDEIM error makes the stiffness of a nearly
+    # void cell indefinite: without the fallback the factorisation reports it
+    # (flag 4); with it the cell is assembled from its exact tensor (flag 16),
+    # whose K matches the oracle's Algorithm 4 with the exact I(mu), and the
+    # solve converges
+    from oracle import assembly, geometry, quadrature
+    from romb_testutil import unpack_upper
+    lat = LI.wrench(9, p=8)
+    n = int(lat.present.sum())
+    cells = lat.present_cells
+    with romb.Context(0) as ctx:
+        romb.romb_train_load(ctx.h, iwp_model)
+        romb.romb_set_exact_fallback(ctx.h, 0)
+        romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
+        try:
+            romb.romb_factor(ctx.h)
+            failed = None
+        except romb.RombError as e:
+            failed = e.status
+        _, flags0 = romb.romb_stats(ctx.h, n)
+        if failed is None:
+            pytest.skip("this model keeps every cell of the 7,290-cell wrench positive definite")
+        assert failed == -6 and np.any(flags0 & 4)
+        bad = np.nonzero(flags0 & 4)[0]
+        romb.romb_set_exact_fallback(ctx.h, 64)
+        romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
+        romb.romb_factor(ctx.h)
+        _, flags = romb.romb_stats(ctx.h, n)
+        assert np.array_equal(np.nonzero(flags & 16)[0], bad) and not np.any(flags & 4)
+        u, its, rel = romb.romb_bddc_solve(ctx.h, _nodes(lat), rtol=1e-8, maxit=800)
+        assert rel[0] <= 1e-8 and np.all(np.isfinite(u))
+        Kg = romb.romb_read(ctx.h, "K").reshape(n, -1)
+    nd = 2 * (lat.p + 1) ** 2
+    nB = (lat.p + 1) ** 2
+    I_pi = assembly.fa_tensor_untrimmed(lat.basis, lat.p, 2)
+    for b in bad:
+        c = int(cells[b])
+        P = geometry.cell_control_points(lat.ctrl, lat.nx, lat.m, c % lat.nx, c // lat.nx)
+        I = assembly.fa_tensor(lat.basis, lat.p, 2, quadrature.trimmed_rule(int(lat.family[c]), lat.mu[c]))
+        Ko = assembly.local_stiffness(I, I_pi, assembly.fa_coefficients(P, lat.E, lat.nu, 2), lat.rho, nB)
+        assert np.abs(unpack_upper(Kg[b], nd) - Ko).max() <= 1e-10 * np.abs(Ko).max()
+        # and it is positive definite on its interior block
+        interior = [2 * k + i for k in range(nB) for i in range(2)
+                    if 0 < k % (lat.p + 1) < lat.p and 0 < k // (lat.p + 1) < lat.p]
+        assert np.linalg.eigvalsh(Ko[np.ix_(interior, interior)]).min() > 0
