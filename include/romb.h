@@ -280,6 +280,8 @@ romb_status romb_stats(romb_ctx* ctx, double* phase_ms, int* flags_out);
  * in FP64 (theta of the cell set to (rho, 1 - rho) against [I_Pi; I(mu)]),
  * marks them with flag 16 and factorises again; a second failure returns
  * ROMB_E_NOT_SPD.  Off (max_cells = 0): the failure is returned at once.
+ * The exact tensors are kept per context and (family, mu), so a cell met
+ * again skips the quadrature (one snapshot takes ~0.3 s on one CTA).
  * Errors: ROMB_E_ARG (max_cells < 0). */
 romb_status romb_set_exact_fallback(romb_ctx* ctx, int max_cells);
 

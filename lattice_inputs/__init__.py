@@ -151,6 +151,12 @@ def lattice(nx: int, ny: int, p: int, m: int, *, seed: int, basis: int = 0,
     X = reference_grid(nx, ny, m)
     if geometry == "smooth":
         ctrl = X + smooth_field(X, seed, amplitude=amplitude)
+        # reject a field that folds the grid: every quadrilateral of the control
+        # grid keeps at least 0.2 of its undeformed area (scaled to a unit cell)
+        G = ctrl.reshape(m * ny + 1, m * nx + 1, 2)
+        ex, ey = G[:-1, 1:] - G[:-1, :-1], G[1:, :-1] - G[:-1, :-1]
+        if (m * m * (ex[..., 0] * ey[..., 1] - ex[..., 1] * ey[..., 0])).min() <= 0.2:
+            raise ValueError("the smooth field folds the control grid (orientation <= 0.2); pick another seed")
     elif geometry == "jitter":
         g = _rng(seed, STREAM_GEOMETRY)
         ctrl = X + g.uniform(-jitter, jitter, size=X.shape)

@@ -869,20 +869,29 @@ static romb_status exact_fallback(romb_ctx* c, bool* applied) {
     sp.hi = R.hi4[0];
     const int nB = (R.p + 1) * (R.p + 1), nL = (R.q + 1) * (R.q + 1);
     const long long n_i = (long long)nB * nB * nL * 4;
-    std::vector<double> I((size_t)n_i);
-    if ((s = romb_train_snapshots_gpu(c->device, &sp, &mu[4 * (size_t)b], 1, I.data())) != ROMB_OK) return s;
-    ROMB_CUDA(cudaSetDevice(c->device));
+    const std::vector<double> key = {(double)R.family, (double)R.kind, (double)R.p, (double)R.q, mu[4 * (size_t)b],
+                                     mu[4 * (size_t)b + 1], mu[4 * (size_t)b + 2], mu[4 * (size_t)b + 3]};
+    auto hit = c->exact_cache.find(key);
+    if (hit == c->exact_cache.end()) {
+      std::vector<double> I((size_t)n_i);
+      if ((s = romb_train_snapshots_gpu(c->device, &sp, &mu[4 * (size_t)b], 1, I.data())) != ROMB_OK) return s;
+      ROMB_CUDA(cudaSetDevice(c->device));
+      // row 1 of U': I(mu) in the pair-major half layout (row 0: the model's I_Pi)
+      std::vector<double> row((size_t)R.n_half);
+      long long pr = 0;
+      for (int k1 = 0; k1 < nB; ++k1)
+        for (int k2 = k1; k2 < nB; ++k2, ++pr)
+          for (int e = 0; e < nL * 4; ++e)
+            row[(size_t)(pr * nL * 4 + e)] = I[(size_t)(((long long)k1 * nB + k2) * nL * 4 + e)];
+      if (c->exact_cache.size() >= 256) c->exact_cache.clear();
+      hit = c->exact_cache.emplace(key, std::move(row)).first;
+    }
+    const std::vector<double>& row = hit->second;
     if (dU_n < 2 * R.n_half) {
       if (dU) romb_free_ptr(c, dU);
       if ((s = romb_alloc_t(c, &dU, 2 * (size_t)R.n_half)) != ROMB_OK) return s;
       dU_n = 2 * R.n_half;
     }
-    // row 1 of U': I(mu) in the pair-major half layout (row 0: the model's I_Pi)
-    std::vector<double> row((size_t)R.n_half);
-    long long pr = 0;
-    for (int k1 = 0; k1 < nB; ++k1)
-      for (int k2 = k1; k2 < nB; ++k2, ++pr)
-        for (int e = 0; e < nL * 4; ++e) row[(size_t)(pr * nL * 4 + e)] = I[(size_t)(((long long)k1 * nB + k2) * nL * 4 + e)];
     std::vector<double> th(128, 0.0);
     th[0] = c->rho;
     th[1] = 1.0 - c->rho;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -230,6 +231,9 @@ struct romb_ctx {
   bool pre32 = false;
   int precond_mode = -1;        // romb_set_precond_precision (survives a new lattice)
   int fallback_max = 64;        // romb_set_exact_fallback (survives a new lattice)
+  // exact tensors of the fallback, row 1 of U' in the half layout, keyed by
+  // (family, basis, p, q, mu): a cell met again skips the quadrature
+  std::map<std::vector<double>, std::vector<double>> exact_cache;
   float* d_G32 = nullptr;       // [cells][nU][nU]
   float* d_Phi32 = nullptr;     // [cells][nU][20]
   int* d_cowner = nullptr;      // [ncoarse_all][4] cell*20 + slot of each owner (-1 none)
