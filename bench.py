@@ -776,7 +776,7 @@ def run_workload5(a):
 
 
 def run_workload6(a):
-    """The paper's benchmark lattice (Sec. 5.2, Eq. RES multi map): quarter
+    """The paper's benchmark lattice (Sec. 5.1.2, Eq. RES multi map): quarter
     annulus, Schwarz Diamond cells with thresholds 0.9 - 0.8 s, p = 8,
     rho = 5e-4, E = 5, nu = 0.25, clamped at s = 0, traction 0.1 downward at
     s = 1; reduced models with n_k = 2 (16 clusters), n_r = 40, r = 6 and 100

@@ -273,7 +273,7 @@ romb_status romb_stats(romb_ctx* ctx, double* phase_ms, int* flags_out);
 
 /* Fallback for cells whose reduced-model stiffness is not positive definite
  * (the MDEIM error of a nearly void cell can exceed the alpha-stabilisation
- * rho I_Pi; Sec. 4.3 asks to retrain such models).  On (default), when
+ * rho I_Pi; Sec. 5.1.2 asks to retrain such models).  On (default), when
  * romb_factor meets a non-positive pivot in at most max_cells cells of a
  * reduced-model assembly, it integrates those cells' tensors I(mu) exactly
  * (the trimmed quadrature of the GPU trainer), forms their K by Algorithm 4

@@ -189,7 +189,7 @@ def lattice(nx: int, ny: int, p: int, m: int, *, seed: int, basis: int = 0,
 
 def quarter_annulus(nx: int, ny: int, p: int = 8, m: int = 4, r0: float = 0.6, r1: float = 1.0,
                     rho: float = 5e-4, name: str = "") -> Lattice:
-    """The benchmark lattice of Sec. 5.2 (Eq. RES multi map): nx x ny cells of
+    """The benchmark lattice of Sec. 5.1.2 (Eq. RES multi map): nx x ny cells of
     the auxiliary square, mapped onto the quarter annulus r0 <= r <= r1 by
     x = r sin(pi/2 s), y = -r cos(pi/2 s), Schwarz Diamond cells with the
     vertex thresholds 0.9 - 0.8 s (s the first auxiliary coordinate), E = 5,

@@ -1,4 +1,4 @@
-"""The paper's benchmark on the GPU (Sec. 5.2, Eq. RES multi map): quarter
+"""The paper's benchmark on the GPU (Sec. 5.1.2, Eq. RES multi map): quarter
 annulus of 64 x 32 Schwarz Diamond cells, thresholds 0.9 - 0.8 s, p = 8,
 rho = 5e-4, q = 2, models with n_k = 2 (16 clusters), n_r = 40, r = 6 and
 100 samples per cluster (Sec. 4.3), trained by the library's GPU trainer.
@@ -7,7 +7,7 @@ Checked: the PCG iteration count against Table RES weak's first row (15;
 within two, the paper does not name its residual norm); the displacement
 against the oracle's solution with the exact fast-assembly tensors (no ROM),
 which differ by the ROM error (the paper sizes its models so that this error
-is of the order of the fast-assembly error, 1e-3, Sec. 5.2.2): within 1e-2
+is of the order of the fast-assembly error, 1e-3, Sec. 5.1.2): within 1e-2
 relative L2; the TF32 split form within 1e-6 of the FP64 form."""
 import os
 

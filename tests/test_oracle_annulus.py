@@ -1,4 +1,4 @@
-"""Pins of the oracle on the paper's benchmark lattice (Sec. 5.2, Eq. RES multi
+"""Pins of the oracle on the paper's benchmark lattice (Sec. 5.1.2, Eq. RES multi
 map: quarter annulus, Schwarz Diamond cells with thresholds 0.9 - 0.8 s,
 p = 8, rho = 5e-4, q = 2) and of the edge parts over which the coarse
 functionals of Sec. 3.3.1 integrate."""
