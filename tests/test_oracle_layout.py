@@ -138,3 +138,22 @@ def test_wrench_layout(scale, cells):
             assert np.linalg.det(geometry.map_eval(P, a, b)[1]).min() > 0
         left = lat.present.reshape(lat.ny, lat.nx)[:, 0]
         assert np.array_equal(np.nonzero(left)[0], [2, 3, 4])
+
+
+def test_wrench_bddc_against_direct_solve():
+    # the 90-cell wrench-like layout (Schoen IWP cells, clamped hole, loaded
+    # handle) at p = 4 with the exact fast-assembly tensors: the BDDC solve
+    # against a direct solve of the assembled system
+    from oracle import offline
+    lat = LI.wrench(1, p=4)
+    with offline._pool(None) as pool:
+        T = pipeline.fa_tensors(lat, pmap=pool.map)
+    K = pipeline.matrices_fa(lat, T)
+    fstar = bddc.lattice_loads(lat)
+    r = pipeline.solve(lat, K, fstar, rtol=1e-12, maxit=400)
+    ref = bddc.direct_solve(lat, K, fstar)
+    assert np.linalg.norm(r["u"] - ref) <= 1e-9 * np.linalg.norm(ref)
+    # the load acts downward on the handle's end: the handle bends down
+    L = r["bddc"].L
+    end = [gy * L.gnx for gy in range(2 * lat.p, 5 * lat.p + 1)]
+    assert np.all(r["u"][end, 1] < 0)
