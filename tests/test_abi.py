@@ -50,3 +50,35 @@ def test_autograd_binding_imports():
     torch = pytest.importorskip("torch")
     from paper_2604_09113_gb300.autograd import Compliance, compliance
     assert issubclass(Compliance, torch.autograd.Function) and callable(compliance)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes structures of the binding against the C compiler's layout of
+    # romb_lattice and romb_train_spec (size and every field offset)
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    _build()
+    import paper_2604_09113_gb300 as romb
+    structs = {"romb_lattice": romb.RombLattice, "romb_train_spec": romb.RombTrainSpec}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "romb.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, what, val = line.split()
+            got[(cname, what)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

@@ -157,3 +157,16 @@ def test_wrench_bddc_against_direct_solve():
     L = r["bddc"].L
     end = [gy * L.gnx for gy in range(2 * lat.p, 5 * lat.p + 1)]
     assert np.all(r["u"][end, 1] < 0)
+
+
+def test_input_generator_rejects_folded_grids():
+    # the smooth displacement field is rescaled to the requested amplitude; an
+    # amplitude of the order of the cell size folds the control grid and the
+    # generator refuses it (the workloads' 0.1 keeps every quadrilateral's
+    # orientation near 1)
+    with pytest.raises(ValueError):
+        LI.lattice(6, 6, 4, 2, seed=3, amplitude=3.0)
+    lat = LI.lattice(6, 6, 4, 2, seed=3)
+    G = lat.ctrl.reshape(2 * 6 + 1, 2 * 6 + 1, 2)
+    ex, ey = G[:-1, 1:] - G[:-1, :-1], G[1:, :-1] - G[:-1, :-1]
+    assert (4 * (ex[..., 0] * ey[..., 1] - ex[..., 1] * ey[..., 0])).min() > 0.5
