@@ -12,7 +12,9 @@ the force model (ROMB_LOADS_REDUCED) and solves.  Checked:
     loads, 1e-8 relative L2 (rtol 1e-12 on both sides);
   * that the reduced loads stay close to the direct edge quadrature (the
     force model and the edge-Jacobian interpolation together, 3e-3);
-  * the argument and state errors of romb_set_load_form.
+  * the argument and state errors of romb_set_load_form;
+  * body forces with the tractions, also on a layout with absent cells and a
+    clamped notch (present cells only), against the oracle at 1e-8.
 """
 import os
 
@@ -170,3 +172,34 @@ def test_body_forces_against_oracle(body_models):
     # and without the body force the tractions alone
     ref0 = pipeline.solve(lat, K, force_rom.lattice_loads_rom(lat, body_models["roms"], tr[0]), rtol=1e-12)
     assert np.linalg.norm(u0[0] - ref0["u"]) / np.linalg.norm(ref0["u"]) < 1e-8
+
+
+def test_reduced_and_body_loads_on_a_layout(body_models):
+    # a layout with an absent block and a clamped notch: the reduced traction
+    # and body loads of the present cells only, against the oracle's solve
+    p = body_models["p"]
+    lat = _lattice(7, 5, p, 35)
+    cx, cy = np.meshgrid(np.arange(lat.nx), np.arange(lat.ny), indexing="xy")
+    cx, cy = cx.ravel(), cy.ravel()
+    lat.present = ~((cx >= 2) & (cx <= 3) & (cy >= 3))
+    ec = np.zeros((lat.ncells, 4), dtype=bool)
+    ec[lat.present & (cy == 2) & (cx >= 2) & (cx <= 3), 3] = True   # the notch's floor clamped
+    lat.edge_clamped = ec
+    lat.mu[~lat.present] = 99.0
+    lat.family[~lat.present] = 7
+    tr = _traction()
+    body = np.array([-0.4, -1.1])
+    nodes = (p * lat.nx + 1) * (p * lat.ny + 1)
+    with romb.Context(0) as ctx:
+        for path in body_models["paths"]:
+            romb.romb_train_load(ctx.h, path)
+        romb.romb_assemble(ctx.h, lat, romb.ROMB_FP64)
+        romb.romb_factor(ctx.h)
+        romb.romb_set_load_form(ctx.h, romb.ROMB_LOADS_REDUCED)
+        romb.romb_set_body_force(ctx.h, *body)
+        u, its, _ = romb.romb_bddc_solve(ctx.h, nodes, traction_sets=tr, rtol=1e-12, maxit=400)
+    fo = force_rom.lattice_loads_rom(lat, body_models["roms"], tr[0], body)
+    K = pipeline.matrices_rom(lat, body_models["roms"])
+    ref = pipeline.solve(lat, K, fo, rtol=1e-12)
+    err = np.linalg.norm(u[0] - ref["u"]) / np.linalg.norm(ref["u"])
+    assert err < 1e-8, (err, its, ref["iters"])
